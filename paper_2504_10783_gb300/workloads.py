@@ -1,0 +1,255 @@
+"""Seeded synthetic inputs: robot models, obstacle sets and candidate waypoints.
+
+This module only builds input data (kinematic parameters, sphere placements,
+obstacle spheres, random waypoints). It contains none of the edge-inflation
+arithmetic: no forward kinematics, no collision test, no sampling, no
+hyperplane placement. Both the CUDA path and the FP64 oracle consume what it
+returns, so it must stay free of either side's computation.
+
+The paper assumes a robot description with kinematics and collision geometry
+(Sec. II) and obstacles given as spheres around perceived voxels (Sec. V-B).
+Its own robot models (FR3, iiwa) are not published, so the workloads here are
+synthetic stand-ins with the same structure:
+
+* ``planar3`` - planar 3-link revolute arm, links of 1.0 m, 4 spheres of
+  r = 0.1 m per link, self pairs between links 1 and 3 only.
+* ``dh7`` - 7-DOF serial arm in standard DH form, 40 spheres along the four
+  links with non-zero offset d, radii tapering from 0.08 m to 0.04 m, self
+  pairs between all non-adjacent sphere-carrying links.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "Robot",
+    "Env",
+    "planar3_robot",
+    "dh7_robot",
+    "planar_disks_candidates",
+    "box_obstacles",
+    "table_cloud_obstacles",
+    "uniform_configs",
+    "random_walk_waypoints",
+]
+
+
+@dataclasses.dataclass
+class Robot:
+    """Serial chain in standard DH form with spheres fixed to its frames.
+
+    Frame 0 is the base (identity). Frame i (1..n) is
+    T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i).
+    Sphere s sits at ``sphere_xyz[s]`` in frame ``sphere_frame[s]`` with radius
+    ``sphere_r[s]``; ``sphere_link`` is a link id used only to build self pairs.
+    """
+
+    name: str
+    a: np.ndarray
+    alpha: np.ndarray
+    d: np.ndarray
+    theta_off: np.ndarray
+    q_lo: np.ndarray
+    q_hi: np.ndarray
+    sphere_frame: np.ndarray  # int32 [N_s]
+    sphere_xyz: np.ndarray  # float64 [N_s, 3]
+    sphere_r: np.ndarray  # float64 [N_s]
+    sphere_link: np.ndarray  # int32 [N_s]
+    self_pairs: np.ndarray  # int32 [P, 2]
+
+    @property
+    def n(self) -> int:
+        return int(self.a.shape[0])
+
+    @property
+    def n_spheres(self) -> int:
+        return int(self.sphere_r.shape[0])
+
+    def to_json(self) -> dict:
+        return {k: (v.tolist() if isinstance(v, np.ndarray) else v)
+                for k, v in dataclasses.asdict(self).items()}
+
+    @staticmethod
+    def from_json(d: dict) -> "Robot":
+        ints = {"sphere_frame", "sphere_link", "self_pairs"}
+        kw = {}
+        for f in dataclasses.fields(Robot):
+            v = d[f.name]
+            if f.name == "name":
+                kw[f.name] = v
+            elif f.name in ints:
+                kw[f.name] = np.asarray(v, dtype=np.int32).reshape(-1, 2) if f.name == "self_pairs" \
+                    else np.asarray(v, dtype=np.int32)
+            else:
+                kw[f.name] = np.asarray(v, dtype=np.float64)
+        kw["sphere_xyz"] = kw["sphere_xyz"].reshape(-1, 3)
+        return Robot(**kw)
+
+
+@dataclasses.dataclass
+class Env:
+    """Obstacle spheres, one row (x, y, z, radius) each."""
+
+    name: str
+    spheres: np.ndarray  # float64 [N_obs, 4]
+
+    @property
+    def n_obs(self) -> int:
+        return int(self.spheres.shape[0])
+
+
+def _pairs_between_links(link: np.ndarray, link_pairs) -> np.ndarray:
+    out = []
+    for la, lb in link_pairs:
+        ia = np.nonzero(link == la)[0]
+        ib = np.nonzero(link == lb)[0]
+        for i in ia:
+            for j in ib:
+                out.append((int(i), int(j)))
+    return np.asarray(out, dtype=np.int32).reshape(-1, 2)
+
+
+def planar3_robot(link_len: float = 1.0, spheres_per_link: int = 4, r: float = 0.1) -> Robot:
+    """Planar 3R arm: DH a_i = link_len, alpha = d = 0, limits [-pi, pi]^3.
+
+    With standard DH, frame i sits at the distal end of link i and its x axis
+    runs along the link, so a sphere a fraction f along link i (from the
+    proximal joint) is the point ((f - 1) * link_len, 0, 0) of frame i.
+    Spheres sit at f = (j + 0.5) / spheres_per_link.
+    """
+    n = 3
+    frames, xyz, rad, link = [], [], [], []
+    for i in range(1, n + 1):
+        for j in range(spheres_per_link):
+            f = (j + 0.5) / spheres_per_link
+            frames.append(i)
+            xyz.append(((f - 1.0) * link_len, 0.0, 0.0))
+            rad.append(r)
+            link.append(i)
+    link = np.asarray(link, dtype=np.int32)
+    return Robot(
+        name="planar3",
+        a=np.full(n, link_len), alpha=np.zeros(n), d=np.zeros(n), theta_off=np.zeros(n),
+        q_lo=np.full(n, -math.pi), q_hi=np.full(n, math.pi),
+        sphere_frame=np.asarray(frames, dtype=np.int32),
+        sphere_xyz=np.asarray(xyz, dtype=np.float64),
+        sphere_r=np.asarray(rad, dtype=np.float64),
+        sphere_link=link,
+        self_pairs=_pairs_between_links(link, [(1, 3)]),
+    )
+
+
+DH7_D = (0.34, 0.0, 0.40, 0.0, 0.40, 0.0, 0.126)
+DH7_ALPHA = (-math.pi / 2, math.pi / 2, math.pi / 2, -math.pi / 2, -math.pi / 2, math.pi / 2, 0.0)
+DH7_LIMITS = (2.9, 2.0, 2.9, 2.0, 2.9, 2.0, 3.0)
+DH7_SPHERES_PER_LINK = (11, 13, 12, 4)
+
+
+def dh7_robot(r_base: float = 0.08, r_tip: float = 0.04) -> Robot:
+    """7-DOF arm, standard DH with a = 0.
+
+    Joint i with d_i != 0 (i = 1, 3, 5, 7) carries a link from the origin of
+    frame i-1 to the origin of frame i along the z axis of frame i-1, i.e. the
+    points (0, 0, f d_i) of frame i-1. The four links get 11, 13, 12 and 4
+    spheres at f = (j + 0.5) / count; the radius tapers linearly with arc
+    length along the chain from r_base at the base to r_tip at the tip.
+    Self pairs: every sphere of link A against every sphere of link B for the
+    non-adjacent link pairs (1, 3), (1, 4), (2, 4).
+    """
+    d = np.asarray(DH7_D)
+    total = float(d.sum())
+    frames, xyz, rad, link = [], [], [], []
+    arc0 = 0.0
+    lid = 0
+    for i in range(7):
+        if d[i] == 0.0:
+            continue
+        cnt = DH7_SPHERES_PER_LINK[lid]
+        lid += 1
+        for j in range(cnt):
+            f = (j + 0.5) / cnt
+            arc = arc0 + f * d[i]
+            frames.append(i)  # frame i-1 in 1-based joint numbering
+            xyz.append((0.0, 0.0, f * d[i]))
+            rad.append(r_base + (r_tip - r_base) * arc / total)
+            link.append(lid)
+        arc0 += d[i]
+    link = np.asarray(link, dtype=np.int32)
+    lim = np.asarray(DH7_LIMITS)
+    return Robot(
+        name="dh7",
+        a=np.zeros(7), alpha=np.asarray(DH7_ALPHA), d=d, theta_off=np.zeros(7),
+        q_lo=-lim, q_hi=lim,
+        sphere_frame=np.asarray(frames, dtype=np.int32),
+        sphere_xyz=np.asarray(xyz, dtype=np.float64),
+        sphere_r=np.asarray(rad, dtype=np.float64),
+        sphere_link=link,
+        self_pairs=_pairs_between_links(link, [(1, 3), (1, 4), (2, 4)]),
+    )
+
+
+def planar_disks_candidates(seed: int, count: int, lo: float = -2.5, hi: float = 2.5,
+                            r_lo: float = 0.1, r_hi: float = 0.3) -> np.ndarray:
+    """Candidate obstacle disks in the plane z = 0: centres uniform in
+    [lo, hi]^2, radii uniform in [r_lo, r_hi]. Rows are (x, y, 0, r)."""
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(lo, hi, size=(count, 2))
+    r = rng.uniform(r_lo, r_hi, size=count)
+    return np.column_stack([xy, np.zeros(count), r])
+
+
+def box_obstacles(seed: int, count: int, box_lo=(0.5, -0.5, 0.0), box_hi=(1.5, 0.5, 1.0),
+                  r_lo: float = 0.02, r_hi: float = 0.10, name: str = "box") -> Env:
+    """Obstacle spheres with centres uniform in an axis-aligned box and radii
+    uniform in [r_lo, r_hi] (default: the 1 m cube 0.5 m ahead of the base)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(np.asarray(box_lo), np.asarray(box_hi), size=(count, 3))
+    r = rng.uniform(r_lo, r_hi, size=count)
+    return Env(name=name, spheres=np.column_stack([c, r]))
+
+
+def table_cloud_obstacles(seed: int, count: int = 1024, r: float = 0.02, voxel: float = 0.02,
+                          table_lo=(0.3, -0.4), table_hi=(1.3, 0.4), table_z: float = 0.0,
+                          n_clusters: int = 6, cluster_pts: int = 80, sigma: float = 0.05,
+                          cluster_z: float = 0.1) -> Env:
+    """Perception-like obstacle set: a planar table sampled on a ``voxel`` grid
+    plus Gaussian clusters of object points on it, voxelised at ``voxel`` and
+    reduced to ``count`` spheres of radius ``r`` at distinct voxel centres by a
+    seeded random subset."""
+    rng = np.random.default_rng(seed)
+    nx = int(round((table_hi[0] - table_lo[0]) / voxel)) + 1
+    ny = int(round((table_hi[1] - table_lo[1]) / voxel)) + 1
+    gx, gy = np.meshgrid(table_lo[0] + voxel * np.arange(nx), table_lo[1] + voxel * np.arange(ny),
+                         indexing="ij")
+    table = np.column_stack([gx.ravel(), gy.ravel(), np.full(gx.size, table_z)])
+    centres = np.column_stack([rng.uniform(table_lo[0], table_hi[0], n_clusters),
+                               rng.uniform(table_lo[1], table_hi[1], n_clusters),
+                               np.full(n_clusters, cluster_z)])
+    pts = [table]
+    for c in centres:
+        p = c + sigma * rng.standard_normal((cluster_pts, 3))
+        pts.append(p[p[:, 2] >= table_z])
+    pts = np.concatenate(pts)
+    vox = np.unique(np.floor(pts / voxel + 0.5).astype(np.int64), axis=0)
+    if vox.shape[0] > count:
+        vox = vox[np.sort(rng.choice(vox.shape[0], size=count, replace=False))]
+    cen = vox.astype(np.float64) * voxel
+    return Env(name="table_cloud", spheres=np.column_stack([cen, np.full(cen.shape[0], r)]))
+
+
+def uniform_configs(seed: int, robot: Robot, count: int) -> np.ndarray:
+    """Configurations uniform in the joint-limit box, shape [count, n]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(robot.q_lo, robot.q_hi, size=(count, robot.n))
+
+
+def random_walk_waypoints(rng: np.random.Generator, robot: Robot, start: np.ndarray,
+                          step: float, shrink: float = 0.8) -> np.ndarray:
+    """One candidate next waypoint: a random direction of length ``step`` from
+    ``start``, clipped to ``shrink`` times the joint limits."""
+    d = rng.standard_normal(robot.n)
+    d *= step / np.linalg.norm(d)
+    return np.clip(start + d, shrink * robot.q_lo, shrink * robot.q_hi)

@@ -1,0 +1,155 @@
+"""Write tests/golden/workloads.json: the seeded synthetic scenes whose
+collision-freeness needs a collision checker, checked by the FP64 oracle only.
+
+* planar3 scene: one seed segment L between two collision-free configurations
+  and 16 obstacle disks (centres uniform in [-2.5, 2.5]^2, r in [0.1, 0.3])
+  drawn one by one and rejected when they come within ``margin`` of the arm
+  anywhere along L.
+* dh7 scene: 64 obstacle spheres in the 1 m cube 0.5 m ahead of the base and
+  a 10-segment seed path from a random walk of 0.5 rad steps inside 0.8x the
+  joint limits; every segment is checked at <= 0.005 rad spacing and kept
+  only when the oracle's signed distance is >= ``margin`` at every check
+  point (the margin bounds how far the arm moves between check points, so the
+  whole segment is collision-free).
+* dh7 batched scenes: 8 obstacle sets of 128-1024 spheres in the same cube
+  and 256 seed paths of 1-40 segments built the same way (written only when
+  ``--batched`` is given; slower).
+* table_cloud scene: 1024 spheres of r = 0.02 from a synthetic table point
+  cloud and a 64-segment seed path (``--stress``).
+
+Run from the repository root:  python tests/golden/make_workloads.py
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import ezo_oracle as orc  # noqa: E402
+from paper_2504_10783_gb300 import workloads as wl  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads.json")
+
+
+def segment_clearance(robot, env, v1, v2, spacing=0.005):
+    n = max(2, int(math.ceil(np.linalg.norm(v2 - v1) / spacing)) + 1)
+    t = np.linspace(0.0, 1.0, n)[:, None]
+    q = (1.0 - t) * v1 + t * v2
+    return float(orc.signed_distance(robot, env, q).min())
+
+
+def planar_scene(seed=7, n_obs=16, margin=0.03):
+    robot = wl.planar3_robot()
+    rng = np.random.default_rng(seed)
+    empty = wl.Env("none", np.zeros((0, 4)))
+    while True:
+        v1 = rng.uniform(0.8 * robot.q_lo, 0.8 * robot.q_hi)
+        step = rng.standard_normal(3)
+        v2 = np.clip(v1 + 1.2 * step / np.linalg.norm(step), 0.8 * robot.q_lo, 0.8 * robot.q_hi)
+        if segment_clearance(robot, empty, v1, v2) >= margin:
+            break
+    t = np.linspace(0.0, 1.0, 400)[:, None]
+    swept = orc.sphere_centres(robot, (1.0 - t) * v1 + t * v2).reshape(-1, 3)
+    obs = []
+    cand_seed = seed * 1000
+    while len(obs) < n_obs:
+        cand = wl.planar_disks_candidates(cand_seed, 64)
+        cand_seed += 1
+        for o in cand:
+            d = np.linalg.norm(swept[:, :2] - o[None, :2], axis=1) - 0.1 - o[3]
+            if d.min() >= margin:
+                obs.append(o)
+                if len(obs) == n_obs:
+                    break
+    env = wl.Env("planar_disks", np.asarray(obs))
+    assert segment_clearance(robot, env, v1, v2) >= margin
+    return {"robot": "planar3", "v1": v1.tolist(), "v2": v2.tolist(), "obstacles": env.spheres.tolist(),
+            "seed": seed, "margin": margin}
+
+
+def random_path(robot, env, rng, n_seg, step=0.5, margin=0.02, tries=400):
+    while True:
+        v = rng.uniform(0.8 * robot.q_lo, 0.8 * robot.q_hi)
+        if orc.signed_distance(robot, env, v[None])[0] >= 2 * margin:
+            break
+    verts = [v]
+    while len(verts) < n_seg + 1:
+        for _ in range(tries):
+            nxt = wl.random_walk_waypoints(rng, robot, verts[-1], step)
+            if segment_clearance(robot, env, verts[-1], nxt) >= margin:
+                verts.append(nxt)
+                break
+        else:
+            return None
+    return np.asarray(verts)
+
+
+def dh7_scene(seed=11, n_obs=64, n_seg=10):
+    robot = wl.dh7_robot()
+    env = wl.box_obstacles(seed, n_obs)
+    rng = np.random.default_rng(seed + 1)
+    path = None
+    while path is None:
+        path = random_path(robot, env, rng, n_seg)
+    return {"robot": "dh7", "env_seed": seed, "n_obs": n_obs, "path": path.tolist()}
+
+
+def batched_scenes(seed=21, n_env=8, n_paths=256):
+    robot = wl.dh7_robot()
+    rng = np.random.default_rng(seed)
+    envs = []
+    for e in range(n_env):
+        cnt = int(rng.integers(128, 1025))
+        envs.append({"env_seed": seed * 100 + e, "n_obs": cnt})
+    paths = []
+    for p in range(n_paths):
+        e = int(rng.integers(0, n_env))
+        env = wl.box_obstacles(envs[e]["env_seed"], envs[e]["n_obs"])
+        nseg = int(rng.integers(1, 41))
+        path = None
+        while path is None:
+            path = random_path(robot, env, rng, nseg)
+        paths.append({"env": e, "path": path.tolist()})
+        print(f"batched path {p}: env {e}, {nseg} segments", flush=True)
+    return {"robot": "dh7", "envs": envs, "paths": paths}
+
+
+def stress_scene(seed=31, n_seg=64):
+    robot = wl.dh7_robot()
+    env = wl.table_cloud_obstacles(seed)
+    rng = np.random.default_rng(seed + 1)
+    path = None
+    while path is None:
+        path = random_path(robot, env, rng, n_seg)
+    return {"robot": "dh7", "cloud_seed": seed, "path": path.tolist()}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--batched", action="store_true")
+    ap.add_argument("--stress", action="store_true")
+    args = ap.parse_args()
+    data = {}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            data = json.load(f)
+    data["planar3"] = planar_scene()
+    data["dh7"] = dh7_scene()
+    if args.batched:
+        data["dh7_batched"] = batched_scenes()
+    if args.stress:
+        data["table_cloud"] = stress_scene()
+    with open(OUT, "w") as f:
+        json.dump(data, f, indent=1)
+    print("wrote", OUT)
+
+
+if __name__ == "__main__":
+    main()
