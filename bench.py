@@ -1,0 +1,330 @@
+"""Benchmark of the EI-ZO hot path on GB300.
+
+One step = inflating the 10-segment seed path of the 7-DOF arm (40 spheres,
+64 obstacle spheres) at eps = delta = 0.05 (N_p = 10^4, N_f = 10, N_ms = 60,
+N_b = 10, N_it = 50): every round of Algorithm 1 for every segment (all
+segments speculatively in one batched run, then the containment skip of
+Sec. VI-A). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode graph|host]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded samples)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "configs collision-checked/s; ms per 10-segment SCS inflation at ε=δ=0.05"
+WORKLOAD = ("7-DOF DH arm (d=[0.34,0,0.40,0,0.40,0,0.126], 40 spheres r 0.04-0.08, 228 self pairs), "
+            "64 obstacle spheres in the 1 m cube 0.5 m ahead, 10-segment collision-free seed path, "
+            "eps=delta=0.05, tau=0.5, N_p=1e4, N_f=10, N_ms=60, N_b=10, Delta_max=0.01, N_it=50")
+PARAMS = dict(eps=0.05, delta=0.05, tau=0.5, step_back_max=0.01, t_col=1e-3, n_p=10000, n_f=10, n_b=10, n_mix=60,
+              n_it_max=50, seed=1)
+KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
+
+
+def load_scene():
+    from paper_2504_10783_gb300 import workloads as wl
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        s = json.load(f)["dh7"]
+    return wl.dh7_robot(), wl.box_obstacles(s["env_seed"], s["n_obs"]), np.asarray(s["path"])
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle legs --
+def oracle_sample(seconds: float, seg_list=None):
+    """Runs the FP64 oracle on segments of the bench path until `seconds`
+    have passed; returns (checks, elapsed, segments inflated, rounds)."""
+    from oracle import ezo_oracle as orc
+    rd, env, path = load_scene()
+    prm = orc.Params(**PARAMS)
+    A0, b0 = orc.joint_box(rd)
+    checks = rounds = segs = 0
+    t0 = time.perf_counter()
+    for k in (seg_list if seg_list is not None else range(path.shape[0] - 1)):
+        res = orc.eizo(rd, env, path[k], path[k + 1], A0, b0, prm, stream=k)
+        checks += res.checks
+        rounds += res.rounds
+        segs += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return checks, time.perf_counter() - t0, segs, rounds
+
+
+def cpu_leg(seconds: float):
+    checks, el, segs, rounds = oracle_sample(seconds)
+    print(json.dumps({"checks": checks, "seconds": el, "segments": segs, "rounds": rounds}))
+
+
+def run_cpu_baseline(seconds: float = 15.0) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "--seconds", str(seconds)],
+                         capture_output=True, text=True, env=env, timeout=600)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    v = d["checks"] / d["seconds"]
+    return {"value": v, "unit": "configs/s", "cores": 1, "kind": "oracle",
+            "ms_per_segment": 1e3 * d["seconds"] / d["segments"],
+            "sample": f"FP64 numpy oracle, Algorithm 1 on the first {d['segments']} segment(s) of the bench path "
+                      f"({d['rounds']} rounds, {d['checks']} exact checks) in {d['seconds']:.1f} s on 1 host thread"}
+
+
+def oracle_round(seg: int):
+    """One round (k = 1) of Algorithm 1 on segment `seg` of the bench path with
+    the oracle: sampling, labels, test, bisection, placement."""
+    from oracle import ezo_oracle as orc
+    rd, env, path = load_scene()
+    prm = orc.Params(**PARAMS)
+    A0, b0 = orc.joint_box(rd)
+    t0 = time.perf_counter()
+    ns = orc.batch_size(1, prm.eps, prm.delta, prm.tau, prm.n_p)
+    S = orc.hit_and_run(A0, b0, path[seg], path[seg + 1], ns, prm.n_mix, prm.seed, seg, 1)
+    rr = orc.eizo_round(rd, env, A0, b0, path[seg], path[seg + 1], 1, prm, S)
+    return ns + rr.cand_index.shape[0] * prm.n_b, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    _, _, path = load_scene()
+    K = path.shape[0] - 1
+    for w in range(args.warmup):
+        oracle_round(w % K)
+    tot_c = 0
+    tot_t = 0.0
+    segs = 0
+    for s in range(args.steps):
+        c, t = oracle_round(s % K)
+        tot_c += c
+        tot_t += t
+        segs += 1
+    v = tot_c / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "configs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + "; one step = round 1 of Algorithm 1 on one segment of the path",
+                       "l2": "host oracle"},
+            "cpu_baseline": {"value": v, "unit": "configs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"round 1 of {segs} segment inflations of the bench path, FP64 numpy oracle"},
+            "e2e": {"value": v, "unit": "configs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------- GPU leg --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="graph", choices=["graph", "host"])
+    ap.add_argument("--cpu-leg", action="store_true")
+    ap.add_argument("--seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_leg:
+        cpu_leg(args.seconds)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_10783_gb300 import ezo
+
+    rd, env_np, path = load_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    K = path.shape[0] - 1
+    prm = ezo.Params.make(**PARAMS)
+    mode = ezo.RUN_GRAPH if args.mode == "graph" else ezo.RUN_HOST_LOOP
+    streams = np.arange(K, dtype=np.uint32) + 1000 * rank  # each rank inflates its own random draw
+    bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm, seg_stream=streams, path_first=np.zeros(K, np.int32))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step():
+        bt.reset()
+        bt.run_path(sequential=False, mode=mode)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs, L2 flushed between steps ----
+    ezo.profile_enable(mode == ezo.RUN_HOST_LOOP)
+    ezo.profile_reset()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    times = []
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        launches += 7 * bt.summary()["rounds"] + 1
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    prof = ezo.profile_read()
+    ezo.profile_enable(False)
+    ms = float(np.sum(times))
+    samp = bisc = 0
+    kept = 0
+    for g in range(K):
+        a, b_ = bt.check_split(g)
+        samp += a
+        bisc += b_
+        kept += bt.segment(g).status != ezo.SEG_SKIPPED
+    checks_per_step = samp + bisc
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * checks_per_step * args.steps / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (FP32 ALU bound) ----
+    flops_cfg = ezo.check_flops(robot, env)
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA
+    roofline = None
+    if mode == ezo.RUN_HOST_LOOP and prof["bisect"][1] > 0:
+        work = {"check": samp * flops_cfg * args.steps, "bisect": bisc * flops_cfg * args.steps}
+        dom = max(("check", "bisect"), key=lambda k: prof[k][0])
+        ach = work[dom] / (prof[dom][0] / 1e3) / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "per_launch_ms": prof[dom][0] / prof[dom][1],
+                    "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                    "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+
+    # ---- end to end through the public API with host buffers ----
+    v1h = np.ascontiguousarray(path[:-1])
+    v2h = np.ascontiguousarray(path[1:])
+    e2e_times = []
+    d2h = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt.reset(v1h, v2h)
+        bt.run_path(sequential=False, mode=mode)
+        d2h = 0
+        for g in range(K):
+            r = bt.segment(g)
+            if r.status != ezo.SEG_SKIPPED:
+                d2h += r.A.nbytes + r.b.nbytes
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = float(np.sum(e2e_times))
+    e2e = {"value": world * checks_per_step * args.steps / e2e_s, "unit": "configs/s",
+           "h2d_bytes_per_step": int(v1h.nbytes + v2h.nbytes), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {"metric": METRIC, "value": value, "unit": "configs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": args.mode, "segments": K, "kept_segments": kept,
+                       "checks_per_step": checks_per_step, "sample_checks": samp, "bisection_checks": bisc,
+                       "ms_per_10_segment_path": ms / args.steps,
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = run_cpu_baseline(args.seconds)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

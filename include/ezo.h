@@ -1,0 +1,256 @@
+/*
+ * ezo.h - C ABI of libezo.so: GPU edge inflation (EI-ZO) of collision-free
+ * configuration-space segments into probabilistically collision-free
+ * H-polytopes, after "Superfast Configuration-Space Convex Set Computation on
+ * GPUs for Online Motion Planning" (arXiv 2504.10783).
+ *
+ * Conventions shared by every entry point:
+ *  - Host pointers (suffix-free) are read during the call and never kept; the
+ *    caller owns them. Device pointers carry the suffix `_dev`; the caller
+ *    owns them too and they must stay valid until the work queued on
+ *    `cuda_stream` has finished.
+ *  - `cuda_stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *    default stream.
+ *  - Opaque handles are created and freed by the library; a handle's device
+ *    memory is allocated with cudaMalloc at creation and freed by its *_free.
+ *  - Every call returns an ezo_status. EZO_OK is 0. On an error the call has
+ *    no effect on its outputs unless stated, and ezo_last_error() returns a
+ *    message for the calling thread. No C++ exception crosses this ABI.
+ *  - Configurations on the device are FP32 in dimension-major layout: value j
+ *    of configuration i is q[j * ldq + i] (ldq >= N).
+ *  - Polytopes are FP64, row-major: row r of A is A[r * n .. r * n + n - 1],
+ *    and P = { x : A x <= b }.
+ */
+#ifndef EZO_H
+#define EZO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EZO_OK = 0,
+  EZO_ERR_INVALID_ARG = 1,
+  /* Sec. IV-C: a candidate collision lies within t_col of the segment; the
+   * segment is likely in collision and no region is built. */
+  EZO_ERR_SEGMENT_IN_COLLISION = 2,
+  EZO_ERR_CAPACITY = 3,
+  EZO_ERR_TIMEOUT = 4,
+  EZO_ERR_CUDA = 5,
+  /* Sec. IV-C "Maximum iterations": N_it rounds ran without the test
+   * accepting; the polytope is returned but carries no guarantee. */
+  EZO_WARN_MAX_ITER = 6
+} ezo_status;
+
+/* Per-segment outcome codes reported by ezo_batch_get_segment. */
+typedef enum {
+  EZO_SEG_ACTIVE = 0,
+  EZO_SEG_ACCEPTED = 1,
+  EZO_SEG_IN_COLLISION = 2,
+  EZO_SEG_CAPACITY = 3,
+  EZO_SEG_MAX_ITER = 6,
+  EZO_SEG_IDLE = 7,
+  EZO_SEG_SKIPPED = 8
+} ezo_segment_status;
+
+/* Parameters of Algorithm 1 (Sec. IV-B, IV-C; parameter tables of the
+ * appendix). eps: admissible fraction in collision; delta: admissible
+ * uncertainty; tau: decision threshold of the unadaptive test (0 < tau < 1,
+ * the paper uses 0.5); step_back_max: Delta_max; t_col: collision tolerance
+ * of the fail-fast rule; n_p: samples to update (N_p); n_f: maximum faces per
+ * iteration (N_f); n_b: bisection steps (N_b); n_mix: hit-and-run mixing
+ * steps (N_ms); n_it_max: iteration cap (N_it); seed: Philox key. */
+typedef struct {
+  double eps;
+  double delta;
+  double tau;
+  double step_back_max;
+  double t_col;
+  int32_t n_p;
+  int32_t n_f;
+  int32_t n_b;
+  int32_t n_mix;
+  int32_t n_it_max;
+  int32_t reserved0;
+  uint64_t seed;
+} ezo_params;
+
+/* Fills `p` with eps = delta = 0.05, tau = 0.5, Delta_max = 0.01,
+ * t_col = 1e-3, N_p = 10000, N_f = 10, N_b = 10, N_ms = 60, N_it = 50, seed 1. */
+void ezo_params_default(ezo_params* p);
+
+typedef struct ezo_robot ezo_robot;
+typedef struct ezo_env ezo_env;
+typedef struct ezo_batch ezo_batch;
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char* ezo_last_error(void);
+
+/* ------------------------------------------------------------------ robot --
+ * Robot description the paper assumes (Sec. II: kinematics and collision
+ * geometry, as in a URDF), restricted to a serial chain in standard DH form
+ * with sphere geometries (Sec. IV-D: sphere and box geometries; boxes are not
+ * supported here). Frame 0 is the base; frame i (1..n) is
+ *   T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i).
+ * n <= 16 joints. Sphere s (n_spheres <= 256) sits at sphere_xyz[3s..3s+2] in
+ * frame sphere_frame[s] (0..n) with radius sphere_r[s] >= 0. self_pairs holds
+ * n_self_pairs pairs (i, j) of sphere indices tested against each other
+ * (n_self_pairs <= 65535). q_lo/q_hi are the joint limits (the usual domain
+ * D). All arrays are host FP64 (int32 for indices), copied at creation.
+ * Errors: EZO_ERR_INVALID_ARG for sizes out of range or bad indices;
+ * EZO_ERR_CUDA if device memory cannot be allocated. */
+ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, const double* d,
+                            const double* theta_off, const double* q_lo, const double* q_hi,
+                            int32_t n_spheres, const int32_t* sphere_frame, const double* sphere_xyz,
+                            const double* sphere_r, int32_t n_self_pairs, const int32_t* self_pairs,
+                            ezo_robot** out);
+void ezo_robot_free(ezo_robot* robot);
+int32_t ezo_robot_dof(const ezo_robot* robot);
+
+/* -------------------------------------------------------------- obstacles --
+ * Obstacle spheres (Sec. V-B: perceived voxels become circumscribing
+ * spheres): n_obs rows (x, y, z, radius) of host FP64, n_obs <= 4096.
+ * Errors: EZO_ERR_INVALID_ARG, EZO_ERR_CUDA. */
+ezo_status ezo_env_create(int32_t n_obs, const double* xyzr, ezo_env** out);
+void ezo_env_free(ezo_env* env);
+
+/* ------------------------------------------------------ collision checker --
+ * The collision checker of Sec. IV-D: forward kinematics of each FP32
+ * configuration q_dev (n x N, dimension-major, stride ldq) and a test of
+ * every robot sphere against every obstacle sphere and of every listed self
+ * pair; flags_dev[i] = 1 iff some pair overlaps (squared centre distance
+ * below the squared sum of radii), else 0. Stream-ordered, asynchronous.
+ * lanes_per_config selects 1, 2, 4 or 8 cooperating lanes per configuration
+ * (0 = choose from N). Errors: EZO_ERR_INVALID_ARG (null handle, N < 0,
+ * ldq < N, bad lanes value), EZO_ERR_CUDA (launch failure). */
+ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
+                               int64_t ldq, uint8_t* flags_dev, int32_t lanes_per_config, void* cuda_stream);
+
+/* Signed distance per configuration: min over the same pairs of
+ * ||c_i - c_j|| - r_i - r_j in FP32 (negative iff in collision). Used to
+ * label data and to bound ambiguous decisions. Stream-ordered. */
+ezo_status ezo_signed_distance(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
+                               int64_t ldq, float* sd_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------- hit-and-run --
+ * UniformSample of Algorithm 1 (Sec. IV-B, IV-D): N independent hit-and-run
+ * walks of n_mix steps inside P = {x : A x <= b}, one walk per output
+ * sample, started on the segment v1..v2 (host FP64, n values each). A_dev is
+ * FP64 m x n with row stride lda, b_dev FP64 m (both device). Walk i draws
+ * Philox4x32-10 blocks with counter (i, draw, round_k, stream_id) and key
+ * (seed low 32 bits, seed high 32 bits). Output x_dev: FP32, n x N,
+ * dimension-major with stride ldx. Stream-ordered. m <= 2048 (the FP32
+ * copy of A is staged in shared memory).
+ * Errors: EZO_ERR_INVALID_ARG, EZO_ERR_CUDA. */
+ezo_status ezo_hit_and_run(const double* A_dev, const double* b_dev, int32_t m, int32_t n, int32_t lda,
+                           const double* v1, const double* v2, int64_t N, int32_t n_mix, uint64_t seed,
+                           uint32_t stream_id, int32_t round_k, float* x_dev, int64_t ldx, void* cuda_stream);
+
+/* ------------------------------------------------------------------ batch --
+ * A batch is a set of segments L_g = conv{v1_g, v2_g} inflated by Algorithm 1
+ * with shared parameters, each starting from the domain D = {A0 x <= b0}
+ * (m0 rows; A0 = NULL selects the robot's joint-limit box, rows +e_i <= q_hi_i
+ * then -e_i <= -q_lo_i). v1, v2: host FP64 n_seg x n. seg_env (nullable, all
+ * 0): obstacle set of each segment, an index into envs. seg_np (nullable):
+ * per-segment N_p. seg_stream (nullable, default g): Philox stream id of each
+ * segment; rounds and walks are the other counter words, so a segment's
+ * result does not depend on what else is in the batch. path_first
+ * (nullable): index of the first segment of the path each segment belongs
+ * to (segments of a path are consecutive); used by ezo_batch_run_path.
+ * The batch allocates its own device memory (state, polytopes, samples,
+ * candidates) sized for m0 + n_f * n_it_max rows (at most 2048) and
+ * max(N_p, M_{N_it}) samples per segment. Errors: EZO_ERR_INVALID_ARG, EZO_ERR_CUDA. */
+ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env* const* envs, int32_t n_seg,
+                            const double* v1, const double* v2, const int32_t* seg_env, const int32_t* seg_np,
+                            const uint32_t* seg_stream, const int32_t* path_first, const double* A0,
+                            const double* b0, int32_t m0, const ezo_params* params, ezo_batch** out);
+void ezo_batch_free(ezo_batch* batch);
+
+/* Puts every segment back to round 1 with its polytope equal to the domain
+ * D, optionally replacing the segment endpoints with host arrays v1, v2
+ * (n_seg x n FP64; NULL keeps the current ones). Stream-ordered; the batch's
+ * device buffers are reused, nothing is allocated. */
+ezo_status ezo_batch_reset(ezo_batch* batch, const double* v1, const double* v2, void* cuda_stream);
+
+/* Run modes. HOST_LOOP launches the round kernels per round and reads a
+ * 16-byte round summary back to decide whether to go on; GRAPH captures one
+ * round into a CUDA graph whose conditional WHILE node repeats it on the
+ * device until no segment is active (one launch, no host round trips). */
+typedef enum { EZO_RUN_HOST_LOOP = 0, EZO_RUN_GRAPH = 1 } ezo_run_mode;
+
+/* Algorithm 1 for every segment of the batch at once, until each one is
+ * accepted, reported in collision (t_col) or has run N_it rounds. Returns
+ * after the stream has finished. Errors: EZO_ERR_CUDA. */
+ezo_status ezo_batch_run(ezo_batch* batch, int32_t mode, void* cuda_stream);
+
+/* Sec. VI-A: the batch's segments form paths (path_first); inflate them in
+ * order, skipping a segment whose endpoints lie in an earlier polytope of the
+ * same path (A x <= b + 1e-9), and stop a path after a segment reported in
+ * collision. sequential = 1 runs one segment at a time (the paper's order);
+ * sequential = 0 inflates all segments speculatively in one batched run and
+ * applies the same skip rule afterwards, which keeps the same polytopes.
+ * Skipped segments report EZO_SEG_SKIPPED. Errors: EZO_ERR_CUDA. */
+ezo_status ezo_batch_run_path(ezo_batch* batch, int32_t sequential, int32_t mode, void* cuda_stream);
+
+/* Per-segment result: status (ezo_segment_status), rounds run, rows m of the
+ * polytope, planes added, exact collision checks performed. Any output
+ * pointer may be NULL. Synchronous (copies from the device). */
+ezo_status ezo_batch_get_segment(const ezo_batch* batch, int32_t seg, int32_t* status, int32_t* rounds,
+                                 int32_t* m, int32_t* planes, int64_t* checks);
+
+/* Copies polytope `seg` (m x n row-major A, m entries of b; host buffers of
+ * at least m_cap x n and m_cap doubles, m_cap from ezo_batch_capacity) and
+ * writes its row count to *m. */
+ezo_status ezo_batch_get_polytope(const ezo_batch* batch, int32_t seg, int32_t* m, double* A, double* b);
+
+/* Row capacity per segment (m0 + n_f * n_it_max) and sample capacity. */
+ezo_status ezo_batch_capacity(const ezo_batch* batch, int32_t* m_cap, int32_t* s_cap);
+
+/* Step-by-step access for tests and tools. ezo_batch_step runs one kernel of
+ * the current round over the batch: 0 round size (a1), 1 hit-and-run (a2),
+ * 2 collision labels (a3, a4), 3 certification and selection (a5, a6),
+ * 4 projection and bisection (a7, a8), 5 hyperplane placement (a9), 6 round
+ * end. Stream-ordered; call ezo_batch_sync before reading. */
+ezo_status ezo_batch_step(ezo_batch* batch, int32_t step, void* cuda_stream);
+ezo_status ezo_batch_sync(ezo_batch* batch, void* cuda_stream);
+
+/* Reads an internal per-segment buffer of the current round into host
+ * memory: 0 samples (FP32, n x s_cap dimension-major), 1 labels (uint8
+ * s_cap), 2 candidate sample indices (int32 N_p), 3 c* (FP64, n x N_p
+ * dimension-major), 4 distance to L of c* (FP64 N_p), 5 bisection decisions
+ * (uint32 N_p, bit s = midpoint s in collision), 6 round state (int32[12]:
+ * k, status, m, |S|, M, count, n_cand, planes, rounds, n_placed, N_p, env),
+ * 7 placed candidate indices of the last round (int32 n_f), 8 step backs of
+ * the last round (FP64 n_f), 9 exact checks split as int64[2] {at samples,
+ * at bisection midpoints}, 10 the batch's round summary (int32[4]: active
+ * segments, rounds run since the last reset, sample tiles, bisection tiles;
+ * `seg` is ignored). `bytes` is the size of `dst`. */
+ezo_status ezo_batch_read(const ezo_batch* batch, int32_t seg, int32_t what, void* dst, int64_t bytes);
+
+/* Overwrites the samples of segment `seg` for the current round (FP32,
+ * n x count dimension-major, count <= s_cap) so that a round can be replayed
+ * on given samples; sets |S| to count. */
+ezo_status ezo_batch_write_samples(ezo_batch* batch, int32_t seg, const float* samples, int32_t count);
+
+/* -------------------------------------------------------------- profiling --
+ * When enabled, ezo_batch_run in HOST_LOOP mode records CUDA events around
+ * every kernel launch on the launch stream; ezo_profile_read returns, for
+ * kernel kind i (0 round size, 1 sample, 2 check, 3 certify, 4 bisect,
+ * 5 place, 6 round end), the total milliseconds and launch count since the
+ * last reset. */
+ezo_status ezo_profile_enable(int32_t on);
+ezo_status ezo_profile_reset(void);
+ezo_status ezo_profile_read(double* ms, int64_t* launches, int32_t n_kinds);
+
+/* Algorithmic FP32 work of one exact configuration check (forward kinematics
+ * plus 8 flops per obstacle pair and per self pair), as used for rooflines. */
+double ezo_check_flops(const ezo_robot* robot, const ezo_env* env);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EZO_H */

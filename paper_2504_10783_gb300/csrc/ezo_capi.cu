@@ -1,0 +1,942 @@
+// Host side of libezo.so: handles, device memory, the round driver (host
+// loop or one CUDA graph with a conditional WHILE node), path inflation with
+// the containment skip (Sec. VI-A) and the C ABI declared in include/ezo.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/ezo.h"
+#include "ezo_engine.cuh"
+
+using namespace ezo;
+
+namespace {
+
+thread_local std::string g_err;
+
+ezo_status fail(ezo_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+ezo_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return EZO_ERR_CUDA;
+}
+
+#define EZO_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr double kU32 = 5.9604644775390625e-8;  // 2^-24
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+// ------------------------------------------------------------- profiling --
+constexpr int kKinds = 7;
+bool g_prof_on = false;
+double g_prof_ms[kKinds] = {0};
+long long g_prof_n[kKinds] = {0};
+
+struct EventPool {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  size_t used = 0;
+  cudaEvent_t get() {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+    return ev[used++];
+  }
+};
+
+}  // namespace
+
+struct ezo_robot {
+  RobotDev host{};
+  RobotDev* d_robot = nullptr;
+  ushort2* d_pairs = nullptr;
+  float* d_rr = nullptr;
+  int n = 0, n_spheres = 0, nsp_pad = 0, n_self = 0;
+  std::vector<double> q_lo, q_hi;
+  double reach = 0.0, r_max = 0.0;
+  double fk_flops = 0.0;
+};
+
+struct ezo_env {
+  float4* d_obs = nullptr;
+  float* d_nhw = nullptr;
+  int n_obs = 0, n_obs_pad = 0;
+  double o_max = 0.0, R_max = 0.0;
+  EnvDev dev() const { return EnvDev{d_obs, d_nhw, n_obs, n_obs_pad}; }
+};
+
+static float band_E(const ezo_robot* r, const ezo_env* e) {
+  // rounding bound of max_j t_ij - hu_i for the fast pair form (|c| <= reach,
+  // |o| <= o_max, radii <= r_max, R_max), with a factor 8 of unit roundoff.
+  const double a = r->reach + e->o_max, b = r->r_max + e->R_max;
+  return (float)(8.0 * kU32 * (a * a + b * b));
+}
+
+extern "C" {
+
+void ezo_params_default(ezo_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps = 0.05;
+  p->delta = 0.05;
+  p->tau = 0.5;
+  p->step_back_max = 0.01;
+  p->t_col = 1e-3;
+  p->n_p = 10000;
+  p->n_f = 10;
+  p->n_b = 10;
+  p->n_mix = 60;
+  p->n_it_max = 50;
+  p->seed = 1;
+}
+
+const char* ezo_last_error(void) { return g_err.c_str(); }
+
+ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, const double* d,
+                            const double* theta_off, const double* q_lo, const double* q_hi, int32_t n_spheres,
+                            const int32_t* sphere_frame, const double* sphere_xyz, const double* sphere_r,
+                            int32_t n_self_pairs, const int32_t* self_pairs, ezo_robot** out) {
+  if (!out) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > EZO_MAX_DOF) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: n must be in [1, 16]");
+  if (n_spheres < 0 || n_spheres > EZO_MAX_SPHERES)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: n_spheres must be in [0, 256]");
+  if (n_self_pairs < 0 || n_self_pairs > 65535)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: n_self_pairs must be in [0, 65535]");
+  if (!a || !alpha || !d || !q_lo || !q_hi || (n_spheres && (!sphere_frame || !sphere_xyz || !sphere_r)) ||
+      (n_self_pairs && !self_pairs))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: null array");
+  for (int s = 0; s < n_spheres; ++s) {
+    if (sphere_frame[s] < 0 || sphere_frame[s] > n)
+      return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: sphere_frame out of [0, n]");
+    if (!(sphere_r[s] >= 0.0)) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: negative sphere radius");
+  }
+  for (int p = 0; p < 2 * n_self_pairs; ++p)
+    if (self_pairs[p] < 0 || self_pairs[p] >= n_spheres)
+      return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: self pair index out of range");
+  for (int j = 0; j < n; ++j)
+    if (!(q_lo[j] <= q_hi[j])) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: q_lo > q_hi");
+
+  ezo_robot* r = new ezo_robot();
+  r->n = n;
+  r->n_spheres = n_spheres;
+  r->nsp_pad = round_up(n_spheres, EZO_CH);
+  r->n_self = n_self_pairs;
+  r->q_lo.assign(q_lo, q_lo + n);
+  r->q_hi.assign(q_hi, q_hi + n);
+  RobotDev& h = r->host;
+  h.n = n;
+  h.n_spheres = n_spheres;
+  h.n_spheres_pad = r->nsp_pad;
+  h.n_self = n_self_pairs;
+  double chain = 0.0;
+  for (int j = 0; j < n; ++j) {
+    h.ca[j] = (float)std::cos(alpha[j]);
+    h.sa[j] = (float)std::sin(alpha[j]);
+    h.a[j] = (float)a[j];
+    h.d[j] = (float)d[j];
+    h.toff[j] = theta_off ? (float)theta_off[j] : 0.f;
+    chain += std::fabs(a[j]) + std::fabs(d[j]);
+  }
+  // sort spheres by frame (stable) so the chain walk can emit them in order
+  std::vector<int> order(n_spheres);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sphere_frame[x] < sphere_frame[y]; });
+  std::vector<int> inv(n_spheres);
+  double loc_max = 0.0;
+  for (int s = 0; s < n_spheres; ++s) {
+    const int o = order[s];
+    inv[o] = s;
+    h.sph[s] = make_float4((float)sphere_xyz[3 * o], (float)sphere_xyz[3 * o + 1], (float)sphere_xyz[3 * o + 2],
+                           (float)sphere_r[o]);
+    loc_max = std::max(loc_max, std::sqrt(sphere_xyz[3 * o] * sphere_xyz[3 * o] +
+                                          sphere_xyz[3 * o + 1] * sphere_xyz[3 * o + 1] +
+                                          sphere_xyz[3 * o + 2] * sphere_xyz[3 * o + 2]));
+    r->r_max = std::max(r->r_max, sphere_r[o]);
+  }
+  for (int s = n_spheres; s < r->nsp_pad; ++s) h.sph[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int f = 0; f <= n + 1; ++f) h.frame_first[f] = 0;
+  {
+    int s = 0;
+    for (int f = 0; f <= n; ++f) {
+      h.frame_first[f] = s;
+      while (s < n_spheres && sphere_frame[order[s]] == f) ++s;
+    }
+    h.frame_first[n + 1] = n_spheres;
+  }
+  r->reach = chain + loc_max;
+  std::vector<ushort2> pairs(std::max(1, n_self_pairs));
+  std::vector<float> rr(std::max(1, n_self_pairs));
+  for (int p = 0; p < n_self_pairs; ++p) {
+    const int i = self_pairs[2 * p], j = self_pairs[2 * p + 1];
+    pairs[p] = make_ushort2((unsigned short)inv[i], (unsigned short)inv[j]);
+    const float s = (float)sphere_r[i] + (float)sphere_r[j];
+    rr[p] = s * s;
+  }
+  // algorithmic FP32 flops: per joint ~45 (rotation and origin update), per
+  // sphere 18 (centre) + 7 (half squared norm), 8 per pair
+  r->fk_flops = 45.0 * n + 25.0 * n_spheres;
+  cudaError_t e;
+  if ((e = cudaMalloc(&r->d_pairs, pairs.size() * sizeof(ushort2))) != cudaSuccess ||
+      (e = cudaMalloc(&r->d_rr, rr.size() * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&r->d_robot, sizeof(RobotDev))) != cudaSuccess) {
+    ezo_robot_free(r);
+    return cuda_fail(e, "ezo_robot_create: cudaMalloc");
+  }
+  h.self_pairs = r->d_pairs;
+  h.self_rr = r->d_rr;
+  if ((e = cudaMemcpy(r->d_pairs, pairs.data(), pairs.size() * sizeof(ushort2), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(r->d_rr, rr.data(), rr.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(r->d_robot, &h, sizeof(RobotDev), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    ezo_robot_free(r);
+    return cuda_fail(e, "ezo_robot_create: cudaMemcpy");
+  }
+  *out = r;
+  g_err.clear();
+  return EZO_OK;
+}
+
+void ezo_robot_free(ezo_robot* r) {
+  if (!r) return;
+  cudaFree(r->d_pairs);
+  cudaFree(r->d_rr);
+  cudaFree(r->d_robot);
+  delete r;
+}
+
+int32_t ezo_robot_dof(const ezo_robot* r) { return r ? r->n : 0; }
+
+ezo_status ezo_env_create(int32_t n_obs, const double* xyzr, ezo_env** out) {
+  if (!out) return fail(EZO_ERR_INVALID_ARG, "ezo_env_create: out is NULL");
+  *out = nullptr;
+  if (n_obs < 0 || n_obs > EZO_MAX_OBS) return fail(EZO_ERR_INVALID_ARG, "ezo_env_create: n_obs must be in [0, 4096]");
+  if (n_obs && !xyzr) return fail(EZO_ERR_INVALID_ARG, "ezo_env_create: xyzr is NULL");
+  for (int j = 0; j < n_obs; ++j)
+    if (!(xyzr[4 * j + 3] >= 0.0)) return fail(EZO_ERR_INVALID_ARG, "ezo_env_create: negative obstacle radius");
+  ezo_env* e = new ezo_env();
+  e->n_obs = n_obs;
+  e->n_obs_pad = round_up(n_obs, EZO_CH);
+  const int np = std::max(1, e->n_obs_pad);
+  std::vector<float4> obs(np, make_float4(0.f, 0.f, 0.f, 0.f));
+  std::vector<float> nhw(np, -1.0e30f);
+  for (int j = 0; j < n_obs; ++j) {
+    const double x = xyzr[4 * j], y = xyzr[4 * j + 1], z = xyzr[4 * j + 2], R = xyzr[4 * j + 3];
+    obs[j] = make_float4((float)x, (float)y, (float)z, (float)R);
+    const double xf = (float)x, yf = (float)y, zf = (float)z, Rf = (float)R;
+    nhw[j] = (float)(-0.5 * (xf * xf + yf * yf + zf * zf - Rf * Rf));
+    e->o_max = std::max(e->o_max, std::sqrt(x * x + y * y + z * z));
+    e->R_max = std::max(e->R_max, R);
+  }
+  cudaError_t err;
+  if ((err = cudaMalloc(&e->d_obs, np * sizeof(float4))) != cudaSuccess ||
+      (err = cudaMalloc(&e->d_nhw, np * sizeof(float))) != cudaSuccess ||
+      (err = cudaMemcpy(e->d_obs, obs.data(), np * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(e->d_nhw, nhw.data(), np * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    ezo_env_free(e);
+    return cuda_fail(err, "ezo_env_create");
+  }
+  *out = e;
+  g_err.clear();
+  return EZO_OK;
+}
+
+void ezo_env_free(ezo_env* e) {
+  if (!e) return;
+  cudaFree(e->d_obs);
+  cudaFree(e->d_nhw);
+  delete e;
+}
+
+static int auto_lanes(long long N) {
+  if (N >= (1ll << 20)) return 1;
+  if (N >= (1ll << 17)) return 2;
+  if (N >= (1ll << 15)) return 4;
+  return 8;
+}
+
+ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
+                               int64_t ldq, uint8_t* flags_dev, int32_t lanes, void* stream) {
+  if (!robot || !env) return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: null handle");
+  if (N < 0 || ldq < N) return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: need 0 <= N <= ldq");
+  if (N > 0 && (!q_dev || !flags_dev)) return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: null buffer");
+  if (lanes == 0) lanes = auto_lanes(N);
+  if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: lanes_per_config must be 0, 1, 2, 4 or 8");
+  cudaError_t e = launch_check_flat(robot->d_robot, robot->n, robot->nsp_pad, env->dev(), band_E(robot, env), q_dev, ldq, N,
+                                    flags_dev, lanes, sm_count() * 32, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ezo_check_collision");
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_signed_distance(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
+                               int64_t ldq, float* sd_dev, void* stream) {
+  if (!robot || !env) return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: null handle");
+  if (N < 0 || ldq < N) return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: need 0 <= N <= ldq");
+  if (N > 0 && (!q_dev || !sd_dev)) return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: null buffer");
+  cudaError_t e = launch_sd_flat(robot->d_robot, robot->n, robot->nsp_pad, env->dev(), q_dev, ldq, N, sd_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ezo_signed_distance");
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_hit_and_run(const double* A_dev, const double* b_dev, int32_t m, int32_t n, int32_t lda,
+                           const double* v1, const double* v2, int64_t N, int32_t n_mix, uint64_t seed,
+                           uint32_t stream_id, int32_t round_k, float* x_dev, int64_t ldx, void* stream) {
+  if (n < 1 || n > EZO_MAX_DOF) return fail(EZO_ERR_INVALID_ARG, "ezo_hit_and_run: n must be in [1, 16]");
+  if (m < 0 || m > 2048 || lda < n) return fail(EZO_ERR_INVALID_ARG, "ezo_hit_and_run: need 0 <= m <= 2048, lda >= n");
+  if (N < 0 || ldx < N || n_mix < 0) return fail(EZO_ERR_INVALID_ARG, "ezo_hit_and_run: bad N, ldx or n_mix");
+  if (!v1 || !v2 || (N > 0 && !x_dev) || (m > 0 && (!A_dev || !b_dev)))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_hit_and_run: null pointer");
+  cudaError_t e = launch_sample_flat(A_dev, b_dev, m, lda, n, v1, v2, N, n_mix, seed, stream_id, round_k, x_dev, ldx,
+                                     (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ezo_hit_and_run");
+  g_err.clear();
+  return EZO_OK;
+}
+
+double ezo_check_flops(const ezo_robot* robot, const ezo_env* env) {
+  if (!robot || !env) return 0.0;
+  return robot->fk_flops + 8.0 * ((double)robot->n_spheres * env->n_obs + robot->n_self);
+}
+
+// ------------------------------------------------------------------ batch --
+}  // extern "C"
+
+struct ezo_batch {
+  const ezo_robot* robot = nullptr;
+  int B = 0, n = 0, m0 = 0, m_cap = 0, s_cap_max = 0, np_max = 0, max_path_len = 1, max_obs_pad = 0;
+  ezo_params prm{};
+  std::vector<SegState> st0;
+  std::vector<int> path_first;
+  std::vector<EnvDevFull> envs;
+  long long total_s = 0, total_c = 0;
+  int max_sample_tiles = 0, max_bisect_tiles = 0;
+  // device buffers
+  SegState* d_st = nullptr;
+  double *d_v1 = nullptr, *d_v2 = nullptr, *d_A = nullptr, *d_b = nullptr;
+  float* d_S = nullptr;
+  uint8_t* d_flags = nullptr;
+  int* d_cidx = nullptr;
+  double *d_cstar = nullptr, *d_dist = nullptr;
+  float *d_c32 = nullptr, *d_cn = nullptr;
+  uint32_t* d_bits = nullptr;
+  int* d_pidx = nullptr;
+  double* d_pdelta = nullptr;
+  int2 *d_stiles = nullptr, *d_btiles = nullptr;
+  RoundSummary* d_sum = nullptr;
+  RoundSummary* h_sum = nullptr;
+  EnvDevFull* d_envs = nullptr;
+  int* d_path_first = nullptr;
+  uint8_t* d_contained = nullptr;
+  SegState* d_st0 = nullptr;    // initial state, for resets
+  double *d_A0 = nullptr, *d_b0 = nullptr;  // initial polytopes
+  std::vector<double> v1h, v2h;
+  BatchView view{};
+  int T_check = 1, T_bisect = 4;
+  int grid_sample = 1, grid_check = 1, grid_bisect = 1;
+  // graph mode
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  EventPool events;
+};
+
+namespace {
+
+ezo_status batch_free_device(ezo_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  void* ptrs[] = {b->d_st,    b->d_v1,    b->d_v2,   b->d_A,    b->d_b,      b->d_S,      b->d_flags,
+                  b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx,
+                  b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->h_sum) cudaFreeHost(b->h_sum);
+  for (auto e : b->events.ev) cudaEventDestroy(e);
+  return EZO_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, std::max<size_t>(1, count) * sizeof(T));
+}
+
+int host_test_size(int k, double eps, double delta, double tau) {
+  const double dk = 6.0 * delta / (M_PI * M_PI * k * (double)k);
+  return (int)std::ceil(2.0 * std::log(1.0 / dk) / (eps * tau * tau));
+}
+
+ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (g_prof_on) {
+    e0 = b->events.get();
+    e1 = b->events.get();
+    b->events.kind.push_back(step);
+    cudaEventRecord(e0, s);
+  }
+  switch (step) {
+    case 0: e = launch_round_begin(b->view, s); break;
+    case 1: e = launch_round_sample(b->view, b->grid_sample, s); break;
+    case 2: e = launch_round_check(b->view, b->T_check, b->grid_check, s); break;
+    case 3: e = launch_round_certify(b->view, s); break;
+    case 4: e = launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s); break;
+    case 5: e = launch_round_place(b->view, s); break;
+    case 6: e = launch_round_end(b->view, s); break;
+    default: return fail(EZO_ERR_INVALID_ARG, "ezo_batch_step: step must be in [0, 6]");
+  }
+  if (g_prof_on) cudaEventRecord(e1, s);
+  if (e != cudaSuccess) return cuda_fail(e, "round kernel launch");
+  return EZO_OK;
+}
+
+void collect_profile(ezo_batch* b) {
+  if (!g_prof_on) return;
+  for (size_t i = 0; i < b->events.kind.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->events.ev[2 * i], b->events.ev[2 * i + 1]) == cudaSuccess) {
+      g_prof_ms[b->events.kind[i]] += ms;
+      g_prof_n[b->events.kind[i]] += 1;
+    }
+  }
+  b->events.kind.clear();
+  b->events.used = 0;
+}
+
+ezo_status run_host_loop(ezo_batch* b, cudaStream_t s) {
+  for (int r = 0; r <= b->prm.n_it_max + 1; ++r) {
+    for (int step = 0; step < 7; ++step) {
+      ezo_status st = launch_step(b, step, s);
+      if (st != EZO_OK) return st;
+    }
+    EZO_CUDA(cudaMemcpyAsync(b->h_sum, b->d_sum, sizeof(RoundSummary), cudaMemcpyDeviceToHost, s));
+    EZO_CUDA(cudaStreamSynchronize(s));
+    collect_profile(b);
+    if (b->h_sum->active == 0) break;
+  }
+  return EZO_OK;
+}
+
+ezo_status build_graph(ezo_batch* b) {
+#if CUDART_VERSION >= 12040
+  EZO_CUDA(cudaGraphCreate(&b->graph, 0));
+  cudaGraphConditionalHandle h;
+  EZO_CUDA(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  EZO_CUDA(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (!b->cap_stream) EZO_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  BatchView saved = b->view;
+  b->view.graph_cond = (unsigned long long)h;
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  EZO_CUDA(cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  ezo_status st = EZO_OK;
+  for (int step = 0; step < 7 && st == EZO_OK; ++step) st = launch_step(b, step, b->cap_stream);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &captured);
+  g_prof_on = prof;
+  b->view = saved;
+  if (st != EZO_OK) return st;
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  EZO_CUDA(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+  return EZO_OK;
+#else
+  return fail(EZO_ERR_CUDA, "graph mode needs CUDA 12.4 or newer");
+#endif
+}
+
+ezo_status run_graph(ezo_batch* b, cudaStream_t s) {
+  if (!b->gexec) {
+    ezo_status st = build_graph(b);
+    if (st != EZO_OK) return st;
+  }
+  EZO_CUDA(cudaGraphLaunch(b->gexec, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  return EZO_OK;
+}
+
+ezo_status run_batch(ezo_batch* b, int mode, cudaStream_t s) {
+  if (mode == EZO_RUN_GRAPH) return run_graph(b, s);
+  return run_host_loop(b, s);
+}
+
+ezo_status set_status(ezo_batch* b, int g, int status, cudaStream_t s) {
+  EZO_CUDA(cudaMemcpyAsync(&b->d_st[g].status, &status, sizeof(int), cudaMemcpyHostToDevice, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  return EZO_OK;
+}
+
+ezo_status read_states(ezo_batch* b, std::vector<SegState>& out, cudaStream_t s) {
+  out.resize(b->B);
+  EZO_CUDA(cudaMemcpyAsync(out.data(), b->d_st, sizeof(SegState) * b->B, cudaMemcpyDeviceToHost, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  return EZO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env* const* envs, int32_t n_seg,
+                            const double* v1, const double* v2, const int32_t* seg_env, const int32_t* seg_np,
+                            const uint32_t* seg_stream, const int32_t* path_first, const double* A0,
+                            const double* b0, int32_t m0, const ezo_params* prm, ezo_batch** out) {
+  if (!out) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: out is NULL");
+  *out = nullptr;
+  if (!robot || !prm || n_env < 1 || !envs) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: null argument");
+  if (n_seg < 1 || !v1 || !v2) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: need n_seg >= 1 and v1, v2");
+  if (!(prm->eps > 0.0 && prm->eps < 1.0) || !(prm->delta > 0.0 && prm->delta < 1.0) ||
+      !(prm->tau > 0.0 && prm->tau < 1.0) || !(prm->step_back_max >= 0.0) || !(prm->t_col >= 0.0) ||
+      prm->n_p < 1 || prm->n_f < 1 || prm->n_b < 0 || prm->n_b > 32 || prm->n_mix < 0 || prm->n_it_max < 1)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: parameter out of range");
+  for (int e = 0; e < n_env; ++e)
+    if (!envs[e]) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: null env");
+  const int n = robot->n;
+  if (A0 && (m0 < 1 || !b0)) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: bad domain");
+  std::vector<double> A0v, b0v;
+  if (A0) {
+    A0v.assign(A0, A0 + (size_t)m0 * n);
+    b0v.assign(b0, b0 + m0);
+  } else {
+    m0 = 2 * n;
+    A0v.assign((size_t)m0 * n, 0.0);
+    b0v.assign(m0, 0.0);
+    for (int j = 0; j < n; ++j) {
+      A0v[(size_t)j * n + j] = 1.0;
+      b0v[j] = robot->q_hi[j];
+      A0v[(size_t)(n + j) * n + j] = -1.0;
+      b0v[n + j] = -robot->q_lo[j];
+    }
+  }
+  ezo_batch* b = new ezo_batch();
+  b->robot = robot;
+  b->B = n_seg;
+  b->n = n;
+  b->m0 = m0;
+  b->prm = *prm;
+  b->m_cap = m0 + prm->n_f * prm->n_it_max;
+  if (b->m_cap > 2048) {
+    delete b;
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: m0 + n_f * n_it_max must be <= 2048");
+  }
+  const int m_last = host_test_size(prm->n_it_max, prm->eps, prm->delta, prm->tau) + 16;
+  b->st0.resize(n_seg);
+  b->path_first.resize(n_seg);
+  for (int g = 0; g < n_seg; ++g) {
+    SegState& s = b->st0[g];
+    std::memset(&s, 0, sizeof(s));
+    s.k = 1;
+    s.status = SEG_ACTIVE;
+    s.m = m0;
+    s.n_p = seg_np ? seg_np[g] : prm->n_p;
+    if (s.n_p < 1) {
+      delete b;
+      return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: seg_np must be >= 1");
+    }
+    s.env = seg_env ? seg_env[g] : 0;
+    if (s.env < 0 || s.env >= n_env) {
+      delete b;
+      return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: seg_env out of range");
+    }
+    s.stream = seg_stream ? seg_stream[g] : (uint32_t)g;
+    s.s_cap = std::max(s.n_p, m_last);
+    s.sample_off = b->total_s;
+    s.cand_off = b->total_c;
+    b->total_s += s.s_cap;
+    b->total_c += s.n_p;
+    b->s_cap_max = std::max(b->s_cap_max, s.s_cap);
+    b->np_max = std::max(b->np_max, s.n_p);
+    b->max_sample_tiles += (s.s_cap + kTile - 1) / kTile;
+    b->max_bisect_tiles += (s.n_p + kTile - 1) / kTile;
+    b->path_first[g] = path_first ? path_first[g] : 0;
+    if (b->path_first[g] < 0 || b->path_first[g] > g) {
+      delete b;
+      return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: path_first[g] must be in [0, g]");
+    }
+    b->max_path_len = std::max(b->max_path_len, g - b->path_first[g] + 1);
+  }
+  if (b->np_max > (1 << 20)) {
+    delete b;
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: N_p must be <= 2^20");
+  }
+  b->envs.resize(n_env);
+  for (int e = 0; e < n_env; ++e) {
+    b->envs[e].e = envs[e]->dev();
+    b->envs[e].E = band_E(robot, envs[e]);
+    b->max_obs_pad = std::max(b->max_obs_pad, envs[e]->n_obs_pad);
+  }
+  const size_t smem_check = check_smem_bytes(robot->nsp_pad, b->max_obs_pad, 128, 1);
+  if (smem_check > 220 * 1024) {
+    delete b;
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: robot spheres and obstacles exceed shared memory");
+  }
+  const long long B = n_seg, mc = b->m_cap;
+  cudaError_t e = cudaSuccess;
+#define EZO_ALLOC(p, cnt) \
+  if (e == cudaSuccess) e = dalloc(&(p), (size_t)(cnt))
+  EZO_ALLOC(b->d_st, B);
+  EZO_ALLOC(b->d_v1, B * n);
+  EZO_ALLOC(b->d_v2, B * n);
+  EZO_ALLOC(b->d_A, B * mc * n);
+  EZO_ALLOC(b->d_b, B * mc);
+  EZO_ALLOC(b->d_S, b->total_s * n);
+  EZO_ALLOC(b->d_flags, b->total_s);
+  EZO_ALLOC(b->d_cidx, b->total_c);
+  EZO_ALLOC(b->d_cstar, b->total_c * n);
+  EZO_ALLOC(b->d_dist, b->total_c);
+  EZO_ALLOC(b->d_c32, b->total_c * n);
+  EZO_ALLOC(b->d_cn, b->total_c);
+  EZO_ALLOC(b->d_bits, b->total_c);
+  EZO_ALLOC(b->d_pidx, B * prm->n_f);
+  EZO_ALLOC(b->d_pdelta, B * prm->n_f);
+  EZO_ALLOC(b->d_stiles, b->max_sample_tiles);
+  EZO_ALLOC(b->d_btiles, b->max_bisect_tiles);
+  EZO_ALLOC(b->d_sum, 1);
+  EZO_ALLOC(b->d_envs, n_env);
+  EZO_ALLOC(b->d_path_first, B);
+  EZO_ALLOC(b->d_contained, B * b->max_path_len);
+  EZO_ALLOC(b->d_st0, B);
+  EZO_ALLOC(b->d_A0, B * mc * n);
+  EZO_ALLOC(b->d_b0, B * mc);
+#undef EZO_ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_sum, sizeof(RoundSummary));
+  if (e != cudaSuccess) {
+    batch_free_device(b);
+    delete b;
+    return cuda_fail(e, "ezo_batch_create: allocation");
+  }
+  // initial contents
+  std::vector<double> Ah((size_t)B * mc * n, 0.0), bh((size_t)B * mc, 0.0);
+  for (long long g = 0; g < B; ++g) {
+    std::copy(A0v.begin(), A0v.end(), Ah.begin() + g * mc * n);
+    std::copy(b0v.begin(), b0v.end(), bh.begin() + g * mc);
+  }
+#define EZO_H2D(dst, src, bytes) \
+  if (e == cudaSuccess) e = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice)
+  EZO_H2D(b->d_st, b->st0.data(), sizeof(SegState) * B);
+  EZO_H2D(b->d_v1, v1, sizeof(double) * B * n);
+  EZO_H2D(b->d_v2, v2, sizeof(double) * B * n);
+  EZO_H2D(b->d_A, Ah.data(), sizeof(double) * Ah.size());
+  EZO_H2D(b->d_b, bh.data(), sizeof(double) * bh.size());
+  EZO_H2D(b->d_envs, b->envs.data(), sizeof(EnvDevFull) * n_env);
+  EZO_H2D(b->d_path_first, b->path_first.data(), sizeof(int) * B);
+  EZO_H2D(b->d_st0, b->st0.data(), sizeof(SegState) * B);
+  EZO_H2D(b->d_A0, Ah.data(), sizeof(double) * Ah.size());
+  EZO_H2D(b->d_b0, bh.data(), sizeof(double) * bh.size());
+#undef EZO_H2D
+  if (e == cudaSuccess) e = cudaMemset(b->d_sum, 0, sizeof(RoundSummary));
+  if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, (size_t)std::max<long long>(1, b->total_s));
+  if (e != cudaSuccess) {
+    batch_free_device(b);
+    delete b;
+    return cuda_fail(e, "ezo_batch_create: upload");
+  }
+  BatchView& v = b->view;
+  v.B = n_seg;
+  v.n = n;
+  v.m_cap = b->m_cap;
+  v.n_f = prm->n_f;
+  v.n_b = prm->n_b;
+  v.n_mix = prm->n_mix;
+  v.n_it_max = prm->n_it_max;
+  v.eps = prm->eps;
+  v.delta = prm->delta;
+  v.tau = prm->tau;
+  v.step_back_max = prm->step_back_max;
+  v.t_col = prm->t_col;
+  v.key0 = (uint32_t)(prm->seed & 0xffffffffu);
+  v.key1 = (uint32_t)(prm->seed >> 32);
+  v.st = b->d_st;
+  v.v1 = b->d_v1;
+  v.v2 = b->d_v2;
+  v.A = b->d_A;
+  v.b = b->d_b;
+  v.S = b->d_S;
+  v.flags = b->d_flags;
+  v.cand_idx = b->d_cidx;
+  v.cstar = b->d_cstar;
+  v.dist = b->d_dist;
+  v.c32 = b->d_c32;
+  v.cnorm = b->d_cn;
+  v.bits = b->d_bits;
+  v.placed_idx = b->d_pidx;
+  v.placed_delta = b->d_pdelta;
+  v.sample_tiles = b->d_stiles;
+  v.bisect_tiles = b->d_btiles;
+  v.summary = b->d_sum;
+  v.robot = robot->d_robot;
+  v.envs = b->d_envs;
+  v.max_obs_pad = b->max_obs_pad;
+  v.nsp_pad = robot->nsp_pad;
+  v.np_max = b->np_max;
+  v.path_first = b->d_path_first;
+  v.max_path_len = b->max_path_len;
+  v.graph_cond = 0;
+  // launch shapes: lanes per configuration from the work per round
+  const int sms = sm_count();
+  long long tot_np = 0;
+  for (auto& s : b->st0) tot_np += s.n_p;
+  b->T_check = auto_lanes(b->total_s);
+  b->T_bisect = auto_lanes(tot_np);
+  b->grid_sample = std::max(1, std::min(b->max_sample_tiles, sms * 16));
+  b->grid_check = std::max(1, std::min(b->max_sample_tiles, sms * 16));
+  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles, sms * 16));
+  *out = b;
+  g_err.clear();
+  return EZO_OK;
+}
+
+void ezo_batch_free(ezo_batch* b) {
+  if (!b) return;
+  batch_free_device(b);
+  delete b;
+}
+
+ezo_status ezo_batch_reset(ezo_batch* b, const double* v1, const double* v2, void* stream_v) {
+  if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_reset: null batch");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  const size_t B = b->B, n = b->n, mc = b->m_cap;
+  if (v1) EZO_CUDA(cudaMemcpyAsync(b->d_v1, v1, sizeof(double) * B * n, cudaMemcpyHostToDevice, s));
+  if (v2) EZO_CUDA(cudaMemcpyAsync(b->d_v2, v2, sizeof(double) * B * n, cudaMemcpyHostToDevice, s));
+  EZO_CUDA(cudaMemcpyAsync(b->d_st, b->d_st0, sizeof(SegState) * B, cudaMemcpyDeviceToDevice, s));
+  EZO_CUDA(cudaMemcpyAsync(b->d_A, b->d_A0, sizeof(double) * B * mc * n, cudaMemcpyDeviceToDevice, s));
+  EZO_CUDA(cudaMemcpyAsync(b->d_b, b->d_b0, sizeof(double) * B * mc, cudaMemcpyDeviceToDevice, s));
+  EZO_CUDA(cudaMemsetAsync(b->d_sum, 0, sizeof(RoundSummary), s));
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_run(ezo_batch* b, int32_t mode, void* stream) {
+  if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_run: null batch");
+  ezo_status st = run_batch(b, mode, (cudaStream_t)stream);
+  if (st == EZO_OK) g_err.clear();
+  return st;
+}
+
+ezo_status ezo_batch_run_path(ezo_batch* b, int32_t sequential, int32_t mode, void* stream_v) {
+  if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_run_path: null batch");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  const int B = b->B, L = b->max_path_len;
+  std::vector<SegState> sts;
+  std::vector<uint8_t> contained((size_t)B * L);
+  std::vector<int> kept(B, 0);
+  if (sequential) {
+    // every segment idle; activate one at a time in path order
+    for (int g = 0; g < B; ++g) {
+      ezo_status st = set_status(b, g, SEG_IDLE, s);
+      if (st != EZO_OK) return st;
+    }
+    std::vector<int> stopped(B, 0);
+    for (int g = 0; g < B; ++g) {
+      const int pf = b->path_first[g];
+      if (stopped[pf]) continue;
+      bool skip = false;
+      if (g > pf) {
+        EZO_CUDA(cudaMemsetAsync(b->d_contained, 0, (size_t)B * L, s));
+        cudaError_t e = launch_containment(b->view, b->d_contained, 1e-9, s);
+        if (e != cudaSuccess) return cuda_fail(e, "containment");
+        EZO_CUDA(cudaMemcpyAsync(contained.data(), b->d_contained, (size_t)B * L, cudaMemcpyDeviceToHost, s));
+        EZO_CUDA(cudaStreamSynchronize(s));
+        for (int j = pf; j < g; ++j)
+          if (kept[j] && contained[(size_t)g * L + (j - pf)]) skip = true;
+      }
+      if (skip) {
+        ezo_status st = set_status(b, g, SEG_SKIPPED, s);
+        if (st != EZO_OK) return st;
+        continue;
+      }
+      ezo_status st = set_status(b, g, SEG_ACTIVE, s);
+      if (st != EZO_OK) return st;
+      st = run_batch(b, EZO_RUN_HOST_LOOP, s);
+      if (st != EZO_OK) return st;
+      kept[g] = 1;
+      SegState one;
+      EZO_CUDA(cudaMemcpyAsync(&one, &b->d_st[g], sizeof(SegState), cudaMemcpyDeviceToHost, s));
+      EZO_CUDA(cudaStreamSynchronize(s));
+      if (one.status == SEG_IN_COLLISION) stopped[pf] = 1;
+    }
+    (void)mode;
+  } else {
+    ezo_status st = run_batch(b, mode, s);
+    if (st != EZO_OK) return st;
+    EZO_CUDA(cudaMemsetAsync(b->d_contained, 0, (size_t)B * L, s));
+    cudaError_t e = launch_containment(b->view, b->d_contained, 1e-9, s);
+    if (e != cudaSuccess) return cuda_fail(e, "containment");
+    EZO_CUDA(cudaMemcpyAsync(contained.data(), b->d_contained, (size_t)B * L, cudaMemcpyDeviceToHost, s));
+    st = read_states(b, sts, s);
+    if (st != EZO_OK) return st;
+    std::vector<int> stopped(B, 0);
+    for (int g = 0; g < B; ++g) {
+      const int pf = b->path_first[g];
+      bool skip = stopped[pf] != 0;
+      for (int j = pf; j < g && !skip; ++j)
+        if (kept[j] && contained[(size_t)g * L + (j - pf)]) skip = true;
+      if (skip) {
+        st = set_status(b, g, stopped[pf] ? SEG_IDLE : SEG_SKIPPED, s);
+        if (st != EZO_OK) return st;
+        continue;
+      }
+      kept[g] = 1;
+      if (sts[g].status == SEG_IN_COLLISION) stopped[pf] = 1;
+    }
+  }
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_get_segment(const ezo_batch* b, int32_t seg, int32_t* status, int32_t* rounds, int32_t* m,
+                                 int32_t* planes, int64_t* checks) {
+  if (!b || seg < 0 || seg >= b->B) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_get_segment: bad segment");
+  SegState s;
+  EZO_CUDA(cudaMemcpy(&s, &b->d_st[seg], sizeof(SegState), cudaMemcpyDeviceToHost));
+  if (status) *status = s.status;
+  if (rounds) *rounds = s.rounds;
+  if (m) *m = s.m;
+  if (planes) *planes = s.planes;
+  if (checks) *checks = s.checks;
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_get_polytope(const ezo_batch* b, int32_t seg, int32_t* m, double* A, double* bv) {
+  if (!b || seg < 0 || seg >= b->B) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_get_polytope: bad segment");
+  SegState s;
+  EZO_CUDA(cudaMemcpy(&s, &b->d_st[seg], sizeof(SegState), cudaMemcpyDeviceToHost));
+  if (m) *m = s.m;
+  if (A) EZO_CUDA(cudaMemcpy(A, b->d_A + (size_t)seg * b->m_cap * b->n, sizeof(double) * s.m * b->n,
+                             cudaMemcpyDeviceToHost));
+  if (bv) EZO_CUDA(cudaMemcpy(bv, b->d_b + (size_t)seg * b->m_cap, sizeof(double) * s.m, cudaMemcpyDeviceToHost));
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_capacity(const ezo_batch* b, int32_t* m_cap, int32_t* s_cap) {
+  if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_capacity: null batch");
+  if (m_cap) *m_cap = b->m_cap;
+  if (s_cap) *s_cap = b->s_cap_max;
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_step(ezo_batch* b, int32_t step, void* stream) {
+  if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_step: null batch");
+  return launch_step(b, step, (cudaStream_t)stream);
+}
+
+ezo_status ezo_batch_sync(ezo_batch* b, void* stream) {
+  if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_sync: null batch");
+  EZO_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  collect_profile(b);
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_read(const ezo_batch* b, int32_t seg, int32_t what, void* dst, int64_t bytes) {
+  if (!b || seg < 0 || seg >= b->B || !dst) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: bad argument");
+  SegState s;
+  EZO_CUDA(cudaMemcpy(&s, &b->d_st[seg], sizeof(SegState), cudaMemcpyDeviceToHost));
+  const int n = b->n;
+  size_t need = 0;
+  const void* src = nullptr;
+  switch (what) {
+    case 0: need = sizeof(float) * (size_t)n * s.s_cap; src = b->d_S + (size_t)n * s.sample_off; break;
+    case 1: need = (size_t)s.s_cap; src = b->d_flags + s.sample_off; break;
+    case 2: need = sizeof(int) * (size_t)s.n_p; src = b->d_cidx + s.cand_off; break;
+    case 3: need = sizeof(double) * (size_t)n * s.n_p; src = b->d_cstar + (size_t)n * s.cand_off; break;
+    case 4: need = sizeof(double) * (size_t)s.n_p; src = b->d_dist + s.cand_off; break;
+    case 5: need = sizeof(uint32_t) * (size_t)s.n_p; src = b->d_bits + s.cand_off; break;
+    case 6: {
+      if (bytes < (int64_t)(12 * sizeof(int32_t))) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
+      int32_t* o = (int32_t*)dst;
+      const int32_t vals[12] = {s.k, s.status, s.m, s.n_samples, s.m_test, s.count,
+                                s.n_cand, s.planes, s.rounds, s.n_placed, s.n_p, s.env};
+      std::memcpy(o, vals, sizeof(vals));
+      return EZO_OK;
+    }
+    case 9: {
+      if (bytes < (int64_t)(2 * sizeof(int64_t))) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
+      const int64_t vals[2] = {s.checks - s.checks_bisect, s.checks_bisect};
+      std::memcpy(dst, vals, sizeof(vals));
+      return EZO_OK;
+    }
+    case 10: {
+      if (bytes < (int64_t)sizeof(RoundSummary)) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
+      EZO_CUDA(cudaMemcpy(dst, b->d_sum, sizeof(RoundSummary), cudaMemcpyDeviceToHost));
+      return EZO_OK;
+    }
+    case 7: need = sizeof(int) * (size_t)b->prm.n_f; src = b->d_pidx + (size_t)seg * b->prm.n_f; break;
+    case 8: need = sizeof(double) * (size_t)b->prm.n_f; src = b->d_pdelta + (size_t)seg * b->prm.n_f; break;
+    default: return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: unknown buffer");
+  }
+  if (bytes < (int64_t)need) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
+  EZO_CUDA(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_write_samples(ezo_batch* b, int32_t seg, const float* samples, int32_t count) {
+  if (!b || seg < 0 || seg >= b->B || !samples || count < 0)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_write_samples: bad argument");
+  SegState s;
+  EZO_CUDA(cudaMemcpy(&s, &b->d_st[seg], sizeof(SegState), cudaMemcpyDeviceToHost));
+  if (count > s.s_cap) return fail(EZO_ERR_CAPACITY, "ezo_batch_write_samples: count exceeds sample capacity");
+  for (int j = 0; j < b->n; ++j)
+    EZO_CUDA(cudaMemcpy(b->d_S + (size_t)b->n * s.sample_off + (size_t)j * s.s_cap, samples + (size_t)j * count,
+                        sizeof(float) * count, cudaMemcpyHostToDevice));
+  EZO_CUDA(cudaMemcpy(&b->d_st[seg].n_samples, &count, sizeof(int), cudaMemcpyHostToDevice));
+  return EZO_OK;
+}
+
+ezo_status ezo_profile_enable(int32_t on) {
+  g_prof_on = on != 0;
+  return EZO_OK;
+}
+
+ezo_status ezo_profile_reset(void) {
+  for (int i = 0; i < kKinds; ++i) {
+    g_prof_ms[i] = 0.0;
+    g_prof_n[i] = 0;
+  }
+  return EZO_OK;
+}
+
+ezo_status ezo_profile_read(double* ms, int64_t* launches, int32_t n_kinds) {
+  for (int i = 0; i < n_kinds && i < kKinds; ++i) {
+    if (ms) ms[i] = g_prof_ms[i];
+    if (launches) launches[i] = g_prof_n[i];
+  }
+  return EZO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+// Device-side building blocks of the EI-ZO hot path (sm_103a).
+//
+// * Philox4x32-10 counter-based generator (Salmon et al., SC'11), used by the
+//   hit-and-run walks of Sec. IV-B / IV-D.
+// * Forward kinematics of a standard DH chain in FP32 and the sphere
+//   collision test (robot vs obstacle spheres and listed self pairs) that the
+//   paper's GPU collision checker performs (Sec. IV-D, Sec. V-B).
+//
+// Collision test, per robot sphere i and obstacle j:
+//   ||c_i - o_j||^2 < (r_i + R_j)^2
+//   <=>  t_ij = c_i.o_j + r_i R_j - (|o_j|^2 - R_j^2)/2  >  hu_i = (|c_i|^2 - r_i^2)/2.
+// t_ij is four FP32 FMAs per pair; a sphere is decided from max_j t_ij - hu_i
+// when that margin exceeds a rounding bound E, and re-checked with the
+// direct difference form otherwise, so labels equal the direct FP32 test.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define EZO_MAX_DOF 16
+#define EZO_MAX_SPHERES 256
+#define EZO_MAX_OBS 4096
+#define EZO_CH 8
+
+namespace ezo {
+
+// ------------------------------------------------------------------ Philox --
+struct u32x4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+  }
+  return c;
+}
+
+// [0, 1): top 24 bits times 2^-24 (exact in FP32).
+__device__ __forceinline__ float u01_co(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-8f; }
+// (0, 1]: (top 24 bits + 1) times 2^-24 (exact in FP32).
+__device__ __forceinline__ float u01_oc(uint32_t x) { return (float)((x >> 8) + 1u) * 5.9604644775390625e-8f; }
+
+// ------------------------------------------------------------------ robot --
+// Device image of a robot: DH chain plus spheres sorted by the frame they are
+// attached to. Lives in global memory; kernels stage the small part in smem.
+struct RobotDev {
+  int n;              // degrees of freedom (<= EZO_MAX_DOF)
+  int n_spheres;      // real spheres
+  int n_spheres_pad;  // multiple of EZO_CH; padding spheres never collide
+  int n_self;         // listed self pairs
+  float ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
+  int frame_first[EZO_MAX_DOF + 2];  // sorted spheres of frame f: [frame_first[f], frame_first[f+1])
+  float4 sph[EZO_MAX_SPHERES];       // local x, y, z and radius (sorted by frame)
+  const ushort2* self_pairs;         // [n_self] indices into the sorted spheres
+  const float* self_rr;              // [n_self] (r_i + r_j)^2
+};
+
+// The part of RobotDev a block keeps in shared memory.
+struct RobotSmem {
+  float ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
+  int frame_first[EZO_MAX_DOF + 2];
+  int n, n_spheres, n_spheres_pad, n_self;
+};
+
+__device__ __forceinline__ void stage_robot(RobotSmem& rs, float4* sph_s, const RobotDev* __restrict__ rd) {
+  for (int i = threadIdx.x; i < EZO_MAX_DOF; i += blockDim.x) {
+    rs.ca[i] = rd->ca[i];
+    rs.sa[i] = rd->sa[i];
+    rs.a[i] = rd->a[i];
+    rs.d[i] = rd->d[i];
+    rs.toff[i] = rd->toff[i];
+  }
+  for (int i = threadIdx.x; i < EZO_MAX_DOF + 2; i += blockDim.x) rs.frame_first[i] = rd->frame_first[i];
+  if (threadIdx.x == 0) {
+    rs.n = rd->n;
+    rs.n_spheres = rd->n_spheres;
+    rs.n_spheres_pad = rd->n_spheres_pad;
+    rs.n_self = rd->n_self;
+  }
+  const int np = rd->n_spheres_pad;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) sph_s[i] = rd->sph[i];
+}
+
+// Obstacle set in global memory: (x, y, z, R) and -(|o|^2 - R^2)/2, padded to
+// a multiple of EZO_CH with far-away spheres that can never collide.
+struct EnvDev {
+  const float4* obs;
+  const float* nhw;
+  int n_obs;
+  int n_obs_pad;
+};
+
+__device__ __forceinline__ void stage_env(float4* obs_s, float* nhw_s, const EnvDev& e) {
+  for (int i = threadIdx.x; i < e.n_obs_pad; i += blockDim.x) {
+    obs_s[i] = e.obs[i];
+    nhw_s[i] = e.nhw[i];
+  }
+}
+
+// -------------------------------------------------- FK + collision test --
+// One configuration evaluated by a group of T lanes of one warp (T in 1..8).
+// Lane lg of the group computes the centres of spheres s with s % T == lg
+// (every lane walks the chain), the group shares them through smem slot
+// `cen`, then lane lg sweeps obstacles j with j % T == lg and self pairs
+// p with p % T == lg. Returns the group-wide OR. Every lane of the warp must
+// call this together (invalid configurations are evaluated and discarded).
+template <int NDOF, int T>
+__device__ __forceinline__ bool collide_group(const float* __restrict__ q, const RobotSmem& rs,
+                                              const float4* __restrict__ sph_s,
+                                              const float4* __restrict__ obs_s,
+                                              const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
+                                              const ushort2* __restrict__ self_pairs,
+                                              const float* __restrict__ self_rr, float E,
+                                              float4* __restrict__ cen, int lg) {
+  // ---- forward kinematics: columns of R_f and origin o_f, frame by frame ----
+  float c0x = 1.f, c0y = 0.f, c0z = 0.f;
+  float c1x = 0.f, c1y = 1.f, c1z = 0.f;
+  float c2x = 0.f, c2y = 0.f, c2z = 1.f;
+  float px = 0.f, py = 0.f, pz = 0.f;
+  const int n = rs.n;
+#pragma unroll
+  for (int f = 0; f <= NDOF; ++f) {
+    if (f > n) break;
+    if (f > 0) {
+      const int j = f - 1;
+      float s, c;
+      sincosf(q[j] + rs.toff[j], &s, &c);
+      // R_{j} Rz(theta): col0' = c col0 + s col1, col1' = -s col0 + c col1
+      const float n0x = fmaf(c, c0x, s * c1x), n0y = fmaf(c, c0y, s * c1y), n0z = fmaf(c, c0z, s * c1z);
+      const float n1x = fmaf(c, c1x, -s * c0x), n1y = fmaf(c, c1y, -s * c0y), n1z = fmaf(c, c1z, -s * c0z);
+      // o_{j+1} = o_j + a col0' + d col2
+      const float aj = rs.a[j], dj = rs.d[j];
+      px = fmaf(aj, n0x, fmaf(dj, c2x, px));
+      py = fmaf(aj, n0y, fmaf(dj, c2y, py));
+      pz = fmaf(aj, n0z, fmaf(dj, c2z, pz));
+      // Rx(alpha): col1'' = ca col1' + sa col2, col2'' = -sa col1' + ca col2
+      const float ca = rs.ca[j], sa = rs.sa[j];
+      const float m1x = fmaf(ca, n1x, sa * c2x), m1y = fmaf(ca, n1y, sa * c2y), m1z = fmaf(ca, n1z, sa * c2z);
+      const float m2x = fmaf(ca, c2x, -sa * n1x), m2y = fmaf(ca, c2y, -sa * n1y), m2z = fmaf(ca, c2z, -sa * n1z);
+      c0x = n0x; c0y = n0y; c0z = n0z;
+      c1x = m1x; c1y = m1y; c1z = m1z;
+      c2x = m2x; c2y = m2y; c2z = m2z;
+    }
+    const int s_end = rs.frame_first[f + 1];
+    int s = rs.frame_first[f];
+    s += (lg - s) & (T - 1);
+    for (; s < s_end; s += T) {
+      const float4 l = sph_s[s];
+      const float cx = fmaf(c0x, l.x, fmaf(c1x, l.y, fmaf(c2x, l.z, px)));
+      const float cy = fmaf(c0y, l.x, fmaf(c1y, l.y, fmaf(c2y, l.z, py)));
+      const float cz = fmaf(c0z, l.x, fmaf(c1z, l.y, fmaf(c2z, l.z, pz)));
+      const float hu = 0.5f * fmaf(cx, cx, fmaf(cy, cy, fmaf(cz, cz, -l.w * l.w)));
+      cen[s] = make_float4(cx, cy, cz, hu);
+    }
+  }
+  for (int s = rs.n_spheres + lg; s < rs.n_spheres_pad; s += T) cen[s] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+  __syncwarp();
+
+  // ---- robot spheres vs obstacle spheres ----
+  bool hit = false;
+  for (int s0 = 0; s0 < rs.n_spheres_pad; s0 += EZO_CH) {
+    float4 cc[EZO_CH];
+    float rr[EZO_CH], m[EZO_CH];
+#pragma unroll
+    for (int k = 0; k < EZO_CH; ++k) {
+      cc[k] = cen[s0 + k];
+      rr[k] = sph_s[s0 + k].w;
+      m[k] = -3.0e38f;
+    }
+#pragma unroll 4
+    for (int j = lg; j < n_obs_pad; j += T) {
+      const float4 o = obs_s[j];
+      const float w = nhw_s[j];
+#pragma unroll
+      for (int k = 0; k < EZO_CH; ++k) {
+        float t = fmaf(rr[k], o.w, w);
+        t = fmaf(cc[k].z, o.z, t);
+        t = fmaf(cc[k].y, o.y, t);
+        t = fmaf(cc[k].x, o.x, t);
+        m[k] = fmaxf(m[k], t);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < EZO_CH; ++k) {
+      const float diff = m[k] - cc[k].w;
+      if (diff > E) {
+        hit = true;
+      } else if (diff >= -E) {
+        // inside the rounding band of the fast form: decide with differences
+        for (int j = lg; j < n_obs; j += T) {
+          const float4 o = obs_s[j];
+          const float dx = cc[k].x - o.x, dy = cc[k].y - o.y, dz = cc[k].z - o.z;
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float sr = rr[k] + o.w;
+          if (d2 < sr * sr) hit = true;
+        }
+      }
+    }
+  }
+  // ---- listed self pairs (direct difference form) ----
+  for (int p = lg; p < rs.n_self; p += T) {
+    const ushort2 pr = self_pairs[p];
+    const float4 a = cen[pr.x], b = cen[pr.y];
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (d2 < self_rr[p]) hit = true;
+  }
+  __syncwarp();
+  if (T > 1) {
+    unsigned h = hit ? 1u : 0u;
+#pragma unroll
+    for (int off = 1; off < T; off <<= 1) h |= __shfl_xor_sync(0xffffffffu, h, off, T);
+    hit = h != 0u;
+  }
+  return hit;
+}
+
+// Exact signed distance min over pairs of ||c_i - c_j|| - r_i - r_j for one
+// configuration, one lane per configuration (used for labels and checks).
+template <int NDOF>
+__device__ float signed_distance_one(const float* __restrict__ q, const RobotSmem& rs,
+                                     const float4* __restrict__ sph_s, const float4* __restrict__ obs_s,
+                                     int n_obs, const ushort2* __restrict__ self_pairs,
+                                     const float* __restrict__ self_rr, float4* __restrict__ cen) {
+  float c0x = 1.f, c0y = 0.f, c0z = 0.f, c1x = 0.f, c1y = 1.f, c1z = 0.f, c2x = 0.f, c2y = 0.f, c2z = 1.f;
+  float px = 0.f, py = 0.f, pz = 0.f;
+  const int n = rs.n;
+#pragma unroll
+  for (int f = 0; f <= NDOF; ++f) {
+    if (f > n) break;
+    if (f > 0) {
+      const int j = f - 1;
+      float s, c;
+      sincosf(q[j] + rs.toff[j], &s, &c);
+      const float n0x = fmaf(c, c0x, s * c1x), n0y = fmaf(c, c0y, s * c1y), n0z = fmaf(c, c0z, s * c1z);
+      const float n1x = fmaf(c, c1x, -s * c0x), n1y = fmaf(c, c1y, -s * c0y), n1z = fmaf(c, c1z, -s * c0z);
+      const float aj = rs.a[j], dj = rs.d[j];
+      px = fmaf(aj, n0x, fmaf(dj, c2x, px));
+      py = fmaf(aj, n0y, fmaf(dj, c2y, py));
+      pz = fmaf(aj, n0z, fmaf(dj, c2z, pz));
+      const float ca = rs.ca[j], sa = rs.sa[j];
+      const float m1x = fmaf(ca, n1x, sa * c2x), m1y = fmaf(ca, n1y, sa * c2y), m1z = fmaf(ca, n1z, sa * c2z);
+      const float m2x = fmaf(ca, c2x, -sa * n1x), m2y = fmaf(ca, c2y, -sa * n1y), m2z = fmaf(ca, c2z, -sa * n1z);
+      c0x = n0x; c0y = n0y; c0z = n0z;
+      c1x = m1x; c1y = m1y; c1z = m1z;
+      c2x = m2x; c2y = m2y; c2z = m2z;
+    }
+    for (int s = rs.frame_first[f]; s < rs.frame_first[f + 1]; ++s) {
+      const float4 l = sph_s[s];
+      cen[s] = make_float4(fmaf(c0x, l.x, fmaf(c1x, l.y, fmaf(c2x, l.z, px))),
+                           fmaf(c0y, l.x, fmaf(c1y, l.y, fmaf(c2y, l.z, py))),
+                           fmaf(c0z, l.x, fmaf(c1z, l.y, fmaf(c2z, l.z, pz))), l.w);
+    }
+  }
+  float best = 3.0e38f;
+  for (int s = 0; s < rs.n_spheres; ++s) {
+    const float4 c = cen[s];
+    for (int j = 0; j < n_obs; ++j) {
+      const float4 o = obs_s[j];
+      const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
+      best = fminf(best, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - c.w - o.w);
+    }
+  }
+  for (int p = 0; p < rs.n_self; ++p) {
+    const ushort2 pr = self_pairs[p];
+    const float4 a = cen[pr.x], b = cen[pr.y];
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    best = fminf(best, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - a.w - b.w);
+  }
+  return best;
+}
+
+}  // namespace ezo

@@ -1,0 +1,123 @@
+// Shared declarations of the EI-ZO engine: per-segment device state, the
+// batch layout and the kernel launchers (Algorithm 1 of arXiv 2504.10783,
+// one kernel per step, batched over segments).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ezo_device.cuh"
+
+namespace ezo {
+
+enum SegStatus : int {
+  SEG_ACTIVE = 0,
+  SEG_ACCEPTED = 1,
+  SEG_IN_COLLISION = 2,  // t_col triggered (Sec. IV-C)
+  SEG_CAPACITY = 3,
+  SEG_MAX_ITER = 6,      // N_it reached (Sec. IV-C), guarantee void
+  SEG_IDLE = 7,          // not (yet) scheduled in this batch
+  SEG_SKIPPED = 8,       // contained in an earlier polytope (Sec. VI-A)
+};
+
+constexpr int kTile = 128;  // samples / candidates per work tile
+
+struct SegState {
+  int k;          // current round (1-based)
+  int status;     // SegStatus
+  int m;          // rows of A in use
+  int n_samples;  // |S| of the current round
+  int m_test;     // M of the current round
+  int count;      // collisions among the first M samples
+  int n_cand;     // candidates selected this round (<= N_p)
+  int planes;     // hyperplanes added so far
+  int rounds;     // rounds run
+  int n_placed;   // planes added in the last round
+  int n_p;        // N_p of this segment
+  int env;        // obstacle set
+  uint32_t stream;  // Philox stream id (counter word 3)
+  int pad0;
+  long long checks;      // exact collision checks so far
+  long long sample_off;  // first sample slot of this segment
+  long long cand_off;    // first candidate slot
+  int s_cap;             // sample capacity
+  int pad1;
+  long long checks_bisect;  // of which at bisection midpoints
+};
+
+struct EnvDevFull {
+  EnvDev e;
+  float E;  // rounding band of the fast pair test for this robot/env
+  float pad;
+};
+
+struct RoundSummary {
+  int active;
+  int round;
+  int n_sample_tiles;
+  int n_bisect_tiles;
+};
+
+// Everything a round kernel needs, by value (kernel parameter space).
+struct BatchView {
+  int B;      // segments
+  int n;      // DOF
+  int m_cap;  // row capacity per segment
+  int n_f, n_b, n_mix, n_it_max;
+  double eps, delta, tau, step_back_max, t_col;
+  uint32_t key0, key1;
+  SegState* st;
+  const double* v1;  // [B][n]
+  const double* v2;  // [B][n]
+  double* A;         // [B][m_cap][n]
+  double* b;         // [B][m_cap]
+  float* S;          // samples: segment g at S + n*sample_off, [n][s_cap]
+  uint8_t* flags;    // [sample_off + i]
+  int* cand_idx;     // [cand_off + c]
+  double* cstar;     // [n*cand_off + d*n_p + c]
+  double* dist;      // [cand_off + c]
+  float* c32;        // [n*cand_off + d*n_p + c]
+  float* cnorm;      // [cand_off + c]
+  uint32_t* bits;    // [cand_off + c]
+  int* placed_idx;   // [B][n_f]   candidate index of each plane of the last round
+  double* placed_delta;  // [B][n_f]
+  int2* sample_tiles;    // (segment, first sample)
+  int2* bisect_tiles;    // (segment, first candidate)
+  RoundSummary* summary;
+  const RobotDev* robot;
+  const EnvDevFull* envs;
+  int check_projection;  // fail fast: check c_proj before bisecting (Sec. IV-C)
+  int max_obs_pad;       // largest padded obstacle count over the batch's envs
+  int nsp_pad;           // padded sphere count of the robot
+  int np_max;            // largest N_p over the batch
+  const int* path_first; // first segment of the path each segment belongs to
+  int max_path_len;
+  int pad;
+  unsigned long long graph_cond;  // cudaGraphConditionalHandle (0 = none)
+};
+
+// Launchers (ezo_kernels.cu). T = lanes per configuration.
+cudaError_t launch_check_flat(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, float E, const float* q,
+                              long long ldq, long long N, uint8_t* flags, int T, int grid_cap, cudaStream_t s);
+cudaError_t launch_sd_flat(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, const float* q, long long ldq,
+                           long long N, float* sd, cudaStream_t s);
+cudaError_t launch_sample_flat(const double* A, const double* b, int m, int lda, int n, const double* v1h,
+                               const double* v2h, long long N, int n_mix, uint64_t seed, uint32_t stream, int k,
+                               float* out, long long ldo, cudaStream_t s);
+
+cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s);
+cudaError_t launch_round_sample(const BatchView& v, int grid, cudaStream_t s);
+cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s);
+cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s);
+cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s);
+cudaError_t launch_round_place(const BatchView& v, cudaStream_t s);
+cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
+
+// Containment of segment endpoints in earlier polytopes of the same path
+// (Sec. VI-A): contained[k*max_path_len + d] = 1 iff both endpoints of
+// segment k satisfy A_j x <= b_j + tol for j = path_first[k] + d < k.
+cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s);
+
+size_t check_smem_bytes(int n_spheres_pad, int n_obs_pad, int threads, int T);
+
+}  // namespace ezo

@@ -1,0 +1,273 @@
+// EI-ZO round kernels, first half (arXiv 2504.10783, Algorithm 1):
+//   round_begin  - round size: delta_k (Eq. 9), M and |S| = max(N_p, M)
+//   sample       - hit-and-run, one walk per sample (Sec. IV-B, IV-D)
+//   check        - forward kinematics + sphere collision pairs (Sec. IV-D)
+//   certify      - unadaptive test on the first M samples and stable
+//                  selection of the first N_p colliding samples (Sec. IV-B)
+#include "ezo_kernels_common.cuh"
+
+namespace ezo {
+
+// ------------------------------------------------------------ round kernels --
+// Round size of Sec. IV-B: delta_k = 6 delta / (pi^2 k^2),
+// M = ceil(2 ln(1/delta_k) / (eps tau^2)), |S| = max(N_p, M).
+__device__ __forceinline__ int round_test_size(int k, double eps, double delta, double tau) {
+  const double dk = 6.0 * delta / (3.141592653589793 * 3.141592653589793 * (double)k * (double)k);
+  return (int)ceil(2.0 * log(1.0 / dk) / (eps * tau * tau));
+}
+
+__global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
+  __shared__ int warp_sum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < v.B; base += blockDim.x) {
+    const int g = base + threadIdx.x;
+    int tiles = 0;
+    if (g < v.B) {
+      SegState& st = v.st[g];
+      if (st.status == SEG_ACTIVE) {
+        const int M = round_test_size(st.k, v.eps, v.delta, v.tau);
+        int S = M > st.n_p ? M : st.n_p;
+        if (S > st.s_cap) S = st.s_cap;  // capacity is sized for M at N_it; never hit
+        st.m_test = M;
+        st.n_samples = S;
+        st.n_cand = 0;
+        st.count = 0;
+        st.n_placed = 0;
+        tiles = (S + kTile - 1) / kTile;
+      }
+    }
+    // block exclusive scan of tiles
+    int x = tiles;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < nw ? warp_sum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const int excl = carry + (wid ? warp_sum[wid - 1] : 0) + x - tiles;
+    for (int t = 0; t < tiles; ++t) v.sample_tiles[excl + t] = make_int2(g, t * kTile);
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sum[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    v.summary->n_sample_tiles = carry;
+    v.summary->n_bisect_tiles = 0;
+  }
+}
+
+template <int NDOF>
+__global__ void __launch_bounds__(128) k_round_sample(BatchView v) {
+  extern __shared__ float smf[];
+  __shared__ SampleParams p;
+  __shared__ int cur_seg;
+  const int n_tiles = v.summary->n_sample_tiles;
+  float* A32 = smf;
+  float* b32 = smf + v.m_cap * NDOF;
+  if (threadIdx.x == 0) cur_seg = -1;
+  __syncthreads();
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int2 tile = v.sample_tiles[t];
+    const SegState& st = v.st[tile.x];
+    if (tile.x != cur_seg) {
+      __syncthreads();
+      stage_polytope<NDOF>(A32, b32, v.A + (long long)tile.x * v.m_cap * v.n, v.b + (long long)tile.x * v.m_cap,
+                           st.m, v.n, v.n);
+      if (threadIdx.x < EZO_MAX_DOF) {
+        const int j = threadIdx.x;
+        const double a1 = j < v.n ? v.v1[tile.x * v.n + j] : 0.0;
+        const double a2 = j < v.n ? v.v2[tile.x * v.n + j] : 0.0;
+        p.v1f[j] = (float)a1;
+        p.ef[j] = (float)(a2 - a1);
+      }
+      if (threadIdx.x == 0) {
+        p.n_mix = v.n_mix;
+        p.key0 = v.key0;
+        p.key1 = v.key1;
+        p.stream = st.stream;
+        p.round_k = (uint32_t)st.k;
+        cur_seg = tile.x;
+      }
+      __syncthreads();
+    }
+    const int i = tile.y + threadIdx.x;
+    if (i < st.n_samples) {
+      float x[NDOF];
+      hnr_walk<NDOF>(A32, b32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
+      float* S = v.S + (long long)v.n * st.sample_off;
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j)
+        if (j < v.n) S[(long long)j * st.s_cap + i] = x[j];
+    }
+  }
+}
+
+template <int NDOF, int T>
+__global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pad) {
+  extern __shared__ float4 smem4[];
+  __shared__ RobotSmem rs;
+  __shared__ int cur_env;
+  const RobotDev* robot = v.robot;
+  const int nsp = robot->n_spheres_pad;
+  const int groups = blockDim.x / T;
+  float4* sph_s = smem4;
+  float4* obs_s = sph_s + nsp;
+  float4* cen_all = obs_s + max_obs_pad;
+  float* nhw_s = reinterpret_cast<float*>(cen_all + groups * (nsp + 1));
+  stage_robot(rs, sph_s, robot);
+  if (threadIdx.x == 0) cur_env = -1;
+  __syncthreads();
+  const int gi = threadIdx.x / T, lg = threadIdx.x % T;
+  float4* cen = cen_all + gi * (nsp + 1);
+  const int n_tiles = v.summary->n_sample_tiles;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int2 tile = v.sample_tiles[t];
+    const SegState& st = v.st[tile.x];
+    const EnvDevFull& ef = v.envs[st.env];
+    if (st.env != cur_env) {
+      __syncthreads();
+      stage_env(obs_s, nhw_s, ef.e);
+      if (threadIdx.x == 0) cur_env = st.env;
+      __syncthreads();
+    }
+    const float* S = v.S + (long long)v.n * st.sample_off;
+    uint8_t* fl = v.flags + st.sample_off;
+    for (int sub = 0; sub < kTile; sub += groups) {
+      const int i = tile.y + sub + gi;
+      const bool valid = i < st.n_samples;
+      const int ic = valid ? i : tile.y;
+      float qq[NDOF];
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j) qq[j] = (j < v.n) ? S[(long long)j * st.s_cap + ic] : 0.f;
+      const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
+                                              robot->self_pairs, robot->self_rr, ef.E, cen, lg);
+      if (valid && lg == 0) fl[i] = hit ? 1 : 0;
+    }
+  }
+}
+
+// Unadaptive test on the first M samples and stable compaction of the first
+// N_p colliding samples (lowest sample index first). One block per segment.
+__global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
+  const int g = blockIdx.x;
+  SegState& st = v.st[g];
+  if (st.status != SEG_ACTIVE) return;
+  __shared__ int warp_cnt[32];
+  __shared__ int warp_col[32];
+  __shared__ int s_running;
+  __shared__ int s_count;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int S = st.n_samples, M = st.m_test, np = st.n_p;
+  const uint8_t* fl = v.flags + st.sample_off;
+  int* cidx = v.cand_idx + st.cand_off;
+  if (threadIdx.x == 0) {
+    s_running = 0;
+    s_count = 0;
+  }
+  __syncthreads();
+  int my_count = 0;
+  for (int base = 0; base < S; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int f = (i < S) ? (fl[i] != 0) : 0;
+    if (i < M) my_count += f;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int pre = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_col[wid] = __popc(bal);
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < nw ? warp_col[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) warp_cnt[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    const int running = s_running;
+    const int pos = running + (wid ? warp_cnt[wid - 1] : 0) + pre;
+    if (f && pos < np) cidx[pos] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) s_running = running + warp_cnt[nw - 1];
+    __syncthreads();
+    if (s_running >= np && base + (int)blockDim.x >= M) break;
+  }
+  // block reduction of the count over the first M samples
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_count += __shfl_xor_sync(0xffffffffu, my_count, o);
+  if (lane == 0) atomicAdd(&s_count, my_count);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int cnt = s_count;
+    st.count = cnt;
+    st.checks += S;
+    const bool accept = (double)cnt <= (double)M * (1.0 - v.tau) * v.eps;
+    if (accept) {
+      st.status = SEG_ACCEPTED;
+      st.rounds = st.k;
+      st.n_cand = 0;
+    } else {
+      const int nc = s_running < np ? s_running : np;
+      st.n_cand = nc;
+      st.checks += (long long)nc * v.n_b;
+      st.checks_bisect += (long long)nc * v.n_b;
+      const int nt = (nc + kTile - 1) / kTile;
+      const int t0 = atomicAdd(&v.summary->n_bisect_tiles, nt);
+      for (int t = 0; t < nt; ++t) v.bisect_tiles[t0 + t] = make_int2(g, t * kTile);
+    }
+  }
+}
+
+cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s) {
+  k_round_begin<<<1, 1024, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_round_sample(const BatchView& v, int grid, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  EZO_DISPATCH_NDOF(v.n, {
+    const size_t smem = (size_t)v.m_cap * (ND + 1) * sizeof(float);
+    auto kern = k_round_sample<ND>;
+    err = set_smem(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, 128, smem, s>>>(v);
+  });
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T);
+  EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
+    auto kern = k_round_check<ND, TT>;
+    err = set_smem(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+  }));
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s) {
+  k_round_certify<<<v.B, 1024, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+
+}  // namespace ezo

@@ -1,0 +1,351 @@
+// EI-ZO round kernels, second half (arXiv 2504.10783, Algorithm 1, Sec. VI-A):
+//   bisect       - projection onto L (Eqs. 6-7) and N_b bisection steps
+//                  toward it (Sec. IV-B, IV-C)
+//   place        - order by distance to L, place up to N_f half spaces with
+//                  step back (Eqs. 10-12), discard separated candidates
+//   round_end    - round counter, iteration cap N_it (Sec. IV-C)
+//   containment  - segment endpoints inside earlier polytopes (Sec. VI-A)
+#include "ezo_kernels_common.cuh"
+
+namespace ezo {
+
+template <int NDOF, int T>
+__global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_pad) {
+  extern __shared__ float4 smem4[];
+  __shared__ RobotSmem rs;
+  __shared__ int cur_env;
+  const RobotDev* robot = v.robot;
+  const int nsp = robot->n_spheres_pad;
+  const int groups = blockDim.x / T;
+  float4* sph_s = smem4;
+  float4* obs_s = sph_s + nsp;
+  float4* cen_all = obs_s + max_obs_pad;
+  float* nhw_s = reinterpret_cast<float*>(cen_all + groups * (nsp + 1));
+  stage_robot(rs, sph_s, robot);
+  if (threadIdx.x == 0) cur_env = -1;
+  __syncthreads();
+  const int gi = threadIdx.x / T, lg = threadIdx.x % T;
+  float4* cen = cen_all + gi * (nsp + 1);
+  const int n = v.n;
+  const int n_tiles = v.summary->n_bisect_tiles;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int2 tile = v.bisect_tiles[t];
+    const int g = tile.x;
+    const SegState& st = v.st[g];
+    const EnvDevFull& ef = v.envs[st.env];
+    if (st.env != cur_env) {
+      __syncthreads();
+      stage_env(obs_s, nhw_s, ef.e);
+      if (threadIdx.x == 0) cur_env = st.env;
+      __syncthreads();
+    }
+    const double* v1 = v.v1 + (long long)g * n;
+    const double* v2 = v.v2 + (long long)g * n;
+    const float* S = v.S + (long long)n * st.sample_off;
+    const int np = st.n_p;
+    for (int sub = 0; sub < kTile; sub += groups) {
+      const int c = tile.y + sub + gi;
+      const bool valid = c < st.n_cand;
+      const int cc = valid ? c : tile.y;
+      const int si = v.cand_idx[st.cand_off + cc];
+      double cs[NDOF], p[NDOF], dv[NDOF];
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
+      project_fp64<NDOF>(cs, v1, v2, n, p);
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j) dv[j] = (j < n) ? cs[j] - p[j] : 0.0;
+      double lo = 0.0, hi = 1.0;
+      uint32_t bits = 0u;
+      for (int s = 0; s < v.n_b; ++s) {
+        const double mid = 0.5 * (lo + hi);
+        float qq[NDOF];
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) qq[j] = (float)fma(mid, dv[j], p[j]);
+        const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
+                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg);
+        if (hit) {
+          hi = mid;
+          bits |= 1u << s;
+        } else {
+          lo = mid;
+        }
+      }
+      if (valid && lg == 0) {
+        double cst[NDOF], ps[NDOF];
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, dv[j], p[j]) : 0.0;
+        project_fp64<NDOF>(cst, v1, v2, n, ps);
+        double d2 = 0.0;
+        float cn2 = 0.f;
+        const long long co = st.cand_off;
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) {
+          if (j < n) {
+            const double e = cst[j] - ps[j];
+            d2 = fma(e, e, d2);
+            v.cstar[(long long)n * co + (long long)j * np + c] = cst[j];
+            const float f = (float)cst[j];
+            v.c32[(long long)n * co + (long long)j * np + c] = f;
+            cn2 = fmaf(f, f, cn2);
+          }
+        }
+        v.dist[co + c] = sqrt(d2);
+        v.cnorm[co + c] = sqrtf(cn2);
+        v.bits[co + c] = bits;
+      }
+    }
+  }
+}
+
+// Greedy placement: repeatedly take the closest surviving candidate (ties by
+// sample index), place a_i^T x <= b_i - Delta_i, discard candidates with
+// a_i^T c_j > b_i - Delta_i; at most N_f planes. One block per segment.
+// The discard test runs in FP32 with a rounding bound and falls back to FP64
+// inside the bound, so every decision equals the FP64 decision.
+__global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
+  const int g = blockIdx.x;
+  SegState& st = v.st[g];
+  if (st.status != SEG_ACTIVE) return;
+  const int nc = st.n_cand;
+  const int n = v.n;
+  const int np = st.n_p;
+  const long long co = st.cand_off;
+  extern __shared__ uint32_t alive[];  // nc bits
+  __shared__ unsigned long long red_key[32];
+  __shared__ int red_idx[32];
+  __shared__ int s_best;
+  __shared__ double s_a[EZO_MAX_DOF];
+  __shared__ float s_a32[EZO_MAX_DOF];
+  __shared__ double s_beta;
+  __shared__ float s_beta32;
+  __shared__ int s_stop;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nwords = (nc + 31) >> 5;
+  for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+    const int rem = nc - (w << 5);
+    alive[w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+  }
+  if (threadIdx.x == 0) s_stop = 0;
+  __syncthreads();
+  const double* dist = v.dist + co;
+  const int* cidx = v.cand_idx + co;
+  const double* v1 = v.v1 + (long long)g * n;
+  const double* v2 = v.v2 + (long long)g * n;
+  double* A = v.A + (long long)g * v.m_cap * n;
+  double* bb = v.b + (long long)g * v.m_cap;
+  int placed = 0;
+  const float u = 5.9604644775390625e-8f;
+  for (int f = 0; f < v.n_f; ++f) {
+    // argmin over survivors of (distance, sample index)
+    unsigned long long best_key = ~0ull;
+    int best_i = 0x7fffffff;
+    int best_c = -1;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      if (!((alive[c >> 5] >> (c & 31)) & 1u)) continue;
+      const unsigned long long key = (unsigned long long)__double_as_longlong(dist[c]);
+      const int si = cidx[c];
+      if (key < best_key || (key == best_key && si < best_i)) {
+        best_key = key;
+        best_i = si;
+        best_c = c;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best_key, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, best_i, o);
+      const int c2 = __shfl_xor_sync(0xffffffffu, best_c, o);
+      if (k2 < best_key || (k2 == best_key && i2 < best_i)) {
+        best_key = k2;
+        best_i = i2;
+        best_c = c2;
+      }
+    }
+    if (lane == 0) {
+      red_key[wid] = best_key;
+      red_idx[wid] = best_c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long bk = ~0ull;
+      int bi = 0x7fffffff, bc = -1;
+      for (int w = 0; w < nw; ++w) {
+        const int c = red_idx[w];
+        if (c < 0) continue;
+        const unsigned long long k2 = red_key[w];
+        const int i2 = cidx[c];
+        if (k2 < bk || (k2 == bk && i2 < bi)) {
+          bk = k2;
+          bi = i2;
+          bc = c;
+        }
+      }
+      s_best = bc;
+      if (bc < 0) {
+        s_stop = 1;
+      } else if (dist[bc] <= v.t_col) {
+        s_stop = 2;  // segment likely in collision (Sec. IV-C)
+      } else if (st.m >= v.m_cap) {
+        s_stop = 3;
+      } else {
+        // a = grad dist_L(c*) = (c* - c_proj) / ||c* - c_proj||, b = a^T c* (Eq. 10)
+        double cst[EZO_MAX_DOF], ps[EZO_MAX_DOF];
+        for (int j = 0; j < EZO_MAX_DOF; ++j) cst[j] = j < n ? v.cstar[(long long)n * co + (long long)j * np + bc] : 0.0;
+        project_fp64<EZO_MAX_DOF>(cst, v1, v2, n, ps);
+        double nn = 0.0;
+        for (int j = 0; j < n; ++j) nn = fma(cst[j] - ps[j], cst[j] - ps[j], nn);
+        nn = sqrt(nn);
+        double bval = 0.0, av1 = 0.0, av2 = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const double a = (cst[j] - ps[j]) / nn;
+          s_a[j] = a;
+          s_a32[j] = (float)a;
+          bval = fma(a, cst[j], bval);
+          av1 = fma(a, v1[j], av1);
+          av2 = fma(a, v2[j], av2);
+        }
+        // step back (Eqs. 11-12): r = max(a^T v1, a^T v2) - b + Delta_max
+        const double r = fmax(av1, av2) - bval + v.step_back_max;
+        const double delta = r > 0.0 ? v.step_back_max - r : v.step_back_max;
+        const double beta = bval - delta;
+        s_beta = beta;
+        s_beta32 = (float)beta;
+        const int row = st.m;
+        for (int j = 0; j < n; ++j) A[(long long)row * n + j] = s_a[j];
+        bb[row] = beta;
+        st.m = row + 1;
+        v.placed_idx[g * v.n_f + f] = bc;
+        v.placed_delta[g * v.n_f + f] = delta;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    ++placed;
+    const int bc = s_best;
+    const double beta = s_beta;
+    const float beta32 = s_beta32;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      if (!((alive[c >> 5] >> (c & 31)) & 1u)) continue;
+      bool out;
+      if (c == bc) {
+        out = true;
+      } else {
+        float s32 = 0.f;
+        for (int j = 0; j < n; ++j) s32 = fmaf(s_a32[j], v.c32[(long long)n * co + (long long)j * np + c], s32);
+        const float bound = 2.f * (float)(n + 4) * u * (v.cnorm[co + c] + fabsf(beta32)) + 1e-30f;
+        if (fabsf(s32 - beta32) > bound) {
+          out = s32 > beta32;
+        } else {
+          double s = 0.0;
+          for (int j = 0; j < n; ++j) s = fma(s_a[j], v.cstar[(long long)n * co + (long long)j * np + c], s);
+          out = s > beta;
+        }
+      }
+      if (out) atomicAnd(&alive[c >> 5], ~(1u << (c & 31)));
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st.n_placed = placed;
+    st.planes += placed;
+    if (s_stop == 2) {
+      st.status = SEG_IN_COLLISION;
+      st.rounds = st.k;
+    } else if (s_stop == 3) {
+      st.status = SEG_CAPACITY;
+      st.rounds = st.k;
+    }
+  }
+}
+
+__global__ void k_round_end(BatchView v) {
+  __shared__ int s_active;
+  if (threadIdx.x == 0) s_active = 0;
+  __syncthreads();
+  int act = 0;
+  for (int g = threadIdx.x; g < v.B; g += blockDim.x) {
+    SegState& st = v.st[g];
+    if (st.status == SEG_ACTIVE) {
+      if (st.k >= v.n_it_max) {
+        st.status = SEG_MAX_ITER;
+        st.rounds = st.k;
+      } else {
+        st.k += 1;
+        ++act;
+      }
+    }
+  }
+  if (act) atomicAdd(&s_active, act);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    v.summary->active = s_active;
+    v.summary->round += 1;
+#if CUDART_VERSION >= 12040
+    if (v.graph_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)v.graph_cond, s_active > 0 ? 1u : 0u);
+#endif
+  }
+}
+
+__global__ void k_containment(BatchView v, uint8_t* contained, double tol) {
+  // one block per (k, j) pair of the same path with j < k
+  const int k = blockIdx.x;
+  const int j = v.path_first[k] + (int)blockIdx.y;
+  if (j >= k) return;
+  const int n = v.n;
+  const SegState& sj = v.st[j];
+  __shared__ int s_out;
+  if (threadIdx.x == 0) s_out = 0;
+  __syncthreads();
+  const double* A = v.A + (long long)j * v.m_cap * n;
+  const double* b = v.b + (long long)j * v.m_cap;
+  const double* p1 = v.v1 + (long long)k * n;
+  const double* p2 = v.v2 + (long long)k * n;
+  for (int r = threadIdx.x; r < sj.m; r += blockDim.x) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < n; ++c) {
+      s1 = fma(A[(long long)r * n + c], p1[c], s1);
+      s2 = fma(A[(long long)r * n + c], p2[c], s2);
+    }
+    if (s1 > b[r] + tol || s2 > b[r] + tol) s_out = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) contained[(long long)k * v.max_path_len + blockIdx.y] = s_out ? 0 : 1;
+}
+
+cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
+  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T);
+  EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
+    auto kern = k_round_bisect<ND, TT>;
+    err = set_smem(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+  }));
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_round_place(const BatchView& v, cudaStream_t s) {
+  // alive bitmask for the largest N_p of the batch
+  const size_t smem = (size_t)((v.np_max + 31) / 32) * sizeof(uint32_t);
+  cudaError_t err = set_smem(k_round_place, smem);
+  if (err != cudaSuccess) return err;
+  k_round_place<<<v.B, 1024, smem, s>>>(v);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_round_end(const BatchView& v, cudaStream_t s) {
+  k_round_end<<<1, 256, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s) {
+  dim3 grid(v.B, v.max_path_len);
+  k_containment<<<grid, 128, 0, s>>>(v, contained, tol);
+  return cudaGetLastError();
+}
+
+
+}  // namespace ezo

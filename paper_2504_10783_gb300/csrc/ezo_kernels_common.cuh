@@ -1,0 +1,171 @@
+// Device helpers shared by the kernel translation units: hit-and-run walk,
+// polytope staging, shared-memory layout of the collision kernels, FP64
+// projection onto the seed segment, template dispatch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ezo_engine.cuh"
+
+namespace ezo {
+
+// ------------------------------------------------------------- hit-and-run --
+struct SampleParams {
+  float v1f[EZO_MAX_DOF];
+  float ef[EZO_MAX_DOF];
+  int n_mix;
+  uint32_t key0, key1, stream, round_k;
+};
+
+// One hit-and-run walk of `n_mix` steps inside {x : A32 x <= b32}.
+// Random stream: Philox block (walk, draw, round, stream); draw 0 gives the
+// start x = v1 + u (v2 - v1); step s uses draws 1 + s W .. 1 + s W + W - 1
+// whose 4W words are uniforms u_0..: Gaussian pair i from (u_2i, u_2i+1) by
+// Box-Muller, step length from u_{2 ceil(n/2)}.
+template <int NDOF>
+__device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, const float* __restrict__ b32, int m,
+                                         int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
+                                         uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
+                                         float (&x)[NDOF]) {
+  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
+  const int npair = (n + 1) / 2;
+  const int W = (2 * npair + 4) / 4;
+  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
+  const float u0 = u01_co(r0.x);
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
+  for (int s = 0; s < n_mix; ++s) {
+    uint32_t w[4 * WMAX];
+#pragma unroll
+    for (int b = 0; b < WMAX; ++b) {
+      if (b < W) {
+        const u32x4 r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, key0, key1);
+        w[4 * b] = r.x;
+        w[4 * b + 1] = r.y;
+        w[4 * b + 2] = r.z;
+        w[4 * b + 3] = r.w;
+      } else {
+        w[4 * b] = w[4 * b + 1] = w[4 * b + 2] = w[4 * b + 3] = 0u;
+      }
+    }
+    float d[NDOF];
+    float nrm2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < (NDOF + 1) / 2; ++i) {
+      const float rho = sqrtf(-2.f * logf(u01_oc(w[2 * i])));
+      float sn, cs;
+      sincospif(2.f * u01_co(w[2 * i + 1]), &sn, &cs);
+      if (2 * i < NDOF) d[2 * i] = (2 * i < n) ? rho * cs : 0.f;
+      if (2 * i + 1 < NDOF) d[2 * i + 1] = (2 * i + 1 < n) ? rho * sn : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) nrm2 = fmaf(d[j], d[j], nrm2);
+    float ut = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4 * WMAX; ++i)
+      if (i == 2 * npair) ut = u01_co(w[i]);
+    const bool ok = nrm2 > 0.f;
+    const float inv = ok ? 1.f / sqrtf(nrm2) : 0.f;
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) d[j] *= inv;
+    float t_lo = -INFINITY, t_hi = INFINITY;
+    for (int r = 0; r < m; ++r) {
+      const float* a = A32 + r * NDOF;
+      float ax = 0.f, ad = 0.f;
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j) {
+        ax = fmaf(a[j], x[j], ax);
+        ad = fmaf(a[j], d[j], ad);
+      }
+      const float sl = b32[r] - ax;
+      if (ad > 0.f) t_hi = fminf(t_hi, sl / ad);
+      else if (ad < 0.f) t_lo = fmaxf(t_lo, sl / ad);
+    }
+    t_hi = fmaxf(t_hi, 0.f);
+    t_lo = fminf(t_lo, 0.f);
+    if (ok && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
+      const float t = fmaf(ut, t_hi - t_lo, t_lo);
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j) x[j] = fmaf(t, d[j], x[j]);
+    }
+  }
+}
+
+template <int NDOF>
+__device__ __forceinline__ void stage_polytope(float* A32, float* b32, const double* __restrict__ A,
+                                               const double* __restrict__ b, int m, int lda, int n) {
+  for (int i = threadIdx.x; i < m * NDOF; i += blockDim.x) {
+    const int r = i / NDOF, c = i - r * NDOF;
+    A32[i] = (c < n) ? (float)A[(long long)r * lda + c] : 0.f;
+  }
+  for (int r = threadIdx.x; r < m; r += blockDim.x) b32[r] = (float)b[r];
+}
+
+// ------------------------------------------------------- collision checks --
+__host__ __device__ inline size_t check_smem_layout(int nsp, int nobs, int threads, int T) {
+  return (size_t)(nsp + nobs + (threads / T) * (nsp + 1)) * sizeof(float4) + (size_t)nobs * sizeof(float);
+}
+
+
+// Projection of Eqs. (6)-(7) in FP64: c_proj = (1 - alpha) v1 + alpha v2.
+template <int NDOF>
+__device__ __forceinline__ void project_fp64(const double (&c)[NDOF], const double* v1, const double* v2, int n,
+                                             double (&p)[NDOF]) {
+  double ee = 0.0, ce = 0.0;
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    if (j < n) {
+      const double e = v2[j] - v1[j];
+      ee = fma(e, e, ee);
+      ce = fma(c[j] - v1[j], e, ce);
+    }
+  }
+  double alpha = 0.0;
+  if (ee > 0.0) alpha = fmin(fmax(ce / ee, 0.0), 1.0);
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) p[j] = (j < n) ? ((ee > 0.0) ? (1.0 - alpha) * v1[j] + alpha * v2[j] : v1[j]) : 0.0;
+}
+
+#define EZO_DISPATCH_NDOF(n, ...)            \
+  do {                                       \
+    if ((n) == 7) {                          \
+      constexpr int ND = 7;                  \
+      __VA_ARGS__;                           \
+    } else if ((n) == 3) {                   \
+      constexpr int ND = 3;                  \
+      __VA_ARGS__;                           \
+    } else {                                 \
+      constexpr int ND = EZO_MAX_DOF;        \
+      __VA_ARGS__;                           \
+    }                                        \
+  } while (0)
+
+#define EZO_DISPATCH_T(T, ...)               \
+  do {                                       \
+    if ((T) == 1) {                          \
+      constexpr int TT = 1;                  \
+      __VA_ARGS__;                           \
+    } else if ((T) == 2) {                   \
+      constexpr int TT = 2;                  \
+      __VA_ARGS__;                           \
+    } else if ((T) == 4) {                   \
+      constexpr int TT = 4;                  \
+      __VA_ARGS__;                           \
+    } else {                                 \
+      constexpr int TT = 8;                  \
+      __VA_ARGS__;                           \
+    }                                        \
+  } while (0)
+
+// Raises a kernel's dynamic shared memory limit once per (kernel, size).
+template <typename K>
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+  static size_t done = 48 * 1024;
+  if (bytes <= done) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = bytes;
+  return e;
+}
+
+}  // namespace ezo

@@ -1,0 +1,408 @@
+"""Thin ctypes binding of libezo.so (include/ezo.h). Argument marshalling only:
+every step of the inflation runs in the library's CUDA kernels. Device
+buffers are torch tensors; host inputs are numpy arrays. There is no CPU
+fallback: importing this module on a machine without the built library, or
+calling it without a CUDA device, raises."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libezo.so")
+
+EZO_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "segment in collision", 3: "capacity", 4: "timeout",
+                5: "cuda error", 6: "max iterations"}
+SEG_ACTIVE, SEG_ACCEPTED, SEG_IN_COLLISION, SEG_CAPACITY, SEG_MAX_ITER, SEG_IDLE, SEG_SKIPPED = 0, 1, 2, 3, 6, 7, 8
+RUN_HOST_LOOP, RUN_GRAPH = 0, 1
+STEP_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
+
+
+class EzoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ezo status {status} ({STATUS_NAMES.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("delta", C.c_double), ("tau", C.c_double), ("step_back_max", C.c_double),
+                ("t_col", C.c_double), ("n_p", C.c_int32), ("n_f", C.c_int32), ("n_b", C.c_int32),
+                ("n_mix", C.c_int32), ("n_it_max", C.c_int32), ("reserved0", C.c_int32), ("seed", C.c_uint64)]
+
+    @staticmethod
+    def make(**kw) -> "Params":
+        p = Params()
+        lib().ezo_params_default(C.byref(p))
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        return p
+
+
+_lib = None
+_P = C.c_void_p
+_I32 = C.c_int32
+_I64 = C.c_int64
+_DP = C.POINTER(C.c_double)
+
+
+def _sig(lib):
+    f = lib
+    f.ezo_last_error.restype = C.c_char_p
+    f.ezo_params_default.argtypes = [C.POINTER(Params)]
+    f.ezo_robot_create.argtypes = [_I32, _DP, _DP, _DP, _DP, _DP, _DP, _I32, C.POINTER(_I32), _DP, _DP, _I32,
+                                   C.POINTER(_I32), C.POINTER(_P)]
+    f.ezo_robot_free.argtypes = [_P]
+    f.ezo_robot_dof.argtypes = [_P]
+    f.ezo_env_create.argtypes = [_I32, _DP, C.POINTER(_P)]
+    f.ezo_env_free.argtypes = [_P]
+    f.ezo_check_collision.argtypes = [_P, _P, _P, _I64, _I64, _P, _I32, _P]
+    f.ezo_signed_distance.argtypes = [_P, _P, _P, _I64, _I64, _P, _P]
+    f.ezo_hit_and_run.argtypes = [_P, _P, _I32, _I32, _I32, _DP, _DP, _I64, _I32, C.c_uint64, C.c_uint32, _I32, _P,
+                                  _I64, _P]
+    f.ezo_batch_create.argtypes = [_P, _I32, C.POINTER(_P), _I32, _DP, _DP, C.POINTER(_I32), C.POINTER(_I32),
+                                   C.POINTER(C.c_uint32), C.POINTER(_I32), _DP, _DP, _I32, C.POINTER(Params),
+                                   C.POINTER(_P)]
+    f.ezo_batch_free.argtypes = [_P]
+    f.ezo_batch_run.argtypes = [_P, _I32, _P]
+    f.ezo_batch_reset.argtypes = [_P, _DP, _DP, _P]
+    f.ezo_batch_run_path.argtypes = [_P, _I32, _I32, _P]
+    f.ezo_batch_get_segment.argtypes = [_P, _I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32),
+                                        C.POINTER(_I32), C.POINTER(_I64)]
+    f.ezo_batch_get_polytope.argtypes = [_P, _I32, C.POINTER(_I32), _DP, _DP]
+    f.ezo_batch_capacity.argtypes = [_P, C.POINTER(_I32), C.POINTER(_I32)]
+    f.ezo_batch_step.argtypes = [_P, _I32, _P]
+    f.ezo_batch_sync.argtypes = [_P, _P]
+    f.ezo_batch_read.argtypes = [_P, _I32, _I32, _P, _I64]
+    f.ezo_batch_write_samples.argtypes = [_P, _I32, C.POINTER(C.c_float), _I32]
+    f.ezo_profile_enable.argtypes = [_I32]
+    f.ezo_profile_read.argtypes = [_DP, C.POINTER(_I64), _I32]
+    f.ezo_check_flops.argtypes = [_P, _P]
+    f.ezo_check_flops.restype = C.c_double
+    return lib
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() or "
+                               "python -m paper_2504_10783_gb300.build")
+        _lib = _sig(C.CDLL(LIB_PATH))
+    return _lib
+
+
+def _check(status: int):
+    if status != EZO_OK:
+        raise EzoError(status, lib().ezo_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(_I32))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _need_cuda(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}")
+
+
+class Robot:
+    """ezo_robot handle built from a workloads.Robot."""
+
+    def __init__(self, r: workloads.Robot):
+        self.desc = r
+        f64 = lambda x: np.ascontiguousarray(x, dtype=np.float64)
+        i32 = lambda x: np.ascontiguousarray(x, dtype=np.int32)
+        self._keep = [f64(r.a), f64(r.alpha), f64(r.d), f64(r.theta_off), f64(r.q_lo), f64(r.q_hi),
+                      i32(r.sphere_frame), f64(r.sphere_xyz.reshape(-1)), f64(r.sphere_r),
+                      i32(r.self_pairs.reshape(-1))]
+        k = self._keep
+        h = _P()
+        _check(lib().ezo_robot_create(r.n, _dp(k[0]), _dp(k[1]), _dp(k[2]), _dp(k[3]), _dp(k[4]), _dp(k[5]),
+                                      r.n_spheres, _ip(k[6]), _dp(k[7]), _dp(k[8]), r.self_pairs.shape[0],
+                                      _ip(k[9]), C.byref(h)))
+        self.h = h
+        self.n = r.n
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ezo_robot_free(self.h)
+            self.h = None
+
+
+class Env:
+    """ezo_env handle built from an (N_obs, 4) array or a workloads.Env."""
+
+    def __init__(self, spheres):
+        if isinstance(spheres, workloads.Env):
+            spheres = spheres.spheres
+        a = np.ascontiguousarray(spheres, dtype=np.float64).reshape(-1, 4)
+        self.spheres = a
+        h = _P()
+        _check(lib().ezo_env_create(a.shape[0], _dp(a.reshape(-1)), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ezo_env_free(self.h)
+            self.h = None
+
+
+def check_collision(robot: Robot, env: Env, q_dev, flags_dev, lanes: int = 0, stream=None):
+    """flags_dev[i] = 1 iff configuration q_dev[:, i] collides (q_dev: float32
+    CUDA tensor [n, N] with unit stride along N)."""
+    import torch
+    _need_cuda(q_dev, torch.float32, "q_dev")
+    _need_cuda(flags_dev, torch.uint8, "flags_dev")
+    n, N = q_dev.shape
+    if n != robot.n or q_dev.stride(1) != 1 or flags_dev.numel() < N:
+        raise ValueError("q_dev must be [n, N] with stride(1) == 1 and flags_dev must hold N entries")
+    _check(lib().ezo_check_collision(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, q_dev.stride(0),
+                                     C.c_void_p(flags_dev.data_ptr()), lanes, _stream(stream)))
+
+
+def signed_distance(robot: Robot, env: Env, q_dev, sd_dev, stream=None):
+    import torch
+    _need_cuda(q_dev, torch.float32, "q_dev")
+    _need_cuda(sd_dev, torch.float32, "sd_dev")
+    n, N = q_dev.shape
+    if n != robot.n or q_dev.stride(1) != 1 or sd_dev.numel() < N:
+        raise ValueError("bad shapes")
+    _check(lib().ezo_signed_distance(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, q_dev.stride(0),
+                                     C.c_void_p(sd_dev.data_ptr()), _stream(stream)))
+
+
+def hit_and_run(A_dev, b_dev, v1, v2, N: int, n_mix: int, seed: int, stream_id: int, round_k: int, out_dev,
+                stream=None):
+    """N hit-and-run walks inside {A x <= b} (A_dev float64 [m, n] CUDA,
+    b_dev float64 [m]); writes out_dev float32 [n, N]."""
+    import torch
+    _need_cuda(A_dev, torch.float64, "A_dev")
+    _need_cuda(b_dev, torch.float64, "b_dev")
+    _need_cuda(out_dev, torch.float32, "out_dev")
+    m, n = A_dev.shape
+    v1 = np.ascontiguousarray(v1, dtype=np.float64)
+    v2 = np.ascontiguousarray(v2, dtype=np.float64)
+    if out_dev.shape[0] != n or out_dev.stride(1) != 1 or out_dev.shape[1] < N or A_dev.stride(1) != 1:
+        raise ValueError("bad shapes")
+    _check(lib().ezo_hit_and_run(C.c_void_p(A_dev.data_ptr()), C.c_void_p(b_dev.data_ptr()), m, n, A_dev.stride(0),
+                                 _dp(v1), _dp(v2), N, n_mix, seed, stream_id, round_k,
+                                 C.c_void_p(out_dev.data_ptr()), out_dev.stride(0), _stream(stream)))
+
+
+@dataclasses.dataclass
+class SegmentResult:
+    status: int
+    rounds: int
+    m: int
+    planes: int
+    checks: int
+    A: np.ndarray
+    b: np.ndarray
+
+
+class Batch:
+    """ezo_batch: many segments inflated together (Algorithm 1 per segment)."""
+
+    def __init__(self, robot: Robot, envs, v1, v2, params: Params, seg_env=None, seg_np=None, seg_stream=None,
+                 path_first=None, A0=None, b0=None):
+        envs = list(envs) if isinstance(envs, (list, tuple)) else [envs]
+        self.robot = robot
+        self.envs = envs
+        self.n = robot.n
+        v1 = np.ascontiguousarray(np.atleast_2d(v1), dtype=np.float64)
+        v2 = np.ascontiguousarray(np.atleast_2d(v2), dtype=np.float64)
+        self.B = v1.shape[0]
+        self.v1, self.v2 = v1, v2
+        arr = (_P * len(envs))(*[e.h for e in envs])
+        keep = []
+
+        def opt_i32(x):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dtype=np.int32)
+            keep.append(a)
+            return _ip(a)
+
+        def opt_u32(x):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dtype=np.uint32)
+            keep.append(a)
+            return a.ctypes.data_as(C.POINTER(C.c_uint32))
+
+        m0 = 0
+        Ap = bp = None
+        if A0 is not None:
+            A0 = np.ascontiguousarray(A0, dtype=np.float64)
+            b0 = np.ascontiguousarray(b0, dtype=np.float64)
+            keep += [A0, b0]
+            m0 = A0.shape[0]
+            Ap, bp = _dp(A0), _dp(b0)
+        self.params = params
+        h = _P()
+        _check(lib().ezo_batch_create(robot.h, len(envs), arr, self.B, _dp(v1), _dp(v2), opt_i32(seg_env),
+                                      opt_i32(seg_np), opt_u32(seg_stream), opt_i32(path_first), Ap, bp, m0,
+                                      C.byref(params), C.byref(h)))
+        self.h = h
+        mc, sc = _I32(), _I32()
+        _check(lib().ezo_batch_capacity(h, C.byref(mc), C.byref(sc)))
+        self.m_cap, self.s_cap = mc.value, sc.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ezo_batch_free(self.h)
+            self.h = None
+
+    def reset(self, v1=None, v2=None, stream=None):
+        a1 = a2 = None
+        if v1 is not None:
+            self._v1h = np.ascontiguousarray(v1, dtype=np.float64)
+            a1 = _dp(self._v1h)
+        if v2 is not None:
+            self._v2h = np.ascontiguousarray(v2, dtype=np.float64)
+            a2 = _dp(self._v2h)
+        _check(lib().ezo_batch_reset(self.h, a1, a2, _stream(stream)))
+
+    def run(self, mode: int = RUN_HOST_LOOP, stream=None):
+        _check(lib().ezo_batch_run(self.h, mode, _stream(stream)))
+
+    def run_path(self, sequential: bool = True, mode: int = RUN_HOST_LOOP, stream=None):
+        _check(lib().ezo_batch_run_path(self.h, 1 if sequential else 0, mode, _stream(stream)))
+
+    def step(self, step: int, stream=None):
+        _check(lib().ezo_batch_step(self.h, step, _stream(stream)))
+
+    def sync(self, stream=None):
+        _check(lib().ezo_batch_sync(self.h, _stream(stream)))
+
+    def segment(self, g: int) -> SegmentResult:
+        st, rd, m, pl = _I32(), _I32(), _I32(), _I32()
+        ch = _I64()
+        _check(lib().ezo_batch_get_segment(self.h, g, C.byref(st), C.byref(rd), C.byref(m), C.byref(pl),
+                                           C.byref(ch)))
+        A = np.zeros((self.m_cap, self.n))
+        b = np.zeros(self.m_cap)
+        mm = _I32()
+        _check(lib().ezo_batch_get_polytope(self.h, g, C.byref(mm), _dp(A), _dp(b)))
+        return SegmentResult(st.value, rd.value, m.value, pl.value, ch.value, A[: mm.value].copy(),
+                             b[: mm.value].copy())
+
+    def state(self, g: int) -> dict:
+        o = np.zeros(12, dtype=np.int32)
+        _check(lib().ezo_batch_read(self.h, g, 6, C.c_void_p(o.ctypes.data), o.nbytes))
+        keys = ("k", "status", "m", "n_samples", "m_test", "count", "n_cand", "planes", "rounds", "n_placed",
+                "n_p", "env")
+        return dict(zip(keys, (int(x) for x in o)))
+
+    def read(self, g: int, what: str) -> np.ndarray:
+        st = self.state(g)
+        n, npp = self.n, st["n_p"]
+        if what == "samples":
+            o = np.zeros((n, self.s_cap), dtype=np.float32)
+            code = 0
+        elif what == "labels":
+            o = np.zeros(self.s_cap, dtype=np.uint8)
+            code = 1
+        elif what == "cand_idx":
+            o = np.zeros(npp, dtype=np.int32)
+            code = 2
+        elif what == "c_star":
+            o = np.zeros((n, npp), dtype=np.float64)
+            code = 3
+        elif what == "dist":
+            o = np.zeros(npp, dtype=np.float64)
+            code = 4
+        elif what == "bits":
+            o = np.zeros(npp, dtype=np.uint32)
+            code = 5
+        elif what == "placed_idx":
+            o = np.zeros(self.params.n_f, dtype=np.int32)
+            code = 7
+        elif what == "placed_delta":
+            o = np.zeros(self.params.n_f, dtype=np.float64)
+            code = 8
+        else:
+            raise KeyError(what)
+        _check(lib().ezo_batch_read(self.h, g, code, C.c_void_p(o.ctypes.data), o.nbytes))
+        return o
+
+    def check_split(self, g: int):
+        o = np.zeros(2, dtype=np.int64)
+        _check(lib().ezo_batch_read(self.h, g, 9, C.c_void_p(o.ctypes.data), o.nbytes))
+        return int(o[0]), int(o[1])
+
+    def summary(self) -> dict:
+        o = np.zeros(4, dtype=np.int32)
+        _check(lib().ezo_batch_read(self.h, 0, 10, C.c_void_p(o.ctypes.data), o.nbytes))
+        return dict(zip(("active", "rounds", "sample_tiles", "bisect_tiles"), (int(x) for x in o)))
+
+    def write_samples(self, g: int, samples: np.ndarray):
+        s = np.ascontiguousarray(samples, dtype=np.float32)  # [n, count]
+        _check(lib().ezo_batch_write_samples(self.h, g, s.ctypes.data_as(C.POINTER(C.c_float)), s.shape[1]))
+
+
+def profile_enable(on: bool = True):
+    _check(lib().ezo_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(lib().ezo_profile_reset())
+
+
+def profile_read() -> dict:
+    ms = np.zeros(7)
+    cnt = np.zeros(7, dtype=np.int64)
+    _check(lib().ezo_profile_read(_dp(ms), cnt.ctypes.data_as(C.POINTER(_I64)), 7))
+    return {STEP_NAMES[i]: (float(ms[i]), int(cnt[i])) for i in range(7)}
+
+
+def check_flops(robot: Robot, env: Env) -> float:
+    return float(lib().ezo_check_flops(robot.h, env.h))
+
+
+def inflate_segment(robot: Robot, env: Env, v1, v2, params: Params, A0=None, b0=None, stream_id: int = 0,
+                    mode: int = RUN_HOST_LOOP) -> SegmentResult:
+    """Algorithm 1 on one segment (batch of one)."""
+    bt = Batch(robot, [env], v1, v2, params, seg_stream=[stream_id], A0=A0, b0=b0)
+    bt.run(mode)
+    return bt.segment(0)
+
+
+def inflate_path(robot: Robot, env: Env, verts, params: Params, sequential: bool = True, mode: int = RUN_HOST_LOOP,
+                 stream_base: int = 0, A0=None, b0=None):
+    """Sec. VI-A path inflation; returns [(segment index, SegmentResult)] for
+    the segments that were inflated (not skipped), in path order."""
+    verts = np.asarray(verts, dtype=np.float64)
+    K = verts.shape[0] - 1
+    bt = Batch(robot, [env], verts[:-1], verts[1:], params, seg_stream=np.arange(K) + stream_base,
+               path_first=np.zeros(K, dtype=np.int32), A0=A0, b0=b0)
+    bt.run_path(sequential=sequential, mode=mode)
+    out = []
+    for k in range(K):
+        r = bt.segment(k)
+        if r.status not in (SEG_SKIPPED, SEG_IDLE):
+            out.append((k, r))
+    return out

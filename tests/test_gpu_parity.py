@@ -1,0 +1,359 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated here, derived in the design notes):
+* collision labels: bit-exact except where the oracle's signed distance is
+  within AMB = 1e-5 m of zero (FP32 forward kinematics);
+* signed distance: |GPU - oracle| <= 2e-5 m;
+* round size, test count, accept bit, candidate indices: exact;
+* bisection: same decisions except ambiguous midpoints (the oracle follows
+  the GPU there), c* within 1e-9;
+* hyperplanes: rows and offsets within 1e-6 relative, same placement order;
+* hit-and-run: start points within FP32 rounding; walks within 1e-3 for at
+  least 99% of samples; every sample inside P up to 1e-5 (1 + |b|).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ezo_oracle as orc
+from paper_2504_10783_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+AMB = 1e-5
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ezo():
+    from paper_2504_10783_gb300 import build, ezo as e
+    build.build()
+    return e
+
+
+def scenes():
+    with open(os.path.join(GOLDEN, "workloads.json")) as f:
+        return json.load(f)
+
+
+def planar_scene():
+    s = scenes()["planar3"]
+    return wl.planar3_robot(), wl.Env("planar", np.asarray(s["obstacles"])), np.asarray(s["v1"]), np.asarray(s["v2"])
+
+
+def dh7_scene():
+    s = scenes()["dh7"]
+    return wl.dh7_robot(), wl.box_obstacles(s["env_seed"], s["n_obs"]), np.asarray(s["path"])
+
+
+def table_env():
+    return wl.table_cloud_obstacles(31)
+
+
+def to_dev(q):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(q, dtype=np.float32).T)).cuda()
+
+
+def gpu_labels(ezo, robot, env, q, lanes=0):
+    qd = to_dev(q)
+    flags = torch.empty(q.shape[0], dtype=torch.uint8, device="cuda")
+    ezo.check_collision(robot, env, qd, flags, lanes=lanes)
+    torch.cuda.synchronize()
+    return flags.cpu().numpy().astype(bool)
+
+
+def assert_labels_match(rd, env_np, q32, got):
+    q64 = q32.astype(np.float64)
+    ref = orc.in_collision(rd, env_np, q64)
+    diff = got != ref
+    if diff.any():
+        sd = orc.signed_distance(rd, env_np, q64[diff])
+        assert np.all(np.abs(sd) < AMB), f"{int((np.abs(sd) >= AMB).sum())} labels differ outside the band"
+    return ref
+
+
+# ------------------------------------------------------- collision labels --
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("which", ["planar", "dh7", "table"])
+def test_check_collision_matches_oracle(ezo, which, lanes):
+    if which == "planar":
+        rd, env_np, _, _ = planar_scene()
+    elif which == "dh7":
+        rd, env_np, _ = dh7_scene()
+    else:
+        rd, env_np = wl.dh7_robot(), table_env()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    N = 3001  # several blocks and a ragged tail
+    q32 = wl.uniform_configs(17, rd, N).astype(np.float32)
+    got = gpu_labels(ezo, robot, env, q32, lanes)
+    ref = assert_labels_match(rd, env_np, q32, got)
+    assert 0 < ref.sum() < N
+
+
+def test_check_collision_full_batch_sampled(ezo):
+    """The bench's batch size (2e6 configurations) in the bench's launch
+    shape, checked on 3000 sampled configurations."""
+    rd, env_np, _ = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    N = 2_000_000
+    g = torch.Generator(device="cuda").manual_seed(3)
+    lo = torch.tensor(rd.q_lo, dtype=torch.float32, device="cuda")[:, None]
+    hi = torch.tensor(rd.q_hi, dtype=torch.float32, device="cuda")[:, None]
+    q = lo + (hi - lo) * torch.rand((rd.n, N), generator=g, device="cuda")
+    flags = torch.empty(N, dtype=torch.uint8, device="cuda")
+    ezo.check_collision(robot, env, q, flags)
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(0).choice(N, 3000, replace=False)
+    idx[:3] = [0, N - 1, N // 2]
+    q32 = q[:, idx].T.cpu().numpy()
+    got = flags[idx].cpu().numpy().astype(bool)
+    assert_labels_match(rd, env_np, q32, got)
+
+
+def test_check_collision_edge_cases(ezo):
+    rd, env_np, _ = dh7_scene()
+    robot = ezo.Robot(rd)
+    empty = ezo.Env(np.zeros((0, 4)))
+    q32 = wl.uniform_configs(4, rd, 500).astype(np.float32)
+    got = gpu_labels(ezo, robot, empty, q32)
+    assert_labels_match(rd, wl.Env("none", np.zeros((0, 4))), q32, got)
+    # N = 0 is a no-op
+    flags = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    ezo.check_collision(robot, empty, torch.zeros((7, 0), device="cuda"), flags)
+    # touching cases at home pose: +-2e-5 m around tangency
+    c = orc.sphere_centres(rd, np.zeros((1, 7)))[0]
+    for gap, expect in [(2e-5, False), (-2e-5, True)]:
+        o = np.array([[c[20, 0] + rd.sphere_r[20] + 0.05 + gap, c[20, 1], c[20, 2], 0.05]])
+        assert gpu_labels(ezo, robot, ezo.Env(o), np.zeros((1, 7), dtype=np.float32))[0] == expect
+    # a wrong lanes value is rejected
+    with pytest.raises(ezo.EzoError):
+        ezo.check_collision(robot, empty, to_dev(q32), torch.empty(500, dtype=torch.uint8, device="cuda"), lanes=3)
+
+
+def test_signed_distance_matches_oracle(ezo):
+    rd, env_np, _ = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    q32 = wl.uniform_configs(21, rd, 2000).astype(np.float32)
+    sd = torch.empty(2000, device="cuda")
+    ezo.signed_distance(robot, env, to_dev(q32), sd)
+    torch.cuda.synchronize()
+    ref = orc.signed_distance(rd, env_np, q32.astype(np.float64))
+    assert np.abs(sd.cpu().numpy() - ref).max() <= 2e-5
+
+
+# --------------------------------------------------------------- sampling --
+def _gpu_hnr(ezo, A, b, v1, v2, N, n_mix, seed, stream, k):
+    Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    bd = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    out = torch.empty((A.shape[1], N), dtype=torch.float32, device="cuda")
+    ezo.hit_and_run(Ad, bd, v1, v2, N, n_mix, seed, stream, k, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().T.astype(np.float64)
+
+
+def test_hit_and_run_start_points_pin_philox(ezo):
+    rd = wl.dh7_robot()
+    A, b = orc.joint_box(rd)
+    v1, v2 = np.full(7, -0.5), np.full(7, 0.8)
+    x = _gpu_hnr(ezo, A, b, v1, v2, 4099, 0, seed=77, stream=5, k=3)
+    ref = orc.hit_and_run(A, b, v1, v2, 4099, 0, seed=77, stream=5, k=3)
+    assert np.abs(x - ref).max() < 1e-6
+
+
+@pytest.mark.parametrize("which", ["box", "polytope"])
+def test_hit_and_run_matches_oracle_walks(ezo, which):
+    rd = wl.dh7_robot()
+    A, b = orc.joint_box(rd)
+    v1, v2 = np.full(7, -0.5), np.full(7, 0.8)
+    if which == "polytope":
+        rng = np.random.default_rng(1)
+        G = rng.standard_normal((30, 7))
+        G /= np.linalg.norm(G, axis=1, keepdims=True)
+        h = np.maximum(G @ v1, G @ v2) + rng.uniform(0.05, 1.0, 30)
+        A, b = np.vstack([A, G]), np.concatenate([b, h])
+    N = 3000
+    x = _gpu_hnr(ezo, A, b, v1, v2, N, 40, seed=9, stream=2, k=1)
+    ref = orc.hit_and_run(A, b, v1, v2, N, 40, seed=9, stream=2, k=1)
+    err = np.abs(x - ref).max(axis=1)
+    assert np.quantile(err, 0.99) < 1e-3, np.quantile(err, [0.5, 0.9, 0.99])
+    assert np.median(err) < 1e-4
+    assert np.all(x @ A.T <= b + 1e-5 * (1 + np.abs(b)))
+
+
+# ----------------------------------------------------- round-by-round replay --
+def _replay_rounds(ezo, rd, env_np, v1, v2, prm_kw, max_rounds=6):
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(**prm_kw)
+    oprm = orc.Params(eps=prm.eps, delta=prm.delta, tau=prm.tau, step_back_max=prm.step_back_max,
+                      t_col=prm.t_col, n_p=prm.n_p, n_f=prm.n_f, n_b=prm.n_b, n_mix=prm.n_mix,
+                      n_it_max=prm.n_it_max, seed=prm.seed)
+    bt = ezo.Batch(robot, [env], v1, v2, prm)
+    A, b = orc.joint_box(rd)
+    rounds = 0
+    total_amb = 0
+    for k in range(1, max_rounds + 1):
+        for step in range(3):
+            bt.step(step)
+        bt.sync()
+        st = bt.state(0)
+        assert st["k"] == k
+        assert st["m_test"] == orc.test_size(k, oprm.eps, oprm.delta, oprm.tau)
+        assert st["n_samples"] == orc.batch_size(k, oprm.eps, oprm.delta, oprm.tau, oprm.n_p)
+        S = bt.read(0, "samples")[:, : st["n_samples"]].T.astype(np.float64)
+        assert np.all(S @ A.T <= b + 1e-5 * (1 + np.abs(b)))
+        lab = bt.read(0, "labels")[: st["n_samples"]].astype(bool)
+        assert_labels_match(rd, env_np, S.astype(np.float32), lab)
+        bt.step(3)
+        bt.sync()
+        st = bt.state(0)
+        M = st["m_test"]
+        count = int(lab[:M].sum())
+        assert st["count"] == count
+        accept = orc.unadaptive_test(count, M, oprm.eps, oprm.tau)
+        assert (st["status"] == ezo.SEG_ACCEPTED) == accept
+        rounds = k
+        if accept:
+            break
+        idx = np.nonzero(lab)[0][: oprm.n_p]
+        assert st["n_cand"] == idx.size
+        np.testing.assert_array_equal(bt.read(0, "cand_idx")[: idx.size], idx)
+        bt.step(4)
+        bt.sync()
+        nc = idx.size
+        bits = bt.read(0, "bits")[:nc]
+        follow = ((bits[:, None] >> np.arange(oprm.n_b)[None, :]) & 1).astype(bool)
+        br = orc.bisect(rd, env_np, S[idx], v1, v2, oprm.n_b, follow=follow, band=AMB)
+        total_amb += br.ambiguous
+        np.testing.assert_array_equal(br.decisions, follow)
+        cst = bt.read(0, "c_star")[:, :nc].T
+        assert np.abs(cst - br.c_star).max() < 1e-9
+        dist = bt.read(0, "dist")[:nc]
+        np.testing.assert_allclose(dist, orc.dist_to_segment(br.c_star, v1, v2), rtol=1e-12, atol=1e-14)
+        m_before = st["m"]
+        bt.step(5)
+        bt.sync()
+        st = bt.state(0)
+        pl = orc.place_hyperplanes(cst, idx, v1, v2, oprm.n_f, oprm.step_back_max, oprm.t_col)
+        H = st["m"] - m_before
+        assert H == pl.rows_a.shape[0] == st["n_placed"]
+        res = bt.segment(0)
+        np.testing.assert_allclose(res.A[m_before:], pl.rows_a, rtol=1e-6, atol=1e-12)
+        np.testing.assert_allclose(res.b[m_before:], pl.rows_b, rtol=1e-6, atol=1e-12)
+        np.testing.assert_array_equal(bt.read(0, "placed_idx")[:H], pl.order)
+        np.testing.assert_allclose(bt.read(0, "placed_delta")[:H], pl.deltas, rtol=1e-9)
+        assert orc.segment_contained(res.A, res.b, v1, v2, tol=1e-12)
+        A, b = res.A, res.b
+        bt.step(6)
+        bt.sync()
+    return rounds, total_amb
+
+
+def test_round_replay_planar(ezo):
+    rd, env_np, v1, v2 = planar_scene()
+    rounds, _ = _replay_rounds(ezo, rd, env_np, v1, v2,
+                               dict(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, seed=1))
+    assert rounds >= 2
+
+
+def test_round_replay_dh7(ezo):
+    rd, env_np, path = dh7_scene()
+    rounds, _ = _replay_rounds(ezo, rd, env_np, path[0], path[1],
+                               dict(eps=0.05, delta=0.05, n_p=2000, n_f=10, n_b=10, n_mix=60, seed=1), max_rounds=4)
+    assert rounds >= 2
+
+
+# ------------------------------------------------------------- end to end --
+def test_inflate_segment_certified_planar(ezo):
+    rd, env_np, v1, v2 = planar_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, seed=4)
+    res = ezo.inflate_segment(robot, env, v1, v2, prm)
+    assert res.status == ezo.SEG_ACCEPTED and res.planes > 0
+    assert orc.segment_contained(res.A, res.b, v1, v2, tol=1e-12)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(rd.q_lo, rd.q_hi, size=(400000, 3))
+    x = x[np.all(x @ res.A.T <= res.b, axis=1)][:20000]
+    assert orc.in_collision(rd, env_np, x).mean() <= prm.eps
+
+
+def test_graph_mode_equals_host_loop(ezo):
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(n_p=3000, seed=5)
+    outs = []
+    for mode in (ezo.RUN_HOST_LOOP, ezo.RUN_GRAPH):
+        bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm)
+        bt.run(mode)
+        outs.append([bt.segment(g) for g in range(bt.B)])
+    for a, b in zip(*outs):
+        assert (a.status, a.rounds, a.m, a.checks) == (b.status, b.rounds, b.m, b.checks)
+        np.testing.assert_array_equal(a.A, b.A)
+        np.testing.assert_array_equal(a.b, b.b)
+
+
+def test_batched_segments_equal_single_segments(ezo):
+    """Per-segment Philox streams make a segment's result independent of the
+    batch it runs in."""
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(n_p=2000, seed=6)
+    bt = ezo.Batch(robot, [env], path[:4], path[1:5], prm)
+    bt.run()
+    for g in range(4):
+        one = ezo.inflate_segment(robot, env, path[g], path[g + 1], prm, stream_id=g)
+        many = bt.segment(g)
+        np.testing.assert_array_equal(one.A, many.A)
+        assert one.rounds == many.rounds
+
+
+def test_inflate_path_sequential_equals_speculative(ezo):
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(n_p=3000, seed=7)
+    seq = ezo.inflate_path(robot, env, path, prm, sequential=True)
+    spec = ezo.inflate_path(robot, env, path, prm, sequential=False, mode=ezo.RUN_GRAPH)
+    assert [k for k, _ in seq] == [k for k, _ in spec]
+    for (_, a), (_, b) in zip(seq, spec):
+        np.testing.assert_array_equal(a.A, b.A)
+    K = path.shape[0] - 1
+    for k in range(K):
+        assert any(orc.segment_contained(r.A, r.b, path[k], path[k + 1]) for _, r in seq)
+    for k, r in seq:
+        assert r.status == ezo.SEG_ACCEPTED
+        assert orc.segment_contained(r.A, r.b, path[k], path[k + 1], tol=1e-12)
+
+
+def test_inflate_path_matches_oracle_skip_rule(ezo):
+    """A planar path whose second half lies inside the first polytope."""
+    rd, env_np, v1, v2 = planar_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    verts = np.array([v1, 0.5 * (v1 + v2), v2])
+    prm = ezo.Params.make(eps=0.1, delta=0.05, n_p=500, n_f=10, n_b=10, n_mix=20, seed=2)
+    out = ezo.inflate_path(robot, env, verts, prm, sequential=True)
+    assert [k for k, _ in out] == [0]
+
+
+def test_segment_in_collision_reports_tcol(ezo):
+    """A segment that passes through an obstacle: candidates land within
+    t_col of L and the segment is reported in collision (Sec. IV-C)."""
+    rd, env_np, v1, v2 = planar_scene()
+    c = orc.sphere_centres(rd, (0.5 * (v1 + v2))[None])[0]
+    blocked = np.vstack([env_np.spheres, [[c[10, 0], c[10, 1], 0.0, 0.15]]])
+    robot, env = ezo.Robot(rd), ezo.Env(blocked)
+    prm = ezo.Params.make(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=20, n_mix=30, seed=3, t_col=1e-3)
+    res = ezo.inflate_segment(robot, env, v1, v2, prm)
+    assert res.status == ezo.SEG_IN_COLLISION
+
+
+def test_degenerate_segment_point(ezo):
+    """v1 = v2: the projection is v1 (Eq. 6) and inflation still works."""
+    rd, env_np, v1, _ = planar_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, seed=8)
+    res = ezo.inflate_segment(robot, env, v1, v1, prm)
+    assert res.status == ezo.SEG_ACCEPTED
+    assert np.all(res.A @ v1 <= res.b + 1e-12)
