@@ -6,6 +6,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "ezo_engine.cuh"
 
 namespace ezo {
@@ -159,13 +163,29 @@ __device__ __forceinline__ void project_fp64(const double (&c)[NDOF], const doub
   } while (0)
 
 // Raises a kernel's dynamic shared memory limit once per (kernel, size).
+// The cache is keyed by the kernel's address: instantiations that share a
+// signature must not share an entry.
+inline cudaError_t set_smem_impl(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, size_t>> done;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first == kernel && d.second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  for (auto& d : done)
+    if (d.first == kernel) {
+      d.second = bytes;
+      return e;
+    }
+  done.emplace_back(kernel, bytes);
+  return e;
+}
+
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
-  static size_t done = 48 * 1024;
-  if (bytes <= done) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) done = bytes;
-  return e;
+  return set_smem_impl(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 }  // namespace ezo

@@ -120,6 +120,11 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def _ld(t) -> int:
+    """Leading dimension of an [n, N] tensor (any value >= N when n == 1)."""
+    return max(int(t.stride(0)), int(t.shape[1])) if t.shape[0] == 1 else int(t.stride(0))
+
+
 def _need_cuda(t, dtype, name):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -177,9 +182,9 @@ def check_collision(robot: Robot, env: Env, q_dev, flags_dev, lanes: int = 0, st
     _need_cuda(q_dev, torch.float32, "q_dev")
     _need_cuda(flags_dev, torch.uint8, "flags_dev")
     n, N = q_dev.shape
-    if n != robot.n or q_dev.stride(1) != 1 or flags_dev.numel() < N:
+    if n != robot.n or (N > 1 and q_dev.stride(1) != 1) or flags_dev.numel() < N:
         raise ValueError("q_dev must be [n, N] with stride(1) == 1 and flags_dev must hold N entries")
-    _check(lib().ezo_check_collision(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, q_dev.stride(0),
+    _check(lib().ezo_check_collision(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, _ld(q_dev),
                                      C.c_void_p(flags_dev.data_ptr()), lanes, _stream(stream)))
 
 
@@ -188,9 +193,9 @@ def signed_distance(robot: Robot, env: Env, q_dev, sd_dev, stream=None):
     _need_cuda(q_dev, torch.float32, "q_dev")
     _need_cuda(sd_dev, torch.float32, "sd_dev")
     n, N = q_dev.shape
-    if n != robot.n or q_dev.stride(1) != 1 or sd_dev.numel() < N:
-        raise ValueError("bad shapes")
-    _check(lib().ezo_signed_distance(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, q_dev.stride(0),
+    if n != robot.n or (N > 1 and q_dev.stride(1) != 1) or sd_dev.numel() < N:
+        raise ValueError("q_dev must be [n, N] with stride(1) == 1 and sd_dev must hold N entries")
+    _check(lib().ezo_signed_distance(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, _ld(q_dev),
                                      C.c_void_p(sd_dev.data_ptr()), _stream(stream)))
 
 

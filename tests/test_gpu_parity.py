@@ -55,7 +55,7 @@ def table_env():
 
 
 def to_dev(q):
-    return torch.from_numpy(np.ascontiguousarray(np.asarray(q, dtype=np.float32).T)).cuda()
+    return torch.from_numpy(np.asarray(q, dtype=np.float32).T.copy()).cuda().contiguous()
 
 
 def gpu_labels(ezo, robot, env, q, lanes=0):
