@@ -235,6 +235,37 @@ ezo_status ezo_batch_read(const ezo_batch* batch, int32_t seg, int32_t what, voi
  * on given samples; sets |S| to count. */
 ezo_status ezo_batch_write_samples(ezo_batch* batch, int32_t seg, const float* samples, int32_t count);
 
+/* ---------------------------------------------------- no-allocation path --
+ * No counterpart in the paper. For callers that cannot allocate device memory
+ * when they need a region: a real-time control loop that must not block in
+ * cudaMalloc (which can synchronise the device and has no latency bound), or a
+ * host application that fixes the library's device memory at start-up.
+ * Inflates one segment v1..v2 (host FP64, n values each) from the robot's
+ * joint-limit box with the same kernels, parameters and Philox stream
+ * (stream_id) as a one-segment ezo_batch_run in HOST_LOOP mode, so the result
+ * equals that call's. All working memory comes from one file-scope device
+ * array of EZO_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits; the call itself makes no cudaMalloc, cudaFree or
+ * other allocating call. Outputs: A_out (host, at least
+ * (2n + n_f * n_it_max) x n doubles) and b_out (2n + n_f * n_it_max) receive
+ * the polytope, *m_out its row count; status_out (ezo_segment_status),
+ * rounds_out and checks_out may be NULL. The robot and env handles must have
+ * been created beforehand (their creation allocates).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture. The array is shared by every call and keeps the last
+ * call's contents; each call re-initialises what it reads. Calls that overlap
+ * on the GPU (other streams or host threads) race on the array: serialise
+ * them. Blocks until the result is on the host.
+ * Errors: EZO_ERR_INVALID_ARG; EZO_ERR_CAPACITY when the segment needs more
+ * working memory than the array holds (roughly n_p <= 16384 for n = 16) or
+ * more than 2048 rows; EZO_ERR_CUDA. */
+#define EZO_NOALLOC_SCRATCH_BYTES (6u * 1024u * 1024u)
+ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const ezo_env* env, const double* v1,
+                                       const double* v2, const ezo_params* params, uint32_t stream_id,
+                                       double* A_out, double* b_out, int32_t* m_out, int32_t* status_out,
+                                       int32_t* rounds_out, int64_t* checks_out, void* cuda_stream);
+
 /* -------------------------------------------------------------- profiling --
  * When enabled, ezo_batch_run in HOST_LOOP mode records CUDA events around
  * every kernel launch on the launch stream; ezo_profile_read returns, for

@@ -323,6 +323,31 @@ ezo_status ezo_hit_and_run(const double* A_dev, const double* b_dev, int32_t m, 
   return EZO_OK;
 }
 
+// Internal accessors for other translation units of the library (hidden).
+__attribute__((visibility("hidden"))) const RobotDev* ezo_internal_robot_dev(const ezo_robot* r, int* n,
+                                                                               int* nsp_pad, double* q_lo,
+                                                                               double* q_hi) {
+  if (!r) return nullptr;
+  *n = r->n;
+  *nsp_pad = r->nsp_pad;
+  for (int j = 0; j < r->n; ++j) {
+    q_lo[j] = r->q_lo[j];
+    q_hi[j] = r->q_hi[j];
+  }
+  return r->d_robot;
+}
+
+__attribute__((visibility("hidden"))) int ezo_internal_env_dev(const ezo_robot* r, const ezo_env* e,
+                                                                EnvDevFull* out) {
+  if (!r || !e || !out) return 1;
+  out->e = e->dev();
+  out->E = band_E(r, e);
+  out->pad = 0.f;
+  return 0;
+}
+
+__attribute__((visibility("hidden"))) void ezo_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env) {
   if (!robot || !env) return 0.0;
   return robot->fk_flops + 8.0 * ((double)robot->n_spheres * env->n_obs + robot->n_self);
