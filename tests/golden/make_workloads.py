@@ -7,10 +7,11 @@ collision-freeness needs a collision checker, checked by the FP64 oracle only.
   anywhere along L.
 * dh7 scene: 64 obstacle spheres in the 1 m cube 0.5 m ahead of the base and
   a 10-segment seed path from a random walk of 0.5 rad steps inside 0.8x the
-  joint limits; every segment is checked at <= 0.005 rad spacing and kept
-  only when the oracle's signed distance is >= ``margin`` at every check
-  point (the margin bounds how far the arm moves between check points, so the
-  whole segment is collision-free).
+  joint limits that starts near the obstacles and, of 24 collision-free
+  candidate steps, keeps the one closest to them; every segment is checked at
+  <= 0.005 rad spacing and kept only when the oracle's signed distance is
+  >= ``margin`` at every check point (the margin bounds how far the arm moves
+  between check points, so the whole segment is collision-free).
 * dh7 batched scenes: 8 obstacle sets of 128-1024 spheres in the same cube
   and 256 seed paths of 1-40 segments built the same way (written only when
   ``--batched`` is given; slower).
@@ -74,20 +75,35 @@ def planar_scene(seed=7, n_obs=16, margin=0.03):
             "seed": seed, "margin": margin}
 
 
-def random_path(robot, env, rng, n_seg, step=0.5, margin=0.02, tries=400):
+def random_path(robot, env, rng, n_seg, step=0.5, margin=0.02, tries=400, hug=0):
+    """Random walk of `step` rad inside 0.8x the limits. With hug > 0 the walk
+    starts near the obstacles (clearance in [2 margin, 4 margin]) and each step
+    keeps, of `hug` collision-free candidates, the one with the least
+    clearance, so the path runs close to the obstacles."""
     while True:
         v = rng.uniform(0.8 * robot.q_lo, 0.8 * robot.q_hi)
-        if orc.signed_distance(robot, env, v[None])[0] >= 2 * margin:
+        sd0 = orc.signed_distance(robot, env, v[None])[0]
+        if sd0 >= 2 * margin and (not hug or sd0 <= 4 * margin):
             break
     verts = [v]
     while len(verts) < n_seg + 1:
+        best, best_c, found = None, np.inf, 0
         for _ in range(tries):
             nxt = wl.random_walk_waypoints(rng, robot, verts[-1], step)
-            if segment_clearance(robot, env, verts[-1], nxt) >= margin:
-                verts.append(nxt)
+            c = segment_clearance(robot, env, verts[-1], nxt)
+            if c < margin:
+                continue
+            if not hug:
+                best = nxt
                 break
-        else:
+            found += 1
+            if c < best_c:
+                best, best_c = nxt, c
+            if found >= hug:
+                break
+        if best is None:
             return None
+        verts.append(best)
     return np.asarray(verts)
 
 
@@ -97,7 +113,7 @@ def dh7_scene(seed=11, n_obs=64, n_seg=10):
     rng = np.random.default_rng(seed + 1)
     path = None
     while path is None:
-        path = random_path(robot, env, rng, n_seg)
+        path = random_path(robot, env, rng, n_seg, hug=24)
     return {"robot": "dh7", "env_seed": seed, "n_obs": n_obs, "path": path.tolist()}
 
 
