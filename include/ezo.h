@@ -276,6 +276,19 @@ ezo_status ezo_profile_enable(int32_t on);
 ezo_status ezo_profile_reset(void);
 ezo_status ezo_profile_read(double* ms, int64_t* launches, int32_t n_kinds);
 
+/* ------------------------------------------------------------- autotuner --
+ * Launch shape of the collision kernels: the number of warp lanes that share
+ * one configuration (1, 2, 4 or 8). ezo_tune_lanes times the collision
+ * kernel on N uniform configurations of the robot's joint box (N rounded up
+ * to a power of two, at most 2^22) for each choice and returns the fastest;
+ * results are cached per (device, robot shape, padded obstacle count, size
+ * class) for the process. ezo_check_collision with lanes_per_config = 0 and
+ * ezo_batch_create use it unless ezo_set_autotune(0) switched it off, in
+ * which case a size rule is used. Tuning allocates a scratch batch with
+ * cudaMalloc. */
+ezo_status ezo_tune_lanes(const ezo_robot* robot, const ezo_env* env, int64_t N, int32_t* lanes, void* cuda_stream);
+ezo_status ezo_set_autotune(int32_t on);
+
 /* Algorithmic FP32 work of one exact configuration check (forward kinematics
  * plus 8 flops per obstacle pair and per self pair), as used for rooflines. */
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env);

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -200,6 +201,53 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
     const float s = (float)sphere_r[i] + (float)sphere_r[j];
     rr[p] = s * s;
   }
+  // self pairs as blocks [i0, i0+ni) x [k0, k0+nk) of sorted spheres when the
+  // list is exactly such a union (the usual link-pair lists are)
+  {
+    std::vector<std::vector<int>> partners(n_spheres);
+    std::vector<std::pair<int, int>> norm;
+    for (int p = 0; p < n_self_pairs; ++p) {
+      int i = inv[self_pairs[2 * p]], j = inv[self_pairs[2 * p + 1]];
+      if (i > j) std::swap(i, j);
+      norm.emplace_back(i, j);
+    }
+    std::sort(norm.begin(), norm.end());
+    norm.erase(std::unique(norm.begin(), norm.end()), norm.end());
+    for (auto& pr : norm) partners[pr.first].push_back(pr.second);
+    // runs of each sphere's partner list
+    std::vector<std::vector<std::pair<int, int>>> runs(n_spheres);
+    for (int i = 0; i < n_spheres; ++i) {
+      auto& P = partners[i];
+      for (size_t a = 0; a < P.size();) {
+        size_t b = a + 1;
+        while (b < P.size() && P[b] == P[b - 1] + 1) ++b;
+        runs[i].emplace_back(P[a], (int)(b - a));
+        a = b;
+      }
+    }
+    std::vector<int4> blocks;
+    bool ok = (int)norm.size() == n_self_pairs;  // duplicates or i==j pairs: keep the list
+    for (auto& pr : norm)
+      if (pr.first == pr.second) ok = false;
+    for (int i = 0; i < n_spheres && ok;) {
+      if (runs[i].empty()) {
+        ++i;
+        continue;
+      }
+      int e = i + 1;
+      while (e < n_spheres && runs[e] == runs[i]) ++e;
+      for (auto& rn : runs[i]) blocks.push_back(make_int4(i, e - i, rn.first, rn.second));
+      i = e;
+    }
+    if (ok && !blocks.empty() && (int)blocks.size() <= EZO_MAX_SBLK) {
+      h.n_sblk = (int)blocks.size();
+      for (size_t b = 0; b < blocks.size(); ++b) h.sblk[b] = blocks[b];
+    } else {
+      h.n_sblk = 0;
+    }
+    const double a2 = 2.0 * (chain + loc_max), b2 = 2.0 * r->r_max;
+    h.E_self = (float)(8.0 * kU32 * (a2 * a2 + b2 * b2));
+  }
   // algorithmic FP32 flops: per joint ~45 (rotation and origin update), per
   // sphere 18 (centre) + 7 (half squared norm), 8 per pair
   r->fk_flops = 45.0 * n + 25.0 * n_spheres;
@@ -275,6 +323,8 @@ void ezo_env_free(ezo_env* e) {
   delete e;
 }
 
+int ezo_internal_tuned_lanes(const ezo_robot* robot, const ezo_env* env, long long N, cudaStream_t s);
+
 static int auto_lanes(long long N) {
   if (N >= (1ll << 20)) return 1;
   if (N >= (1ll << 17)) return 2;
@@ -287,7 +337,7 @@ ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const
   if (!robot || !env) return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: null handle");
   if (N < 0 || ldq < N) return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: need 0 <= N <= ldq");
   if (N > 0 && (!q_dev || !flags_dev)) return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: null buffer");
-  if (lanes == 0) lanes = auto_lanes(N);
+  if (lanes == 0) lanes = ezo_internal_tuned_lanes(robot, env, N, (cudaStream_t)stream);
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
     return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: lanes_per_config must be 0, 1, 2, 4 or 8");
   cudaError_t e = launch_check_flat(robot->d_robot, robot->n, robot->nsp_pad, env->dev(), band_E(robot, env), q_dev, ldq, N,
@@ -735,10 +785,18 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   v.graph_cond = 0;
   // launch shapes: lanes per configuration from the work per round
   const int sms = sm_count();
-  long long tot_np = 0;
-  for (auto& s : b->st0) tot_np += s.n_p;
-  b->T_check = auto_lanes(b->total_s);
-  b->T_bisect = auto_lanes(tot_np);
+  long long tot_np = 0, tot_s1 = 0;
+  for (auto& s : b->st0) {
+    tot_np += s.n_p;
+    tot_s1 += std::max(s.n_p, host_test_size(1, prm->eps, prm->delta, prm->tau));
+  }
+  // lanes per configuration from the autotuner, at the first round's sample
+  // count (labels) and at a quarter of the candidate capacity (bisection)
+  int e_big = 0;
+  for (int e2 = 1; e2 < n_env; ++e2)
+    if (envs[e2]->n_obs > envs[e_big]->n_obs) e_big = e2;
+  b->T_check = ezo_internal_tuned_lanes(robot, envs[e_big], tot_s1, nullptr);
+  b->T_bisect = ezo_internal_tuned_lanes(robot, envs[e_big], std::max(1ll, tot_np / 4), nullptr);
   b->grid_sample = std::max(1, std::min(b->max_sample_tiles, sms * 16));
   b->grid_check = std::max(1, std::min(b->max_sample_tiles, sms * 16));
   b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles, sms * 16));

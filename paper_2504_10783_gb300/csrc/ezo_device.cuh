@@ -21,6 +21,7 @@
 #define EZO_MAX_SPHERES 256
 #define EZO_MAX_OBS 4096
 #define EZO_CH 8
+#define EZO_MAX_SBLK 16
 
 namespace ezo {
 
@@ -61,6 +62,12 @@ struct RobotDev {
   float4 sph[EZO_MAX_SPHERES];       // local x, y, z and radius (sorted by frame)
   const ushort2* self_pairs;         // [n_self] indices into the sorted spheres
   const float* self_rr;              // [n_self] (r_i + r_j)^2
+  // Self pairs as blocks of sorted spheres [i0, i0 + ni) x [k0, k0 + nk) when
+  // the pair list is such a union (n_sblk > 0, then n_self pairs are not
+  // used); swept like obstacles with band E_self.
+  int n_sblk;
+  float E_self;
+  int4 sblk[EZO_MAX_SBLK];
 };
 
 // The part of RobotDev a block keeps in shared memory.
@@ -68,6 +75,9 @@ struct RobotSmem {
   float ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
   int frame_first[EZO_MAX_DOF + 2];
   int n, n_spheres, n_spheres_pad, n_self;
+  int n_sblk;
+  float E_self;
+  int4 sblk[EZO_MAX_SBLK];
 };
 
 __device__ __forceinline__ void stage_robot(RobotSmem& rs, float4* sph_s, const RobotDev* __restrict__ rd) {
@@ -79,11 +89,14 @@ __device__ __forceinline__ void stage_robot(RobotSmem& rs, float4* sph_s, const 
     rs.toff[i] = rd->toff[i];
   }
   for (int i = threadIdx.x; i < EZO_MAX_DOF + 2; i += blockDim.x) rs.frame_first[i] = rd->frame_first[i];
+  for (int i = threadIdx.x; i < EZO_MAX_SBLK; i += blockDim.x) rs.sblk[i] = rd->sblk[i];
   if (threadIdx.x == 0) {
     rs.n = rd->n;
     rs.n_spheres = rd->n_spheres;
     rs.n_spheres_pad = rd->n_spheres_pad;
     rs.n_self = rd->n_self;
+    rs.n_sblk = rd->n_sblk;
+    rs.E_self = rd->E_self;
   }
   const int np = rd->n_spheres_pad;
   for (int i = threadIdx.x; i < np; i += blockDim.x) sph_s[i] = rd->sph[i];
@@ -103,6 +116,13 @@ __device__ __forceinline__ void stage_env(float4* obs_s, float* nhw_s, const Env
     obs_s[i] = e.obs[i];
     nhw_s[i] = e.nhw[i];
   }
+}
+
+// max of three floats in one instruction (PTX max.f32 with three inputs).
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
 }
 
 // -------------------------------------------------- FK + collision test --
@@ -164,7 +184,7 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
   for (int s = rs.n_spheres + lg; s < rs.n_spheres_pad; s += T) cen[s] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
   __syncwarp();
 
-  // ---- robot spheres vs obstacle spheres ----
+  // ---- robot spheres vs obstacle spheres: two obstacles per step ----
   bool hit = false;
   for (int s0 = 0; s0 < rs.n_spheres_pad; s0 += EZO_CH) {
     float4 cc[EZO_CH];
@@ -175,8 +195,25 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
       rr[k] = sph_s[s0 + k].w;
       m[k] = -3.0e38f;
     }
-#pragma unroll 4
-    for (int j = lg; j < n_obs_pad; j += T) {
+    int j = lg;
+#pragma unroll 2
+    for (; j + T < n_obs_pad; j += 2 * T) {
+      const float4 o1 = obs_s[j], o2 = obs_s[j + T];
+      const float w1 = nhw_s[j], w2 = nhw_s[j + T];
+#pragma unroll
+      for (int k = 0; k < EZO_CH; ++k) {
+        float t1 = fmaf(rr[k], o1.w, w1);
+        float t2 = fmaf(rr[k], o2.w, w2);
+        t1 = fmaf(cc[k].z, o1.z, t1);
+        t2 = fmaf(cc[k].z, o2.z, t2);
+        t1 = fmaf(cc[k].y, o1.y, t1);
+        t2 = fmaf(cc[k].y, o2.y, t2);
+        t1 = fmaf(cc[k].x, o1.x, t1);
+        t2 = fmaf(cc[k].x, o2.x, t2);
+        m[k] = fmax3f(m[k], t1, t2);
+      }
+    }
+    if (j < n_obs_pad) {
       const float4 o = obs_s[j];
       const float w = nhw_s[j];
 #pragma unroll
@@ -195,8 +232,8 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
         hit = true;
       } else if (diff >= -E) {
         // inside the rounding band of the fast form: decide with differences
-        for (int j = lg; j < n_obs; j += T) {
-          const float4 o = obs_s[j];
+        for (int jj = lg; jj < n_obs; jj += T) {
+          const float4 o = obs_s[jj];
           const float dx = cc[k].x - o.x, dy = cc[k].y - o.y, dz = cc[k].z - o.z;
           const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           const float sr = rr[k] + o.w;
@@ -205,13 +242,61 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
       }
     }
   }
-  // ---- listed self pairs (direct difference form) ----
-  for (int p = lg; p < rs.n_self; p += T) {
-    const ushort2 pr = self_pairs[p];
-    const float4 a = cen[pr.x], b = cen[pr.y];
-    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (d2 < self_rr[p]) hit = true;
+  // ---- self pairs ----
+  if (rs.n_sblk > 0) {
+    // blocks [i0, i0 + ni) x [k0, k0 + nk) of sorted spheres, same fast form
+    // with the partner's (c_k, r_k) as the obstacle and -hu_k as its offset
+    const float Es = rs.E_self;
+    for (int bk = 0; bk < rs.n_sblk; ++bk) {
+      const int4 B = rs.sblk[bk];
+      for (int s0 = B.x; s0 < B.x + B.y; s0 += EZO_CH) {
+        float4 cc[EZO_CH];
+        float rr[EZO_CH], m[EZO_CH];
+#pragma unroll
+        for (int k = 0; k < EZO_CH; ++k) {
+          const bool in = s0 + k < B.x + B.y;
+          cc[k] = in ? cen[s0 + k] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+          rr[k] = in ? sph_s[s0 + k].w : 0.f;
+          m[k] = -3.0e38f;
+        }
+        for (int q = B.z + lg; q < B.z + B.w; q += T) {
+          const float4 o = cen[q];
+          const float ro = sph_s[q].w;
+#pragma unroll
+          for (int k = 0; k < EZO_CH; ++k) {
+            float t = fmaf(rr[k], ro, -o.w);
+            t = fmaf(cc[k].z, o.z, t);
+            t = fmaf(cc[k].y, o.y, t);
+            t = fmaf(cc[k].x, o.x, t);
+            m[k] = fmaxf(m[k], t);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < EZO_CH; ++k) {
+          const float diff = m[k] - cc[k].w;
+          if (diff > Es) {
+            hit = true;
+          } else if (diff >= -Es) {
+            for (int q = B.z + lg; q < B.z + B.w; q += T) {
+              const float4 o = cen[q];
+              const float dx = cc[k].x - o.x, dy = cc[k].y - o.y, dz = cc[k].z - o.z;
+              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float sr = rr[k] + sph_s[q].w;
+              if (d2 < sr * sr) hit = true;
+            }
+          }
+        }
+      }
+    }
+  } else {
+    // explicit pair list (direct difference form)
+    for (int p = lg; p < rs.n_self; p += T) {
+      const ushort2 pr = self_pairs[p];
+      const float4 a = cen[pr.x], b = cen[pr.y];
+      const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (d2 < self_rr[p]) hit = true;
+    }
   }
   __syncwarp();
   if (T > 1) {

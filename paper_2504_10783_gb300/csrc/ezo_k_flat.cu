@@ -10,14 +10,13 @@ template <int NDOF>
 __global__ void __launch_bounds__(128) k_sample_flat(const double* __restrict__ A, const double* __restrict__ b,
                                                      int m, int lda, int n, SampleParams p,
                                                      float* __restrict__ out, long long ldo, long long N) {
-  extern __shared__ float smf[];
-  float* A32 = smf;
-  float* b32 = smf + m * NDOF;
-  stage_polytope<NDOF>(A32, b32, A, b, m, lda, n);
+  extern __shared__ float4 smf4[];
+  float* A32 = reinterpret_cast<float*>(smf4);
+  stage_polytope<NDOF>(A32, A, b, m, lda, n);
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     float x[NDOF];
-    hnr_walk<NDOF>(A32, b32, m, n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
+    hnr_walk<NDOF>(A32, m, n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
 #pragma unroll
     for (int j = 0; j < NDOF; ++j)
       if (j < n) out[(long long)j * ldo + i] = x[j];
@@ -135,7 +134,7 @@ cudaError_t launch_sample_flat(const double* A, const double* b, int m, int lda,
   const long long grid = (N + threads - 1) / threads;
   cudaError_t err = cudaSuccess;
   EZO_DISPATCH_NDOF(n, {
-    const size_t smem = (size_t)m * (ND + 1) * sizeof(float);
+    const size_t smem = (size_t)std::max(1, m) * hnr_row_stride<ND>() * sizeof(float);
     auto kern = k_sample_flat<ND>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;

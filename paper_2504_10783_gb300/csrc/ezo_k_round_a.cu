@@ -72,12 +72,11 @@ __global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
 
 template <int NDOF>
 __global__ void __launch_bounds__(128) k_round_sample(BatchView v) {
-  extern __shared__ float smf[];
+  extern __shared__ float4 smf4[];
   __shared__ SampleParams p;
   __shared__ int cur_seg;
   const int n_tiles = v.summary->n_sample_tiles;
-  float* A32 = smf;
-  float* b32 = smf + v.m_cap * NDOF;
+  float* A32 = reinterpret_cast<float*>(smf4);
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -85,8 +84,8 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v) {
     const SegState& st = v.st[tile.x];
     if (tile.x != cur_seg) {
       __syncthreads();
-      stage_polytope<NDOF>(A32, b32, v.A + (long long)tile.x * v.m_cap * v.n, v.b + (long long)tile.x * v.m_cap,
-                           st.m, v.n, v.n);
+      stage_polytope<NDOF>(A32, v.A + (long long)tile.x * v.m_cap * v.n, v.b + (long long)tile.x * v.m_cap, st.m,
+                           v.n, v.n);
       if (threadIdx.x < EZO_MAX_DOF) {
         const int j = threadIdx.x;
         const double a1 = j < v.n ? v.v1[tile.x * v.n + j] : 0.0;
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v) {
     const int i = tile.y + threadIdx.x;
     if (i < st.n_samples) {
       float x[NDOF];
-      hnr_walk<NDOF>(A32, b32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
+      hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
       float* S = v.S + (long long)v.n * st.sample_off;
 #pragma unroll
       for (int j = 0; j < NDOF; ++j)
@@ -241,7 +240,7 @@ cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s) {
 cudaError_t launch_round_sample(const BatchView& v, int grid, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   EZO_DISPATCH_NDOF(v.n, {
-    const size_t smem = (size_t)v.m_cap * (ND + 1) * sizeof(float);
+    const size_t smem = (size_t)v.m_cap * hnr_row_stride<ND>() * sizeof(float);
     auto kern = k_round_sample<ND>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;

@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
   const long long co = st.cand_off;
   extern __shared__ uint32_t alive[];  // nc bits
   __shared__ unsigned long long red_key[32];
+  __shared__ int red_sidx[32];
   __shared__ int red_idx[32];
   __shared__ int s_best;
   __shared__ double s_a[EZO_MAX_DOF];
@@ -163,59 +164,63 @@ __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
     }
     if (lane == 0) {
       red_key[wid] = best_key;
+      red_sidx[wid] = best_i;
       red_idx[wid] = best_c;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long bk = ~0ull;
-      int bi = 0x7fffffff, bc = -1;
-      for (int w = 0; w < nw; ++w) {
-        const int c = red_idx[w];
-        if (c < 0) continue;
-        const unsigned long long k2 = red_key[w];
-        const int i2 = cidx[c];
+    if (wid == 0) {
+      unsigned long long bk = lane < nw ? red_key[lane] : ~0ull;
+      int bi = lane < nw ? red_sidx[lane] : 0x7fffffff;
+      int bc = lane < nw ? red_idx[lane] : -1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        const int c2 = __shfl_xor_sync(0xffffffffu, bc, o);
         if (k2 < bk || (k2 == bk && i2 < bi)) {
           bk = k2;
           bi = i2;
-          bc = c;
+          bc = c2;
         }
       }
-      s_best = bc;
-      if (bc < 0) {
-        s_stop = 1;
-      } else if (dist[bc] <= v.t_col) {
-        s_stop = 2;  // segment likely in collision (Sec. IV-C)
-      } else if (st.m >= v.m_cap) {
-        s_stop = 3;
-      } else {
-        // a = grad dist_L(c*) = (c* - c_proj) / ||c* - c_proj||, b = a^T c* (Eq. 10)
-        double cst[EZO_MAX_DOF], ps[EZO_MAX_DOF];
-        for (int j = 0; j < EZO_MAX_DOF; ++j) cst[j] = j < n ? v.cstar[(long long)n * co + (long long)j * np + bc] : 0.0;
-        project_fp64<EZO_MAX_DOF>(cst, v1, v2, n, ps);
-        double nn = 0.0;
-        for (int j = 0; j < n; ++j) nn = fma(cst[j] - ps[j], cst[j] - ps[j], nn);
-        nn = sqrt(nn);
-        double bval = 0.0, av1 = 0.0, av2 = 0.0;
-        for (int j = 0; j < n; ++j) {
-          const double a = (cst[j] - ps[j]) / nn;
-          s_a[j] = a;
-          s_a32[j] = (float)a;
-          bval = fma(a, cst[j], bval);
-          av1 = fma(a, v1[j], av1);
-          av2 = fma(a, v2[j], av2);
+      if (lane == 0) {
+        s_best = bc;
+        if (bc < 0) {
+          s_stop = 1;
+        } else if (dist[bc] <= v.t_col) {
+          s_stop = 2;  // segment likely in collision (Sec. IV-C)
+        } else if (st.m >= v.m_cap) {
+          s_stop = 3;
+        } else {
+          // a = grad dist_L(c*) = (c* - c_proj) / ||c* - c_proj||, b = a^T c* (Eq. 10)
+          double cst[EZO_MAX_DOF], ps[EZO_MAX_DOF];
+          for (int j = 0; j < EZO_MAX_DOF; ++j) cst[j] = j < n ? v.cstar[(long long)n * co + (long long)j * np + bc] : 0.0;
+          project_fp64<EZO_MAX_DOF>(cst, v1, v2, n, ps);
+          double nn = 0.0;
+          for (int j = 0; j < n; ++j) nn = fma(cst[j] - ps[j], cst[j] - ps[j], nn);
+          nn = sqrt(nn);
+          double bval = 0.0, av1 = 0.0, av2 = 0.0;
+          for (int j = 0; j < n; ++j) {
+            const double a = (cst[j] - ps[j]) / nn;
+            s_a[j] = a;
+            s_a32[j] = (float)a;
+            bval = fma(a, cst[j], bval);
+            av1 = fma(a, v1[j], av1);
+            av2 = fma(a, v2[j], av2);
+          }
+          // step back (Eqs. 11-12): r = max(a^T v1, a^T v2) - b + Delta_max
+          const double r = fmax(av1, av2) - bval + v.step_back_max;
+          const double delta = r > 0.0 ? v.step_back_max - r : v.step_back_max;
+          const double beta = bval - delta;
+          s_beta = beta;
+          s_beta32 = (float)beta;
+          const int row = st.m;
+          for (int j = 0; j < n; ++j) A[(long long)row * n + j] = s_a[j];
+          bb[row] = beta;
+          st.m = row + 1;
+          v.placed_idx[g * v.n_f + f] = bc;
+          v.placed_delta[g * v.n_f + f] = delta;
         }
-        // step back (Eqs. 11-12): r = max(a^T v1, a^T v2) - b + Delta_max
-        const double r = fmax(av1, av2) - bval + v.step_back_max;
-        const double delta = r > 0.0 ? v.step_back_max - r : v.step_back_max;
-        const double beta = bval - delta;
-        s_beta = beta;
-        s_beta32 = (float)beta;
-        const int row = st.m;
-        for (int j = 0; j < n; ++j) A[(long long)row * n + j] = s_a[j];
-        bb[row] = beta;
-        st.m = row + 1;
-        v.placed_idx[g * v.n_f + f] = bc;
-        v.placed_delta[g * v.n_f + f] = delta;
       }
     }
     __syncthreads();

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -27,12 +28,20 @@ struct SampleParams {
 // start x = v1 + u (v2 - v1); step s uses draws 1 + s W .. 1 + s W + W - 1
 // whose 4W words are uniforms u_0..: Gaussian pair i from (u_2i, u_2i+1) by
 // Box-Muller, step length from u_{2 ceil(n/2)}.
+// Shared-memory record of one polytope row for the sampler: a_r (NDOF floats,
+// zero-padded) then b_r, rounded up to whole float4s.
 template <int NDOF>
-__device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, const float* __restrict__ b32, int m,
+__host__ __device__ constexpr int hnr_row_stride() {
+  return (NDOF + 4) & ~3;
+}
+
+template <int NDOF>
+__device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
                                          uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
                                          float (&x)[NDOF]) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
+  constexpr int RS = hnr_row_stride<NDOF>();
   const int npair = (n + 1) / 2;
   const int W = (2 * npair + 4) / 4;
   const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
@@ -75,16 +84,26 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, const fl
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
     for (int r = 0; r < m; ++r) {
-      const float* a = A32 + r * NDOF;
+      // row r of A and b[r] in one padded record: RS / 4 broadcast loads
+      const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
+      float av[RS];
+#pragma unroll
+      for (int qd = 0; qd < RS / 4; ++qd) {
+        const float4 v4 = row[qd];
+        av[4 * qd] = v4.x;
+        av[4 * qd + 1] = v4.y;
+        av[4 * qd + 2] = v4.z;
+        av[4 * qd + 3] = v4.w;
+      }
       float ax = 0.f, ad = 0.f;
 #pragma unroll
       for (int j = 0; j < NDOF; ++j) {
-        ax = fmaf(a[j], x[j], ax);
-        ad = fmaf(a[j], d[j], ad);
+        ax = fmaf(av[j], x[j], ax);
+        ad = fmaf(av[j], d[j], ad);
       }
-      const float sl = b32[r] - ax;
-      if (ad > 0.f) t_hi = fminf(t_hi, sl / ad);
-      else if (ad < 0.f) t_lo = fmaxf(t_lo, sl / ad);
+      const float sl = av[NDOF] - ax;
+      if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(sl, ad));
+      else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(sl, ad));
     }
     t_hi = fmaxf(t_hi, 0.f);
     t_lo = fminf(t_lo, 0.f);
@@ -97,13 +116,13 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, const fl
 }
 
 template <int NDOF>
-__device__ __forceinline__ void stage_polytope(float* A32, float* b32, const double* __restrict__ A,
+__device__ __forceinline__ void stage_polytope(float* A32, const double* __restrict__ A,
                                                const double* __restrict__ b, int m, int lda, int n) {
-  for (int i = threadIdx.x; i < m * NDOF; i += blockDim.x) {
-    const int r = i / NDOF, c = i - r * NDOF;
-    A32[i] = (c < n) ? (float)A[(long long)r * lda + c] : 0.f;
+  constexpr int RS = hnr_row_stride<NDOF>();
+  for (int i = threadIdx.x; i < m * RS; i += blockDim.x) {
+    const int r = i / RS, c = i - r * RS;
+    A32[i] = (c < n) ? (float)A[(long long)r * lda + c] : (c == NDOF ? (float)b[r] : 0.f);
   }
-  for (int r = threadIdx.x; r < m; r += blockDim.x) b32[r] = (float)b[r];
 }
 
 // ------------------------------------------------------- collision checks --

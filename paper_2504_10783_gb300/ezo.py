@@ -84,6 +84,8 @@ def _sig(lib):
     f.ezo_batch_write_samples.argtypes = [_P, _I32, C.POINTER(C.c_float), _I32]
     f.ezo_profile_enable.argtypes = [_I32]
     f.ezo_profile_read.argtypes = [_DP, C.POINTER(_I64), _I32]
+    f.ezo_tune_lanes.argtypes = [_P, _P, _I64, C.POINTER(_I32), _P]
+    f.ezo_set_autotune.argtypes = [_I32]
     f.ezo_check_flops.argtypes = [_P, _P]
     f.ezo_check_flops.restype = C.c_double
     return lib
@@ -382,6 +384,17 @@ def profile_read() -> dict:
     cnt = np.zeros(7, dtype=np.int64)
     _check(lib().ezo_profile_read(_dp(ms), cnt.ctypes.data_as(C.POINTER(_I64)), 7))
     return {STEP_NAMES[i]: (float(ms[i]), int(cnt[i])) for i in range(7)}
+
+
+def tune_lanes(robot: Robot, env: Env, N: int, stream=None) -> int:
+    """Autotuned lanes per configuration for a batch of N configurations."""
+    out = _I32()
+    _check(lib().ezo_tune_lanes(robot.h, env.h, N, C.byref(out), _stream(stream)))
+    return out.value
+
+
+def set_autotune(on: bool = True):
+    _check(lib().ezo_set_autotune(1 if on else 0))
 
 
 def check_flops(robot: Robot, env: Env) -> float:
