@@ -316,6 +316,23 @@ def main():
                     "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
                     "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}}
 
+    # ---- the plain method for comparison: one segment at a time in path order
+    #      (host launch loop, containment skip before each segment) ----
+    plain_ms = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.reset()
+        bt.run_path(sequential=True, mode=ezo.RUN_HOST_LOOP)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    kept_plain = sum(bt.segment(g).status != ezo.SEG_SKIPPED for g in range(K))
+    plain = {"ms_per_path": float(np.median(plain_ms)), "kept_segments": int(kept_plain),
+             "what": "sequential per-segment inflation (paper's order), host-driven launch loop"}
+
     # ---- the collision checker alone on the paper's batch size (2e6 configs) ----
     checker = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg)
 
@@ -352,7 +369,7 @@ def main():
                        "checks_per_step": checks_per_step, "sample_checks": samp, "bisection_checks": bisc,
                        "ms_per_10_segment_path": ms / args.steps,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "checker_2e6": checker, "e2e": e2e, "gpu_launches": launches + checker["launches"],
+            "roofline": roofline, "plain_sequential": plain, "checker_2e6": checker, "e2e": e2e, "gpu_launches": launches + checker["launches"],
             "clocks": clocks}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args.seconds)

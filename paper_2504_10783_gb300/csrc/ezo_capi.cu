@@ -424,6 +424,7 @@ struct ezo_batch {
   double *d_cstar = nullptr, *d_dist = nullptr;
   float *d_c32 = nullptr, *d_cn = nullptr;
   uint32_t* d_bits = nullptr;
+  double *d_ga = nullptr, *d_gb = nullptr;
   int* d_pidx = nullptr;
   double* d_pdelta = nullptr;
   int2 *d_stiles = nullptr, *d_btiles = nullptr;
@@ -436,7 +437,7 @@ struct ezo_batch {
   double *d_A0 = nullptr, *d_b0 = nullptr;  // initial polytopes
   std::vector<double> v1h, v2h;
   BatchView view{};
-  int T_check = 1, T_bisect = 4;
+  int T_check = 1, T_bisect = 4, split_below = 0;
   int grid_sample = 1, grid_check = 1, grid_bisect = 1;
   // graph mode
   cudaGraph_t graph = nullptr;
@@ -452,7 +453,7 @@ ezo_status batch_free_device(ezo_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   void* ptrs[] = {b->d_st,    b->d_v1,    b->d_v2,   b->d_A,    b->d_b,      b->d_S,      b->d_flags,
-                  b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx,
+                  b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx, b->d_ga, b->d_gb,
                   b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -482,7 +483,7 @@ ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
   }
   switch (step) {
     case 0: e = launch_round_begin(b->view, s); break;
-    case 1: e = launch_round_sample(b->view, b->grid_sample, s); break;
+    case 1: e = launch_round_sample(b->view, b->split_below, b->grid_sample, s); break;
     case 2: e = launch_round_check(b->view, b->T_check, b->grid_check, s); break;
     case 3: e = launch_round_certify(b->view, s); break;
     case 4: e = launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s); break;
@@ -698,6 +699,8 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   EZO_ALLOC(b->d_c32, b->total_c * n);
   EZO_ALLOC(b->d_cn, b->total_c);
   EZO_ALLOC(b->d_bits, b->total_c);
+  EZO_ALLOC(b->d_ga, b->total_c * n);
+  EZO_ALLOC(b->d_gb, b->total_c);
   EZO_ALLOC(b->d_pidx, B * prm->n_f);
   EZO_ALLOC(b->d_pdelta, B * prm->n_f);
   EZO_ALLOC(b->d_stiles, b->max_sample_tiles);
@@ -770,6 +773,8 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   v.c32 = b->d_c32;
   v.cnorm = b->d_cn;
   v.bits = b->d_bits;
+  v.ga = b->d_ga;
+  v.gb = b->d_gb;
   v.placed_idx = b->d_pidx;
   v.placed_delta = b->d_pdelta;
   v.sample_tiles = b->d_stiles;
@@ -796,10 +801,16 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   for (int e2 = 1; e2 < n_env; ++e2)
     if (envs[e2]->n_obs > envs[e_big]->n_obs) e_big = e2;
   b->T_check = ezo_internal_tuned_lanes(robot, envs[e_big], tot_s1, nullptr);
-  b->T_bisect = ezo_internal_tuned_lanes(robot, envs[e_big], std::max(1ll, tot_np / 4), nullptr);
-  b->grid_sample = std::max(1, std::min(b->max_sample_tiles, sms * 16));
-  b->grid_check = std::max(1, std::min(b->max_sample_tiles, sms * 16));
-  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles, sms * 16));
+  // Bisection runs N_b dependent checks per candidate on the few thousand
+  // candidates of a round, so it is latency bound: eight lanes per candidate
+  // unless a round can hold enough candidates to fill the GPU at fewer lanes.
+  b->T_bisect = tot_np >= (1ll << 20) ? ezo_internal_tuned_lanes(robot, envs[e_big], tot_np / 4, nullptr) : 8;
+  // walks share eight lanes in rounds with fewer walks than one warp per
+  // scheduler would hold at one lane per walk
+  b->split_below = (sms * 4 * 32) / kTile;
+  b->grid_sample = std::max(1, std::min(b->max_sample_tiles * 8, sms * 16));
+  b->grid_check = std::max(1, std::min(b->max_sample_tiles * b->T_check, sms * 16));
+  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * b->T_bisect, sms * 16));
   *out = b;
   g_err.clear();
   return EZO_OK;

@@ -79,6 +79,8 @@ struct BatchView {
   float* c32;        // [n*cand_off + d*n_p + c]
   float* cnorm;      // [cand_off + c]
   uint32_t* bits;    // [cand_off + c]
+  double* ga;        // plane normal grad dist_L(c*): [n*cand_off + d*n_p + c]
+  double* gb;        // plane offset a^T c*: [cand_off + c]
   int* placed_idx;   // [B][n_f]   candidate index of each plane of the last round
   double* placed_delta;  // [B][n_f]
   int2* sample_tiles;    // (segment, first sample)
@@ -106,7 +108,9 @@ cudaError_t launch_sample_flat(const double* A, const double* b, int m, int lda,
                                float* out, long long ldo, cudaStream_t s);
 
 cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s);
-cudaError_t launch_round_sample(const BatchView& v, int grid, cudaStream_t s);
+// Walks share eight lanes when the round has fewer than split_below_tiles
+// sample tiles (0: never).
+cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int grid, cudaStream_t s);
 cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s);
 cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s);
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s);

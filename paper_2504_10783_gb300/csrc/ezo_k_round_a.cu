@@ -70,17 +70,53 @@ __global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
   }
 }
 
+// Hit-and-run for every active segment. When the round has few walks (few
+// active segments) eight lanes share each walk, which cuts the latency of the
+// sequential N_ms steps; otherwise each lane runs one walk. The choice is made
+// on the device from the round's tile count, so it also works inside a graph.
+// A 128-thread block covers a tile of kTile walks in one or eight passes.
+template <int NDOF, int TSS>
+__device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& st, const float* A32,
+                                            const SampleParams& p, int2 tile, int pass) {
+  constexpr int WPB = 128 / TSS;
+  const int gi = threadIdx.x / TSS, lw = threadIdx.x % TSS;
+  float* S = v.S + (long long)v.n * st.sample_off;
+  const int i = tile.y + pass * WPB + gi;
+  float x[NDOF];
+  if (TSS == 1) {
+    if (i >= st.n_samples) return;
+    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
+  } else {
+    const int ic = i < st.n_samples ? i : tile.y;
+    hnr_walk_split<NDOF, TSS, 8>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)ic, p.round_k,
+                                 p.stream, lw, x);
+    if (i >= st.n_samples || lw != 0) return;
+  }
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j)
+    if (j < v.n) S[(long long)j * st.s_cap + i] = x[j];
+}
+
+// Hit-and-run for every active segment. When the round has few walks (few
+// active segments) eight lanes share each walk, which cuts the latency of the
+// sequential N_ms steps; otherwise each lane runs one walk. The choice is made
+// on the device from the round's tile count, so it also works inside a graph.
+// Work units are (tile, pass) pairs: a tile of kTile walks takes one pass of
+// 128 walks at one lane each, or eight passes of 16 walks at eight lanes each,
+// and the passes of a tile go to different blocks.
 template <int NDOF>
-__global__ void __launch_bounds__(128) k_round_sample(BatchView v) {
+__global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_below_tiles) {
   extern __shared__ float4 smf4[];
   __shared__ SampleParams p;
   __shared__ int cur_seg;
   const int n_tiles = v.summary->n_sample_tiles;
+  const bool split = n_tiles < split_below_tiles;
+  const int passes = split ? 8 : 1;
   float* A32 = reinterpret_cast<float*>(smf4);
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();
-  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int2 tile = v.sample_tiles[t];
+  for (int u = blockIdx.x; u < n_tiles * passes; u += gridDim.x) {
+    const int2 tile = v.sample_tiles[u / passes];
     const SegState& st = v.st[tile.x];
     if (tile.x != cur_seg) {
       __syncthreads();
@@ -103,15 +139,8 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v) {
       }
       __syncthreads();
     }
-    const int i = tile.y + threadIdx.x;
-    if (i < st.n_samples) {
-      float x[NDOF];
-      hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
-      float* S = v.S + (long long)v.n * st.sample_off;
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j)
-        if (j < v.n) S[(long long)j * st.s_cap + i] = x[j];
-    }
+    if (split) sample_pass<NDOF, 8>(v, st, A32, p, tile, u % passes);
+    else sample_pass<NDOF, 1>(v, st, A32, p, tile, 0);
   }
 }
 
@@ -133,8 +162,11 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
   const int gi = threadIdx.x / T, lg = threadIdx.x % T;
   float4* cen = cen_all + gi * (nsp + 1);
   const int n_tiles = v.summary->n_sample_tiles;
-  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int2 tile = v.sample_tiles[t];
+  constexpr int PASSES = kTile / (128 / T);
+  // work units are (tile, pass): the passes of a tile go to different blocks
+  for (int u = blockIdx.x; u < n_tiles * PASSES; u += gridDim.x) {
+    const int2 tile = v.sample_tiles[u / PASSES];
+    const int sub = (u % PASSES) * groups;
     const SegState& st = v.st[tile.x];
     const EnvDevFull& ef = v.envs[st.env];
     if (st.env != cur_env) {
@@ -145,7 +177,7 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
     }
     const float* S = v.S + (long long)v.n * st.sample_off;
     uint8_t* fl = v.flags + st.sample_off;
-    for (int sub = 0; sub < kTile; sub += groups) {
+    {
       const int i = tile.y + sub + gi;
       const bool valid = i < st.n_samples;
       const int ic = valid ? i : tile.y;
@@ -237,18 +269,17 @@ cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s) {
 }
 
 
-cudaError_t launch_round_sample(const BatchView& v, int grid, cudaStream_t s) {
+cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int grid, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   EZO_DISPATCH_NDOF(v.n, {
     const size_t smem = (size_t)v.m_cap * hnr_row_stride<ND>() * sizeof(float);
     auto kern = k_round_sample<ND>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, 128, smem, s>>>(v);
+    kern<<<grid, 128, smem, s>>>(v, split_below_tiles);
   });
   return cudaGetLastError();
 }
-
 
 cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s) {
   cudaError_t err = cudaSuccess;

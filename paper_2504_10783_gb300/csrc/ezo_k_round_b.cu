@@ -28,8 +28,11 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
   float4* cen = cen_all + gi * (nsp + 1);
   const int n = v.n;
   const int n_tiles = v.summary->n_bisect_tiles;
-  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int2 tile = v.bisect_tiles[t];
+  static_assert(kTile % (128 / T) == 0, "tile must be a whole number of passes");
+  // work units are (tile, pass): the T passes of a tile go to different blocks
+  for (int u = blockIdx.x; u < n_tiles * T; u += gridDim.x) {
+    const int2 tile = v.bisect_tiles[u / T];
+    const int sub = (u % T) * groups;
     const int g = tile.x;
     const SegState& st = v.st[g];
     const EnvDevFull& ef = v.envs[st.env];
@@ -43,7 +46,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
     const double* v2 = v.v2 + (long long)g * n;
     const float* S = v.S + (long long)n * st.sample_off;
     const int np = st.n_p;
-    for (int sub = 0; sub < kTile; sub += groups) {
+    {
       const int c = tile.y + sub + gi;
       const bool valid = c < st.n_cand;
       const int cc = valid ? c : tile.y;
@@ -89,9 +92,22 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
             cn2 = fmaf(f, f, cn2);
           }
         }
-        v.dist[co + c] = sqrt(d2);
+        const double dist = sqrt(d2);
+        v.dist[co + c] = dist;
         v.cnorm[co + c] = sqrtf(cn2);
         v.bits[co + c] = bits;
+        // tangent plane of Eq. (10) at c*: a = (c* - c_proj) / dist_L(c*), b = a^T c*
+        const double inv = dist > 0.0 ? 1.0 / dist : 0.0;
+        double bval = 0.0;
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) {
+          if (j < n) {
+            const double a = (cst[j] - ps[j]) * inv;
+            v.ga[(long long)n * co + (long long)j * np + c] = a;
+            bval = fma(a, cst[j], bval);
+          }
+        }
+        v.gb[co + c] = bval;
       }
     }
   }
@@ -192,19 +208,12 @@ __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
         } else if (st.m >= v.m_cap) {
           s_stop = 3;
         } else {
-          // a = grad dist_L(c*) = (c* - c_proj) / ||c* - c_proj||, b = a^T c* (Eq. 10)
-          double cst[EZO_MAX_DOF], ps[EZO_MAX_DOF];
-          for (int j = 0; j < EZO_MAX_DOF; ++j) cst[j] = j < n ? v.cstar[(long long)n * co + (long long)j * np + bc] : 0.0;
-          project_fp64<EZO_MAX_DOF>(cst, v1, v2, n, ps);
-          double nn = 0.0;
-          for (int j = 0; j < n; ++j) nn = fma(cst[j] - ps[j], cst[j] - ps[j], nn);
-          nn = sqrt(nn);
-          double bval = 0.0, av1 = 0.0, av2 = 0.0;
+          // a = grad dist_L(c*), b = a^T c* (Eq. 10), computed by the bisection kernel
+          double bval = v.gb[co + bc], av1 = 0.0, av2 = 0.0;
           for (int j = 0; j < n; ++j) {
-            const double a = (cst[j] - ps[j]) / nn;
+            const double a = v.ga[(long long)n * co + (long long)j * np + bc];
             s_a[j] = a;
             s_a32[j] = (float)a;
-            bval = fma(a, cst[j], bval);
             av1 = fma(a, v1[j], av1);
             av2 = fma(a, v2[j], av2);
           }

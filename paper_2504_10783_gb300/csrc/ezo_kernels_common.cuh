@@ -115,6 +115,158 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
   }
 }
 
+// The same walk as hnr_walk, shared by TS consecutive lanes of a warp (TS in
+// 2, 4, 8): lane lw draws Philox blocks lw, lw + TS, .. of each step and the
+// Box-Muller pairs they hold; the direction and the step uniform are
+// broadcast by shuffles; lane lw scans polytope rows lw, lw + TS, .. and the
+// chord bounds are combined with min/max shuffles. When the polytope has at
+// most TS * RPL rows, each lane keeps the slack b_r - a_r x of its rows in
+// registers and updates it by s_r -= t q_r instead of recomputing a_r x
+// (the slack then carries FP32 rounding of the updates, about 1e-7 per
+// step). All lanes of the warp must call this together.
+template <int NDOF, int TS, int RPL>
+__device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, int m, int n, const float* v1f,
+                                               const float* ef, int n_mix, uint32_t key0, uint32_t key1,
+                                               uint32_t walk, uint32_t rk, uint32_t stream, int lw,
+                                               float (&x)[NDOF]) {
+  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
+  constexpr int RS = hnr_row_stride<NDOF>();
+  constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
+  const int npair = (n + 1) / 2;
+  const int W = (2 * npair + 4) / 4;
+  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
+  const float u0 = u01_co(r0.x);
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
+  // slack b_r - a_r x of this lane's rows, kept in registers when they fit
+  const bool inc = m <= TS * RPL;
+  float slk[RPL];
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    const int r = lw + i * TS;
+    slk[i] = 0.f;
+    if (inc && r < m) {
+      const float* a = A32 + r * RS;
+      float ax = 0.f;
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j) ax = fmaf(a[j], x[j], ax);
+      slk[i] = a[NDOF] - ax;
+    }
+  }
+  for (int s = 0; s < n_mix; ++s) {
+    // this lane's blocks: Gaussians z[4b .. 4b+3] from words 4b .. 4b+3
+    float z[4 * BPL];
+    float ut_part = 0.f;
+#pragma unroll
+    for (int bl = 0; bl < BPL; ++bl) {
+      const int b = lw + bl * TS;
+      u32x4 r = u32x4{0u, 0u, 0u, 0u};
+      if (b < W) r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, key0, key1);
+      const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int pair = 2 * b + h;  // words 4b + 2h, 4b + 2h + 1
+        float za = 0.f, zb = 0.f;
+        if (pair < npair) {
+          const float rho = sqrtf(-2.f * logf(u01_oc(wv[2 * h])));
+          float sn, cs;
+          sincospif(2.f * u01_co(wv[2 * h + 1]), &sn, &cs);
+          za = rho * cs;
+          zb = rho * sn;
+        }
+        z[4 * bl + 2 * h] = za;
+        z[4 * bl + 2 * h + 1] = zb;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (4 * b + c == 2 * npair) ut_part = u01_co(wv[c]);
+    }
+    // gather the direction: component j lives in lane (j / 4) % TS, slot
+    // 4 * ((j / 4) / TS) + j % 4
+    float d[NDOF];
+    float nrm2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      const int b = j / 4;
+      const float v = __shfl_sync(0xffffffffu, z[4 * (b / TS) + (j & 3)], b % TS, TS);
+      d[j] = (j < n) ? v : 0.f;
+      nrm2 = fmaf(d[j], d[j], nrm2);
+    }
+    const int ub = (2 * npair) / 4;
+    const float ut = __shfl_sync(0xffffffffu, ut_part, ub % TS, TS);
+    const bool ok = nrm2 > 0.f;
+    const float inv = ok ? 1.f / sqrtf(nrm2) : 0.f;
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) d[j] *= inv;
+    float t_lo = -INFINITY, t_hi = INFINITY;
+    float qv[RPL];
+    if (inc) {
+      // rows lw + TS i: slack kept up to date in registers
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lw + i * TS;
+        qv[i] = 0.f;
+        if (r < m) {
+          const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
+          float av[RS];
+#pragma unroll
+          for (int qd = 0; qd < RS / 4; ++qd) {
+            const float4 v4 = row[qd];
+            av[4 * qd] = v4.x;
+            av[4 * qd + 1] = v4.y;
+            av[4 * qd + 2] = v4.z;
+            av[4 * qd + 3] = v4.w;
+          }
+          float ad = 0.f;
+#pragma unroll
+          for (int j = 0; j < NDOF; ++j) ad = fmaf(av[j], d[j], ad);
+          qv[i] = ad;
+          if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(slk[i], ad));
+          else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(slk[i], ad));
+        }
+      }
+    } else {
+      for (int r = lw; r < m; r += TS) {
+        const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
+        float av[RS];
+#pragma unroll
+        for (int qd = 0; qd < RS / 4; ++qd) {
+          const float4 v4 = row[qd];
+          av[4 * qd] = v4.x;
+          av[4 * qd + 1] = v4.y;
+          av[4 * qd + 2] = v4.z;
+          av[4 * qd + 3] = v4.w;
+        }
+        float ax = 0.f, ad = 0.f;
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) {
+          ax = fmaf(av[j], x[j], ax);
+          ad = fmaf(av[j], d[j], ad);
+        }
+        const float sl = av[NDOF] - ax;
+        if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(sl, ad));
+        else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(sl, ad));
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < TS; o <<= 1) {
+      t_hi = fminf(t_hi, __shfl_xor_sync(0xffffffffu, t_hi, o, TS));
+      t_lo = fmaxf(t_lo, __shfl_xor_sync(0xffffffffu, t_lo, o, TS));
+    }
+    t_hi = fmaxf(t_hi, 0.f);
+    t_lo = fminf(t_lo, 0.f);
+    if (ok && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
+      const float t = fmaf(ut, t_hi - t_lo, t_lo);
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j) x[j] = fmaf(t, d[j], x[j]);
+      if (inc) {
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) slk[i] = fmaf(-t, qv[i], slk[i]);
+      }
+    }
+  }
+}
+
 template <int NDOF>
 __device__ __forceinline__ void stage_polytope(float* A32, const double* __restrict__ A,
                                                const double* __restrict__ b, int m, int lda, int n) {

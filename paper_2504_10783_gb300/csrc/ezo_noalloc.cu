@@ -126,7 +126,7 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   const size_t pad = 256;
   const size_t need = sizeof(SegState) + 2 * n * sizeof(double) + m_cap * n * sizeof(double) +
                       m_cap * sizeof(double) + s_cap * n * sizeof(float) + s_cap + (size_t)np * sizeof(int) +
-                      (size_t)np * n * (sizeof(double) + sizeof(float)) + (size_t)np * (sizeof(double) + 8) +
+                      (size_t)np * n * (2 * sizeof(double) + sizeof(float)) + (size_t)np * (2 * sizeof(double) + 8) +
                       (size_t)prm->n_f * (sizeof(int) + sizeof(double)) + (st_tiles + bi_tiles) * sizeof(int2) +
                       sizeof(RoundSummary) + sizeof(EnvDevFull) + sizeof(int) + 24 * pad;
   if (need > (size_t)EZO_NOALLOC_SCRATCH_BYTES)
@@ -153,6 +153,8 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   float* d_c32 = c.take<float>((size_t)np * n);
   float* d_cn = c.take<float>(np);
   uint32_t* d_bits = c.take<uint32_t>(np);
+  double* d_ga = c.take<double>((size_t)np * n);
+  double* d_gb = c.take<double>(np);
   int* d_pidx = c.take<int>(prm->n_f);
   double* d_pdelta = c.take<double>(prm->n_f);
   int2* d_stiles = c.take<int2>(st_tiles);
@@ -224,6 +226,8 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   v.c32 = d_c32;
   v.cnorm = d_cn;
   v.bits = d_bits;
+  v.ga = d_ga;
+  v.gb = d_gb;
   v.placed_idx = d_pidx;
   v.placed_delta = d_pdelta;
   v.sample_tiles = d_stiles;
@@ -241,14 +245,15 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   int dev = 0, sms = 1;
   NA_CUDA(cudaGetDevice(&dev));
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid_s = (int)std::max<long long>(1, std::min<long long>(st_tiles, (long long)sms * 16));
-  const int grid_b = (int)std::max<long long>(1, std::min<long long>(bi_tiles, (long long)sms * 16));
-  const int T_check = lanes_for(s_cap), T_bis = lanes_for(np);
+  const int T_check = lanes_for(s_cap), T_bis = np >= (1 << 20) ? lanes_for((long long)np / 4) : 8;
+  const int grid_s = (int)std::max<long long>(1, std::min<long long>(st_tiles * 8, (long long)sms * 16));
+  const int grid_c = (int)std::max<long long>(1, std::min<long long>(st_tiles * T_check, (long long)sms * 16));
+  const int grid_b = (int)std::max<long long>(1, std::min<long long>(bi_tiles * T_bis, (long long)sms * 16));
   RoundSummary h{};
   for (int r = 0; r <= prm->n_it_max + 1; ++r) {
     NA_CUDA(launch_round_begin(v, s));
-    NA_CUDA(launch_round_sample(v, grid_s, s));
-    NA_CUDA(launch_round_check(v, T_check, grid_s, s));
+    NA_CUDA(launch_round_sample(v, (sms * 4 * 32) / kTile, grid_s, s));
+    NA_CUDA(launch_round_check(v, T_check, grid_c, s));
     NA_CUDA(launch_round_certify(v, s));
     NA_CUDA(launch_round_bisect(v, T_bis, grid_b, s));
     NA_CUDA(launch_round_place(v, s));

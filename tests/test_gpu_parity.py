@@ -205,6 +205,10 @@ def _replay_rounds(ezo, rd, env_np, v1, v2, prm_kw, max_rounds=6):
         assert st["n_samples"] == orc.batch_size(k, oprm.eps, oprm.delta, oprm.tau, oprm.n_p)
         S = bt.read(0, "samples")[:, : st["n_samples"]].T.astype(np.float64)
         assert np.all(S @ A.T <= b + 1e-5 * (1 + np.abs(b)))
+        # the round's walks (several lanes per walk here) follow the FP64 walks
+        ref = orc.hit_and_run(A, b, v1, v2, 600, oprm.n_mix, oprm.seed, 0, k)
+        err = np.abs(S[:600] - ref).max(axis=1)
+        assert np.quantile(err, 0.99) < 1e-3 and np.median(err) < 1e-4, np.quantile(err, [0.5, 0.99])
         lab = bt.read(0, "labels")[: st["n_samples"]].astype(bool)
         assert_labels_match(rd, env_np, S.astype(np.float32), lab)
         bt.step(3)
