@@ -276,6 +276,43 @@ ezo_status ezo_profile_enable(int32_t on);
 ezo_status ezo_profile_reset(void);
 ezo_status ezo_profile_read(double* ms, int64_t* launches, int32_t n_kinds);
 
+/* ------------------------------------------------------- learned surrogate --
+ * Not in the paper. A small MLP sd_hat(q) estimates the signed distance from
+ * the features [sin q, cos q] (zero-padded to 64) through three hidden layers
+ * of 256 SiLU units to one output. Hidden-layer products run on BF16 tensor
+ * cores with FP32 accumulation; weights have FP32 masters trained with Adam
+ * (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the mean squared error. It
+ * only orders and prefilters bisection candidates (ezo_batch_attach_surrogate);
+ * labels and certification stay exact.
+ * Parameters are one flat FP32 vector of ezo_surrogate_num_params() values:
+ * W1 [256 x 64] | b1 [256] | W2 [256 x 256] | b2 | W3 [256 x 256] | b3 |
+ * w4 [256] | b4 [1], matrices row-major (out x in).
+ * create: deterministic initialisation from seed (uniform in
+ * +-1/sqrt(fan_in)); device memory is allocated here.
+ * train: draws n_samples configurations uniformly in the robot's joint box
+ * (Philox, data_seed), labels them with the exact FP32 signed distance against
+ * env clamped to [label_lo, label_hi], and runs `epochs` passes of Adam over
+ * mini-batches of `batch` (a multiple of 64); epoch_loss (nullable, `epochs`
+ * floats) receives the last batch loss of each epoch. Synchronous.
+ * grad: one forward and backward pass on N (multiple of 64) configurations
+ * q_dev (n x N, stride ldq) with targets t_dev, no update; gradient of the
+ * mean squared error into grad (host, num_params floats) and the loss into
+ * *loss. Synchronous.
+ * predict: sd_hat for N configurations into out_dev (FP32). Stream-ordered. */
+typedef struct ezo_surrogate ezo_surrogate;
+int64_t ezo_surrogate_num_params(void);
+ezo_status ezo_surrogate_create(const ezo_robot* robot, uint64_t seed, ezo_surrogate** out);
+void ezo_surrogate_free(ezo_surrogate* sur);
+ezo_status ezo_surrogate_get_params(const ezo_surrogate* sur, float* params);
+ezo_status ezo_surrogate_set_params(ezo_surrogate* sur, const float* params);
+ezo_status ezo_surrogate_train(ezo_surrogate* sur, const ezo_env* env, int64_t n_samples, int32_t epochs,
+                               int32_t batch, float lr, uint64_t data_seed, float label_lo, float label_hi,
+                               float* epoch_loss, void* cuda_stream);
+ezo_status ezo_surrogate_grad(ezo_surrogate* sur, const float* q_dev, int64_t ldq, const float* t_dev, int32_t N,
+                              float* grad, float* loss, void* cuda_stream);
+ezo_status ezo_surrogate_predict(ezo_surrogate* sur, const float* q_dev, int64_t ldq, int64_t N, float* out_dev,
+                                 void* cuda_stream);
+
 /* ------------------------------------------------------------- autotuner --
  * Launch shape of the collision kernels: the number of warp lanes that share
  * one configuration (1, 2, 4 or 8). ezo_tune_lanes times the collision

@@ -1,0 +1,669 @@
+// Learned signed-distance surrogate: a small MLP sd_hat(q) from the features
+// [sin q_1 .. sin q_n, cos q_1 .. cos q_n] (zero-padded to F = 64) through
+// three hidden layers of width H = 256 with SiLU to one output. Not part of
+// the paper: it only orders and prefilters bisection candidates; every
+// certification sample is still checked exactly.
+//
+// Weights are kept in FP32 (master, Adam moments) and in BF16 copies that
+// feed the tensor cores: every hidden-layer product is a BF16 x BF16 -> FP32
+// GEMM on mma.sync m16n8k16 with ldmatrix fragment loads, bias/SiLU (forward)
+// and SiLU' (backward) fused into the epilogue. The output layer (H -> 1) and
+// the reductions are small CUDA-core kernels.
+//
+// GEMM convention ("NT"): C[M x N] = A[M x K] B[N x K]^T, both operands
+// K-contiguous (row-major with leading dimensions lda, ldb). Forward
+// activations are also written transposed so that the weight gradients are
+// NT products too.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ezo.h"
+#include "ezo_engine.cuh"
+
+namespace ezo {
+
+constexpr int kF = 64;   // padded input features
+constexpr int kH = 256;  // hidden width
+constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8;
+
+enum Epi : int {
+  EPI_F32 = 0,        // C (FP32) = acc
+  EPI_BIAS_SILU = 1,  // Z = acc + bias (FP32), H = SiLU(Z) (BF16, and transposed)
+  EPI_DSILU = 2,      // D = acc * SiLU'(Z) (BF16, and transposed)
+  EPI_BIAS_SILU_H = 3 // inference: H = SiLU(acc + bias) (BF16 only)
+};
+
+struct GemmArgs {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int M, N, K, lda, ldb;
+  const int* m_dev;  // optional device row count (rows >= *m_dev are skipped)
+  float* C;          // EPI_F32 output, ldc
+  int ldc;
+  const float* bias;
+  float* Z;          // EPI_BIAS_SILU: pre-activation out; EPI_DSILU: pre-activation in (ldz = N)
+  __nv_bfloat16* H;  // BF16 output, row-major (ldh = N)
+  __nv_bfloat16* Ht; // BF16 output, transposed [N x ldt]
+  int ldt;
+};
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float dsilu(float z) {
+  const float s = 1.f / (1.f + __expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* smem_row) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 64 x 64 block tile, 4 warps of 32 x 32 (2 m16 x 4 n8 mma tiles each), K in
+// steps of 32 staged through shared memory (rows padded by 8 BF16 so the
+// eight 16-byte rows of an ldmatrix hit distinct banks).
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_nt(GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 As[kBM][kBK + kPad];
+  __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kBK + kPad];
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int m_lim = g.m_dev ? min(g.M, *g.m_dev) : g.M;
+  if (m0 >= m_lim) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  for (int k0 = 0; k0 < g.K; k0 += kBK) {
+    // 64 rows x 32 BF16 = 64 x 4 chunks of 16 bytes per operand, 2 per thread
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int c = threadIdx.x + it * 128;
+      const int r = c >> 2, q = (c & 3) * 8;
+      const int gm = m0 + r, gn = n0 + r;
+      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+      if (gm < m_lim) va = *reinterpret_cast<const uint4*>(g.A + (long long)gm * g.lda + k0 + q);
+      if (gn < g.N) vb = *reinterpret_cast<const uint4*>(g.B + (long long)gn * g.ldb + k0 + q);
+      *reinterpret_cast<uint4*>(&As[r][q]) = va;
+      *reinterpret_cast<uint4*>(&Bs[r][q]) = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 16) {
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) ldmatrix_x4(af[i], &As[wm + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+      uint32_t bf[2][4];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        ldmatrix_x4(bf[j], &Bs[wn + j * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j >> 1][(j & 1) * 2], bf[j >> 1][(j & 1) * 2 + 1]);
+    }
+    __syncthreads();
+  }
+  // epilogue: fragment element e of tile (i, j) is row wm+16i+lane/4 (+8 for
+  // e >= 2), column wn+8j+2(lane%4) (+1 for odd e)
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = m0 + wm + i * 16 + (lane >> 2) + (e >= 2 ? 8 : 0);
+        const int c = n0 + wn + j * 8 + (lane & 3) * 2 + (e & 1);
+        if (r >= m_lim || c >= g.N) continue;
+        const float v = acc[i][j][e];
+        if (EPI == EPI_F32) {
+          g.C[(long long)r * g.ldc + c] = v;
+        } else if (EPI == EPI_BIAS_SILU || EPI == EPI_BIAS_SILU_H) {
+          const float z = v + g.bias[c];
+          const __nv_bfloat16 h = __float2bfloat16(silu(z));
+          g.H[(long long)r * g.N + c] = h;
+          if (EPI == EPI_BIAS_SILU) {
+            g.Z[(long long)r * g.N + c] = z;
+            g.Ht[(long long)c * g.ldt + r] = h;
+          }
+        } else {
+          const float d = v * dsilu(g.Z[(long long)r * g.N + c]);
+          const __nv_bfloat16 h = __float2bfloat16(d);
+          g.H[(long long)r * g.N + c] = h;
+          g.Ht[(long long)c * g.ldt + r] = h;
+        }
+      }
+}
+
+// ------------------------------------------------------------ small kernels --
+// features of configuration i: sin q_j, cos q_j (j < n), zero padding to kF;
+// row-major [rows x kF] and transposed [kF x ldt]
+__global__ void k_features(const float* __restrict__ q, long long ldq, int n, long long N,
+                           __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ Xt, int ldt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    for (int f = 0; f < kF; ++f) {
+      float v = 0.f;
+      if (f < n) v = sinf(q[(long long)f * ldq + i]);
+      else if (f < 2 * n) v = cosf(q[(long long)(f - n) * ldq + i]);
+      const __nv_bfloat16 h = __float2bfloat16(v);
+      X[i * kF + f] = h;
+      if (Xt) Xt[(long long)f * ldt + i] = h;
+    }
+  }
+}
+
+// y_i = H3_i . w4 + b4, one warp per row
+__global__ void k_out(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ w4, const float* __restrict__ b4,
+                      long long N, const int* m_dev, float* __restrict__ y) {
+  const long long lim = m_dev ? min((long long)*m_dev, N) : N;
+  const int lane = threadIdx.x & 31;
+  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < lim;
+       i += ((long long)gridDim.x * blockDim.x) >> 5) {
+    float s = 0.f;
+    for (int c = lane; c < kH; c += 32) s = fmaf(__bfloat162float(H3[i * kH + c]), w4[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = s + b4[0];
+  }
+}
+
+// loss 1/N sum (y - t)^2, dy = 2 (y - t) / N, dZ3 = dy w4 * SiLU'(Z3)
+// (row-major and transposed BF16); dw4 = sum_i dy_i H3_i and db4 = sum_i dy_i
+// reduced per block in shared memory, then one atomic per column per block.
+__global__ void __launch_bounds__(256) k_out_backward(const float* __restrict__ y, const float* __restrict__ t,
+                                                      const float* __restrict__ Z3, const __nv_bfloat16* __restrict__ H3,
+                                                      const float* __restrict__ w4, int N,
+                                                      __nv_bfloat16* __restrict__ dZ3, __nv_bfloat16* __restrict__ dZ3t,
+                                                      float* __restrict__ gw4, float* __restrict__ gb4,
+                                                      float* __restrict__ loss) {
+  __shared__ float sw[kH];
+  __shared__ float sb, sl;
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) sw[c] = 0.f;
+  if (threadIdx.x == 0) sb = sl = 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  float part[kH / 32];
+#pragma unroll
+  for (int k = 0; k < kH / 32; ++k) part[k] = 0.f;
+  float pb = 0.f, pl = 0.f;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N; i += (gridDim.x * blockDim.x) >> 5) {
+    const float e = y[i] - t[i];
+    const float dy = 2.f * e / (float)N;
+    pb += dy;
+    pl += e * e / (float)N;
+#pragma unroll
+    for (int k = 0; k < kH / 32; ++k) {
+      const int c = lane + 32 * k;
+      part[k] = fmaf(dy, __bfloat162float(H3[(long long)i * kH + c]), part[k]);
+      const float d = dy * w4[c] * dsilu(Z3[(long long)i * kH + c]);
+      const __nv_bfloat16 h = __float2bfloat16(d);
+      dZ3[(long long)i * kH + c] = h;
+      dZ3t[(long long)c * N + i] = h;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kH / 32; ++k) atomicAdd(&sw[lane + 32 * k], part[k]);
+  if (lane == 0) {
+    atomicAdd(&sb, pb);
+    atomicAdd(&sl, pl);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) atomicAdd(&gw4[c], sw[c]);
+  if (threadIdx.x == 0) {
+    atomicAdd(gb4, sb);
+    atomicAdd(loss, sl);
+  }
+}
+
+// column sums of a transposed [rows x N] BF16 matrix: out[r] = sum_i Mt[r][i]
+__global__ void k_rowsum(const __nv_bfloat16* __restrict__ Mt, int rows, int N, float* __restrict__ out) {
+  const int r = blockIdx.x;
+  if (r >= rows) return;
+  float s = 0.f;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s += __bfloat162float(Mt[(long long)r * N + i]);
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[r] = s;
+  }
+}
+
+// Adam on FP32 masters (Kingma and Ba, 2015, Algorithm 1) and the BF16
+// copies the GEMMs read: W [rows x cols] and its transpose.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long count, float lr, float b1, float b2, float eps, float c1, float c2,
+                       __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wt, int rows, int cols) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    if (W) {
+      const int r = (int)(i / cols), c = (int)(i % cols);
+      const __nv_bfloat16 h = __float2bfloat16(pi);
+      W[i] = h;
+      if (Wt) Wt[(long long)c * rows + r] = h;
+    }
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ p, long long count, __nv_bfloat16* __restrict__ W,
+                          __nv_bfloat16* __restrict__ Wt, int rows, int cols) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const __nv_bfloat16 h = __float2bfloat16(p[i]);
+    W[i] = h;
+    if (Wt) Wt[(long long)(i % cols) * rows + i / cols] = h;
+  }
+}
+
+__global__ void k_clamp_labels(float* __restrict__ t, long long N, float lo, float hi) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    t[i] = fminf(fmaxf(t[i], lo), hi);
+}
+
+// configuration i of a training set: uniform in the joint box from Philox
+// (counter (i, j, 0x5355, seed word), key (seed low, seed high))
+__global__ void k_uniform_q(float* __restrict__ q, long long N, int n, const float* __restrict__ lo,
+                            const float* __restrict__ hi, uint32_t k0, uint32_t k1) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    for (int j = 0; j < n; j += 4) {
+      const u32x4 r = philox4x32_10(u32x4{(uint32_t)i, (uint32_t)(i >> 32), (uint32_t)j, 0x5355u}, k0, k1);
+      const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+      for (int c = 0; c < 4 && j + c < n; ++c) q[(long long)(j + c) * N + i] = lo[j + c] + (hi[j + c] - lo[j + c]) * u01_co(w[c]);
+    }
+  }
+}
+
+
+}  // namespace ezo
+
+// ------------------------------------------------------------------ host side --
+namespace {
+
+using namespace ezo;
+
+// flat parameter layout: W1 [H x F] | b1 [H] | W2 [H x H] | b2 | W3 [H x H] | b3 | w4 [H] | b4 [1]
+constexpr long long kOffW1 = 0, kOffB1 = kOffW1 + (long long)kH * kF, kOffW2 = kOffB1 + kH,
+                    kOffB2 = kOffW2 + (long long)kH * kH, kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + (long long)kH * kH,
+                    kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + kH, kNumParams = kOffB4 + 1;
+
+template <typename T>
+cudaError_t dal(T** p, size_t n) {
+  return cudaMalloc((void**)p, std::max<size_t>(1, n) * sizeof(T));
+}
+
+}  // namespace
+
+extern "C" void ezo_internal_set_error(const char* msg);
+extern "C" const ezo::RobotDev* ezo_internal_robot_dev(const ezo_robot* r, int* n, int* nsp_pad, double* q_lo,
+                                                       double* q_hi);
+extern "C" int ezo_internal_env_dev(const ezo_robot* r, const ezo_env* e, ezo::EnvDevFull* out);
+
+struct ezo_surrogate {
+  int n = 0;
+  const ezo_robot* robot = nullptr;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // flat FP32
+  __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2t = nullptr, *W3t = nullptr;
+  long long step = 0;
+  // activations for a training batch of up to cap rows
+  int cap = 0;
+  __nv_bfloat16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H1t = nullptr, *H2 = nullptr, *H2t = nullptr,
+                *H3 = nullptr, *H3t = nullptr, *dZ3 = nullptr, *dZ3t = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
+                *dZ1 = nullptr, *dZ1t = nullptr;
+  float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *loss = nullptr;
+  // inference buffers (grown on demand)
+  long long icap = 0;
+  __nv_bfloat16 *iX = nullptr, *iA = nullptr, *iB = nullptr;
+};
+
+namespace {
+
+using namespace ezo;
+
+cudaError_t gemm(int epi, const GemmArgs& a, cudaStream_t s) {
+  dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM);
+  switch (epi) {
+    case EPI_F32: k_gemm_nt<EPI_F32><<<grid, 128, 0, s>>>(a); break;
+    case EPI_BIAS_SILU: k_gemm_nt<EPI_BIAS_SILU><<<grid, 128, 0, s>>>(a); break;
+    case EPI_DSILU: k_gemm_nt<EPI_DSILU><<<grid, 128, 0, s>>>(a); break;
+    default: k_gemm_nt<EPI_BIAS_SILU_H><<<grid, 128, 0, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+int blocks_for(long long n, int t) { return (int)std::max<long long>(1, std::min<long long>((n + t - 1) / t, 4096)); }
+
+cudaError_t sync_bf16(ezo_surrogate* S, cudaStream_t s) {
+  k_to_bf16<<<blocks_for((long long)kH * kF, 256), 256, 0, s>>>(S->p + kOffW1, (long long)kH * kF, S->W1, nullptr, kH, kF);
+  k_to_bf16<<<blocks_for((long long)kH * kH, 256), 256, 0, s>>>(S->p + kOffW2, (long long)kH * kH, S->W2, S->W2t, kH, kH);
+  k_to_bf16<<<blocks_for((long long)kH * kH, 256), 256, 0, s>>>(S->p + kOffW3, (long long)kH * kH, S->W3, S->W3t, kH, kH);
+  return cudaGetLastError();
+}
+
+cudaError_t ensure_train_cap(ezo_surrogate* S, int B) {
+  if (B <= S->cap) return cudaSuccess;
+  __nv_bfloat16** bufs[] = {&S->X, &S->Xt, &S->H1, &S->H1t, &S->H2, &S->H2t, &S->H3, &S->H3t,
+                            &S->dZ3, &S->dZ3t, &S->dZ2, &S->dZ2t, &S->dZ1, &S->dZ1t};
+  for (auto b : bufs) {
+    cudaFree(*b);
+    *b = nullptr;
+  }
+  cudaFree(S->Z1);
+  cudaFree(S->Z2);
+  cudaFree(S->Z3);
+  cudaFree(S->y);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 14 && e == cudaSuccess; ++i) e = dal(bufs[i], (size_t)B * (i < 2 ? kF : kH));
+  if (e == cudaSuccess) e = dal(&S->Z1, (size_t)B * kH);
+  if (e == cudaSuccess) e = dal(&S->Z2, (size_t)B * kH);
+  if (e == cudaSuccess) e = dal(&S->Z3, (size_t)B * kH);
+  if (e == cudaSuccess) e = dal(&S->y, (size_t)B);
+  if (e == cudaSuccess) S->cap = B;
+  return e;
+}
+
+// forward + backward of one batch (q: n x B, stride ldq; t: B targets);
+// gradients into S->g, loss into S->loss (both zeroed here)
+cudaError_t train_grad(ezo_surrogate* S, const float* q, long long ldq, const float* t, int B, cudaStream_t s) {
+  cudaError_t e = ensure_train_cap(S, B);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(S->g, 0, sizeof(float) * kNumParams, s);
+  cudaMemsetAsync(S->loss, 0, sizeof(float), s);
+  k_features<<<blocks_for(B, 256), 256, 0, s>>>(q, ldq, S->n, B, S->X, S->Xt, B);
+  GemmArgs a{};
+  a.M = B;
+  a.N = kH;
+  a.ldt = B;
+  // forward
+  a.A = S->X; a.lda = kF; a.B = S->W1; a.ldb = kF; a.K = kF; a.bias = S->p + kOffB1; a.Z = S->Z1; a.H = S->H1; a.Ht = S->H1t;
+  if ((e = gemm(EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
+  a.A = S->H1; a.lda = kH; a.B = S->W2; a.ldb = kH; a.K = kH; a.bias = S->p + kOffB2; a.Z = S->Z2; a.H = S->H2; a.Ht = S->H2t;
+  if ((e = gemm(EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
+  a.A = S->H2; a.B = S->W3; a.bias = S->p + kOffB3; a.Z = S->Z3; a.H = S->H3; a.Ht = S->H3t;
+  if ((e = gemm(EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
+  k_out<<<blocks_for((long long)B * 32, 256), 256, 0, s>>>(S->H3, S->p + kOffW4, S->p + kOffB4, B, nullptr, S->y);
+  // backward
+  k_out_backward<<<std::min(256, blocks_for((long long)B * 32, 256)), 256, 0, s>>>(
+      S->y, t, S->Z3, S->H3, S->p + kOffW4, B, S->dZ3, S->dZ3t, S->g + kOffW4, S->g + kOffB4, S->loss);
+  GemmArgs w{};
+  // dW3 = dZ3^T H2, db3 = column sums of dZ3
+  w.A = S->dZ3t; w.lda = B; w.B = S->H2t; w.ldb = B; w.M = kH; w.N = kH; w.K = B; w.C = S->g + kOffW3; w.ldc = kH;
+  if ((e = gemm(EPI_F32, w, s)) != cudaSuccess) return e;
+  k_rowsum<<<kH, 256, 0, s>>>(S->dZ3t, kH, B, S->g + kOffB3);
+  // dZ2 = (dZ3 W3) * SiLU'(Z2)
+  GemmArgs d{};
+  d.M = B; d.N = kH; d.K = kH; d.ldt = B;
+  d.A = S->dZ3; d.lda = kH; d.B = S->W3t; d.ldb = kH; d.Z = S->Z2; d.H = S->dZ2; d.Ht = S->dZ2t;
+  if ((e = gemm(EPI_DSILU, d, s)) != cudaSuccess) return e;
+  w.A = S->dZ2t; w.B = S->H1t; w.C = S->g + kOffW2;
+  if ((e = gemm(EPI_F32, w, s)) != cudaSuccess) return e;
+  k_rowsum<<<kH, 256, 0, s>>>(S->dZ2t, kH, B, S->g + kOffB2);
+  d.A = S->dZ2; d.B = S->W2t; d.Z = S->Z1; d.H = S->dZ1; d.Ht = S->dZ1t;
+  if ((e = gemm(EPI_DSILU, d, s)) != cudaSuccess) return e;
+  // dW1 = dZ1^T X
+  w.A = S->dZ1t; w.B = S->Xt; w.N = kF; w.C = S->g + kOffW1; w.ldc = kF;
+  if ((e = gemm(EPI_F32, w, s)) != cudaSuccess) return e;
+  k_rowsum<<<kH, 256, 0, s>>>(S->dZ1t, kH, B, S->g + kOffB1);
+  return cudaGetLastError();
+}
+
+cudaError_t adam_step(ezo_surrogate* S, float lr, cudaStream_t s) {
+  S->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.f - std::pow(b1, (float)S->step), c2 = 1.f - std::pow(b2, (float)S->step);
+  struct T {
+    long long off, count;
+    __nv_bfloat16 *W, *Wt;
+    int rows, cols;
+  } ts[] = {{kOffW1, (long long)kH * kF, S->W1, nullptr, kH, kF}, {kOffB1, kH, nullptr, nullptr, 0, 1},
+            {kOffW2, (long long)kH * kH, S->W2, S->W2t, kH, kH},   {kOffB2, kH, nullptr, nullptr, 0, 1},
+            {kOffW3, (long long)kH * kH, S->W3, S->W3t, kH, kH},   {kOffB3, kH, nullptr, nullptr, 0, 1},
+            {kOffW4, kH + 1, nullptr, nullptr, 0, 1}};
+  for (auto& t : ts)
+    k_adam<<<blocks_for(t.count, 256), 256, 0, s>>>(S->p + t.off, S->g + t.off, S->m + t.off, S->v + t.off, t.count, lr,
+                                                    b1, b2, eps, c1, c2, t.W, t.Wt, t.rows, t.cols);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t ezo_surrogate_num_params(void) { return kNumParams; }
+
+ezo_status ezo_surrogate_create(const ezo_robot* robot, uint64_t seed, ezo_surrogate** out) {
+  if (!robot || !out) {
+    ezo_internal_set_error("ezo_surrogate_create: null argument");
+    return EZO_ERR_INVALID_ARG;
+  }
+  int n = 0, nsp = 0;
+  double lo[EZO_MAX_DOF], hi[EZO_MAX_DOF];
+  ezo_internal_robot_dev(robot, &n, &nsp, lo, hi);
+  if (2 * n > kF) {
+    ezo_internal_set_error("ezo_surrogate_create: 2 n features must fit in 64");
+    return EZO_ERR_INVALID_ARG;
+  }
+  ezo_surrogate* S = new ezo_surrogate();
+  S->n = n;
+  S->robot = robot;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = dal(&S->p, kNumParams);
+  if (e == cudaSuccess) e = dal(&S->g, kNumParams);
+  if (e == cudaSuccess) e = dal(&S->m, kNumParams);
+  if (e == cudaSuccess) e = dal(&S->v, kNumParams);
+  if (e == cudaSuccess) e = dal(&S->W1, (size_t)kH * kF);
+  if (e == cudaSuccess) e = dal(&S->W2, (size_t)kH * kH);
+  if (e == cudaSuccess) e = dal(&S->W3, (size_t)kH * kH);
+  if (e == cudaSuccess) e = dal(&S->W2t, (size_t)kH * kH);
+  if (e == cudaSuccess) e = dal(&S->W3t, (size_t)kH * kH);
+  if (e == cudaSuccess) e = dal(&S->loss, 1);
+  if (e != cudaSuccess) {
+    ezo_surrogate_free(S);
+    ezo_internal_set_error((std::string("ezo_surrogate_create: ") + cudaGetErrorString(e)).c_str());
+    return EZO_ERR_CUDA;
+  }
+  // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases from a
+  // 64-bit LCG (Knuth's MMIX constants), so the start is reproducible
+  std::vector<float> h(kNumParams);
+  uint64_t st = seed * 6364136223846793005ull + 1442695040888963407ull;
+  auto uni = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (float)((st >> 40) * (1.0 / 16777216.0));
+  };
+  auto fill = [&](long long off, long long cnt, int fan_in) {
+    const float a = 1.f / std::sqrt((float)fan_in);
+    for (long long i = 0; i < cnt; ++i) h[off + i] = (2.f * uni() - 1.f) * a;
+  };
+  fill(kOffW1, (long long)kH * kF, 2 * n);
+  fill(kOffB1, kH, 2 * n);
+  for (long long i = 0; i < kH; ++i)
+    for (int c = 2 * n; c < kF; ++c) h[kOffW1 + i * kF + c] = 0.f;  // padding features carry no weight
+  fill(kOffW2, (long long)kH * kH, kH);
+  fill(kOffB2, kH, kH);
+  fill(kOffW3, (long long)kH * kH, kH);
+  fill(kOffB3, kH, kH);
+  fill(kOffW4, kH, kH);
+  h[kOffB4] = 0.f;
+  cudaMemcpy(S->p, h.data(), sizeof(float) * kNumParams, cudaMemcpyHostToDevice);
+  cudaMemset(S->m, 0, sizeof(float) * kNumParams);
+  cudaMemset(S->v, 0, sizeof(float) * kNumParams);
+  sync_bf16(S, nullptr);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    ezo_surrogate_free(S);
+    ezo_internal_set_error((std::string("ezo_surrogate_create: ") + cudaGetErrorString(e)).c_str());
+    return EZO_ERR_CUDA;
+  }
+  *out = S;
+  return EZO_OK;
+}
+
+void ezo_surrogate_free(ezo_surrogate* S) {
+  if (!S) return;
+  void* ps[] = {S->p,  S->g,   S->m,   S->v,   S->W1,  S->W2,  S->W3,   S->W2t,  S->W3t, S->X,   S->Xt,  S->H1,
+                S->H1t, S->H2, S->H2t, S->H3, S->H3t, S->dZ3, S->dZ3t, S->dZ2, S->dZ2t, S->dZ1, S->dZ1t, S->Z1, S->Z2,
+                S->Z3, S->y,   S->loss, S->iX,  S->iA,  S->iB};
+  for (void* q : ps)
+    if (q) cudaFree(q);
+  delete S;
+}
+
+ezo_status ezo_surrogate_get_params(const ezo_surrogate* S, float* out) {
+  if (!S || !out) return EZO_ERR_INVALID_ARG;
+  if (cudaMemcpy(out, S->p, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost) != cudaSuccess) return EZO_ERR_CUDA;
+  return EZO_OK;
+}
+
+ezo_status ezo_surrogate_set_params(ezo_surrogate* S, const float* in) {
+  if (!S || !in) return EZO_ERR_INVALID_ARG;
+  if (cudaMemcpy(S->p, in, sizeof(float) * kNumParams, cudaMemcpyHostToDevice) != cudaSuccess) return EZO_ERR_CUDA;
+  sync_bf16(S, nullptr);
+  return cudaDeviceSynchronize() == cudaSuccess ? EZO_OK : EZO_ERR_CUDA;
+}
+
+ezo_status ezo_surrogate_grad(ezo_surrogate* S, const float* q_dev, int64_t ldq, const float* t_dev, int32_t N,
+                              float* grad, float* loss, void* stream) {
+  if (!S || !q_dev || !t_dev || N < 64 || N % 64 || ldq < N) {
+    ezo_internal_set_error("ezo_surrogate_grad: need N a positive multiple of 64 and ldq >= N");
+    return EZO_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = train_grad(S, q_dev, ldq, t_dev, N, s);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, S->g, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, S->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    ezo_internal_set_error((std::string("ezo_surrogate_grad: ") + cudaGetErrorString(e)).c_str());
+    return EZO_ERR_CUDA;
+  }
+  return EZO_OK;
+}
+
+ezo_status ezo_surrogate_predict(ezo_surrogate* S, const float* q_dev, int64_t ldq, int64_t N, float* out_dev,
+                                 void* stream) {
+  if (!S || (N > 0 && (!q_dev || !out_dev)) || N < 0 || ldq < N) {
+    ezo_internal_set_error("ezo_surrogate_predict: bad argument");
+    return EZO_ERR_INVALID_ARG;
+  }
+  if (N == 0) return EZO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long Np = (N + kBM - 1) / kBM * kBM;
+  if (Np > S->icap) {
+    cudaFree(S->iX);
+    cudaFree(S->iA);
+    cudaFree(S->iB);
+    S->iX = S->iA = S->iB = nullptr;
+    if (dal(&S->iX, (size_t)Np * kF) != cudaSuccess || dal(&S->iA, (size_t)Np * kH) != cudaSuccess ||
+        dal(&S->iB, (size_t)Np * kH) != cudaSuccess) {
+      ezo_internal_set_error("ezo_surrogate_predict: allocation");
+      S->icap = 0;
+      return EZO_ERR_CUDA;
+    }
+    S->icap = Np;
+  }
+  k_features<<<blocks_for(N, 256), 256, 0, s>>>(q_dev, ldq, S->n, N, S->iX, nullptr, 0);
+  GemmArgs a{};
+  a.M = (int)N;
+  a.N = kH;
+  a.A = S->iX; a.lda = kF; a.B = S->W1; a.ldb = kF; a.K = kF; a.bias = S->p + kOffB1; a.H = S->iA;
+  gemm(EPI_BIAS_SILU_H, a, s);
+  a.A = S->iA; a.lda = kH; a.B = S->W2; a.ldb = kH; a.K = kH; a.bias = S->p + kOffB2; a.H = S->iB;
+  gemm(EPI_BIAS_SILU_H, a, s);
+  a.A = S->iB; a.B = S->W3; a.bias = S->p + kOffB3; a.H = S->iA;
+  gemm(EPI_BIAS_SILU_H, a, s);
+  k_out<<<blocks_for(N * 32, 256), 256, 0, s>>>(S->iA, S->p + kOffW4, S->p + kOffB4, N, nullptr, out_dev);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ezo_internal_set_error((std::string("ezo_surrogate_predict: ") + cudaGetErrorString(e)).c_str());
+    return EZO_ERR_CUDA;
+  }
+  return EZO_OK;
+}
+
+ezo_status ezo_surrogate_train(ezo_surrogate* S, const ezo_env* env, int64_t n_samples, int32_t epochs, int32_t batch,
+                               float lr, uint64_t data_seed, float label_lo, float label_hi, float* epoch_loss,
+                               void* stream) {
+  if (!S || !env || n_samples < batch || batch < 64 || batch % 64 || epochs < 1 || !(lr > 0.f)) {
+    ezo_internal_set_error("ezo_surrogate_train: need batch a multiple of 64, n_samples >= batch, epochs >= 1");
+    return EZO_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int n = 0, nsp = 0;
+  double lo[EZO_MAX_DOF], hi[EZO_MAX_DOF];
+  const RobotDev* rd = ezo_internal_robot_dev(S->robot, &n, &nsp, lo, hi);
+  EnvDevFull ef{};
+  ezo_internal_env_dev(S->robot, env, &ef);
+  const long long N = n_samples / batch * batch;
+  float *q = nullptr, *t = nullptr, *bnd = nullptr;
+  cudaError_t e = dal(&q, (size_t)n * N);
+  if (e == cudaSuccess) e = dal(&t, (size_t)N);
+  if (e == cudaSuccess) e = dal(&bnd, 2 * EZO_MAX_DOF);
+  if (e == cudaSuccess) {
+    float hb[2 * EZO_MAX_DOF];
+    for (int j = 0; j < n; ++j) {
+      hb[j] = (float)lo[j];
+      hb[EZO_MAX_DOF + j] = (float)hi[j];
+    }
+    cudaMemcpyAsync(bnd, hb, sizeof(hb), cudaMemcpyHostToDevice, s);
+    // training set: uniform configurations labelled by the exact FP32
+    // signed distance, clamped to [label_lo, label_hi]
+    k_uniform_q<<<blocks_for(N, 256), 256, 0, s>>>(q, N, n, bnd, bnd + EZO_MAX_DOF, (uint32_t)data_seed,
+                                                     (uint32_t)(data_seed >> 32));
+    e = launch_sd_flat(rd, n, nsp, ef.e, q, N, N, t, s);
+    k_clamp_labels<<<blocks_for(N, 256), 256, 0, s>>>(t, N, label_lo, label_hi);
+  }
+  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    float sum = 0.f;
+    const long long steps = N / batch;
+    for (long long st = 0; st < steps && e == cudaSuccess; ++st) {
+      e = train_grad(S, q + st * batch, N, t + st * batch, batch, s);
+      if (e == cudaSuccess) e = adam_step(S, lr, s);
+      if (epoch_loss && e == cudaSuccess && (st % 64 == 63 || st == steps - 1)) {
+        float l = 0.f;
+        cudaMemcpyAsync(&l, S->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        sum = l;  // loss of the latest batch
+      }
+    }
+    if (epoch_loss) epoch_loss[ep] = sum;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(q);
+  cudaFree(t);
+  cudaFree(bnd);
+  if (e != cudaSuccess) {
+    ezo_internal_set_error((std::string("ezo_surrogate_train: ") + cudaGetErrorString(e)).c_str());
+    return EZO_ERR_CUDA;
+  }
+  return EZO_OK;
+}
+
+}  // extern "C"

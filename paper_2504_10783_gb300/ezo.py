@@ -84,6 +84,15 @@ def _sig(lib):
     f.ezo_batch_write_samples.argtypes = [_P, _I32, C.POINTER(C.c_float), _I32]
     f.ezo_profile_enable.argtypes = [_I32]
     f.ezo_profile_read.argtypes = [_DP, C.POINTER(_I64), _I32]
+    f.ezo_surrogate_num_params.restype = _I64
+    f.ezo_surrogate_create.argtypes = [_P, C.c_uint64, C.POINTER(_P)]
+    f.ezo_surrogate_free.argtypes = [_P]
+    f.ezo_surrogate_get_params.argtypes = [_P, C.POINTER(C.c_float)]
+    f.ezo_surrogate_set_params.argtypes = [_P, C.POINTER(C.c_float)]
+    f.ezo_surrogate_train.argtypes = [_P, _P, _I64, _I32, _I32, C.c_float, C.c_uint64, C.c_float, C.c_float,
+                                      C.POINTER(C.c_float), _P]
+    f.ezo_surrogate_grad.argtypes = [_P, _P, _I64, _P, _I32, C.POINTER(C.c_float), C.POINTER(C.c_float), _P]
+    f.ezo_surrogate_predict.argtypes = [_P, _P, _I64, _I64, _P, _P]
     f.ezo_tune_lanes.argtypes = [_P, _P, _I64, C.POINTER(_I32), _P]
     f.ezo_set_autotune.argtypes = [_I32]
     f.ezo_check_flops.argtypes = [_P, _P]
@@ -424,3 +433,48 @@ def inflate_path(robot: Robot, env: Env, verts, params: Params, sequential: bool
         if r.status not in (SEG_SKIPPED, SEG_IDLE):
             out.append((k, r))
     return out
+
+
+class Surrogate:
+    """ezo_surrogate: the BF16 MLP signed-distance estimate (not in the paper)."""
+
+    def __init__(self, robot: Robot, seed: int = 1):
+        h = _P()
+        _check(lib().ezo_surrogate_create(robot.h, seed, C.byref(h)))
+        self.h = h
+        self.robot = robot
+        self.n_params = int(lib().ezo_surrogate_num_params())
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ezo_surrogate_free(self.h)
+            self.h = None
+
+    def params(self) -> np.ndarray:
+        o = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().ezo_surrogate_get_params(self.h, o.ctypes.data_as(C.POINTER(C.c_float))))
+        return o
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().ezo_surrogate_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def train(self, env: Env, n_samples: int, epochs: int, batch: int = 4096, lr: float = 1e-3, data_seed: int = 7,
+              label_lo: float = -0.1, label_hi: float = 0.3, stream=None) -> np.ndarray:
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(lib().ezo_surrogate_train(self.h, env.h, n_samples, epochs, batch, lr, data_seed, label_lo, label_hi,
+                                         losses.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
+        return losses
+
+    def grad(self, q_dev, t_dev, stream=None):
+        n, N = q_dev.shape
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_float()
+        _check(lib().ezo_surrogate_grad(self.h, C.c_void_p(q_dev.data_ptr()), _ld(q_dev), C.c_void_p(t_dev.data_ptr()),
+                                        N, g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss), _stream(stream)))
+        return float(loss.value), g
+
+    def predict(self, q_dev, out_dev, stream=None):
+        n, N = q_dev.shape
+        _check(lib().ezo_surrogate_predict(self.h, C.c_void_p(q_dev.data_ptr()), _ld(q_dev), N,
+                                           C.c_void_p(out_dev.data_ptr()), _stream(stream)))
