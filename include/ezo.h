@@ -225,7 +225,7 @@ ezo_status ezo_batch_sync(ezo_batch* batch, void* cuda_stream);
  * k, status, m, |S|, M, count, n_cand, planes, rounds, n_placed, N_p, env),
  * 7 placed candidate indices of the last round (int32 n_f), 8 step backs of
  * the last round (FP64 n_f), 9 exact checks split as int64[2] {at samples,
- * at bisection midpoints}, 10 the batch's round summary (int32[4]: active
+ * at bisection midpoints}, 11 surrogate evaluations (int64), 10 the batch's round summary (int32[4]: active
  * segments, rounds run since the last reset, sample tiles, bisection tiles;
  * `seg` is ignored). `bytes` is the size of `dst`. */
 ezo_status ezo_batch_read(const ezo_batch* batch, int32_t seg, int32_t what, void* dst, int64_t bytes);
@@ -312,6 +312,16 @@ ezo_status ezo_surrogate_grad(ezo_surrogate* sur, const float* q_dev, int64_t ld
                               float* grad, float* loss, void* cuda_stream);
 ezo_status ezo_surrogate_predict(ezo_surrogate* sur, const float* q_dev, int64_t ldq, int64_t N, float* out_dev,
                                  void* cuda_stream);
+
+/* Surrogate-guided bisection for a batch (not in the paper): in each round
+ * the N_b bisection steps of every candidate are taken on sd_hat (predicted
+ * collision iff sd_hat < margin, one MLP batch per step); each end point is
+ * then checked exactly and kept when it collides, otherwise that candidate
+ * gets the exact bisection of Sec. IV-B. Labels, the unadaptive test and the
+ * planes use exact checks only. sur = NULL detaches. The robot must have at
+ * most 8 joints. Allocates the batch's surrogate buffers on first use.
+ * ezo_batch_read code 11 returns the surrogate evaluations (int64). */
+ezo_status ezo_batch_attach_surrogate(ezo_batch* batch, ezo_surrogate* sur, float margin);
 
 /* ------------------------------------------------------------- autotuner --
  * Launch shape of the collision kernels: the number of warp lanes that share

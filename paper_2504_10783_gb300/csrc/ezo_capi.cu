@@ -444,6 +444,11 @@ struct ezo_batch {
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap_stream = nullptr;
   EventPool events;
+  // surrogate-guided bisection
+  ezo_surrogate* sur = nullptr;
+  long long sur_rows = 0;
+  void *s_X = nullptr, *s_hA = nullptr, *s_hB = nullptr;
+  float* s_y = nullptr;
 };
 
 namespace {
@@ -454,7 +459,9 @@ ezo_status batch_free_device(ezo_batch* b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   void* ptrs[] = {b->d_st,    b->d_v1,    b->d_v2,   b->d_A,    b->d_b,      b->d_S,      b->d_flags,
                   b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx, b->d_ga, b->d_gb,
-                  b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0};
+                  b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0,
+                  b->s_X, b->s_hA, b->s_hB, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
+                  b->view.s_bits, b->view.s_ok, b->view.s_rows};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_sum) cudaFreeHost(b->h_sum);
@@ -472,6 +479,42 @@ int host_test_size(int k, double eps, double delta, double tau) {
   return (int)std::ceil(2.0 * std::log(1.0 / dk) / (eps * tau * tau));
 }
 
+}  // namespace
+
+extern "C" cudaError_t ezo_internal_mlp_forward(ezo_surrogate* S, const void* X, long long rows_cap, const int* m_dev,
+                                                void* hA, void* hB, float* yhat, cudaStream_t s);
+extern "C" int ezo_internal_surrogate_dof(const ezo_surrogate* S);
+
+namespace {
+
+// Step 4 with a surrogate: N_b surrogate bisection steps for every candidate
+// (one MLP batch per step), one exact check of each end point, exact
+// bisection for the candidates whose end point is free.
+cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
+  if (!b->sur) {
+    b->view.bis_mode = 0;
+    return launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
+  }
+  const int g = (int)std::max<long long>(1, std::min<long long>((b->sur_rows + 255) / 256, 4096));
+  cudaError_t e = launch_sbis_init(b->view, g, s);
+  for (int st = 0; st < b->prm.n_b && e == cudaSuccess; ++st) {
+    e = launch_sbis_mid(b->view, b->s_X, g, s);
+    if (e == cudaSuccess)
+      e = ezo_internal_mlp_forward(b->sur, b->s_X, b->sur_rows, b->view.s_rows, b->s_hA, b->s_hB, b->s_y, s);
+    if (e == cudaSuccess) e = launch_sbis_update(b->view, b->s_y, st, g, s);
+  }
+  if (e == cudaSuccess) {
+    b->view.bis_mode = 1;
+    e = launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
+  }
+  if (e == cudaSuccess) {
+    b->view.bis_mode = 2;
+    e = launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
+  }
+  b->view.bis_mode = 0;
+  return e;
+}
+
 ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -486,7 +529,7 @@ ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
     case 1: e = launch_round_sample(b->view, b->split_below, b->grid_sample, s); break;
     case 2: e = launch_round_check(b->view, b->T_check, b->grid_check, s); break;
     case 3: e = launch_round_certify(b->view, s); break;
-    case 4: e = launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s); break;
+    case 4: e = launch_bisect_step(b, s); break;
     case 5: e = launch_round_place(b->view, s); break;
     case 6: e = launch_round_end(b->view, s); break;
     default: return fail(EZO_ERR_INVALID_ARG, "ezo_batch_step: step must be in [0, 6]");
@@ -822,6 +865,49 @@ void ezo_batch_free(ezo_batch* b) {
   delete b;
 }
 
+ezo_status ezo_batch_attach_surrogate(ezo_batch* b, ezo_surrogate* sur, float margin) {
+  if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_attach_surrogate: null batch");
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+  }
+  if (!sur) {
+    b->sur = nullptr;
+    b->view.sbis = 0;
+    return EZO_OK;
+  }
+  if (ezo_internal_surrogate_dof(sur) != b->n || b->n > 8)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_attach_surrogate: surrogate of another robot, or more than 8 joints");
+  const long long rows = (long long)b->max_bisect_tiles * kTile;
+  if (rows > b->sur_rows) {
+    void* ps[] = {b->s_X, b->s_hA, b->s_hB, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
+                  b->view.s_bits, b->view.s_ok, b->view.s_rows};
+    for (void* p : ps)
+      if (p) cudaFree(p);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&b->s_X, (size_t)rows * 64 * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b->s_hA, (size_t)rows * 256 * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b->s_hB, (size_t)rows * 256 * 2);
+    if (e == cudaSuccess) e = dalloc(&b->s_y, rows);
+    if (e == cudaSuccess) e = dalloc(&b->view.s_p32, rows * 8);
+    if (e == cudaSuccess) e = dalloc(&b->view.s_d32, rows * 8);
+    if (e == cudaSuccess) e = dalloc(&b->view.s_lo, rows);
+    if (e == cudaSuccess) e = dalloc(&b->view.s_hi, rows);
+    if (e == cudaSuccess) e = dalloc(&b->view.s_bits, rows);
+    if (e == cudaSuccess) e = dalloc(&b->view.s_ok, rows);
+    if (e == cudaSuccess) e = dalloc(&b->view.s_rows, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "ezo_batch_attach_surrogate: allocation");
+    b->sur_rows = rows;
+  }
+  b->sur = sur;
+  b->view.sbis = 1;
+  b->view.sbis_margin = margin;
+  g_err.clear();
+  return EZO_OK;
+}
+
 ezo_status ezo_batch_reset(ezo_batch* b, const double* v1, const double* v2, void* stream_v) {
   if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_reset: null batch");
   cudaStream_t s = (cudaStream_t)stream_v;
@@ -983,6 +1069,12 @@ ezo_status ezo_batch_read(const ezo_batch* b, int32_t seg, int32_t what, void* d
       if (bytes < (int64_t)(2 * sizeof(int64_t))) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
       const int64_t vals[2] = {s.checks - s.checks_bisect, s.checks_bisect};
       std::memcpy(dst, vals, sizeof(vals));
+      return EZO_OK;
+    }
+    case 11: {
+      if (bytes < (int64_t)sizeof(int64_t)) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
+      const int64_t val = s.sur_evals;
+      std::memcpy(dst, &val, sizeof(val));
       return EZO_OK;
     }
     case 10: {

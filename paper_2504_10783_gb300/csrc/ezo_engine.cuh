@@ -43,6 +43,7 @@ struct SegState {
   int s_cap;             // sample capacity
   int pad1;
   long long checks_bisect;  // of which at bisection midpoints
+  long long sur_evals;      // surrogate evaluations (surrogate-guided bisection)
 };
 
 struct EnvDevFull {
@@ -96,6 +97,18 @@ struct BatchView {
   int max_path_len;
   int pad;
   unsigned long long graph_cond;  // cudaGraphConditionalHandle (0 = none)
+  // surrogate-guided bisection (0 = exact bisection only)
+  int sbis;          // 1 when a surrogate is attached
+  int bis_mode;      // bisection kernel mode: 0 exact, 1 verify surrogate end point, 2 exact for fallbacks
+  float sbis_margin; // predicted collision iff sd_hat < margin
+  int pad2;
+  float* s_p32;      // [row * 8 + j] projection onto L (FP32)
+  float* s_d32;      // [row * 8 + j] c - c_proj (FP32)
+  float* s_lo;       // [row] bracket (fractions along [c_proj, c])
+  float* s_hi;
+  uint32_t* s_bits;  // [row] surrogate decisions
+  uint8_t* s_ok;     // [row] 1 when the surrogate end point was verified in collision
+  int* s_rows;       // device row count of this round (n_bisect_tiles * kTile)
 };
 
 // Launchers (ezo_kernels.cu). T = lanes per configuration.
@@ -114,6 +127,10 @@ cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int g
 cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s);
 cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s);
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s);
+// surrogate-guided bisection helpers (ezo_k_sbis.cu)
+cudaError_t launch_sbis_init(const BatchView& v, int grid, cudaStream_t s);
+cudaError_t launch_sbis_mid(const BatchView& v, void* X_bf16, int grid, cudaStream_t s);
+cudaError_t launch_sbis_update(const BatchView& v, const float* yhat, int step, int grid, cudaStream_t s);
 cudaError_t launch_round_place(const BatchView& v, cudaStream_t s);
 cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 

@@ -88,7 +88,7 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
     hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
   } else {
     const int ic = i < st.n_samples ? i : tile.y;
-    hnr_walk_split<NDOF, TSS, 8>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)ic, p.round_k,
+    hnr_walk_split<NDOF, TSS>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)ic, p.round_k,
                                  p.stream, lw, x);
     if (i >= st.n_samples || lw != 0) return;
   }
@@ -254,8 +254,12 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
     } else {
       const int nc = s_running < np ? s_running : np;
       st.n_cand = nc;
-      st.checks += (long long)nc * v.n_b;
-      st.checks_bisect += (long long)nc * v.n_b;
+      if (v.sbis) {
+        st.sur_evals += (long long)nc * v.n_b;  // exact checks are counted where they run
+      } else {
+        st.checks += (long long)nc * v.n_b;
+        st.checks_bisect += (long long)nc * v.n_b;
+      }
       const int nt = (nc + kTile - 1) / kTile;
       const int t0 = atomicAdd(&v.summary->n_bisect_tiles, nt);
       for (int t = 0; t < nt; ++t) v.bisect_tiles[t0 + t] = make_int2(g, t * kTile);

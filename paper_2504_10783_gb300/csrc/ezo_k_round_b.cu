@@ -48,7 +48,15 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
     const int np = st.n_p;
     {
       const int c = tile.y + sub + gi;
-      const bool valid = c < st.n_cand;
+      const int row = (u / T) * kTile + sub + gi;  // surrogate row of this candidate
+      bool valid = c < st.n_cand;
+      if (v.bis_mode == 2) {
+        // exact bisection only where the surrogate end point failed; a warp
+        // whose candidates all passed skips the work together
+        const bool need = valid && !v.s_ok[row];
+        if (!__any_sync(0xffffffffu, need)) continue;
+        valid = need;
+      }
       const int cc = valid ? c : tile.y;
       const int si = v.cand_idx[st.cand_off + cc];
       double cs[NDOF], p[NDOF], dv[NDOF];
@@ -59,7 +67,26 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
       for (int j = 0; j < NDOF; ++j) dv[j] = (j < n) ? cs[j] - p[j] : 0.0;
       double lo = 0.0, hi = 1.0;
       uint32_t bits = 0u;
-      for (int s = 0; s < v.n_b; ++s) {
+      if (v.bis_mode == 1) {
+        // verify the surrogate's end point with one exact check
+        hi = (double)v.s_hi[row];
+        bits = v.s_bits[row];
+        float qq[NDOF];
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) qq[j] = (float)fma(hi, dv[j], p[j]);
+        const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
+                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg);
+        if (valid && lg == 0) {
+          v.s_ok[row] = hit ? 1 : 0;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), 1ull);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), 1ull);
+        }
+        if (!hit) valid = false;  // no output: the exact pass (mode 2) redoes this candidate
+      } else if (v.bis_mode == 2 && valid && lg == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), (unsigned long long)v.n_b);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), (unsigned long long)v.n_b);
+      }
+      for (int s = 0; s < (v.bis_mode == 1 ? 0 : v.n_b); ++s) {
         const double mid = 0.5 * (lo + hi);
         float qq[NDOF];
 #pragma unroll

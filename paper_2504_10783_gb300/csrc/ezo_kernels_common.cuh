@@ -119,12 +119,11 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 // 2, 4, 8): lane lw draws Philox blocks lw, lw + TS, .. of each step and the
 // Box-Muller pairs they hold; the direction and the step uniform are
 // broadcast by shuffles; lane lw scans polytope rows lw, lw + TS, .. and the
-// chord bounds are combined with min/max shuffles. When the polytope has at
-// most TS * RPL rows, each lane keeps the slack b_r - a_r x of its rows in
-// registers and updates it by s_r -= t q_r instead of recomputing a_r x
-// (the slack then carries FP32 rounding of the updates, about 1e-7 per
-// step). All lanes of the warp must call this together.
-template <int NDOF, int TS, int RPL>
+// chord bounds are combined with min/max shuffles. Every lane ends with the
+// same x, bit-identical to hnr_walk's (same per-row arithmetic; min and max do
+// not depend on the order), so a segment's samples do not depend on how many
+// other walks share its round. All lanes of the warp must call this together.
+template <int NDOF, int TS>
 __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, int m, int n, const float* v1f,
                                                const float* ef, int n_mix, uint32_t key0, uint32_t key1,
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
@@ -138,21 +137,6 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
   const float u0 = u01_co(r0.x);
 #pragma unroll
   for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
-  // slack b_r - a_r x of this lane's rows, kept in registers when they fit
-  const bool inc = m <= TS * RPL;
-  float slk[RPL];
-#pragma unroll
-  for (int i = 0; i < RPL; ++i) {
-    const int r = lw + i * TS;
-    slk[i] = 0.f;
-    if (inc && r < m) {
-      const float* a = A32 + r * RS;
-      float ax = 0.f;
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) ax = fmaf(a[j], x[j], ax);
-      slk[i] = a[NDOF] - ax;
-    }
-  }
   for (int s = 0; s < n_mix; ++s) {
     // this lane's blocks: Gaussians z[4b .. 4b+3] from words 4b .. 4b+3
     float z[4 * BPL];
@@ -199,54 +183,26 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    float qv[RPL];
-    if (inc) {
-      // rows lw + TS i: slack kept up to date in registers
+    for (int r = lw; r < m; r += TS) {
+      const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
+      float av[RS];
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int r = lw + i * TS;
-        qv[i] = 0.f;
-        if (r < m) {
-          const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
-          float av[RS];
-#pragma unroll
-          for (int qd = 0; qd < RS / 4; ++qd) {
-            const float4 v4 = row[qd];
-            av[4 * qd] = v4.x;
-            av[4 * qd + 1] = v4.y;
-            av[4 * qd + 2] = v4.z;
-            av[4 * qd + 3] = v4.w;
-          }
-          float ad = 0.f;
-#pragma unroll
-          for (int j = 0; j < NDOF; ++j) ad = fmaf(av[j], d[j], ad);
-          qv[i] = ad;
-          if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(slk[i], ad));
-          else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(slk[i], ad));
-        }
+      for (int qd = 0; qd < RS / 4; ++qd) {
+        const float4 v4 = row[qd];
+        av[4 * qd] = v4.x;
+        av[4 * qd + 1] = v4.y;
+        av[4 * qd + 2] = v4.z;
+        av[4 * qd + 3] = v4.w;
       }
-    } else {
-      for (int r = lw; r < m; r += TS) {
-        const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
-        float av[RS];
+      float ax = 0.f, ad = 0.f;
 #pragma unroll
-        for (int qd = 0; qd < RS / 4; ++qd) {
-          const float4 v4 = row[qd];
-          av[4 * qd] = v4.x;
-          av[4 * qd + 1] = v4.y;
-          av[4 * qd + 2] = v4.z;
-          av[4 * qd + 3] = v4.w;
-        }
-        float ax = 0.f, ad = 0.f;
-#pragma unroll
-        for (int j = 0; j < NDOF; ++j) {
-          ax = fmaf(av[j], x[j], ax);
-          ad = fmaf(av[j], d[j], ad);
-        }
-        const float sl = av[NDOF] - ax;
-        if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(sl, ad));
-        else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(sl, ad));
+      for (int j = 0; j < NDOF; ++j) {
+        ax = fmaf(av[j], x[j], ax);
+        ad = fmaf(av[j], d[j], ad);
       }
+      const float sl = av[NDOF] - ax;
+      if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(sl, ad));
+      else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(sl, ad));
     }
 #pragma unroll
     for (int o = 1; o < TS; o <<= 1) {
@@ -259,10 +215,6 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
       const float t = fmaf(ut, t_hi - t_lo, t_lo);
 #pragma unroll
       for (int j = 0; j < NDOF; ++j) x[j] = fmaf(t, d[j], x[j]);
-      if (inc) {
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) slk[i] = fmaf(-t, qv[i], slk[i]);
-      }
     }
   }
 }

@@ -455,6 +455,33 @@ cudaError_t adam_step(ezo_surrogate* S, float lr, cudaStream_t s) {
 
 }  // namespace
 
+// Forward pass on BF16 feature rows X [rows_cap x 64] for the rows below the
+// device count *m_dev; hA, hB are [rows_cap x 256] BF16 scratch. Internal.
+extern "C" __attribute__((visibility("hidden"))) cudaError_t ezo_internal_mlp_forward(
+    ezo_surrogate* S, const void* X, long long rows_cap, const int* m_dev, void* hA, void* hB, float* yhat,
+    cudaStream_t s) {
+  GemmArgs a{};
+  a.M = (int)rows_cap;
+  a.N = kH;
+  a.m_dev = m_dev;
+  a.A = static_cast<const __nv_bfloat16*>(X); a.lda = kF; a.B = S->W1; a.ldb = kF; a.K = kF; a.bias = S->p + kOffB1;
+  a.H = static_cast<__nv_bfloat16*>(hA);
+  cudaError_t e = gemm(EPI_BIAS_SILU_H, a, s);
+  if (e != cudaSuccess) return e;
+  a.A = static_cast<const __nv_bfloat16*>(hA); a.lda = kH; a.B = S->W2; a.ldb = kH; a.K = kH; a.bias = S->p + kOffB2;
+  a.H = static_cast<__nv_bfloat16*>(hB);
+  if ((e = gemm(EPI_BIAS_SILU_H, a, s)) != cudaSuccess) return e;
+  a.A = static_cast<const __nv_bfloat16*>(hB); a.B = S->W3; a.bias = S->p + kOffB3; a.H = static_cast<__nv_bfloat16*>(hA);
+  if ((e = gemm(EPI_BIAS_SILU_H, a, s)) != cudaSuccess) return e;
+  k_out<<<blocks_for(rows_cap * 32, 256), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(hA), S->p + kOffW4,
+                                                        S->p + kOffB4, rows_cap, m_dev, yhat);
+  return cudaGetLastError();
+}
+
+extern "C" __attribute__((visibility("hidden"))) int ezo_internal_surrogate_dof(const ezo_surrogate* S) {
+  return S ? S->n : 0;
+}
+
 extern "C" {
 
 int64_t ezo_surrogate_num_params(void) { return kNumParams; }

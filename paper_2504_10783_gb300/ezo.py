@@ -93,6 +93,7 @@ def _sig(lib):
                                       C.POINTER(C.c_float), _P]
     f.ezo_surrogate_grad.argtypes = [_P, _P, _I64, _P, _I32, C.POINTER(C.c_float), C.POINTER(C.c_float), _P]
     f.ezo_surrogate_predict.argtypes = [_P, _P, _I64, _I64, _P, _P]
+    f.ezo_batch_attach_surrogate.argtypes = [_P, _P, C.c_float]
     f.ezo_tune_lanes.argtypes = [_P, _P, _I64, C.POINTER(_I32), _P]
     f.ezo_set_autotune.argtypes = [_I32]
     f.ezo_check_flops.argtypes = [_P, _P]
@@ -369,6 +370,16 @@ class Batch:
         o = np.zeros(2, dtype=np.int64)
         _check(lib().ezo_batch_read(self.h, g, 9, C.c_void_p(o.ctypes.data), o.nbytes))
         return int(o[0]), int(o[1])
+
+    def attach_surrogate(self, sur, margin: float = 0.0):
+        """Surrogate-guided bisection (None detaches)."""
+        self._sur = sur
+        _check(lib().ezo_batch_attach_surrogate(self.h, sur.h if sur is not None else None, margin))
+
+    def surrogate_evals(self, g: int) -> int:
+        o = np.zeros(1, dtype=np.int64)
+        _check(lib().ezo_batch_read(self.h, g, 11, C.c_void_p(o.ctypes.data), o.nbytes))
+        return int(o[0])
 
     def summary(self) -> dict:
         o = np.zeros(4, dtype=np.int32)

@@ -184,6 +184,23 @@ def test_hit_and_run_matches_oracle_walks(ezo, which):
     assert np.all(x @ A.T <= b + 1e-5 * (1 + np.abs(b)))
 
 
+def test_round_walks_equal_flat_walks(ezo):
+    """The round sampler (several lanes per walk in small rounds) gives the
+    flat sampler's samples bit for bit: same Philox draws, same arithmetic."""
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(n_p=3000, seed=13)
+    bt = ezo.Batch(robot, [env], path[2], path[3], prm, seg_stream=[7])
+    bt.step(0)
+    bt.step(1)
+    bt.sync()
+    st = bt.state(0)
+    S = bt.read(0, "samples")[:, : st["n_samples"]].T.astype(np.float64)
+    A, b = orc.joint_box(rd)
+    x = _gpu_hnr(ezo, A, b, path[2], path[3], st["n_samples"], prm.n_mix, 13, 7, 1)
+    np.testing.assert_array_equal(S, x)
+
+
 # ----------------------------------------------------- round-by-round replay --
 def _replay_rounds(ezo, rd, env_np, v1, v2, prm_kw, max_rounds=6):
     robot, env = ezo.Robot(rd), ezo.Env(env_np)

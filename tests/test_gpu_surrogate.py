@@ -88,13 +88,115 @@ def test_surrogate_training_learns_signed_distance(ezo):
     rd, env_np = _scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
     sur = ezo.Surrogate(robot, seed=5)
-    losses = sur.train(env, n_samples=1 << 18, epochs=4, batch=4096, lr=1e-3, data_seed=11)
-    assert np.all(np.isfinite(losses)) and losses[-1] < 0.5 * losses[0]
-    # held-out configurations: compare with exact labels
+    # held-out configurations with exact labels
     q = wl.uniform_configs(9, rd, 4096).astype(np.float32)
+    sd = np.clip(orc.signed_distance(rd, env_np, q.astype(np.float64)), -0.1, 0.3)
+    qd = torch.from_numpy(q.T.copy()).cuda()
+    out = torch.empty(q.shape[0], device="cuda")
+
+    def rmse():
+        sur.predict(qd, out)
+        torch.cuda.synchronize()
+        return float(np.sqrt(np.mean((out.cpu().numpy() - sd) ** 2)))
+
+    before = rmse()
+    losses = sur.train(env, n_samples=1 << 18, epochs=4, batch=4096, lr=1e-3, data_seed=11)
+    after = rmse()
+    assert np.all(np.isfinite(losses)) and losses[-1] <= losses[0]
+    assert after < 0.5 * before and after < 0.5 * float(np.std(sd)), (before, after, float(np.std(sd)))
+
+
+@pytest.fixture(scope="module")
+def trained(ezo):
+    rd, env_np = _scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    sur = ezo.Surrogate(robot, seed=6)
+    sur.train(env, n_samples=1 << 20, epochs=3, batch=4096, lr=1e-3, data_seed=12)
+    return rd, env_np, robot, env, sur
+
+
+def test_surrogate_false_negative_rate_reported(ezo, trained):
+    rd, env_np, robot, env, sur = trained
+    q = wl.uniform_configs(10, rd, 20000).astype(np.float32)
     out = torch.empty(q.shape[0], device="cuda")
     sur.predict(torch.from_numpy(q.T.copy()).cuda(), out)
     torch.cuda.synchronize()
-    sd = np.clip(orc.signed_distance(rd, env_np, q.astype(np.float64)), -0.1, 0.3)
-    rmse = float(np.sqrt(np.mean((out.cpu().numpy() - sd) ** 2)))
-    assert rmse < 0.5 * float(np.std(sd)), (rmse, float(np.std(sd)))
+    col = orc.in_collision(rd, env_np, q.astype(np.float64))
+    pred = out.cpu().numpy() < 0.0
+    fn = float(np.mean(~pred[col])) if col.any() else 0.0
+    fp = float(np.mean(pred[~col]))
+    print(f"surrogate false-negative rate {fn:.3f}, false-positive rate {fp:.3f} on {q.shape[0]} configurations")
+    assert fn < 0.5 and fp < 0.5
+
+
+def test_surrogate_bisection_round_replay(ezo, trained):
+    """One round with surrogate-guided bisection: every candidate end point is
+    exactly in collision on [c_proj, c]; candidates whose surrogate end point
+    was free carry the exact bisection; placement equals the oracle's on the
+    GPU's end points."""
+    rd, env_np, robot, env, sur = trained
+    with open(os.path.join(GOLDEN, "workloads.json")) as f:
+        path = np.asarray(json.load(f)["dh7"]["path"])
+    v1, v2 = path[3], path[4]
+    prm = ezo.Params.make(n_p=2000, seed=21)
+    bt = ezo.Batch(robot, [env], v1, v2, prm)
+    bt.attach_surrogate(sur, 0.0)
+    for step in range(4):
+        bt.step(step)
+    bt.sync()
+    st = bt.state(0)
+    assert st["status"] == ezo.SEG_ACTIVE and st["n_cand"] > 0
+    nc = st["n_cand"]
+    S = bt.read(0, "samples")[:, : st["n_samples"]].T.astype(np.float64)
+    idx = bt.read(0, "cand_idx")[:nc]
+    bt.step(4)
+    bt.sync()
+    cst = bt.read(0, "c_star")[:, :nc].T
+    bits = bt.read(0, "bits")[:nc]
+    c = S[idx]
+    p = orc.project_onto_segment(c, v1, v2)
+    # c* = p + f (c - p) with a dyadic f in (0, 1]
+    f = np.einsum("ij,ij->i", cst - p, c - p) / np.einsum("ij,ij->i", c - p, c - p)
+    np.testing.assert_allclose(cst, p + f[:, None] * (c - p), atol=1e-9)
+    assert np.all((f > 0) & (f <= 1 + 1e-12))
+    sd = orc.signed_distance(rd, env_np, cst)
+    assert np.all(sd < 1e-5), "an end point is not in collision"
+    follow = ((bits[:, None] >> np.arange(prm.n_b)[None, :]) & 1).astype(bool)
+    ex = orc.bisect(rd, env_np, c, v1, v2, prm.n_b, follow=follow, band=1e-5)
+    same = np.all(np.abs(ex.c_star - cst) < 1e-9, axis=1)
+    print(f"{nc} candidates, {int(same.sum())} with the exact bisection's end point, "
+          f"{bt.check_split(0)[1]} exact bisection checks vs {nc * prm.n_b} without the surrogate")
+    m_before = st["m"]
+    bt.step(5)
+    bt.sync()
+    st = bt.state(0)
+    pl = orc.place_hyperplanes(cst, idx, v1, v2, prm.n_f, prm.step_back_max, prm.t_col)
+    res = bt.segment(0)
+    np.testing.assert_allclose(res.A[m_before:], pl.rows_a, rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(res.b[m_before:], pl.rows_b, rtol=1e-6, atol=1e-12)
+
+
+def test_surrogate_path_gain_and_validity(ezo, trained):
+    """The whole 10-segment path with and without the surrogate: every
+    polytope contains its segment and is accepted by the exact test, and the
+    surrogate cuts the exact checks spent in bisection."""
+    rd, env_np, robot, env, sur = trained
+    with open(os.path.join(GOLDEN, "workloads.json")) as f:
+        path = np.asarray(json.load(f)["dh7"]["path"])
+    K = path.shape[0] - 1
+    prm = ezo.Params.make(n_p=10000, seed=1)
+    out = {}
+    for use in (False, True):
+        bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm)
+        if use:
+            bt.attach_surrogate(sur, 0.0)
+        bt.run(ezo.RUN_GRAPH)
+        bis = sum(bt.check_split(g)[1] for g in range(K))
+        for g in range(K):
+            r = bt.segment(g)
+            assert r.status == ezo.SEG_ACCEPTED
+            assert orc.segment_contained(r.A, r.b, path[g], path[g + 1], tol=1e-12)
+        out[use] = (bis, sum(bt.surrogate_evals(g) for g in range(K)))
+    print(f"exact bisection checks: {out[False][0]} without, {out[True][0]} with the surrogate "
+          f"({out[True][1]} surrogate evaluations)")
+    assert out[True][0] < 0.6 * out[False][0]
