@@ -175,6 +175,54 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- GPU leg --
+def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args):
+    """Trains the BF16 MLP on 2^22 exact labels (4 epochs), reports its
+    false-negative / false-positive rates on 2^16 fresh configurations, and
+    times the path with surrogate-guided bisection."""
+    from paper_2504_10783_gb300 import workloads as wl
+    sur = ezo.Surrogate(robot, seed=6)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sur.train(env, n_samples=1 << 22, epochs=4, batch=4096, lr=1e-3, data_seed=12)
+    e1.record(stream)
+    e1.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    q = torch.from_numpy(wl.uniform_configs(10, rd, 1 << 16).astype(np.float32).T.copy()).cuda()
+    y = torch.empty(q.shape[1], device="cuda")
+    flags = torch.empty(q.shape[1], dtype=torch.uint8, device="cuda")
+    sur.predict(q, y)
+    ezo.check_collision(robot, env, q, flags)
+    torch.cuda.synchronize()
+    yv, col = y.cpu().numpy(), flags.cpu().numpy().astype(bool)
+    fn0 = float(np.mean(yv[col] >= 0.0)) if col.any() else 0.0
+    fp0 = float(np.mean(yv[~col] < 0.0))
+    bt.attach_surrogate(sur, 0.0)
+    times = []
+    for _ in range(max(3, args.steps // 2) + 2):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bt.reset()
+        bt.run_path(sequential=False, mode=mode)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    times = times[2:]
+    samp = bisc = evals = 0
+    for g in range(K):
+        x, y2 = bt.check_split(g)
+        samp += x
+        bisc += y2
+        evals += bt.surrogate_evals(g)
+    bt.attach_surrogate(None)
+    return {"ms_per_path": float(np.median(times)), "train_ms": train_ms, "train_samples": 1 << 22, "epochs": 4,
+            "fn_rate_margin0": fn0, "fp_rate_margin0": fp0, "sample_checks": samp, "bisection_checks": bisc,
+            "surrogate_evals": evals,
+            "what": "same path, bisection steps on the BF16 MLP, end points verified exactly, exact fallback"}
+
+
 def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg, N=2_000_000, reps=10):
     """ezo_check_collision on N uniform configurations (configurations and
     flags resident in HBM, L2 flushed between launches), CUDA events."""
@@ -216,6 +264,7 @@ def main():
     ap.add_argument("--cpu-leg", action="store_true")
     ap.add_argument("--seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args()
     if args.cpu_leg:
         cpu_leg(args.seconds)
@@ -333,6 +382,12 @@ def main():
     plain = {"ms_per_path": float(np.median(plain_ms)), "kept_segments": int(kept_plain),
              "what": "sequential per-segment inflation (paper's order), host-driven launch loop"}
 
+    # ---- batched + learned surrogate (spec item 4): train on exact
+    #      labels, then the same path with surrogate-guided bisection ----
+    sur_info = None
+    if not args.no_surrogate:
+        sur_info = measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args)
+
     # ---- the collision checker alone on the paper's batch size (2e6 configs) ----
     checker = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg)
 
@@ -369,7 +424,7 @@ def main():
                        "checks_per_step": checks_per_step, "sample_checks": samp, "bisection_checks": bisc,
                        "ms_per_10_segment_path": ms / args.steps,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "plain_sequential": plain, "checker_2e6": checker, "e2e": e2e, "gpu_launches": launches + checker["launches"],
+            "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "e2e": e2e, "gpu_launches": launches + checker["launches"],
             "clocks": clocks}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args.seconds)
