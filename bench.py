@@ -174,6 +174,104 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# --------------------------------------------------- batched and stress workloads --
+def _event_ms(torch, stream, fn):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_workload(args):
+    """--workload batched: 8 obstacle sets of 128-1024 spheres, seed paths of
+    1-40 segments, per-segment N_p log-uniform in [1e3, 1e5]; all segments of
+    all paths inflated in one batch under one CUDA graph, against the plain
+    per-segment launch loop. --workload stress: table point cloud (1024
+    spheres of 2 cm), 64-segment path, N_p = 1e6 samples per round: plain,
+    batched, batched + surrogate."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_10783_gb300 import ezo, workloads as wl
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        scenes = json.load(f)
+    rd = wl.dh7_robot()
+    robot = ezo.Robot(rd)
+    out = {"workload": args.workload}
+    if args.workload == "batched":
+        sc = scenes["dh7_batched"]
+        envs_np = [wl.box_obstacles(e["env_seed"], e["n_obs"]) for e in sc["envs"]]
+        envs = [ezo.Env(e) for e in envs_np]
+        paths = sc["paths"][: args.paths]
+        v1, v2, seg_env, path_first = [], [], [], []
+        for pth in paths:
+            verts = np.asarray(pth["path"])
+            first = len(v1)
+            for k in range(verts.shape[0] - 1):
+                v1.append(verts[k])
+                v2.append(verts[k + 1])
+                seg_env.append(pth["env"])
+                path_first.append(first)
+        B = len(v1)
+        rng = np.random.default_rng(5)
+        seg_np = np.round(10 ** rng.uniform(3, 5, B)).astype(np.int32)
+        prm = ezo.Params.make(eps=0.05, delta=0.05, n_p=10000, n_f=10, n_b=10, n_mix=60, n_it_max=50, seed=1)
+        bt = ezo.Batch(robot, envs, np.asarray(v1), np.asarray(v2), prm, seg_env=seg_env, seg_np=seg_np,
+                       seg_stream=np.arange(B), path_first=path_first)
+        t_graph = []
+        for rep in range(2):
+            t_graph.append(_event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False,
+                                                                                     mode=ezo.RUN_GRAPH))))
+        checks = sum(sum(bt.check_split(g)) for g in range(B))
+        kept = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
+        t_loop = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)))
+        kept_loop = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
+        out.update({"paths": len(paths), "segments": B, "samples_per_round": int(seg_np.sum()),
+                    "obstacles": [e["n_obs"] for e in sc["envs"]],
+                    "batched_graph_ms": float(min(t_graph)), "batched_checks": int(checks),
+                    "batched_configs_per_s": checks / (min(t_graph) / 1e3), "kept_segments": int(kept),
+                    "per_segment_loop_ms": float(t_loop), "kept_segments_loop": int(kept_loop),
+                    "speedup": float(t_loop / min(t_graph))})
+    else:
+        sc = scenes["table_cloud"]
+        env_np = wl.table_cloud_obstacles(sc["cloud_seed"])
+        env = ezo.Env(env_np)
+        verts = np.asarray(sc["path"])
+        K = verts.shape[0] - 1
+        prm = ezo.Params.make(eps=0.05, delta=0.05, n_p=args.np_stress, n_f=10, n_b=10, n_mix=60, n_it_max=50,
+                              seed=1)
+        bt = ezo.Batch(robot, [env], verts[:-1], verts[1:], prm, seg_stream=np.arange(K),
+                       path_first=np.zeros(K, np.int32))
+
+        def counts():
+            c = sum(sum(bt.check_split(g)) for g in range(K))
+            kept = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(K))
+            return int(c), int(kept)
+
+        t_plain = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)))
+        c_plain, k_plain = counts()
+        t_batch = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)))
+        c_batch, k_batch = counts()
+        sur = ezo.Surrogate(robot, seed=7)
+        t_train = _event_ms(torch, stream, lambda: sur.train(env, n_samples=1 << 23, epochs=4, batch=4096,
+                                                             lr=1e-3, data_seed=13))
+        bt.attach_surrogate(sur, 0.0)
+        t_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)))
+        c_sur, k_sur = counts()
+        evals = sum(bt.surrogate_evals(g) for g in range(K))
+        out.update({"segments": K, "obstacles": int(env_np.n_obs), "n_p": args.np_stress,
+                    "plain_ms": t_plain, "plain_checks": c_plain, "plain_kept": k_plain,
+                    "batched_ms": t_batch, "batched_checks": c_batch, "batched_kept": k_batch,
+                    "surrogate_train_ms": t_train, "batched_surrogate_ms": t_sur, "batched_surrogate_checks": c_sur,
+                    "surrogate_evals": int(evals), "batched_surrogate_kept": k_sur})
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------- GPU leg --
 def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args):
     """Trains the BF16 MLP on 2^22 exact labels (4 epochs), reports its
@@ -265,12 +363,18 @@ def main():
     ap.add_argument("--seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--workload", default="path", choices=["path", "batched", "stress"])
+    ap.add_argument("--paths", type=int, default=256, help="batched: number of seed paths")
+    ap.add_argument("--np-stress", type=int, default=1_000_000, help="stress: samples per round and segment")
     args = ap.parse_args()
     if args.cpu_leg:
         cpu_leg(args.seconds)
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "path":
+        run_workload(args)
         return
 
     import torch
@@ -335,12 +439,13 @@ def main():
     prof = ezo.profile_read()
     ezo.profile_enable(False)
     ms = float(np.sum(times))
-    samp = bisc = 0
+    samp = bisc = sflops = 0
     kept = 0
     for g in range(K):
         a, b_ = bt.check_split(g)
         samp += a
         bisc += b_
+        sflops += bt.sample_flops(g)
         kept += bt.segment(g).status != ezo.SEG_SKIPPED
     checks_per_step = samp + bisc
     if dist is not None:
@@ -356,8 +461,9 @@ def main():
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA
     roofline = None
     if mode == ezo.RUN_HOST_LOOP and prof["bisect"][1] > 0:
-        work = {"check": samp * flops_cfg * args.steps, "bisect": bisc * flops_cfg * args.steps}
-        dom = max(("check", "bisect"), key=lambda k: prof[k][0])
+        work = {"check": samp * flops_cfg * args.steps, "bisect": bisc * flops_cfg * args.steps,
+                "sample": sflops * args.steps}
+        dom = max(("check", "bisect", "sample"), key=lambda k: prof[k][0])
         ach = work[dom] / (prof[dom][0] / 1e3) / 1e12
         roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None,

@@ -224,8 +224,9 @@ ezo_status ezo_batch_sync(ezo_batch* batch, void* cuda_stream);
  * (uint32 N_p, bit s = midpoint s in collision), 6 round state (int32[12]:
  * k, status, m, |S|, M, count, n_cand, planes, rounds, n_placed, N_p, env),
  * 7 placed candidate indices of the last round (int32 n_f), 8 step backs of
- * the last round (FP64 n_f), 9 exact checks split as int64[2] {at samples,
- * at bisection midpoints}, 11 surrogate evaluations (int64), 10 the batch's round summary (int32[4]: active
+ * the last round (FP64 n_f), 9 work counters int64[3] {exact checks at
+ * samples, exact checks at bisection midpoints, algorithmic FP32 flops of the
+ * hit-and-run walks: per walk step m (4n + 2) + 14n}, 11 surrogate evaluations (int64), 10 the batch's round summary (int32[4]: active
  * segments, rounds run since the last reset, sample tiles, bisection tiles;
  * `seg` is ignored). `bytes` is the size of `dst`. */
 ezo_status ezo_batch_read(const ezo_batch* batch, int32_t seg, int32_t what, void* dst, int64_t bytes);

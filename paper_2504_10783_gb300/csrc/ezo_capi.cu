@@ -1066,8 +1066,8 @@ ezo_status ezo_batch_read(const ezo_batch* b, int32_t seg, int32_t what, void* d
       return EZO_OK;
     }
     case 9: {
-      if (bytes < (int64_t)(2 * sizeof(int64_t))) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
-      const int64_t vals[2] = {s.checks - s.checks_bisect, s.checks_bisect};
+      if (bytes < (int64_t)(3 * sizeof(int64_t))) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
+      const int64_t vals[3] = {s.checks - s.checks_bisect, s.checks_bisect, s.sample_flops};
       std::memcpy(dst, vals, sizeof(vals));
       return EZO_OK;
     }

@@ -44,6 +44,7 @@ struct SegState {
   int pad1;
   long long checks_bisect;  // of which at bisection midpoints
   long long sur_evals;      // surrogate evaluations (surrogate-guided bisection)
+  long long sample_flops;   // algorithmic FP32 work of the hit-and-run walks so far
 };
 
 struct EnvDevFull {

@@ -33,6 +33,10 @@ __global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
         if (S > st.s_cap) S = st.s_cap;  // capacity is sized for M at N_it; never hit
         st.m_test = M;
         st.n_samples = S;
+        // algorithmic FP32 work of this round's walks: per step and row two
+        // n-term dot products, a subtraction and a ratio; per step n Gaussians
+        // (Box-Muller, ~10 flops each), normalisation and the move (4n)
+        st.sample_flops += (long long)S * v.n_mix * ((long long)st.m * (4 * v.n + 2) + 14 * v.n);
         st.n_cand = 0;
         st.count = 0;
         st.n_placed = 0;
@@ -98,20 +102,21 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
 }
 
 // Hit-and-run for every active segment. When the round has few walks (few
-// active segments) eight lanes share each walk, which cuts the latency of the
-// sequential N_ms steps; otherwise each lane runs one walk. The choice is made
-// on the device from the round's tile count, so it also works inside a graph.
-// Work units are (tile, pass) pairs: a tile of kTile walks takes one pass of
-// 128 walks at one lane each, or eight passes of 16 walks at eight lanes each,
-// and the passes of a tile go to different blocks.
+// active segments) several lanes share each walk, which cuts the latency of
+// the sequential N_ms steps and fills the GPU; with many walks each lane runs
+// one. The choice is made on the device from the round's tile count, so it
+// also works inside a graph. Work units are (tile, pass) pairs: a tile of
+// kTile walks takes one pass at one lane per walk, or 2 or 8 passes at 2 or 8
+// lanes per walk, and the passes of a tile go to different blocks.
 template <int NDOF>
 __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_below_tiles) {
   extern __shared__ float4 smf4[];
   __shared__ SampleParams p;
   __shared__ int cur_seg;
   const int n_tiles = v.summary->n_sample_tiles;
-  const bool split = n_tiles < split_below_tiles;
-  const int passes = split ? 8 : 1;
+  // eight lanes per walk below the threshold, two up to eight times it,
+  // one above (more walks than the GPU holds warps)
+  const int passes = n_tiles < split_below_tiles ? 8 : (n_tiles < 8 * split_below_tiles ? 2 : 1);
   float* A32 = reinterpret_cast<float*>(smf4);
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();
@@ -139,7 +144,8 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
       }
       __syncthreads();
     }
-    if (split) sample_pass<NDOF, 8>(v, st, A32, p, tile, u % passes);
+    if (passes == 8) sample_pass<NDOF, 8>(v, st, A32, p, tile, u % passes);
+    else if (passes == 2) sample_pass<NDOF, 2>(v, st, A32, p, tile, u % passes);
     else sample_pass<NDOF, 1>(v, st, A32, p, tile, 0);
   }
 }

@@ -367,9 +367,16 @@ class Batch:
         return o
 
     def check_split(self, g: int):
-        o = np.zeros(2, dtype=np.int64)
+        """(exact checks at samples, exact checks at bisection midpoints)."""
+        o = np.zeros(3, dtype=np.int64)
         _check(lib().ezo_batch_read(self.h, g, 9, C.c_void_p(o.ctypes.data), o.nbytes))
         return int(o[0]), int(o[1])
+
+    def sample_flops(self, g: int) -> int:
+        """Algorithmic FP32 flops of the hit-and-run walks of segment g."""
+        o = np.zeros(3, dtype=np.int64)
+        _check(lib().ezo_batch_read(self.h, g, 9, C.c_void_p(o.ctypes.data), o.nbytes))
+        return int(o[2])
 
     def attach_surrogate(self, sur, margin: float = 0.0):
         """Surrogate-guided bisection (None detaches)."""
