@@ -175,14 +175,17 @@ def run_reference(args):
 
 
 # --------------------------------------------------- batched and stress workloads --
-def _event_ms(torch, stream, fn):
+def _event_ms(torch, stream, fn, label=""):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
     fn()
     b.record(stream)
     b.synchronize()
-    return a.elapsed_time(b)
+    ms = a.elapsed_time(b)
+    if label:
+        print(f"[bench] {label}: {ms:.1f} ms", file=sys.stderr, flush=True)
+    return ms
 
 
 def run_workload(args):
@@ -226,17 +229,27 @@ def run_workload(args):
         t_graph = []
         for rep in range(2):
             t_graph.append(_event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False,
-                                                                                     mode=ezo.RUN_GRAPH))))
+                                                                                     mode=ezo.RUN_GRAPH)),
+                                    "batched graph"))
         checks = sum(sum(bt.check_split(g)) for g in range(B))
         kept = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
-        t_loop = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)))
+        t_wave = []
+        for rep in range(2):
+            t_wave.append(_event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
+                                    "wavefront graph"))
+        checks_wave = sum(sum(bt.check_split(g)) for g in range(B))
+        kept_wave = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
+        t_loop = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)), "per-segment loop")
         kept_loop = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
         out.update({"paths": len(paths), "segments": B, "samples_per_round": int(seg_np.sum()),
                     "obstacles": [e["n_obs"] for e in sc["envs"]],
                     "batched_graph_ms": float(min(t_graph)), "batched_checks": int(checks),
                     "batched_configs_per_s": checks / (min(t_graph) / 1e3), "kept_segments": int(kept),
+                    "wavefront_graph_ms": float(min(t_wave)), "wavefront_checks": int(checks_wave),
+                    "kept_segments_wavefront": int(kept_wave),
                     "per_segment_loop_ms": float(t_loop), "kept_segments_loop": int(kept_loop),
-                    "speedup": float(t_loop / min(t_graph))})
+                    "speedup_wavefront_vs_loop": float(t_loop / min(t_wave)),
+                    "speedup_speculative_vs_loop": float(t_loop / min(t_graph))})
     else:
         sc = scenes["table_cloud"]
         env_np = wl.table_cloud_obstacles(sc["cloud_seed"])
@@ -253,15 +266,17 @@ def run_workload(args):
             kept = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(K))
             return int(c), int(kept)
 
-        t_plain = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)))
+        t_plain = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)), "plain")
         c_plain, k_plain = counts()
-        t_batch = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)))
+        t_batch = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
+                            "batched")
         c_batch, k_batch = counts()
         sur = ezo.Surrogate(robot, seed=7)
         t_train = _event_ms(torch, stream, lambda: sur.train(env, n_samples=1 << 23, epochs=4, batch=4096,
-                                                             lr=1e-3, data_seed=13))
+                                                             lr=1e-3, data_seed=13), "surrogate training")
         bt.attach_surrogate(sur, 0.0)
-        t_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)))
+        t_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
+                          "batched + surrogate")
         c_sur, k_sur = counts()
         evals = sum(bt.surrogate_evals(g) for g in range(K))
         out.update({"segments": K, "obstacles": int(env_np.n_obs), "n_p": args.np_stress,

@@ -189,10 +189,13 @@ ezo_status ezo_batch_run(ezo_batch* batch, int32_t mode, void* cuda_stream);
 /* Sec. VI-A: the batch's segments form paths (path_first); inflate them in
  * order, skipping a segment whose endpoints lie in an earlier polytope of the
  * same path (A x <= b + 1e-9), and stop a path after a segment reported in
- * collision. sequential = 1 runs one segment at a time (the paper's order);
- * sequential = 0 inflates all segments speculatively in one batched run and
- * applies the same skip rule afterwards, which keeps the same polytopes.
- * Skipped segments report EZO_SEG_SKIPPED. Errors: EZO_ERR_CUDA. */
+ * collision. sequential = 1 runs one segment at a time over all paths (the
+ * paper's order, a host-driven launch loop); sequential = 2 ("wavefront")
+ * keeps each path's order but runs the current segment of every path in one
+ * batched run per wave; sequential = 0 inflates all segments speculatively
+ * in one batched run and applies the same skip rule afterwards. All three
+ * keep the same polytopes. Skipped segments report EZO_SEG_SKIPPED, segments
+ * after a collision EZO_SEG_IDLE. Errors: EZO_ERR_CUDA. */
 ezo_status ezo_batch_run_path(ezo_batch* batch, int32_t sequential, int32_t mode, void* cuda_stream);
 
 /* Per-segment result: status (ezo_segment_status), rounds run, rows m of the

@@ -936,7 +936,55 @@ ezo_status ezo_batch_run_path(ezo_batch* b, int32_t sequential, int32_t mode, vo
   std::vector<SegState> sts;
   std::vector<uint8_t> contained((size_t)B * L);
   std::vector<int> kept(B, 0);
-  if (sequential) {
+  if (sequential == 2) {
+    // wavefront: each path runs its segments in order with the skip rule;
+    // the current segments of all paths share one batched run per wave
+    ezo_status st = read_states(b, sts, s);
+    if (st != EZO_OK) return st;
+    for (int g = 0; g < B; ++g) sts[g].status = SEG_IDLE;
+    EZO_CUDA(cudaMemcpyAsync(b->d_st, sts.data(), sizeof(SegState) * B, cudaMemcpyHostToDevice, s));
+    std::vector<int> next(B, -1), stopped(B, 0);  // per path (indexed by its first segment)
+    for (int g = 0; g < B; ++g)
+      if (b->path_first[g] == g) next[g] = g;
+    for (int wave = 0; wave <= B; ++wave) {
+      EZO_CUDA(cudaMemsetAsync(b->d_contained, 0, (size_t)B * L, s));
+      cudaError_t e = launch_containment(b->view, b->d_contained, 1e-9, s);
+      if (e != cudaSuccess) return cuda_fail(e, "containment");
+      EZO_CUDA(cudaMemcpyAsync(contained.data(), b->d_contained, (size_t)B * L, cudaMemcpyDeviceToHost, s));
+      st = read_states(b, sts, s);
+      if (st != EZO_OK) return st;
+      int active = 0;
+      for (int pf = 0; pf < B; ++pf) {
+        if (next[pf] < 0 || stopped[pf]) continue;
+        int g = next[pf];
+        while (g < B && b->path_first[g] == pf) {
+          bool skip = false;
+          for (int j = pf; j < g && !skip; ++j)
+            if (kept[j] && contained[(size_t)g * L + (j - pf)]) skip = true;
+          if (!skip) break;
+          sts[g].status = SEG_SKIPPED;
+          ++g;
+        }
+        if (g < B && b->path_first[g] == pf) {
+          sts[g].status = SEG_ACTIVE;
+          kept[g] = 1;
+          next[pf] = g + 1;
+          ++active;
+        } else {
+          next[pf] = -1;
+        }
+      }
+      EZO_CUDA(cudaMemcpyAsync(b->d_st, sts.data(), sizeof(SegState) * B, cudaMemcpyHostToDevice, s));
+      if (!active) break;
+      st = run_batch(b, mode, s);
+      if (st != EZO_OK) return st;
+      st = read_states(b, sts, s);
+      if (st != EZO_OK) return st;
+      for (int g = 0; g < B; ++g)
+        if (kept[g] && sts[g].status == SEG_IN_COLLISION) stopped[b->path_first[g]] = 1;
+    }
+    EZO_CUDA(cudaStreamSynchronize(s));
+  } else if (sequential) {
     // every segment idle; activate one at a time in path order
     for (int g = 0; g < B; ++g) {
       ezo_status st = set_status(b, g, SEG_IDLE, s);

@@ -308,13 +308,16 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
   return hit;
 }
 
-// Exact signed distance min over pairs of ||c_i - c_j|| - r_i - r_j for one
-// configuration, one lane per configuration (used for labels and checks).
+// Signed distance min over pairs of ||c_i - c_j|| - r_i - r_j for one
+// configuration, one lane per configuration, exact below `cap` and equal to
+// cap above it (a pair whose squared distance is at least (r_i + r_j + cap)^2
+// cannot bring the minimum below cap, so its square root is skipped).
 template <int NDOF>
 __device__ float signed_distance_one(const float* __restrict__ q, const RobotSmem& rs,
                                      const float4* __restrict__ sph_s, const float4* __restrict__ obs_s,
                                      int n_obs, const ushort2* __restrict__ self_pairs,
-                                     const float* __restrict__ self_rr, float4* __restrict__ cen) {
+                                     const float* __restrict__ self_rr, float4* __restrict__ cen,
+                                     float cap) {
   float c0x = 1.f, c0y = 0.f, c0z = 0.f, c1x = 0.f, c1y = 1.f, c1z = 0.f, c2x = 0.f, c2y = 0.f, c2z = 1.f;
   float px = 0.f, py = 0.f, pz = 0.f;
   const int n = rs.n;
@@ -345,20 +348,24 @@ __device__ float signed_distance_one(const float* __restrict__ q, const RobotSme
                            fmaf(c0z, l.x, fmaf(c1z, l.y, fmaf(c2z, l.z, pz))), l.w);
     }
   }
-  float best = 3.0e38f;
+  float best = cap;
   for (int s = 0; s < rs.n_spheres; ++s) {
     const float4 c = cen[s];
     for (int j = 0; j < n_obs; ++j) {
       const float4 o = obs_s[j];
       const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
-      best = fminf(best, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - c.w - o.w);
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float lim = c.w + o.w + best;
+      if (lim > 0.f && d2 < lim * lim) best = fminf(best, sqrtf(d2) - c.w - o.w);
     }
   }
   for (int p = 0; p < rs.n_self; ++p) {
     const ushort2 pr = self_pairs[p];
     const float4 a = cen[pr.x], b = cen[pr.y];
     const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    best = fminf(best, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - a.w - b.w);
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float lim = a.w + b.w + best;
+    if (lim > 0.f && d2 < lim * lim) best = fminf(best, sqrtf(d2) - a.w - b.w);
   }
   return best;
 }

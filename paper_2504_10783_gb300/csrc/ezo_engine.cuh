@@ -115,8 +115,9 @@ struct BatchView {
 // Launchers (ezo_kernels.cu). T = lanes per configuration.
 cudaError_t launch_check_flat(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, float E, const float* q,
                               long long ldq, long long N, uint8_t* flags, int T, int grid_cap, cudaStream_t s);
+// signed distance, exact below cap (3e38: exact everywhere)
 cudaError_t launch_sd_flat(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, const float* q, long long ldq,
-                           long long N, float* sd, cudaStream_t s);
+                           long long N, float* sd, cudaStream_t s, float cap = 3.0e38f);
 cudaError_t launch_sample_flat(const double* A, const double* b, int m, int lda, int n, const double* v1h,
                                const double* v2h, long long N, int n_mix, uint64_t seed, uint32_t stream, int k,
                                float* out, long long ldo, cudaStream_t s);

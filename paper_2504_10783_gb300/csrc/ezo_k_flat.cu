@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_check_flat(const RobotDev* __restrict__
 template <int NDOF>
 __global__ void __launch_bounds__(128) k_sd_flat(const RobotDev* __restrict__ robot, EnvDev env,
                                                  const float* __restrict__ q, long long ldq, long long N,
-                                                 float* __restrict__ sd) {
+                                                 float* __restrict__ sd, float cap) {
   extern __shared__ float4 smem4[];
   __shared__ RobotSmem rs;
   const int nsp = robot->n_spheres_pad;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(128) k_sd_flat(const RobotDev* __restrict__ ro
     float qq[NDOF];
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) qq[j] = (j < rs.n) ? q[j * ldq + i] : 0.f;
-    sd[i] = signed_distance_one<NDOF>(qq, rs, sph_s, obs_s, env.n_obs, robot->self_pairs, robot->self_rr, cen);
+    sd[i] = signed_distance_one<NDOF>(qq, rs, sph_s, obs_s, env.n_obs, robot->self_pairs, robot->self_rr, cen, cap);
   }
 }
 
@@ -100,7 +100,7 @@ cudaError_t launch_check_flat(const RobotDev* robot, int n, int nsp_pad, const E
 
 
 cudaError_t launch_sd_flat(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, const float* q, long long ldq,
-                           long long N, float* sd, cudaStream_t s) {
+                           long long N, float* sd, cudaStream_t s, float cap) {
   if (N <= 0) return cudaSuccess;
   cudaError_t err = cudaSuccess;
   const int threads = 64;
@@ -110,7 +110,7 @@ cudaError_t launch_sd_flat(const RobotDev* robot, int n, int nsp_pad, const EnvD
     auto kern = k_sd_flat<ND>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
-    kern<<<(unsigned)grid, threads, smem, s>>>(robot, env, q, ldq, N, sd);
+    kern<<<(unsigned)grid, threads, smem, s>>>(robot, env, q, ldq, N, sd, cap);
   });
   return cudaGetLastError();
 }

@@ -81,7 +81,7 @@ template <int EPI>
 __global__ void __launch_bounds__(128) k_gemm_nt(GemmArgs g) {
   __shared__ __align__(16) __nv_bfloat16 As[kBM][kBK + kPad];
   __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kBK + kPad];
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
   const int m_lim = g.m_dev ? min(g.M, *g.m_dev) : g.M;
   if (m0 >= m_lim) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -349,7 +349,7 @@ namespace {
 using namespace ezo;
 
 cudaError_t gemm(int epi, const GemmArgs& a, cudaStream_t s) {
-  dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM);
+  dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);  // M tiles on x (no 65535 limit)
   switch (epi) {
     case EPI_F32: k_gemm_nt<EPI_F32><<<grid, 128, 0, s>>>(a); break;
     case EPI_BIAS_SILU: k_gemm_nt<EPI_BIAS_SILU><<<grid, 128, 0, s>>>(a); break;
@@ -664,7 +664,7 @@ ezo_status ezo_surrogate_train(ezo_surrogate* S, const ezo_env* env, int64_t n_s
     // signed distance, clamped to [label_lo, label_hi]
     k_uniform_q<<<blocks_for(N, 256), 256, 0, s>>>(q, N, n, bnd, bnd + EZO_MAX_DOF, (uint32_t)data_seed,
                                                      (uint32_t)(data_seed >> 32));
-    e = launch_sd_flat(rd, n, nsp, ef.e, q, N, N, t, s);
+    e = launch_sd_flat(rd, n, nsp, ef.e, q, N, N, t, s, label_hi);
     k_clamp_labels<<<blocks_for(N, 256), 256, 0, s>>>(t, N, label_lo, label_hi);
   }
   for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {

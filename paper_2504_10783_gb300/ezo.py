@@ -306,8 +306,11 @@ class Batch:
     def run(self, mode: int = RUN_HOST_LOOP, stream=None):
         _check(lib().ezo_batch_run(self.h, mode, _stream(stream)))
 
-    def run_path(self, sequential: bool = True, mode: int = RUN_HOST_LOOP, stream=None):
-        _check(lib().ezo_batch_run_path(self.h, 1 if sequential else 0, mode, _stream(stream)))
+    def run_path(self, sequential=True, mode: int = RUN_HOST_LOOP, stream=None):
+        """sequential: True/1 one segment at a time, 2 wavefront over paths,
+        False/0 speculative (all segments, skip rule applied afterwards)."""
+        seq = 2 if sequential == 2 else (1 if sequential else 0)
+        _check(lib().ezo_batch_run_path(self.h, seq, mode, _stream(stream)))
 
     def step(self, step: int, stream=None):
         _check(lib().ezo_batch_step(self.h, step, _stream(stream)))

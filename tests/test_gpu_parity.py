@@ -378,3 +378,36 @@ def test_degenerate_segment_point(ezo):
     res = ezo.inflate_segment(robot, env, v1, v1, prm)
     assert res.status == ezo.SEG_ACCEPTED
     assert np.all(res.A @ v1 <= res.b + 1e-12)
+
+
+def test_wavefront_equals_sequential_on_several_paths(ezo):
+    """Three seed paths over two obstacle sets with uneven N_p: the wavefront
+    mode (one segment per path per batched wave) keeps the polytopes of the
+    paper's one-segment-at-a-time order."""
+    sc = scenes()["dh7_batched"]
+    rd = wl.dh7_robot()
+    robot = ezo.Robot(rd)
+    use = [p for p in sc["paths"] if len(p["path"]) <= 6][:3]
+    env_ids = sorted({p["env"] for p in use})
+    envs = [ezo.Env(wl.box_obstacles(sc["envs"][e]["env_seed"], sc["envs"][e]["n_obs"])) for e in env_ids]
+    v1, v2, seg_env, pf = [], [], [], []
+    for p in use:
+        verts = np.asarray(p["path"])
+        first = len(v1)
+        for k in range(verts.shape[0] - 1):
+            v1.append(verts[k])
+            v2.append(verts[k + 1])
+            seg_env.append(env_ids.index(p["env"]))
+            pf.append(first)
+    B = len(v1)
+    seg_np = np.asarray([1000 + 700 * (g % 4) for g in range(B)], dtype=np.int32)
+    prm = ezo.Params.make(n_p=2000, seed=17)
+    res = {}
+    for seq in (1, 2):
+        bt = ezo.Batch(robot, envs, np.asarray(v1), np.asarray(v2), prm, seg_env=seg_env, seg_np=seg_np,
+                       path_first=pf)
+        bt.run_path(sequential=seq, mode=ezo.RUN_GRAPH if seq == 2 else ezo.RUN_HOST_LOOP)
+        res[seq] = [bt.segment(g) for g in range(B)]
+    for a, b in zip(res[1], res[2]):
+        assert a.status == b.status
+        np.testing.assert_array_equal(a.A, b.A)
