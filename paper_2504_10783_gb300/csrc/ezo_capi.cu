@@ -649,6 +649,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   const int n = robot->n;
   if (A0 && (m0 < 1 || !b0)) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: bad domain");
   std::vector<double> A0v, b0v;
+  const bool joint_box = (A0 == nullptr);
   if (A0) {
     A0v.assign(A0, A0 + (size_t)m0 * n);
     b0v.assign(b0, b0 + m0);
@@ -831,6 +832,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   v.path_first = b->d_path_first;
   v.max_path_len = b->max_path_len;
   v.graph_cond = 0;
+  v.box_rows = joint_box ? 2 * n : 0;
   // launch shapes: lanes per configuration from the work per round
   const int sms = sm_count();
   long long tot_np = 0, tot_s1 = 0;

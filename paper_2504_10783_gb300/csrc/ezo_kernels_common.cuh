@@ -28,6 +28,18 @@ struct SampleParams {
 // start x = v1 + u (v2 - v1); step s uses draws 1 + s W .. 1 + s W + W - 1
 // whose 4W words are uniforms u_0..: Gaussian pair i from (u_2i, u_2i+1) by
 // Box-Muller, step length from u_{2 ceil(n/2)}.
+// One Box-Muller pair from two 32-bit words: rho = sqrt(-2 ln u1) with u1 in
+// (0, 1], angle 2 pi u2 with u2 in [0, 1). The hardware approximations of ln
+// and of sin/cos (absolute error ~2^-21 on [-pi, pi]) are used; the angle is
+// shifted to pi (2 u2 - 1) in [-pi, pi), which negates sine and cosine.
+__device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& za, float& zb) {
+  const float rho = sqrtf(-2.f * __logf(u01_oc(w1)));
+  float sn, cs;
+  __sincosf(3.14159265358979f * fmaf(2.f, u01_co(w2), -1.f), &sn, &cs);
+  za = -rho * cs;
+  zb = -rho * sn;
+}
+
 // Shared-memory record of one polytope row for the sampler: a_r (NDOF floats,
 // zero-padded) then b_r, rounded up to whole float4s.
 template <int NDOF>
@@ -35,11 +47,33 @@ __host__ __device__ constexpr int hnr_row_stride() {
   return (NDOF + 4) & ~3;
 }
 
+// Chord bounds from the joint-box rows (rows j: +e_j <= hi_j, rows n + j:
+// -e_j <= -lo_j): the same arithmetic the generic row loop performs on those
+// rows (its dot products with e_j are exactly x_j and d_j), without the
+// dot products.
+template <int NDOF, int TS = 1>
+__device__ __forceinline__ void box_chord(const float* __restrict__ A32, int n, const float (&x)[NDOF],
+                                          const float (&d)[NDOF], float& t_lo, float& t_hi, int lw = 0) {
+  constexpr int RS = (NDOF + 4) & ~3;
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    if (j < n && (j % TS) == lw) {
+      const float hi = A32[j * RS + NDOF], nlo = A32[(n + j) * RS + NDOF];
+      const float s1 = hi - x[j], s2 = nlo - (-x[j]);
+      const float q1 = d[j], q2 = -d[j];
+      if (q1 > 0.f) t_hi = fminf(t_hi, __fdividef(s1, q1));
+      else if (q1 < 0.f) t_lo = fmaxf(t_lo, __fdividef(s1, q1));
+      if (q2 > 0.f) t_hi = fminf(t_hi, __fdividef(s2, q2));
+      else if (q2 < 0.f) t_lo = fmaxf(t_lo, __fdividef(s2, q2));
+    }
+  }
+}
+
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
                                          uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
-                                         float (&x)[NDOF]) {
+                                         float (&x)[NDOF], int box_rows = 0) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
   constexpr int RS = hnr_row_stride<NDOF>();
   const int npair = (n + 1) / 2;
@@ -66,11 +100,10 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
     float nrm2 = 0.f;
 #pragma unroll
     for (int i = 0; i < (NDOF + 1) / 2; ++i) {
-      const float rho = sqrtf(-2.f * logf(u01_oc(w[2 * i])));
-      float sn, cs;
-      sincospif(2.f * u01_co(w[2 * i + 1]), &sn, &cs);
-      if (2 * i < NDOF) d[2 * i] = (2 * i < n) ? rho * cs : 0.f;
-      if (2 * i + 1 < NDOF) d[2 * i + 1] = (2 * i + 1 < n) ? rho * sn : 0.f;
+      float za, zb;
+      box_muller(w[2 * i], w[2 * i + 1], za, zb);
+      if (2 * i < NDOF) d[2 * i] = (2 * i < n) ? za : 0.f;
+      if (2 * i + 1 < NDOF) d[2 * i + 1] = (2 * i + 1 < n) ? zb : 0.f;
     }
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) nrm2 = fmaf(d[j], d[j], nrm2);
@@ -83,7 +116,8 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    for (int r = 0; r < m; ++r) {
+    if (box_rows) box_chord<NDOF>(A32, n, x, d, t_lo, t_hi);
+    for (int r = box_rows; r < m; ++r) {
       // row r of A and b[r] in one padded record: RS / 4 broadcast loads
       const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
       float av[RS];
@@ -127,7 +161,7 @@ template <int NDOF, int TS>
 __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, int m, int n, const float* v1f,
                                                const float* ef, int n_mix, uint32_t key0, uint32_t key1,
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
-                                               float (&x)[NDOF]) {
+                                               float (&x)[NDOF], int box_rows = 0) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
   constexpr int RS = hnr_row_stride<NDOF>();
   constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
@@ -151,13 +185,7 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
       for (int h = 0; h < 2; ++h) {
         const int pair = 2 * b + h;  // words 4b + 2h, 4b + 2h + 1
         float za = 0.f, zb = 0.f;
-        if (pair < npair) {
-          const float rho = sqrtf(-2.f * logf(u01_oc(wv[2 * h])));
-          float sn, cs;
-          sincospif(2.f * u01_co(wv[2 * h + 1]), &sn, &cs);
-          za = rho * cs;
-          zb = rho * sn;
-        }
+        if (pair < npair) box_muller(wv[2 * h], wv[2 * h + 1], za, zb);
         z[4 * bl + 2 * h] = za;
         z[4 * bl + 2 * h + 1] = zb;
       }
@@ -183,7 +211,8 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    for (int r = lw; r < m; r += TS) {
+    if (box_rows) box_chord<NDOF, TS>(A32, n, x, d, t_lo, t_hi, lw);
+    for (int r = box_rows + lw; r < m; r += TS) {
       const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
       float av[RS];
 #pragma unroll

@@ -16,7 +16,9 @@ collision-freeness needs a collision checker, checked by the FP64 oracle only.
   and 256 seed paths of 1-40 segments built the same way (written only when
   ``--batched`` is given; slower).
 * table_cloud scene: 1024 spheres of r = 0.02 from a synthetic table point
-  cloud and a 64-segment seed path (``--stress``).
+  cloud and a 64-segment seed path that runs close to them (of 12
+  collision-free candidate steps the one with the least clearance)
+  (``--stress``).
 
 Run from the repository root:  python tests/golden/make_workloads.py
 """
@@ -143,7 +145,7 @@ def stress_scene(seed=31, n_seg=64):
     rng = np.random.default_rng(seed + 1)
     path = None
     while path is None:
-        path = random_path(robot, env, rng, n_seg)
+        path = random_path(robot, env, rng, n_seg, hug=12)
     return {"robot": "dh7", "cloud_seed": seed, "path": path.tolist()}
 
 
@@ -151,16 +153,18 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--batched", action="store_true")
     ap.add_argument("--stress", action="store_true")
+    ap.add_argument("--only-stress", action="store_true", help="rewrite only the table_cloud scene")
     args = ap.parse_args()
     data = {}
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    data["planar3"] = planar_scene()
-    data["dh7"] = dh7_scene()
+    if not args.only_stress:
+        data["planar3"] = planar_scene()
+        data["dh7"] = dh7_scene()
     if args.batched:
         data["dh7_batched"] = batched_scenes()
-    if args.stress:
+    if args.stress or args.only_stress:
         data["table_cloud"] = stress_scene()
     with open(OUT, "w") as f:
         json.dump(data, f, indent=1)
