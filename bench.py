@@ -271,6 +271,9 @@ def run_workload(args):
         t_batch = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
                             "batched")
         c_batch, k_batch = counts()
+        t_wave = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
+                           "in order, rounds in one graph")
+        c_wave, k_wave = counts()
         sur = ezo.Surrogate(robot, seed=7)
         t_train = _event_ms(torch, stream, lambda: sur.train(env, n_samples=1 << 23, epochs=4, batch=4096,
                                                              lr=1e-3, data_seed=13), "surrogate training")
@@ -278,12 +281,17 @@ def run_workload(args):
         t_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
                           "batched + surrogate")
         c_sur, k_sur = counts()
+        t_wave_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
+                               "in order + surrogate")
+        c_wave_sur, _ = counts()
         evals = sum(bt.surrogate_evals(g) for g in range(K))
         out.update({"segments": K, "obstacles": int(env_np.n_obs), "n_p": args.np_stress,
                     "plain_ms": t_plain, "plain_checks": c_plain, "plain_kept": k_plain,
                     "batched_ms": t_batch, "batched_checks": c_batch, "batched_kept": k_batch,
+                    "in_order_graph_ms": t_wave, "in_order_graph_checks": c_wave,
                     "surrogate_train_ms": t_train, "batched_surrogate_ms": t_sur, "batched_surrogate_checks": c_sur,
-                    "surrogate_evals": int(evals), "batched_surrogate_kept": k_sur})
+                    "surrogate_evals": int(evals), "batched_surrogate_kept": k_sur,
+                    "in_order_surrogate_ms": t_wave_sur, "in_order_surrogate_checks": c_wave_sur})
     print(json.dumps(out))
 
 
