@@ -95,6 +95,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------- multi-rank --
+def aggregate_ranks(ms: float, units: float, dist=None):
+    """Whole-job timing over replicas: every rank inflates its own path, the
+    job time is the slowest rank's and the units add up (weak scaling). With
+    no process group the inputs are returned unchanged."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, units
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # --------------------------------------------------------------- oracle legs --
 def oracle_sample(seconds: float, seg_list=None):
     """Runs the FP64 oracle on segments of the bench path until `seconds`
@@ -471,11 +487,8 @@ def main():
         sflops += bt.sample_flops(g)
         kept += bt.segment(g).status != ezo.SEG_SKIPPED
     checks_per_step = samp + bisc
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * checks_per_step * args.steps / (ms / 1e3)
+    ms, units = aggregate_ranks(ms, checks_per_step * args.steps, dist)
+    value = units / (ms / 1e3)
 
     # ---- roofline of the dominant kernel (FP32 ALU bound) ----
     flops_cfg = ezo.check_flops(robot, env)

@@ -77,81 +77,85 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 // 64 x 64 block tile, 4 warps of 32 x 32 (2 m16 x 4 n8 mma tiles each), K in
 // steps of 32 staged through shared memory (rows padded by 8 BF16 so the
 // eight 16-byte rows of an ldmatrix hit distinct banks).
+// Persistent over M tiles: block (x, y) takes M tiles x, x + gridDim.x, ..
+// below the row count (device-side when m_dev is set, so a graph launched
+// with a fixed grid does no work for absent rows).
 template <int EPI>
 __global__ void __launch_bounds__(128) k_gemm_nt(GemmArgs g) {
   __shared__ __align__(16) __nv_bfloat16 As[kBM][kBK + kPad];
   __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kBK + kPad];
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
   const int m_lim = g.m_dev ? min(g.M, *g.m_dev) : g.M;
-  if (m0 >= m_lim) return;
+  const int n0 = blockIdx.y * kBN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  for (int k0 = 0; k0 < g.K; k0 += kBK) {
-    // 64 rows x 32 BF16 = 64 x 4 chunks of 16 bytes per operand, 2 per thread
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const int c = threadIdx.x + it * 128;
-      const int r = c >> 2, q = (c & 3) * 8;
-      const int gm = m0 + r, gn = n0 + r;
-      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-      if (gm < m_lim) va = *reinterpret_cast<const uint4*>(g.A + (long long)gm * g.lda + k0 + q);
-      if (gn < g.N) vb = *reinterpret_cast<const uint4*>(g.B + (long long)gn * g.ldb + k0 + q);
-      *reinterpret_cast<uint4*>(&As[r][q]) = va;
-      *reinterpret_cast<uint4*>(&Bs[r][q]) = vb;
+  for (int m0 = blockIdx.x * kBM; m0 < m_lim; m0 += gridDim.x * kBM) {
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+  #pragma unroll
+    for (int i = 0; i < 2; ++i)
+  #pragma unroll
+      for (int j = 0; j < 4; ++j)
+  #pragma unroll
+        for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int k0 = 0; k0 < g.K; k0 += kBK) {
+      // 64 rows x 32 BF16 = 64 x 4 chunks of 16 bytes per operand, 2 per thread
+  #pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int c = threadIdx.x + it * 128;
+        const int r = c >> 2, q = (c & 3) * 8;
+        const int gm = m0 + r, gn = n0 + r;
+        uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+        if (gm < m_lim) va = *reinterpret_cast<const uint4*>(g.A + (long long)gm * g.lda + k0 + q);
+        if (gn < g.N) vb = *reinterpret_cast<const uint4*>(g.B + (long long)gn * g.ldb + k0 + q);
+        *reinterpret_cast<uint4*>(&As[r][q]) = va;
+        *reinterpret_cast<uint4*>(&Bs[r][q]) = vb;
+      }
+      __syncthreads();
+  #pragma unroll
+      for (int kk = 0; kk < kBK; kk += 16) {
+        uint32_t af[2][4];
+  #pragma unroll
+        for (int i = 0; i < 2; ++i) ldmatrix_x4(af[i], &As[wm + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+        uint32_t bf[2][4];
+  #pragma unroll
+        for (int j = 0; j < 2; ++j)
+          ldmatrix_x4(bf[j], &Bs[wn + j * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
+  #pragma unroll
+        for (int i = 0; i < 2; ++i)
+  #pragma unroll
+          for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j >> 1][(j & 1) * 2], bf[j >> 1][(j & 1) * 2 + 1]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t af[2][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) ldmatrix_x4(af[i], &As[wm + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-      uint32_t bf[2][4];
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-        ldmatrix_x4(bf[j], &Bs[wn + j * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j >> 1][(j & 1) * 2], bf[j >> 1][(j & 1) * 2 + 1]);
-    }
-    __syncthreads();
-  }
-  // epilogue: fragment element e of tile (i, j) is row wm+16i+lane/4 (+8 for
-  // e >= 2), column wn+8j+2(lane%4) (+1 for odd e)
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = m0 + wm + i * 16 + (lane >> 2) + (e >= 2 ? 8 : 0);
-        const int c = n0 + wn + j * 8 + (lane & 3) * 2 + (e & 1);
-        if (r >= m_lim || c >= g.N) continue;
-        const float v = acc[i][j][e];
-        if (EPI == EPI_F32) {
-          g.C[(long long)r * g.ldc + c] = v;
-        } else if (EPI == EPI_BIAS_SILU || EPI == EPI_BIAS_SILU_H) {
-          const float z = v + g.bias[c];
-          const __nv_bfloat16 h = __float2bfloat16(silu(z));
-          g.H[(long long)r * g.N + c] = h;
-          if (EPI == EPI_BIAS_SILU) {
-            g.Z[(long long)r * g.N + c] = z;
+    // epilogue: fragment element e of tile (i, j) is row wm+16i+lane/4 (+8 for
+    // e >= 2), column wn+8j+2(lane%4) (+1 for odd e)
+  #pragma unroll
+    for (int i = 0; i < 2; ++i)
+  #pragma unroll
+      for (int j = 0; j < 4; ++j)
+  #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = m0 + wm + i * 16 + (lane >> 2) + (e >= 2 ? 8 : 0);
+          const int c = n0 + wn + j * 8 + (lane & 3) * 2 + (e & 1);
+          if (r >= m_lim || c >= g.N) continue;
+          const float v = acc[i][j][e];
+          if (EPI == EPI_F32) {
+            g.C[(long long)r * g.ldc + c] = v;
+          } else if (EPI == EPI_BIAS_SILU || EPI == EPI_BIAS_SILU_H) {
+            const float z = v + g.bias[c];
+            const __nv_bfloat16 h = __float2bfloat16(silu(z));
+            g.H[(long long)r * g.N + c] = h;
+            if (EPI == EPI_BIAS_SILU) {
+              g.Z[(long long)r * g.N + c] = z;
+              g.Ht[(long long)c * g.ldt + r] = h;
+            }
+          } else {
+            const float d = v * dsilu(g.Z[(long long)r * g.N + c]);
+            const __nv_bfloat16 h = __float2bfloat16(d);
+            g.H[(long long)r * g.N + c] = h;
             g.Ht[(long long)c * g.ldt + r] = h;
           }
-        } else {
-          const float d = v * dsilu(g.Z[(long long)r * g.N + c]);
-          const __nv_bfloat16 h = __float2bfloat16(d);
-          g.H[(long long)r * g.N + c] = h;
-          g.Ht[(long long)c * g.ldt + r] = h;
         }
-      }
+  }
 }
 
 // ------------------------------------------------------------ small kernels --
@@ -349,7 +353,16 @@ namespace {
 using namespace ezo;
 
 cudaError_t gemm(int epi, const GemmArgs& a, cudaStream_t s) {
-  dim3 grid((a.M + kBM - 1) / kBM, (a.N + kBN - 1) / kBN);  // M tiles on x (no 65535 limit)
+  // M tiles on x, at most a few waves of blocks (the kernel loops over the rest)
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int n_tiles = (a.N + kBN - 1) / kBN;
+  const long long m_tiles = (a.M + kBM - 1) / kBM;
+  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(m_tiles, (long long)sms * 16 / n_tiles + 1)), n_tiles);
   switch (epi) {
     case EPI_F32: k_gemm_nt<EPI_F32><<<grid, 128, 0, s>>>(a); break;
     case EPI_BIAS_SILU: k_gemm_nt<EPI_BIAS_SILU><<<grid, 128, 0, s>>>(a); break;
