@@ -437,7 +437,7 @@ struct ezo_batch {
   double *d_A0 = nullptr, *d_b0 = nullptr;  // initial polytopes
   std::vector<double> v1h, v2h;
   BatchView view{};
-  int T_check = 1, T_bisect = 4, split_below = 0;
+  int T_check = 1, T_bisect = 4, split_below = 0, T_spec = 0;
   int grid_sample = 1, grid_check = 1, grid_bisect = 1;
   // graph mode
   cudaGraph_t graph = nullptr;
@@ -493,7 +493,7 @@ namespace {
 cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
   if (!b->sur) {
     b->view.bis_mode = 0;
-    return launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
+    return launch_round_bisect(b->view, b->view.bis_spec ? b->T_spec : b->T_bisect, b->grid_bisect, s);
   }
   const int g = (int)std::max<long long>(1, std::min<long long>((b->sur_rows + 255) / 256, 4096));
   cudaError_t e = launch_sbis_init(b->view, g, s);
@@ -850,12 +850,17 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   // candidates of a round, so it is latency bound: eight lanes per candidate
   // unless a round can hold enough candidates to fill the GPU at fewer lanes.
   b->T_bisect = tot_np >= (1ll << 20) ? ezo_internal_tuned_lanes(robot, envs[e_big], tot_np / 4, nullptr) : 8;
+  // small rounds: three bisection levels per pass with 7 groups of 4 lanes
+  if (tot_np < (1ll << 20)) {
+    b->view.bis_spec = 1;
+    b->T_spec = 4;
+  }
   // walks share eight lanes in rounds with fewer walks than one warp per
   // scheduler would hold at one lane per walk
   b->split_below = (sms * 4 * 32) / kTile;
   b->grid_sample = std::max(1, std::min(b->max_sample_tiles * 8, sms * 16));
   b->grid_check = std::max(1, std::min(b->max_sample_tiles * b->T_check, sms * 16));
-  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * b->T_bisect, sms * 16));
+  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * std::max(b->T_bisect, 32), sms * 16));
   *out = b;
   g_err.clear();
   return EZO_OK;
