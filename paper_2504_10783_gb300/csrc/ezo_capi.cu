@@ -437,7 +437,7 @@ struct ezo_batch {
   double *d_A0 = nullptr, *d_b0 = nullptr;  // initial polytopes
   std::vector<double> v1h, v2h;
   BatchView view{};
-  int T_check = 1, T_bisect = 4, split_below = 0, T_spec = 0;
+  int T_check = 1, T_bisect = 4, split_below = 0;
   int grid_sample = 1, grid_check = 1, grid_bisect = 1;
   // graph mode
   cudaGraph_t graph = nullptr;
@@ -493,7 +493,7 @@ namespace {
 cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
   if (!b->sur) {
     b->view.bis_mode = 0;
-    return launch_round_bisect(b->view, b->view.bis_spec ? b->T_spec : b->T_bisect, b->grid_bisect, s);
+    return launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
   }
   const int g = (int)std::max<long long>(1, std::min<long long>((b->sur_rows + 255) / 256, 4096));
   cudaError_t e = launch_sbis_init(b->view, g, s);
@@ -649,7 +649,6 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   const int n = robot->n;
   if (A0 && (m0 < 1 || !b0)) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: bad domain");
   std::vector<double> A0v, b0v;
-  const bool joint_box = (A0 == nullptr);
   if (A0) {
     A0v.assign(A0, A0 + (size_t)m0 * n);
     b0v.assign(b0, b0 + m0);
@@ -832,7 +831,6 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   v.path_first = b->d_path_first;
   v.max_path_len = b->max_path_len;
   v.graph_cond = 0;
-  v.box_rows = joint_box ? 2 * n : 0;
   // launch shapes: lanes per configuration from the work per round
   const int sms = sm_count();
   long long tot_np = 0, tot_s1 = 0;
@@ -850,17 +848,12 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   // candidates of a round, so it is latency bound: eight lanes per candidate
   // unless a round can hold enough candidates to fill the GPU at fewer lanes.
   b->T_bisect = tot_np >= (1ll << 20) ? ezo_internal_tuned_lanes(robot, envs[e_big], tot_np / 4, nullptr) : 8;
-  // small rounds: three bisection levels per pass with 7 groups of 4 lanes
-  if (tot_np < (1ll << 20)) {
-    b->view.bis_spec = 1;
-    b->T_spec = 4;
-  }
   // walks share eight lanes in rounds with fewer walks than one warp per
   // scheduler would hold at one lane per walk
   b->split_below = (sms * 4 * 32) / kTile;
   b->grid_sample = std::max(1, std::min(b->max_sample_tiles * 8, sms * 16));
   b->grid_check = std::max(1, std::min(b->max_sample_tiles * b->T_check, sms * 16));
-  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * std::max(b->T_bisect, 32), sms * 16));
+  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * b->T_bisect, sms * 16));
   *out = b;
   g_err.clear();
   return EZO_OK;

@@ -110,8 +110,6 @@ struct BatchView {
   uint32_t* s_bits;  // [row] surrogate decisions
   uint8_t* s_ok;     // [row] 1 when the surrogate end point was verified in collision
   int* s_rows;       // device row count of this round (n_bisect_tiles * kTile)
-  int box_rows;      // 2n when rows 0..2n-1 are the joint box (+e_j <= hi_j, then -e_j <= -lo_j), else 0
-  int bis_spec;      // exact bisection checks three levels per pass (7 lane groups per candidate)
 };
 
 // Launchers (ezo_kernels.cu). T = lanes per configuration.

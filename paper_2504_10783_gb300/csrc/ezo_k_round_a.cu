@@ -89,12 +89,11 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
   float x[NDOF];
   if (TSS == 1) {
     if (i >= st.n_samples) return;
-    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x,
-                   v.box_rows);
+    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
   } else {
     const int ic = i < st.n_samples ? i : tile.y;
     hnr_walk_split<NDOF, TSS>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)ic, p.round_k,
-                              p.stream, lw, x, v.box_rows);
+                              p.stream, lw, x);
     if (i >= st.n_samples || lw != 0) return;
   }
 #pragma unroll

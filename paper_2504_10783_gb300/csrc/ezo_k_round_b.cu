@@ -140,134 +140,6 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
   }
 }
 
-// Exact bisection with three levels per pass: the 7 dyadic points
-// lo + (hi - lo) k / 8 (k = 1..7) of a candidate's bracket are checked at
-// once by 7 groups of T lanes, then the three decisions are read off in the
-// order sequential bisection takes them (1/2, then 1/4 or 3/4, then an odd
-// eighth). Every point equals the sequential midpoint exactly (dyadic
-// fractions in FP64), so decisions, bits and c* are those of k_round_bisect;
-// the dependent chain is ceil(N_b / 3) checks instead of N_b. A warp holds
-// 32 / (7 T) candidates; lanes past them evaluate a copy and are ignored.
-template <int NDOF, int T>
-__global__ void __launch_bounds__(128) k_round_bisect_spec(BatchView v, int max_obs_pad) {
-  extern __shared__ float4 smem4[];
-  __shared__ RobotSmem rs;
-  __shared__ int cur_env;
-  constexpr int GL = 7 * T;       // lanes per candidate
-  constexpr int CPW = 32 / GL;    // candidates per warp
-  constexpr int CPB = 4 * CPW;    // candidates per 128-thread block pass
-  constexpr int PASSES = kTile / CPB;
-  static_assert(CPW >= 1 && kTile % CPB == 0, "lane layout");
-  const RobotDev* robot = v.robot;
-  const int nsp = robot->n_spheres_pad;
-  const int groups = blockDim.x / T;
-  float4* sph_s = smem4;
-  float4* obs_s = sph_s + nsp;
-  float4* cen_all = obs_s + max_obs_pad;
-  float* nhw_s = reinterpret_cast<float*>(cen_all + groups * (nsp + 1));
-  stage_robot(rs, sph_s, robot);
-  if (threadIdx.x == 0) cur_env = -1;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cw = min(lane / GL, CPW - 1);  // candidate of this lane within the warp
-  const bool real = lane < CPW * GL;
-  const int gk = real ? (lane % GL) / T : 0;  // point k = gk + 1 of the level
-  const int lg = lane % T;
-  float4* cen = cen_all + (threadIdx.x / T) * (nsp + 1);
-  const int n = v.n;
-  const int n_tiles = v.summary->n_bisect_tiles;
-  for (int u = blockIdx.x; u < n_tiles * PASSES; u += gridDim.x) {
-    const int2 tile = v.bisect_tiles[u / PASSES];
-    const int g = tile.x;
-    const SegState& st = v.st[g];
-    const EnvDevFull& ef = v.envs[st.env];
-    if (st.env != cur_env) {
-      __syncthreads();
-      stage_env(obs_s, nhw_s, ef.e);
-      if (threadIdx.x == 0) cur_env = st.env;
-      __syncthreads();
-    }
-    const double* v1 = v.v1 + (long long)g * n;
-    const double* v2 = v.v2 + (long long)g * n;
-    const float* S = v.S + (long long)n * st.sample_off;
-    const int np = st.n_p;
-    const int c = tile.y + (u % PASSES) * CPB + warp * CPW + cw;
-    const bool valid = real && c < st.n_cand;
-    const int cc = c < st.n_cand ? c : tile.y;
-    const int si = v.cand_idx[st.cand_off + cc];
-    double cs[NDOF], p[NDOF], dv[NDOF];
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
-    project_fp64<NDOF>(cs, v1, v2, n, p);
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) dv[j] = (j < n) ? cs[j] - p[j] : 0.0;
-    double lo = 0.0, hi = 1.0;
-    uint32_t bits = 0u;
-    for (int s0 = 0; s0 < v.n_b; s0 += 3) {
-      const int L = min(3, v.n_b - s0);
-      const int npts = (1 << L) - 1;
-      const double f = lo + (hi - lo) * (double)(min(gk, npts - 1) + 1) / (double)(1 << L);
-      float qq[NDOF];
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) qq[j] = (float)fma(f, dv[j], p[j]);
-      const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
-                                              robot->self_pairs, robot->self_rr, ef.E, cen, lg);
-      const unsigned bal = __ballot_sync(0xffffffffu, hit && lg == 0);
-      // result of point k (1..npts) of this lane's candidate
-      int klo = 0, khi = 1 << L;
-      for (int step = 0; step < L; ++step) {
-        const int km = (klo + khi) >> 1;
-        const bool r = (bal >> (cw * GL + (km - 1) * T)) & 1u;
-        if (r) {
-          khi = km;
-          bits |= 1u << (s0 + step);
-        } else {
-          klo = km;
-        }
-      }
-      const double w = (hi - lo) / (double)(1 << L);
-      const double nlo = lo + w * klo, nhi = lo + w * khi;
-      lo = nlo;
-      hi = nhi;
-    }
-    if (valid && gk == 0 && lg == 0) {
-      double cst[NDOF], ps[NDOF];
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, dv[j], p[j]) : 0.0;
-      project_fp64<NDOF>(cst, v1, v2, n, ps);
-      double d2 = 0.0;
-      float cn2 = 0.f;
-      const long long co = st.cand_off;
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) {
-        if (j < n) {
-          const double e = cst[j] - ps[j];
-          d2 = fma(e, e, d2);
-          v.cstar[(long long)n * co + (long long)j * np + c] = cst[j];
-          const float f32 = (float)cst[j];
-          v.c32[(long long)n * co + (long long)j * np + c] = f32;
-          cn2 = fmaf(f32, f32, cn2);
-        }
-      }
-      const double dist = sqrt(d2);
-      v.dist[co + c] = dist;
-      v.cnorm[co + c] = sqrtf(cn2);
-      v.bits[co + c] = bits;
-      const double inv = dist > 0.0 ? 1.0 / dist : 0.0;
-      double bval = 0.0;
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) {
-        if (j < n) {
-          const double a = (cst[j] - ps[j]) * inv;
-          v.ga[(long long)n * co + (long long)j * np + c] = a;
-          bval = fma(a, cst[j], bval);
-        }
-      }
-      v.gb[co + c] = bval;
-    }
-  }
-}
-
 // Greedy placement: repeatedly take the closest surviving candidate (ties by
 // sample index), place a_i^T x <= b_i - Delta_i, discard candidates with
 // a_i^T c_j > b_i - Delta_i; at most N_f planes. One block per segment.
@@ -501,28 +373,6 @@ __global__ void k_containment(BatchView v, uint8_t* contained, double tol) {
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T);
-  if (v.bis_mode == 0 && v.bis_spec && T <= 4) {
-    // three levels per pass (7 groups of T lanes per candidate)
-    EZO_DISPATCH_NDOF(v.n, {
-      if (T == 4) {
-        auto kern = k_round_bisect_spec<ND, 4>;
-        err = set_smem(kern, smem);
-        if (err != cudaSuccess) return err;
-        kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
-      } else if (T == 2) {
-        auto kern = k_round_bisect_spec<ND, 2>;
-        err = set_smem(kern, smem);
-        if (err != cudaSuccess) return err;
-        kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
-      } else {
-        auto kern = k_round_bisect_spec<ND, 1>;
-        err = set_smem(kern, smem);
-        if (err != cudaSuccess) return err;
-        kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
-      }
-    });
-    return cudaGetLastError();
-  }
   EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
     auto kern = k_round_bisect<ND, TT>;
     err = set_smem(kern, smem);

@@ -47,33 +47,11 @@ __host__ __device__ constexpr int hnr_row_stride() {
   return (NDOF + 4) & ~3;
 }
 
-// Chord bounds from the joint-box rows (rows j: +e_j <= hi_j, rows n + j:
-// -e_j <= -lo_j): the same arithmetic the generic row loop performs on those
-// rows (its dot products with e_j are exactly x_j and d_j), without the
-// dot products.
-template <int NDOF, int TS = 1>
-__device__ __forceinline__ void box_chord(const float* __restrict__ A32, int n, const float (&x)[NDOF],
-                                          const float (&d)[NDOF], float& t_lo, float& t_hi, int lw = 0) {
-  constexpr int RS = (NDOF + 4) & ~3;
-#pragma unroll
-  for (int j = 0; j < NDOF; ++j) {
-    if (j < n && (j % TS) == lw) {
-      const float hi = A32[j * RS + NDOF], nlo = A32[(n + j) * RS + NDOF];
-      const float s1 = hi - x[j], s2 = nlo - (-x[j]);
-      const float q1 = d[j], q2 = -d[j];
-      if (q1 > 0.f) t_hi = fminf(t_hi, __fdividef(s1, q1));
-      else if (q1 < 0.f) t_lo = fmaxf(t_lo, __fdividef(s1, q1));
-      if (q2 > 0.f) t_hi = fminf(t_hi, __fdividef(s2, q2));
-      else if (q2 < 0.f) t_lo = fmaxf(t_lo, __fdividef(s2, q2));
-    }
-  }
-}
-
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
                                          uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
-                                         float (&x)[NDOF], int box_rows = 0) {
+                                         float (&x)[NDOF]) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
   constexpr int RS = hnr_row_stride<NDOF>();
   const int npair = (n + 1) / 2;
@@ -116,8 +94,7 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    if (box_rows) box_chord<NDOF>(A32, n, x, d, t_lo, t_hi);
-    for (int r = box_rows; r < m; ++r) {
+    for (int r = 0; r < m; ++r) {
       // row r of A and b[r] in one padded record: RS / 4 broadcast loads
       const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
       float av[RS];
@@ -161,7 +138,7 @@ template <int NDOF, int TS>
 __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, int m, int n, const float* v1f,
                                                const float* ef, int n_mix, uint32_t key0, uint32_t key1,
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
-                                               float (&x)[NDOF], int box_rows = 0) {
+                                               float (&x)[NDOF]) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
   constexpr int RS = hnr_row_stride<NDOF>();
   constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
@@ -211,8 +188,7 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    if (box_rows) box_chord<NDOF, TS>(A32, n, x, d, t_lo, t_hi, lw);
-    for (int r = box_rows + lw; r < m; r += TS) {
+    for (int r = lw; r < m; r += TS) {
       const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
       float av[RS];
 #pragma unroll

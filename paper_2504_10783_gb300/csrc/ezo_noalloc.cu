@@ -241,7 +241,6 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   v.path_first = d_pf;
   v.max_path_len = 1;
   v.graph_cond = 0;
-  v.box_rows = 2 * n;
 
   int dev = 0, sms = 1;
   NA_CUDA(cudaGetDevice(&dev));
