@@ -21,7 +21,11 @@ by step in float64, written for a reader to check against the paper:
   Sec. IV-B, IV-C;
 * greedy, sorted hyperplane placement with at most N_f faces per iteration:
   Sec. IV-B and the parameter tables of the appendix;
-* path inflation with the containment skip: Sec. VI-A.
+* path inflation with the containment skip: Sec. VI-A;
+* recovery from detected collisions: fine discretisation of a path and its
+  collision check, set editing with the last steps of Algorithm 1 on given
+  collisions that lie in the set, and the coverage test of the seed path:
+  Sec. VI-B (step 0.1 rad from the appendix).
 
 Where the paper is silent the oracle takes these readings (each one is also a
 parameter or a documented choice of the CUDA library):
@@ -38,6 +42,9 @@ parameter or a documented choice of the CUDA library):
   discarded when a^T c_j > b - Delta for a row added this round;
 * a segment L_k is skipped when both its endpoints satisfy A x <= b + 1e-9 for
   an earlier polytope.
+* a path edge is cut into N_k = max(1, ceil(|e|_2 / step)) equal pieces and
+  checked at all N_k + 1 points; a set is edited with the given collisions
+  that satisfy A c <= b + 1e-9, the first N_p by index, without a test.
 
 Parity status: every function here is pinned by tests under ``tests/`` against
 closed forms, invariants, brute force or published vectors, except the
@@ -522,4 +529,97 @@ def inflate_path(robot, env, verts, prm: Params, A0=None, b0=None, stream_base: 
         out.append((k, res))
         if res.status == STATUS_SEGMENT_IN_COLLISION:
             break
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Recovering from detected collisions (Sec. VI-B): a path or trajectory is
+# checked at fine steps; the collisions that lie in a set are excluded from
+# it with the last steps of Algorithm 1 (bisection, ordering, placement);
+# then every segment of the seed path must still lie in some set, and a
+# segment that does not is inflated again.
+# ---------------------------------------------------------------------------
+def path_points(verts, step: float):
+    """Fine discretisation of a piecewise-linear path (Sec. VI-B; the
+    appendix uses steps of 0.1 rad). Edge k, from v_k to v_{k+1}, is cut into
+    N_k = max(1, ceil(|v_{k+1} - v_k|_2 / step)) equal pieces and its N_k + 1
+    points v_k + (i / N_k)(v_{k+1} - v_k), i = 0..N_k, are checked (both
+    ends, so a shared vertex is checked by both of its edges). |e|_2 is the
+    square root of e_0^2 + e_1^2 + .. summed in that order.
+    Returns (points [N, n], edge index of each point [N])."""
+    verts = np.atleast_2d(np.asarray(verts, dtype=np.float64))
+    pts, eid = [], []
+    for k in range(verts.shape[0] - 1):
+        e = verts[k + 1] - verts[k]
+        ss = 0.0
+        for x in e:
+            ss += float(x) * float(x)
+        nk = max(1, int(math.ceil(math.sqrt(ss) / step)))
+        for i in range(nk + 1):
+            pts.append(verts[k] + (i / nk) * e)
+            eid.append(k)
+    n = verts.shape[1]
+    return np.asarray(pts, dtype=np.float64).reshape(-1, n), np.asarray(eid, dtype=np.int64)
+
+
+def check_path(robot, env, verts, step: float):
+    """Labels of the points of path_points and, per edge, whether any of its
+    points collides. Returns (edge flags [K] bool, point labels [N] bool,
+    points [N, n], edge index [N])."""
+    P, eid = path_points(verts, step)
+    lab = in_collision(robot, env, P) if P.shape[0] else np.zeros(0, dtype=bool)
+    K = max(0, np.atleast_2d(verts).shape[0] - 1)
+    edge = np.zeros(K, dtype=bool)
+    for i in range(P.shape[0]):
+        if lab[i]:
+            edge[eid[i]] = True
+    return edge, lab, P, eid
+
+
+def points_inside(A, b, X, tol: float = 1e-9) -> np.ndarray:
+    """Rows of X that satisfy A x <= b + tol."""
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    A = np.asarray(A, dtype=np.float64)
+    if A.shape[0] == 0:
+        return np.ones(X.shape[0], dtype=bool)
+    return np.all(X @ A.T <= np.asarray(b)[None, :] + tol, axis=1)
+
+
+@dataclass
+class EditResult:
+    A: np.ndarray
+    b: np.ndarray
+    inside: np.ndarray  # [N] bool, the given configuration lies in P
+    labels: np.ndarray  # [N] bool, in collision
+    cand_index: np.ndarray  # indices of the configurations that were bisected
+    bisect: BisectResult
+    place: PlaceResult
+
+
+def edit_polytope(robot, env, A, b, v1, v2, cfgs, prm: Params, follow=None, band: float = 0.0) -> EditResult:
+    """Sec. VI-B set editing: the given configurations that lie in P
+    (A c <= b + 1e-9) and collide form S_col; the first N_p of them by index
+    are bisected toward the seed segment L = [v1, v2] and ordered, and
+    hyperplanes are placed exactly as in a round of Algorithm 1 (no sampling
+    and no test). The new rows are appended to P."""
+    X = np.atleast_2d(np.asarray(cfgs, dtype=np.float64))
+    inside = points_inside(A, b, X)
+    lab = in_collision(robot, env, X) if X.shape[0] else np.zeros(0, dtype=bool)
+    idx = np.nonzero(inside & lab)[0][: prm.n_p]
+    br = bisect(robot, env, X[idx], v1, v2, prm.n_b, follow=follow, band=band)
+    pl = place_hyperplanes(br.c_star, idx, v1, v2, prm.n_f, prm.step_back_max, prm.t_col)
+    A2 = np.vstack([np.asarray(A, dtype=np.float64), pl.rows_a])
+    b2 = np.concatenate([np.asarray(b, dtype=np.float64), pl.rows_b])
+    return EditResult(A2, b2, inside, lab, idx, br, pl)
+
+
+def path_coverage(polys, verts, tol: float = 1e-9) -> np.ndarray:
+    """Sec. VI-B: segment k of the seed path is covered when both of its
+    endpoints lie in one of the polytopes (A x <= b + tol), hence the whole
+    segment, by convexity. ``polys`` is a list of (A, b). Returns [K] bool."""
+    verts = np.atleast_2d(np.asarray(verts, dtype=np.float64))
+    K = verts.shape[0] - 1
+    out = np.zeros(K, dtype=bool)
+    for k in range(K):
+        out[k] = any(segment_contained(A, b, verts[k], verts[k + 1], tol) for A, b in polys)
     return out
