@@ -31,6 +31,11 @@ WORKLOAD = ("7-DOF DH arm (d=[0.34,0,0.40,0,0.40,0,0.126], 40 spheres r 0.04-0.0
             "eps=delta=0.05, tau=0.5, N_p=1e4, N_f=10, N_ms=60, N_b=10, Delta_max=0.01, N_it=50")
 PARAMS = dict(eps=0.05, delta=0.05, tau=0.5, step_back_max=0.01, t_col=1e-3, n_p=10000, n_f=10, n_b=10, n_mix=60,
               n_it_max=50, seed=1)
+N_SEEDS = 20
+# DRAM bytes per launch of the round kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum, ncu, this workload); None where not captured for the
+# current kernel
+TRAFFIC = {}
 KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
 
 
@@ -402,6 +407,8 @@ def main():
     ap.add_argument("--seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed path steps and the kernel pass (no plain, surrogate or checker legs)")
     ap.add_argument("--workload", default="path", choices=["path", "batched", "stress"])
     ap.add_argument("--paths", type=int, default=256, help="batched: number of seed paths")
     ap.add_argument("--np-stress", type=int, default=1_000_000, help="stress: samples per round and segment")
@@ -438,79 +445,108 @@ def main():
     rd, env_np, path = load_scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
     K = path.shape[0] - 1
-    prm = ezo.Params.make(**PARAMS)
     mode = ezo.RUN_GRAPH if args.mode == "graph" else ezo.RUN_HOST_LOOP
     streams = np.arange(K, dtype=np.uint32) + 1000 * rank  # each rank inflates its own random draw
-    bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm, seg_stream=streams, path_first=np.zeros(K, np.int32))
+    # one batch per Philox seed 1..N_SEEDS; step i inflates the path with seed 1 + i % N_SEEDS
+    batches = [ezo.Batch(robot, [env], path[:-1], path[1:], ezo.Params.make(**dict(PARAMS, seed=sd)),
+                         seg_stream=streams, path_first=np.zeros(K, np.int32)) for sd in range(1, N_SEEDS + 1)]
+    bt = batches[0]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
-    def step():
-        bt.reset()
-        bt.run_path(sequential=False, mode=mode)
+    def step(i, run_mode=mode):
+        b = batches[i % N_SEEDS]
+        b.reset()
+        b.run_path(sequential=False, mode=run_mode)
 
-    for _ in range(max(3, args.warmup)):
-        step()
+    for i in range(N_SEEDS):  # every batch once (graph instantiation), then the warm-up steps
+        step(i)
+    for i in range(max(3, args.warmup)):
+        step(i)
     torch.cuda.synchronize()
 
+    # per-seed work: exact checks (sample labels, bisection midpoints), FP32
+    # FLOPs of the walks, kept segments and rounds (the same on every run)
+    flops_cfg = ezo.check_flops(robot, env)
+    work = []
+    for b in batches:
+        samp = bisc = sflops = kept = 0
+        for g in range(K):
+            x, y2 = b.check_split(g)
+            samp += x
+            bisc += y2
+            sflops += b.sample_flops(g)
+            kept += b.segment(g).status != ezo.SEG_SKIPPED
+        work.append({"sample_checks": samp, "bisection_checks": bisc, "sample_flops": sflops, "kept": kept,
+                     "rounds": b.summary()["rounds"]})
+
     # ---- timed region: device-resident inputs, L2 flushed between steps ----
-    ezo.profile_enable(mode == ezo.RUN_HOST_LOOP)
-    ezo.profile_reset()
     clk = ClockSampler(local)
     clk.start()
     barrier()
     torch.cuda.synchronize()
     times = []
     launches = 0
-    for _ in range(args.steps):
+    units = 0
+    for i in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        step(i)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-        launches += 7 * bt.summary()["rounds"] + 1
+        w = work[i % N_SEEDS]
+        units += w["sample_checks"] + w["bisection_checks"]
+        launches += 7 * w["rounds"] + 1
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    prof = ezo.profile_read()
-    ezo.profile_enable(False)
     ms = float(np.sum(times))
-    samp = bisc = sflops = 0
-    kept = 0
-    for g in range(K):
-        a, b_ = bt.check_split(g)
-        samp += a
-        bisc += b_
-        sflops += bt.sample_flops(g)
-        kept += bt.segment(g).status != ezo.SEG_SKIPPED
-    checks_per_step = samp + bisc
-    ms, units = aggregate_ranks(ms, checks_per_step * args.steps, dist)
-    value = units / (ms / 1e3)
+    ms, units_all = aggregate_ranks(ms, units, dist)
+    value = units_all / (ms / 1e3)
 
-    # ---- roofline of the dominant kernel (FP32 ALU bound) ----
-    flops_cfg = ezo.check_flops(robot, env)
+    # ---- roofline of the dominant kernel (FP32 ALU bound): the same steps
+    #      in host-loop mode with CUDA events around every kernel launch on
+    #      the launching stream (a graph launch cannot be split by events) ----
     props = torch.cuda.get_device_properties(local)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA
-    roofline = None
-    if mode == ezo.RUN_HOST_LOOP and prof["bisect"][1] > 0:
-        work = {"check": samp * flops_cfg * args.steps, "bisect": bisc * flops_cfg * args.steps,
-                "sample": sflops * args.steps}
-        dom = max(("check", "bisect", "sample"), key=lambda k: prof[k][0])
-        ach = work[dom] / (prof[dom][0] / 1e3) / 1e12
-        roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
-                    "per_launch_ms": prof[dom][0] / prof[dom][1],
-                    "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
-                    "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+    ezo.profile_enable(True)
+    ezo.profile_reset()
+    for i in range(args.steps):
+        flush.zero_()
+        step(i, ezo.RUN_HOST_LOOP)
+    torch.cuda.synchronize()
+    prof = ezo.profile_read()
+    ezo.profile_enable(False)
+    other_launches = int(sum(v[1] for v in prof.values()))
+    tot = {"check": 0.0, "bisect": 0.0, "sample": 0.0}
+    for i in range(args.steps):
+        w = work[i % N_SEEDS]
+        tot["check"] += w["sample_checks"] * flops_cfg
+        tot["bisect"] += w["bisection_checks"] * flops_cfg
+        tot["sample"] += w["sample_flops"]
+    dom = max(tot, key=lambda k: prof[k][0])
+    ach = tot[dom] / (prof[dom][0] / 1e3) / 1e12
+    path_tf = sum(tot.values()) / (float(np.sum(times)) / 1e3) / 1e12
+    roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": TRAFFIC.get(dom),
+                "per_launch_ms": prof[dom][0] / prof[dom][1],
+                "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                "measured_in": "host-loop pass over the same steps, CUDA events around each launch",
+                "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+                "whole_path": {"achieved": path_tf, "frac": path_tf / peak,
+                               "what": "all algorithmic FP32 FLOPs of the path (walks + exact checks) / step time"}}
+    w0 = work[0]
+    samp, bisc, kept = w0["sample_checks"], w0["bisection_checks"], w0["kept"]
+    checks_per_step = units / args.steps
 
     # ---- the plain method for comparison: one segment at a time in path order
     #      (host launch loop, containment skip before each segment) ----
     plain_ms = []
-    for _ in range(max(3, args.steps // 4)):
+    for _ in range(0 if args.no_extras else max(3, args.steps // 4)):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -520,38 +556,48 @@ def main():
         e1.record(stream)
         e1.synchronize()
         plain_ms.append(e0.elapsed_time(e1))
-    kept_plain = sum(bt.segment(g).status != ezo.SEG_SKIPPED for g in range(K))
-    plain = {"ms_per_path": float(np.median(plain_ms)), "kept_segments": int(kept_plain),
-             "what": "sequential per-segment inflation (paper's order), host-driven launch loop"}
+    plain = None
+    if plain_ms:
+        kept_plain = sum(bt.segment(g).status != ezo.SEG_SKIPPED for g in range(K))
+        plain = {"ms_per_path": float(np.median(plain_ms)), "kept_segments": int(kept_plain),
+                 "what": "sequential per-segment inflation (paper's order), host-driven launch loop"}
 
     # ---- batched + learned surrogate (spec item 4): train on exact
     #      labels, then the same path with surrogate-guided bisection ----
     sur_info = None
-    if not args.no_surrogate:
+    if not args.no_surrogate and not args.no_extras:
         sur_info = measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args)
 
     # ---- the collision checker alone on the paper's batch size (2e6 configs) ----
-    checker = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg)
+    checker = checker_1e8 = {"launches": 0}
+    if not args.no_extras:
+        checker = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg)
+        checker_1e8 = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg,
+                                      N=100_000_000, reps=3)
 
     # ---- end to end through the public API with host buffers ----
     v1h = np.ascontiguousarray(path[:-1])
     v2h = np.ascontiguousarray(path[1:])
     e2e_times = []
     d2h = 0
-    for _ in range(args.steps):
+    e2e_units = 0
+    for i in range(args.steps):
+        b = batches[i % N_SEEDS]
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        bt.reset(v1h, v2h)
-        bt.run_path(sequential=False, mode=mode)
+        b.reset(v1h, v2h)
+        b.run_path(sequential=False, mode=mode)
         d2h = 0
         for g in range(K):
-            r = bt.segment(g)
+            r = b.segment(g)
             if r.status != ezo.SEG_SKIPPED:
                 d2h += r.A.nbytes + r.b.nbytes
         e2e_times.append(time.perf_counter() - t0)
+        w = work[i % N_SEEDS]
+        e2e_units += w["sample_checks"] + w["bisection_checks"]
     e2e_s = float(np.sum(e2e_times))
-    e2e = {"value": world * checks_per_step * args.steps / e2e_s, "unit": "configs/s",
+    e2e = {"value": world * e2e_units / e2e_s, "unit": "configs/s",
            "h2d_bytes_per_step": int(v1h.nbytes + v2h.nbytes), "d2h_bytes_per_step": int(d2h),
            "ms_per_step": 1e3 * e2e_s / args.steps}
 
@@ -562,11 +608,15 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "configs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mode": args.mode, "segments": K, "kept_segments": kept,
-                       "checks_per_step": checks_per_step, "sample_checks": samp, "bisection_checks": bisc,
+            "config": {"workload": WORKLOAD, "mode": args.mode, "segments": K, "seeds": f"1..{N_SEEDS}, step i: seed 1 + i % {N_SEEDS}",
+                       "checks_per_step": checks_per_step, "seed1": {"kept_segments": kept, "sample_checks": samp,
+                                                                      "bisection_checks": bisc},
                        "ms_per_10_segment_path": ms / args.steps,
+                       "ms_p50": float(np.percentile(times, 50)), "ms_p90": float(np.percentile(times, 90)),
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "e2e": e2e, "gpu_launches": launches + checker["launches"],
+            "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "checker_1e8": checker_1e8, "e2e": e2e,
+            "gpu_launches": launches,
+            "gpu_launches_outside_timed_region": other_launches + checker["launches"] + checker_1e8["launches"],
             "clocks": clocks}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args.seconds)

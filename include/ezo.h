@@ -212,6 +212,13 @@ ezo_status ezo_batch_get_polytope(const ezo_batch* batch, int32_t seg, int32_t* 
 /* Row capacity per segment (m0 + n_f * n_it_max) and sample capacity. */
 ezo_status ezo_batch_capacity(const ezo_batch* batch, int32_t* m_cap, int32_t* s_cap);
 
+/* Lanes of a warp that share one hit-and-run walk (Algorithm 1, sampling
+ * step): 1, 2, 4 or 8, or 0 (the default) to choose per round on the device
+ * from the number of walks, eight lanes when the round has fewer walks than
+ * the GPU holds threads. Every choice draws the same samples bit for bit; only
+ * the speed differs. EZO_ERR_INVALID_ARG for any other value. */
+ezo_status ezo_batch_set_sample_lanes(ezo_batch* batch, int32_t lanes);
+
 /* Step-by-step access for tests and tools. ezo_batch_step runs one kernel of
  * the current round over the batch: 0 round size (a1), 1 hit-and-run (a2),
  * 2 collision labels (a3, a4), 3 certification and selection (a5, a6),
@@ -238,6 +245,66 @@ ezo_status ezo_batch_read(const ezo_batch* batch, int32_t seg, int32_t what, voi
  * n x count dimension-major, count <= s_cap) so that a round can be replayed
  * on given samples; sets |S| to count. */
 ezo_status ezo_batch_write_samples(ezo_batch* batch, int32_t seg, const float* samples, int32_t count);
+
+/* ------------------------------------------------------------- recovery --
+ * Sec. VI-B: a trajectory planned in the sets is checked at fine steps; the
+ * collisions found in a set are excluded from it by repeating the last steps
+ * of Algorithm 1 (bisection toward the seed segment, ordering, hyperplane
+ * placement with step back and t_col, at most N_f planes); afterwards every
+ * segment of the seed path must lie in some set of its path, and segments
+ * that no longer do are inflated again. */
+
+/* Fine discretisation of a piecewise-linear path (host only): edge k, from
+ * v_k to v_{k+1} (rows of `verts`, n_verts x n FP64 row-major), is cut into
+ * N_k = max(1, ceil(|v_{k+1} - v_k|_2 / step)) pieces and checked at its
+ * N_k + 1 points v_k + (i / N_k)(v_{k+1} - v_k), i = 0..N_k (the appendix
+ * checks paths at 0.1 rad). Writes N_k + 1 to edge_points[k] (nullable,
+ * n_verts - 1 entries) and the sum to *total. EZO_ERR_INVALID_ARG for
+ * step <= 0, a non-finite step or edge, n outside [1, 16]. */
+ezo_status ezo_path_points(const double* verts, int32_t n_verts, int32_t n, double step, int64_t* edge_points,
+                           int64_t* total);
+
+/* Collision check of those points on the GPU: each point is interpolated in
+ * FP64 (product and sum rounded separately), rounded to FP32 and checked with
+ * the same forward kinematics and sphere test as ezo_check_collision.
+ * edge_flags (host, n_verts - 1 bytes): 1 when any point of the edge
+ * collides. point_flags_dev (nullable, device, point_cap bytes): 1 per
+ * colliding point, in edge order. *n_points (nullable) receives the point
+ * count. Synchronous; uses stream-ordered scratch (cudaMallocAsync).
+ * EZO_ERR_CAPACITY when point_cap is below the point count. */
+ezo_status ezo_check_path(const ezo_robot* robot, const ezo_env* env, const double* verts, int32_t n_verts,
+                          double step, uint8_t* edge_flags, uint8_t* point_flags_dev, int64_t point_cap,
+                          int64_t* n_points, void* cuda_stream);
+
+/* Replaces the current polytope of segment `seg` with m rows (A: m x n FP64
+ * row-major, b: m entries; host buffers, copied), for editing sets computed
+ * elsewhere. EZO_ERR_CAPACITY when m > m_cap. Synchronous. */
+ezo_status ezo_batch_set_polytope(ezo_batch* batch, int32_t seg, int32_t m, const double* A, const double* b,
+                                  void* cuda_stream);
+
+/* Set editing: for every segment whose polytope P is final (accepted, or N_it
+ * reached), the configurations cfg (n_cfg x n FP64 row-major, host; rounded
+ * to FP32 like samples) that collide and lie in P (A c <= b + 1e-9, FP64) form
+ * S_col; its first N_p by index are bisected toward the segment and planes are
+ * placed as in a round of Algorithm 1, with no test; rows are appended to P.
+ * Per segment, ezo_batch_read(.., 6, ..) then reports count = |S_col|,
+ * n_cand and n_placed; a segment whose candidate lies within t_col of it
+ * becomes EZO_SEG_IN_COLLISION, one without room for N_f more rows
+ * EZO_SEG_CAPACITY. EZO_ERR_CAPACITY when n_cfg exceeds a segment's sample
+ * capacity; EZO_ERR_INVALID_ARG while a segment is still active.
+ * Synchronous. */
+ezo_status ezo_batch_edit(ezo_batch* batch, int64_t n_cfg, const double* cfg, void* cuda_stream);
+
+/* covered[g] (host, n_seg bytes) = 1 when both endpoints of segment g lie in
+ * the final polytope (accepted or N_it reached) of some segment of the same
+ * path, A x <= b + 1e-9; then the whole segment does. Synchronous. */
+ezo_status ezo_batch_coverage(ezo_batch* batch, uint8_t* covered, void* cuda_stream);
+
+/* Inflates the segments with which[g] != 0 again from round 1 with P = D (the
+ * batch's domain), keeping every other segment as it is, and runs them in
+ * `mode` until done. Check counters accumulate. Synchronous.
+ * EZO_ERR_INVALID_ARG while a segment is still active. */
+ezo_status ezo_batch_reinflate(ezo_batch* batch, const uint8_t* which, int32_t mode, void* cuda_stream);
 
 /* ---------------------------------------------------- no-allocation path --
  * No counterpart in the paper. For callers that cannot allocate device memory

@@ -12,9 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libezo.so")
-SOURCES = ["ezo_capi.cu", "ezo_k_flat.cu", "ezo_k_round_a.cu", "ezo_k_round_b.cu", "ezo_noalloc.cu", "ezo_tune.cu", "ezo_mlp.cu", "ezo_k_sbis.cu"]
+SOURCES = ["ezo_capi.cu", "ezo_k_flat.cu", "ezo_k_round_a.cu", "ezo_k_round_b.cu", "ezo_noalloc.cu", "ezo_tune.cu", "ezo_mlp.cu", "ezo_k_sbis.cu", "ezo_k_recover.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off"]
 
 
 def nvcc() -> str:

@@ -865,6 +865,19 @@ void ezo_batch_free(ezo_batch* b) {
   delete b;
 }
 
+ezo_status ezo_batch_set_sample_lanes(ezo_batch* b, int32_t lanes) {
+  if (!b || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_sample_lanes: lanes must be 0, 1, 2, 4 or 8");
+  if (b->gexec) {  // the graph holds the view by value
+    cudaGraphExecDestroy(b->gexec);
+    cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+  }
+  b->view.sample_lanes = lanes;
+  return EZO_OK;
+}
+
 ezo_status ezo_batch_attach_surrogate(ezo_batch* b, ezo_surrogate* sur, float margin) {
   if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_attach_surrogate: null batch");
   if (b->gexec) {
@@ -1149,6 +1162,183 @@ ezo_status ezo_batch_write_samples(ezo_batch* b, int32_t seg, const float* sampl
     EZO_CUDA(cudaMemcpy(b->d_S + (size_t)b->n * s.sample_off + (size_t)j * s.s_cap, samples + (size_t)j * count,
                         sizeof(float) * count, cudaMemcpyHostToDevice));
   EZO_CUDA(cudaMemcpy(&b->d_st[seg].n_samples, &count, sizeof(int), cudaMemcpyHostToDevice));
+  return EZO_OK;
+}
+
+// ------------------------------------------------ recovery (Sec. VI-B) --
+ezo_status ezo_batch_set_polytope(ezo_batch* b, int32_t seg, int32_t m, const double* A, const double* bb,
+                                  void* stream_v) {
+  if (!b || seg < 0 || seg >= b->B || m < 0 || (m > 0 && (!A || !bb)))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_polytope: bad argument");
+  if (m > b->m_cap) return fail(EZO_ERR_CAPACITY, "ezo_batch_set_polytope: more rows than the batch's m_cap");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  const size_t n = b->n;
+  if (m > 0) {
+    EZO_CUDA(cudaMemcpyAsync(b->d_A + (size_t)seg * b->m_cap * n, A, sizeof(double) * m * n,
+                             cudaMemcpyHostToDevice, s));
+    EZO_CUDA(cudaMemcpyAsync(b->d_b + (size_t)seg * b->m_cap, bb, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  }
+  EZO_CUDA(cudaMemcpyAsync(&b->d_st[seg].m, &m, sizeof(int), cudaMemcpyHostToDevice, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_edit(ezo_batch* b, int64_t n_cfg, const double* cfg, void* stream_v) {
+  if (!b || n_cfg < 0 || (n_cfg > 0 && !cfg)) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_edit: bad argument");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  std::vector<SegState> sts;
+  ezo_status st = read_states(b, sts, s);
+  if (st != EZO_OK) return st;
+  std::vector<int> targets;
+  for (int g = 0; g < b->B; ++g) {
+    if (sts[g].status == SEG_ACTIVE) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_edit: the batch is still running");
+    if (sts[g].status == SEG_ACCEPTED || sts[g].status == SEG_MAX_ITER) {
+      if (n_cfg > sts[g].s_cap) return fail(EZO_ERR_CAPACITY, "ezo_batch_edit: more configurations than samples fit");
+      targets.push_back(g);
+    }
+  }
+  if (targets.empty() || n_cfg == 0) {
+    g_err.clear();
+    return EZO_OK;
+  }
+  const size_t n = b->n, N = (size_t)n_cfg;
+  std::vector<float> soa(n * N);
+  for (size_t i = 0; i < N; ++i)
+    for (size_t j = 0; j < n; ++j) soa[j * N + i] = (float)cfg[i * n + j];
+  std::vector<SegState> saved = sts;
+  for (int g : targets) {
+    EZO_CUDA(cudaMemcpy2DAsync(b->d_S + n * (size_t)sts[g].sample_off, sizeof(float) * (size_t)sts[g].s_cap,
+                               soa.data(), sizeof(float) * N, sizeof(float) * N, n, cudaMemcpyHostToDevice, s));
+    sts[g].status = SEG_ACTIVE;
+    sts[g].n_samples = (int)n_cfg;
+  }
+  EZO_CUDA(cudaMemcpyAsync(b->d_st, sts.data(), sizeof(SegState) * b->B, cudaMemcpyHostToDevice, s));
+  EZO_CUDA(cudaMemsetAsync(b->d_sum, 0, sizeof(RoundSummary), s));
+  b->view.edit = 1;
+  const int steps[5] = {0, 2, 3, 4, 5};  // round size, labels, selection, bisection, placement
+  for (int k = 0; k < 5 && st == EZO_OK; ++k) st = launch_step(b, steps[k], s);
+  b->view.edit = 0;
+  if (st != EZO_OK) return st;
+  st = read_states(b, sts, s);
+  collect_profile(b);
+  if (st != EZO_OK) return st;
+  for (int g : targets)
+    if (sts[g].status == SEG_ACTIVE) sts[g].status = saved[g].status;  // else in collision (t_col) or full
+  EZO_CUDA(cudaMemcpyAsync(b->d_st, sts.data(), sizeof(SegState) * b->B, cudaMemcpyHostToDevice, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_coverage(ezo_batch* b, uint8_t* covered, void* stream_v) {
+  if (!b || !covered) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_coverage: bad argument");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  EZO_CUDA(cudaMemsetAsync(b->d_contained, 0, (size_t)b->B, s));
+  cudaError_t e = launch_coverage(b->view, b->d_contained, 1e-9, s);
+  if (e != cudaSuccess) return cuda_fail(e, "coverage");
+  EZO_CUDA(cudaMemcpyAsync(covered, b->d_contained, (size_t)b->B, cudaMemcpyDeviceToHost, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_reinflate(ezo_batch* b, const uint8_t* which, int32_t mode, void* stream_v) {
+  if (!b || !which) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_reinflate: bad argument");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  std::vector<SegState> sts;
+  ezo_status st = read_states(b, sts, s);
+  if (st != EZO_OK) return st;
+  const size_t n = b->n, mc = b->m_cap;
+  int any = 0;
+  for (int g = 0; g < b->B; ++g) {
+    if (sts[g].status == SEG_ACTIVE) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_reinflate: the batch is still running");
+    if (!which[g]) continue;
+    // back to round 1 with P = D, keeping the counters of earlier runs
+    SegState r = b->st0[g];
+    r.checks = sts[g].checks;
+    r.checks_bisect = sts[g].checks_bisect;
+    r.sur_evals = sts[g].sur_evals;
+    r.sample_flops = sts[g].sample_flops;
+    r.planes = 0;
+    sts[g] = r;
+    EZO_CUDA(cudaMemcpyAsync(b->d_A + g * mc * n, b->d_A0 + g * mc * n, sizeof(double) * mc * n,
+                             cudaMemcpyDeviceToDevice, s));
+    EZO_CUDA(cudaMemcpyAsync(b->d_b + g * mc, b->d_b0 + g * mc, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s));
+    any = 1;
+  }
+  if (!any) {
+    g_err.clear();
+    return EZO_OK;
+  }
+  EZO_CUDA(cudaMemcpyAsync(b->d_st, sts.data(), sizeof(SegState) * b->B, cudaMemcpyHostToDevice, s));
+  EZO_CUDA(cudaMemsetAsync(b->d_sum, 0, sizeof(RoundSummary), s));
+  st = run_batch(b, mode, s);
+  if (st == EZO_OK) g_err.clear();
+  return st;
+}
+
+ezo_status ezo_path_points(const double* verts, int32_t n_verts, int32_t n, double step, int64_t* edge_points,
+                           int64_t* total) {
+  if (!total || n_verts < 0 || n < 1 || n > EZO_MAX_DOF || (n_verts > 0 && !verts) || !(step > 0.0) ||
+      !std::isfinite(step))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_path_points: bad argument");
+  long long tot = 0;
+  for (int k = 0; k + 1 < n_verts; ++k) {
+    double ss = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double e = verts[(size_t)(k + 1) * n + j] - verts[(size_t)k * n + j];
+      ss += e * e;
+    }
+    const double q = std::ceil(std::sqrt(ss) / step);
+    if (!std::isfinite(q) || q > 1e12) return fail(EZO_ERR_INVALID_ARG, "ezo_path_points: non-finite or huge edge");
+    const long long pts = std::max(1ll, (long long)q) + 1;
+    if (edge_points) edge_points[k] = pts;
+    tot += pts;
+  }
+  *total = tot;
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_check_path(const ezo_robot* robot, const ezo_env* env, const double* verts, int32_t n_verts,
+                          double step, uint8_t* edge_flags, uint8_t* point_flags_dev, int64_t point_cap,
+                          int64_t* n_points, void* stream_v) {
+  if (!robot || !env || (n_verts > 1 && !edge_flags))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_check_path: bad argument");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  const int K = std::max(0, n_verts - 1), n = robot->n;
+  std::vector<int64_t> cnt((size_t)std::max(K, 1));
+  std::vector<long long> off((size_t)K + 1, 0);
+  int64_t N = 0;
+  ezo_status st = ezo_path_points(verts, n_verts, n, step, cnt.data(), &N);
+  if (st != EZO_OK) return st;
+  if (n_points) *n_points = N;
+  if (point_flags_dev && point_cap < N) return fail(EZO_ERR_CAPACITY, "ezo_check_path: point_cap < points");
+  if (K == 0) {
+    g_err.clear();
+    return EZO_OK;
+  }
+  for (int k = 0; k < K; ++k) off[k + 1] = off[k] + cnt[k];
+  // one scratch block: vertices (FP64), edge offsets, edge flags
+  const size_t vb = sizeof(double) * (size_t)n_verts * n, ob = sizeof(long long) * (size_t)(K + 1);
+  char* scratch = nullptr;
+  EZO_CUDA(cudaMallocAsync((void**)&scratch, vb + ob + (size_t)K, s));
+  double* d_verts = (double*)scratch;
+  long long* d_off = (long long*)(scratch + vb);
+  uint8_t* d_edge = (uint8_t*)(scratch + vb + ob);
+  cudaError_t e = cudaMemcpyAsync(d_verts, verts, vb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), ob, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_edge, 0, (size_t)K, s);
+  if (e == cudaSuccess) {
+    const int lanes = ezo_internal_tuned_lanes(robot, env, N, s);
+    e = launch_check_path(robot->d_robot, n, robot->nsp_pad, env->dev(), band_E(robot, env), d_verts, K, d_off, N,
+                          point_flags_dev, d_edge, lanes, sm_count() * 32, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(edge_flags, d_edge, (size_t)K, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "ezo_check_path");
+  g_err.clear();
   return EZO_OK;
 }
 

@@ -146,13 +146,42 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
   float c2x = 0.f, c2y = 0.f, c2z = 1.f;
   float px = 0.f, py = 0.f, pz = 0.f;
   const int n = rs.n;
+  // sine and cosine of every joint angle. With T lanes per configuration,
+  // lane lg evaluates joints lg, lg + T, .. (all lanes run the same
+  // instructions on their own angle) and the group exchanges the results;
+  // the values are the same as one lane evaluating all of them.
+  float sj[NDOF], cj[NDOF];
+  if (T == 1) {
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      sj[j] = 0.f;
+      cj[j] = 1.f;
+      if (j < n) sincosf(q[j] + rs.toff[j], &sj[j], &cj[j]);
+    }
+  } else {
+    constexpr int JPL = (NDOF + T - 1) / T;
+    float ms[JPL], mc[JPL];
+#pragma unroll
+    for (int k = 0; k < JPL; ++k) {
+      const int jm = lg + k * T;
+      float ang = 0.f;
+#pragma unroll
+      for (int j = 0; j < NDOF; ++j)
+        if (j == jm && j < n) ang = q[j] + rs.toff[j];
+      sincosf(ang, &ms[k], &mc[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      sj[j] = __shfl_sync(0xffffffffu, ms[j / T], j % T, T);
+      cj[j] = __shfl_sync(0xffffffffu, mc[j / T], j % T, T);
+    }
+  }
 #pragma unroll
   for (int f = 0; f <= NDOF; ++f) {
     if (f > n) break;
     if (f > 0) {
       const int j = f - 1;
-      float s, c;
-      sincosf(q[j] + rs.toff[j], &s, &c);
+      const float s = sj[j], c = cj[j];
       // R_{j} Rz(theta): col0' = c col0 + s col1, col1' = -s col0 + c col1
       const float n0x = fmaf(c, c0x, s * c1x), n0y = fmaf(c, c0y, s * c1y), n0z = fmaf(c, c0z, s * c1z);
       const float n1x = fmaf(c, c1x, -s * c0x), n1y = fmaf(c, c1y, -s * c0y), n1z = fmaf(c, c1z, -s * c0z);

@@ -102,7 +102,8 @@ struct BatchView {
   int sbis;          // 1 when a surrogate is attached
   int bis_mode;      // bisection kernel mode: 0 exact, 1 verify surrogate end point, 2 exact for fallbacks
   float sbis_margin; // predicted collision iff sd_hat < margin
-  int pad2;
+  int sample_lanes;  // lanes per hit-and-run walk: 0 = chosen per round from the tile count, else 1, 2, 4 or 8
+  int edit;          // set editing (Sec. VI-B): the samples are given configurations, no test
   float* s_p32;      // [row * 8 + j] projection onto L (FP32)
   float* s_d32;      // [row * 8 + j] c - c_proj (FP32)
   float* s_lo;       // [row] bracket (fractions along [c_proj, c])
@@ -140,6 +141,11 @@ cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 // (Sec. VI-A): contained[k*max_path_len + d] = 1 iff both endpoints of
 // segment k satisfy A_j x <= b_j + tol for j = path_first[k] + d < k.
 cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s);
+// recovery (Sec. VI-B)
+cudaError_t launch_check_path(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, float E,
+                              const double* verts, int n_edges, const long long* off, long long N,
+                              uint8_t* point_flags, uint8_t* edge_flags, int T, int grid_cap, cudaStream_t s);
+cudaError_t launch_coverage(const BatchView& v, uint8_t* covered, double tol, cudaStream_t s);
 
 size_t check_smem_bytes(int n_spheres_pad, int n_obs_pad, int threads, int T);
 

@@ -27,7 +27,14 @@ __global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
     int tiles = 0;
     if (g < v.B) {
       SegState& st = v.st[g];
-      if (st.status == SEG_ACTIVE) {
+      if (st.status == SEG_ACTIVE && v.edit) {
+        // set editing: the given configurations are already in place
+        st.m_test = 0;
+        st.n_cand = 0;
+        st.count = 0;
+        st.n_placed = 0;
+        tiles = (st.n_samples + kTile - 1) / kTile;
+      } else if (st.status == SEG_ACTIVE) {
         const int M = round_test_size(st.k, v.eps, v.delta, v.tau);
         int S = M > st.n_p ? M : st.n_p;
         if (S > st.s_cap) S = st.s_cap;  // capacity is sized for M at N_it; never hit
@@ -116,7 +123,8 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
   const int n_tiles = v.summary->n_sample_tiles;
   // eight lanes per walk below the threshold, two up to eight times it,
   // one above (more walks than the GPU holds warps)
-  const int passes = n_tiles < split_below_tiles ? 8 : (n_tiles < 8 * split_below_tiles ? 2 : 1);
+  const int passes = v.sample_lanes ? v.sample_lanes
+                                    : (n_tiles < split_below_tiles ? 8 : (n_tiles < 8 * split_below_tiles ? 2 : 1));
   float* A32 = reinterpret_cast<float*>(smf4);
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();
@@ -145,6 +153,7 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
       __syncthreads();
     }
     if (passes == 8) sample_pass<NDOF, 8>(v, st, A32, p, tile, u % passes);
+    else if (passes == 4) sample_pass<NDOF, 4>(v, st, A32, p, tile, u % passes);
     else if (passes == 2) sample_pass<NDOF, 2>(v, st, A32, p, tile, u % passes);
     else sample_pass<NDOF, 1>(v, st, A32, p, tile, 0);
   }
@@ -197,8 +206,26 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
   }
 }
 
+// Set editing (Sec. VI-B): configuration x is a candidate when it collides
+// and lies in the current polytope, A x <= b + 1e-9 in FP64.
+__device__ __forceinline__ bool edit_inside(const BatchView& v, int g, const SegState& st, int i) {
+  const int n = v.n;
+  const double* A = v.A + (long long)g * v.m_cap * n;
+  const double* b = v.b + (long long)g * v.m_cap;
+  const float* S = v.S + (long long)n * st.sample_off;
+  double x[EZO_MAX_DOF];
+  for (int j = 0; j < n; ++j) x[j] = (double)S[(long long)j * st.s_cap + i];
+  for (int r = 0; r < st.m; ++r) {
+    double ax = 0.0;
+    for (int j = 0; j < n; ++j) ax = fma(A[(long long)r * n + j], x[j], ax);
+    if (ax > b[r] + 1e-9) return false;
+  }
+  return true;
+}
+
 // Unadaptive test on the first M samples and stable compaction of the first
 // N_p colliding samples (lowest sample index first). One block per segment.
+// In set editing there is no test and a candidate must also lie in P.
 __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
   const int g = blockIdx.x;
   SegState& st = v.st[g];
@@ -219,7 +246,8 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
   int my_count = 0;
   for (int base = 0; base < S; base += blockDim.x) {
     const int i = base + threadIdx.x;
-    const int f = (i < S) ? (fl[i] != 0) : 0;
+    int f = (i < S) ? (fl[i] != 0) : 0;
+    if (v.edit && f) f = edit_inside(v, g, st, i) ? 1 : 0;
     if (i < M) my_count += f;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     const int pre = __popc(bal & ((1u << lane) - 1u));
@@ -241,7 +269,7 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
     __syncthreads();
     if (threadIdx.x == 0) s_running = running + warp_cnt[nw - 1];
     __syncthreads();
-    if (s_running >= np && base + (int)blockDim.x >= M) break;
+    if (!v.edit && s_running >= np && base + (int)blockDim.x >= M) break;
   }
   // block reduction of the count over the first M samples
 #pragma unroll
@@ -249,10 +277,10 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
   if (lane == 0) atomicAdd(&s_count, my_count);
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int cnt = s_count;
+    const int cnt = v.edit ? s_running : s_count;  // editing: colliding configurations in P
     st.count = cnt;
     st.checks += S;
-    const bool accept = (double)cnt <= (double)M * (1.0 - v.tau) * v.eps;
+    const bool accept = !v.edit && (double)cnt <= (double)M * (1.0 - v.tau) * v.eps;
     if (accept) {
       st.status = SEG_ACCEPTED;
       st.rounds = st.k;

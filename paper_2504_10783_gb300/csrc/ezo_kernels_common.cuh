@@ -47,13 +47,48 @@ __host__ __device__ constexpr int hnr_row_stride() {
   return (NDOF + 4) & ~3;
 }
 
+// Chord bounds from polytope rows r0, r0 + step, .. < m: for row r the slack
+// b_r - a_r . x and the rate a_r . d give the crossing t = slack / rate,
+// which bounds the chord from above when the rate is positive and from below
+// when it is negative. Four rows are processed per iteration so that their
+// dot-product chains overlap; each row's arithmetic does not depend on how
+// the rows are split between lanes, and min/max do not depend on the order.
+template <int NDOF>
+__device__ __forceinline__ void chord_rows(const float* __restrict__ A32, int r0, int m, int step,
+                                           const float (&x)[NDOF], const float (&d)[NDOF], float& t_lo,
+                                           float& t_hi) {
+  constexpr int RS = hnr_row_stride<NDOF>();
+#pragma unroll 4
+  for (int r = r0; r < m; r += step) {
+    // row r of A and b[r] in one padded record: RS / 4 broadcast loads
+    const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
+    float av[RS];
+#pragma unroll
+    for (int qd = 0; qd < RS / 4; ++qd) {
+      const float4 v4 = row[qd];
+      av[4 * qd] = v4.x;
+      av[4 * qd + 1] = v4.y;
+      av[4 * qd + 2] = v4.z;
+      av[4 * qd + 3] = v4.w;
+    }
+    float ax = 0.f, ad = 0.f;
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      ax = fmaf(av[j], x[j], ax);
+      ad = fmaf(av[j], d[j], ad);
+    }
+    const float q = __fdividef(av[NDOF] - ax, ad);
+    if (ad > 0.f) t_hi = fminf(t_hi, q);
+    if (ad < 0.f) t_lo = fmaxf(t_lo, q);
+  }
+}
+
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
                                          uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
                                          float (&x)[NDOF]) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
-  constexpr int RS = hnr_row_stride<NDOF>();
   const int npair = (n + 1) / 2;
   const int W = (2 * npair + 4) / 4;
   const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
@@ -94,28 +129,7 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    for (int r = 0; r < m; ++r) {
-      // row r of A and b[r] in one padded record: RS / 4 broadcast loads
-      const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
-      float av[RS];
-#pragma unroll
-      for (int qd = 0; qd < RS / 4; ++qd) {
-        const float4 v4 = row[qd];
-        av[4 * qd] = v4.x;
-        av[4 * qd + 1] = v4.y;
-        av[4 * qd + 2] = v4.z;
-        av[4 * qd + 3] = v4.w;
-      }
-      float ax = 0.f, ad = 0.f;
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) {
-        ax = fmaf(av[j], x[j], ax);
-        ad = fmaf(av[j], d[j], ad);
-      }
-      const float sl = av[NDOF] - ax;
-      if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(sl, ad));
-      else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(sl, ad));
-    }
+    chord_rows<NDOF>(A32, 0, m, 1, x, d, t_lo, t_hi);
     t_hi = fmaxf(t_hi, 0.f);
     t_lo = fminf(t_lo, 0.f);
     if (ok && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
@@ -140,7 +154,6 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
                                                float (&x)[NDOF]) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
-  constexpr int RS = hnr_row_stride<NDOF>();
   constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
   const int npair = (n + 1) / 2;
   const int W = (2 * npair + 4) / 4;
@@ -188,27 +201,7 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    for (int r = lw; r < m; r += TS) {
-      const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
-      float av[RS];
-#pragma unroll
-      for (int qd = 0; qd < RS / 4; ++qd) {
-        const float4 v4 = row[qd];
-        av[4 * qd] = v4.x;
-        av[4 * qd + 1] = v4.y;
-        av[4 * qd + 2] = v4.z;
-        av[4 * qd + 3] = v4.w;
-      }
-      float ax = 0.f, ad = 0.f;
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) {
-        ax = fmaf(av[j], x[j], ax);
-        ad = fmaf(av[j], d[j], ad);
-      }
-      const float sl = av[NDOF] - ax;
-      if (ad > 0.f) t_hi = fminf(t_hi, __fdividef(sl, ad));
-      else if (ad < 0.f) t_lo = fmaxf(t_lo, __fdividef(sl, ad));
-    }
+    chord_rows<NDOF>(A32, lw, m, TS, x, d, t_lo, t_hi);
 #pragma unroll
     for (int o = 1; o < TS; o <<= 1) {
       t_hi = fminf(t_hi, __shfl_xor_sync(0xffffffffu, t_hi, o, TS));

@@ -94,6 +94,14 @@ def _sig(lib):
     f.ezo_surrogate_grad.argtypes = [_P, _P, _I64, _P, _I32, C.POINTER(C.c_float), C.POINTER(C.c_float), _P]
     f.ezo_surrogate_predict.argtypes = [_P, _P, _I64, _I64, _P, _P]
     f.ezo_batch_attach_surrogate.argtypes = [_P, _P, C.c_float]
+    f.ezo_batch_set_sample_lanes.argtypes = [_P, _I32]
+    f.ezo_path_points.argtypes = [_DP, _I32, _I32, C.c_double, C.POINTER(_I64), C.POINTER(_I64)]
+    f.ezo_check_path.argtypes = [_P, _P, _DP, _I32, C.c_double, C.POINTER(C.c_uint8), _P, _I64,
+                                 C.POINTER(_I64), _P]
+    f.ezo_batch_set_polytope.argtypes = [_P, _I32, _I32, _DP, _DP, _P]
+    f.ezo_batch_edit.argtypes = [_P, _I64, _DP, _P]
+    f.ezo_batch_coverage.argtypes = [_P, C.POINTER(C.c_uint8), _P]
+    f.ezo_batch_reinflate.argtypes = [_P, C.POINTER(C.c_uint8), _I32, _P]
     f.ezo_tune_lanes.argtypes = [_P, _P, _I64, C.POINTER(_I32), _P]
     f.ezo_set_autotune.argtypes = [_I32]
     f.ezo_check_flops.argtypes = [_P, _P]
@@ -198,6 +206,38 @@ def check_collision(robot: Robot, env: Env, q_dev, flags_dev, lanes: int = 0, st
         raise ValueError("q_dev must be [n, N] with stride(1) == 1 and flags_dev must hold N entries")
     _check(lib().ezo_check_collision(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, _ld(q_dev),
                                      C.c_void_p(flags_dev.data_ptr()), lanes, _stream(stream)))
+
+
+def path_points(verts, step: float, n: int | None = None):
+    """Point count of each edge of a piecewise-linear path checked at `step`
+    (Sec. VI-B) and the total: (int64 [K], total)."""
+    v = np.ascontiguousarray(np.atleast_2d(verts), dtype=np.float64)
+    K = max(0, v.shape[0] - 1)
+    cnt = np.zeros(max(K, 1), dtype=np.int64)
+    tot = _I64()
+    _check(lib().ezo_path_points(_dp(v), v.shape[0], n or v.shape[1], step, cnt.ctypes.data_as(C.POINTER(_I64)),
+                                 C.byref(tot)))
+    return cnt[:K], int(tot.value)
+
+
+def check_path(robot: Robot, env: Env, verts, step: float, point_flags_dev=None, stream=None):
+    """Collision check of a piecewise-linear path at `step` (Sec. VI-B):
+    returns (edge flags bool [K], point count); point_flags_dev (uint8 CUDA
+    tensor, optional) receives one flag per point in edge order."""
+    import torch
+    v = np.ascontiguousarray(np.atleast_2d(verts), dtype=np.float64)
+    if v.shape[1] != robot.n:
+        raise ValueError("verts must be [n_verts, n]")
+    K = max(0, v.shape[0] - 1)
+    edge = np.zeros(max(K, 1), dtype=np.uint8)
+    cap, ptr = 0, None
+    if point_flags_dev is not None:
+        _need_cuda(point_flags_dev, torch.uint8, "point_flags_dev")
+        cap, ptr = point_flags_dev.numel(), C.c_void_p(point_flags_dev.data_ptr())
+    npts = _I64()
+    _check(lib().ezo_check_path(robot.h, env.h, _dp(v), v.shape[0], step,
+                                edge.ctypes.data_as(C.POINTER(C.c_uint8)), ptr, cap, C.byref(npts), _stream(stream)))
+    return edge[:K].astype(bool), int(npts.value)
 
 
 def signed_distance(robot: Robot, env: Env, q_dev, sd_dev, stream=None):
@@ -385,6 +425,38 @@ class Batch:
         """Surrogate-guided bisection (None detaches)."""
         self._sur = sur
         _check(lib().ezo_batch_attach_surrogate(self.h, sur.h if sur is not None else None, margin))
+
+    def set_polytope(self, g: int, A, b, stream=None):
+        """Replace segment g's current polytope with A x <= b (host FP64)."""
+        A = np.ascontiguousarray(np.atleast_2d(A), dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if A.shape[0] and A.shape[1] != self.n or b.shape[0] != A.shape[0]:
+            raise ValueError("A must be [m, n] and b [m]")
+        _check(lib().ezo_batch_set_polytope(self.h, g, A.shape[0], _dp(A), _dp(b), _stream(stream)))
+
+    def edit(self, cfg, stream=None):
+        """Sec. VI-B set editing with the given configurations [N, n]."""
+        c = np.ascontiguousarray(np.atleast_2d(cfg), dtype=np.float64)
+        if c.size and c.shape[1] != self.n:
+            raise ValueError("cfg must be [N, n]")
+        _check(lib().ezo_batch_edit(self.h, c.shape[0] if c.size else 0, _dp(c), _stream(stream)))
+
+    def coverage(self, stream=None) -> np.ndarray:
+        """Per segment: covered by some final polytope of its path (bool)."""
+        out = np.zeros(self.B, dtype=np.uint8)
+        _check(lib().ezo_batch_coverage(self.h, out.ctypes.data_as(C.POINTER(C.c_uint8)), _stream(stream)))
+        return out.astype(bool)
+
+    def reinflate(self, which, mode: int = RUN_HOST_LOOP, stream=None):
+        """Inflate the segments with which[g] again from the domain."""
+        w = np.ascontiguousarray(np.asarray(which, dtype=bool).astype(np.uint8))
+        if w.shape[0] != self.B:
+            raise ValueError("which must have one entry per segment")
+        _check(lib().ezo_batch_reinflate(self.h, w.ctypes.data_as(C.POINTER(C.c_uint8)), mode, _stream(stream)))
+
+    def set_sample_lanes(self, lanes: int):
+        """Lanes per hit-and-run walk (0 = chosen per round, else 1, 2, 4, 8)."""
+        _check(lib().ezo_batch_set_sample_lanes(self.h, int(lanes)))
 
     def surrogate_evals(self, g: int) -> int:
         o = np.zeros(1, dtype=np.int64)

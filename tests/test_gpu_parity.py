@@ -184,21 +184,36 @@ def test_hit_and_run_matches_oracle_walks(ezo, which):
     assert np.all(x @ A.T <= b + 1e-5 * (1 + np.abs(b)))
 
 
-def test_round_walks_equal_flat_walks(ezo):
-    """The round sampler (several lanes per walk in small rounds) gives the
-    flat sampler's samples bit for bit: same Philox draws, same arithmetic."""
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8])
+def test_round_walks_equal_flat_walks(ezo, lanes):
+    """The round sampler gives the flat sampler's samples bit for bit for
+    every number of lanes per walk (same Philox draws, same per-row
+    arithmetic), in round 1 (the joint box) and in round 2, whose polytope
+    carries the planes placed in round 1."""
     rd, env_np, path = dh7_scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
     prm = ezo.Params.make(n_p=3000, seed=13)
     bt = ezo.Batch(robot, [env], path[2], path[3], prm, seg_stream=[7])
-    bt.step(0)
-    bt.step(1)
-    bt.sync()
-    st = bt.state(0)
-    S = bt.read(0, "samples")[:, : st["n_samples"]].T.astype(np.float64)
-    A, b = orc.joint_box(rd)
-    x = _gpu_hnr(ezo, A, b, path[2], path[3], st["n_samples"], prm.n_mix, 13, 7, 1)
-    np.testing.assert_array_equal(S, x)
+    bt.set_sample_lanes(lanes)
+    seen_planes = False
+    for k in (1, 2):
+        bt.step(0)
+        bt.step(1)
+        bt.sync()
+        st = bt.state(0)
+        if st["k"] != k:
+            break  # accepted in round 1
+        seg = bt.segment(0)
+        seen_planes |= seg.A.shape[0] > 14
+        S = bt.read(0, "samples")[:, : st["n_samples"]].T.astype(np.float64)
+        x = _gpu_hnr(ezo, seg.A, seg.b, path[2], path[3], st["n_samples"], prm.n_mix, 13, 7, k)
+        np.testing.assert_array_equal(S, x)
+        for step in range(2, 7):
+            bt.step(step)
+        bt.sync()
+    assert seen_planes
+    with pytest.raises(RuntimeError):
+        bt.set_sample_lanes(3)
 
 
 # ----------------------------------------------------- round-by-round replay --
