@@ -35,7 +35,9 @@ parameter or a documented choice of the CUDA library):
 * directions are n Box-Muller Gaussians, normalised; the chord [t_lo, t_hi]
   comes from the slack s = b - A x and q = A d, with t_lo <= 0 <= t_hi forced;
 * random numbers come from Philox4x32-10 (Salmon et al., SC'11) with counter
-  (walk, draw, round, stream) and key (seed low, seed high);
+  (walk, draw, round, stream) and key (seed low, seed high); a step's
+  Gaussians use the top 24 bits of its words and its step length the low
+  bytes of the first three, so 7 joints need two blocks per step;
 * "the first N_p samples in S_col" are the colliding samples of lowest index;
 * bisection runs on the segment [c_proj, c]; c* is its colliding end;
 * candidates are sorted by (distance to L, sample index); a candidate is
@@ -104,9 +106,20 @@ def seed_key(seed: int):
 
 
 def blocks_per_step(n: int) -> int:
-    """Philox blocks drawn per hit-and-run step: 2*ceil(n/2) uniforms for the
-    Box-Muller Gaussians of the direction plus one for the step length."""
-    return (2 * ((n + 1) // 2) + 1 + 3) // 4
+    """Philox blocks drawn per hit-and-run step: 2*ceil(n/2) words for the
+    Box-Muller Gaussians of the direction (at least one block); the step
+    length takes the low bytes of the first three words, which the 24-bit
+    uniforms leave unused."""
+    return max(1, (2 * ((n + 1) // 2) + 3) // 4)
+
+
+def step_uniform(w0, w1, w2) -> np.ndarray:
+    """The step length's uniform in [0, 1): the low bytes of three words
+    as one 24-bit integer (w0 lowest), times 2^-24."""
+    m = np.uint64(0xFF)
+    w0, w1, w2 = (np.asarray(w, dtype=np.uint64) for w in (w0, w1, w2))
+    t = (w0 & m) | ((w1 & m) << np.uint64(8)) | ((w2 & m) << np.uint64(16))
+    return t.astype(np.float64) * 2.0 ** -24
 
 
 # ---------------------------------------------------------------------------
@@ -269,10 +282,11 @@ def hit_and_run(A, b, v1, v2, n_samples: int, n_mix: int, seed: int, stream: int
     Walk j draws Philox blocks with counter (j, draw, k, stream):
     draw 0 gives the start u (word 0): x = v1 + u (v2 - v1);
     step s uses draws 1 + s W .. 1 + s W + W - 1 (W = blocks_per_step(n)),
-    whose words in order are uniforms u_0, u_1, ...; Gaussian pair i is
-    sqrt(-2 ln u'_{2i}) (cos, sin)(2 pi u_{2i+1}) with u' in (0, 1]; the
-    direction is the first n Gaussians normalised; the step is
-    t = t_lo + u_{2 ceil(n/2)} (t_hi - t_lo) on the chord of P through x.
+    whose words in order are w_0, w_1, ...; Gaussian pair i is
+    sqrt(-2 ln u'(w_{2i})) (cos, sin)(2 pi u(w_{2i+1})) from the top 24 bits
+    (u' in (0, 1], u in [0, 1)); the direction is the first n Gaussians
+    normalised; the step is t = t_lo + u_t (t_hi - t_lo) on the chord of P
+    through x, u_t = step_uniform(w_0, w_1, w_2) from the low bytes.
     """
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -302,7 +316,7 @@ def hit_and_run(A, b, v1, v2, n_samples: int, n_mix: int, seed: int, stream: int
         nrm = np.linalg.norm(dvec, axis=1)
         ok = nrm > 0.0
         dvec = np.where(ok[:, None], dvec / np.where(ok, nrm, 1.0)[:, None], 0.0)
-        ut = u01_closed_open(words[:, 2 * npair])
+        ut = step_uniform(words[:, 0], words[:, 1], words[:, 2])
         slack = b[None, :] - x @ A.T
         qd = dvec @ A.T
         with np.errstate(divide="ignore", invalid="ignore"):

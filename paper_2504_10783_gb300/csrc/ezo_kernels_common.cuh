@@ -25,13 +25,19 @@ struct SampleParams {
 
 // One hit-and-run walk of `n_mix` steps inside {x : A32 x <= b32}.
 // Random stream: Philox block (walk, draw, round, stream); draw 0 gives the
-// start x = v1 + u (v2 - v1); step s uses draws 1 + s W .. 1 + s W + W - 1
-// whose 4W words are uniforms u_0..: Gaussian pair i from (u_2i, u_2i+1) by
-// Box-Muller, step length from u_{2 ceil(n/2)}.
+// start x = v1 + u (v2 - v1); step s uses draws 1 + s W .. 1 + s W + W - 1,
+// W = max(1, ceil(2 ceil(n/2) / 4)), whose words w_0.. give Gaussian pair i
+// from the top 24 bits of (w_2i, w_2i+1) by Box-Muller and the step length
+// from the low bytes of w_0, w_1, w_2 (one 24-bit integer, w_0 lowest).
 // One Box-Muller pair from two 32-bit words: rho = sqrt(-2 ln u1) with u1 in
 // (0, 1], angle 2 pi u2 with u2 in [0, 1). The hardware approximations of ln
 // and of sin/cos (absolute error ~2^-21 on [-pi, pi]) are used; the angle is
 // shifted to pi (2 u2 - 1) in [-pi, pi), which negates sine and cosine.
+__device__ __forceinline__ float step_uniform(uint32_t w0, uint32_t w1, uint32_t w2) {
+  const uint32_t t = (w0 & 0xffu) | ((w1 & 0xffu) << 8) | ((w2 & 0xffu) << 16);
+  return (float)t * 5.9604644775390625e-8f;  // 2^-24
+}
+
 __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& za, float& zb) {
   const float rho = sqrtf(-2.f * __logf(u01_oc(w1)));
   float sn, cs;
@@ -88,9 +94,9 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
                                          uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
                                          float (&x)[NDOF]) {
-  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
+  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
   const int npair = (n + 1) / 2;
-  const int W = (2 * npair + 4) / 4;
+  const int W = max(1, (2 * npair + 3) / 4);
   const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
   const float u0 = u01_co(r0.x);
 #pragma unroll
@@ -120,10 +126,7 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
     }
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) nrm2 = fmaf(d[j], d[j], nrm2);
-    float ut = 0.f;
-#pragma unroll
-    for (int i = 0; i < 4 * WMAX; ++i)
-      if (i == 2 * npair) ut = u01_co(w[i]);
+    const float ut = step_uniform(w[0], w[1], w[2]);
     const bool ok = nrm2 > 0.f;
     const float inv = ok ? 1.f / sqrtf(nrm2) : 0.f;
 #pragma unroll
@@ -153,10 +156,10 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
                                                const float* ef, int n_mix, uint32_t key0, uint32_t key1,
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
                                                float (&x)[NDOF]) {
-  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 4) / 4;
+  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
   constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
   const int npair = (n + 1) / 2;
-  const int W = (2 * npair + 4) / 4;
+  const int W = max(1, (2 * npair + 3) / 4);
   const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
   const float u0 = u01_co(r0.x);
 #pragma unroll
@@ -179,9 +182,7 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
         z[4 * bl + 2 * h] = za;
         z[4 * bl + 2 * h + 1] = zb;
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (4 * b + c == 2 * npair) ut_part = u01_co(wv[c]);
+      if (b == 0) ut_part = step_uniform(wv[0], wv[1], wv[2]);
     }
     // gather the direction: component j lives in lane (j / 4) % TS, slot
     // 4 * ((j / 4) / TS) + j % 4
@@ -194,8 +195,7 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
       d[j] = (j < n) ? v : 0.f;
       nrm2 = fmaf(d[j], d[j], nrm2);
     }
-    const int ub = (2 * npair) / 4;
-    const float ut = __shfl_sync(0xffffffffu, ut_part, ub % TS, TS);
+    const float ut = __shfl_sync(0xffffffffu, ut_part, 0, TS);  // block 0 lives in lane 0
     const bool ok = nrm2 > 0.f;
     const float inv = ok ? 1.f / sqrtf(nrm2) : 0.f;
 #pragma unroll

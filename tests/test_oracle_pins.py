@@ -35,7 +35,11 @@ def test_uniform_conversions_exact_ends():
     assert orc.u01_closed_open(0xFFFFFFFF) == 1.0 - 2.0 ** -24
     assert orc.u01_open_closed(0) == 2.0 ** -24
     assert orc.u01_open_closed(0xFFFFFFFF) == 1.0
-    assert orc.blocks_per_step(3) == 2 and orc.blocks_per_step(7) == 3 and orc.blocks_per_step(2) == 1
+    assert orc.blocks_per_step(1) == 1 and orc.blocks_per_step(3) == 1 and orc.blocks_per_step(7) == 2
+    assert orc.blocks_per_step(8) == 2 and orc.blocks_per_step(9) == 3 and orc.blocks_per_step(16) == 4
+    # the step uniform: low bytes as one 24-bit integer, w0 lowest
+    assert orc.step_uniform(0xFFFFFF00, 0x000000FF, 0x12345600) == 0xFF00 * 2.0 ** -24
+    assert orc.step_uniform(0xFF, 0xFF, 0xFF) == 1.0 - 2.0 ** -24
 
 
 def test_philox_uniforms_are_uniform():
