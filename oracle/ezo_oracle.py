@@ -130,15 +130,20 @@ def dh_frames(robot, q) -> tuple[np.ndarray, np.ndarray]:
     """Frames of a standard DH chain for configurations ``q[N, n]``.
 
     Returns rotations R[N, n+1, 3, 3] and origins o[N, n+1, 3]; frame 0 is the
-    identity and T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i).
+    identity and T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i)
+    for a revolute joint, T_i = T_{i-1} Rz(theta_off_i) Tz(d_i + q_i) Tx(a_i)
+    Rx(alpha_i) for a prismatic one (``robot.prismatic``).
     """
     q = np.atleast_2d(np.asarray(q, dtype=np.float64))
     N, n = q.shape
     R = np.zeros((N, n + 1, 3, 3))
     o = np.zeros((N, n + 1, 3))
     R[:, 0] = np.eye(3)
+    prism = np.zeros(n, dtype=bool) if getattr(robot, "joint_type", None) is None \
+        else np.asarray(robot.joint_type) == 1
     for i in range(n):
-        th = q[:, i] + robot.theta_off[i]
+        th = (0.0 * q[:, i] if prism[i] else q[:, i]) + robot.theta_off[i]
+        dd = robot.d[i] + q[:, i] if prism[i] else np.full(N, robot.d[i])
         ct, st = np.cos(th), np.sin(th)
         ca, sa = math.cos(robot.alpha[i]), math.sin(robot.alpha[i])
         # Rz(th) Tz(d) Tx(a) Rx(alpha) as a rotation and a translation.
@@ -151,7 +156,7 @@ def dh_frames(robot, q) -> tuple[np.ndarray, np.ndarray]:
         L[:, 1, 2] = -ct * sa
         L[:, 2, 1] = sa
         L[:, 2, 2] = ca
-        t = np.stack([robot.a[i] * ct, robot.a[i] * st, np.full(N, robot.d[i])], axis=1)
+        t = np.stack([robot.a[i] * ct, robot.a[i] * st, dd], axis=1)
         R[:, i + 1] = R[:, i] @ L
         o[:, i + 1] = o[:, i] + np.einsum("nij,nj->ni", R[:, i], t)
     return R, o

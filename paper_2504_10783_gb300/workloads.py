@@ -34,6 +34,8 @@ __all__ = [
     "table_cloud_obstacles",
     "uniform_configs",
     "random_walk_waypoints",
+    "point2_robot",
+    "forest_obstacles",
 ]
 
 
@@ -42,7 +44,10 @@ class Robot:
     """Serial chain in standard DH form with spheres fixed to its frames.
 
     Frame 0 is the base (identity). Frame i (1..n) is
-    T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i).
+    T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i)
+    for a revolute joint (``joint_type[i-1] == 0``, the default) and
+    T_i = T_{i-1} Rz(theta_off_i) Tz(d_i + q_i) Tx(a_i) Rx(alpha_i)
+    for a prismatic one (``joint_type[i-1] == 1``).
     Sphere s sits at ``sphere_xyz[s]`` in frame ``sphere_frame[s]`` with radius
     ``sphere_r[s]``; ``sphere_link`` is a link id used only to build self pairs.
     """
@@ -59,6 +64,13 @@ class Robot:
     sphere_r: np.ndarray  # float64 [N_s]
     sphere_link: np.ndarray  # int32 [N_s]
     self_pairs: np.ndarray  # int32 [P, 2]
+    joint_type: np.ndarray | None = None  # int32 [n]: 0 revolute, 1 prismatic; None = all revolute
+
+    @property
+    def prismatic(self) -> np.ndarray:
+        if self.joint_type is None:
+            return np.zeros(self.n, dtype=bool)
+        return np.asarray(self.joint_type) == 1
 
     @property
     def n(self) -> int:
@@ -77,10 +89,12 @@ class Robot:
         ints = {"sphere_frame", "sphere_link", "self_pairs"}
         kw = {}
         for f in dataclasses.fields(Robot):
-            v = d[f.name]
+            v = d.get(f.name)
+            if v is None:
+                continue
             if f.name == "name":
                 kw[f.name] = v
-            elif f.name in ints:
+            elif f.name in ints or f.name == "joint_type":
                 kw[f.name] = np.asarray(v, dtype=np.int32).reshape(-1, 2) if f.name == "self_pairs" \
                     else np.asarray(v, dtype=np.int32)
             else:
@@ -189,6 +203,35 @@ def dh7_robot(r_base: float = 0.08, r_tip: float = 0.04) -> Robot:
         sphere_link=link,
         self_pairs=_pairs_between_links(link, [(1, 3), (1, 4), (2, 4)]),
     )
+
+
+def point2_robot(side: float = 10.0) -> Robot:
+    """A point moving in a square of side ``side`` (the Forest benchmark of
+    Sec. V): two prismatic joints, the first along the base z axis
+    (alpha = -pi/2 turns the next joint axis onto the base y axis), the second
+    along y, so the point sits at (0, q_1, q_0). One sphere of radius 0 at
+    frame 2; obstacles of the plane (x, y) are spheres at (0, y, x)."""
+    n = 2
+    return Robot(
+        name="point2",
+        a=np.zeros(n), alpha=np.array([-math.pi / 2, 0.0]), d=np.zeros(n), theta_off=np.zeros(n),
+        q_lo=np.zeros(n), q_hi=np.full(n, side),
+        sphere_frame=np.array([2], dtype=np.int32), sphere_xyz=np.zeros((1, 3)), sphere_r=np.zeros(1),
+        sphere_link=np.array([2], dtype=np.int32), self_pairs=np.zeros((0, 2), dtype=np.int32),
+        joint_type=np.ones(n, dtype=np.int32),
+    )
+
+
+def forest_obstacles(seed: int, count: int = 15, r: float = 0.35, side: float = 10.0,
+                     centre: float = 7.0) -> Env:
+    """Forest of Sec. V: ``count`` disks of radius ``r`` with centres uniform
+    in the central square of side ``centre`` of the ``side`` x ``side``
+    domain, as spheres (0, y, x, r) for point2_robot."""
+    rng = np.random.default_rng(seed)
+    lo = 0.5 * (side - centre)
+    xy = rng.uniform(lo, lo + centre, size=(count, 2))
+    sph = np.column_stack([np.zeros(count), xy[:, 1], xy[:, 0], np.full(count, r)])
+    return Env("forest", sph)
 
 
 def planar_disks_candidates(seed: int, count: int, lo: float = -2.5, hi: float = 2.5,

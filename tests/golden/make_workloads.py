@@ -15,6 +15,8 @@ collision-freeness needs a collision checker, checked by the FP64 oracle only.
 * dh7 batched scenes: 8 obstacle sets of 128-1024 spheres in the same cube
   and 256 seed paths of 1-40 segments built the same way (written only when
   ``--batched`` is given; slower).
+* forest scene: the point robot among 15 disks (Sec. V) and a seed path from
+  the bottom left to the top right corner (``--only-forest`` rewrites it).
 * table_cloud scene: 1024 spheres of r = 0.02 from a synthetic table point
   cloud and a 64-segment seed path that runs close to them (of 12
   collision-free candidate steps the one with the least clearance)
@@ -149,19 +151,49 @@ def stress_scene(seed=31, n_seg=64):
     return {"robot": "dh7", "cloud_seed": seed, "path": path.tolist()}
 
 
+def forest_scene(seed=41, step=1.0, margin=0.02, max_steps=80):
+    """Forest of Sec. V (15 disks of r = 0.35 in the central 7 x 7 square of
+    the 10 x 10 domain, point robot): a seed path from (0.5, 0.5) toward
+    (9.5, 9.5) in steps of ``step`` whose heading is the goal direction plus
+    N(0, 0.6) rad noise, each segment kept when its clearance (checked every
+    0.005) is at least ``margin``; the goal is appended once it is in reach
+    by a collision-free segment."""
+    robot = wl.point2_robot()
+    env = wl.forest_obstacles(seed)
+    rng = np.random.default_rng(seed + 1)
+    goal = np.array([9.5, 9.5])
+    verts = [np.array([0.5, 0.5])]
+    for _ in range(max_steps):
+        cur = verts[-1]
+        if np.linalg.norm(goal - cur) <= 1.5 and segment_clearance(robot, env, cur, goal) >= margin:
+            verts.append(goal)
+            break
+        for _ in range(200):
+            phi = math.atan2(*(goal - cur)[::-1]) + rng.normal(0.0, 0.6)
+            nxt = np.clip(cur + step * np.array([math.cos(phi), math.sin(phi)]), 0.2, 9.8)
+            if segment_clearance(robot, env, cur, nxt) >= margin:
+                verts.append(nxt)
+                break
+    assert np.allclose(verts[-1], goal)
+    return {"robot": "point2", "forest_seed": seed, "path": np.asarray(verts).tolist()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--batched", action="store_true")
     ap.add_argument("--stress", action="store_true")
     ap.add_argument("--only-stress", action="store_true", help="rewrite only the table_cloud scene")
+    ap.add_argument("--only-forest", action="store_true", help="rewrite only the forest scene")
     args = ap.parse_args()
     data = {}
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    if not args.only_stress:
+    if not args.only_stress and not args.only_forest:
         data["planar3"] = planar_scene()
         data["dh7"] = dh7_scene()
+    if not args.only_stress:
+        data["forest"] = forest_scene()
     if args.batched:
         data["dh7_batched"] = batched_scenes()
     if args.stress or args.only_stress:

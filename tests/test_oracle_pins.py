@@ -71,12 +71,13 @@ def _elementary_chain(r, q):
     """Independent construction: 4x4 products of the four elementary moves."""
     T = np.eye(4)
     out = [T.copy()]
+    prism = r.prismatic
     for i in range(r.n):
-        th = q[i] + r.theta_off[i]
+        th = r.theta_off[i] + (0.0 if prism[i] else q[i])
         Rz = np.eye(4)
         Rz[:2, :2] = [[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]]
         Tz = np.eye(4)
-        Tz[2, 3] = r.d[i]
+        Tz[2, 3] = r.d[i] + (q[i] if prism[i] else 0.0)
         Tx = np.eye(4)
         Tx[0, 3] = r.a[i]
         al = r.alpha[i]
@@ -87,7 +88,19 @@ def _elementary_chain(r, q):
     return out
 
 
-@pytest.mark.parametrize("robot", [wl.dh7_robot(), wl.planar3_robot()], ids=lambda r: r.name)
+def _mixed_robot():
+    """A 4-joint chain with prismatic joints 2 and 4 and non-zero offsets."""
+    r = wl.dh7_robot()
+    return wl.Robot(name="mixed", a=np.array([0.1, 0.0, 0.3, 0.05]), alpha=np.array([0.4, -1.2, 0.0, 0.7]),
+                    d=np.array([0.2, 0.1, 0.0, 0.3]), theta_off=np.array([0.3, -0.5, 0.1, 0.0]),
+                    q_lo=np.array([-2.0, 0.0, -2.0, -0.5]), q_hi=np.array([2.0, 1.0, 2.0, 0.5]),
+                    sphere_frame=r.sphere_frame[:0], sphere_xyz=r.sphere_xyz[:0], sphere_r=r.sphere_r[:0],
+                    sphere_link=r.sphere_link[:0], self_pairs=r.self_pairs[:0],
+                    joint_type=np.array([0, 1, 0, 1], dtype=np.int32))
+
+
+@pytest.mark.parametrize("robot", [wl.dh7_robot(), wl.planar3_robot(), _mixed_robot(), wl.point2_robot()],
+                         ids=lambda r: r.name)
 def test_dh_frames_match_elementary_products(robot):
     q = wl.uniform_configs(3, robot, 20)
     R, o = orc.dh_frames(robot, q)
@@ -465,3 +478,35 @@ def test_inflate_dh7_path_covers_every_segment():
     for k, res in out:
         assert res.status == 0
         assert orc.segment_contained(res.A, res.b, verts[k], verts[k + 1], tol=1e-12)
+
+
+# ------------------------------------------------------- Forest (Sec. V) ----
+def test_point_robot_and_forest_closed_forms():
+    """The point robot sits at (0, q_1, q_0); a configuration collides iff
+    its distance to a disk centre is below 0.35 (brute force over disks)."""
+    r = wl.point2_robot()
+    env = wl.forest_obstacles(41)
+    assert env.n_obs == 15 and np.all(env.spheres[:, 3] == 0.35)
+    assert np.all((env.spheres[:, 1:3] >= 1.5) & (env.spheres[:, 1:3] <= 8.5)) and np.all(env.spheres[:, 0] == 0)
+    q = wl.uniform_configs(5, r, 4000)
+    c = orc.sphere_centres(r, q)[:, 0, :]
+    np.testing.assert_allclose(c, np.column_stack([np.zeros(4000), q[:, 1], q[:, 0]]), atol=1e-12)
+    brute = np.zeros(4000, dtype=bool)
+    for i in range(4000):
+        for o in env.spheres:
+            if (q[i, 0] - o[2]) ** 2 + (q[i, 1] - o[1]) ** 2 < o[3] ** 2:
+                brute[i] = True
+    lab = orc.in_collision(r, env, q)
+    np.testing.assert_array_equal(lab, brute)
+    assert 0.05 < lab.mean() < 0.3
+
+
+def test_forest_seed_path_is_collision_free():
+    s = load_scene()["forest"]
+    r = wl.point2_robot()
+    env = wl.forest_obstacles(s["forest_seed"])
+    V = np.asarray(s["path"])
+    assert np.allclose(V[0], [0.5, 0.5]) and np.allclose(V[-1], [9.5, 9.5])
+    for k in range(V.shape[0] - 1):
+        t = np.linspace(0.0, 1.0, 2000)[:, None]
+        assert orc.signed_distance(r, env, V[k] + t * (V[k + 1] - V[k])).min() >= 0.02
