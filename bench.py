@@ -396,6 +396,53 @@ def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, fl
 
 
 
+def measure_forest(ezo, torch, stream, flush, props, sm_max, N=2_000_000, reps=10):
+    """Forest benchmark of Sec. V: the point robot among 15 disks of r = 0.35.
+    The collision checker on N uniform configurations (the paper's batch and
+    its 19.9 M configs/s on an RTX 3090), and the seed path inflated with the
+    paper's Forest parameters (eps = 0.01, delta = 0.05, N_p = 1000,
+    N_f = 10, N_ms = 30, Delta_max = 0.01), Philox seeds 1..5."""
+    from paper_2504_10783_gb300 import workloads as wl
+    with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+        s = json.load(f)["forest"]
+    rd, env_np, path = wl.point2_robot(), wl.forest_obstacles(s["forest_seed"]), np.asarray(s["path"])
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    q = 10.0 * torch.rand((2, N), generator=g, device="cuda")
+    flags = torch.empty(N, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ezo.check_collision(robot, env, q, flags)
+    ms = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        ms += _event_ms(torch, stream, lambda: ezo.check_collision(robot, env, q, flags))
+    per = ms / reps
+    flops_cfg = ezo.check_flops(robot, env)
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    K = path.shape[0] - 1
+    times, kept = [], []
+    for sd in range(1, 6):
+        prm = ezo.Params.make(eps=0.01, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, step_back_max=0.01,
+                              n_it_max=50, seed=sd)
+        bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm, seg_stream=np.arange(K, dtype=np.uint32),
+                       path_first=np.zeros(K, np.int32))
+        for _ in range(2):
+            bt.reset()
+            bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)
+        for _ in range(3):
+            flush.zero_()
+            times.append(_event_ms(torch, stream, lambda: (bt.reset(),
+                                                           bt.run_path(sequential=False, mode=ezo.RUN_GRAPH))))
+        kept.append(int(sum(bt.segment(k).status != ezo.SEG_SKIPPED for k in range(K))))
+    return {"checker": {"batch": N, "configs_per_s": N / (per / 1e3), "ms_per_launch": per,
+                        "roofline": {"bound": "alu", "achieved": N * flops_cfg / (per / 1e3) / 1e12, "peak": peak,
+                                     "unit": "TFLOP/s", "frac": N * flops_cfg / (per / 1e3) / 1e12 / peak},
+                        "paper_context": "paper: ~19.9 M configs/s in the Forest, RTX 3090, same batch size"},
+            "path": {"segments": K, "ms_median": float(np.median(times)), "ms_p90": float(np.percentile(times, 90)),
+                     "kept_segments": kept, "seeds": "1..5"},
+            "launches": 3 + reps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -569,8 +616,9 @@ def main():
         sur_info = measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args)
 
     # ---- the collision checker alone on the paper's batch size (2e6 configs) ----
-    checker = checker_1e8 = {"launches": 0}
+    checker = checker_1e8 = forest = {"launches": 0}
     if not args.no_extras:
+        forest = measure_forest(ezo, torch, stream, flush, props, sm_max)
         checker = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg)
         checker_1e8 = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg,
                                       N=100_000_000, reps=3)
@@ -614,9 +662,10 @@ def main():
                        "ms_per_10_segment_path": ms / args.steps,
                        "ms_p50": float(np.percentile(times, 50)), "ms_p90": float(np.percentile(times, 90)),
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "checker_1e8": checker_1e8, "e2e": e2e,
+            "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "checker_1e8": checker_1e8, "forest": forest, "e2e": e2e,
             "gpu_launches": launches,
-            "gpu_launches_outside_timed_region": other_launches + checker["launches"] + checker_1e8["launches"],
+            "gpu_launches_outside_timed_region": other_launches + checker["launches"] + checker_1e8["launches"] +
+            forest["launches"],
             "clocks": clocks}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args.seconds)

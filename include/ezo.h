@@ -94,7 +94,11 @@ const char* ezo_last_error(void);
  * geometry, as in a URDF), restricted to a serial chain in standard DH form
  * with sphere geometries (Sec. IV-D: sphere and box geometries; boxes are not
  * supported here). Frame 0 is the base; frame i (1..n) is
- *   T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i).
+ *   T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i)
+ * for a revolute joint and
+ *   T_i = T_{i-1} Rz(theta_off_i) Tz(d_i + q_i) Tx(a_i) Rx(alpha_i)
+ * for a prismatic one (joint_type[i-1] = 1; joint_type NULL = all revolute;
+ * two prismatic joints make the point robot of the Forest benchmark, Sec. V).
  * n <= 16 joints. Sphere s (n_spheres <= 256) sits at sphere_xyz[3s..3s+2] in
  * frame sphere_frame[s] (0..n) with radius sphere_r[s] >= 0. self_pairs holds
  * n_self_pairs pairs (i, j) of sphere indices tested against each other
@@ -106,7 +110,7 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
                             const double* theta_off, const double* q_lo, const double* q_hi,
                             int32_t n_spheres, const int32_t* sphere_frame, const double* sphere_xyz,
                             const double* sphere_r, int32_t n_self_pairs, const int32_t* self_pairs,
-                            ezo_robot** out);
+                            const int32_t* joint_type, ezo_robot** out);
 void ezo_robot_free(ezo_robot* robot);
 int32_t ezo_robot_dof(const ezo_robot* robot);
 

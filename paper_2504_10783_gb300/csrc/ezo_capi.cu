@@ -83,6 +83,7 @@ struct ezo_robot {
   std::vector<double> q_lo, q_hi;
   double reach = 0.0, r_max = 0.0;
   double fk_flops = 0.0;
+  bool prismatic = false;  // any prismatic joint
 };
 
 struct ezo_env {
@@ -123,7 +124,8 @@ const char* ezo_last_error(void) { return g_err.c_str(); }
 ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, const double* d,
                             const double* theta_off, const double* q_lo, const double* q_hi, int32_t n_spheres,
                             const int32_t* sphere_frame, const double* sphere_xyz, const double* sphere_r,
-                            int32_t n_self_pairs, const int32_t* self_pairs, ezo_robot** out) {
+                            int32_t n_self_pairs, const int32_t* self_pairs, const int32_t* joint_type,
+                            ezo_robot** out) {
   if (!out) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: out is NULL");
   *out = nullptr;
   if (n < 1 || n > EZO_MAX_DOF) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: n must be in [1, 16]");
@@ -142,8 +144,11 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
   for (int p = 0; p < 2 * n_self_pairs; ++p)
     if (self_pairs[p] < 0 || self_pairs[p] >= n_spheres)
       return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: self pair index out of range");
-  for (int j = 0; j < n; ++j)
+  for (int j = 0; j < n; ++j) {
     if (!(q_lo[j] <= q_hi[j])) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: q_lo > q_hi");
+    if (joint_type && joint_type[j] != 0 && joint_type[j] != 1)
+      return fail(EZO_ERR_INVALID_ARG, "ezo_robot_create: joint_type must be 0 (revolute) or 1 (prismatic)");
+  }
 
   ezo_robot* r = new ezo_robot();
   r->n = n;
@@ -164,7 +169,12 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
     h.a[j] = (float)a[j];
     h.d[j] = (float)d[j];
     h.toff[j] = theta_off ? (float)theta_off[j] : 0.f;
-    chain += std::fabs(a[j]) + std::fabs(d[j]);
+    const bool prism = joint_type && joint_type[j] == 1;
+    h.kth[j] = prism ? 0.f : 1.f;
+    h.kd[j] = prism ? 1.f : 0.f;
+    r->prismatic = r->prismatic || prism;
+    // the farthest a sphere can get from the base bounds the rounding band
+    chain += std::fabs(a[j]) + std::fabs(d[j]) + (prism ? std::max(std::fabs(q_lo[j]), std::fabs(q_hi[j])) : 0.0);
   }
   // sort spheres by frame (stable) so the chain walk can emit them in order
   std::vector<int> order(n_spheres);
@@ -397,6 +407,10 @@ __attribute__((visibility("hidden"))) int ezo_internal_env_dev(const ezo_robot* 
 }
 
 __attribute__((visibility("hidden"))) void ezo_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
+__attribute__((visibility("hidden"))) int ezo_internal_robot_prismatic(const ezo_robot* r) {
+  return r && r->prismatic ? 1 : 0;
+}
 
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env) {
   if (!robot || !env) return 0.0;
@@ -694,6 +708,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
       return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: seg_env out of range");
     }
     s.stream = seg_stream ? seg_stream[g] : (uint32_t)g;
+    s.box_rows = A0 ? 0 : 2 * n;  // the sampler skips the dot products of the joint-box rows
     s.s_cap = std::max(s.n_p, m_last);
     s.sample_off = b->total_s;
     s.cand_off = b->total_c;
@@ -1179,6 +1194,8 @@ ezo_status ezo_batch_set_polytope(ezo_batch* b, int32_t seg, int32_t m, const do
     EZO_CUDA(cudaMemcpyAsync(b->d_b + (size_t)seg * b->m_cap, bb, sizeof(double) * m, cudaMemcpyHostToDevice, s));
   }
   EZO_CUDA(cudaMemcpyAsync(&b->d_st[seg].m, &m, sizeof(int), cudaMemcpyHostToDevice, s));
+  const int no_box = 0;  // rows 0..2n-1 are no longer known to be the joint box
+  EZO_CUDA(cudaMemcpyAsync(&b->d_st[seg].box_rows, &no_box, sizeof(int), cudaMemcpyHostToDevice, s));
   EZO_CUDA(cudaStreamSynchronize(s));
   return EZO_OK;
 }

@@ -58,6 +58,9 @@ struct RobotDev {
   int n_spheres_pad;  // multiple of EZO_CH; padding spheres never collide
   int n_self;         // listed self pairs
   float ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
+  // joint j turns by kth_j q_j + toff_j and slides by d_j + kd_j q_j:
+  // (kth, kd) = (1, 0) for a revolute joint, (0, 1) for a prismatic one
+  float kth[EZO_MAX_DOF], kd[EZO_MAX_DOF];
   int frame_first[EZO_MAX_DOF + 2];  // sorted spheres of frame f: [frame_first[f], frame_first[f+1])
   float4 sph[EZO_MAX_SPHERES];       // local x, y, z and radius (sorted by frame)
   const ushort2* self_pairs;         // [n_self] indices into the sorted spheres
@@ -73,6 +76,7 @@ struct RobotDev {
 // The part of RobotDev a block keeps in shared memory.
 struct RobotSmem {
   float ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
+  float kth[EZO_MAX_DOF], kd[EZO_MAX_DOF];
   int frame_first[EZO_MAX_DOF + 2];
   int n, n_spheres, n_spheres_pad, n_self;
   int n_sblk;
@@ -87,6 +91,8 @@ __device__ __forceinline__ void stage_robot(RobotSmem& rs, float4* sph_s, const 
     rs.a[i] = rd->a[i];
     rs.d[i] = rd->d[i];
     rs.toff[i] = rd->toff[i];
+    rs.kth[i] = rd->kth[i];
+    rs.kd[i] = rd->kd[i];
   }
   for (int i = threadIdx.x; i < EZO_MAX_DOF + 2; i += blockDim.x) rs.frame_first[i] = rd->frame_first[i];
   for (int i = threadIdx.x; i < EZO_MAX_SBLK; i += blockDim.x) rs.sblk[i] = rd->sblk[i];
@@ -156,7 +162,7 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
     for (int j = 0; j < NDOF; ++j) {
       sj[j] = 0.f;
       cj[j] = 1.f;
-      if (j < n) sincosf(q[j] + rs.toff[j], &sj[j], &cj[j]);
+      if (j < n) sincosf(fmaf(q[j], rs.kth[j], rs.toff[j]), &sj[j], &cj[j]);
     }
   } else {
     constexpr int JPL = (NDOF + T - 1) / T;
@@ -167,7 +173,7 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
       float ang = 0.f;
 #pragma unroll
       for (int j = 0; j < NDOF; ++j)
-        if (j == jm && j < n) ang = q[j] + rs.toff[j];
+        if (j == jm && j < n) ang = fmaf(q[j], rs.kth[j], rs.toff[j]);
       sincosf(ang, &ms[k], &mc[k]);
     }
 #pragma unroll
@@ -186,7 +192,7 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
       const float n0x = fmaf(c, c0x, s * c1x), n0y = fmaf(c, c0y, s * c1y), n0z = fmaf(c, c0z, s * c1z);
       const float n1x = fmaf(c, c1x, -s * c0x), n1y = fmaf(c, c1y, -s * c0y), n1z = fmaf(c, c1z, -s * c0z);
       // o_{j+1} = o_j + a col0' + d col2
-      const float aj = rs.a[j], dj = rs.d[j];
+      const float aj = rs.a[j], dj = fmaf(q[j], rs.kd[j], rs.d[j]);
       px = fmaf(aj, n0x, fmaf(dj, c2x, px));
       py = fmaf(aj, n0y, fmaf(dj, c2y, py));
       pz = fmaf(aj, n0z, fmaf(dj, c2z, pz));
@@ -356,10 +362,10 @@ __device__ float signed_distance_one(const float* __restrict__ q, const RobotSme
     if (f > 0) {
       const int j = f - 1;
       float s, c;
-      sincosf(q[j] + rs.toff[j], &s, &c);
+      sincosf(fmaf(q[j], rs.kth[j], rs.toff[j]), &s, &c);
       const float n0x = fmaf(c, c0x, s * c1x), n0y = fmaf(c, c0y, s * c1y), n0z = fmaf(c, c0z, s * c1z);
       const float n1x = fmaf(c, c1x, -s * c0x), n1y = fmaf(c, c1y, -s * c0y), n1z = fmaf(c, c1z, -s * c0z);
-      const float aj = rs.a[j], dj = rs.d[j];
+      const float aj = rs.a[j], dj = fmaf(q[j], rs.kd[j], rs.d[j]);
       px = fmaf(aj, n0x, fmaf(dj, c2x, px));
       py = fmaf(aj, n0y, fmaf(dj, c2y, py));
       pz = fmaf(aj, n0z, fmaf(dj, c2z, pz));

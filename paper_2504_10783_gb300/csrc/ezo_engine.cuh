@@ -36,7 +36,7 @@ struct SegState {
   int n_p;        // N_p of this segment
   int env;        // obstacle set
   uint32_t stream;  // Philox stream id (counter word 3)
-  int pad0;
+  int box_rows;     // 2n when rows 0..2n-1 are the joint box (+e_j <= hi_j, then -e_j <= -lo_j), else 0
   long long checks;      // exact collision checks so far
   long long sample_off;  // first sample slot of this segment
   long long cand_off;    // first candidate slot

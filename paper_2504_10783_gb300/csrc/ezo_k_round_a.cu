@@ -81,11 +81,8 @@ __global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
   }
 }
 
-// Hit-and-run for every active segment. When the round has few walks (few
-// active segments) eight lanes share each walk, which cuts the latency of the
-// sequential N_ms steps; otherwise each lane runs one walk. The choice is made
-// on the device from the round's tile count, so it also works inside a graph.
-// A 128-thread block covers a tile of kTile walks in one or eight passes.
+// One pass of a 128-thread block over a tile of kTile walks at TSS lanes per
+// walk (a tile takes TSS passes); writes the samples dimension-major.
 template <int NDOF, int TSS>
 __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& st, const float* A32,
                                             const SampleParams& p, int2 tile, int pass) {
@@ -96,11 +93,12 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
   float x[NDOF];
   if (TSS == 1) {
     if (i >= st.n_samples) return;
-    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
+    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x,
+                   st.box_rows);
   } else {
     const int ic = i < st.n_samples ? i : tile.y;
     hnr_walk_split<NDOF, TSS>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)ic, p.round_k,
-                              p.stream, lw, x);
+                              p.stream, lw, x, st.box_rows);
     if (i >= st.n_samples || lw != 0) return;
   }
 #pragma unroll
@@ -113,18 +111,20 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
 // the sequential N_ms steps and fills the GPU; with many walks each lane runs
 // one. The choice is made on the device from the round's tile count, so it
 // also works inside a graph. Work units are (tile, pass) pairs: a tile of
-// kTile walks takes one pass at one lane per walk, or 2 or 8 passes at 2 or 8
-// lanes per walk, and the passes of a tile go to different blocks.
+// kTile walks takes one pass at one lane per walk, or 2, 4 or 8 passes at 2,
+// 4 or 8 lanes per walk, and the passes of a tile go to different blocks.
 template <int NDOF>
 __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_below_tiles) {
   extern __shared__ float4 smf4[];
   __shared__ SampleParams p;
   __shared__ int cur_seg;
   const int n_tiles = v.summary->n_sample_tiles;
-  // eight lanes per walk below the threshold, two up to eight times it,
-  // one above (more walks than the GPU holds warps)
+  // S = split_below_tiles tiles of 128 walks at 4 warps per SM scheduler
+  // fill the GPU with one lane per walk; measured on the 7-DOF arm, one lane
+  // is fastest from 1.5 S tiles up, two from S / 2, four from S / 8
+  const int S = split_below_tiles;
   const int passes = v.sample_lanes ? v.sample_lanes
-                                    : (n_tiles < split_below_tiles ? 8 : (n_tiles < 8 * split_below_tiles ? 2 : 1));
+                                    : (2 * n_tiles >= 3 * S ? 1 : (2 * n_tiles >= S ? 2 : (8 * n_tiles >= S ? 4 : 8)));
   float* A32 = reinterpret_cast<float*>(smf4);
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();

@@ -89,11 +89,36 @@ __device__ __forceinline__ void chord_rows(const float* __restrict__ A32, int r0
   }
 }
 
+// The same chord bounds for the joint-box rows 0..2n-1 (row j: +e_j x <= hi_j,
+// row n + j: -e_j x <= -lo_j) without their dot products: with a = +-e_j the
+// general rows compute a^T x = +-x_j and a^T d = +-d_j exactly, so the slack,
+// the ratio and the bounds below are bit for bit theirs.
+template <int NDOF>
+__device__ __forceinline__ void chord_box(const float* __restrict__ A32, int n, const float (&x)[NDOF],
+                                          const float (&d)[NDOF], float& t_lo, float& t_hi) {
+  constexpr int RS = hnr_row_stride<NDOF>();
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    if (j < n) {
+      const float q1 = __fdividef(A32[j * RS + NDOF] - x[j], d[j]);
+      const float q2 = __fdividef(A32[(n + j) * RS + NDOF] + x[j], -d[j]);
+      if (d[j] > 0.f) {
+        t_hi = fminf(t_hi, q1);
+        t_lo = fmaxf(t_lo, q2);
+      }
+      if (d[j] < 0.f) {
+        t_lo = fmaxf(t_lo, q1);
+        t_hi = fminf(t_hi, q2);
+      }
+    }
+  }
+}
+
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
                                          uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
-                                         float (&x)[NDOF]) {
+                                         float (&x)[NDOF], int box_rows = 0) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
   const int npair = (n + 1) / 2;
   const int W = max(1, (2 * npair + 3) / 4);
@@ -132,7 +157,8 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    chord_rows<NDOF>(A32, 0, m, 1, x, d, t_lo, t_hi);
+    if (box_rows) chord_box<NDOF>(A32, n, x, d, t_lo, t_hi);
+    chord_rows<NDOF>(A32, box_rows, m, 1, x, d, t_lo, t_hi);
     t_hi = fmaxf(t_hi, 0.f);
     t_lo = fminf(t_lo, 0.f);
     if (ok && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
@@ -155,7 +181,7 @@ template <int NDOF, int TS>
 __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, int m, int n, const float* v1f,
                                                const float* ef, int n_mix, uint32_t key0, uint32_t key1,
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
-                                               float (&x)[NDOF]) {
+                                               float (&x)[NDOF], int box_rows = 0) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
   constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
   const int npair = (n + 1) / 2;
@@ -201,7 +227,8 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    chord_rows<NDOF>(A32, lw, m, TS, x, d, t_lo, t_hi);
+    if (box_rows) chord_box<NDOF>(A32, n, x, d, t_lo, t_hi);  // every lane: cheap, and min/max repeat safely
+    chord_rows<NDOF>(A32, box_rows + lw, m, TS, x, d, t_lo, t_hi);
 #pragma unroll
     for (int o = 1; o < TS; o <<= 1) {
       t_hi = fminf(t_hi, __shfl_xor_sync(0xffffffffu, t_hi, o, TS));

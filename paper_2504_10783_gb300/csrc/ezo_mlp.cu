@@ -326,6 +326,7 @@ cudaError_t dal(T** p, size_t n) {
 
 }  // namespace
 
+extern "C" int ezo_internal_robot_prismatic(const ezo_robot* r);
 extern "C" void ezo_internal_set_error(const char* msg);
 extern "C" const ezo::RobotDev* ezo_internal_robot_dev(const ezo_robot* r, int* n, int* nsp_pad, double* q_lo,
                                                        double* q_hi);
@@ -509,6 +510,11 @@ ezo_status ezo_surrogate_create(const ezo_robot* robot, uint64_t seed, ezo_surro
   ezo_internal_robot_dev(robot, &n, &nsp, lo, hi);
   if (2 * n > kF) {
     ezo_internal_set_error("ezo_surrogate_create: 2 n features must fit in 64");
+    return EZO_ERR_INVALID_ARG;
+  }
+  if (ezo_internal_robot_prismatic(robot)) {
+    // the features sin q, cos q identify revolute joint angles only
+    ezo_internal_set_error("ezo_surrogate_create: prismatic joints are not supported by the [sin q, cos q] features");
     return EZO_ERR_INVALID_ARG;
   }
   ezo_surrogate* S = new ezo_surrogate();

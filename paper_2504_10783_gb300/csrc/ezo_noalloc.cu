@@ -173,6 +173,7 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   s0.n_p = np;
   s0.env = 0;
   s0.stream = stream_id;
+  s0.box_rows = 2 * n;  // the domain built below is the joint box
   s0.s_cap = (int)s_cap;
   std::vector<double> A0((size_t)m0 * n, 0.0), b0(m0, 0.0);
   for (int j = 0; j < n; ++j) {

@@ -58,7 +58,7 @@ def _sig(lib):
     f.ezo_last_error.restype = C.c_char_p
     f.ezo_params_default.argtypes = [C.POINTER(Params)]
     f.ezo_robot_create.argtypes = [_I32, _DP, _DP, _DP, _DP, _DP, _DP, _I32, C.POINTER(_I32), _DP, _DP, _I32,
-                                   C.POINTER(_I32), C.POINTER(_P)]
+                                   C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_P)]
     f.ezo_robot_free.argtypes = [_P]
     f.ezo_robot_dof.argtypes = [_P]
     f.ezo_env_create.argtypes = [_I32, _DP, C.POINTER(_P)]
@@ -162,12 +162,13 @@ class Robot:
         i32 = lambda x: np.ascontiguousarray(x, dtype=np.int32)
         self._keep = [f64(r.a), f64(r.alpha), f64(r.d), f64(r.theta_off), f64(r.q_lo), f64(r.q_hi),
                       i32(r.sphere_frame), f64(r.sphere_xyz.reshape(-1)), f64(r.sphere_r),
-                      i32(r.self_pairs.reshape(-1))]
+                      i32(r.self_pairs.reshape(-1)),
+                      i32(r.joint_type) if getattr(r, "joint_type", None) is not None else None]
         k = self._keep
         h = _P()
         _check(lib().ezo_robot_create(r.n, _dp(k[0]), _dp(k[1]), _dp(k[2]), _dp(k[3]), _dp(k[4]), _dp(k[5]),
                                       r.n_spheres, _ip(k[6]), _dp(k[7]), _dp(k[8]), r.self_pairs.shape[0],
-                                      _ip(k[9]), C.byref(h)))
+                                      _ip(k[9]), _ip(k[10]) if k[10] is not None else None, C.byref(h)))
         self.h = h
         self.n = r.n
 

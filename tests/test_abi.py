@@ -48,7 +48,7 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     out = ctypes.c_void_p()
     st = ezo.lib().ezo_env_create(-1, None, ctypes.byref(out))
     assert st == 1 and not out.value
-    st = ezo.lib().ezo_robot_create(0, None, None, None, None, None, None, 0, None, None, None, 0, None,
+    st = ezo.lib().ezo_robot_create(0, None, None, None, None, None, None, 0, None, None, None, 0, None, None,
                                     ctypes.byref(out))
     assert st == 1
     assert b"n must be" in ezo.lib().ezo_last_error()

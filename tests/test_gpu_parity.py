@@ -302,6 +302,84 @@ def test_round_replay_dh7(ezo):
     assert rounds >= 2
 
 
+# ------------------------------------------------------- Forest (Sec. V) --
+FOREST_PRM = dict(eps=0.01, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, step_back_max=0.01)
+
+
+def forest_scene():
+    s = scenes()["forest"]
+    return wl.point2_robot(), wl.forest_obstacles(s["forest_seed"]), np.asarray(s["path"])
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+def test_forest_labels_match_oracle(ezo, lanes):
+    """Point robot (two prismatic joints) among 15 disks: labels exact
+    except within 1e-5 of a disk boundary."""
+    rd, env_np, _ = forest_scene()
+    q = wl.uniform_configs(21, rd, 200000)
+    got = gpu_labels(ezo, ezo.Robot(rd), ezo.Env(env_np), q, lanes=lanes)
+    ref = assert_labels_match(rd, env_np, q.astype(np.float32), got)
+    assert 0.05 < ref.mean() < 0.3
+
+
+def test_prismatic_chain_signed_distance_matches_oracle(ezo):
+    """A 4-joint chain with two prismatic joints and offsets: the GPU's
+    forward kinematics, through the signed distance, against the oracle."""
+    base = wl.dh7_robot()
+    rd = wl.Robot(name="mixed", a=np.array([0.1, 0.0, 0.3, 0.05]), alpha=np.array([0.4, -1.2, 0.0, 0.7]),
+                  d=np.array([0.2, 0.1, 0.0, 0.3]), theta_off=np.array([0.3, -0.5, 0.1, 0.0]),
+                  q_lo=np.array([-2.0, 0.0, -2.0, -0.5]), q_hi=np.array([2.0, 1.0, 2.0, 0.5]),
+                  sphere_frame=np.array([1, 2, 2, 3, 4, 4], dtype=np.int32),
+                  sphere_xyz=np.array([[0, 0, 0.1], [0.1, 0, 0], [0, 0.1, 0], [0, 0, 0], [0.05, 0, 0], [0, 0, 0.05]]),
+                  sphere_r=np.full(6, 0.05), sphere_link=np.array([1, 2, 2, 3, 4, 4], dtype=np.int32),
+                  self_pairs=np.array([[0, 4], [0, 5]], dtype=np.int32),
+                  joint_type=np.array([0, 1, 0, 1], dtype=np.int32))
+    env_np = wl.box_obstacles(4, 64, box_lo=(-0.6, -0.6, -0.2), box_hi=(0.6, 0.6, 1.0))
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    q = wl.uniform_configs(22, rd, 20000)
+    sd = torch.empty(q.shape[0], device="cuda")
+    ezo.signed_distance(robot, env, to_dev(q), sd)
+    torch.cuda.synchronize()
+    ref = orc.signed_distance(rd, env_np, q.astype(np.float32).astype(np.float64))
+    assert np.abs(sd.cpu().numpy() - ref).max() <= 2e-5
+    got = gpu_labels(ezo, robot, env, q)
+    lab = assert_labels_match(rd, env_np, q.astype(np.float32), got)
+    assert 0.05 < lab.mean() < 0.95
+
+
+def test_round_replay_forest(ezo):
+    rd, env_np, path = forest_scene()
+    k = int(np.argmax(np.linalg.norm(np.diff(path, axis=0), axis=1)))
+    rounds, _ = _replay_rounds(ezo, rd, env_np, path[k], path[k + 1], dict(FOREST_PRM, seed=3), max_rounds=5)
+    assert rounds >= 1
+
+
+def test_forest_path_polytopes_contain_segments_and_certify(ezo):
+    """The whole Forest seed path with the paper's Forest parameters: every
+    kept polytope is accepted, holds its segment, and an independent uniform
+    sample of it collides at a rate within eps (binomial 4-sigma margin)."""
+    rd, env_np, path = forest_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    K = path.shape[0] - 1
+    bt = ezo.Batch(robot, [env], path[:-1], path[1:], ezo.Params.make(**dict(FOREST_PRM, seed=7)),
+                   seg_stream=np.arange(K, dtype=np.uint32), path_first=np.zeros(K, np.int32))
+    bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)
+    rng = np.random.default_rng(8)
+    kept = 0
+    for g in range(K):
+        r = bt.segment(g)
+        if r.status == ezo.SEG_SKIPPED:
+            continue
+        kept += 1
+        assert r.status == ezo.SEG_ACCEPTED
+        assert orc.segment_contained(r.A, r.b, path[g], path[g + 1], tol=1e-12)
+        x = rng.uniform(rd.q_lo, rd.q_hi, size=(200000, 2))
+        x = x[np.all(x @ r.A.T <= r.b, axis=1)][:20000]
+        rate = orc.in_collision(rd, env_np, x).mean()
+        assert rate <= FOREST_PRM["eps"] + 4 * np.sqrt(FOREST_PRM["eps"] / x.shape[0])
+    assert bt.coverage().all() and kept >= 1
+
+
 # ------------------------------------------------------------- end to end --
 def test_inflate_segment_certified_planar(ezo):
     rd, env_np, v1, v2 = planar_scene()
