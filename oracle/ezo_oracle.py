@@ -22,6 +22,10 @@ by step in float64, written for a reader to check against the paper:
 * greedy, sorted hyperplane placement with at most N_f faces per iteration:
   Sec. IV-B and the parameter tables of the appendix;
 * path inflation with the containment skip: Sec. VI-A;
+* box collision geometries (Sec. IV-D: the checker supports boxes and
+  spheres; Sec. VII: an arm described by 11 boxes): sphere-box distance and
+  the separating-axis test for box pairs, for robot boxes, obstacle boxes and
+  listed self pairs;
 * recovery from detected collisions: fine discretisation of a path and its
   collision check, set editing with the last steps of Algorithm 1 on given
   collisions that lie in the set, and the coverage test of the seed path:
@@ -44,6 +48,9 @@ parameter or a documented choice of the CUDA library):
   discarded when a^T c_j > b - Delta for a row added this round;
 * a segment L_k is skipped when both its endpoints satisfy A x <= b + 1e-9 for
   an earlier polytope.
+* box-box pairs skip cross-product axes of edges within ~0.6 degrees of
+  parallel (|a x b|^2 < 1e-4); a point of radius 0 overlaps a box only when
+  strictly inside it;
 * a path edge is cut into N_k = max(1, ceil(|e|_2 / step)) equal pieces and
   checked at all N_k + 1 points; a set is edited with the given collisions
   that satisfy A c <= b + 1e-9, the first N_p by index, without a test.
@@ -169,6 +176,105 @@ def sphere_centres(robot, q) -> np.ndarray:
     return np.einsum("nsij,sj->nsi", R[:, f], robot.sphere_xyz) + o[:, f]
 
 
+def box_poses(robot, q):
+    """World centres [N, B, 3] and rotations [N, B, 3, 3] (columns = box
+    axes) of the robot's boxes."""
+    R, o = dh_frames(robot, q)
+    f = robot.box_frame
+    c = np.einsum("nbij,bj->nbi", R[:, f], robot.box_xyz) + o[:, f]
+    rot = np.einsum("nbij,bjk->nbik", R[:, f], robot.box_rot)
+    return c, rot
+
+
+def sphere_box_distance(c, r, bc, bR, bh):
+    """Signed distance from a sphere (centre c, radius r) to an oriented box
+    (centre bc, axes the columns of bR, half extents bh): the point's signed
+    distance to the box minus r; broadcasts over leading dimensions. Outside
+    the box the point distance is the norm of max(|p| - h, 0) with p the centre
+    in box coordinates; inside it is the largest |p_i| - h_i (negative). The
+    sphere and the box overlap iff the result is negative."""
+    p = np.einsum("...ji,...j->...i", bR, c - bc)
+    qv = np.abs(p) - bh
+    outside = np.sqrt(np.sum(np.maximum(qv, 0.0) ** 2, axis=-1))
+    inside = np.minimum(np.max(qv, axis=-1), 0.0)
+    return outside + inside - r
+
+
+BOX_EDGE_SKIP = 1e-4  # edge-edge axes with |a x b|^2 below this are not tested
+
+
+def box_box_separation(ca, Ra, ha, cb, Rb, hb):
+    """Separating-axis test of two oriented boxes (Gottschalk et al., OBBTree,
+    SIGGRAPH'96): the largest over the candidate axes L (the three axes of
+    each box and the nine cross products of one axis of each, normalised) of
+    |(cb - ca) . L| - sum_k ha_k |a_k . L| - sum_k hb_k |b_k . L|. Cross
+    products with |a x b|^2 < BOX_EDGE_SKIP (edges within ~0.6 degrees of
+    parallel) are left out; the face axes cover those contacts up to a gap of
+    edge length x 0.01. The boxes overlap iff the result is negative (then no
+    axis separates them); when positive it is a lower bound of their
+    distance. Broadcasts over leading dimensions."""
+    T = cb - ca
+    axes = [Ra[..., :, k] for k in range(3)] + [Rb[..., :, k] for k in range(3)]
+    best = None
+    cand = []
+    for L in axes:
+        cand.append((L, None))
+    for i in range(3):
+        for j in range(3):
+            L = np.cross(Ra[..., :, i], Rb[..., :, j])
+            n2 = np.sum(L * L, axis=-1)
+            cand.append((L / np.sqrt(np.maximum(n2, 1e-300))[..., None], n2 >= BOX_EDGE_SKIP))
+    for L, ok in cand:
+        proj = np.abs(np.sum(T * L, axis=-1))
+        ra = sum(ha[..., k] * np.abs(np.sum(Ra[..., :, k] * L, axis=-1)) for k in range(3))
+        rb = sum(hb[..., k] * np.abs(np.sum(Rb[..., :, k] * L, axis=-1)) for k in range(3))
+        sep = proj - ra - rb
+        if ok is not None:
+            sep = np.where(ok, sep, -np.inf)
+        best = sep if best is None else np.maximum(best, sep)
+    return best
+
+
+def _box_pair_min(robot, env, c, rc, bc, bR):
+    """Smallest pair value over the pairs that involve a box: robot spheres x
+    obstacle boxes, robot boxes x obstacle spheres and boxes, and the listed
+    sphere-box and box-box self pairs (sphere_box_distance and
+    box_box_separation; negative iff that pair overlaps)."""
+    N = c.shape[0]
+    m = np.full(N, np.inf)
+    eb = env.boxes if getattr(env, "boxes", None) is not None else np.zeros((0, 15))
+    ec, eh, eR = eb[:, 0:3], eb[:, 3:6], eb[:, 6:15].reshape(-1, 3, 3)
+    if c.shape[1] and eb.shape[0]:
+        d = sphere_box_distance(c[:, :, None, :], rc[None, :, None], ec[None, None], eR[None, None], eh[None, None])
+        m = np.minimum(m, d.min(axis=(1, 2)))
+    if bc is not None and bc.shape[1]:
+        bh = robot.box_half
+        obs = np.asarray(env.spheres, dtype=np.float64)
+        if obs.shape[0]:
+            d = sphere_box_distance(obs[None, None, :, :3], obs[None, None, :, 3], bc[:, :, None, :],
+                                    bR[:, :, None], bh[None, :, None, :])
+            m = np.minimum(m, d.min(axis=(1, 2)))
+        if eb.shape[0]:
+            sep = box_box_separation(bc[:, :, None, :], bR[:, :, None], bh[None, :, None, :], ec[None, None],
+                                     eR[None, None], eh[None, None])
+            m = np.minimum(m, sep.min(axis=(1, 2)))
+        sb = robot.self_sb if robot.self_sb is not None else np.zeros((0, 2), dtype=np.int32)
+        if sb.shape[0]:
+            d = sphere_box_distance(c[:, sb[:, 0]], rc[sb[:, 0]][None], bc[:, sb[:, 1]], bR[:, sb[:, 1]],
+                                    bh[sb[:, 1]][None])
+            m = np.minimum(m, d.min(axis=1))
+        bbp = robot.self_bb if robot.self_bb is not None else np.zeros((0, 2), dtype=np.int32)
+        if bbp.shape[0]:
+            sep = box_box_separation(bc[:, bbp[:, 0]], bR[:, bbp[:, 0]], bh[bbp[:, 0]][None], bc[:, bbp[:, 1]],
+                                     bR[:, bbp[:, 1]], bh[bbp[:, 1]][None])
+            m = np.minimum(m, sep.min(axis=1))
+    return m
+
+
+def _has_boxes(robot, env) -> bool:
+    return bool(getattr(robot, "n_boxes", 0)) or bool(getattr(env, "boxes", None) is not None and len(env.boxes))
+
+
 def _chunks(N: int, size: int):
     for s in range(0, N, size):
         yield s, min(N, s + size)
@@ -195,13 +301,18 @@ def in_collision(robot, env, q, chunk: int = 512) -> np.ndarray:
             diff = c[:, sp[:, 0]] - c[:, sp[:, 1]]
             d2 = np.einsum("npk,npk->np", diff, diff)
             hit |= (d2 < ((r[sp[:, 0]] + r[sp[:, 1]]) ** 2)[None]).any(axis=1)
+        if _has_boxes(robot, env):
+            bc, bR = box_poses(robot, q[s:e]) if getattr(robot, "n_boxes", 0) else (None, None)
+            hit |= _box_pair_min(robot, env, c, r, bc, bR) < 0.0
         out[s:e] = hit
     return out
 
 
 def signed_distance(robot, env, q, chunk: int = 512) -> np.ndarray:
     """Smallest ||c_i - c_j|| - r_i - r_j over all obstacle and self pairs
-    (negative iff the configuration is in collision)."""
+    (negative iff the configuration is in collision). Pairs with a box add
+    sphere_box_distance (exact) and box_box_separation (its sign decides the
+    label; when positive a lower bound of the distance)."""
     q = np.atleast_2d(np.asarray(q, dtype=np.float64))
     out = np.full(q.shape[0], np.inf)
     obs = np.asarray(env.spheres, dtype=np.float64)
@@ -210,7 +321,7 @@ def signed_distance(robot, env, q, chunk: int = 512) -> np.ndarray:
     for s, e in _chunks(q.shape[0], chunk):
         c = sphere_centres(robot, q[s:e])
         m = np.full(e - s, np.inf)
-        if obs.shape[0]:
+        if obs.shape[0] and c.shape[1]:
             diff = c[:, :, None, :] - obs[None, None, :, :3]
             dist = np.sqrt(np.einsum("nsok,nsok->nso", diff, diff))
             m = np.minimum(m, (dist - r[None, :, None] - obs[None, None, :, 3]).min(axis=(1, 2)))
@@ -218,6 +329,9 @@ def signed_distance(robot, env, q, chunk: int = 512) -> np.ndarray:
             diff = c[:, sp[:, 0]] - c[:, sp[:, 1]]
             dist = np.sqrt(np.einsum("npk,npk->np", diff, diff))
             m = np.minimum(m, (dist - (r[sp[:, 0]] + r[sp[:, 1]])[None]).min(axis=1))
+        if _has_boxes(robot, env):
+            bc, bR = box_poses(robot, q[s:e]) if getattr(robot, "n_boxes", 0) else (None, None)
+            m = np.minimum(m, _box_pair_min(robot, env, c, r, bc, bR))
         out[s:e] = m
     return out
 

@@ -36,6 +36,10 @@ __all__ = [
     "random_walk_waypoints",
     "point2_robot",
     "forest_obstacles",
+    "rot_zyx",
+    "box_row",
+    "box_arm_robot",
+    "tabletop_box_env",
 ]
 
 
@@ -50,6 +54,8 @@ class Robot:
     for a prismatic one (``joint_type[i-1] == 1``).
     Sphere s sits at ``sphere_xyz[s]`` in frame ``sphere_frame[s]`` with radius
     ``sphere_r[s]``; ``sphere_link`` is a link id used only to build self pairs.
+    Box k (optional) sits in frame ``box_frame[k]`` with centre ``box_xyz[k]``,
+    axes the columns of ``box_rot[k]`` and half extents ``box_half[k]``.
     """
 
     name: str
@@ -65,6 +71,18 @@ class Robot:
     sphere_link: np.ndarray  # int32 [N_s]
     self_pairs: np.ndarray  # int32 [P, 2]
     joint_type: np.ndarray | None = None  # int32 [n]: 0 revolute, 1 prismatic; None = all revolute
+    # oriented boxes fixed to frames: centre in the frame, rotation (columns =
+    # box axes in the frame), half extents; self pairs sphere x box, box x box
+    box_frame: np.ndarray | None = None  # int32 [B]
+    box_xyz: np.ndarray | None = None  # float64 [B, 3]
+    box_rot: np.ndarray | None = None  # float64 [B, 3, 3]
+    box_half: np.ndarray | None = None  # float64 [B, 3]
+    self_sb: np.ndarray | None = None  # int32 [P, 2] (sphere, box)
+    self_bb: np.ndarray | None = None  # int32 [P, 2] (box, box)
+
+    @property
+    def n_boxes(self) -> int:
+        return 0 if self.box_frame is None else int(len(self.box_frame))
 
     @property
     def prismatic(self) -> np.ndarray:
@@ -100,15 +118,32 @@ class Robot:
             else:
                 kw[f.name] = np.asarray(v, dtype=np.float64)
         kw["sphere_xyz"] = kw["sphere_xyz"].reshape(-1, 3)
+        for k in ("box_frame",):
+            if k in kw:
+                kw[k] = kw[k].astype(np.int32)
+        for k in ("self_sb", "self_bb"):
+            if k in kw:
+                kw[k] = kw[k].astype(np.int32).reshape(-1, 2)
+        if "box_xyz" in kw:
+            kw["box_xyz"] = kw["box_xyz"].reshape(-1, 3)
+            kw["box_rot"] = kw["box_rot"].reshape(-1, 3, 3)
+            kw["box_half"] = kw["box_half"].reshape(-1, 3)
         return Robot(**kw)
 
 
 @dataclasses.dataclass
 class Env:
-    """Obstacle spheres, one row (x, y, z, radius) each."""
+    """Obstacle spheres, one row (x, y, z, radius) each, and optional oriented
+    boxes, one row (centre x, y, z, half extents hx, hy, hz, rotation R row
+    major, 9 entries; the columns of R are the box axes in the world)."""
 
     name: str
     spheres: np.ndarray  # float64 [N_obs, 4]
+    boxes: np.ndarray | None = None  # float64 [N_box, 15]
+
+    @property
+    def n_boxes(self) -> int:
+        return 0 if self.boxes is None else int(self.boxes.shape[0])
 
     @property
     def n_obs(self) -> int:
@@ -232,6 +267,71 @@ def forest_obstacles(seed: int, count: int = 15, r: float = 0.35, side: float = 
     xy = rng.uniform(lo, lo + centre, size=(count, 2))
     sph = np.column_stack([np.zeros(count), xy[:, 1], xy[:, 0], np.full(count, r)])
     return Env("forest", sph)
+
+
+def rot_zyx(yaw: float, pitch: float, roll: float) -> np.ndarray:
+    """Rz(yaw) Ry(pitch) Rx(roll)."""
+    cz, sz, cy, sy, cx, sx = (math.cos(yaw), math.sin(yaw), math.cos(pitch), math.sin(pitch), math.cos(roll),
+                              math.sin(roll))
+    Rz = np.array([[cz, -sz, 0.0], [sz, cz, 0.0], [0.0, 0.0, 1.0]])
+    Ry = np.array([[cy, 0.0, sy], [0.0, 1.0, 0.0], [-sy, 0.0, cy]])
+    Rx = np.array([[1.0, 0.0, 0.0], [0.0, cx, -sx], [0.0, sx, cx]])
+    return Rz @ Ry @ Rx
+
+
+def box_row(centre, half, R) -> np.ndarray:
+    """One Env.boxes row."""
+    return np.concatenate([np.asarray(centre, dtype=np.float64), np.asarray(half, dtype=np.float64),
+                           np.asarray(R, dtype=np.float64).reshape(9)])
+
+
+def box_arm_robot(w: float = 0.06) -> Robot:
+    """The 7-DOF chain of dh7_robot described by 11 boxes and no spheres, as
+    the hardware arm of Sec. VII: one box of half width ``w`` along each of the
+    four link segments with d != 0 (fixed to the frame whose z axis carries the
+    segment, from its origin to d along z) and a cube of half side ``w + 0.01``
+    at each joint origin 1..7. Self pairs: every box pair whose frames differ by
+    at least 3."""
+    r = dh7_robot()
+    n = r.n
+    frames, xyz, half = [], [], []
+    for i in range(n):
+        if r.d[i] != 0.0:
+            frames.append(i)
+            xyz.append((0.0, 0.0, 0.5 * r.d[i]))
+            half.append((w, w, 0.5 * abs(r.d[i])))
+    for f in range(1, n + 1):
+        frames.append(f)
+        xyz.append((0.0, 0.0, 0.0))
+        half.append((w + 0.01,) * 3)
+    B = len(frames)
+    fr = np.asarray(frames, dtype=np.int32)
+    bb = [(i, j) for i in range(B) for j in range(i + 1, B) if abs(int(fr[i]) - int(fr[j])) >= 3]
+    return Robot(
+        name="box_arm", a=r.a, alpha=r.alpha, d=r.d, theta_off=r.theta_off, q_lo=r.q_lo, q_hi=r.q_hi,
+        sphere_frame=np.zeros(0, dtype=np.int32), sphere_xyz=np.zeros((0, 3)), sphere_r=np.zeros(0),
+        sphere_link=np.zeros(0, dtype=np.int32), self_pairs=np.zeros((0, 2), dtype=np.int32),
+        box_frame=fr, box_xyz=np.asarray(xyz), box_rot=np.repeat(np.eye(3)[None], B, axis=0),
+        box_half=np.asarray(half), self_sb=np.zeros((0, 2), dtype=np.int32),
+        self_bb=np.asarray(bb, dtype=np.int32).reshape(-1, 2),
+    )
+
+
+def tabletop_box_env(seed: int, n_vox: int = 160, voxel: float = 0.08) -> Env:
+    """Table-top scene of Sec. VII: a table box, a rotated box and a shelf-like
+    box on it, and voxel spheres circumscribing ``voxel``-sized cubes (r =
+    voxel sqrt(3) / 2) from a few seeded clusters above the table."""
+    rng = np.random.default_rng(seed)
+    boxes = [box_row((0.65, 0.0, -0.02), (0.45, 0.7, 0.02), np.eye(3)),
+             box_row((0.6, -0.35, 0.12), (0.08, 0.05, 0.12), rot_zyx(rng.uniform(-1, 1), 0.0, 0.0)),
+             box_row((0.75, 0.3, 0.2), (0.05, 0.2, 0.2), rot_zyx(rng.uniform(-0.5, 0.5), rng.uniform(-0.2, 0.2),
+                                                            rng.uniform(-0.2, 0.2)))]
+    centres = rng.uniform((0.4, -0.5, 0.05), (1.0, 0.5, 0.5), size=(5, 3))
+    pts = centres[rng.integers(0, 5, size=n_vox)] + rng.normal(0.0, 0.06, size=(n_vox, 3))
+    vox = np.unique(np.floor(pts / voxel).astype(np.int64), axis=0)
+    c = (vox + 0.5) * voxel
+    sph = np.column_stack([c, np.full(c.shape[0], voxel * math.sqrt(3.0) / 2.0)])
+    return Env("tabletop_boxes", sph, np.asarray(boxes))
 
 
 def planar_disks_candidates(seed: int, count: int, lo: float = -2.5, hi: float = 2.5,
