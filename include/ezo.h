@@ -111,6 +111,22 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
                             int32_t n_spheres, const int32_t* sphere_frame, const double* sphere_xyz,
                             const double* sphere_r, int32_t n_self_pairs, const int32_t* self_pairs,
                             const int32_t* joint_type, ezo_robot** out);
+
+/* Oriented boxes fixed to the robot's frames (Sec. IV-D: the checker supports
+ * box and sphere geometries; Sec. VII: an arm described by 11 boxes). Box k
+ * (n_box <= 32) sits in frame box_frame[k] (0..n) with centre box_xyz[3k..],
+ * rotation box_rot[9k..] (3 x 3 row major; its columns are the box axes in the
+ * frame) and half extents box_half[3k..] >= 0. sb_pairs lists n_sb self pairs
+ * (sphere index, box index), bb_pairs n_bb pairs (box, box). A box overlaps
+ * an obstacle sphere or a robot sphere when the sphere centre is strictly
+ * inside it or closer than the radius; two boxes overlap when none of the 15
+ * separating-axis candidates separates them (cross products of edges within
+ * ~0.6 degrees of parallel, |a x b|^2 < 1e-4, are left out). Replaces boxes
+ * added before; call before the robot is used. Host arrays, copied.
+ * EZO_ERR_INVALID_ARG for counts or indices out of range. */
+ezo_status ezo_robot_add_boxes(ezo_robot* robot, int32_t n_box, const int32_t* box_frame, const double* box_xyz,
+                               const double* box_rot, const double* box_half, int32_t n_sb, const int32_t* sb_pairs,
+                               int32_t n_bb, const int32_t* bb_pairs);
 void ezo_robot_free(ezo_robot* robot);
 int32_t ezo_robot_dof(const ezo_robot* robot);
 
@@ -119,6 +135,12 @@ int32_t ezo_robot_dof(const ezo_robot* robot);
  * spheres): n_obs rows (x, y, z, radius) of host FP64, n_obs <= 4096.
  * Errors: EZO_ERR_INVALID_ARG, EZO_ERR_CUDA. */
 ezo_status ezo_env_create(int32_t n_obs, const double* xyzr, ezo_env** out);
+/* Oriented obstacle boxes (at most 64): one row of 15 doubles per box,
+ * centre (3), half extents (3), rotation (9, row major, columns = box axes in
+ * the world). Replaces boxes added before; call before the env is used. The
+ * signed-distance call and surrogate training take sphere geometries only and
+ * return EZO_ERR_INVALID_ARG when boxes are present. */
+ezo_status ezo_env_add_boxes(ezo_env* env, int32_t n_box, const double* boxes);
 void ezo_env_free(ezo_env* env);
 
 /* ------------------------------------------------------ collision checker --

@@ -12,7 +12,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libezo.so")
-SOURCES = ["ezo_capi.cu", "ezo_k_flat.cu", "ezo_k_round_a.cu", "ezo_k_round_b.cu", "ezo_noalloc.cu", "ezo_tune.cu", "ezo_mlp.cu", "ezo_k_sbis.cu", "ezo_k_recover.cu"]
+SOURCES = ["ezo_capi.cu", "ezo_k_flat.cu", "ezo_k_round_a.cu", "ezo_k_round_b.cu", "ezo_noalloc.cu", "ezo_tune.cu",
+           "ezo_mlp.cu", "ezo_k_sbis.cu", "ezo_k_recover.cu"]
+# the collision kernels for scenes with box geometries: the same sources built
+# a second time with EZO_BOX_TU=1, in parallel with the rest
+BOX_SOURCES = ["ezo_k_flat.cu", "ezo_k_round_a.cu", "ezo_k_round_b.cu", "ezo_k_recover.cu"]
+UNITS = [(src, src.replace(".cu", ".o"), []) for src in SOURCES] + \
+        [(src, src.replace(".cu", "_box.o"), ["-DEZO_BOX_TU=1"]) for src in BOX_SOURCES]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off"]
 
@@ -43,9 +49,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, obj_name, extra = unit
+        obj = os.path.join(BUILD, obj_name)
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -53,8 +60,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr, file=sys.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + ".tmp"
     cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

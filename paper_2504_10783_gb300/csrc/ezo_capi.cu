@@ -79,11 +79,14 @@ struct ezo_robot {
   RobotDev* d_robot = nullptr;
   ushort2* d_pairs = nullptr;
   float* d_rr = nullptr;
+  ushort2 *d_sbp = nullptr, *d_bbp = nullptr;  // self pairs with a box
+  std::vector<int> sphere_sorted;              // caller's sphere index -> sorted index
   int n = 0, n_spheres = 0, nsp_pad = 0, n_self = 0;
   std::vector<double> q_lo, q_hi;
   double reach = 0.0, r_max = 0.0;
   double fk_flops = 0.0;
   bool prismatic = false;  // any prismatic joint
+  int n_box = 0, n_sbp = 0, n_bbp = 0;
 };
 
 struct ezo_env {
@@ -91,7 +94,9 @@ struct ezo_env {
   float* d_nhw = nullptr;
   int n_obs = 0, n_obs_pad = 0;
   double o_max = 0.0, R_max = 0.0;
-  EnvDev dev() const { return EnvDev{d_obs, d_nhw, n_obs, n_obs_pad}; }
+  float4* d_box = nullptr;  // obstacle boxes, 4 float4 each
+  int n_box = 0;
+  EnvDev dev() const { return EnvDev{d_obs, d_nhw, n_obs, n_obs_pad, d_box, n_box, 0}; }
 };
 
 static float band_E(const ezo_robot* r, const ezo_env* e) {
@@ -203,6 +208,7 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
     h.frame_first[n + 1] = n_spheres;
   }
   r->reach = chain + loc_max;
+  r->sphere_sorted = inv;
   std::vector<ushort2> pairs(std::max(1, n_self_pairs));
   std::vector<float> rr(std::max(1, n_self_pairs));
   for (int p = 0; p < n_self_pairs; ++p) {
@@ -286,6 +292,8 @@ void ezo_robot_free(ezo_robot* r) {
   if (!r) return;
   cudaFree(r->d_pairs);
   cudaFree(r->d_rr);
+  cudaFree(r->d_sbp);
+  cudaFree(r->d_bbp);
   cudaFree(r->d_robot);
   delete r;
 }
@@ -330,17 +338,106 @@ void ezo_env_free(ezo_env* e) {
   if (!e) return;
   cudaFree(e->d_obs);
   cudaFree(e->d_nhw);
+  cudaFree(e->d_box);
   delete e;
 }
 
-int ezo_internal_tuned_lanes(const ezo_robot* robot, const ezo_env* env, long long N, cudaStream_t s);
-
-static int auto_lanes(long long N) {
-  if (N >= (1ll << 20)) return 1;
-  if (N >= (1ll << 17)) return 2;
-  if (N >= (1ll << 15)) return 4;
-  return 8;
+ezo_status ezo_robot_add_boxes(ezo_robot* r, int32_t n_box, const int32_t* box_frame, const double* box_xyz,
+                               const double* box_rot, const double* box_half, int32_t n_sb, const int32_t* sb_pairs,
+                               int32_t n_bb, const int32_t* bb_pairs) {
+  if (!r) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: null robot");
+  if (n_box < 0 || n_box > EZO_MAX_BOX) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: n_box must be in [0, 32]");
+  if (n_sb < 0 || n_bb < 0 || n_sb > 65535 || n_bb > 65535)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: pair counts must be in [0, 65535]");
+  if (n_box && (!box_frame || !box_xyz || !box_rot || !box_half)) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: null array");
+  if ((n_sb && !sb_pairs) || (n_bb && !bb_pairs)) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: null pair array");
+  for (int k = 0; k < n_box; ++k) {
+    if (box_frame[k] < 0 || box_frame[k] > r->n) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: box_frame out of [0, n]");
+    for (int c = 0; c < 3; ++c)
+      if (!(box_half[3 * k + c] >= 0.0)) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: negative half extent");
+  }
+  for (int p = 0; p < n_sb; ++p)
+    if (sb_pairs[2 * p] < 0 || sb_pairs[2 * p] >= r->n_spheres || sb_pairs[2 * p + 1] < 0 || sb_pairs[2 * p + 1] >= n_box)
+      return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: sphere-box pair index out of range");
+  for (int p = 0; p < 2 * n_bb; ++p)
+    if (bb_pairs[p] < 0 || bb_pairs[p] >= n_box) return fail(EZO_ERR_INVALID_ARG, "ezo_robot_add_boxes: box pair index out of range");
+  RobotDev& h = r->host;
+  // sort boxes by frame (stable), four float4 each: (centre, h_x), (axis k = column k of R, h_y / h_z / 0)
+  std::vector<int> order(n_box), inv(n_box);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return box_frame[x] < box_frame[y]; });
+  for (int k = 0; k < n_box; ++k) {
+    const int o = order[k];
+    inv[o] = k;
+    const double* R = box_rot + 9 * o;  // row major, columns are the box axes
+    const double* hh = box_half + 3 * o;
+    h.box_l[4 * k] = make_float4((float)box_xyz[3 * o], (float)box_xyz[3 * o + 1], (float)box_xyz[3 * o + 2], (float)hh[0]);
+    for (int a = 0; a < 3; ++a)
+      h.box_l[4 * k + 1 + a] = make_float4((float)R[a], (float)R[3 + a], (float)R[6 + a], a < 2 ? (float)hh[a + 1] : 0.f);
+  }
+  {
+    int k = 0;
+    for (int f = 0; f <= r->n; ++f) {
+      h.box_first[f] = k;
+      while (k < n_box && box_frame[order[k]] == f) ++k;
+    }
+    h.box_first[r->n + 1] = n_box;
+  }
+  h.n_box = n_box;
+  std::vector<ushort2> sb(std::max(1, n_sb)), bb(std::max(1, n_bb));
+  for (int p = 0; p < n_sb; ++p)
+    sb[p] = make_ushort2((unsigned short)r->sphere_sorted[sb_pairs[2 * p]], (unsigned short)inv[sb_pairs[2 * p + 1]]);
+  for (int p = 0; p < n_bb; ++p)
+    bb[p] = make_ushort2((unsigned short)inv[bb_pairs[2 * p]], (unsigned short)inv[bb_pairs[2 * p + 1]]);
+  cudaFree(r->d_sbp);
+  cudaFree(r->d_bbp);
+  r->d_sbp = r->d_bbp = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&r->d_sbp, sb.size() * sizeof(ushort2))) != cudaSuccess ||
+      (e = cudaMalloc(&r->d_bbp, bb.size() * sizeof(ushort2))) != cudaSuccess ||
+      (e = cudaMemcpy(r->d_sbp, sb.data(), sb.size() * sizeof(ushort2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(r->d_bbp, bb.data(), bb.size() * sizeof(ushort2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "ezo_robot_add_boxes");
+  h.n_sbp = n_sb;
+  h.n_bbp = n_bb;
+  h.sb_pairs = r->d_sbp;
+  h.bb_pairs = r->d_bbp;
+  r->n_box = n_box;
+  r->n_sbp = n_sb;
+  r->n_bbp = n_bb;
+  // pose work per box (centre 9 + axes 27 multiply-adds)
+  r->fk_flops = 45.0 * r->n + 25.0 * r->n_spheres + 72.0 * n_box;
+  if ((e = cudaMemcpy(r->d_robot, &h, sizeof(RobotDev), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "ezo_robot_add_boxes");
+  g_err.clear();
+  return EZO_OK;
 }
+
+ezo_status ezo_env_add_boxes(ezo_env* e, int32_t n_box, const double* boxes) {
+  if (!e || n_box < 0 || n_box > EZO_MAX_EBOX || (n_box && !boxes))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_env_add_boxes: need an env and 0 <= n_box <= 64");
+  std::vector<float4> b((size_t)std::max(1, 4 * n_box));
+  for (int k = 0; k < n_box; ++k) {
+    const double* x = boxes + 15 * k;  // centre, half extents, R row major (columns = axes)
+    for (int c = 3; c < 6; ++c)
+      if (!(x[c] >= 0.0)) return fail(EZO_ERR_INVALID_ARG, "ezo_env_add_boxes: negative half extent");
+    const double* R = x + 6;
+    b[4 * k] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+    for (int a = 0; a < 3; ++a)
+      b[4 * k + 1 + a] = make_float4((float)R[a], (float)R[3 + a], (float)R[6 + a], a < 2 ? (float)x[4 + a] : 0.f);
+  }
+  cudaFree(e->d_box);
+  e->d_box = nullptr;
+  cudaError_t err;
+  if ((err = cudaMalloc(&e->d_box, b.size() * sizeof(float4))) != cudaSuccess ||
+      (err = cudaMemcpy(e->d_box, b.data(), b.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(err, "ezo_env_add_boxes");
+  e->n_box = n_box;
+  g_err.clear();
+  return EZO_OK;
+}
+
+int ezo_internal_tuned_lanes(const ezo_robot* robot, const ezo_env* env, long long N, cudaStream_t s);
 
 ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
                                int64_t ldq, uint8_t* flags_dev, int32_t lanes, void* stream) {
@@ -350,7 +447,7 @@ ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const
   if (lanes == 0) lanes = ezo_internal_tuned_lanes(robot, env, N, (cudaStream_t)stream);
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
     return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: lanes_per_config must be 0, 1, 2, 4 or 8");
-  cudaError_t e = launch_check_flat(robot->d_robot, robot->n, robot->nsp_pad, env->dev(), band_E(robot, env), q_dev, ldq, N,
+  cudaError_t e = launch_check_flat(robot->d_robot, robot->n, robot->nsp_pad, robot->n_box, env->dev(), band_E(robot, env), q_dev, ldq, N,
                                     flags_dev, lanes, sm_count() * 32, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "ezo_check_collision");
   g_err.clear();
@@ -362,6 +459,8 @@ ezo_status ezo_signed_distance(const ezo_robot* robot, const ezo_env* env, const
   if (!robot || !env) return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: null handle");
   if (N < 0 || ldq < N) return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: need 0 <= N <= ldq");
   if (N > 0 && (!q_dev || !sd_dev)) return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: null buffer");
+  if (robot->n_box || env->n_box)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: sphere geometries only (the robot or env has boxes)");
   cudaError_t e = launch_sd_flat(robot->d_robot, robot->n, robot->nsp_pad, env->dev(), q_dev, ldq, N, sd_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "ezo_signed_distance");
   g_err.clear();
@@ -412,9 +511,16 @@ __attribute__((visibility("hidden"))) int ezo_internal_robot_prismatic(const ezo
   return r && r->prismatic ? 1 : 0;
 }
 
+__attribute__((visibility("hidden"))) int ezo_internal_robot_boxes(const ezo_robot* r) { return r ? r->n_box : 0; }
+
+__attribute__((visibility("hidden"))) int ezo_internal_env_boxes(const ezo_env* e) { return e ? e->n_box : 0; }
+
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env) {
   if (!robot || !env) return 0.0;
-  return robot->fk_flops + 8.0 * ((double)robot->n_spheres * env->n_obs + robot->n_self);
+  // 8 flops per sphere pair, ~30 per sphere-box pair, ~330 per box-box pair
+  return robot->fk_flops + 8.0 * ((double)robot->n_spheres * env->n_obs + robot->n_self) +
+         30.0 * ((double)robot->n_spheres * env->n_box + (double)robot->n_box * env->n_obs + robot->n_sbp) +
+         330.0 * ((double)robot->n_box * env->n_box + robot->n_bbp);
 }
 
 // ------------------------------------------------------------------ batch --
@@ -422,7 +528,7 @@ double ezo_check_flops(const ezo_robot* robot, const ezo_env* env) {
 
 struct ezo_batch {
   const ezo_robot* robot = nullptr;
-  int B = 0, n = 0, m0 = 0, m_cap = 0, s_cap_max = 0, np_max = 0, max_path_len = 1, max_obs_pad = 0;
+  int B = 0, n = 0, m0 = 0, m_cap = 0, s_cap_max = 0, np_max = 0, max_path_len = 1, max_obs_pad = 0, max_ebox = 0;
   ezo_params prm{};
   std::vector<SegState> st0;
   std::vector<int> path_first;
@@ -734,8 +840,9 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
     b->envs[e].e = envs[e]->dev();
     b->envs[e].E = band_E(robot, envs[e]);
     b->max_obs_pad = std::max(b->max_obs_pad, envs[e]->n_obs_pad);
+    b->max_ebox = std::max(b->max_ebox, envs[e]->n_box);
   }
-  const size_t smem_check = check_smem_bytes(robot->nsp_pad, b->max_obs_pad, 128, 1);
+  const size_t smem_check = check_smem_bytes(robot->nsp_pad, b->max_obs_pad, 128, 1, robot->n_box, b->max_ebox);
   if (smem_check > 220 * 1024) {
     delete b;
     return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: robot spheres and obstacles exceed shared memory");
@@ -841,6 +948,8 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   v.robot = robot->d_robot;
   v.envs = b->d_envs;
   v.max_obs_pad = b->max_obs_pad;
+  v.max_ebox = b->max_ebox;
+  v.n_rbox = robot->n_box;
   v.nsp_pad = robot->nsp_pad;
   v.np_max = b->np_max;
   v.path_first = b->d_path_first;
@@ -1348,7 +1457,7 @@ ezo_status ezo_check_path(const ezo_robot* robot, const ezo_env* env, const doub
   if (e == cudaSuccess) e = cudaMemsetAsync(d_edge, 0, (size_t)K, s);
   if (e == cudaSuccess) {
     const int lanes = ezo_internal_tuned_lanes(robot, env, N, s);
-    e = launch_check_path(robot->d_robot, n, robot->nsp_pad, env->dev(), band_E(robot, env), d_verts, K, d_off, N,
+    e = launch_check_path(robot->d_robot, n, robot->nsp_pad, robot->n_box, env->dev(), band_E(robot, env), d_verts, K, d_off, N,
                           point_flags_dev, d_edge, lanes, sm_count() * 32, s);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(edge_flags, d_edge, (size_t)K, cudaMemcpyDeviceToHost, s);

@@ -22,6 +22,8 @@
 #define EZO_MAX_OBS 4096
 #define EZO_CH 8
 #define EZO_MAX_SBLK 16
+#define EZO_MAX_BOX 32    // robot boxes
+#define EZO_MAX_EBOX 64   // obstacle boxes per environment
 
 namespace ezo {
 
@@ -71,6 +73,15 @@ struct RobotDev {
   int n_sblk;
   float E_self;
   int4 sblk[EZO_MAX_SBLK];
+  // Oriented boxes fixed to frames (sorted by frame, box_first like
+  // frame_first), four float4 each in the frame: (centre, h_x), (axis 0, h_y),
+  // (axis 1, h_z), (axis 2, 0); self pairs sphere x box and box x box
+  int n_box;
+  int box_first[EZO_MAX_DOF + 2];
+  float4 box_l[4 * EZO_MAX_BOX];
+  int n_sbp, n_bbp;
+  const ushort2* sb_pairs;  // (sorted sphere, sorted box)
+  const ushort2* bb_pairs;  // (sorted box, sorted box)
 };
 
 // The part of RobotDev a block keeps in shared memory.
@@ -78,6 +89,8 @@ struct RobotSmem {
   float ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
   float kth[EZO_MAX_DOF], kd[EZO_MAX_DOF];
   int frame_first[EZO_MAX_DOF + 2];
+  int box_first[EZO_MAX_DOF + 2];
+  int n_box, n_sbp, n_bbp;
   int n, n_spheres, n_spheres_pad, n_self;
   int n_sblk;
   float E_self;
@@ -94,7 +107,10 @@ __device__ __forceinline__ void stage_robot(RobotSmem& rs, float4* sph_s, const 
     rs.kth[i] = rd->kth[i];
     rs.kd[i] = rd->kd[i];
   }
-  for (int i = threadIdx.x; i < EZO_MAX_DOF + 2; i += blockDim.x) rs.frame_first[i] = rd->frame_first[i];
+  for (int i = threadIdx.x; i < EZO_MAX_DOF + 2; i += blockDim.x) {
+    rs.frame_first[i] = rd->frame_first[i];
+    rs.box_first[i] = rd->box_first[i];
+  }
   for (int i = threadIdx.x; i < EZO_MAX_SBLK; i += blockDim.x) rs.sblk[i] = rd->sblk[i];
   if (threadIdx.x == 0) {
     rs.n = rd->n;
@@ -103,9 +119,18 @@ __device__ __forceinline__ void stage_robot(RobotSmem& rs, float4* sph_s, const 
     rs.n_self = rd->n_self;
     rs.n_sblk = rd->n_sblk;
     rs.E_self = rd->E_self;
+    rs.n_box = rd->n_box;
+    rs.n_sbp = rd->n_sbp;
+    rs.n_bbp = rd->n_bbp;
   }
   const int np = rd->n_spheres_pad;
   for (int i = threadIdx.x; i < np; i += blockDim.x) sph_s[i] = rd->sph[i];
+}
+
+// The robot's boxes in their frames (4 float4 per box) into shared memory.
+__device__ __forceinline__ void stage_robot_boxes(float4* rbox_l, const RobotDev* __restrict__ rd) {
+  const int nb = 4 * rd->n_box;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) rbox_l[i] = rd->box_l[i];
 }
 
 // Obstacle set in global memory: (x, y, z, R) and -(|o|^2 - R^2)/2, padded to
@@ -115,6 +140,9 @@ struct EnvDev {
   const float* nhw;
   int n_obs;
   int n_obs_pad;
+  const float4* box;  // obstacle boxes, 4 float4 each: (centre, h_x), (axis 0, h_y), (axis 1, h_z), (axis 2, 0)
+  int n_box;
+  int pad;
 };
 
 __device__ __forceinline__ void stage_env(float4* obs_s, float* nhw_s, const EnvDev& e) {
@@ -124,6 +152,90 @@ __device__ __forceinline__ void stage_env(float4* obs_s, float* nhw_s, const Env
   }
 }
 
+__device__ __forceinline__ void stage_env_boxes(float4* ebox_s, const EnvDev& e) {
+  for (int i = threadIdx.x; i < 4 * e.n_box; i += blockDim.x) ebox_s[i] = e.box[i];
+}
+
+// Box geometry of one collision group (all in shared memory).
+struct BoxCtx {
+  const float4* rbox_l;  // robot boxes in their frames
+  const float4* ebox;    // obstacle boxes of the current environment
+  float4* rbox_w;        // this group's robot boxes in the world
+  int n_ebox;
+  const ushort2* sb_pairs;
+  const ushort2* bb_pairs;
+};
+
+// Sphere (centre c.xyz, radius r) against an oriented box B (4 float4): the
+// centre in box coordinates p_k = axis_k . (c - centre), q_k = abs(p_k) - h_k;
+// overlap iff the centre is strictly inside (every q_k < 0) or the squared
+// norm of max(q, 0) is below r^2.
+__device__ __forceinline__ bool sphere_box_hit(float4 c, float r, const float4* __restrict__ B) {
+  const float4 b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
+  const float dx = c.x - b0.x, dy = c.y - b0.y, dz = c.z - b0.z;
+  const float q0 = fabsf(fmaf(dx, b1.x, fmaf(dy, b1.y, dz * b1.z))) - b0.w;
+  const float q1 = fabsf(fmaf(dx, b2.x, fmaf(dy, b2.y, dz * b2.z))) - b1.w;
+  const float q2 = fabsf(fmaf(dx, b3.x, fmaf(dy, b3.y, dz * b3.z))) - b2.w;
+  if (q0 < 0.f && q1 < 0.f && q2 < 0.f) return true;
+  const float m0 = fmaxf(q0, 0.f), m1 = fmaxf(q1, 0.f), m2 = fmaxf(q2, 0.f);
+  return fmaf(m0, m0, fmaf(m1, m1, m2 * m2)) < r * r;
+}
+
+// Separating-axis test of two oriented boxes, written in A's frame: with
+// t = A^T (c_B - c_A) and R = A^T B, a candidate axis L separates when
+// abs(t . L) - sum_k hA_k abs(L_k) - sum_k hB_k abs(r_k . L) >= 0 (r_k the
+// columns of R); the candidates are A's axes, B's axes and e_i x r_j, the
+// latter skipped when abs(L)^2 < 1e-4 (nearly parallel edges). The boxes
+// overlap iff no candidate separates them. Scaling L does not change the sign,
+// so the cross products are not normalised.
+__device__ __forceinline__ bool box_box_hit(const float4* __restrict__ A, const float4* __restrict__ B) {
+  const float4 a0 = A[0], a1 = A[1], a2 = A[2], a3 = A[3];
+  const float4 b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
+  const float ha[3] = {a0.w, a1.w, a2.w}, hb[3] = {b0.w, b1.w, b2.w};
+  const float Tx = b0.x - a0.x, Ty = b0.y - a0.y, Tz = b0.z - a0.z;
+  const float ax[3][3] = {{a1.x, a1.y, a1.z}, {a2.x, a2.y, a2.z}, {a3.x, a3.y, a3.z}};
+  const float bx[3][3] = {{b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z}, {b3.x, b3.y, b3.z}};
+  float t[3], R[3][3], aR[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    t[i] = fmaf(Tx, ax[i][0], fmaf(Ty, ax[i][1], Tz * ax[i][2]));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R[i][j] = fmaf(ax[i][0], bx[j][0], fmaf(ax[i][1], bx[j][1], ax[i][2] * bx[j][2]));
+      aR[i][j] = fabsf(R[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)  // A's axes
+    if (fabsf(t[i]) - ha[i] - fmaf(hb[0], aR[i][0], fmaf(hb[1], aR[i][1], hb[2] * aR[i][2])) >= 0.f) return false;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {  // B's axes
+    const float tj = fmaf(t[0], R[0][j], fmaf(t[1], R[1][j], t[2] * R[2][j]));
+    if (fabsf(tj) - fmaf(ha[0], aR[0][j], fmaf(ha[1], aR[1][j], ha[2] * aR[2][j])) - hb[j] >= 0.f) return false;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      // L = e_i x r_j in A's frame
+      float L[3];
+      L[i] = 0.f;
+      L[(i + 1) % 3] = -R[(i + 2) % 3][j];
+      L[(i + 2) % 3] = R[(i + 1) % 3][j];
+      const float n2 = fmaf(L[0], L[0], fmaf(L[1], L[1], L[2] * L[2]));
+      if (n2 < 1e-4f) continue;
+      const float tl = fmaf(t[0], L[0], fmaf(t[1], L[1], t[2] * L[2]));
+      const float ra = fmaf(ha[0], fabsf(L[0]), fmaf(ha[1], fabsf(L[1]), ha[2] * fabsf(L[2])));
+      float rb = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        rb = fmaf(hb[k], fabsf(fmaf(R[0][k], L[0], fmaf(R[1][k], L[1], R[2][k] * L[2]))), rb);
+      if (fabsf(tl) - ra - rb >= 0.f) return false;
+    }
+  }
+  return true;
+}
+
 // max of three floats in one instruction (PTX max.f32 with three inputs).
 __device__ __forceinline__ float fmax3f(float a, float b, float c) {
   float d;
@@ -131,21 +243,76 @@ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
   return d;
 }
 
+// World poses of the boxes [b0, b1) of one frame (rotation columns c0..c2,
+// origin in the .w entries): centre o + R c, axes R a_k; boxes b with
+// b % T == lg on this lane.
+template <int T>
+__device__ __forceinline__ void box_poses_of_frame(int b0, int b1, int lg, float4 c0, float4 c1, float4 c2,
+                                                const BoxCtx& bx) {
+  int b = b0 + ((lg - b0) & (T - 1));
+  for (; b < b1; b += T) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 l = bx.rbox_l[4 * b + k];
+      const float ox = k == 0 ? c0.w : 0.f, oy = k == 0 ? c1.w : 0.f, oz = k == 0 ? c2.w : 0.f;
+      bx.rbox_w[4 * b + k] = make_float4(fmaf(c0.x, l.x, fmaf(c1.x, l.y, fmaf(c2.x, l.z, ox))),
+                                         fmaf(c0.y, l.x, fmaf(c1.y, l.y, fmaf(c2.y, l.z, oy))),
+                                         fmaf(c0.z, l.x, fmaf(c1.z, l.y, fmaf(c2.z, l.z, oz))), l.w);
+    }
+  }
+}
+
+// The pairs of one configuration that involve a box, split over the T lanes
+// of its group: robot spheres x obstacle boxes, robot boxes x obstacle
+// spheres and boxes, listed sphere-box and box-box self pairs. Returns this
+// lane's OR.
+template <int T>
+__device__ __forceinline__ bool box_pairs_hit(const RobotSmem& rs, const float4* __restrict__ sph_s,
+                                           const float4* __restrict__ obs_s, int n_obs, const float4* __restrict__ cen,
+                                           int lg, const BoxCtx& bx) {
+  bool hit = false;
+  const int ns = rs.n_spheres, nb = rs.n_box, ne = bx.n_ebox;
+  for (int p = lg; p < ns * ne && !hit; p += T) {  // robot spheres x obstacle boxes
+    const int s = p / ne, e = p - s * ne;
+    hit = sphere_box_hit(cen[s], sph_s[s].w, bx.ebox + 4 * e);
+  }
+  for (int p = lg; p < nb * n_obs && !hit; p += T) {  // robot boxes x obstacle spheres
+    const int b = p / n_obs, o = p - b * n_obs;
+    const float4 ob = obs_s[o];
+    hit = sphere_box_hit(ob, ob.w, bx.rbox_w + 4 * b);
+  }
+  for (int p = lg; p < nb * ne && !hit; p += T) {  // robot boxes x obstacle boxes
+    const int b = p / ne, e = p - b * ne;
+    hit = box_box_hit(bx.rbox_w + 4 * b, bx.ebox + 4 * e);
+  }
+  for (int p = lg; p < rs.n_sbp && !hit; p += T) {  // self: sphere x box
+    const ushort2 pr = bx.sb_pairs[p];
+    hit = sphere_box_hit(cen[pr.x], sph_s[pr.x].w, bx.rbox_w + 4 * pr.y);
+  }
+  for (int p = lg; p < rs.n_bbp && !hit; p += T) {  // self: box x box
+    const ushort2 pr = bx.bb_pairs[p];
+    hit = box_box_hit(bx.rbox_w + 4 * pr.x, bx.rbox_w + 4 * pr.y);
+  }
+  return hit;
+}
+
 // -------------------------------------------------- FK + collision test --
-// One configuration evaluated by a group of T lanes of one warp (T in 1..8).
+// One configuration evaluated by a group of T lanes of one warp (T in 1..8);
+// BOX adds the box geometries (robot boxes posed along the chain, pairs with
+// a box after the sphere pairs).
 // Lane lg of the group computes the centres of spheres s with s % T == lg
 // (every lane walks the chain), the group shares them through smem slot
 // `cen`, then lane lg sweeps obstacles j with j % T == lg and self pairs
 // p with p % T == lg. Returns the group-wide OR. Every lane of the warp must
 // call this together (invalid configurations are evaluated and discarded).
-template <int NDOF, int T>
+template <int NDOF, int T, bool BOX = false>
 __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const RobotSmem& rs,
                                               const float4* __restrict__ sph_s,
                                               const float4* __restrict__ obs_s,
                                               const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
                                               const ushort2* __restrict__ self_pairs,
                                               const float* __restrict__ self_rr, float E,
-                                              float4* __restrict__ cen, int lg) {
+                                              float4* __restrict__ cen, int lg, const BoxCtx& bx) {
   // ---- forward kinematics: columns of R_f and origin o_f, frame by frame ----
   float c0x = 1.f, c0y = 0.f, c0z = 0.f;
   float c1x = 0.f, c1y = 1.f, c1z = 0.f;
@@ -215,6 +382,9 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
       const float hu = 0.5f * fmaf(cx, cx, fmaf(cy, cy, fmaf(cz, cz, -l.w * l.w)));
       cen[s] = make_float4(cx, cy, cz, hu);
     }
+    if constexpr (BOX)
+      box_poses_of_frame<T>(rs.box_first[f], rs.box_first[f + 1], lg, make_float4(c0x, c0y, c0z, px),
+                            make_float4(c1x, c1y, c1z, py), make_float4(c2x, c2y, c2z, pz), bx);
   }
   for (int s = rs.n_spheres + lg; s < rs.n_spheres_pad; s += T) cen[s] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
   __syncwarp();
@@ -332,6 +502,11 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (d2 < self_rr[p]) hit = true;
     }
+  }
+  // ---- pairs with a box (direct tests; compiled only into the kernels for
+  //      scenes with boxes, so sphere-only scenes keep their register budget) ----
+  if constexpr (BOX) {
+    if (!hit) hit = box_pairs_hit<T>(rs, sph_s, obs_s, n_obs, cen, lg, bx);
   }
   __syncwarp();
   if (T > 1) {

@@ -102,6 +102,8 @@ struct BatchView {
   int sbis;          // 1 when a surrogate is attached
   int bis_mode;      // bisection kernel mode: 0 exact, 1 verify surrogate end point, 2 exact for fallbacks
   float sbis_margin; // predicted collision iff sd_hat < margin
+  int n_rbox;        // robot boxes
+  int max_ebox;      // largest obstacle box count over the environments
   int sample_lanes;  // lanes per hit-and-run walk: 0 = chosen per round from the tile count, else 1, 2, 4 or 8
   int edit;          // set editing (Sec. VI-B): the samples are given configurations, no test
   float* s_p32;      // [row * 8 + j] projection onto L (FP32)
@@ -114,8 +116,9 @@ struct BatchView {
 };
 
 // Launchers (ezo_kernels.cu). T = lanes per configuration.
-cudaError_t launch_check_flat(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, float E, const float* q,
-                              long long ldq, long long N, uint8_t* flags, int T, int grid_cap, cudaStream_t s);
+cudaError_t launch_check_flat(const RobotDev* robot, int n, int nsp_pad, int n_rbox, const EnvDev& env, float E,
+                              const float* q, long long ldq, long long N, uint8_t* flags, int T, int grid_cap,
+                              cudaStream_t s);
 // signed distance, exact below cap (3e38: exact everywhere)
 cudaError_t launch_sd_flat(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, const float* q, long long ldq,
                            long long N, float* sd, cudaStream_t s, float cap = 3.0e38f);
@@ -142,11 +145,21 @@ cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 // segment k satisfy A_j x <= b_j + tol for j = path_first[k] + d < k.
 cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s);
 // recovery (Sec. VI-B)
-cudaError_t launch_check_path(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, float E,
+cudaError_t launch_check_path(const RobotDev* robot, int n, int nsp_pad, int n_rbox, const EnvDev& env, float E,
                               const double* verts, int n_edges, const long long* off, long long N,
                               uint8_t* point_flags, uint8_t* edge_flags, int T, int grid_cap, cudaStream_t s);
 cudaError_t launch_coverage(const BatchView& v, uint8_t* covered, double tol, cudaStream_t s);
+// the same collision launchers for scenes with box geometries (compiled in
+// separate translation units so that the sphere-only kernels stay lean)
+cudaError_t launch_check_flat_box(const RobotDev* robot, int n, int nsp_pad, int n_rbox, const EnvDev& env, float E,
+                                  const float* q, long long ldq, long long N, uint8_t* flags, int T, int grid_cap,
+                                  cudaStream_t s);
+cudaError_t launch_check_path_box(const RobotDev* robot, int n, int nsp_pad, int n_rbox, const EnvDev& env, float E,
+                                  const double* verts, int n_edges, const long long* off, long long N,
+                                  uint8_t* point_flags, uint8_t* edge_flags, int T, int grid_cap, cudaStream_t s);
+cudaError_t launch_round_check_box(const BatchView& v, int T, int grid, cudaStream_t s);
+cudaError_t launch_round_bisect_box(const BatchView& v, int T, int grid, cudaStream_t s);
 
-size_t check_smem_bytes(int n_spheres_pad, int n_obs_pad, int threads, int T);
+size_t check_smem_bytes(int n_spheres_pad, int n_obs_pad, int threads, int T, int n_rbox = 0, int n_ebox = 0);
 
 }  // namespace ezo

@@ -9,12 +9,20 @@
 // bisection, placement) on the given configurations.
 #include "ezo_kernels_common.cuh"
 
+#ifndef EZO_BOX_TU
+#define EZO_BOX_TU 0  // 1: this translation unit holds only the box-geometry collision kernels
+#endif
+
 namespace ezo {
+
+#if !EZO_BOX_TU
 
 // Point i of the discretised path: edge k with off[k] <= i < off[k + 1],
 // t = (i - off[k]) / N_k with N_k = off[k + 1] - off[k] - 1 pieces, and
 // q = v_k + t (v_{k+1} - v_k) with separately rounded FP64 products and sums.
-template <int NDOF, int T>
+#endif  // !EZO_BOX_TU
+
+template <int NDOF, int T, bool BOX>
 __global__ void __launch_bounds__(128) k_check_path(const RobotDev* __restrict__ robot, EnvDev env, float E,
                                                     const double* __restrict__ verts, int n_edges,
                                                     const long long* __restrict__ off, long long N,
@@ -22,17 +30,20 @@ __global__ void __launch_bounds__(128) k_check_path(const RobotDev* __restrict__
                                                     uint8_t* __restrict__ edge_flags) {
   extern __shared__ float4 smem4[];
   __shared__ RobotSmem rs;
-  const int nsp = robot->n_spheres_pad;
+  const int nsp = robot->n_spheres_pad, nrbox = robot->n_box;
   const int groups = blockDim.x / T;
-  float4* sph_s = smem4;
-  float4* obs_s = sph_s + nsp;
-  float4* cen_all = obs_s + env.n_obs_pad;
-  float* nhw_s = reinterpret_cast<float*>(cen_all + groups * (nsp + 1));
+  const GeomSmem gs = carve_geom(smem4, nsp, env.n_obs_pad, groups, nrbox, env.n_box);
+  float4* sph_s = gs.sph;
+  float4* obs_s = gs.obs;
+  float* nhw_s = gs.nhw;
   stage_robot(rs, sph_s, robot);
+  stage_robot_boxes(gs.rbox_l, robot);
   stage_env(obs_s, nhw_s, env);
+  stage_env_boxes(gs.ebox, env);
   __syncthreads();
   const int gi = threadIdx.x / T, lg = threadIdx.x % T;
-  float4* cen = cen_all + gi * (nsp + 1);
+  float4* cen = gs.cen_all + gi * (nsp + 1);
+  const BoxCtx bx = box_ctx(gs, robot, nrbox, env.n_box, gi);
   const int n = rs.n;
   for (long long base = (long long)blockIdx.x * groups; base < N; base += (long long)gridDim.x * groups) {
     const long long i = base + gi;
@@ -52,8 +63,8 @@ __global__ void __launch_bounds__(128) k_check_path(const RobotDev* __restrict__
 #pragma unroll
     for (int j = 0; j < NDOF; ++j)
       qq[j] = (j < n) ? (float)__dadd_rn(va[j], __dmul_rn(t, __dsub_rn(vb[j], va[j]))) : 0.f;
-    const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, env.n_obs, env.n_obs_pad,
-                                            robot->self_pairs, robot->self_rr, E, cen, lg);
+    const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, env.n_obs, env.n_obs_pad,
+                                            robot->self_pairs, robot->self_rr, E, cen, lg, bx);
     if (i < N && lg == 0) {
       if (point_flags) point_flags[i] = hit ? 1 : 0;
       if (hit) edge_flags[k] = 1;  // every writer stores the same value
@@ -61,24 +72,50 @@ __global__ void __launch_bounds__(128) k_check_path(const RobotDev* __restrict__
   }
 }
 
-cudaError_t launch_check_path(const RobotDev* robot, int n, int nsp_pad, const EnvDev& env, float E,
+#if EZO_BOX_TU
+cudaError_t launch_check_path_box(const RobotDev* robot, int n, int nsp_pad, int n_rbox, const EnvDev& env, float E,
                               const double* verts, int n_edges, const long long* off, long long N,
                               uint8_t* point_flags, uint8_t* edge_flags, int T, int grid_cap, cudaStream_t s) {
   if (N <= 0 || n_edges <= 0) return cudaSuccess;
   cudaError_t err = cudaSuccess;
   const int threads = 128;
-  const size_t smem = check_smem_layout(nsp_pad, env.n_obs_pad, threads, T);
+  const size_t smem = check_smem_layout(nsp_pad, env.n_obs_pad, threads, T, n_rbox, env.n_box);
   const long long groups = threads / T;
   long long grid = (N + groups - 1) / groups;
   if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+  constexpr bool BB = EZO_BOX_TU != 0;
   EZO_DISPATCH_NDOF(n, EZO_DISPATCH_T(T, {
-    auto kern = k_check_path<ND, TT>;
+    auto kern = k_check_path<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
     kern<<<(unsigned)grid, threads, smem, s>>>(robot, env, E, verts, n_edges, off, N, point_flags, edge_flags);
   }));
   return cudaGetLastError();
 }
+#else
+cudaError_t launch_check_path(const RobotDev* robot, int n, int nsp_pad, int n_rbox, const EnvDev& env, float E,
+                              const double* verts, int n_edges, const long long* off, long long N,
+                              uint8_t* point_flags, uint8_t* edge_flags, int T, int grid_cap, cudaStream_t s) {
+  if (n_rbox || env.n_box) return launch_check_path_box(robot, n, nsp_pad, n_rbox, env, E, verts, n_edges, off, N, point_flags, edge_flags, T, grid_cap, s);
+  if (N <= 0 || n_edges <= 0) return cudaSuccess;
+  cudaError_t err = cudaSuccess;
+  const int threads = 128;
+  const size_t smem = check_smem_layout(nsp_pad, env.n_obs_pad, threads, T, n_rbox, env.n_box);
+  const long long groups = threads / T;
+  long long grid = (N + groups - 1) / groups;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+  constexpr bool BB = EZO_BOX_TU != 0;
+  EZO_DISPATCH_NDOF(n, EZO_DISPATCH_T(T, {
+    auto kern = k_check_path<ND, TT, BB>;
+    err = set_smem(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<(unsigned)grid, threads, smem, s>>>(robot, env, E, verts, n_edges, off, N, point_flags, edge_flags);
+  }));
+  return cudaGetLastError();
+}
+#endif
+
+#if !EZO_BOX_TU
 
 // One block per (segment k, polytope j of the same path): covered[k] = 1 when
 // polytope j exists (its segment was accepted or ran N_it rounds) and holds
@@ -114,5 +151,7 @@ cudaError_t launch_coverage(const BatchView& v, uint8_t* covered, double tol, cu
   k_coverage<<<grid, 128, 0, s>>>(v, covered, tol);
   return cudaGetLastError();
 }
+
+#endif  // !EZO_BOX_TU
 
 }  // namespace ezo

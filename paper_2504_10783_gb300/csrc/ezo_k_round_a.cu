@@ -6,7 +6,13 @@
 //                  selection of the first N_p colliding samples (Sec. IV-B)
 #include "ezo_kernels_common.cuh"
 
+#ifndef EZO_BOX_TU
+#define EZO_BOX_TU 0  // 1: this translation unit holds only the box-geometry collision kernels
+#endif
+
 namespace ezo {
+
+#if !EZO_BOX_TU
 
 // ------------------------------------------------------------ round kernels --
 // Round size of Sec. IV-B: delta_k = 6 delta / (pi^2 k^2),
@@ -159,23 +165,26 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
   }
 }
 
-template <int NDOF, int T>
+#endif  // !EZO_BOX_TU
+
+template <int NDOF, int T, bool BOX>
 __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pad) {
   extern __shared__ float4 smem4[];
   __shared__ RobotSmem rs;
   __shared__ int cur_env;
   const RobotDev* robot = v.robot;
-  const int nsp = robot->n_spheres_pad;
+  const int nsp = robot->n_spheres_pad, nrbox = robot->n_box;
   const int groups = blockDim.x / T;
-  float4* sph_s = smem4;
-  float4* obs_s = sph_s + nsp;
-  float4* cen_all = obs_s + max_obs_pad;
-  float* nhw_s = reinterpret_cast<float*>(cen_all + groups * (nsp + 1));
+  const GeomSmem gs = carve_geom(smem4, nsp, max_obs_pad, groups, nrbox, v.max_ebox);
+  float4* sph_s = gs.sph;
+  float4* obs_s = gs.obs;
+  float* nhw_s = gs.nhw;
   stage_robot(rs, sph_s, robot);
+  stage_robot_boxes(gs.rbox_l, robot);
   if (threadIdx.x == 0) cur_env = -1;
   __syncthreads();
   const int gi = threadIdx.x / T, lg = threadIdx.x % T;
-  float4* cen = cen_all + gi * (nsp + 1);
+  float4* cen = gs.cen_all + gi * (nsp + 1);
   const int n_tiles = v.summary->n_sample_tiles;
   constexpr int PASSES = kTile / (128 / T);
   // work units are (tile, pass): the passes of a tile go to different blocks
@@ -187,9 +196,11 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
     if (st.env != cur_env) {
       __syncthreads();
       stage_env(obs_s, nhw_s, ef.e);
+      stage_env_boxes(gs.ebox, ef.e);
       if (threadIdx.x == 0) cur_env = st.env;
       __syncthreads();
     }
+    const BoxCtx bx = box_ctx(gs, robot, nrbox, ef.e.n_box, gi);
     const float* S = v.S + (long long)v.n * st.sample_off;
     uint8_t* fl = v.flags + st.sample_off;
     {
@@ -199,12 +210,14 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
       float qq[NDOF];
 #pragma unroll
       for (int j = 0; j < NDOF; ++j) qq[j] = (j < v.n) ? S[(long long)j * st.s_cap + ic] : 0.f;
-      const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
-                                              robot->self_pairs, robot->self_rr, ef.E, cen, lg);
+      const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
+                                              robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
       if (valid && lg == 0) fl[i] = hit ? 1 : 0;
     }
   }
 }
+
+#if !EZO_BOX_TU
 
 // Set editing (Sec. VI-B): configuration x is a candidate when it collides
 // and lies in the current polytope, A x <= b + 1e-9 in FP64.
@@ -319,17 +332,38 @@ cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int g
   return cudaGetLastError();
 }
 
-cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s) {
+#endif  // !EZO_BOX_TU
+
+#if EZO_BOX_TU
+cudaError_t launch_round_check_box(const BatchView& v, int T, int grid, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
-  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T);
+  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T, v.n_rbox, v.max_ebox);
+  constexpr bool BB = EZO_BOX_TU != 0;
   EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
-    auto kern = k_round_check<ND, TT>;
+    auto kern = k_round_check<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
     kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
   }));
   return cudaGetLastError();
 }
+#else
+cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s) {
+  if (v.n_rbox || v.max_ebox) return launch_round_check_box(v, T, grid, s);
+  cudaError_t err = cudaSuccess;
+  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T, v.n_rbox, v.max_ebox);
+  constexpr bool BB = EZO_BOX_TU != 0;
+  EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
+    auto kern = k_round_check<ND, TT, BB>;
+    err = set_smem(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+  }));
+  return cudaGetLastError();
+}
+#endif
+
+#if !EZO_BOX_TU
 
 
 cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s) {
@@ -337,5 +371,7 @@ cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+
+#endif  // !EZO_BOX_TU
 
 }  // namespace ezo

@@ -7,25 +7,30 @@
 //   containment  - segment endpoints inside earlier polytopes (Sec. VI-A)
 #include "ezo_kernels_common.cuh"
 
+#ifndef EZO_BOX_TU
+#define EZO_BOX_TU 0  // 1: this translation unit holds only the box-geometry collision kernels
+#endif
+
 namespace ezo {
 
-template <int NDOF, int T>
+template <int NDOF, int T, bool BOX>
 __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_pad) {
   extern __shared__ float4 smem4[];
   __shared__ RobotSmem rs;
   __shared__ int cur_env;
   const RobotDev* robot = v.robot;
-  const int nsp = robot->n_spheres_pad;
+  const int nsp = robot->n_spheres_pad, nrbox = robot->n_box;
   const int groups = blockDim.x / T;
-  float4* sph_s = smem4;
-  float4* obs_s = sph_s + nsp;
-  float4* cen_all = obs_s + max_obs_pad;
-  float* nhw_s = reinterpret_cast<float*>(cen_all + groups * (nsp + 1));
+  const GeomSmem gs = carve_geom(smem4, nsp, max_obs_pad, groups, nrbox, v.max_ebox);
+  float4* sph_s = gs.sph;
+  float4* obs_s = gs.obs;
+  float* nhw_s = gs.nhw;
   stage_robot(rs, sph_s, robot);
+  stage_robot_boxes(gs.rbox_l, robot);
   if (threadIdx.x == 0) cur_env = -1;
   __syncthreads();
   const int gi = threadIdx.x / T, lg = threadIdx.x % T;
-  float4* cen = cen_all + gi * (nsp + 1);
+  float4* cen = gs.cen_all + gi * (nsp + 1);
   const int n = v.n;
   const int n_tiles = v.summary->n_bisect_tiles;
   static_assert(kTile % (128 / T) == 0, "tile must be a whole number of passes");
@@ -39,9 +44,11 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
     if (st.env != cur_env) {
       __syncthreads();
       stage_env(obs_s, nhw_s, ef.e);
+      stage_env_boxes(gs.ebox, ef.e);
       if (threadIdx.x == 0) cur_env = st.env;
       __syncthreads();
     }
+    const BoxCtx bx = box_ctx(gs, robot, nrbox, ef.e.n_box, gi);
     const double* v1 = v.v1 + (long long)g * n;
     const double* v2 = v.v2 + (long long)g * n;
     const float* S = v.S + (long long)n * st.sample_off;
@@ -74,8 +81,8 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
         float qq[NDOF];
 #pragma unroll
         for (int j = 0; j < NDOF; ++j) qq[j] = (float)fma(hi, dv[j], p[j]);
-        const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
-                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg);
+        const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
+                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
         if (valid && lg == 0) {
           v.s_ok[row] = hit ? 1 : 0;
           atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), 1ull);
@@ -91,8 +98,8 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
         float qq[NDOF];
 #pragma unroll
         for (int j = 0; j < NDOF; ++j) qq[j] = (float)fma(mid, dv[j], p[j]);
-        const bool hit = collide_group<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
-                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg);
+        const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
+                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
         if (hit) {
           hi = mid;
           bits |= 1u << s;
@@ -139,6 +146,8 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
     }
   }
 }
+
+#if !EZO_BOX_TU
 
 // Greedy placement: repeatedly take the closest surviving candidate (ties by
 // sample index), place a_i^T x <= b_i - Delta_i, discard candidates with
@@ -370,17 +379,38 @@ __global__ void k_containment(BatchView v, uint8_t* contained, double tol) {
   if (threadIdx.x == 0) contained[(long long)k * v.max_path_len + blockIdx.y] = s_out ? 0 : 1;
 }
 
-cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s) {
+#endif  // !EZO_BOX_TU
+
+#if EZO_BOX_TU
+cudaError_t launch_round_bisect_box(const BatchView& v, int T, int grid, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
-  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T);
+  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T, v.n_rbox, v.max_ebox);
+  constexpr bool BB = EZO_BOX_TU != 0;
   EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
-    auto kern = k_round_bisect<ND, TT>;
+    auto kern = k_round_bisect<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
     kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
   }));
   return cudaGetLastError();
 }
+#else
+cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s) {
+  if (v.n_rbox || v.max_ebox) return launch_round_bisect_box(v, T, grid, s);
+  cudaError_t err = cudaSuccess;
+  const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T, v.n_rbox, v.max_ebox);
+  constexpr bool BB = EZO_BOX_TU != 0;
+  EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
+    auto kern = k_round_bisect<ND, TT, BB>;
+    err = set_smem(kern, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+  }));
+  return cudaGetLastError();
+}
+#endif
+
+#if !EZO_BOX_TU
 
 cudaError_t launch_round_place(const BatchView& v, cudaStream_t s) {
   // alive bitmask for the largest N_p of the batch
@@ -404,5 +434,7 @@ cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double to
   return cudaGetLastError();
 }
 
+
+#endif  // !EZO_BOX_TU
 
 }  // namespace ezo

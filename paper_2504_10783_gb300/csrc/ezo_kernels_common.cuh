@@ -255,8 +255,49 @@ __device__ __forceinline__ void stage_polytope(float* A32, const double* __restr
 }
 
 // ------------------------------------------------------- collision checks --
-__host__ __device__ inline size_t check_smem_layout(int nsp, int nobs, int threads, int T) {
-  return (size_t)(nsp + nobs + (threads / T) * (nsp + 1)) * sizeof(float4) + (size_t)nobs * sizeof(float);
+// Shared memory of the collision kernels: robot spheres, obstacles, per group
+// sphere centres, obstacle offsets, then the boxes (robot boxes in their
+// frames, obstacle boxes, per group robot boxes in the world; 4 float4 each).
+__host__ __device__ inline size_t check_smem_layout(int nsp, int nobs, int threads, int T, int nrbox = 0,
+                                                    int nebox = 0) {
+  const int groups = threads / T;
+  return (size_t)(nsp + nobs + groups * (nsp + 1)) * sizeof(float4) + (size_t)nobs * sizeof(float) +
+         (size_t)4 * (nrbox + nebox + groups * nrbox) * sizeof(float4);
+}
+
+struct GeomSmem {
+  float4* sph;
+  float4* obs;
+  float4* cen_all;
+  float* nhw;
+  float4* rbox_l;
+  float4* ebox;
+  float4* rbox_w_all;
+};
+
+// nobs is a multiple of 8, so the box arrays after the obstacle offsets stay
+// 16-byte aligned
+__device__ __forceinline__ GeomSmem carve_geom(float4* base, int nsp, int nobs, int groups, int nrbox, int nebox) {
+  GeomSmem g;
+  g.sph = base;
+  g.obs = g.sph + nsp;
+  g.cen_all = g.obs + nobs;
+  g.nhw = reinterpret_cast<float*>(g.cen_all + groups * (nsp + 1));
+  g.rbox_l = reinterpret_cast<float4*>(g.nhw + nobs);
+  g.ebox = g.rbox_l + 4 * nrbox;
+  g.rbox_w_all = g.ebox + 4 * nebox;
+  return g;
+}
+
+__device__ __forceinline__ BoxCtx box_ctx(const GeomSmem& g, const RobotDev* robot, int nrbox, int n_ebox, int gi) {
+  BoxCtx b;
+  b.rbox_l = g.rbox_l;
+  b.ebox = g.ebox;
+  b.rbox_w = g.rbox_w_all + gi * 4 * nrbox;
+  b.n_ebox = n_ebox;
+  b.sb_pairs = robot->sb_pairs;
+  b.bb_pairs = robot->bb_pairs;
+  return b;
 }
 
 
@@ -293,6 +334,19 @@ __device__ __forceinline__ void project_fp64(const double (&c)[NDOF], const doub
     }                                        \
   } while (0)
 
+// BB = whether the scene has box geometries (separate kernels keep the
+// sphere-only ones at their register budget)
+#define EZO_DISPATCH_BOX(flag, ...) \
+  do {                              \
+    if (flag) {                     \
+      constexpr bool BB = true;     \
+      __VA_ARGS__;                  \
+    } else {                        \
+      constexpr bool BB = false;    \
+      __VA_ARGS__;                  \
+    }                               \
+  } while (0)
+
 #define EZO_DISPATCH_T(T, ...)               \
   do {                                       \
     if ((T) == 1) {                          \
@@ -313,10 +367,13 @@ __device__ __forceinline__ void project_fp64(const double (&c)[NDOF], const doub
 // Raises a kernel's dynamic shared memory limit once per (kernel, size).
 // The cache is keyed by the kernel's address: instantiations that share a
 // signature must not share an entry.
+// Raises a kernel's dynamic shared-memory limit to `bytes` (cached per
+// kernel). The default 48 KB limit covers static and dynamic shared memory
+// together, so the attribute is set for anything above 32 KB.
 inline cudaError_t set_smem_impl(const void* kernel, size_t bytes) {
   static std::mutex mu;
   static std::vector<std::pair<const void*, size_t>> done;
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes <= 32 * 1024) return cudaSuccess;
   std::lock_guard<std::mutex> lock(mu);
   for (auto& d : done)
     if (d.first == kernel && d.second >= bytes) return cudaSuccess;

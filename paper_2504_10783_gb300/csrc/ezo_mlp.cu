@@ -326,6 +326,8 @@ cudaError_t dal(T** p, size_t n) {
 
 }  // namespace
 
+extern "C" int ezo_internal_robot_boxes(const ezo_robot* r);
+extern "C" int ezo_internal_env_boxes(const ezo_env* e);
 extern "C" int ezo_internal_robot_prismatic(const ezo_robot* r);
 extern "C" void ezo_internal_set_error(const char* msg);
 extern "C" const ezo::RobotDev* ezo_internal_robot_dev(const ezo_robot* r, int* n, int* nsp_pad, double* q_lo,
@@ -659,6 +661,11 @@ ezo_status ezo_surrogate_train(ezo_surrogate* S, const ezo_env* env, int64_t n_s
                                void* stream) {
   if (!S || !env || n_samples < batch || batch < 64 || batch % 64 || epochs < 1 || !(lr > 0.f)) {
     ezo_internal_set_error("ezo_surrogate_train: need batch a multiple of 64, n_samples >= batch, epochs >= 1");
+    return EZO_ERR_INVALID_ARG;
+  }
+  if (ezo_internal_robot_boxes(S->robot) || ezo_internal_env_boxes(env)) {
+    // the labels come from the sphere signed-distance kernel
+    ezo_internal_set_error("ezo_surrogate_train: sphere geometries only (the robot or env has boxes)");
     return EZO_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;

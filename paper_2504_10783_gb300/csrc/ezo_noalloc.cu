@@ -95,6 +95,7 @@ int lanes_for(long long N) {
 
 // The robot and env handles are defined in ezo_capi.cu; these accessors give
 // this file the device images it needs without touching that code path.
+extern "C" int ezo_internal_robot_boxes(const ezo_robot* r);
 extern "C" const ezo::RobotDev* ezo_internal_robot_dev(const ezo_robot* r, int* n, int* nsp_pad, double* q_lo,
                                                        double* q_hi);
 extern "C" int ezo_internal_env_dev(const ezo_robot* r, const ezo_env* e, ezo::EnvDevFull* out);
@@ -237,6 +238,8 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   v.robot = rdev;
   v.envs = d_env;
   v.max_obs_pad = envf.e.n_obs_pad;
+  v.max_ebox = envf.e.n_box;
+  v.n_rbox = ezo_internal_robot_boxes(robot);
   v.nsp_pad = nsp_pad;
   v.np_max = np;
   v.path_first = d_pf;

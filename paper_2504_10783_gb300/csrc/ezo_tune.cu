@@ -24,6 +24,7 @@ extern "C" const ezo::RobotDev* ezo_internal_robot_dev(const ezo_robot* r, int* 
                                                        double* q_hi);
 extern "C" int ezo_internal_env_dev(const ezo_robot* r, const ezo_env* e, ezo::EnvDevFull* out);
 extern "C" void ezo_internal_set_error(const char* msg);
+extern "C" int ezo_internal_robot_boxes(const ezo_robot* r);
 
 namespace {
 
@@ -38,7 +39,7 @@ __global__ void k_uniform_configs(float* q, long long N, int n, const float* lo,
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int, int, int>, int> g_tune_cache;
 bool g_autotune = true;
 
 int size_class(long long N) {
@@ -70,7 +71,8 @@ extern "C" __attribute__((visibility("hidden"))) int ezo_internal_tuned_lanes(co
   int dev = 0;
   cudaGetDevice(&dev);
   const int cls = size_class(N);
-  const auto key = std::make_tuple(dev, n, nsp, head.n_self, ef.e.n_obs_pad, cls);
+  const int nrbox = ezo_internal_robot_boxes(robot);
+  const auto key = std::make_tuple(dev, n, nsp, head.n_self, ef.e.n_obs_pad, cls, nrbox, ef.e.n_box);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -101,11 +103,11 @@ extern "C" __attribute__((visibility("hidden"))) int ezo_internal_tuned_lanes(co
     for (int li = 0; li < 4; ++li) {
       const int T = lanes[li];
       // one warm-up launch, then the best of three
-      if (launch_check_flat(rd, n, nsp, ef.e, ef.E, q, M, M, flags, T, sms * 32, s) != cudaSuccess) continue;
+      if (launch_check_flat(rd, n, nsp, nrbox, ef.e, ef.E, q, M, M, flags, T, sms * 32, s) != cudaSuccess) continue;
       float t_best = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(e0, s);
-        launch_check_flat(rd, n, nsp, ef.e, ef.E, q, M, M, flags, T, sms * 32, s);
+        launch_check_flat(rd, n, nsp, nrbox, ef.e, ef.E, q, M, M, flags, T, sms * 32, s);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -95,6 +95,9 @@ def _sig(lib):
     f.ezo_surrogate_predict.argtypes = [_P, _P, _I64, _I64, _P, _P]
     f.ezo_batch_attach_surrogate.argtypes = [_P, _P, C.c_float]
     f.ezo_batch_set_sample_lanes.argtypes = [_P, _I32]
+    f.ezo_robot_add_boxes.argtypes = [_P, _I32, C.POINTER(_I32), _DP, _DP, _DP, _I32, C.POINTER(_I32), _I32,
+                                      C.POINTER(_I32)]
+    f.ezo_env_add_boxes.argtypes = [_P, _I32, _DP]
     f.ezo_path_points.argtypes = [_DP, _I32, _I32, C.c_double, C.POINTER(_I64), C.POINTER(_I64)]
     f.ezo_check_path.argtypes = [_P, _P, _DP, _I32, C.c_double, C.POINTER(C.c_uint8), _P, _I64,
                                  C.POINTER(_I64), _P]
@@ -171,6 +174,16 @@ class Robot:
                                       _ip(k[9]), _ip(k[10]) if k[10] is not None else None, C.byref(h)))
         self.h = h
         self.n = r.n
+        if getattr(r, "n_boxes", 0):
+            i32 = lambda x: np.ascontiguousarray(x, dtype=np.int32)
+            sb = i32(r.self_sb if r.self_sb is not None else np.zeros((0, 2))).reshape(-1)
+            bb = i32(r.self_bb if r.self_bb is not None else np.zeros((0, 2))).reshape(-1)
+            self._keep_boxes = [i32(r.box_frame), f64(r.box_xyz.reshape(-1)), f64(r.box_rot.reshape(-1)),
+                                f64(r.box_half.reshape(-1)), sb, bb]
+            kb = self._keep_boxes
+            _check(lib().ezo_robot_add_boxes(self.h, r.n_boxes, _ip(kb[0]), _dp(kb[1]), _dp(kb[2]), _dp(kb[3]),
+                                             sb.size // 2, _ip(sb) if sb.size else None, bb.size // 2,
+                                             _ip(bb) if bb.size else None))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -179,16 +192,21 @@ class Robot:
 
 
 class Env:
-    """ezo_env handle built from an (N_obs, 4) array or a workloads.Env."""
+    """ezo_env handle built from an (N_obs, 4) array or a workloads.Env
+    (spheres and, when present, oriented boxes)."""
 
-    def __init__(self, spheres):
+    def __init__(self, spheres, boxes=None):
         if isinstance(spheres, workloads.Env):
+            boxes = spheres.boxes if boxes is None else boxes
             spheres = spheres.spheres
         a = np.ascontiguousarray(spheres, dtype=np.float64).reshape(-1, 4)
         self.spheres = a
         h = _P()
         _check(lib().ezo_env_create(a.shape[0], _dp(a.reshape(-1)), C.byref(h)))
         self.h = h
+        if boxes is not None and len(boxes):
+            self.boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 15)
+            _check(lib().ezo_env_add_boxes(self.h, self.boxes.shape[0], _dp(self.boxes.reshape(-1))))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -17,6 +17,8 @@ collision-freeness needs a collision checker, checked by the FP64 oracle only.
   ``--batched`` is given; slower).
 * forest scene: the point robot among 15 disks (Sec. V) and a seed path from
   the bottom left to the top right corner (``--only-forest`` rewrites it).
+* boxes scene: the 11-box arm over a table-top scene with boxes and voxel
+  spheres and an 8-segment seed path (``--only-boxes``).
 * table_cloud scene: 1024 spheres of r = 0.02 from a synthetic table point
   cloud and a 64-segment seed path that runs close to them (of 12
   collision-free candidate steps the one with the least clearance)
@@ -178,22 +180,39 @@ def forest_scene(seed=41, step=1.0, margin=0.02, max_steps=80):
     return {"robot": "point2", "forest_seed": seed, "path": np.asarray(verts).tolist()}
 
 
+def box_scene(seed=51, n_seg=8):
+    """Box geometries (Sec. IV-D, VII): the 11-box arm over a table-top scene
+    (table, two boxes, voxel spheres) and an 8-segment seed path that keeps,
+    of 8 collision-free candidate steps, the one with the least clearance."""
+    robot = wl.box_arm_robot()
+    env = wl.tabletop_box_env(seed)
+    rng = np.random.default_rng(seed + 1)
+    path = None
+    while path is None:
+        path = random_path(robot, env, rng, n_seg, hug=8)
+    return {"robot": "box_arm", "env_seed": seed, "path": path.tolist()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--batched", action="store_true")
     ap.add_argument("--stress", action="store_true")
     ap.add_argument("--only-stress", action="store_true", help="rewrite only the table_cloud scene")
     ap.add_argument("--only-forest", action="store_true", help="rewrite only the forest scene")
+    ap.add_argument("--only-boxes", action="store_true", help="rewrite only the box scene")
     args = ap.parse_args()
     data = {}
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    if not args.only_stress and not args.only_forest:
+    only = args.only_stress or args.only_forest or args.only_boxes
+    if not only:
         data["planar3"] = planar_scene()
         data["dh7"] = dh7_scene()
-    if not args.only_stress:
+    if not only or args.only_forest:
         data["forest"] = forest_scene()
+    if not only or args.only_boxes:
+        data["boxes"] = box_scene()
     if args.batched:
         data["dh7_batched"] = batched_scenes()
     if args.stress or args.only_stress:

@@ -112,3 +112,16 @@ def test_box_arm_poses_and_labels():
     assert 0.2 < lab.mean() < 0.9
     # the arm straight up misses everything: the table top is at z = 0 and 0.2 m away
     assert not orc.in_collision(r, env, np.zeros((1, 7)))[0]
+
+
+def test_box_seed_path_is_collision_free():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "workloads.json")) as f:
+        s = json.load(f)["boxes"]
+    r = wl.box_arm_robot()
+    env = wl.tabletop_box_env(s["env_seed"])
+    V = np.asarray(s["path"])
+    for k in range(V.shape[0] - 1):
+        t = np.linspace(0.0, 1.0, 200)[:, None]
+        assert orc.signed_distance(r, env, V[k] + t * (V[k + 1] - V[k])).min() >= 0.02

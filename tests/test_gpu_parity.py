@@ -66,13 +66,13 @@ def gpu_labels(ezo, robot, env, q, lanes=0):
     return flags.cpu().numpy().astype(bool)
 
 
-def assert_labels_match(rd, env_np, q32, got):
+def assert_labels_match(rd, env_np, q32, got, band=AMB):
     q64 = q32.astype(np.float64)
     ref = orc.in_collision(rd, env_np, q64)
     diff = got != ref
     if diff.any():
         sd = orc.signed_distance(rd, env_np, q64[diff])
-        assert np.all(np.abs(sd) < AMB), f"{int((np.abs(sd) >= AMB).sum())} labels differ outside the band"
+        assert np.all(np.abs(sd) < band), f"{int((np.abs(sd) >= band).sum())} labels differ outside the band"
     return ref
 
 
@@ -217,7 +217,7 @@ def test_round_walks_equal_flat_walks(ezo, lanes):
 
 
 # ----------------------------------------------------- round-by-round replay --
-def _replay_rounds(ezo, rd, env_np, v1, v2, prm_kw, max_rounds=6):
+def _replay_rounds(ezo, rd, env_np, v1, v2, prm_kw, max_rounds=6, band=AMB):
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
     prm = ezo.Params.make(**prm_kw)
     oprm = orc.Params(eps=prm.eps, delta=prm.delta, tau=prm.tau, step_back_max=prm.step_back_max,
@@ -242,7 +242,7 @@ def _replay_rounds(ezo, rd, env_np, v1, v2, prm_kw, max_rounds=6):
         err = np.abs(S[:600] - ref).max(axis=1)
         assert np.quantile(err, 0.99) < 1e-3 and np.median(err) < 1e-4, np.quantile(err, [0.5, 0.99])
         lab = bt.read(0, "labels")[: st["n_samples"]].astype(bool)
-        assert_labels_match(rd, env_np, S.astype(np.float32), lab)
+        assert_labels_match(rd, env_np, S.astype(np.float32), lab, band)
         bt.step(3)
         bt.sync()
         st = bt.state(0)
@@ -262,7 +262,7 @@ def _replay_rounds(ezo, rd, env_np, v1, v2, prm_kw, max_rounds=6):
         nc = idx.size
         bits = bt.read(0, "bits")[:nc]
         follow = ((bits[:, None] >> np.arange(oprm.n_b)[None, :]) & 1).astype(bool)
-        br = orc.bisect(rd, env_np, S[idx], v1, v2, oprm.n_b, follow=follow, band=AMB)
+        br = orc.bisect(rd, env_np, S[idx], v1, v2, oprm.n_b, follow=follow, band=band)
         total_amb += br.ambiguous
         np.testing.assert_array_equal(br.decisions, follow)
         cst = bt.read(0, "c_star")[:, :nc].T
@@ -378,6 +378,77 @@ def test_forest_path_polytopes_contain_segments_and_certify(ezo):
         rate = orc.in_collision(rd, env_np, x).mean()
         assert rate <= FOREST_PRM["eps"] + 4 * np.sqrt(FOREST_PRM["eps"] / x.shape[0])
     assert bt.coverage().all() and kept >= 1
+
+
+# ---------------------------------------------------- box geometries (IV-D) --
+# Box pairs are decided in FP32 by a separating-axis test whose cross-product
+# axes are not normalised; the label band for scenes with boxes is 5e-5 m on
+# the oracle's FP64 value (its error bound for the largest skipped-axis angle).
+AMB_BOX = 5e-5
+
+
+def box_scene():
+    s = scenes()["boxes"]
+    return wl.box_arm_robot(), wl.tabletop_box_env(s["env_seed"]), np.asarray(s["path"])
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_box_arm_labels_match_oracle(ezo, lanes):
+    """11-box arm (26 box-box self pairs) over a table box, two rotated boxes
+    and voxel spheres: every pair type with a box, against the FP64 oracle."""
+    rd, env_np, _ = box_scene()
+    q = wl.uniform_configs(31, rd, 20000)
+    got = gpu_labels(ezo, ezo.Robot(rd), ezo.Env(env_np), q, lanes=lanes)
+    ref = assert_labels_match(rd, env_np, q.astype(np.float32), got, AMB_BOX)
+    assert 0.2 < ref.mean() < 0.9
+
+
+def test_sphere_arm_with_boxes_and_self_box_pairs(ezo):
+    """The 40-sphere arm with the 11 boxes added, sphere-box self pairs
+    between the first link's spheres and the boxes of frames >= 4, over the
+    table-top scene: sphere x box, box x sphere, box x box, both self kinds."""
+    base, env_np, _ = box_scene()
+    sph = wl.dh7_robot()
+    link1 = np.nonzero(sph.sphere_link == sph.sphere_link.min())[0]
+    far = np.nonzero(base.box_frame >= 4)[0]
+    sb = np.array([(i, k) for i in link1 for k in far], dtype=np.int32)
+    rd = wl.Robot(name="mixed_boxes", a=sph.a, alpha=sph.alpha, d=sph.d, theta_off=sph.theta_off, q_lo=sph.q_lo,
+                  q_hi=sph.q_hi, sphere_frame=sph.sphere_frame, sphere_xyz=sph.sphere_xyz, sphere_r=sph.sphere_r,
+                  sphere_link=sph.sphere_link, self_pairs=sph.self_pairs, box_frame=base.box_frame,
+                  box_xyz=base.box_xyz, box_rot=base.box_rot, box_half=base.box_half, self_sb=sb,
+                  self_bb=base.self_bb)
+    q = wl.uniform_configs(32, rd, 20000)
+    got = gpu_labels(ezo, ezo.Robot(rd), ezo.Env(env_np), q)
+    ref = assert_labels_match(rd, env_np, q.astype(np.float32), got, AMB_BOX)
+    assert 0.2 < ref.mean() < 0.95
+    # sphere geometries only: the signed distance refuses boxes
+    sd = torch.empty(16, device="cuda")
+    with pytest.raises(RuntimeError):
+        ezo.signed_distance(ezo.Robot(rd), ezo.Env(env_np), to_dev(q[:16]), sd)
+
+
+def test_round_replay_boxes(ezo):
+    rd, env_np, path = box_scene()
+    rounds, _ = _replay_rounds(ezo, rd, env_np, path[0], path[1],
+                               dict(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, seed=2),
+                               max_rounds=3, band=AMB_BOX)
+    assert rounds >= 1
+
+
+def test_box_path_polytopes_contain_segments(ezo):
+    rd, env_np, path = box_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    K = path.shape[0] - 1
+    bt = ezo.Batch(robot, [env], path[:-1], path[1:],
+                   ezo.Params.make(eps=0.1, delta=0.05, n_p=2000, n_f=10, n_b=10, n_mix=30, n_it_max=20, seed=3),
+                   seg_stream=np.arange(K, dtype=np.uint32), path_first=np.zeros(K, np.int32))
+    bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)
+    for g in range(K):
+        r = bt.segment(g)
+        if r.status != ezo.SEG_SKIPPED:
+            assert r.status in (ezo.SEG_ACCEPTED, ezo.SEG_MAX_ITER)
+            assert orc.segment_contained(r.A, r.b, path[g], path[g + 1], tol=1e-12)
+    assert bt.coverage().all()
 
 
 # ------------------------------------------------------------- end to end --
