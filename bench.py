@@ -35,7 +35,9 @@ N_SEEDS = 20
 # DRAM bytes per launch of the round kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, ncu, this workload); None where not captured for the
 # current kernel
-TRAFFIC = {}
+TRAFFIC = {"sample": 87808}  # round kernel capture, one launch (10 segments x 1e4 walks)
+# DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe)
+CHECKER_TRAFFIC_2E6 = 56078336 + 154368
 KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
 
 
@@ -390,7 +392,8 @@ def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, fl
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     return {"batch": N, "configs_per_s": N / (per / 1e3), "ms_per_launch": per,
             "roofline": {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
-                         "flops_per_config": flops_cfg, "traffic": None},
+                         "flops_per_config": flops_cfg,
+                         "traffic": CHECKER_TRAFFIC_2E6 if N == 2_000_000 else None},
             "paper_context": "paper: ~8.6 M configs/s, Franka (1187 pairs), RTX 3090, same batch size",
             "launches": reps + 3}
 
@@ -454,6 +457,8 @@ def main():
     ap.add_argument("--seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--only-checker", action="store_true",
+                    help="only the collision checker on 2e6 configurations (for profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed path steps and the kernel pass (no plain, surrogate or checker legs)")
     ap.add_argument("--workload", default="path", choices=["path", "batched", "stress"])
@@ -491,6 +496,13 @@ def main():
 
     rd, env_np, path = load_scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    if args.only_checker:
+        # autotuner (4 lane counts x 4 launches), 3 warm-up and 10 timed launches
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+        props = torch.cuda.get_device_properties(local)
+        print(json.dumps(measure_checker(ezo, torch, robot, env, rd, torch.cuda.current_stream(), flush, props,
+                                         2070.0, ezo.check_flops(robot, env))))
+        return
     K = path.shape[0] - 1
     mode = ezo.RUN_GRAPH if args.mode == "graph" else ezo.RUN_HOST_LOOP
     streams = np.arange(K, dtype=np.uint32) + 1000 * rank  # each rank inflates its own random draw

@@ -320,12 +320,14 @@ __device__ __forceinline__ void project_fp64(const double (&c)[NDOF], const doub
   for (int j = 0; j < NDOF; ++j) p[j] = (j < n) ? ((ee > 0.0) ? (1.0 - alpha) * v1[j] + alpha * v2[j] : v1[j]) : 0.0;
 }
 
+// ND = the smallest compiled chain length >= n (3, 7 or 16); every kernel
+// guards its loops with j < n, so shorter chains run in a longer template.
 #define EZO_DISPATCH_NDOF(n, ...)            \
   do {                                       \
-    if ((n) == 7) {                          \
+    if ((n) > 3 && (n) <= 7) {               \
       constexpr int ND = 7;                  \
       __VA_ARGS__;                           \
-    } else if ((n) == 3) {                   \
+    } else if ((n) <= 3) {                   \
       constexpr int ND = 3;                  \
       __VA_ARGS__;                           \
     } else {                                 \
