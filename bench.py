@@ -32,6 +32,7 @@ WORKLOAD = ("7-DOF DH arm (d=[0.34,0,0.40,0,0.40,0,0.126], 40 spheres r 0.04-0.0
 PARAMS = dict(eps=0.05, delta=0.05, tau=0.5, step_back_max=0.01, t_col=1e-3, n_p=10000, n_f=10, n_b=10, n_mix=60,
               n_it_max=50, seed=1)
 N_SEEDS = 20
+SEGSTATE_BYTES = 112  # sizeof(SegState): per-segment device state read back with the polytopes
 # DRAM bytes per launch of the round kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, ncu, this workload); None where not captured for the
 # current kernel
@@ -636,8 +637,9 @@ def main():
                                       N=100_000_000, reps=3)
 
     # ---- end to end through the public API with host buffers ----
-    v1h = np.ascontiguousarray(path[:-1])
-    v2h = np.ascontiguousarray(path[1:])
+    # the step's inputs in pinned host memory
+    v1h = torch.from_numpy(np.ascontiguousarray(path[:-1])).pin_memory().numpy()
+    v2h = torch.from_numpy(np.ascontiguousarray(path[1:])).pin_memory().numpy()
     e2e_times = []
     d2h = 0
     e2e_units = 0
@@ -648,11 +650,9 @@ def main():
         t0 = time.perf_counter()
         b.reset(v1h, v2h)
         b.run_path(sequential=False, mode=mode)
-        d2h = 0
-        for g in range(K):
-            r = b.segment(g)
-            if r.status != ezo.SEG_SKIPPED:
-                d2h += r.A.nbytes + r.b.nbytes
+        status, As, bs = b.polytopes()  # every segment's polytope in three copies
+        m_read = max(a.shape[0] for a in As)
+        d2h = int(K * (m_read * (rd.n + 1) * 8 + SEGSTATE_BYTES))
         e2e_times.append(time.perf_counter() - t0)
         w = work[i % N_SEEDS]
         e2e_units += w["sample_checks"] + w["bisection_checks"]

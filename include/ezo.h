@@ -235,6 +235,16 @@ ezo_status ezo_batch_get_segment(const ezo_batch* batch, int32_t seg, int32_t* s
  * writes its row count to *m. */
 ezo_status ezo_batch_get_polytope(const ezo_batch* batch, int32_t seg, int32_t* m, double* A, double* b);
 
+/* Every segment at once, for end-to-end readers: status[g] and m[g] (host,
+ * n_seg entries each), and, when A / b are given, the first m_read = max_g
+ * m[g] rows of every polytope into A (host, n_seg x rows x n, row major per
+ * segment: segment g's row r at A[(g * rows + r) * n]) and b (n_seg x rows);
+ * rows beyond m[g] are not meaningful. *m_read (nullable) receives m_read.
+ * One state copy and one strided copy each for A and b. Synchronous.
+ * EZO_ERR_CAPACITY when rows < m_read. */
+ezo_status ezo_batch_get_polytopes(const ezo_batch* batch, int32_t* status, int32_t* m, double* A, double* b,
+                                   int32_t rows, int32_t* m_read, void* cuda_stream);
+
 /* Row capacity per segment (m0 + n_f * n_it_max) and sample capacity. */
 ezo_status ezo_batch_capacity(const ezo_batch* batch, int32_t* m_cap, int32_t* s_cap);
 

@@ -1209,6 +1209,35 @@ ezo_status ezo_batch_get_polytope(const ezo_batch* b, int32_t seg, int32_t* m, d
   return EZO_OK;
 }
 
+ezo_status ezo_batch_get_polytopes(const ezo_batch* b, int32_t* status, int32_t* m, double* A, double* bv,
+                                   int32_t rows, int32_t* m_read, void* stream_v) {
+  if (!b || !status || !m || rows < 0 || ((A || bv) && rows < 1))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_get_polytopes: bad argument");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  std::vector<SegState> sts(b->B);
+  EZO_CUDA(cudaMemcpyAsync(sts.data(), b->d_st, sizeof(SegState) * b->B, cudaMemcpyDeviceToHost, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  int mmax = 0;
+  for (int g = 0; g < b->B; ++g) {
+    status[g] = sts[g].status;
+    m[g] = sts[g].m;
+    mmax = std::max(mmax, sts[g].m);
+  }
+  if (m_read) *m_read = mmax;
+  if ((A || bv) && mmax > rows) return fail(EZO_ERR_CAPACITY, "ezo_batch_get_polytopes: rows below the largest m");
+  const size_t n = b->n, mc = b->m_cap;
+  // the first mmax rows of every segment: one strided copy each for A and b
+  if (A && mmax)
+    EZO_CUDA(cudaMemcpy2DAsync(A, sizeof(double) * rows * n, b->d_A, sizeof(double) * mc * n, sizeof(double) * mmax * n,
+                               b->B, cudaMemcpyDeviceToHost, s));
+  if (bv && mmax)
+    EZO_CUDA(cudaMemcpy2DAsync(bv, sizeof(double) * rows, b->d_b, sizeof(double) * mc, sizeof(double) * mmax, b->B,
+                               cudaMemcpyDeviceToHost, s));
+  EZO_CUDA(cudaStreamSynchronize(s));
+  g_err.clear();
+  return EZO_OK;
+}
+
 ezo_status ezo_batch_capacity(const ezo_batch* b, int32_t* m_cap, int32_t* s_cap) {
   if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_capacity: null batch");
   if (m_cap) *m_cap = b->m_cap;

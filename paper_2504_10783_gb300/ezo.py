@@ -95,6 +95,7 @@ def _sig(lib):
     f.ezo_surrogate_predict.argtypes = [_P, _P, _I64, _I64, _P, _P]
     f.ezo_batch_attach_surrogate.argtypes = [_P, _P, C.c_float]
     f.ezo_batch_set_sample_lanes.argtypes = [_P, _I32]
+    f.ezo_batch_get_polytopes.argtypes = [_P, C.POINTER(_I32), C.POINTER(_I32), _DP, _DP, _I32, C.POINTER(_I32), _P]
     f.ezo_robot_add_boxes.argtypes = [_P, _I32, C.POINTER(_I32), _DP, _DP, _DP, _I32, C.POINTER(_I32), _I32,
                                       C.POINTER(_I32)]
     f.ezo_env_add_boxes.argtypes = [_P, _I32, _DP]
@@ -388,6 +389,18 @@ class Batch:
         _check(lib().ezo_batch_get_polytope(self.h, g, C.byref(mm), _dp(A), _dp(b)))
         return SegmentResult(st.value, rd.value, m.value, pl.value, ch.value, A[: mm.value].copy(),
                              b[: mm.value].copy())
+
+    def polytopes(self, stream=None):
+        """Every segment's (status, A, b) with three device-to-host copies:
+        returns (status int32 [B], list of A [m_g, n], list of b [m_g])."""
+        st = np.zeros(self.B, dtype=np.int32)
+        m = np.zeros(self.B, dtype=np.int32)
+        A = np.empty((self.B, self.m_cap, self.n))
+        b = np.empty((self.B, self.m_cap))
+        mr = _I32()
+        _check(lib().ezo_batch_get_polytopes(self.h, st.ctypes.data_as(C.POINTER(_I32)), m.ctypes.data_as(C.POINTER(_I32)),
+                                             _dp(A), _dp(b), self.m_cap, C.byref(mr), _stream(stream)))
+        return st, [A[g, : m[g]] for g in range(self.B)], [b[g, : m[g]] for g in range(self.B)]
 
     def state(self, g: int) -> dict:
         o = np.zeros(12, dtype=np.int32)

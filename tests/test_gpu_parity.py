@@ -495,6 +495,21 @@ def test_batched_segments_equal_single_segments(ezo):
         assert one.rounds == many.rounds
 
 
+def test_bulk_polytope_read_equals_per_segment_reads(ezo):
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    K = path.shape[0] - 1
+    bt = ezo.Batch(robot, [env], path[:-1], path[1:], ezo.Params.make(n_p=2000, n_mix=30, seed=4),
+                   seg_stream=np.arange(K, dtype=np.uint32), path_first=np.zeros(K, np.int32))
+    bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)
+    st, As, bs = bt.polytopes()
+    for g in range(K):
+        r = bt.segment(g)
+        assert st[g] == r.status
+        np.testing.assert_array_equal(As[g], r.A)
+        np.testing.assert_array_equal(bs[g], r.b)
+
+
 def test_inflate_path_sequential_equals_speculative(ezo):
     rd, env_np, path = dh7_scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
