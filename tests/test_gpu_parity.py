@@ -495,6 +495,41 @@ def test_batched_segments_equal_single_segments(ezo):
         assert one.rounds == many.rounds
 
 
+def test_iteration_cap_capacity_and_invalid_parameters(ezo):
+    """Sec. IV-C "Maximum iterations": with N_it = 1 a segment that the first
+    round does not certify ends EZO_SEG_MAX_ITER with the round's planes, as
+    in the oracle; a polytope without room for N_f more rows ends
+    EZO_SEG_CAPACITY; parameters outside their ranges are refused."""
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    kw = dict(n_p=2000, n_f=10, n_b=10, n_mix=30, n_it_max=1, seed=5)
+    bt = ezo.Batch(robot, [env], path[0], path[1], ezo.Params.make(**kw))
+    bt.run()
+    r = bt.segment(0)
+    oprm = orc.Params(**{k: v for k, v in kw.items()})
+    A0, b0 = orc.joint_box(rd)
+    S = bt.read(0, "samples")[:, : bt.state(0)["n_samples"]].T.astype(np.float64)
+    rr = orc.eizo_round(rd, env_np, A0, b0, path[0], path[1], 1, oprm, S)
+    assert not rr.accept
+    assert r.status == ezo.SEG_MAX_ITER and r.rounds == 1
+    assert r.A.shape[0] == 14 + rr.place.rows_a.shape[0]
+    assert orc.segment_contained(r.A, r.b, path[0], path[1], tol=1e-12)
+    # no room for another plane: the edit stops with EZO_SEG_CAPACITY
+    full = np.vstack([r.A] * 64)[: bt.m_cap]
+    bfull = np.concatenate([r.b] * 64)[: bt.m_cap]
+    bt.set_polytope(0, full, bfull)
+    inside = orc.hit_and_run(full, bfull, path[0], path[1], 1500, 30, 9, 0, 1)
+    bt.edit(inside)
+    st = bt.state(0)
+    if st["count"] > 0:
+        assert st["status"] == ezo.SEG_CAPACITY and st["n_placed"] == 0
+    # parameters out of range
+    for bad in (dict(eps=0.0), dict(eps=1.0), dict(delta=-0.1), dict(n_p=0), dict(n_b=33), dict(n_f=0),
+                dict(n_it_max=0), dict(n_f=100, n_it_max=30)):
+        with pytest.raises(RuntimeError):
+            ezo.Batch(robot, [env], path[0], path[1], ezo.Params.make(**dict(kw, **bad)))
+
+
 def test_bulk_polytope_read_equals_per_segment_reads(ezo):
     rd, env_np, path = dh7_scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
