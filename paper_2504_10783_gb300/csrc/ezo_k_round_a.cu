@@ -257,14 +257,28 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
   }
   __syncthreads();
   int my_count = 0;
-  for (int base = 0; base < S; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    int f = (i < S) ? (fl[i] != 0) : 0;
-    if (v.edit && f) f = edit_inside(v, g, st, i) ? 1 : 0;
-    if (i < M) my_count += f;
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    const int pre = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) warp_col[wid] = __popc(bal);
+  // four consecutive samples per thread and pass (fewer block barriers)
+  constexpr int PER = 4;
+  for (int base = 0; base < S; base += PER * (int)blockDim.x) {
+    const int i0 = base + PER * (int)threadIdx.x;
+    int f[PER];
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = i0 + k;
+      f[k] = (i < S) ? (fl[i] != 0) : 0;
+      if (v.edit && f[k]) f[k] = edit_inside(v, g, st, i) ? 1 : 0;
+      if (i < M) my_count += f[k];
+      cnt += f[k];
+    }
+    // stable positions: warp scan of the per-thread counts, then the warps
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_col[wid] = x;
     __syncthreads();
     if (wid == 0) {
       int w = lane < nw ? warp_col[lane] : 0;
@@ -277,12 +291,18 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
     }
     __syncthreads();
     const int running = s_running;
-    const int pos = running + (wid ? warp_cnt[wid - 1] : 0) + pre;
-    if (f && pos < np) cidx[pos] = i;
+    int pos = running + (wid ? warp_cnt[wid - 1] : 0) + x - cnt;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      if (f[k]) {
+        if (pos < np) cidx[pos] = i0 + k;
+        ++pos;
+      }
+    }
     __syncthreads();
     if (threadIdx.x == 0) s_running = running + warp_cnt[nw - 1];
     __syncthreads();
-    if (!v.edit && s_running >= np && base + (int)blockDim.x >= M) break;
+    if (!v.edit && s_running >= np && base + PER * (int)blockDim.x >= M) break;
   }
   // block reduction of the count over the first M samples
 #pragma unroll
