@@ -201,6 +201,9 @@ __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
       best_c = c;
     }
   }
+  // warp 0's lane j < n keeps the segment's endpoints' coordinate j
+  const double my_v1 = (wid == 0 && lane < n) ? v1[lane] : 0.0;
+  const double my_v2 = (wid == 0 && lane < n) ? v2[lane] : 0.0;
   for (int f = 0; f < v.n_f; ++f) {
     // block arg-min of (distance, sample index) over the survivors
 #pragma unroll
@@ -235,32 +238,53 @@ __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
           bc = c2;
         }
       }
+      // the plane, with the loads of warp 0's lanes in flight together: lane
+      // j < n holds a_j = (grad dist_L(c*))_j (Eq. 10, from the bisection
+      // kernel) and v1_j, v2_j; lane 0 the distance and b = a^T c*
+      const bool have = bc >= 0;
+      double a = 0.0, dbc = 0.0, bval = 0.0;
+      if (have && lane < n) a = v.ga[(long long)n * co + (long long)lane * np + bc];
+      if (have && lane == 0) {
+        dbc = dist[bc];
+        bval = v.gb[co + bc];
+      }
+      double av1 = a * my_v1, av2 = a * my_v2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        av1 += __shfl_xor_sync(0xffffffffu, av1, o);
+        av2 += __shfl_xor_sync(0xffffffffu, av2, o);
+      }
+      int stop = 0;
+      double beta = 0.0, delta = 0.0;
+      int row = 0;
       if (lane == 0) {
-        s_best = bc;
-        if (bc < 0) {
-          s_stop = 1;
-        } else if (dist[bc] <= v.t_col) {
-          s_stop = 2;  // segment likely in collision (Sec. IV-C)
+        if (!have) {
+          stop = 1;
+        } else if (dbc <= v.t_col) {
+          stop = 2;  // segment likely in collision (Sec. IV-C)
         } else if (st.m >= v.m_cap) {
-          s_stop = 3;
+          stop = 3;
         } else {
-          // a = grad dist_L(c*), b = a^T c* (Eq. 10), computed by the bisection kernel
-          double bval = v.gb[co + bc], av1 = 0.0, av2 = 0.0;
-          for (int j = 0; j < n; ++j) {
-            const double a = v.ga[(long long)n * co + (long long)j * np + bc];
-            s_a[j] = a;
-            s_a32[j] = (float)a;
-            av1 = fma(a, v1[j], av1);
-            av2 = fma(a, v2[j], av2);
-          }
           // step back (Eqs. 11-12): r = max(a^T v1, a^T v2) - b + Delta_max
           const double r = fmax(av1, av2) - bval + v.step_back_max;
-          const double delta = r > 0.0 ? v.step_back_max - r : v.step_back_max;
-          const double beta = bval - delta;
+          delta = r > 0.0 ? v.step_back_max - r : v.step_back_max;
+          beta = bval - delta;
+          row = st.m;
+        }
+      }
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      row = __shfl_sync(0xffffffffu, row, 0);
+      if (stop == 0 && lane < n) {
+        s_a[lane] = a;
+        s_a32[lane] = (float)a;
+        A[(long long)row * n + lane] = a;
+      }
+      if (lane == 0) {
+        s_best = bc;
+        s_stop = stop;
+        if (stop == 0) {
           s_beta = beta;
           s_beta32 = (float)beta;
-          const int row = st.m;
-          for (int j = 0; j < n; ++j) A[(long long)row * n + j] = s_a[j];
           bb[row] = beta;
           st.m = row + 1;
           v.placed_idx[g * v.n_f + f] = bc;
