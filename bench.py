@@ -559,7 +559,7 @@ def main():
         times.append(e0.elapsed_time(e1))
         w = work[i % N_SEEDS]
         units += w["sample_checks"] + w["bisection_checks"]
-        launches += 7 * w["rounds"] + 1
+        launches += 6 * w["rounds"] + 2  # first sizing, 6 kernels per round, containment
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()

@@ -641,7 +641,7 @@ ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
   if (g_prof_on) {
     e0 = b->events.get();
     e1 = b->events.get();
-    b->events.kind.push_back(step);
+    b->events.kind.push_back(step == 7 ? 6 : step);  // the fused close counts as round end
     cudaEventRecord(e0, s);
   }
   switch (step) {
@@ -652,6 +652,7 @@ ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
     case 4: e = launch_bisect_step(b, s); break;
     case 5: e = launch_round_place(b->view, s); break;
     case 6: e = launch_round_end(b->view, s); break;
+    case 7: e = launch_round_close(b->view, s); break;  // 6 fused with the next round's 0
     default: return fail(EZO_ERR_INVALID_ARG, "ezo_batch_step: step must be in [0, 6]");
   }
   if (g_prof_on) cudaEventRecord(e1, s);
@@ -672,9 +673,15 @@ void collect_profile(ezo_batch* b) {
   b->events.used = 0;
 }
 
+// The run loops size the first round once; every round then ends with the
+// fused round-close kernel, which also sizes the next round.
+const int kRoundSteps[6] = {1, 2, 3, 4, 5, 7};
+
 ezo_status run_host_loop(ezo_batch* b, cudaStream_t s) {
+  ezo_status st0 = launch_step(b, 0, s);
+  if (st0 != EZO_OK) return st0;
   for (int r = 0; r <= b->prm.n_it_max + 1; ++r) {
-    for (int step = 0; step < 7; ++step) {
+    for (int step : kRoundSteps) {
       ezo_status st = launch_step(b, step, s);
       if (st != EZO_OK) return st;
     }
@@ -689,6 +696,22 @@ ezo_status run_host_loop(ezo_batch* b, cudaStream_t s) {
 ezo_status build_graph(ezo_batch* b) {
 #if CUDART_VERSION >= 12040
   EZO_CUDA(cudaGraphCreate(&b->graph, 0));
+  if (!b->cap_stream) EZO_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  // the first round's sizing, then a WHILE node whose body runs a round and
+  // sizes the next one
+  EZO_CUDA(cudaStreamBeginCaptureToGraph(b->cap_stream, b->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  ezo_status st = launch_step(b, 0, b->cap_stream);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &captured);
+  if (st != EZO_OK || ce != cudaSuccess) {
+    g_prof_on = prof;
+    return st != EZO_OK ? st : cuda_fail(ce, "cudaStreamEndCapture");
+  }
+  cudaGraphNode_t first = nullptr;
+  size_t n_nodes = 1;
+  EZO_CUDA(cudaGraphGetNodes(b->graph, &first, &n_nodes));
   cudaGraphConditionalHandle h;
   EZO_CUDA(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp{};
@@ -697,18 +720,16 @@ ezo_status build_graph(ezo_batch* b) {
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  EZO_CUDA(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &cp));
+  EZO_CUDA(cudaGraphAddNode(&node, b->graph, &first, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if (!b->cap_stream) EZO_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   BatchView saved = b->view;
   b->view.graph_cond = (unsigned long long)h;
-  const bool prof = g_prof_on;
-  g_prof_on = false;
   EZO_CUDA(cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  ezo_status st = EZO_OK;
-  for (int step = 0; step < 7 && st == EZO_OK; ++step) st = launch_step(b, step, b->cap_stream);
-  cudaGraph_t captured = nullptr;
-  cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &captured);
+  for (int step : kRoundSteps) {
+    if (st != EZO_OK) break;
+    st = launch_step(b, step, b->cap_stream);
+  }
+  ce = cudaStreamEndCapture(b->cap_stream, &captured);
   g_prof_on = prof;
   b->view = saved;
   if (st != EZO_OK) return st;

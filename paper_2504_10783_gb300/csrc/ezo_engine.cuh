@@ -144,6 +144,8 @@ cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 // (Sec. VI-A): contained[k*max_path_len + d] = 1 iff both endpoints of
 // segment k satisfy A_j x <= b_j + tol for j = path_first[k] + d < k.
 cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s);
+// round end fused with the next round's sizing (the run loops' last kernel)
+cudaError_t launch_round_close(const BatchView& v, cudaStream_t s);
 // recovery (Sec. VI-B)
 cudaError_t launch_check_path(const RobotDev* robot, int n, int nsp_pad, int n_rbox, const EnvDev& env, float E,
                               const double* verts, int n_edges, const long long* off, long long N,

@@ -22,7 +22,9 @@ __device__ __forceinline__ int round_test_size(int k, double eps, double delta, 
   return (int)ceil(2.0 * log(1.0 / dk) / (eps * tau * tau));
 }
 
-__global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
+// Round size of every active segment and the round's list of sample tiles
+// (block-wide exclusive scan over the segments). Runs in one block.
+__device__ __forceinline__ void round_begin_block(const BatchView& v) {
   __shared__ int warp_sum[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -85,6 +87,24 @@ __global__ void __launch_bounds__(1024) k_round_begin(BatchView v) {
     v.summary->n_sample_tiles = carry;
     v.summary->n_bisect_tiles = 0;
   }
+}
+
+__global__ void __launch_bounds__(1024) k_round_begin(BatchView v) { round_begin_block(v); }
+
+// End of a round fused with the next round's sizing (one launch fewer per
+// round in the run loops): every active segment that reached N_it stops
+// (Sec. IV-C), the others go to round k + 1, the next round's sample tiles are
+// listed, and the round summary (and a graph's WHILE condition) is set.
+__global__ void __launch_bounds__(1024) k_round_close(BatchView v) {
+  __shared__ int s_active;
+  if (threadIdx.x == 0) s_active = 0;
+  __syncthreads();
+  const int act = round_end_segments(v);
+  if (act) atomicAdd(&s_active, act);
+  __syncthreads();
+  round_begin_block(v);
+  __syncthreads();
+  if (threadIdx.x == 0) round_summary_close(v, s_active);
 }
 
 // One pass of a 128-thread block over a tile of kTile walks at TSS lanes per
@@ -336,6 +356,11 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
 
 cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s) {
   k_round_begin<<<1, 1024, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_close(const BatchView& v, cudaStream_t s) {
+  k_round_close<<<1, 1024, 0, s>>>(v);
   return cudaGetLastError();
 }
 

@@ -353,28 +353,10 @@ __global__ void k_round_end(BatchView v) {
   __shared__ int s_active;
   if (threadIdx.x == 0) s_active = 0;
   __syncthreads();
-  int act = 0;
-  for (int g = threadIdx.x; g < v.B; g += blockDim.x) {
-    SegState& st = v.st[g];
-    if (st.status == SEG_ACTIVE) {
-      if (st.k >= v.n_it_max) {
-        st.status = SEG_MAX_ITER;
-        st.rounds = st.k;
-      } else {
-        st.k += 1;
-        ++act;
-      }
-    }
-  }
+  const int act = round_end_segments(v);
   if (act) atomicAdd(&s_active, act);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    v.summary->active = s_active;
-    v.summary->round += 1;
-#if CUDART_VERSION >= 12040
-    if (v.graph_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)v.graph_cond, s_active > 0 ? 1u : 0u);
-#endif
-  }
+  if (threadIdx.x == 0) round_summary_close(v, s_active);
 }
 
 __global__ void k_containment(BatchView v, uint8_t* contained, double tol) {

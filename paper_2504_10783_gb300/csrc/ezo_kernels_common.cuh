@@ -254,6 +254,37 @@ __device__ __forceinline__ void stage_polytope(float* A32, const double* __restr
   }
 }
 
+// ------------------------------------------------------------- round end --
+// Sec. IV-C "Maximum iterations": an active segment that ran N_it rounds
+// stops with EZO_SEG_MAX_ITER, the others move to the next round. Returns the
+// number of this thread's segments that stay active.
+__device__ __forceinline__ int round_end_segments(const BatchView& v) {
+  int act = 0;
+  for (int g = threadIdx.x; g < v.B; g += blockDim.x) {
+    SegState& st = v.st[g];
+    if (st.status == SEG_ACTIVE) {
+      if (st.k >= v.n_it_max) {
+        st.status = SEG_MAX_ITER;
+        st.rounds = st.k;
+      } else {
+        st.k += 1;
+        ++act;
+      }
+    }
+  }
+  return act;
+}
+
+// Round summary after a round (one thread): active segments, rounds run and,
+// inside a graph, the WHILE condition.
+__device__ __forceinline__ void round_summary_close(const BatchView& v, int active) {
+  v.summary->active = active;
+  v.summary->round += 1;
+#if CUDART_VERSION >= 12040
+  if (v.graph_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)v.graph_cond, active > 0 ? 1u : 0u);
+#endif
+}
+
 // ------------------------------------------------------- collision checks --
 // Shared memory of the collision kernels: robot spheres, obstacles, per group
 // sphere centres, obstacle offsets, then the boxes (robot boxes in their
