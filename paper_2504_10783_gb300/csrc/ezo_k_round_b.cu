@@ -66,12 +66,22 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
       }
       const int cc = valid ? c : tile.y;
       const int si = v.cand_idx[st.cand_off + cc];
-      double cs[NDOF], p[NDOF], dv[NDOF];
+      // the bracket [c_proj, c] in FP32 for the midpoints: q = c_proj + f (c -
+      // c_proj) with dyadic f (GB300's FP64 rate is 1/64 of FP32; the
+      // decisions only need the FP32 configuration); the end point c* is
+      // formed in FP64 after the loop
+      float p32[NDOF], dv32[NDOF];
+      {
+        double cs[NDOF], p[NDOF];
 #pragma unroll
-      for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
-      project_fp64<NDOF>(cs, v1, v2, n, p);
+        for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
+        project_fp64<NDOF>(cs, v1, v2, n, p);
 #pragma unroll
-      for (int j = 0; j < NDOF; ++j) dv[j] = (j < n) ? cs[j] - p[j] : 0.0;
+        for (int j = 0; j < NDOF; ++j) {
+          p32[j] = (float)p[j];
+          dv32[j] = (j < n) ? (float)(cs[j] - p[j]) : 0.f;
+        }
+      }
       double lo = 0.0, hi = 1.0;
       uint32_t bits = 0u;
       if (v.bis_mode == 1) {
@@ -80,7 +90,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
         bits = v.s_bits[row];
         float qq[NDOF];
 #pragma unroll
-        for (int j = 0; j < NDOF; ++j) qq[j] = (float)fma(hi, dv[j], p[j]);
+        for (int j = 0; j < NDOF; ++j) qq[j] = fmaf((float)hi, dv32[j], p32[j]);
         const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
                                                 robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
         if (valid && lg == 0) {
@@ -97,7 +107,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
         const double mid = 0.5 * (lo + hi);
         float qq[NDOF];
 #pragma unroll
-        for (int j = 0; j < NDOF; ++j) qq[j] = (float)fma(mid, dv[j], p[j]);
+        for (int j = 0; j < NDOF; ++j) qq[j] = fmaf((float)mid, dv32[j], p32[j]);
         const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
                                                 robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
         if (hit) {
@@ -108,9 +118,13 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
         }
       }
       if (valid && lg == 0) {
-        double cst[NDOF], ps[NDOF];
+        // c* = c_proj + hi (c - c_proj) in FP64 (the bracket again, exactly)
+        double cs[NDOF], p[NDOF], cst[NDOF], ps[NDOF];
 #pragma unroll
-        for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, dv[j], p[j]) : 0.0;
+        for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
+        project_fp64<NDOF>(cs, v1, v2, n, p);
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, cs[j] - p[j], p[j]) : 0.0;
         project_fp64<NDOF>(cst, v1, v2, n, ps);
         double d2 = 0.0;
         float cn2 = 0.f;
