@@ -988,13 +988,12 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   int e_big = 0;
   for (int e2 = 1; e2 < n_env; ++e2)
     if (envs[e2]->n_obs > envs[e_big]->n_obs) e_big = e2;
-  b->T_check = ezo_internal_tuned_lanes(robot, envs[e_big], tot_s1, nullptr);
-  // the tuner times one flat launch of the round-1 size; later rounds have
-  // fewer samples, and below ~1e6 samples per round two lanes per
-  // configuration measured faster than one over a whole inflation (1e5
-  // samples per round: 0.22 vs 0.28 ms per path), so one lane is kept for
-  // larger rounds only
-  if (b->T_check < 2 && tot_s1 < (1ll << 20)) b->T_check = 2;
+  // the tuner times one flat launch of the round-1 size, but the round
+  // kernel's work units and the smaller later rounds favour two lanes per
+  // configuration below ~1e6 samples per round (1e5 samples per round, whole
+  // inflation: 0.22 ms at 2 lanes, 0.28 at 1, 0.24 at 4, while the flat
+  // tuner ranks them within its noise); larger rounds take the tuner's pick
+  b->T_check = tot_s1 < (1ll << 20) ? 2 : ezo_internal_tuned_lanes(robot, envs[e_big], tot_s1, nullptr);
   // Bisection runs N_b dependent checks per candidate on the few thousand
   // candidates of a round, so it is latency bound: eight lanes per candidate
   // unless a round can hold enough candidates to fill the GPU at fewer lanes.
