@@ -92,8 +92,9 @@ const char* ezo_last_error(void);
 /* ------------------------------------------------------------------ robot --
  * Robot description the paper assumes (Sec. II: kinematics and collision
  * geometry, as in a URDF), restricted to a serial chain in standard DH form
- * with sphere geometries (Sec. IV-D: sphere and box geometries; boxes are not
- * supported here). Frame 0 is the base; frame i (1..n) is
+ * with sphere geometries here and oriented boxes added by
+ * ezo_robot_add_boxes (Sec. IV-D: sphere and box geometries). Frame 0 is the
+ * base; frame i (1..n) is
  *   T_i = T_{i-1} Rz(q_i + theta_off_i) Tz(d_i) Tx(a_i) Rx(alpha_i)
  * for a revolute joint and
  *   T_i = T_{i-1} Rz(theta_off_i) Tz(d_i + q_i) Tx(a_i) Rx(alpha_i)
