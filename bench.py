@@ -139,21 +139,59 @@ def oracle_sample(seconds: float, seg_list=None):
     return checks, time.perf_counter() - t0, segs, rounds
 
 
-def cpu_leg(seconds: float):
-    checks, el, segs, rounds = oracle_sample(seconds)
-    print(json.dumps({"checks": checks, "seconds": el, "segments": segs, "rounds": rounds}))
+def oracle_worker(args):
+    """One host core: segments w, w + P, .. of the bench path (cycling, with
+    a fresh Philox stream per pass) until `seconds` have passed."""
+    w, P, seconds = args
+    from oracle import ezo_oracle as orc
+    rd, env, path = load_scene()
+    K = path.shape[0] - 1
+    prm = orc.Params(**PARAMS)
+    A0, b0 = orc.joint_box(rd)
+    checks = segs = 0
+    t0 = time.perf_counter()
+    i = w
+    while time.perf_counter() - t0 < seconds:
+        k = i % K
+        res = orc.eizo(rd, env, path[k], path[k + 1], A0, b0, prm, stream=k + 1000 * (i // K))
+        checks += res.checks
+        segs += 1
+        i += P
+    return checks, time.perf_counter() - t0, segs
+
+
+def cpu_leg(seconds: float, workers: int = 1):
+    if workers <= 1:
+        checks, el, segs, rounds = oracle_sample(seconds)
+        print(json.dumps({"checks": checks, "seconds": el, "segments": segs, "rounds": rounds}))
+        return
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(oracle_worker, [(w, workers, seconds) for w in range(workers)])
+    print(json.dumps({"checks": sum(r[0] for r in res), "seconds": max(r[1] for r in res),
+                      "segments": sum(r[2] for r in res), "workers": workers}))
 
 
 def run_cpu_baseline(seconds: float = 15.0) -> dict:
+    """The FP64 oracle on the host: all cores (one process per core, each on
+    its own segments) as the baseline, and one core beside it."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "--seconds", str(seconds)],
-                         capture_output=True, text=True, env=env, timeout=600)
-    d = json.loads(out.stdout.strip().splitlines()[-1])
-    v = d["checks"] / d["seconds"]
-    return {"value": v, "unit": "configs/s", "cores": 1, "kind": "oracle",
-            "ms_per_segment": 1e3 * d["seconds"] / d["segments"],
-            "sample": f"FP64 numpy oracle, Algorithm 1 on the first {d['segments']} segment(s) of the bench path "
-                      f"({d['rounds']} rounds, {d['checks']} exact checks) in {d['seconds']:.1f} s on 1 host thread"}
+    me = os.path.abspath(__file__)
+    out1 = subprocess.run([sys.executable, me, "--cpu-leg", "--seconds", str(seconds)],
+                          capture_output=True, text=True, env=env, timeout=600)
+    d1 = json.loads(out1.stdout.strip().splitlines()[-1])
+    P = max(1, min(os.cpu_count() or 1, 64))
+    outp = subprocess.run([sys.executable, me, "--cpu-leg", "--seconds", str(seconds), "--cpu-workers", str(P)],
+                          capture_output=True, text=True, env=env, timeout=900)
+    dp = json.loads(outp.stdout.strip().splitlines()[-1])
+    one = {"value": d1["checks"] / d1["seconds"], "cores": 1, "ms_per_segment": 1e3 * d1["seconds"] / d1["segments"],
+           "sample": f"Algorithm 1 on the first {d1['segments']} segment(s) of the bench path ({d1['rounds']} rounds, "
+                     f"{d1['checks']} exact checks) in {d1['seconds']:.1f} s on 1 host thread"}
+    return {"value": dp["checks"] / dp["seconds"], "unit": "configs/s", "cores": P, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, Algorithm 1 on segments of the bench path, {P} processes (one per host "
+                      f"core, one numpy thread each): {dp['segments']} segment inflations, {dp['checks']} exact "
+                      f"checks in {dp['seconds']:.1f} s",
+            "one_core": one}
 
 
 def oracle_round(seg: int):
@@ -368,7 +406,8 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flus
             "what": "same path, bisection steps on the BF16 MLP, end points verified exactly, exact fallback"}
 
 
-def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg, N=2_000_000, reps=10):
+def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg, N=2_000_000, reps=10,
+                    traffic=None):
     """ezo_check_collision on N uniform configurations (configurations and
     flags resident in HBM, L2 flushed between launches), CUDA events."""
     g = torch.Generator(device="cuda").manual_seed(1)
@@ -394,7 +433,7 @@ def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, fl
     return {"batch": N, "configs_per_s": N / (per / 1e3), "ms_per_launch": per,
             "roofline": {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                          "flops_per_config": flops_cfg,
-                         "traffic": CHECKER_TRAFFIC_2E6 if N == 2_000_000 else None},
+                         "traffic": traffic},
             "paper_context": "paper: ~8.6 M configs/s, Franka (1187 pairs), RTX 3090, same batch size",
             "launches": reps + 3}
 
@@ -456,6 +495,7 @@ def main():
     ap.add_argument("--mode", default="graph", choices=["graph", "host"])
     ap.add_argument("--cpu-leg", action="store_true")
     ap.add_argument("--seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-workers", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--only-checker", action="store_true",
@@ -467,7 +507,7 @@ def main():
     ap.add_argument("--np-stress", type=int, default=1_000_000, help="stress: samples per round and segment")
     args = ap.parse_args()
     if args.cpu_leg:
-        cpu_leg(args.seconds)
+        cpu_leg(args.seconds, args.cpu_workers)
         return
     if args.impl == "reference":
         run_reference(args)
@@ -630,11 +670,24 @@ def main():
 
     # ---- the collision checker alone on the paper's batch size (2e6 configs) ----
     checker = checker_1e8 = forest = {"launches": 0}
+    envs_more = {}
     if not args.no_extras:
         forest = measure_forest(ezo, torch, stream, flush, props, sm_max)
-        checker = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg)
+        checker = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg,
+                                  traffic=CHECKER_TRAFFIC_2E6)
         checker_1e8 = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg,
                                       N=100_000_000, reps=3)
+        # the checker on the other obstacle sets of the survey's measurement plan:
+        # the planar arm among 16 disks and the arm among a 1024-sphere cloud
+        from paper_2504_10783_gb300 import workloads as wl
+        with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+            pl = json.load(f)["planar3"]
+        envs_more = {}
+        for name, rdx, envx in (("planar3_16_disks", wl.planar3_robot(), wl.Env("planar", np.asarray(pl["obstacles"]))),
+                                ("dh7_table_cloud_1024", rd, wl.table_cloud_obstacles(31))):
+            rx, ex = ezo.Robot(rdx), ezo.Env(envx)
+            envs_more[name] = measure_checker(ezo, torch, rx, ex, rdx, stream, flush, props, sm_max,
+                                              ezo.check_flops(rx, ex))
 
     # ---- end to end through the public API with host buffers ----
     # the step's inputs in pinned host memory
@@ -674,10 +727,11 @@ def main():
                        "ms_per_10_segment_path": ms / args.steps,
                        "ms_p50": float(np.percentile(times, 50)), "ms_p90": float(np.percentile(times, 90)),
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "checker_1e8": checker_1e8, "forest": forest, "e2e": e2e,
+            "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "checker_1e8": checker_1e8, "checker_other_envs_2e6": envs_more,
+            "forest": forest, "e2e": e2e,
             "gpu_launches": launches,
             "gpu_launches_outside_timed_region": other_launches + checker["launches"] + checker_1e8["launches"] +
-            forest["launches"],
+            forest["launches"] + sum(c["launches"] for c in envs_more.values()),
             "clocks": clocks}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args.seconds)
