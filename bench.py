@@ -662,7 +662,7 @@ def main():
         plain = {"ms_per_path": float(np.median(plain_ms)), "kept_segments": int(kept_plain),
                  "what": "sequential per-segment inflation (paper's order), host-driven launch loop"}
 
-    # ---- batched + learned surrogate (spec item 4): train on exact
+    # ---- batched + learned surrogate: train on exact
     #      labels, then the same path with surrogate-guided bisection ----
     sur_info = None
     if not args.no_surrogate and not args.no_extras:
@@ -677,7 +677,7 @@ def main():
                                   traffic=CHECKER_TRAFFIC_2E6)
         checker_1e8 = measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, flops_cfg,
                                       N=100_000_000, reps=3)
-        # the checker on the other obstacle sets of the survey's measurement plan:
+        # the checker on two more obstacle sets:
         # the planar arm among 16 disks and the arm among a 1024-sphere cloud
         from paper_2504_10783_gb300 import workloads as wl
         with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
