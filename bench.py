@@ -639,6 +639,11 @@ def main():
                 "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
                 "whole_path": {"achieved": path_tf, "frac": path_tf / peak,
                                "what": "all algorithmic FP32 FLOPs of the path (walks + exact checks) / step time"}}
+    # calibration beside the nominal peak: the achieved rate of independent
+    # FMA chains on every SM (outside the timed region)
+    ffma = ezo.probe_fp32_fma(stream)
+    roofline["fma_probe"] = {"measured": ffma, "unit": "TFLOP/s", "frac_of_nominal": ffma / peak,
+                             "kernel_frac_of_measured": ach / ffma}
     w0 = work[0]
     samp, bisc, kept = w0["sample_checks"], w0["bisection_checks"], w0["kept"]
     checks_per_step = units / args.steps
@@ -731,7 +736,7 @@ def main():
             "forest": forest, "e2e": e2e,
             "gpu_launches": launches,
             "gpu_launches_outside_timed_region": other_launches + checker["launches"] + checker_1e8["launches"] +
-            forest["launches"] + sum(c["launches"] for c in envs_more.values()),
+            forest["launches"] + sum(c["launches"] for c in envs_more.values()) + 4,  # + the FMA probe
             "clocks": clocks}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args.seconds)

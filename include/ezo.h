@@ -444,6 +444,14 @@ ezo_status ezo_batch_attach_surrogate(ezo_batch* batch, ezo_surrogate* sur, floa
 ezo_status ezo_tune_lanes(const ezo_robot* robot, const ezo_env* env, int64_t N, int32_t* lanes, void* cuda_stream);
 ezo_status ezo_set_autotune(int32_t on);
 
+/* FP32 calibration of the ALU roofline: times a kernel of independent fused
+ * multiply-add chains that fills every warp slot of every SM (best of three
+ * launches after one warm-up) and writes the achieved FP32 rate, two flops
+ * per FMA, in TFLOP/s into *tflops. Allocates and frees a small scratch
+ * buffer; synchronous on cuda_stream. EZO_ERR_INVALID_ARG for tflops = NULL,
+ * EZO_ERR_CUDA on a failed allocation or launch. */
+ezo_status ezo_probe_fp32_fma(double* tflops, void* cuda_stream);
+
 /* Algorithmic FP32 work of one exact configuration check (forward kinematics
  * plus 8 flops per obstacle pair and per self pair), as used for rooflines. */
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env);

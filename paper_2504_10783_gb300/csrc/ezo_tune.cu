@@ -150,3 +150,69 @@ extern "C" ezo_status ezo_tune_lanes(const ezo_robot* robot, const ezo_env* env,
   ezo_internal_set_error("");
   return EZO_OK;
 }
+
+// ---- FP32 FMA calibration: independent FMA chains on every SM ----
+namespace {
+
+constexpr int kProbeChains = 8;
+
+__global__ void __launch_bounds__(256) k_fma_probe(float* out, int reps, float a, float c) {
+  float x[kProbeChains];
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) x[i] = threadIdx.x * 1e-3f + (float)i;
+  for (int r = 0; r < reps; ++r) {
+#pragma unroll
+    for (int i = 0; i < kProbeChains; ++i) x[i] = fmaf(x[i], a, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) s += x[i];
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" ezo_status ezo_probe_fp32_fma(double* tflops, void* cuda_stream) {
+  if (!tflops) {
+    ezo_internal_set_error("ezo_probe_fp32_fma: tflops is NULL");
+    return EZO_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // 8 blocks of 256 threads per SM: every warp slot filled
+  const int blocks = sms * 8, threads = 256, reps = 20000;
+  float* out = nullptr;
+  if (cudaMalloc(&out, sizeof(float) * (size_t)blocks * threads) != cudaSuccess) {
+    cudaGetLastError();
+    ezo_internal_set_error("ezo_probe_fp32_fma: cudaMalloc failed");
+    return EZO_ERR_CUDA;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  k_fma_probe<<<blocks, threads, 0, s>>>(out, reps, 0.999f, 1e-3f);  // warm-up
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, s);
+    k_fma_probe<<<blocks, threads, 0, s>>>(out, reps, 0.999f, 1e-3f);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  const cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess) {
+    ezo_internal_set_error(cudaGetErrorString(err));
+    return EZO_ERR_CUDA;
+  }
+  const double flops = 2.0 * kProbeChains * (double)reps * blocks * threads;
+  *tflops = flops / (best * 1e-3) * 1e-12;
+  ezo_internal_set_error("");
+  return EZO_OK;
+}

@@ -108,6 +108,7 @@ def _sig(lib):
     f.ezo_batch_reinflate.argtypes = [_P, C.POINTER(C.c_uint8), _I32, _P]
     f.ezo_tune_lanes.argtypes = [_P, _P, _I64, C.POINTER(_I32), _P]
     f.ezo_set_autotune.argtypes = [_I32]
+    f.ezo_probe_fp32_fma.argtypes = [_DP, _P]
     f.ezo_check_flops.argtypes = [_P, _P]
     f.ezo_check_flops.restype = C.c_double
     return lib
@@ -529,6 +530,13 @@ def tune_lanes(robot: Robot, env: Env, N: int, stream=None) -> int:
 
 def set_autotune(on: bool = True):
     _check(lib().ezo_set_autotune(1 if on else 0))
+
+
+def probe_fp32_fma(stream=None) -> float:
+    """Measured FP32 FMA rate of the current device in TFLOP/s."""
+    out = C.c_double()
+    _check(lib().ezo_probe_fp32_fma(C.byref(out), _stream(stream)))
+    return out.value
 
 
 def check_flops(robot: Robot, env: Env) -> float:

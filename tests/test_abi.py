@@ -52,3 +52,6 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
                                     ctypes.byref(out))
     assert st == 1
     assert b"n must be" in ezo.lib().ezo_last_error()
+    st = ezo.lib().ezo_probe_fp32_fma(None, None)
+    assert st == 1
+    assert b"tflops" in ezo.lib().ezo_last_error()

@@ -625,3 +625,14 @@ def test_wavefront_equals_sequential_on_several_paths(ezo):
     for a, b in zip(res[1], res[2]):
         assert a.status == b.status
         np.testing.assert_array_equal(a.A, b.A)
+
+
+def test_fp32_fma_probe_within_the_nominal_peak(ezo):
+    """The FMA calibration lies between half and 105% of the nominal FP32 rate
+    (SMs x 128 lanes x 2 flops x the maximum SM clock)."""
+    tf = ezo.probe_fp32_fma()
+    prop = torch.cuda.get_device_properties(0)
+    nominal = prop.multi_processor_count * 128 * 2 * 2.07e9 * 1e-12 if prop.major == 10 else None
+    assert tf > 0
+    if nominal is not None:
+        assert 0.5 * nominal < tf < 1.05 * nominal, (tf, nominal)
