@@ -358,6 +358,16 @@ def run_workload(args):
 
 
 # ------------------------------------------------------------------- GPU leg --
+def bf16_peak():
+    """Dense BF16 peak in TFLOP/s for a kernel timed alone: the measured burst
+    figure of this GPU pool when the peaks file is present, else 1900."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
 def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args):
     """Trains the BF16 MLP on 2^22 exact labels (4 epochs), reports its
     false-negative / false-positive rates on 2^16 fresh configurations, and
@@ -400,9 +410,29 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flus
         bisc += y2
         evals += bt.surrogate_evals(g)
     bt.attach_surrogate(None)
+    # inference throughput of the MLP alone (features, three BF16 GEMMs with
+    # fused bias + SiLU, output layer) on 2^20 configurations, timed alone
+    # against the burst BF16 peak
+    nb = 1 << 20
+    qb = torch.from_numpy(wl.uniform_configs(11, rd, nb).astype(np.float32).T.copy()).cuda()
+    yb = torch.empty(nb, device="cuda")
+    for _ in range(3):
+        sur.predict(qb, yb)
+    e0.record(stream)
+    for _ in range(10):
+        sur.predict(qb, yb)
+    e1.record(stream)
+    e1.synchronize()
+    inf_ms = e0.elapsed_time(e1) / 10
+    gemm_flops = 2.0 * nb * (64 * 256 + 2 * 256 * 256)  # the three hidden-layer GEMMs (features padded to 64)
+    peak_bf16, peak_src = bf16_peak()
+    inf_tf = gemm_flops / (inf_ms / 1e3) / 1e12
     return {"ms_per_path": float(np.median(times)), "train_ms": train_ms, "train_samples": 1 << 22, "epochs": 4,
             "fn_rate_margin0": fn0, "fp_rate_margin0": fp0, "sample_checks": samp, "bisection_checks": bisc,
             "surrogate_evals": evals,
+            "inference": {"batch": nb, "ms": inf_ms, "gemm_tflops": inf_tf, "peak": peak_bf16, "peak_source": peak_src,
+                          "frac": inf_tf / peak_bf16,
+                          "what": "GEMM flops of the three hidden layers / time of the whole forward pass"},
             "what": "same path, bisection steps on the BF16 MLP, end points verified exactly, exact fallback"}
 
 
