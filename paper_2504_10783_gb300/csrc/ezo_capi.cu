@@ -567,7 +567,7 @@ struct ezo_batch {
   // surrogate-guided bisection
   ezo_surrogate* sur = nullptr;
   long long sur_rows = 0;
-  void *s_X = nullptr, *s_hA = nullptr, *s_hB = nullptr;
+  void* s_X = nullptr;
   float* s_y = nullptr;
 };
 
@@ -580,7 +580,7 @@ ezo_status batch_free_device(ezo_batch* b) {
   void* ptrs[] = {b->d_st,    b->d_v1,    b->d_v2,   b->d_A,    b->d_b,      b->d_S,      b->d_flags,
                   b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx, b->d_ga, b->d_gb,
                   b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0,
-                  b->s_X, b->s_hA, b->s_hB, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
+                  b->s_X, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
                   b->view.s_bits, b->view.s_ok, b->view.s_rows};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -602,7 +602,7 @@ int host_test_size(int k, double eps, double delta, double tau) {
 }  // namespace
 
 extern "C" cudaError_t ezo_internal_mlp_forward(ezo_surrogate* S, const void* X, long long rows_cap, const int* m_dev,
-                                                void* hA, void* hB, float* yhat, cudaStream_t s);
+                                                float* yhat, cudaStream_t s);
 extern "C" int ezo_internal_surrogate_dof(const ezo_surrogate* S);
 
 namespace {
@@ -620,7 +620,7 @@ cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
   for (int st = 0; st < b->prm.n_b && e == cudaSuccess; ++st) {
     e = launch_sbis_mid(b->view, b->s_X, g, s);
     if (e == cudaSuccess)
-      e = ezo_internal_mlp_forward(b->sur, b->s_X, b->sur_rows, b->view.s_rows, b->s_hA, b->s_hB, b->s_y, s);
+      e = ezo_internal_mlp_forward(b->sur, b->s_X, b->sur_rows, b->view.s_rows, b->s_y, s);
     if (e == cudaSuccess) e = launch_sbis_update(b->view, b->s_y, st, g, s);
   }
   if (e == cudaSuccess) {
@@ -1045,14 +1045,12 @@ ezo_status ezo_batch_attach_surrogate(ezo_batch* b, ezo_surrogate* sur, float ma
     return fail(EZO_ERR_INVALID_ARG, "ezo_batch_attach_surrogate: surrogate of another robot, or more than 8 joints");
   const long long rows = (long long)b->max_bisect_tiles * kTile;
   if (rows > b->sur_rows) {
-    void* ps[] = {b->s_X, b->s_hA, b->s_hB, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
+    void* ps[] = {b->s_X, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
                   b->view.s_bits, b->view.s_ok, b->view.s_rows};
     for (void* p : ps)
       if (p) cudaFree(p);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&b->s_X, (size_t)rows * 64 * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&b->s_hA, (size_t)rows * 256 * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&b->s_hB, (size_t)rows * 256 * 2);
     if (e == cudaSuccess) e = dalloc(&b->s_y, rows);
     if (e == cudaSuccess) e = dalloc(&b->view.s_p32, rows * 8);
     if (e == cudaSuccess) e = dalloc(&b->view.s_d32, rows * 8);

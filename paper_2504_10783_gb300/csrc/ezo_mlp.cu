@@ -28,6 +28,13 @@
 
 namespace ezo {
 
+// tensor-core forward pass (ezo_mlp_tc.cu)
+size_t mlp_tc_image_bytes();
+cudaError_t mlp_tc_build_image(const void* W1, const void* W2, const void* W3, void* img, cudaStream_t s);
+cudaError_t mlp_tc_forward(const void* X, const float* q, long long ldq, int n, long long rows_cap, const int* m_dev,
+                           const void* img, const float* b1, const float* b2, const float* b3, const float* w4,
+                           const float* b4, float* y, int* err, cudaStream_t s);
+
 constexpr int kF = 64;   // padded input features
 constexpr int kH = 256;  // hidden width
 constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8;
@@ -35,8 +42,7 @@ constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8;
 enum Epi : int {
   EPI_F32 = 0,        // C (FP32) = acc
   EPI_BIAS_SILU = 1,  // Z = acc + bias (FP32), H = SiLU(Z) (BF16, and transposed)
-  EPI_DSILU = 2,      // D = acc * SiLU'(Z) (BF16, and transposed)
-  EPI_BIAS_SILU_H = 3 // inference: H = SiLU(acc + bias) (BF16 only)
+  EPI_DSILU = 2       // D = acc * SiLU'(Z) (BF16, and transposed)
 };
 
 struct GemmArgs {
@@ -140,14 +146,12 @@ __global__ void __launch_bounds__(128) k_gemm_nt(GemmArgs g) {
           const float v = acc[i][j][e];
           if (EPI == EPI_F32) {
             g.C[(long long)r * g.ldc + c] = v;
-          } else if (EPI == EPI_BIAS_SILU || EPI == EPI_BIAS_SILU_H) {
+          } else if (EPI == EPI_BIAS_SILU) {
             const float z = v + g.bias[c];
             const __nv_bfloat16 h = __float2bfloat16(silu(z));
             g.H[(long long)r * g.N + c] = h;
-            if (EPI == EPI_BIAS_SILU) {
-              g.Z[(long long)r * g.N + c] = z;
-              g.Ht[(long long)c * g.ldt + r] = h;
-            }
+            g.Z[(long long)r * g.N + c] = z;
+            g.Ht[(long long)c * g.ldt + r] = h;
           } else {
             const float d = v * dsilu(g.Z[(long long)r * g.N + c]);
             const __nv_bfloat16 h = __float2bfloat16(d);
@@ -346,9 +350,10 @@ struct ezo_surrogate {
                 *H3 = nullptr, *H3t = nullptr, *dZ3 = nullptr, *dZ3t = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
                 *dZ1 = nullptr, *dZ1t = nullptr;
   float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *loss = nullptr;
-  // inference buffers (grown on demand)
-  long long icap = 0;
-  __nv_bfloat16 *iX = nullptr, *iA = nullptr, *iB = nullptr;
+  // inference: the swizzled weight image of the tensor-core forward kernel
+  // and its error flag
+  void* wimg = nullptr;
+  int* tc_err = nullptr;
 };
 
 namespace {
@@ -369,8 +374,7 @@ cudaError_t gemm(int epi, const GemmArgs& a, cudaStream_t s) {
   switch (epi) {
     case EPI_F32: k_gemm_nt<EPI_F32><<<grid, 128, 0, s>>>(a); break;
     case EPI_BIAS_SILU: k_gemm_nt<EPI_BIAS_SILU><<<grid, 128, 0, s>>>(a); break;
-    case EPI_DSILU: k_gemm_nt<EPI_DSILU><<<grid, 128, 0, s>>>(a); break;
-    default: k_gemm_nt<EPI_BIAS_SILU_H><<<grid, 128, 0, s>>>(a); break;
+    default: k_gemm_nt<EPI_DSILU><<<grid, 128, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
@@ -381,7 +385,9 @@ cudaError_t sync_bf16(ezo_surrogate* S, cudaStream_t s) {
   k_to_bf16<<<blocks_for((long long)kH * kF, 256), 256, 0, s>>>(S->p + kOffW1, (long long)kH * kF, S->W1, nullptr, kH, kF);
   k_to_bf16<<<blocks_for((long long)kH * kH, 256), 256, 0, s>>>(S->p + kOffW2, (long long)kH * kH, S->W2, S->W2t, kH, kH);
   k_to_bf16<<<blocks_for((long long)kH * kH, 256), 256, 0, s>>>(S->p + kOffW3, (long long)kH * kH, S->W3, S->W3t, kH, kH);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = mlp_tc_build_image(S->W1, S->W2, S->W3, S->wimg, s);
+  return e;
 }
 
 cudaError_t ensure_train_cap(ezo_surrogate* S, int B) {
@@ -472,26 +478,11 @@ cudaError_t adam_step(ezo_surrogate* S, float lr, cudaStream_t s) {
 }  // namespace
 
 // Forward pass on BF16 feature rows X [rows_cap x 64] for the rows below the
-// device count *m_dev; hA, hB are [rows_cap x 256] BF16 scratch. Internal.
+// device count *m_dev, on the tensor cores. Internal.
 extern "C" __attribute__((visibility("hidden"))) cudaError_t ezo_internal_mlp_forward(
-    ezo_surrogate* S, const void* X, long long rows_cap, const int* m_dev, void* hA, void* hB, float* yhat,
-    cudaStream_t s) {
-  GemmArgs a{};
-  a.M = (int)rows_cap;
-  a.N = kH;
-  a.m_dev = m_dev;
-  a.A = static_cast<const __nv_bfloat16*>(X); a.lda = kF; a.B = S->W1; a.ldb = kF; a.K = kF; a.bias = S->p + kOffB1;
-  a.H = static_cast<__nv_bfloat16*>(hA);
-  cudaError_t e = gemm(EPI_BIAS_SILU_H, a, s);
-  if (e != cudaSuccess) return e;
-  a.A = static_cast<const __nv_bfloat16*>(hA); a.lda = kH; a.B = S->W2; a.ldb = kH; a.K = kH; a.bias = S->p + kOffB2;
-  a.H = static_cast<__nv_bfloat16*>(hB);
-  if ((e = gemm(EPI_BIAS_SILU_H, a, s)) != cudaSuccess) return e;
-  a.A = static_cast<const __nv_bfloat16*>(hB); a.B = S->W3; a.bias = S->p + kOffB3; a.H = static_cast<__nv_bfloat16*>(hA);
-  if ((e = gemm(EPI_BIAS_SILU_H, a, s)) != cudaSuccess) return e;
-  k_out<<<blocks_for(rows_cap * 32, 256), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(hA), S->p + kOffW4,
-                                                        S->p + kOffB4, rows_cap, m_dev, yhat);
-  return cudaGetLastError();
+    ezo_surrogate* S, const void* X, long long rows_cap, const int* m_dev, float* yhat, cudaStream_t s) {
+  return mlp_tc_forward(X, nullptr, 0, S->n, rows_cap, m_dev, S->wimg, S->p + kOffB1, S->p + kOffB2, S->p + kOffB3, S->p + kOffW4,
+                        S->p + kOffB4, yhat, S->tc_err, s);
 }
 
 extern "C" __attribute__((visibility("hidden"))) int ezo_internal_surrogate_dof(const ezo_surrogate* S) {
@@ -533,6 +524,9 @@ ezo_status ezo_surrogate_create(const ezo_robot* robot, uint64_t seed, ezo_surro
   if (e == cudaSuccess) e = dal(&S->W2t, (size_t)kH * kH);
   if (e == cudaSuccess) e = dal(&S->W3t, (size_t)kH * kH);
   if (e == cudaSuccess) e = dal(&S->loss, 1);
+  if (e == cudaSuccess) e = cudaMalloc(&S->wimg, mlp_tc_image_bytes());
+  if (e == cudaSuccess) e = dal(&S->tc_err, 1);
+  if (e == cudaSuccess) e = cudaMemset(S->tc_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     ezo_surrogate_free(S);
     ezo_internal_set_error((std::string("ezo_surrogate_create: ") + cudaGetErrorString(e)).c_str());
@@ -578,7 +572,7 @@ void ezo_surrogate_free(ezo_surrogate* S) {
   if (!S) return;
   void* ps[] = {S->p,  S->g,   S->m,   S->v,   S->W1,  S->W2,  S->W3,   S->W2t,  S->W3t, S->X,   S->Xt,  S->H1,
                 S->H1t, S->H2, S->H2t, S->H3, S->H3t, S->dZ3, S->dZ3t, S->dZ2, S->dZ2t, S->dZ1, S->dZ1t, S->Z1, S->Z2,
-                S->Z3, S->y,   S->loss, S->iX,  S->iA,  S->iB};
+                S->Z3, S->y,   S->loss, S->wimg, S->tc_err};
   for (void* q : ps)
     if (q) cudaFree(q);
   delete S;
@@ -623,31 +617,9 @@ ezo_status ezo_surrogate_predict(ezo_surrogate* S, const float* q_dev, int64_t l
   }
   if (N == 0) return EZO_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  const long long Np = (N + kBM - 1) / kBM * kBM;
-  if (Np > S->icap) {
-    cudaFree(S->iX);
-    cudaFree(S->iA);
-    cudaFree(S->iB);
-    S->iX = S->iA = S->iB = nullptr;
-    if (dal(&S->iX, (size_t)Np * kF) != cudaSuccess || dal(&S->iA, (size_t)Np * kH) != cudaSuccess ||
-        dal(&S->iB, (size_t)Np * kH) != cudaSuccess) {
-      ezo_internal_set_error("ezo_surrogate_predict: allocation");
-      S->icap = 0;
-      return EZO_ERR_CUDA;
-    }
-    S->icap = Np;
-  }
-  k_features<<<blocks_for(N, 256), 256, 0, s>>>(q_dev, ldq, S->n, N, S->iX, nullptr, 0);
-  GemmArgs a{};
-  a.M = (int)N;
-  a.N = kH;
-  a.A = S->iX; a.lda = kF; a.B = S->W1; a.ldb = kF; a.K = kF; a.bias = S->p + kOffB1; a.H = S->iA;
-  gemm(EPI_BIAS_SILU_H, a, s);
-  a.A = S->iA; a.lda = kH; a.B = S->W2; a.ldb = kH; a.K = kH; a.bias = S->p + kOffB2; a.H = S->iB;
-  gemm(EPI_BIAS_SILU_H, a, s);
-  a.A = S->iB; a.B = S->W3; a.bias = S->p + kOffB3; a.H = S->iA;
-  gemm(EPI_BIAS_SILU_H, a, s);
-  k_out<<<blocks_for(N * 32, 256), 256, 0, s>>>(S->iA, S->p + kOffW4, S->p + kOffB4, N, nullptr, out_dev);
+  // features computed inside the forward kernel from the configurations
+  mlp_tc_forward(nullptr, q_dev, ldq, S->n, N, nullptr, S->wimg, S->p + kOffB1, S->p + kOffB2, S->p + kOffB3, S->p + kOffW4, S->p + kOffB4,
+                 out_dev, S->tc_err, s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     ezo_internal_set_error((std::string("ezo_surrogate_predict: ") + cudaGetErrorString(e)).c_str());
@@ -708,6 +680,8 @@ ezo_status ezo_surrogate_train(ezo_surrogate* S, const ezo_env* env, int64_t n_s
     }
     if (epoch_loss) epoch_loss[ep] = sum;
   }
+  // the tensor-core forward pass reads the updated BF16 weights from its image
+  if (e == cudaSuccess) e = mlp_tc_build_image(S->W1, S->W2, S->W3, S->wimg, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(q);
   cudaFree(t);

@@ -1,0 +1,477 @@
+// Forward pass of the learned signed-distance surrogate on the 5th-generation
+// tensor cores: one persistent kernel runs all three hidden layers of a
+// 128-row tile (features [128 x 64] -> 256 -> 256 -> 256 -> 1) with the
+// accumulators in tensor memory and the activations in shared memory, so a
+// row costs its configuration (or 128 bytes of features) and 4 bytes of
+// output in HBM.
+//
+// Roles (544 threads):
+//   warps 0-15 epilogue: warp w owns rows 32 (w % 4) .. +31 of the tile (the
+//              tensor-memory lanes it may read) and, in each K-chunk c of 64
+//              columns, the 16 columns 64 c + 16 (w / 4) .. +15. It stages
+//              the feature tile, then for each layer reads its 64 accumulator
+//              columns, adds the bias, applies SiLU, rounds to BF16 and writes
+//              the next layer's input to shared memory chunk by chunk; the
+//              last layer is reduced against w4 into y.
+//   warp 16    lane 0 streams the weights (nine 32 KB chunks per tile: W1,
+//              then W2 and W3 in four K-chunks of 64) with bulk asynchronous
+//              copies through a four-stage ring and issues the tcgen05.mma
+//              instructions (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32);
+//              the whole warp allocates and frees the 512 tensor-memory
+//              columns.
+// Two accumulators (columns 0-255 and 256-511) alternate from layer to
+// layer, the MMAs of K-chunk c of a layer start as soon as chunk c of its
+// input is written (the epilogue writes the chunks in order), and the next
+// tile's features are staged while the current tile is in its second layer,
+// so the tensor cores work on the next layer (or the next tile's first
+// layer) while the epilogue is still busy with the current one.
+//
+// Shared-memory operands use the K-major 128-byte swizzled layout: a row of
+// 64 BF16 values is 128 bytes, 8 rows form a 1024-byte atom, and 16-byte
+// chunk c of row r sits at chunk position c ^ (r % 8). The weights are kept
+// in global memory as images of that layout (built once per weight update),
+// so each chunk is one contiguous bulk copy.
+//
+// Every wait on an mbarrier gives up after about two seconds: the kernel
+// then records an error code, writes NaN for the rows it has not finished and
+// still frees its tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ezo {
+
+namespace {
+
+constexpr int kTcRows = 128;            // rows per tile (UMMA M)
+constexpr int kTcH = 256;               // hidden width (UMMA N)
+constexpr int kTcF = 64;                // padded features
+constexpr int kChunkBytes = kTcH * 128; // one weight chunk: 256 rows x 64 BF16
+constexpr int kChunksPerTile = 9;       // W1, W2 x 4, W3 x 4
+constexpr int kStages = 4;
+constexpr int kXBytes = kTcRows * 128;  // feature tile
+constexpr int kHBytes = kTcRows * 512;  // hidden tile: 4 K-chunks of 16 KB
+constexpr int kSmemBytes = kXBytes + kHBytes + kStages * kChunkBytes + 1024;  // + alignment slack
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = kEpiThreads + 32;
+constexpr int kTmemCols = 2 * kTcH;  // two accumulators
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
+// A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcH >> 3) << 17) |
+                            ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor for a K-major 128B-swizzled operand whose
+// 8-row atoms are 1024 bytes apart: start address >> 4 (bits 0-13), leading
+// byte offset 16 >> 4 (bits 16-29, unused by this layout), stride byte offset
+// 1024 >> 4 (bits 32-45), descriptor version 1 (bit 46), base offset 0,
+// swizzle mode 2 = 128 bytes (bits 61-63)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(b, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane (no wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of 16-byte chunk c of row r in a 128B-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw128(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+// SiLU(z) = z sigmoid(z) = h + h tanh(h) with h = z / 2, on the hardware
+// tanh approximation (relative error about 2^-11, below the BF16 rounding of
+// the result)
+__device__ __forceinline__ float silu_tc(float z) {
+  const float h = 0.5f * z;
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+  return fmaf(h, t, h);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+struct TcArgs {
+  const __nv_bfloat16* X;  // [rows_cap x 64] feature rows, or null: features from q
+  const float* q;          // configurations, n x rows_cap with stride ldq (when X is null)
+  long long ldq;
+  int n;
+  long long rows_cap;
+  const int* m_dev;        // optional device row count
+  const uint8_t* wimg;     // 9 swizzled weight chunks
+  const float* b1;
+  const float* b2;
+  const float* b3;
+  const float* w4;
+  const float* b4;
+  float* y;
+  int* err;                // set to 1 when a wait gave up
+};
+
+// this thread's share of one feature row: from X the 16-byte chunks 2 sc
+// and 2 sc + 1; from q the features of joints sc, sc + 4, .. (sin q_j at
+// column j, cos q_j at column n + j, as in training; the zero padding
+// columns were written once at the start)
+__device__ __forceinline__ void stage_features(const TcArgs& g, uint8_t* sX, int row, int sc, long long grow,
+                                               bool live) {
+  if (g.X) {
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int c = 2 * sc + cc;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (live) v = *reinterpret_cast<const uint4*>(g.X + grow * kTcF + c * 8);
+      *reinterpret_cast<uint4*>(sX + sw128(row, c)) = v;
+    }
+    return;
+  }
+  for (int j = sc; j < g.n; j += 4) {
+    float sn = 0.f, cs = 0.f;
+    if (live) {
+      const float qj = g.q[(long long)j * g.ldq + grow];
+      sn = sinf(qj);
+      cs = cosf(qj);
+    }
+    const int fc = g.n + j;
+    *reinterpret_cast<__nv_bfloat16*>(sX + sw128(row, j >> 3) + (j & 7) * 2) = __float2bfloat16(sn);
+    *reinterpret_cast<__nv_bfloat16*>(sX + sw128(row, fc >> 3) + (fc & 7) * 2) = __float2bfloat16(cs);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t w_full[kStages], w_empty[kStages], x_ready, h_ready[4], acc_full[2],
+      acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float sbias[3][kTcH];
+  __shared__ float sw4[kTcH];
+  __shared__ float ypart[2][4][kTcRows];
+
+  const uint32_t base_u32 = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* base = smem_raw + (base_u32 - smem_u32(smem_raw));
+  uint8_t* sX = base;
+  uint8_t* sH = base + kXBytes;
+  uint8_t* sW = base + kXBytes + kHBytes;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long m_lim = g.m_dev ? min((long long)*g.m_dev, g.rows_cap) : g.rows_cap;
+  const long long n_tiles = (m_lim + kTcRows - 1) / kTcRows;
+
+  // feature tile starts zero: the padding columns stay zero when the features
+  // are computed from q
+  for (int i = tid; i < kXBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < kTcH; i += kThreads) {
+    sbias[0][i] = g.b1[i];
+    sbias[1][i] = g.b2[i];
+    sbias[2][i] = g.b3[i];
+    sw4[i] = g.w4[i];
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&w_full[s], 1);
+      mbar_init(&w_empty[s], 1);
+    }
+    mbar_init(&x_ready, kEpiThreads);
+    for (int c = 0; c < 4; ++c) mbar_init(&h_ready[c], kEpiThreads);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], kEpiThreads);
+    }
+    mbar_init(&mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kEpiWarps) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_slot;
+  bool ok = true;
+
+  if (warp == kEpiWarps) {
+    if (lane == 0) {
+      // ---- weight producer and MMA issuer ----
+      long long my_tiles = 0;
+      for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) ++my_tiles;
+      const long long total = my_tiles * kChunksPerTile;
+      long long wl = 0, wi = 0;
+      auto top_up = [&](long long limit) {
+        while (ok && wl < total && wl < limit) {
+          const int st = (int)(wl % kStages);
+          if (wl >= kStages && !mbar_wait(&w_empty[st], (uint32_t)((wl / kStages - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&w_full[st], kChunkBytes);
+          bulk_g2s(sW + st * kChunkBytes, g.wimg + (wl % kChunksPerTile) * kChunkBytes, kChunkBytes, &w_full[st]);
+          ++wl;
+        }
+      };
+      for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+        for (int L = 0; L < 3 && ok; ++L) {
+          const long long G = 3 * tl + L;  // layers so far: accumulator G % 2, its use G / 2
+          const int a = (int)(G & 1);
+          const long long use = G >> 1;
+          top_up(wi + kStages - 1);
+          // the accumulator's previous contents have been read by every epilogue thread
+          if (use >= 1 && !mbar_wait(&acc_empty[a], (uint32_t)((use - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          if (L == 0 && !mbar_wait(&x_ready, (uint32_t)(tl & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dacc = tbase + (uint32_t)(a * kTcH);
+          const int nch = L == 0 ? 1 : 4;
+          for (int kc = 0; kc < nch && ok; ++kc) {
+            // K-chunk kc of this layer's input, written by the warps that own it
+            if (L > 0 && !mbar_wait(&h_ready[kc], (uint32_t)((2 * tl + L - 1) & 1))) {
+              ok = false;
+              break;
+            }
+            top_up(wi + kStages - 1);
+            const int st = (int)(wi % kStages);
+            if (!mbar_wait(&w_full[st], (uint32_t)((wi / kStages) & 1))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(L == 0 ? sX : sH + kc * (kTcRows * 128));
+            const uint32_t b0 = smem_u32(sW + st * kChunkBytes);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) umma(dacc, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), (kc | kk) != 0);
+            umma_commit(&w_empty[st]);
+            ++wi;
+          }
+          if (ok) umma_commit(&acc_full[a]);
+        }
+      }
+      if (!ok) {
+        atomicExch(g.err, 1);
+        // let the copies already issued land before the block exits
+        for (long long c = wi; c < wl; ++c) mbar_wait(&w_full[c % kStages], (uint32_t)((c / kStages) & 1));
+      }
+      // every MMA issued here has completed before the columns are freed
+      umma_commit(&mma_done);
+      if (!mbar_wait(&mma_done, 0)) atomicExch(g.err, 1);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps ----
+    const int lq = warp & 3, sc = warp >> 2;
+    const int row = lq * 32 + lane;
+    const uint32_t lane_addr = tbase + ((uint32_t)(lq * 32) << 16) + (uint32_t)(sc * 16);
+    long long t = blockIdx.x;
+    if (t < n_tiles) {
+      const long long grow = t * kTcRows + row;
+      stage_features(g, sX, row, sc, grow, grow < m_lim);
+      proxy_fence();
+      mbar_arrive(&x_ready);
+    }
+    for (long long tl = 0; t < n_tiles; t += gridDim.x, ++tl) {
+      const long long grow = t * kTcRows + row;
+      const bool live = grow < m_lim;
+      float part = 0.f;
+      for (int L = 0; L < 3; ++L) {
+        const long long G = 3 * tl + L;
+        const int a = (int)(G & 1);
+        if (ok && !mbar_wait(&acc_full[a], (uint32_t)((G >> 1) & 1))) ok = false;
+        // the tensor-memory loads below are warp-collective: the warp goes on
+        // only if all its lanes saw the phase complete
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc_fence_after();
+        // columns 64 c + 16 sc .. +15 of accumulator a, c = 0..3
+        uint32_t r[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld16(lane_addr + (uint32_t)(a * kTcH + 64 * c), r[c]);
+        tmem_wait_ld();
+        tc_fence_before();
+        mbar_arrive(&acc_empty[a]);
+        if (L == 1 && ok) {
+          // the first layer of this tile has finished reading the feature
+          // tile: stage the next tile's features now
+          const long long tn = t + gridDim.x;
+          if (tn < n_tiles) {
+            const long long gn = tn * kTcRows + row;
+            stage_features(g, sX, row, sc, gn, gn < m_lim);
+            proxy_fence();
+            mbar_arrive(&x_ready);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float* bias = sbias[L] + 64 * c + 16 * sc;
+          if (L < 2) {
+            uint32_t p[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              p[j] = pack_bf16(silu_tc(__uint_as_float(r[c][2 * j]) + bias[2 * j]),
+                               silu_tc(__uint_as_float(r[c][2 * j + 1]) + bias[2 * j + 1]));
+            uint8_t* hk = sH + c * (kTcRows * 128);
+            *reinterpret_cast<uint4*>(hk + sw128(row, 2 * sc)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4*>(hk + sw128(row, 2 * sc + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
+            proxy_fence();
+            mbar_arrive(&h_ready[c]);
+          } else {
+            const float* w4 = sw4 + 64 * c + 16 * sc;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float z = __uint_as_float(r[c][j]) + bias[j];
+              part = fmaf(__bfloat162float(__float2bfloat16(silu_tc(z))), w4[j], part);
+            }
+          }
+        }
+      }
+      ypart[tl & 1][sc][row] = part;
+      asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+      if (sc == 0 && live) {
+        const float* yp = &ypart[tl & 1][0][row];
+        g.y[grow] = ok ? ((yp[0] + yp[kTcRows]) + (yp[2 * kTcRows] + yp[3 * kTcRows])) + g.b4[0]
+                       : __int_as_float(0x7fc00000);
+      }
+    }
+    if (!ok) atomicExch(g.err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kEpiWarps) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+  }
+}
+
+// image of the three hidden-layer weight matrices in the swizzled K-major
+// layout: chunk 0 = W1 [256 x 64], chunks 1..4 = W2 columns 64 (j - 1) ..,
+// chunks 5..8 = W3 likewise; element (n, k) of a chunk at byte
+// sw128(n, k / 8) + 2 (k % 8)
+__global__ void k_mlp_tc_image(const __nv_bfloat16* __restrict__ W1, const __nv_bfloat16* __restrict__ W2,
+                               const __nv_bfloat16* __restrict__ W3, uint8_t* __restrict__ img) {
+  const int total = kChunksPerTile * kTcH * 64;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int j = i / (kTcH * 64), rem = i % (kTcH * 64), n = rem / 64, k = rem % 64;
+    __nv_bfloat16 w;
+    if (j == 0) w = W1[n * kTcF + k];
+    else if (j <= 4) w = W2[n * kTcH + (j - 1) * 64 + k];
+    else w = W3[n * kTcH + (j - 5) * 64 + k];
+    *reinterpret_cast<__nv_bfloat16*>(img + j * kChunkBytes + sw128(n, k >> 3) + (k & 7) * 2) = w;
+  }
+}
+
+}  // namespace
+
+size_t mlp_tc_image_bytes() { return (size_t)kChunksPerTile * kChunkBytes; }
+
+cudaError_t mlp_tc_build_image(const void* W1, const void* W2, const void* W3, void* img, cudaStream_t s) {
+  k_mlp_tc_image<<<(kChunksPerTile * kTcH * 64 + 255) / 256, 256, 0, s>>>(
+      static_cast<const __nv_bfloat16*>(W1), static_cast<const __nv_bfloat16*>(W2),
+      static_cast<const __nv_bfloat16*>(W3), static_cast<uint8_t*>(img));
+  return cudaGetLastError();
+}
+
+// y[i] = sd_hat of row i for rows i < min(*m_dev, rows_cap) (all rows_cap
+// rows when m_dev is null): from feature rows X (16-byte aligned, rows of 64
+// BF16) or, when X is null, from configurations q (n x rows_cap, stride ldq).
+cudaError_t mlp_tc_forward(const void* X, const float* q, long long ldq, int n, long long rows_cap, const int* m_dev,
+                           const void* img, const float* b1, const float* b2, const float* b3, const float* w4,
+                           const float* b4, float* y, int* err, cudaStream_t s) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  }
+  if (rows_cap <= 0) return cudaSuccess;
+  const long long tiles = (rows_cap + kTcRows - 1) / kTcRows;
+  TcArgs a{static_cast<const __nv_bfloat16*>(X), q, ldq, n, rows_cap, m_dev, static_cast<const uint8_t*>(img),
+           b1, b2, b3, w4, b4, y, err};
+  k_mlp_forward_tc<<<(unsigned)(tiles < sms ? tiles : sms), kThreads, kSmemBytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ezo

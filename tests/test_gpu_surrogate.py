@@ -69,12 +69,15 @@ def test_surrogate_gradient_matches_oracle(ezo):
         o += c
 
 
-def test_surrogate_predict_matches_oracle(ezo):
+@pytest.mark.parametrize("N", [1, 129, 1000, 40037])
+def test_surrogate_predict_matches_oracle(ezo, N):
+    """The tensor-core forward pass (128-row tiles, one persistent block per
+    SM) against the FP64 oracle: a single row, a ragged second tile, several
+    blocks, and several tiles per block with a ragged last tile."""
     rd, _ = _scene()
     robot = ezo.Robot(rd)
     sur = ezo.Surrogate(robot, seed=4)
     rng = np.random.default_rng(2)
-    N = 1000  # not a multiple of the 64-row tile
     q = rng.uniform(rd.q_lo, rd.q_hi, size=(N, 7)).astype(np.float32)
     out = torch.empty(N, device="cuda")
     sur.predict(torch.from_numpy(q.T.copy()).cuda(), out)
