@@ -256,7 +256,8 @@ def run_workload(args):
     all paths inflated in one batch under one CUDA graph, against the plain
     per-segment launch loop. --workload stress: table point cloud (1024
     spheres of 2 cm), 64-segment path, N_p = 1e6 samples per round: plain,
-    batched, batched + surrogate."""
+    batched, batched + surrogate. --workload surrogate: the MLP's forward pass
+    alone on 2^rows_log2 configurations."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -312,6 +313,28 @@ def run_workload(args):
                     "per_segment_loop_ms": float(t_loop), "kept_segments_loop": int(kept_loop),
                     "speedup_wavefront_vs_loop": float(t_loop / min(t_wave)),
                     "speedup_speculative_vs_loop": float(t_loop / min(t_graph))})
+    elif args.workload == "surrogate":
+        # inference of the BF16 MLP alone (tensor-core forward pass with the
+        # features computed in the kernel) on 2^rows_log2 configurations; the
+        # weights are the seeded initialisation (the time does not depend on them)
+        nb = 1 << args.rows_log2
+        sur = ezo.Surrogate(robot, seed=6)
+        q = torch.from_numpy(wl.uniform_configs(11, rd, nb).astype(np.float32).T.copy()).cuda()
+        y = torch.empty(nb, device="cuda")
+        for _ in range(args.warmup):
+            sur.predict(q, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sur.predict(q, y)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        gemm_flops = 2.0 * nb * (64 * 256 + 2 * 256 * 256)
+        peak, src = bf16_peak()
+        tf = gemm_flops / (ms / 1e3) / 1e12
+        out.update({"rows": nb, "ms": ms, "rows_per_s": nb / (ms / 1e3), "gemm_tflops": tf, "peak": peak,
+                    "peak_source": src, "frac": tf / peak, "nan_outputs": int(torch.isnan(y).sum())})
     else:
         sc = scenes["table_cloud"]
         env_np = wl.table_cloud_obstacles(sc["cloud_seed"])
@@ -532,7 +555,8 @@ def main():
                     help="only the collision checker on 2e6 configurations (for profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed path steps and the kernel pass (no plain, surrogate or checker legs)")
-    ap.add_argument("--workload", default="path", choices=["path", "batched", "stress"])
+    ap.add_argument("--workload", default="path", choices=["path", "batched", "stress", "surrogate"])
+    ap.add_argument("--rows-log2", type=int, default=20, help="surrogate: log2 of the configurations per call")
     ap.add_argument("--paths", type=int, default=256, help="batched: number of seed paths")
     ap.add_argument("--np-stress", type=int, default=1_000_000, help="stress: samples per round and segment")
     args = ap.parse_args()
