@@ -388,7 +388,10 @@ ezo_status ezo_profile_read(double* ms, int64_t* launches, int32_t n_kinds);
  * Not in the paper. A small MLP sd_hat(q) estimates the signed distance from
  * the features [sin q, cos q] (zero-padded to 64) through three hidden layers
  * of 256 SiLU units to one output. Hidden-layer products run on BF16 tensor
- * cores with FP32 accumulation; weights have FP32 masters trained with Adam
+ * cores with FP32 accumulation (inference: one kernel per 128-row tile with
+ * the accumulators in tensor memory and SiLU on the hardware tanh
+ * approximation, relative error ~2^-11 before the BF16 rounding of each
+ * activation); weights have FP32 masters trained with Adam
  * (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the mean squared error. It
  * only orders and prefilters bisection candidates (ezo_batch_attach_surrogate);
  * labels and certification stay exact.
