@@ -5,7 +5,7 @@
 // row costs its configuration (or 128 bytes of features) and 4 bytes of
 // output in HBM.
 //
-// Roles (544 threads):
+// Roles (576 threads):
 //   warps 0-15 epilogue: warp w owns rows 32 (w % 4) .. +31 of the tile (the
 //              tensor-memory lanes it may read) and, in each K-chunk c of 64
 //              columns, the 16 columns 64 c + 16 (w / 4) .. +15. It stages
@@ -13,12 +13,13 @@
 //              columns, adds the bias, applies SiLU, rounds to BF16 and writes
 //              the next layer's input to shared memory chunk by chunk; the
 //              last layer is reduced against w4 into y.
-//   warp 16    lane 0 streams the weights (nine 32 KB chunks per tile: W1,
+//   warp 16    lane 0 issues the tcgen05.mma instructions (M = 128,
+//              N = 256, K = 16, BF16 x BF16 -> FP32); the whole warp
+//              allocates and frees the 512 tensor-memory columns.
+//   warp 17    lane 0 streams the weights (nine 32 KB chunks per tile: W1,
 //              then W2 and W3 in four K-chunks of 64) with bulk asynchronous
-//              copies through a four-stage ring and issues the tcgen05.mma
-//              instructions (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32);
-//              the whole warp allocates and frees the 512 tensor-memory
-//              columns.
+//              copies through a four-stage ring, ahead of the MMAs by the
+//              depth of the ring.
 // Two accumulators (columns 0-255 and 256-511) alternate from layer to
 // layer, the MMAs of K-chunk c of a layer start as soon as chunk c of its
 // input is written (the epilogue writes the chunks in order), and the next
@@ -55,7 +56,7 @@ constexpr int kHBytes = kTcRows * 512;  // hidden tile: 4 K-chunks of 16 KB
 constexpr int kSmemBytes = kXBytes + kHBytes + kStages * kChunkBytes + 1024;  // + alignment slack
 constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = kEpiThreads + 32;
+constexpr int kThreads = kEpiThreads + 64;  // + the MMA warp and the weight producer warp
 constexpr int kTmemCols = 2 * kTcH;  // two accumulators
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
@@ -270,31 +271,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
   const uint32_t tbase = tmem_slot;
   bool ok = true;
 
-  if (warp == kEpiWarps) {
+  if (warp == kEpiWarps + 1) {
     if (lane == 0) {
-      // ---- weight producer and MMA issuer ----
       long long my_tiles = 0;
       for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) ++my_tiles;
       const long long total = my_tiles * kChunksPerTile;
-      long long wl = 0, wi = 0;
-      auto top_up = [&](long long limit) {
-        while (ok && wl < total && wl < limit) {
-          const int st = (int)(wl % kStages);
-          if (wl >= kStages && !mbar_wait(&w_empty[st], (uint32_t)((wl / kStages - 1) & 1))) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&w_full[st], kChunkBytes);
-          bulk_g2s(sW + st * kChunkBytes, g.wimg + (wl % kChunksPerTile) * kChunkBytes, kChunkBytes, &w_full[st]);
-          ++wl;
+      long long wl = 0;
+      for (; wl < total; ++wl) {
+        const int st = (int)(wl % kStages);
+        if (wl >= kStages && !mbar_wait(&w_empty[st], (uint32_t)((wl / kStages - 1) & 1))) {
+          ok = false;
+          break;
         }
-      };
+        mbar_expect_tx(&w_full[st], kChunkBytes);
+        bulk_g2s(sW + st * kChunkBytes, g.wimg + (wl % kChunksPerTile) * kChunkBytes, kChunkBytes, &w_full[st]);
+      }
+      if (!ok) atomicExch(g.err, 1);
+      for (long long c = (wl > kStages ? wl - kStages : 0); c < wl; ++c)
+        mbar_wait(&w_full[c % kStages], (uint32_t)((c / kStages) & 1));
+    }
+    __syncwarp();
+  } else if (warp == kEpiWarps) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      long long my_tiles = 0;
+      for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) ++my_tiles;
+      long long wi = 0;
       for (long long tl = 0; tl < my_tiles && ok; ++tl) {
         for (int L = 0; L < 3 && ok; ++L) {
           const long long G = 3 * tl + L;  // layers so far: accumulator G % 2, its use G / 2
           const int a = (int)(G & 1);
           const long long use = G >> 1;
-          top_up(wi + kStages - 1);
           // the accumulator's previous contents have been read by every epilogue thread
           if (use >= 1 && !mbar_wait(&acc_empty[a], (uint32_t)((use - 1) & 1))) {
             ok = false;
@@ -313,8 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
               ok = false;
               break;
             }
-            top_up(wi + kStages - 1);
-            const int st = (int)(wi % kStages);
+              const int st = (int)(wi % kStages);
             if (!mbar_wait(&w_full[st], (uint32_t)((wi / kStages) & 1))) {
               ok = false;
               break;
@@ -330,11 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
           if (ok) umma_commit(&acc_full[a]);
         }
       }
-      if (!ok) {
-        atomicExch(g.err, 1);
-        // let the copies already issued land before the block exits
-        for (long long c = wi; c < wl; ++c) mbar_wait(&w_full[c % kStages], (uint32_t)((c / kStages) & 1));
-      }
+      if (!ok) atomicExch(g.err, 1);
       // every MMA issued here has completed before the columns are freed
       umma_commit(&mma_done);
       if (!mbar_wait(&mma_done, 0)) atomicExch(g.err, 1);
