@@ -334,7 +334,8 @@ def run_workload(args):
         peak, src = bf16_peak()
         tf = gemm_flops / (ms / 1e3) / 1e12
         out.update({"rows": nb, "ms": ms, "rows_per_s": nb / (ms / 1e3), "gemm_tflops": tf, "peak": peak,
-                    "peak_source": src, "frac": tf / peak, "nan_outputs": int(torch.isnan(y).sum())})
+                    "peak_source": src, "frac": tf / peak, "nan_outputs": int(torch.isnan(y).sum()),
+                    "wait_timed_out": sur.timed_out()})
     else:
         sc = scenes["table_cloud"]
         env_np = wl.table_cloud_obstacles(sc["cloud_seed"])

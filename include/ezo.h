@@ -423,6 +423,12 @@ ezo_status ezo_surrogate_grad(ezo_surrogate* sur, const float* q_dev, int64_t ld
                               float* grad, float* loss, void* cuda_stream);
 ezo_status ezo_surrogate_predict(ezo_surrogate* sur, const float* q_dev, int64_t ldq, int64_t N, float* out_dev,
                                  void* cuda_stream);
+/* Health of the tensor-core forward pass: every wait inside it is bounded
+ * (about 2 s); a wait that gave up writes NaN for the rows not finished and
+ * sets a flag on the device. *timed_out receives that flag (0 or 1) after the
+ * work queued on cuda_stream has finished; reset != 0 clears it.
+ * Synchronous. EZO_ERR_INVALID_ARG for NULL arguments. */
+ezo_status ezo_surrogate_status(ezo_surrogate* sur, int32_t* timed_out, int32_t reset, void* cuda_stream);
 
 /* Surrogate-guided bisection for a batch (not in the paper): in each round
  * the N_b bisection steps of every candidate are taken on sd_hat (predicted

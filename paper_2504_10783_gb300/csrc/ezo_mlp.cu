@@ -628,6 +628,25 @@ ezo_status ezo_surrogate_predict(ezo_surrogate* S, const float* q_dev, int64_t l
   return EZO_OK;
 }
 
+ezo_status ezo_surrogate_status(ezo_surrogate* S, int32_t* timed_out, int32_t reset, void* stream) {
+  if (!S || !timed_out) {
+    ezo_internal_set_error("ezo_surrogate_status: null argument");
+    return EZO_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, S->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(S->tc_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    ezo_internal_set_error((std::string("ezo_surrogate_status: ") + cudaGetErrorString(e)).c_str());
+    return EZO_ERR_CUDA;
+  }
+  *timed_out = v != 0 ? 1 : 0;
+  ezo_internal_set_error("");
+  return EZO_OK;
+}
+
 ezo_status ezo_surrogate_train(ezo_surrogate* S, const ezo_env* env, int64_t n_samples, int32_t epochs, int32_t batch,
                                float lr, uint64_t data_seed, float label_lo, float label_hi, float* epoch_loss,
                                void* stream) {

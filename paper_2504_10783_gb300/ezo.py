@@ -93,6 +93,7 @@ def _sig(lib):
                                       C.POINTER(C.c_float), _P]
     f.ezo_surrogate_grad.argtypes = [_P, _P, _I64, _P, _I32, C.POINTER(C.c_float), C.POINTER(C.c_float), _P]
     f.ezo_surrogate_predict.argtypes = [_P, _P, _I64, _I64, _P, _P]
+    f.ezo_surrogate_status.argtypes = [_P, C.POINTER(_I32), _I32, _P]
     f.ezo_batch_attach_surrogate.argtypes = [_P, _P, C.c_float]
     f.ezo_batch_set_sample_lanes.argtypes = [_P, _I32]
     f.ezo_batch_get_polytopes.argtypes = [_P, C.POINTER(_I32), C.POINTER(_I32), _DP, _DP, _I32, C.POINTER(_I32), _P]
@@ -611,3 +612,9 @@ class Surrogate:
         n, N = q_dev.shape
         _check(lib().ezo_surrogate_predict(self.h, C.c_void_p(q_dev.data_ptr()), _ld(q_dev), N,
                                            C.c_void_p(out_dev.data_ptr()), _stream(stream)))
+
+    def timed_out(self, reset: bool = False, stream=None) -> bool:
+        """Whether a bounded wait of the tensor-core forward pass gave up."""
+        out = _I32()
+        _check(lib().ezo_surrogate_status(self.h, C.byref(out), 1 if reset else 0, _stream(stream)))
+        return bool(out.value)

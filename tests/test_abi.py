@@ -55,3 +55,5 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     st = ezo.lib().ezo_probe_fp32_fma(None, None)
     assert st == 1
     assert b"tflops" in ezo.lib().ezo_last_error()
+    st = ezo.lib().ezo_surrogate_status(None, None, 0, None)
+    assert st == 1

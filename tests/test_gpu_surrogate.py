@@ -84,6 +84,7 @@ def test_surrogate_predict_matches_oracle(ezo, N):
     torch.cuda.synchronize()
     y_ref, _ = so.forward(gpu_weights_as_used(sur.params()), bf16_round(so.features(q.astype(np.float64))))
     y = out.cpu().numpy()
+    assert not sur.timed_out()
     assert np.abs(y - y_ref).max() <= 1e-2 * max(1.0, np.abs(y_ref).max())
 
 
