@@ -567,8 +567,6 @@ struct ezo_batch {
   // surrogate-guided bisection
   ezo_surrogate* sur = nullptr;
   long long sur_rows = 0;
-  void* s_X = nullptr;
-  float* s_y = nullptr;
 };
 
 namespace {
@@ -580,7 +578,7 @@ ezo_status batch_free_device(ezo_batch* b) {
   void* ptrs[] = {b->d_st,    b->d_v1,    b->d_v2,   b->d_A,    b->d_b,      b->d_S,      b->d_flags,
                   b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx, b->d_ga, b->d_gb,
                   b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0,
-                  b->s_X, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
+                  b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
                   b->view.s_bits, b->view.s_ok, b->view.s_rows};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -601,15 +599,16 @@ int host_test_size(int k, double eps, double delta, double tau) {
 
 }  // namespace
 
-extern "C" cudaError_t ezo_internal_mlp_forward(ezo_surrogate* S, const void* X, long long rows_cap, const int* m_dev,
-                                                float* yhat, cudaStream_t s);
+extern "C" cudaError_t ezo_internal_mlp_bisect(ezo_surrogate* S, long long rows_cap, const int* m_dev,
+                                               const float* s_p32, const float* s_d32, float* s_lo, float* s_hi,
+                                               uint32_t* s_bits, int n_b, float margin, cudaStream_t s);
 extern "C" int ezo_internal_surrogate_dof(const ezo_surrogate* S);
 
 namespace {
 
 // Step 4 with a surrogate: N_b surrogate bisection steps for every candidate
-// (one MLP batch per step), one exact check of each end point, exact
-// bisection for the candidates whose end point is free.
+// (all of them in one tensor-core launch), one exact check of each end point,
+// exact bisection for the candidates whose end point is free.
 cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
   if (!b->sur) {
     b->view.bis_mode = 0;
@@ -617,12 +616,9 @@ cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
   }
   const int g = (int)std::max<long long>(1, std::min<long long>((b->sur_rows + 255) / 256, 4096));
   cudaError_t e = launch_sbis_init(b->view, g, s);
-  for (int st = 0; st < b->prm.n_b && e == cudaSuccess; ++st) {
-    e = launch_sbis_mid(b->view, b->s_X, g, s);
-    if (e == cudaSuccess)
-      e = ezo_internal_mlp_forward(b->sur, b->s_X, b->sur_rows, b->view.s_rows, b->s_y, s);
-    if (e == cudaSuccess) e = launch_sbis_update(b->view, b->s_y, st, g, s);
-  }
+  if (e == cudaSuccess)
+    e = ezo_internal_mlp_bisect(b->sur, b->sur_rows, b->view.s_rows, b->view.s_p32, b->view.s_d32, b->view.s_lo,
+                                b->view.s_hi, b->view.s_bits, b->prm.n_b, b->view.sbis_margin, s);
   if (e == cudaSuccess) {
     b->view.bis_mode = 1;
     e = launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
@@ -1045,13 +1041,11 @@ ezo_status ezo_batch_attach_surrogate(ezo_batch* b, ezo_surrogate* sur, float ma
     return fail(EZO_ERR_INVALID_ARG, "ezo_batch_attach_surrogate: surrogate of another robot, or more than 8 joints");
   const long long rows = (long long)b->max_bisect_tiles * kTile;
   if (rows > b->sur_rows) {
-    void* ps[] = {b->s_X, b->s_y, b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
+    void* ps[] = {b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
                   b->view.s_bits, b->view.s_ok, b->view.s_rows};
     for (void* p : ps)
       if (p) cudaFree(p);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&b->s_X, (size_t)rows * 64 * 2);
-    if (e == cudaSuccess) e = dalloc(&b->s_y, rows);
     if (e == cudaSuccess) e = dalloc(&b->view.s_p32, rows * 8);
     if (e == cudaSuccess) e = dalloc(&b->view.s_d32, rows * 8);
     if (e == cudaSuccess) e = dalloc(&b->view.s_lo, rows);

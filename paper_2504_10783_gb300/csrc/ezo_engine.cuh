@@ -135,8 +135,6 @@ cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s);
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s);
 // surrogate-guided bisection helpers (ezo_k_sbis.cu)
 cudaError_t launch_sbis_init(const BatchView& v, int grid, cudaStream_t s);
-cudaError_t launch_sbis_mid(const BatchView& v, void* X_bf16, int grid, cudaStream_t s);
-cudaError_t launch_sbis_update(const BatchView& v, const float* yhat, int step, int grid, cudaStream_t s);
 cudaError_t launch_round_place(const BatchView& v, cudaStream_t s);
 cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 

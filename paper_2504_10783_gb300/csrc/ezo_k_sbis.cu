@@ -1,9 +1,10 @@
 // Surrogate-guided bisection (not in the paper): the N_b bisection steps of
 // every candidate of a round are first taken on the learned signed distance
-// (predicted collision iff sd_hat < margin), evaluated for all candidates at
-// once as one MLP batch per step; the bisection kernel then verifies each end
-// point with one exact check and redoes the exact bisection of Sec. IV-B for
-// candidates whose end point is not in collision.
+// (predicted collision iff sd_hat < margin), all of them in one launch of the
+// tensor-core forward kernel (ezo_mlp_tc.cu) on the brackets set up here; the
+// bisection kernel then verifies each end point with one exact check and
+// redoes the exact bisection of Sec. IV-B for candidates whose end point is
+// not in collision.
 //
 // Row r of the MLP batch is candidate tile.y + (r % kTile) of bisection tile
 // r / kTile (the same numbering the bisection kernel uses).
@@ -13,8 +14,6 @@
 #include "ezo_kernels_common.cuh"
 
 namespace ezo {
-
-constexpr int kFeat = 64;
 
 // c_proj and c - c_proj per row (FP64 projection, stored in FP32), bracket [0, 1]
 template <int NDOF>
@@ -49,48 +48,8 @@ __global__ void k_sbis_init(BatchView v) {
   }
 }
 
-// features [sin q, cos q, 0..] of the midpoint of each row's bracket
-__global__ void k_sbis_mid(BatchView v, __nv_bfloat16* __restrict__ X) {
-  const int rows = *v.s_rows;
-  const int n = v.n;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-    const float f = 0.5f * (v.s_lo[r] + v.s_hi[r]);
-    for (int k = 0; k < kFeat; ++k) {
-      float val = 0.f;
-      if (k < n) val = sinf(fmaf(f, v.s_d32[r * 8 + k], v.s_p32[r * 8 + k]));
-      else if (k < 2 * n) val = cosf(fmaf(f, v.s_d32[r * 8 + k - n], v.s_p32[r * 8 + k - n]));
-      X[(long long)r * kFeat + k] = __float2bfloat16(val);
-    }
-  }
-}
-
-// one surrogate bisection step: keep the end predicted in collision
-__global__ void k_sbis_update(BatchView v, const float* __restrict__ yhat, int step) {
-  const int rows = *v.s_rows;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-    const float lo = v.s_lo[r], hi = v.s_hi[r];
-    const float f = 0.5f * (lo + hi);
-    if (yhat[r] < v.sbis_margin) {
-      v.s_hi[r] = f;
-      v.s_bits[r] |= 1u << step;
-    } else {
-      v.s_lo[r] = f;
-    }
-  }
-}
-
 cudaError_t launch_sbis_init(const BatchView& v, int grid, cudaStream_t s) {
   EZO_DISPATCH_NDOF(v.n, { k_sbis_init<ND><<<grid, 256, 0, s>>>(v); });
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sbis_mid(const BatchView& v, void* X, int grid, cudaStream_t s) {
-  k_sbis_mid<<<grid, 256, 0, s>>>(v, static_cast<__nv_bfloat16*>(X));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sbis_update(const BatchView& v, const float* yhat, int step, int grid, cudaStream_t s) {
-  k_sbis_update<<<grid, 256, 0, s>>>(v, yhat, step);
   return cudaGetLastError();
 }
 

@@ -31,9 +31,13 @@ namespace ezo {
 // tensor-core forward pass (ezo_mlp_tc.cu)
 size_t mlp_tc_image_bytes();
 cudaError_t mlp_tc_build_image(const void* W1, const void* W2, const void* W3, void* img, cudaStream_t s);
-cudaError_t mlp_tc_forward(const void* X, const float* q, long long ldq, int n, long long rows_cap, const int* m_dev,
+cudaError_t mlp_tc_forward(const float* q, long long ldq, int n, long long rows_cap, const int* m_dev,
                            const void* img, const float* b1, const float* b2, const float* b3, const float* w4,
                            const float* b4, float* y, int* err, cudaStream_t s);
+cudaError_t mlp_tc_bisect(int n, long long rows_cap, const int* m_dev, const void* img, const float* b1,
+                          const float* b2, const float* b3, const float* w4, const float* b4, const float* s_p32,
+                          const float* s_d32, float* s_lo, float* s_hi, uint32_t* s_bits, int n_b, float margin,
+                          int* err, cudaStream_t s);
 
 constexpr int kF = 64;   // padded input features
 constexpr int kH = 256;  // hidden width
@@ -477,12 +481,13 @@ cudaError_t adam_step(ezo_surrogate* S, float lr, cudaStream_t s) {
 
 }  // namespace
 
-// Forward pass on BF16 feature rows X [rows_cap x 64] for the rows below the
-// device count *m_dev, on the tensor cores. Internal.
-extern "C" __attribute__((visibility("hidden"))) cudaError_t ezo_internal_mlp_forward(
-    ezo_surrogate* S, const void* X, long long rows_cap, const int* m_dev, float* yhat, cudaStream_t s) {
-  return mlp_tc_forward(X, nullptr, 0, S->n, rows_cap, m_dev, S->wimg, S->p + kOffB1, S->p + kOffB2, S->p + kOffB3, S->p + kOffW4,
-                        S->p + kOffB4, yhat, S->tc_err, s);
+// n_b surrogate bisection steps on the brackets of the rows below the device
+// count *m_dev, in one tensor-core launch. Internal.
+extern "C" __attribute__((visibility("hidden"))) cudaError_t ezo_internal_mlp_bisect(
+    ezo_surrogate* S, long long rows_cap, const int* m_dev, const float* s_p32, const float* s_d32, float* s_lo,
+    float* s_hi, uint32_t* s_bits, int n_b, float margin, cudaStream_t s) {
+  return mlp_tc_bisect(S->n, rows_cap, m_dev, S->wimg, S->p + kOffB1, S->p + kOffB2, S->p + kOffB3, S->p + kOffW4,
+                       S->p + kOffB4, s_p32, s_d32, s_lo, s_hi, s_bits, n_b, margin, S->tc_err, s);
 }
 
 extern "C" __attribute__((visibility("hidden"))) int ezo_internal_surrogate_dof(const ezo_surrogate* S) {
@@ -618,7 +623,7 @@ ezo_status ezo_surrogate_predict(ezo_surrogate* S, const float* q_dev, int64_t l
   if (N == 0) return EZO_OK;
   cudaStream_t s = (cudaStream_t)stream;
   // features computed inside the forward kernel from the configurations
-  mlp_tc_forward(nullptr, q_dev, ldq, S->n, N, nullptr, S->wimg, S->p + kOffB1, S->p + kOffB2, S->p + kOffB3, S->p + kOffW4, S->p + kOffB4,
+  mlp_tc_forward(q_dev, ldq, S->n, N, nullptr, S->wimg, S->p + kOffB1, S->p + kOffB2, S->p + kOffB3, S->p + kOffW4, S->p + kOffB4,
                  out_dev, S->tc_err, s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -2,8 +2,11 @@
 // tensor cores: one persistent kernel runs all three hidden layers of a
 // 128-row tile (features [128 x 64] -> 256 -> 256 -> 256 -> 1) with the
 // accumulators in tensor memory and the activations in shared memory, so a
-// row costs its configuration (or 128 bytes of features) and 4 bytes of
-// output in HBM.
+// row costs its configuration and 4 bytes of output in HBM. In its
+// bisection mode the kernel runs all N_b surrogate bisection steps of a tile
+// in one launch: each step's features are those of the midpoints of the
+// rows' brackets, and the step's prediction halves the brackets in shared
+// memory before the next step.
 //
 // Roles (576 threads):
 //   warps 0-15 epilogue: warp w owns rows 32 (w % 4) .. +31 of the tile (the
@@ -12,7 +15,8 @@
 //              the feature tile, then for each layer reads its 64 accumulator
 //              columns, adds the bias, applies SiLU, rounds to BF16 and writes
 //              the next layer's input to shared memory chunk by chunk; the
-//              last layer is reduced against w4 into y.
+//              last layer is reduced against w4 into y (or into the bisection
+//              step).
 //   warp 16    lane 0 issues the tcgen05.mma instructions (M = 128,
 //              N = 256, K = 16, BF16 x BF16 -> FP32); the whole warp
 //              allocates and frees the 512 tensor-memory columns.
@@ -171,8 +175,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 struct TcArgs {
-  const __nv_bfloat16* X;  // [rows_cap x 64] feature rows, or null: features from q
-  const float* q;          // configurations, n x rows_cap with stride ldq (when X is null)
+  const float* q;          // configurations, n x rows_cap with stride ldq (plain forward pass)
   long long ldq;
   int n;
   long long rows_cap;
@@ -185,28 +188,44 @@ struct TcArgs {
   const float* b4;
   float* y;
   int* err;                // set to 1 when a wait gave up
+  // surrogate bisection (when s_p32 is set): n_b steps per row on the
+  // bracket [lo, hi] of c_proj + f (c - c_proj); y is not written
+  const float* s_p32;      // rows x 8: c_proj
+  const float* s_d32;      // rows x 8: c - c_proj
+  float* s_lo;
+  float* s_hi;
+  uint32_t* s_bits;        // bit k: step k predicted a collision
+  int n_b;
+  float margin;            // predicted collision iff sd_hat < margin
 };
 
-// this thread's share of one feature row: from X the 16-byte chunks 2 sc
-// and 2 sc + 1; from q the features of joints sc, sc + 4, .. (sin q_j at
-// column j, cos q_j at column n + j, as in training; the zero padding
-// columns were written once at the start)
+// this thread's share of one feature row: the features of joints sc, sc + 4,
+// .. (sin q_j at column j, cos q_j at column n + j, as in training; the zero
+// padding columns were written once at the start)
 __device__ __forceinline__ void stage_features(const TcArgs& g, uint8_t* sX, int row, int sc, long long grow,
                                                bool live) {
-  if (g.X) {
-#pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      const int c = 2 * sc + cc;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (live) v = *reinterpret_cast<const uint4*>(g.X + grow * kTcF + c * 8);
-      *reinterpret_cast<uint4*>(sX + sw128(row, c)) = v;
-    }
-    return;
-  }
   for (int j = sc; j < g.n; j += 4) {
     float sn = 0.f, cs = 0.f;
     if (live) {
       const float qj = g.q[(long long)j * g.ldq + grow];
+      sn = sinf(qj);
+      cs = cosf(qj);
+    }
+    const int fc = g.n + j;
+    *reinterpret_cast<__nv_bfloat16*>(sX + sw128(row, j >> 3) + (j & 7) * 2) = __float2bfloat16(sn);
+    *reinterpret_cast<__nv_bfloat16*>(sX + sw128(row, fc >> 3) + (fc & 7) * 2) = __float2bfloat16(cs);
+  }
+}
+
+// features of the midpoint f = (lo + hi) / 2 of a row's bracket: q_j =
+// c_proj_j + f (c_j - c_proj_j), joints sc, sc + 4, ..
+__device__ __forceinline__ void stage_bracket_features(const TcArgs& g, uint8_t* sX, int row, int sc,
+                                                       long long grow, bool live, float lo, float hi) {
+  const float f = 0.5f * (lo + hi);
+  for (int j = sc; j < g.n; j += 4) {
+    float sn = 0.f, cs = 0.f;
+    if (live) {
+      const float qj = fmaf(f, g.s_d32[grow * 8 + j], g.s_p32[grow * 8 + j]);
       sn = sinf(qj);
       cs = cosf(qj);
     }
@@ -224,6 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
   __shared__ float sbias[3][kTcH];
   __shared__ float sw4[kTcH];
   __shared__ float ypart[2][4][kTcRows];
+  __shared__ float br_lo[kTcRows], br_hi[kTcRows];  // bisection: the brackets of the current tile
+  __shared__ uint32_t br_bits[kTcRows];
 
   const uint32_t base_u32 = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* base = smem_raw + (base_u32 - smem_u32(smem_raw));
@@ -234,6 +255,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long m_lim = g.m_dev ? min((long long)*g.m_dev, g.rows_cap) : g.rows_cap;
   const long long n_tiles = (m_lim + kTcRows - 1) / kTcRows;
+  // work items: (tile, bisection step), steps innermost; one step per tile
+  // for a plain forward pass
+  const bool bis = g.s_p32 != nullptr;
+  const int n_steps = bis ? g.n_b : 1;
+  long long my_items = 0;
+  for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) my_items += n_steps;
 
   // feature tile starts zero: the padding columns stay zero when the features
   // are computed from q
@@ -273,9 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
 
   if (warp == kEpiWarps + 1) {
     if (lane == 0) {
-      long long my_tiles = 0;
-      for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) ++my_tiles;
-      const long long total = my_tiles * kChunksPerTile;
+      const long long total = my_items * kChunksPerTile;
       long long wl = 0;
       for (; wl < total; ++wl) {
         const int st = (int)(wl % kStages);
@@ -294,10 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
   } else if (warp == kEpiWarps) {
     if (lane == 0) {
       // ---- MMA issuer ----
-      long long my_tiles = 0;
-      for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) ++my_tiles;
       long long wi = 0;
-      for (long long tl = 0; tl < my_tiles && ok; ++tl) {
+      for (long long tl = 0; tl < my_items && ok; ++tl) {
         for (int L = 0; L < 3 && ok; ++L) {
           const long long G = 3 * tl + L;  // layers so far: accumulator G % 2, its use G / 2
           const int a = (int)(G & 1);
@@ -347,15 +370,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
     const int lq = warp & 3, sc = warp >> 2;
     const int row = lq * 32 + lane;
     const uint32_t lane_addr = tbase + ((uint32_t)(lq * 32) << 16) + (uint32_t)(sc * 16);
-    long long t = blockIdx.x;
-    if (t < n_tiles) {
-      const long long grow = t * kTcRows + row;
-      stage_features(g, sX, row, sc, grow, grow < m_lim);
+    auto tile_of = [&](long long it) { return blockIdx.x + (it / n_steps) * (long long)gridDim.x; };
+    // bisection: the brackets of a tile's rows, held by the sc = 0 threads
+    auto load_brackets = [&](long long it) {
+      const long long grow = tile_of(it) * kTcRows + row;
+      if (sc == 0) {
+        const bool live = grow < m_lim;
+        br_lo[row] = live ? g.s_lo[grow] : 0.f;
+        br_hi[row] = live ? g.s_hi[grow] : 1.f;
+        br_bits[row] = live ? g.s_bits[grow] : 0u;
+      }
+    };
+    auto stage_item = [&](long long it) {
+      const long long grow = tile_of(it) * kTcRows + row;
+      if (bis) stage_bracket_features(g, sX, row, sc, grow, grow < m_lim, br_lo[row], br_hi[row]);
+      else stage_features(g, sX, row, sc, grow, grow < m_lim);
       proxy_fence();
       mbar_arrive(&x_ready);
+    };
+    if (my_items > 0) {
+      if (bis) {
+        load_brackets(0);
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+      }
+      stage_item(0);
     }
-    for (long long tl = 0; t < n_tiles; t += gridDim.x, ++tl) {
-      const long long grow = t * kTcRows + row;
+    for (long long tl = 0; tl < my_items; ++tl) {
+      const long long grow = tile_of(tl) * kTcRows + row;
       const bool live = grow < m_lim;
       float part = 0.f;
       for (int L = 0; L < 3; ++L) {
@@ -374,16 +415,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(&acc_empty[a]);
-        if (L == 1 && ok) {
+        if (L == 1 && ok && !bis && tl + 1 < my_items) {
           // the first layer of this tile has finished reading the feature
           // tile: stage the next tile's features now
-          const long long tn = t + gridDim.x;
-          if (tn < n_tiles) {
-            const long long gn = tn * kTcRows + row;
-            stage_features(g, sX, row, sc, gn, gn < m_lim);
-            proxy_fence();
-            mbar_arrive(&x_ready);
-          }
+          stage_item(tl + 1);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -411,10 +446,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(TcArgs g) {
       }
       ypart[tl & 1][sc][row] = part;
       asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
-      if (sc == 0 && live) {
+      float yv = __int_as_float(0x7fc00000);
+      if (sc == 0 && ok) {
         const float* yp = &ypart[tl & 1][0][row];
-        g.y[grow] = ok ? ((yp[0] + yp[kTcRows]) + (yp[2 * kTcRows] + yp[3 * kTcRows])) + g.b4[0]
-                       : __int_as_float(0x7fc00000);
+        yv = ((yp[0] + yp[kTcRows]) + (yp[2 * kTcRows] + yp[3 * kTcRows])) + g.b4[0];
+      }
+      if (!bis) {
+        if (sc == 0 && live) g.y[grow] = yv;
+        continue;
+      }
+      // one bisection step: keep the end predicted in collision
+      const int step = (int)(tl % n_steps);
+      if (sc == 0 && live) {
+        const float f = 0.5f * (br_lo[row] + br_hi[row]);
+        if (yv < g.margin) {
+          br_hi[row] = f;
+          br_bits[row] |= 1u << step;
+        } else {
+          br_lo[row] = f;
+        }
+        if (step == n_steps - 1) {
+          g.s_lo[grow] = br_lo[row];
+          g.s_hi[grow] = br_hi[row];
+          g.s_bits[grow] = br_bits[row];
+        }
+      }
+      if (tl + 1 < my_items) {
+        if (step == n_steps - 1) load_brackets(tl + 1);
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+        if (ok) stage_item(tl + 1);
       }
     }
     if (!ok) atomicExch(g.err, 1);
@@ -455,10 +515,9 @@ cudaError_t mlp_tc_build_image(const void* W1, const void* W2, const void* W3, v
   return cudaGetLastError();
 }
 
-// y[i] = sd_hat of row i for rows i < min(*m_dev, rows_cap) (all rows_cap
-// rows when m_dev is null): from feature rows X (16-byte aligned, rows of 64
-// BF16) or, when X is null, from configurations q (n x rows_cap, stride ldq).
-cudaError_t mlp_tc_forward(const void* X, const float* q, long long ldq, int n, long long rows_cap, const int* m_dev,
+// y[i] = sd_hat of configuration i (q: n x rows_cap, stride ldq) for rows
+// i < min(*m_dev, rows_cap) (all rows_cap rows when m_dev is null).
+cudaError_t mlp_tc_forward(const float* q, long long ldq, int n, long long rows_cap, const int* m_dev,
                            const void* img, const float* b1, const float* b2, const float* b3, const float* w4,
                            const float* b4, float* y, int* err, cudaStream_t s) {
   static int sms = 0;
@@ -470,8 +529,31 @@ cudaError_t mlp_tc_forward(const void* X, const float* q, long long ldq, int n, 
   }
   if (rows_cap <= 0) return cudaSuccess;
   const long long tiles = (rows_cap + kTcRows - 1) / kTcRows;
-  TcArgs a{static_cast<const __nv_bfloat16*>(X), q, ldq, n, rows_cap, m_dev, static_cast<const uint8_t*>(img),
-           b1, b2, b3, w4, b4, y, err};
+  TcArgs a{q, ldq, n, rows_cap, m_dev, static_cast<const uint8_t*>(img), b1, b2, b3, w4, b4, y, err, nullptr,
+           nullptr, nullptr, nullptr, nullptr, 0, 0.f};
+  k_mlp_forward_tc<<<(unsigned)(tiles < sms ? tiles : sms), kThreads, kSmemBytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+// n_b surrogate bisection steps for rows i < min(*m_dev, rows_cap) in one
+// launch: row i's bracket [s_lo[i], s_hi[i]] of s_p32 + f s_d32 (rows of 8
+// floats) is halved n_b times, keeping the end where sd_hat < margin, and
+// bit k of s_bits[i] records step k's prediction of a collision.
+cudaError_t mlp_tc_bisect(int n, long long rows_cap, const int* m_dev, const void* img, const float* b1,
+                          const float* b2, const float* b3, const float* w4, const float* b4, const float* s_p32,
+                          const float* s_d32, float* s_lo, float* s_hi, uint32_t* s_bits, int n_b, float margin,
+                          int* err, cudaStream_t s) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  }
+  if (rows_cap <= 0 || n_b <= 0 || n_b > 32) return rows_cap <= 0 || n_b <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  const long long tiles = (rows_cap + kTcRows - 1) / kTcRows;
+  TcArgs a{nullptr, 0, n, rows_cap, m_dev, static_cast<const uint8_t*>(img), b1, b2, b3, w4, b4, nullptr, err, s_p32,
+           s_d32, s_lo, s_hi, s_bits, n_b, margin};
   k_mlp_forward_tc<<<(unsigned)(tiles < sms ? tiles : sms), kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
