@@ -432,7 +432,8 @@ ezo_status ezo_surrogate_status(ezo_surrogate* sur, int32_t* timed_out, int32_t 
 
 /* Surrogate-guided bisection for a batch (not in the paper): in each round
  * the N_b bisection steps of every candidate are taken on sd_hat (predicted
- * collision iff sd_hat < margin, one MLP batch per step); each end point is
+ * collision iff sd_hat < margin; all steps of all candidates in one
+ * tensor-core launch); each end point is
  * then checked exactly and kept when it collides, otherwise that candidate
  * gets the exact bisection of Sec. IV-B. Labels, the unadaptive test and the
  * planes use exact checks only. sur = NULL detaches. The robot must have at
