@@ -392,10 +392,11 @@ def bf16_peak():
         return 1900.0, "fallback"
 
 
-def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args):
+def measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream, flush, K, args):
     """Trains the BF16 MLP on 2^22 exact labels (4 epochs), reports its
     false-negative / false-positive rates on 2^16 fresh configurations, and
-    times the path with surrogate-guided bisection."""
+    times the path with surrogate-guided bisection on the same Philox seeds
+    as the timed exact steps (mean over the seeds, like ms_per_step)."""
     from paper_2504_10783_gb300 import workloads as wl
     sur = ezo.Surrogate(robot, seed=6)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -414,9 +415,12 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flus
     yv, col = y.cpu().numpy(), flags.cpu().numpy().astype(bool)
     fn0 = float(np.mean(yv[col] >= 0.0)) if col.any() else 0.0
     fp0 = float(np.mean(yv[~col] < 0.0))
-    bt.attach_surrogate(sur, 0.0)
     times = []
-    for _ in range(max(3, args.steps // 2) + 2):
+    samp = bisc = evals = 0
+    for bt in batches:
+        bt.attach_surrogate(sur, 0.0)
+        bt.reset()
+        bt.run_path(sequential=False, mode=mode)  # builds this batch's graph with the surrogate step
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -426,14 +430,13 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flus
         b.record(stream)
         b.synchronize()
         times.append(a.elapsed_time(b))
-    times = times[2:]
-    samp = bisc = evals = 0
-    for g in range(K):
-        x, y2 = bt.check_split(g)
-        samp += x
-        bisc += y2
-        evals += bt.surrogate_evals(g)
-    bt.attach_surrogate(None)
+        for g in range(K):
+            x, y2 = bt.check_split(g)
+            samp += x
+            bisc += y2
+            evals += bt.surrogate_evals(g)
+        bt.attach_surrogate(None)
+    ns = len(batches)
     # inference throughput of the MLP alone (features, three BF16 GEMMs with
     # fused bias + SiLU, output layer) on 2^20 configurations, timed alone
     # against the burst BF16 peak
@@ -451,9 +454,10 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flus
     gemm_flops = 2.0 * nb * (64 * 256 + 2 * 256 * 256)  # the three hidden-layer GEMMs (features padded to 64)
     peak_bf16, peak_src = bf16_peak()
     inf_tf = gemm_flops / (inf_ms / 1e3) / 1e12
-    return {"ms_per_path": float(np.median(times)), "train_ms": train_ms, "train_samples": 1 << 22, "epochs": 4,
-            "fn_rate_margin0": fn0, "fp_rate_margin0": fp0, "sample_checks": samp, "bisection_checks": bisc,
-            "surrogate_evals": evals,
+    return {"ms_per_path": float(np.mean(times)), "ms_per_path_seed1": float(times[0]), "seeds": ns,
+            "train_ms": train_ms, "train_samples": 1 << 22, "epochs": 4,
+            "fn_rate_margin0": fn0, "fp_rate_margin0": fp0, "sample_checks_per_path": samp / ns,
+            "bisection_checks_per_path": bisc / ns, "surrogate_evals_per_path": evals / ns,
             "inference": {"batch": nb, "ms": inf_ms, "gemm_tflops": inf_tf, "peak": peak_bf16, "peak_source": peak_src,
                           "frac": inf_tf / peak_bf16,
                           "what": "GEMM flops of the three hidden layers / time of the whole forward pass"},
@@ -706,27 +710,28 @@ def main():
     # ---- the plain method for comparison: one segment at a time in path order
     #      (host launch loop, containment skip before each segment) ----
     plain_ms = []
-    for _ in range(0 if args.no_extras else max(3, args.steps // 4)):
+    for b_ in ([] if args.no_extras else batches):  # the same seeds as the timed steps
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        bt.reset()
-        bt.run_path(sequential=True, mode=ezo.RUN_HOST_LOOP)
+        b_.reset()
+        b_.run_path(sequential=True, mode=ezo.RUN_HOST_LOOP)
         e1.record(stream)
         e1.synchronize()
         plain_ms.append(e0.elapsed_time(e1))
     plain = None
     if plain_ms:
         kept_plain = sum(bt.segment(g).status != ezo.SEG_SKIPPED for g in range(K))
-        plain = {"ms_per_path": float(np.median(plain_ms)), "kept_segments": int(kept_plain),
-                 "what": "sequential per-segment inflation (paper's order), host-driven launch loop"}
+        plain = {"ms_per_path": float(np.mean(plain_ms)), "ms_per_path_seed1": float(plain_ms[0]),
+                 "seeds": len(plain_ms), "kept_segments_seed1": int(kept_plain),
+                 "what": "sequential per-segment inflation (paper's order), host-driven launch loop, mean over seeds"}
 
     # ---- batched + learned surrogate: train on exact
     #      labels, then the same path with surrogate-guided bisection ----
     sur_info = None
     if not args.no_surrogate and not args.no_extras:
-        sur_info = measure_surrogate(ezo, torch, robot, env, rd, env_np, bt, mode, stream, flush, K, args)
+        sur_info = measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream, flush, K, args)
 
     # ---- the collision checker alone on the paper's batch size (2e6 configs) ----
     checker = checker_1e8 = forest = {"launches": 0}
