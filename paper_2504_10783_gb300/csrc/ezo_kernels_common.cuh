@@ -153,7 +153,7 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
     for (int j = 0; j < NDOF; ++j) nrm2 = fmaf(d[j], d[j], nrm2);
     const float ut = step_uniform(w[0], w[1], w[2]);
     const bool ok = nrm2 > 0.f;
-    const float inv = ok ? 1.f / sqrtf(nrm2) : 0.f;
+    const float inv = ok ? rsqrtf(nrm2) : 0.f;
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
@@ -223,7 +223,7 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
     }
     const float ut = __shfl_sync(0xffffffffu, ut_part, 0, TS);  // block 0 lives in lane 0
     const bool ok = nrm2 > 0.f;
-    const float inv = ok ? 1.f / sqrtf(nrm2) : 0.f;
+    const float inv = ok ? rsqrtf(nrm2) : 0.f;
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
