@@ -406,7 +406,7 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream,
     e1.record(stream)
     e1.synchronize()
     train_ms = e0.elapsed_time(e1)
-    q = torch.from_numpy(wl.uniform_configs(10, rd, 1 << 16).astype(np.float32).T.copy()).cuda()
+    q = torch.from_numpy(wl.uniform_configs(10, rd, 1 << 20).astype(np.float32).T.copy()).cuda()  # held out
     y = torch.empty(q.shape[1], device="cuda")
     flags = torch.empty(q.shape[1], dtype=torch.uint8, device="cuda")
     sur.predict(q, y)
@@ -437,6 +437,11 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream,
             evals += bt.surrogate_evals(g)
         bt.attach_surrogate(None)
     ns = len(batches)
+    # each candidate takes n_b surrogate steps, then one exact check of its end
+    # point, and n_b exact steps when that end point is free
+    n_b = PARAMS["n_b"]
+    n_cand = evals / n_b
+    n_fail = max(0.0, (bisc - n_cand) / n_b)
     # inference throughput of the MLP alone (features, three BF16 GEMMs with
     # fused bias + SiLU, output layer) on 2^20 configurations, timed alone
     # against the burst BF16 peak
@@ -458,6 +463,8 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream,
             "train_ms": train_ms, "train_samples": 1 << 22, "epochs": 4,
             "fn_rate_margin0": fn0, "fp_rate_margin0": fp0, "sample_checks_per_path": samp / ns,
             "bisection_checks_per_path": bisc / ns, "surrogate_evals_per_path": evals / ns,
+            "held_out_configs": 1 << 20,
+            "end_points_verified_in_collision": (1.0 - n_fail / n_cand) if n_cand else None,
             "inference": {"batch": nb, "ms": inf_ms, "gemm_tflops": inf_tf, "peak": peak_bf16, "peak_source": peak_src,
                           "frac": inf_tf / peak_bf16,
                           "what": "GEMM flops of the three hidden layers / time of the whole forward pass"},
