@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
 // a_i^T c_j > b_i - Delta_i; at most N_f planes. One block per segment.
 // The discard test runs in FP32 with a rounding bound and falls back to FP64
 // inside the bound, so every decision equals the FP64 decision.
+template <int NDOF>
 __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
   const int g = blockIdx.x;
   SegState& st = v.st[g];
@@ -323,8 +324,14 @@ __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
       if (c == bc) {
         out = true;
       } else {
+        // the candidate's coordinates in one batch of loads, then the dot product
+        float cj[NDOF];
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) cj[j] = (j < n) ? v.c32[(long long)n * co + (long long)j * np + c] : 0.f;
         float s32 = 0.f;
-        for (int j = 0; j < n; ++j) s32 = fmaf(s_a32[j], v.c32[(long long)n * co + (long long)j * np + c], s32);
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j)
+          if (j < n) s32 = fmaf(s_a32[j], cj[j], s32);
         const float bound = 2.f * (float)(n + 4) * u * (v.cnorm[co + c] + fabsf(beta32)) + 1e-30f;
         if (fabsf(s32 - beta32) > bound) {
           out = s32 > beta32;
@@ -435,9 +442,12 @@ cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_
 cudaError_t launch_round_place(const BatchView& v, cudaStream_t s) {
   // alive bitmask for the largest N_p of the batch
   const size_t smem = (size_t)((v.np_max + 31) / 32) * sizeof(uint32_t);
-  cudaError_t err = set_smem(k_round_place, smem);
-  if (err != cudaSuccess) return err;
-  k_round_place<<<v.B, 1024, smem, s>>>(v);
+  cudaError_t err = cudaSuccess;
+  EZO_DISPATCH_NDOF(v.n, {
+    err = set_smem(k_round_place<ND>, smem);
+    if (err != cudaSuccess) return err;
+    k_round_place<ND><<<v.B, 1024, smem, s>>>(v);
+  });
   return cudaGetLastError();
 }
 
