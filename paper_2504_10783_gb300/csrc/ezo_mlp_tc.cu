@@ -26,10 +26,11 @@
 //              depth of the ring.
 // Two accumulators (columns 0-255 and 256-511) alternate from layer to
 // layer, the MMAs of K-chunk c of a layer start as soon as chunk c of its
-// input is written (the epilogue writes the chunks in order), and the next
-// tile's features are staged while the current tile is in its second layer,
-// so the tensor cores work on the next layer (or the next tile's first
-// layer) while the epilogue is still busy with the current one.
+// input is written (the epilogue writes the chunks in order), and (in the
+// plain forward pass) the next tile's features are staged while the current
+// tile is in its second layer, so the tensor cores work on the next layer (or
+// the next tile's first layer) while the epilogue is still busy with the
+// current one.
 //
 // Shared-memory operands use the K-major 128-byte swizzled layout: a row of
 // 64 BF16 values is 128 bytes, 8 rows form a 1024-byte atom, and 16-byte
@@ -38,8 +39,9 @@
 // so each chunk is one contiguous bulk copy.
 //
 // Every wait on an mbarrier gives up after about two seconds: the kernel
-// then records an error code, writes NaN for the rows it has not finished and
-// still frees its tensor memory.
+// then records an error code, writes NaN for the rows it has not finished
+// (in the bisection mode such rows take every later step as free) and still
+// frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
