@@ -36,7 +36,7 @@ SEGSTATE_BYTES = 112  # sizeof(SegState): per-segment device state read back wit
 # DRAM bytes per launch of the round kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, ncu, this workload); None where not captured for the
 # current kernel
-TRAFFIC = {"sample": 85760}  # round kernel capture, one launch (10 segments x 1e4 walks)
+TRAFFIC = {"sample": 94208}  # round kernel capture, one launch (10 segments x 1e4 walks)
 # DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe)
 CHECKER_TRAFFIC_2E6 = 56078336 + 154368
 KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")

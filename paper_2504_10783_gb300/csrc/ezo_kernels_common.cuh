@@ -30,16 +30,18 @@ struct SampleParams {
 // from the top 24 bits of (w_2i, w_2i+1) by Box-Muller and the step length
 // from the low bytes of w_0, w_1, w_2 (one 24-bit integer, w_0 lowest).
 // One Box-Muller pair from two 32-bit words: rho = sqrt(-2 ln u1) with u1 in
-// (0, 1], angle 2 pi u2 with u2 in [0, 1). The hardware approximations of ln
-// and of sin/cos (absolute error ~2^-21 on [-pi, pi]) are used; the angle is
-// shifted to pi (2 u2 - 1) in [-pi, pi), which negates sine and cosine.
+// (0, 1], angle 2 pi u2 with u2 in [0, 1). The hardware approximations of ln,
+// of the reciprocal square root and of sin/cos (absolute error ~2^-21 on
+// [-pi, pi]) are used; the angle is shifted to pi (2 u2 - 1) in [-pi, pi),
+// which negates sine and cosine.
 __device__ __forceinline__ float step_uniform(uint32_t w0, uint32_t w1, uint32_t w2) {
   const uint32_t t = (w0 & 0xffu) | ((w1 & 0xffu) << 8) | ((w2 & 0xffu) << 16);
   return (float)t * 5.9604644775390625e-8f;  // 2^-24
 }
 
 __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& za, float& zb) {
-  const float rho = sqrtf(-2.f * __logf(u01_oc(w1)));
+  const float tt = -2.f * __logf(u01_oc(w1));
+  const float rho = tt > 0.f ? tt * rsqrtf(tt) : 0.f;  // sqrt(tt) from the reciprocal square root
   float sn, cs;
   __sincosf(3.14159265358979f * fmaf(2.f, u01_co(w2), -1.f), &sn, &cs);
   za = -rho * cs;
@@ -115,6 +117,30 @@ __device__ __forceinline__ void chord_box(const float* __restrict__ A32, int n, 
   }
 }
 
+// chord_box with the joint-box bounds held in registers (bhi[j] = b of row j,
+// blo[j] = b of row n + j): the same arithmetic, without reloading the
+// bounds at every walk step
+template <int NDOF>
+__device__ __forceinline__ void chord_box_r(int n, const float (&bhi)[NDOF], const float (&blo)[NDOF],
+                                            const float (&x)[NDOF], const float (&d)[NDOF], float& t_lo,
+                                            float& t_hi) {
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    if (j < n) {
+      const float q1 = __fdividef(bhi[j] - x[j], d[j]);
+      const float q2 = __fdividef(blo[j] + x[j], -d[j]);
+      if (d[j] > 0.f) {
+        t_hi = fminf(t_hi, q1);
+        t_lo = fmaxf(t_lo, q2);
+      }
+      if (d[j] < 0.f) {
+        t_lo = fmaxf(t_lo, q1);
+        t_hi = fminf(t_hi, q2);
+      }
+    }
+  }
+}
+
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
@@ -127,6 +153,14 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
   const float u0 = u01_co(r0.x);
 #pragma unroll
   for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
+  // the joint-box bounds, loaded once for all steps
+  constexpr int RSB = hnr_row_stride<NDOF>();
+  float bhi[NDOF], blo[NDOF];
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    bhi[j] = (box_rows && j < n) ? A32[j * RSB + NDOF] : 0.f;
+    blo[j] = (box_rows && j < n) ? A32[(n + j) * RSB + NDOF] : 0.f;
+  }
   for (int s = 0; s < n_mix; ++s) {
     uint32_t w[4 * WMAX];
 #pragma unroll
@@ -158,7 +192,7 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
-    if (box_rows) chord_box<NDOF>(A32, n, x, d, t_lo, t_hi);
+    if (box_rows) chord_box_r<NDOF>(n, bhi, blo, x, d, t_lo, t_hi);
     chord_rows<NDOF>(A32, box_rows, m, 1, x, d, t_lo, t_hi);
     t_hi = fmaxf(t_hi, 0.f);
     t_lo = fminf(t_lo, 0.f);
