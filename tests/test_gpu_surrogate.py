@@ -88,6 +88,31 @@ def test_surrogate_predict_matches_oracle(ezo, N):
     assert np.abs(y - y_ref).max() <= 1e-2 * max(1.0, np.abs(y_ref).max())
 
 
+def test_surrogate_predict_rows_do_not_depend_on_the_batch(ezo):
+    """A row's prediction is the same bits whatever batch it is in: alone,
+    in a ragged tile, or deep in a batch where each block runs several tiles
+    (the same configuration placed at row 0, 130 and 39,000)."""
+    rd, _ = _scene()
+    sur = ezo.Surrogate(ezo.Robot(rd), seed=8)
+    rng = np.random.default_rng(3)
+    big = rng.uniform(rd.q_lo, rd.q_hi, size=(40037, 7)).astype(np.float32)
+    probe = big[:5].copy()
+    big[130:135] = probe
+    big[39000:39005] = probe
+
+    def run(q):
+        out = torch.empty(q.shape[0], device="cuda")
+        sur.predict(torch.from_numpy(q.T.copy()).cuda(), out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    alone = run(probe)
+    y = run(big)
+    np.testing.assert_array_equal(y[:5], alone)
+    np.testing.assert_array_equal(y[130:135], alone)
+    np.testing.assert_array_equal(y[39000:39005], alone)
+
+
 def test_surrogate_training_learns_signed_distance(ezo):
     rd, env_np = _scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
