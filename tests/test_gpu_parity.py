@@ -302,6 +302,55 @@ def test_round_replay_dh7(ezo):
     assert rounds >= 2
 
 
+# ------------------------------------------ longer chains (16-joint kernels) --
+def chain10_robot():
+    """A 10-joint DH chain (a = 0.15 m, alternating twists, two spheres of
+    4 cm per link, self pairs between links at least three apart): chains of
+    more than 7 joints run the kernels compiled for up to 16 joints."""
+    n = 10
+    a = np.full(n, 0.15)
+    alpha = np.array([np.pi / 2, -np.pi / 2] * 5)
+    d = np.zeros(n)
+    d[0] = 0.2
+    frames, xyz, rad, link = [], [], [], []
+    for k in range(1, n + 1):
+        for f in (0.25, 0.75):
+            frames.append(k)
+            xyz.append((-(1 - f) * a[k - 1], 0.0, 0.0))
+            rad.append(0.04)
+            link.append(k)
+    link = np.asarray(link, dtype=np.int32)
+    pairs = [(i, j) for i in range(1, n + 1) for j in range(i + 3, n + 1)]
+    return wl.Robot(name="chain10", a=a, alpha=alpha, d=d, theta_off=np.zeros(n), q_lo=np.full(n, -2.5),
+                    q_hi=np.full(n, 2.5), sphere_frame=np.asarray(frames, dtype=np.int32),
+                    sphere_xyz=np.asarray(xyz), sphere_r=np.asarray(rad), sphere_link=link,
+                    self_pairs=wl._pairs_between_links(link, pairs))
+
+
+CHAIN10_V1 = np.array([0.8861, 0.0227, 0.9525, -0.8383, 0.2147, -0.247, 0.6038, -0.6509, 0.7433, 0.0879])
+CHAIN10_V2 = np.array([1.1274, 0.0089, 0.9108, -0.665, 0.5052, -0.3252, 0.8852, -0.3935, 0.5499, 0.1532])
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+def test_chain10_labels_match_oracle(ezo, lanes):
+    rd, env_np = chain10_robot(), wl.box_obstacles(5, 32)
+    q32 = wl.uniform_configs(17, rd, 3001).astype(np.float32)
+    got = gpu_labels(ezo, ezo.Robot(rd), ezo.Env(env_np), q32, lanes)
+    ref = assert_labels_match(rd, env_np, q32, got)
+    assert 0 < ref.sum() < q32.shape[0]
+
+
+def test_round_replay_chain10(ezo):
+    """Rounds of a 10-joint chain replayed step by step against the oracle
+    (walks, labels, test, candidates, bisection, planes)."""
+    rd, env_np = chain10_robot(), wl.box_obstacles(5, 32)
+    assert orc.signed_distance(rd, env_np, CHAIN10_V1[None, :] + np.linspace(0, 1, 200)[:, None]
+                               * (CHAIN10_V2 - CHAIN10_V1)[None, :]).min() > 0.1
+    rounds, _ = _replay_rounds(ezo, rd, env_np, CHAIN10_V1, CHAIN10_V2,
+                               dict(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, seed=3), max_rounds=3)
+    assert rounds >= 2
+
+
 # ------------------------------------------------------- Forest (Sec. V) --
 FOREST_PRM = dict(eps=0.01, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, step_back_max=0.01)
 
