@@ -240,6 +240,31 @@ def dh7_robot(r_base: float = 0.08, r_tip: float = 0.04) -> Robot:
     )
 
 
+def chain_robot(n: int = 10, a: float = 0.15, r: float = 0.04) -> Robot:
+    """An n-joint DH chain for chains longer than the 7-DOF arm: link length a,
+    twists alternating +-pi/2, a base offset d_1 = 0.2 m, joint limits +-2.5
+    rad, two spheres of radius r per link at a quarter and three quarters of
+    its length (attached to the link's distal frame), and self pairs between
+    links at least three apart."""
+    a_ = np.full(n, a)
+    alpha = np.array([np.pi / 2 if i % 2 == 0 else -np.pi / 2 for i in range(n)])
+    d = np.zeros(n)
+    d[0] = 0.2
+    frames, xyz, rad, link = [], [], [], []
+    for k in range(1, n + 1):
+        for f in (0.25, 0.75):
+            frames.append(k)
+            xyz.append((-(1 - f) * a, 0.0, 0.0))
+            rad.append(r)
+            link.append(k)
+    link = np.asarray(link, dtype=np.int32)
+    pairs = [(i, j) for i in range(1, n + 1) for j in range(i + 3, n + 1)]
+    return Robot(name=f"chain{n}", a=a_, alpha=alpha, d=d, theta_off=np.zeros(n), q_lo=np.full(n, -2.5),
+                 q_hi=np.full(n, 2.5), sphere_frame=np.asarray(frames, dtype=np.int32),
+                 sphere_xyz=np.asarray(xyz, dtype=np.float64), sphere_r=np.asarray(rad, dtype=np.float64),
+                 sphere_link=link, self_pairs=_pairs_between_links(link, pairs))
+
+
 def point2_robot(side: float = 10.0) -> Robot:
     """A point moving in a square of side ``side`` (the Forest benchmark of
     Sec. V): two prismatic joints, the first along the base z axis

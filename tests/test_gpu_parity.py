@@ -304,27 +304,7 @@ def test_round_replay_dh7(ezo):
 
 # ------------------------------------------ longer chains (16-joint kernels) --
 def chain10_robot():
-    """A 10-joint DH chain (a = 0.15 m, alternating twists, two spheres of
-    4 cm per link, self pairs between links at least three apart): chains of
-    more than 7 joints run the kernels compiled for up to 16 joints."""
-    n = 10
-    a = np.full(n, 0.15)
-    alpha = np.array([np.pi / 2, -np.pi / 2] * 5)
-    d = np.zeros(n)
-    d[0] = 0.2
-    frames, xyz, rad, link = [], [], [], []
-    for k in range(1, n + 1):
-        for f in (0.25, 0.75):
-            frames.append(k)
-            xyz.append((-(1 - f) * a[k - 1], 0.0, 0.0))
-            rad.append(0.04)
-            link.append(k)
-    link = np.asarray(link, dtype=np.int32)
-    pairs = [(i, j) for i in range(1, n + 1) for j in range(i + 3, n + 1)]
-    return wl.Robot(name="chain10", a=a, alpha=alpha, d=d, theta_off=np.zeros(n), q_lo=np.full(n, -2.5),
-                    q_hi=np.full(n, 2.5), sphere_frame=np.asarray(frames, dtype=np.int32),
-                    sphere_xyz=np.asarray(xyz), sphere_r=np.asarray(rad), sphere_link=link,
-                    self_pairs=wl._pairs_between_links(link, pairs))
+    return wl.chain_robot(10)
 
 
 CHAIN10_V1 = np.array([0.8861, 0.0227, 0.9525, -0.8383, 0.2147, -0.247, 0.6038, -0.6509, 0.7433, 0.0879])

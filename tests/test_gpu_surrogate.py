@@ -88,6 +88,25 @@ def test_surrogate_predict_matches_oracle(ezo, N):
     assert np.abs(y - y_ref).max() <= 1e-2 * max(1.0, np.abs(y_ref).max())
 
 
+@pytest.mark.parametrize("which", ["planar3", "chain10"])
+def test_surrogate_predict_other_chain_lengths(ezo, which):
+    """Feature staging for 3 joints (6 features, one 16-byte chunk) and for
+    10 joints (20 features over three chunks, written by all four column
+    groups) against the FP64 oracle."""
+    if which == "planar3":
+        rd = wl.planar3_robot()
+    else:
+        rd = wl.chain_robot(10)
+    sur = ezo.Surrogate(ezo.Robot(rd), seed=9)
+    q = wl.uniform_configs(23, rd, 2051).astype(np.float32)
+    out = torch.empty(q.shape[0], device="cuda")
+    sur.predict(torch.from_numpy(q.T.copy()).cuda(), out)
+    torch.cuda.synchronize()
+    y_ref, _ = so.forward(gpu_weights_as_used(sur.params()), bf16_round(so.features(q.astype(np.float64))))
+    y = out.cpu().numpy()
+    assert np.abs(y - y_ref).max() <= 1e-2 * max(1.0, np.abs(y_ref).max())
+
+
 def test_surrogate_predict_rows_do_not_depend_on_the_batch(ezo):
     """A row's prediction is the same bits whatever batch it is in: alone,
     in a ragged tile, or deep in a batch where each block runs several tiles
