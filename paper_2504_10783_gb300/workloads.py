@@ -243,9 +243,9 @@ def dh7_robot(r_base: float = 0.08, r_tip: float = 0.04) -> Robot:
 def chain_robot(n: int = 10, a: float = 0.15, r: float = 0.04) -> Robot:
     """An n-joint DH chain for chains longer than the 7-DOF arm: link length a,
     twists alternating +-pi/2, a base offset d_1 = 0.2 m, joint limits +-2.5
-    rad, two spheres of radius r per link at a quarter and three quarters of
-    its length (attached to the link's distal frame), and self pairs between
-    links at least three apart."""
+    rad, two spheres of radius r per link on its distal frame k at
+    o_k - (1 - f) a x_k, f = 1/4 and 3/4 (along the a part of the link), and
+    self pairs between links at least three apart."""
     a_ = np.full(n, a)
     alpha = np.array([np.pi / 2 if i % 2 == 0 else -np.pi / 2 for i in range(n)])
     d = np.zeros(n)

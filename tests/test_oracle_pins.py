@@ -99,8 +99,8 @@ def _mixed_robot():
                     joint_type=np.array([0, 1, 0, 1], dtype=np.int32))
 
 
-@pytest.mark.parametrize("robot", [wl.dh7_robot(), wl.planar3_robot(), _mixed_robot(), wl.point2_robot()],
-                         ids=lambda r: r.name)
+@pytest.mark.parametrize("robot", [wl.dh7_robot(), wl.planar3_robot(), _mixed_robot(), wl.point2_robot(),
+                                   wl.chain_robot(10)], ids=lambda r: r.name)
 def test_dh_frames_match_elementary_products(robot):
     q = wl.uniform_configs(3, robot, 20)
     R, o = orc.dh_frames(robot, q)
@@ -129,6 +129,28 @@ def test_planar_sphere_centres_sum_of_angles():
                 np.testing.assert_allclose(c[k, s, :2], p, atol=1e-12)
                 assert abs(c[k, s, 2]) < 1e-15
                 s += 1
+
+
+def test_chain_robot_layout():
+    """The n-joint chain: two spheres per link on its distal frame k at
+    o_k - (1 - f) a x_k (f = 1/4, 3/4), which for the links without a d
+    offset (k >= 2) lies between the origins of frames k - 1 and k, and self
+    pairs between links at least three apart (4 sphere pairs per link
+    pair)."""
+    n = 10
+    r = wl.chain_robot(n)
+    assert r.sphere_frame.tolist() == [k for k in range(1, n + 1) for _ in range(2)]
+    link_pairs = sum(max(0, n - (i + 2)) for i in range(1, n + 1))
+    assert r.self_pairs.shape == (4 * link_pairs, 2) == (112, 2)
+    assert np.all(np.abs(r.sphere_link[r.self_pairs[:, 0]] - r.sphere_link[r.self_pairs[:, 1]]) >= 3)
+    q = wl.uniform_configs(5, r, 10)
+    R, o = orc.dh_frames(r, q)
+    c = orc.sphere_centres(r, q)
+    for k in range(1, n + 1):
+        for j, f in ((2 * (k - 1), 0.25), (2 * (k - 1) + 1, 0.75)):
+            np.testing.assert_allclose(c[:, j], o[:, k] - (1 - f) * 0.15 * R[:, k][:, :, 0], atol=1e-12)
+            if k >= 2:
+                np.testing.assert_allclose(c[:, j], o[:, k - 1] + f * (o[:, k] - o[:, k - 1]), atol=1e-12)
 
 
 def test_dh7_sphere_layout():
