@@ -458,6 +458,28 @@ def test_eizo_planar_contains_segment_and_is_certified():
     assert orc.in_collision(r, env, x).mean() <= prm.eps
 
 
+def test_eizo_planar_collision_fraction_on_a_dense_grid():
+    """The planar polytope's collision fraction by brute force: the centres
+    of a 96^3 grid over the joint box that lie in P, checked one by one. It
+    is within eps, and within 0.02 of the rejection-sampling estimate."""
+    s = load_scene()["planar3"]
+    r = wl.planar3_robot()
+    env = wl.Env("p", np.array(s["obstacles"]))
+    v1, v2 = np.array(s["v1"]), np.array(s["v2"])
+    A0, b0 = orc.joint_box(r)
+    prm = orc.Params(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, seed=1)
+    res = orc.eizo(r, env, v1, v2, A0, b0, prm)
+    g = 96
+    axes = [np.linspace(lo, hi, g, endpoint=False) + (hi - lo) / (2 * g) for lo, hi in zip(r.q_lo, r.q_hi)]
+    X = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    X = X[np.all(X @ res.A.T <= res.b, axis=1)]
+    assert X.shape[0] > 10000
+    grid = orc.in_collision(r, env, X).mean()
+    mc = orc.in_collision(r, env, _uniform_in_polytope_by_rejection(r, res.A, res.b, 20000, 5)).mean()
+    assert grid <= prm.eps
+    assert abs(grid - mc) <= 0.02, (grid, mc)
+
+
 def test_eizo_certificate_holds_over_seeds():
     """The guarantee of Sec. III-A: P[collision fraction > eps] <= delta.
     Over 24 seeds at eps = 0.1, delta = 0.05 at most a few may exceed eps."""
