@@ -162,6 +162,27 @@ ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const
 ezo_status ezo_signed_distance(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
                                int64_t ldq, float* sd_dev, void* cuda_stream);
 
+/* Forward kinematics of the collision checker against FP64 (Sec. II, the
+ * robot's kinematic chain; Sec. IV-D, the checker that places the collision
+ * spheres). The checker computes the sphere centres in FP32 from the FP32
+ * configuration and FP32 copies of the chain's constants; the reference is
+ * the same chain in FP64 from the FP64 constants given to ezo_robot_create,
+ * on the same configuration widened to FP64.
+ * ezo_sphere_centres writes the centres of the N configurations q_dev (n x N,
+ * stride ldq) to out_dev (device FP64, 3 * n_spheres * N values): coordinate
+ * c of sphere s of configuration i at out_dev[(3 s + c) * N + i], spheres in
+ * the order of their frames (stable in the caller's order within a frame);
+ * fp64 = 0 gives the checker's FP32 centres, fp64 = 1 the FP64 ones.
+ * ezo_fk_error writes err_dev[i] (device FP32, N values) = the largest
+ * distance in metres between a sphere's FP32 and FP64 centre for
+ * configuration i. Box geometries are not included. Stream-ordered.
+ * Errors: EZO_ERR_INVALID_ARG (null handle or buffer, N < 0, ldq < N, fp64
+ * not 0 or 1), EZO_ERR_CUDA. */
+ezo_status ezo_sphere_centres(const ezo_robot* robot, const float* q_dev, int64_t N, int64_t ldq, int32_t fp64,
+                              double* out_dev, void* cuda_stream);
+ezo_status ezo_fk_error(const ezo_robot* robot, const float* q_dev, int64_t N, int64_t ldq, float* err_dev,
+                        void* cuda_stream);
+
 /* ------------------------------------------------------------- hit-and-run --
  * UniformSample of Algorithm 1 (Sec. IV-B, IV-D): N independent hit-and-run
  * walks of n_mix steps inside P = {x : A x <= b}, one walk per output
@@ -269,11 +290,13 @@ ezo_status ezo_batch_sync(ezo_batch* batch, void* cuda_stream);
  * s_cap), 2 candidate sample indices (int32 N_p), 3 c* (FP64, n x N_p
  * dimension-major), 4 distance to L of c* (FP64 N_p), 5 bisection decisions
  * (uint32 N_p, bit s = midpoint s in collision), 6 round state (int32[12]:
- * k, status, m, |S|, M, count, n_cand, planes, rounds, n_placed, N_p, env),
+ * k, status, m, |S|, M, count, n_cand, planes, rounds, n_placed, N_p, env,
+ * and s_cap, the segment's sample capacity and the stride of its samples,
+ * as a 13th value when `bytes` holds it),
  * 7 placed candidate indices of the last round (int32 n_f), 8 step backs of
  * the last round (FP64 n_f), 9 work counters int64[3] {exact checks at
  * samples, exact checks at bisection midpoints, algorithmic FP32 flops of the
- * hit-and-run walks: per walk step m (4n + 2) + 14n}, 11 surrogate evaluations (int64), 10 the batch's round summary (int32[4]: active
+ * hit-and-run walks: per walk step 2mn + 5m + 6n}, 11 surrogate evaluations (int64), 10 the batch's round summary (int32[4]: active
  * segments, rounds run since the last reset, sample tiles, bisection tiles;
  * `seg` is ignored). `bytes` is the size of `dst`. */
 ezo_status ezo_batch_read(const ezo_batch* batch, int32_t seg, int32_t what, void* dst, int64_t bytes);
@@ -350,8 +373,8 @@ ezo_status ezo_batch_reinflate(ezo_batch* batch, const uint8_t* which, int32_t m
  * host application that fixes the library's device memory at start-up.
  * Inflates one segment v1..v2 (host FP64, n values each) from the robot's
  * joint-limit box with the same kernels, parameters and Philox stream
- * (stream_id) as a one-segment ezo_batch_run in HOST_LOOP mode, so the result
- * equals that call's. All working memory comes from one file-scope device
+ * (stream_id) as a one-segment ezo_batch_run in HOST_LOOP mode, so the
+ * polytope, status, rounds and check count equal that call's bit for bit. All working memory comes from one file-scope device
  * array of EZO_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
  * until the process exits; the call itself makes no cudaMalloc, cudaFree or
  * other allocating call. Outputs: A_out (host, at least
@@ -360,12 +383,20 @@ ezo_status ezo_batch_reinflate(ezo_batch* batch, const uint8_t* which, int32_t m
  * rounds_out and checks_out may be NULL. The robot and env handles must have
  * been created beforehand (their creation allocates).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture. The array is shared by every call and keeps the last
- * call's contents; each call re-initialises what it reads. Calls that overlap
- * on the GPU (other streams or host threads) race on the array: serialise
- * them. Blocks until the result is on the host.
- * Errors: EZO_ERR_INVALID_ARG; EZO_ERR_CAPACITY when the segment needs more
+ * (cudaGetSymbolAddress) for that device. With CUDA's lazy module loading
+ * that first call (like the first launch of each kernel) also loads the
+ * library's device code and with it the array, which can allocate and
+ * synchronise: make one call per device at start-up, outside the section
+ * that must not allocate, and before any stream capture. Later calls make no
+ * allocation. The array is shared by every call and keeps the last call's
+ * contents; each call re-initialises what it reads. Calls that overlap on
+ * the GPU (other streams or host threads) race on the array: serialise them.
+ * A call that fails after queueing work waits for its stream before it
+ * returns, so the array is idle afterwards. Blocks until the result is on the
+ * host.
+ * Errors: EZO_ERR_INVALID_ARG (also when the robot's spheres and the
+ * obstacles do not fit the collision kernels' shared memory, checked before
+ * anything runs); EZO_ERR_CAPACITY when the segment needs more
  * working memory than the array holds (roughly n_p <= 16384 for n = 16) or
  * more than 2048 rows; EZO_ERR_CUDA. */
 #define EZO_NOALLOC_SCRATCH_BYTES (6u * 1024u * 1024u)

@@ -77,6 +77,7 @@ struct EventPool {
 struct ezo_robot {
   RobotDev host{};
   RobotDev* d_robot = nullptr;
+  RobotFK64* d_fk64 = nullptr;  // FP64 chain for the kinematics error
   ushort2* d_pairs = nullptr;
   float* d_rr = nullptr;
   ushort2 *d_sbp = nullptr, *d_bbp = nullptr;  // self pairs with a box
@@ -267,10 +268,30 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
   // algorithmic FP32 flops: per joint ~45 (rotation and origin update), per
   // sphere 18 (centre) + 7 (half squared norm), 8 per pair
   r->fk_flops = 45.0 * n + 25.0 * n_spheres;
+  RobotFK64 h64{};
+  h64.n = n;
+  h64.n_spheres = n_spheres;
+  for (int j = 0; j < n; ++j) {
+    h64.ca[j] = std::cos(alpha[j]);
+    h64.sa[j] = std::sin(alpha[j]);
+    h64.a[j] = a[j];
+    h64.d[j] = d[j];
+    h64.toff[j] = theta_off ? theta_off[j] : 0.0;
+    h64.kth[j] = h.kth[j];
+    h64.kd[j] = h.kd[j];
+  }
+  for (int f = 0; f < EZO_MAX_DOF + 2; ++f) h64.frame_first[f] = h.frame_first[f];
+  for (int s = 0; s < n_spheres; ++s) {
+    const int o = order[s];
+    h64.sx[s] = sphere_xyz[3 * o];
+    h64.sy[s] = sphere_xyz[3 * o + 1];
+    h64.sz[s] = sphere_xyz[3 * o + 2];
+  }
   cudaError_t e;
   if ((e = cudaMalloc(&r->d_pairs, pairs.size() * sizeof(ushort2))) != cudaSuccess ||
       (e = cudaMalloc(&r->d_rr, rr.size() * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&r->d_robot, sizeof(RobotDev))) != cudaSuccess) {
+      (e = cudaMalloc(&r->d_robot, sizeof(RobotDev))) != cudaSuccess ||
+      (e = cudaMalloc(&r->d_fk64, sizeof(RobotFK64))) != cudaSuccess) {
     ezo_robot_free(r);
     return cuda_fail(e, "ezo_robot_create: cudaMalloc");
   }
@@ -279,7 +300,8 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
   if ((e = cudaMemcpy(r->d_pairs, pairs.data(), pairs.size() * sizeof(ushort2), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemcpy(r->d_rr, rr.data(), rr.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(r->d_robot, &h, sizeof(RobotDev), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      (e = cudaMemcpy(r->d_robot, &h, sizeof(RobotDev), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(r->d_fk64, &h64, sizeof(RobotFK64), cudaMemcpyHostToDevice)) != cudaSuccess) {
     ezo_robot_free(r);
     return cuda_fail(e, "ezo_robot_create: cudaMemcpy");
   }
@@ -295,6 +317,7 @@ void ezo_robot_free(ezo_robot* r) {
   cudaFree(r->d_sbp);
   cudaFree(r->d_bbp);
   cudaFree(r->d_robot);
+  cudaFree(r->d_fk64);
   delete r;
 }
 
@@ -463,6 +486,28 @@ ezo_status ezo_signed_distance(const ezo_robot* robot, const ezo_env* env, const
     return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: sphere geometries only (the robot or env has boxes)");
   cudaError_t e = launch_sd_flat(robot->d_robot, robot->n, robot->nsp_pad, env->dev(), q_dev, ldq, N, sd_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "ezo_signed_distance");
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_sphere_centres(const ezo_robot* robot, const float* q_dev, int64_t N, int64_t ldq, int32_t fp64,
+                              double* out_dev, void* cuda_stream) {
+  if (!robot || (N > 0 && (!q_dev || !out_dev)) || N < 0 || ldq < N || (fp64 != 0 && fp64 != 1))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_sphere_centres: bad argument");
+  const cudaError_t e = launch_fk_centres(robot->d_robot, robot->d_fk64, robot->n, robot->nsp_pad, q_dev, ldq, N,
+                                          fp64, out_dev, nullptr, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ezo_sphere_centres");
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_fk_error(const ezo_robot* robot, const float* q_dev, int64_t N, int64_t ldq, float* err_dev,
+                        void* cuda_stream) {
+  if (!robot || (N > 0 && (!q_dev || !err_dev)) || N < 0 || ldq < N)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_fk_error: bad argument");
+  const cudaError_t e = launch_fk_centres(robot->d_robot, robot->d_fk64, robot->n, robot->nsp_pad, q_dev, ldq, N, 2,
+                                          nullptr, err_dev, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ezo_fk_error");
   g_err.clear();
   return EZO_OK;
 }
@@ -1292,9 +1337,9 @@ ezo_status ezo_batch_read(const ezo_batch* b, int32_t seg, int32_t what, void* d
     case 6: {
       if (bytes < (int64_t)(12 * sizeof(int32_t))) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
       int32_t* o = (int32_t*)dst;
-      const int32_t vals[12] = {s.k, s.status, s.m, s.n_samples, s.m_test, s.count,
-                                s.n_cand, s.planes, s.rounds, s.n_placed, s.n_p, s.env};
-      std::memcpy(o, vals, sizeof(vals));
+      const int32_t vals[13] = {s.k, s.status, s.m, s.n_samples, s.m_test, s.count, s.n_cand,
+                                s.planes, s.rounds, s.n_placed, s.n_p, s.env, s.s_cap};
+      std::memcpy(o, vals, bytes >= (int64_t)sizeof(vals) ? sizeof(vals) : 12 * sizeof(int32_t));
       return EZO_OK;
     }
     case 9: {

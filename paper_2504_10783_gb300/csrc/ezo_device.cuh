@@ -86,6 +86,17 @@ struct RobotDev {
   const ushort2* bb_pairs;  // (sorted box, sorted box)
 };
 
+// The chain and the spheres in FP64 as given at creation (spheres sorted as
+// in RobotDev), for the FP64 reference kinematics that the forward-kinematics
+// error of the FP32 checker is measured against.
+struct RobotFK64 {
+  int n, n_spheres;
+  double ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
+  double kth[EZO_MAX_DOF], kd[EZO_MAX_DOF];
+  int frame_first[EZO_MAX_DOF + 2];
+  double sx[EZO_MAX_SPHERES], sy[EZO_MAX_SPHERES], sz[EZO_MAX_SPHERES];
+};
+
 // The part of RobotDev a block keeps in shared memory.
 struct RobotSmem {
   float ca[EZO_MAX_DOF], sa[EZO_MAX_DOF], a[EZO_MAX_DOF], d[EZO_MAX_DOF], toff[EZO_MAX_DOF];
@@ -147,11 +158,25 @@ struct EnvDev {
   int pad;
 };
 
+// Shared-memory image of an obstacle set, in pairs of spheres (2p, 2p + 1):
+// obs_s[2p] = (x_2p, x_2p+1, y_2p, y_2p+1), obs_s[2p + 1] = (z_2p, z_2p+1,
+// R_2p, R_2p+1), and nhw_s[j] = -(|o_j|^2 - R_j^2)/2 in sphere order, so one
+// 128-bit load gives a coordinate of two obstacles as the float2 operand of a
+// packed FP32 FMA. n_obs_pad is a multiple of 8, so pairs never straddle the
+// padding. obs_at(j) reads sphere j back as (x, y, z, R).
 __device__ __forceinline__ void stage_env(float4* obs_s, float* nhw_s, const EnvDev& e) {
-  for (int i = threadIdx.x; i < e.n_obs_pad; i += blockDim.x) {
-    obs_s[i] = e.obs[i];
-    nhw_s[i] = e.nhw[i];
+  for (int p = threadIdx.x; p < e.n_obs_pad / 2; p += blockDim.x) {
+    const float4 a = e.obs[2 * p], b = e.obs[2 * p + 1];
+    obs_s[2 * p] = make_float4(a.x, b.x, a.y, b.y);
+    obs_s[2 * p + 1] = make_float4(a.z, b.z, a.w, b.w);
   }
+  for (int i = threadIdx.x; i < e.n_obs_pad; i += blockDim.x) nhw_s[i] = e.nhw[i];
+}
+
+__device__ __forceinline__ float4 obs_at(const float4* __restrict__ obs_s, int j) {
+  const float* A = reinterpret_cast<const float*>(obs_s + (j & ~1));
+  const int h = j & 1;
+  return make_float4(A[h], A[2 + h], A[4 + h], A[6 + h]);
 }
 
 __device__ __forceinline__ void stage_env_boxes(float4* ebox_s, const EnvDev& e) {
@@ -280,7 +305,7 @@ __device__ __forceinline__ bool box_pairs_hit(const RobotSmem& rs, const float4*
   }
   for (int p = lg; p < nb * n_obs && !hit; p += T) {  // robot boxes x obstacle spheres
     const int b = p / n_obs, o = p - b * n_obs;
-    const float4 ob = obs_s[o];
+    const float4 ob = obs_at(obs_s, o);
     hit = sphere_box_hit(ob, ob.w, bx.rbox_w + 4 * b);
   }
   for (int p = lg; p < nb * ne && !hit; p += T) {  // robot boxes x obstacle boxes
@@ -299,23 +324,16 @@ __device__ __forceinline__ bool box_pairs_hit(const RobotSmem& rs, const float4*
 }
 
 // -------------------------------------------------- FK + collision test --
-// One configuration evaluated by a group of T lanes of one warp (T in 1..8);
-// BOX adds the box geometries (robot boxes posed along the chain, pairs with
-// a box after the sphere pairs).
-// Lane lg of the group computes the centres of spheres s with s % T == lg
-// (every lane walks the chain), the group shares them through smem slot
-// `cen`, then lane lg sweeps obstacles j with j % T == lg and self pairs
-// p with p % T == lg. Returns the group-wide OR. Every lane of the warp must
-// call this together (invalid configurations are evaluated and discarded).
+// Forward kinematics of one configuration by a group of T lanes (T in
+// 1..8) of one warp, as the collision checker runs it: the group's lanes share
+// the joint sines and cosines, lane lg writes the centres of spheres s with
+// s % T == lg into the group's shared slot `cen` as (x, y, z, (|c|^2 - r^2)/2)
+// (padding spheres get an infinite last entry), and BOX poses the robot's
+// boxes. Ends with a warp barrier; every lane of the warp must call it.
 template <int NDOF, int T, bool BOX = false>
-__device__ __forceinline__ bool collide_group(const float* __restrict__ q, const RobotSmem& rs,
-                                              const float4* __restrict__ sph_s,
-                                              const float4* __restrict__ obs_s,
-                                              const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
-                                              const ushort2* __restrict__ self_pairs,
-                                              const float* __restrict__ self_rr, float E,
-                                              float4* __restrict__ cen, int lg, const BoxCtx& bx) {
-  // ---- forward kinematics: columns of R_f and origin o_f, frame by frame ----
+__device__ __forceinline__ void fk_group(const float* __restrict__ q, const RobotSmem& rs,
+                                         const float4* __restrict__ sph_s, float4* __restrict__ cen, int lg,
+                                         const BoxCtx& bx) {
   float c0x = 1.f, c0y = 0.f, c0z = 0.f;
   float c1x = 0.f, c1y = 1.f, c1z = 0.f;
   float c2x = 0.f, c2y = 0.f, c2z = 1.f;
@@ -390,61 +408,82 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
   }
   for (int s = rs.n_spheres + lg; s < rs.n_spheres_pad; s += T) cen[s] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
   __syncwarp();
+}
 
-  // ---- robot spheres vs obstacle spheres: two obstacles per step ----
+// One configuration evaluated by a group of T lanes of one warp (T in 1..8);
+// BOX adds the box geometries (robot boxes posed along the chain, pairs with
+// a box after the sphere pairs).
+// Lane lg of the group computes the centres of spheres s with s % T == lg
+// (every lane walks the chain), the group shares them through smem slot
+// `cen`, then lane lg sweeps the obstacle pairs p (obstacles 2p, 2p + 1) with
+// p % T == lg and self pairs p with p % T == lg. Returns the group-wide OR.
+// Every lane of the warp must call this together (invalid configurations are
+// evaluated and discarded).
+template <int NDOF, int T, bool BOX = false>
+__device__ __forceinline__ bool collide_group(const float* __restrict__ q, const RobotSmem& rs,
+                                              const float4* __restrict__ sph_s,
+                                              const float4* __restrict__ obs_s,
+                                              const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
+                                              const ushort2* __restrict__ self_pairs,
+                                              const float* __restrict__ self_rr, float E,
+                                              float4* __restrict__ cen, int lg, const BoxCtx& bx) {
+  fk_group<NDOF, T, BOX>(q, rs, sph_s, cen, lg, bx);
+
+  // ---- robot spheres vs obstacle spheres: one pair of obstacles per step,
+  //      both evaluated by packed FP32 FMAs (each half is an fma.rn of its
+  //      own, so t_ij is bit for bit the scalar chain's) ----
   bool hit = false;
+  const int n_pairs = n_obs_pad >> 1;
+  const float2* __restrict__ nhw2 = reinterpret_cast<const float2*>(nhw_s);
   for (int s0 = 0; s0 < rs.n_spheres_pad; s0 += EZO_CH) {
-    float4 cc[EZO_CH];
-    float rr[EZO_CH], m[EZO_CH];
+    float2 cx[EZO_CH], cy[EZO_CH], cz[EZO_CH], cr[EZO_CH];
+    float m[EZO_CH];
 #pragma unroll
     for (int k = 0; k < EZO_CH; ++k) {
-      cc[k] = cen[s0 + k];
-      rr[k] = sph_s[s0 + k].w;
+      const float4 c = cen[s0 + k];
+      const float r = sph_s[s0 + k].w;
+      cx[k] = make_float2(c.x, c.x);
+      cy[k] = make_float2(c.y, c.y);
+      cz[k] = make_float2(c.z, c.z);
+      cr[k] = make_float2(r, r);
       m[k] = -3.0e38f;
     }
-    int j = lg;
 #pragma unroll 2
-    for (; j + T < n_obs_pad; j += 2 * T) {
-      const float4 o1 = obs_s[j], o2 = obs_s[j + T];
-      const float w1 = nhw_s[j], w2 = nhw_s[j + T];
+    for (int p = lg; p < n_pairs; p += T) {
+      const float4 xy = obs_s[2 * p], zr = obs_s[2 * p + 1];
+      const float2 w = nhw2[p];
+      const float2 ox = make_float2(xy.x, xy.y), oy = make_float2(xy.z, xy.w);
+      const float2 oz = make_float2(zr.x, zr.y), oR = make_float2(zr.z, zr.w);
 #pragma unroll
       for (int k = 0; k < EZO_CH; ++k) {
-        float t1 = fmaf(rr[k], o1.w, w1);
-        float t2 = fmaf(rr[k], o2.w, w2);
-        t1 = fmaf(cc[k].z, o1.z, t1);
-        t2 = fmaf(cc[k].z, o2.z, t2);
-        t1 = fmaf(cc[k].y, o1.y, t1);
-        t2 = fmaf(cc[k].y, o2.y, t2);
-        t1 = fmaf(cc[k].x, o1.x, t1);
-        t2 = fmaf(cc[k].x, o2.x, t2);
-        m[k] = fmax3f(m[k], t1, t2);
-      }
-    }
-    if (j < n_obs_pad) {
-      const float4 o = obs_s[j];
-      const float w = nhw_s[j];
-#pragma unroll
-      for (int k = 0; k < EZO_CH; ++k) {
-        float t = fmaf(rr[k], o.w, w);
-        t = fmaf(cc[k].z, o.z, t);
-        t = fmaf(cc[k].y, o.y, t);
-        t = fmaf(cc[k].x, o.x, t);
-        m[k] = fmaxf(m[k], t);
+        float2 t = __ffma2_rn(cr[k], oR, w);
+        t = __ffma2_rn(cz[k], oz, t);
+        t = __ffma2_rn(cy[k], oy, t);
+        t = __ffma2_rn(cx[k], ox, t);
+        m[k] = fmax3f(m[k], t.x, t.y);
       }
     }
 #pragma unroll
     for (int k = 0; k < EZO_CH; ++k) {
-      const float diff = m[k] - cc[k].w;
+      const float4 c = cen[s0 + k];
+      const float diff = m[k] - c.w;
       if (diff > E) {
         hit = true;
       } else if (diff >= -E) {
-        // inside the rounding band of the fast form: decide with differences
-        for (int jj = lg; jj < n_obs; jj += T) {
-          const float4 o = obs_s[jj];
-          const float dx = cc[k].x - o.x, dy = cc[k].y - o.y, dz = cc[k].z - o.z;
-          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float sr = rr[k] + o.w;
-          if (d2 < sr * sr) hit = true;
+        // inside the rounding band of the fast form: decide with differences,
+        // over the same obstacles as this lane's maximum (its pairs)
+        const float r = cr[k].x;
+        for (int jj = 2 * lg; jj < n_obs; jj += 2 * T) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (jj + h < n_obs) {
+              const float4 o = obs_at(obs_s, jj + h);
+              const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
+              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float sr = r + o.w;
+              if (d2 < sr * sr) hit = true;
+            }
+          }
         }
       }
     }
@@ -564,7 +603,7 @@ __device__ float signed_distance_one(const float* __restrict__ q, const RobotSme
   for (int s = 0; s < rs.n_spheres; ++s) {
     const float4 c = cen[s];
     for (int j = 0; j < n_obs; ++j) {
-      const float4 o = obs_s[j];
+      const float4 o = obs_at(obs_s, j);
       const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const float lim = c.w + o.w + best;

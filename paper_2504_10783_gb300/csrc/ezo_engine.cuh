@@ -160,6 +160,8 @@ cudaError_t launch_check_path_box(const RobotDev* robot, int n, int nsp_pad, int
 cudaError_t launch_round_check_box(const BatchView& v, int T, int grid, cudaStream_t s);
 cudaError_t launch_round_bisect_box(const BatchView& v, int T, int grid, cudaStream_t s);
 
+cudaError_t launch_fk_centres(const RobotDev* robot, const RobotFK64* r64, int n, int nsp_pad, const float* q,
+                              long long ldq, long long N, int mode, double* out_c, float* err, cudaStream_t s);
 size_t check_smem_bytes(int n_spheres_pad, int n_obs_pad, int threads, int T, int n_rbox = 0, int n_ebox = 0);
 
 }  // namespace ezo

@@ -48,10 +48,14 @@ __device__ __forceinline__ void round_begin_block(const BatchView& v) {
         if (S > st.s_cap) S = st.s_cap;  // capacity is sized for M at N_it; never hit
         st.m_test = M;
         st.n_samples = S;
-        // algorithmic FP32 work of this round's walks: per step and row two
-        // n-term dot products, a subtraction and a ratio; per step n Gaussians
-        // (Box-Muller, ~10 flops each), normalisation and the move (4n)
-        st.sample_flops += (long long)S * v.n_mix * ((long long)st.m * (4 * v.n + 2) + 14 * v.n);
+        // algorithmic FP32 work of this round's walks, per walk step
+        // 2mn + 5m + 6n: the rate a_r . d of every row (2n), the slack update
+        // s_r -= t q_r, the ratio and the two bound updates (5 per row), and
+        // the direction's normalisation and the move (6n). The Gaussians'
+        // transcendental functions and the random-number generator are not
+        // counted, nor the second dot product per row that this kernel uses
+        // instead of carrying the slack.
+        st.sample_flops += (long long)S * v.n_mix * (2ll * st.m * v.n + 5ll * st.m + 6ll * v.n);
         st.n_cand = 0;
         st.count = 0;
         st.n_placed = 0;
@@ -368,7 +372,7 @@ cudaError_t launch_round_close(const BatchView& v, cudaStream_t s) {
 cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int grid, cudaStream_t s) {
   cudaError_t err = cudaSuccess;
   EZO_DISPATCH_NDOF(v.n, {
-    const size_t smem = (size_t)v.m_cap * hnr_row_stride<ND>() * sizeof(float);
+    const size_t smem = hnr_smem_bytes<ND>(v.m_cap);
     auto kern = k_round_sample<ND>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;

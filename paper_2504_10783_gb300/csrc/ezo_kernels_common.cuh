@@ -48,47 +48,59 @@ __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& za, 
   zb = -rho * sn;
 }
 
-// Shared-memory record of one polytope row for the sampler: a_r (NDOF floats,
-// zero-padded) then b_r, rounded up to whole float4s.
+// Shared-memory image of a polytope for the sampler, two rows per record:
+// record P holds rows 2P and 2P + 1 interleaved, a_{2P,j} and a_{2P+1,j} at
+// floats 2j and 2j + 1 (j < NDOF, zero-padded), then b_{2P} and b_{2P+1}, the
+// record rounded up to whole float4s. One 64-bit load gives a coefficient of
+// two rows as the float2 operand of a packed FP32 FMA. A missing last row of
+// an odd count is a zero row (rate 0, so it bounds nothing).
 template <int NDOF>
-__host__ __device__ constexpr int hnr_row_stride() {
-  return (NDOF + 4) & ~3;
+__host__ __device__ constexpr int hnr_pair_stride() {
+  return (2 * NDOF + 5) & ~3;
 }
 
-// Chord bounds from polytope rows r0, r0 + step, .. < m: for row r the slack
-// b_r - a_r . x and the rate a_r . d give the crossing t = slack / rate,
-// which bounds the chord from above when the rate is positive and from below
-// when it is negative. Eight rows are processed per iteration so that their
-// dot-product chains overlap (measured against 2, 4, 12 and 16); each row's
-// arithmetic does not depend on how the rows are split between lanes, and
-// min/max do not depend on the order.
 template <int NDOF>
-__device__ __forceinline__ void chord_rows(const float* __restrict__ A32, int r0, int m, int step,
-                                           const float (&x)[NDOF], const float (&d)[NDOF], float& t_lo,
-                                           float& t_hi) {
-  constexpr int RS = hnr_row_stride<NDOF>();
-#pragma unroll 8
-  for (int r = r0; r < m; r += step) {
-    // row r of A and b[r] in one padded record: RS / 4 broadcast loads
-    const float4* row = reinterpret_cast<const float4*>(A32 + r * RS);
-    float av[RS];
-#pragma unroll
-    for (int qd = 0; qd < RS / 4; ++qd) {
-      const float4 v4 = row[qd];
-      av[4 * qd] = v4.x;
-      av[4 * qd + 1] = v4.y;
-      av[4 * qd + 2] = v4.z;
-      av[4 * qd + 3] = v4.w;
-    }
-    float ax = 0.f, ad = 0.f;
+__host__ __device__ constexpr size_t hnr_smem_bytes(int m) {
+  return (size_t)((m > 1 ? m : 1) + 1) / 2 * hnr_pair_stride<NDOF>() * sizeof(float);
+}
+
+// b of row r in the paired image
+template <int NDOF>
+__device__ __forceinline__ float hnr_row_b(const float* __restrict__ A32, int r) {
+  return A32[(r >> 1) * hnr_pair_stride<NDOF>() + 2 * NDOF + (r & 1)];
+}
+
+// Chord bounds from the row pairs P0, P0 + step, .. < P1: for row r the slack
+// b_r - a_r . x and the rate a_r . d give the crossing t = slack / rate, which
+// bounds the chord from above when the rate is positive and from below when
+// it is negative. Both rows of a pair advance together in packed FP32 FMAs
+// against x and d duplicated into both halves (xx, dd); each half is the
+// scalar chain fmaf(a_j, x_j, .) over j = 0 .. NDOF-1 from 0, so every row's
+// slack, rate and ratio are bit for bit those of a row taken alone, and
+// min/max do not depend on the order or on how the pairs are split between
+// lanes. Four pairs per iteration let the chains overlap.
+template <int NDOF>
+__device__ __forceinline__ void chord_pairs(const float* __restrict__ A32, int P0, int P1, int step,
+                                            const float2 (&xx)[NDOF], const float2 (&dd)[NDOF], float& t_lo,
+                                            float& t_hi) {
+  constexpr int PS = hnr_pair_stride<NDOF>();
+#pragma unroll 4
+  for (int P = P0; P < P1; P += step) {
+    const float2* rec = reinterpret_cast<const float2*>(A32 + P * PS);
+    float2 ax = make_float2(0.f, 0.f), ad = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) {
-      ax = fmaf(av[j], x[j], ax);
-      ad = fmaf(av[j], d[j], ad);
+      const float2 a = rec[j];
+      ax = __ffma2_rn(a, xx[j], ax);
+      ad = __ffma2_rn(a, dd[j], ad);
     }
-    const float q = __fdividef(av[NDOF] - ax, ad);
-    if (ad > 0.f) t_hi = fminf(t_hi, q);
-    if (ad < 0.f) t_lo = fmaxf(t_lo, q);
+    const float2 bb = rec[NDOF];
+    const float q0 = __fdividef(bb.x - ax.x, ad.x);
+    const float q1 = __fdividef(bb.y - ax.y, ad.y);
+    if (ad.x > 0.f) t_hi = fminf(t_hi, q0);
+    if (ad.x < 0.f) t_lo = fmaxf(t_lo, q0);
+    if (ad.y > 0.f) t_hi = fminf(t_hi, q1);
+    if (ad.y < 0.f) t_lo = fmaxf(t_lo, q1);
   }
 }
 
@@ -99,12 +111,11 @@ __device__ __forceinline__ void chord_rows(const float* __restrict__ A32, int r0
 template <int NDOF>
 __device__ __forceinline__ void chord_box(const float* __restrict__ A32, int n, const float (&x)[NDOF],
                                           const float (&d)[NDOF], float& t_lo, float& t_hi) {
-  constexpr int RS = hnr_row_stride<NDOF>();
 #pragma unroll
   for (int j = 0; j < NDOF; ++j) {
     if (j < n) {
-      const float q1 = __fdividef(A32[j * RS + NDOF] - x[j], d[j]);
-      const float q2 = __fdividef(A32[(n + j) * RS + NDOF] + x[j], -d[j]);
+      const float q1 = __fdividef(hnr_row_b<NDOF>(A32, j) - x[j], d[j]);
+      const float q2 = __fdividef(hnr_row_b<NDOF>(A32, n + j) + x[j], -d[j]);
       if (d[j] > 0.f) {
         t_hi = fminf(t_hi, q1);
         t_lo = fmaxf(t_lo, q2);
@@ -141,6 +152,18 @@ __device__ __forceinline__ void chord_box_r(int n, const float (&bhi)[NDOF], con
   }
 }
 
+// x and d in both halves of a float2, the operands chord_pairs multiplies
+// each row pair with
+template <int NDOF>
+__device__ __forceinline__ void dup_pairs(const float (&x)[NDOF], const float (&d)[NDOF], float2 (&xx)[NDOF],
+                                          float2 (&dd)[NDOF]) {
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    xx[j] = make_float2(x[j], x[j]);
+    dd[j] = make_float2(d[j], d[j]);
+  }
+}
+
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
@@ -154,12 +177,11 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 #pragma unroll
   for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
   // the joint-box bounds, loaded once for all steps
-  constexpr int RSB = hnr_row_stride<NDOF>();
   float bhi[NDOF], blo[NDOF];
 #pragma unroll
   for (int j = 0; j < NDOF; ++j) {
-    bhi[j] = (box_rows && j < n) ? A32[j * RSB + NDOF] : 0.f;
-    blo[j] = (box_rows && j < n) ? A32[(n + j) * RSB + NDOF] : 0.f;
+    bhi[j] = (box_rows && j < n) ? hnr_row_b<NDOF>(A32, j) : 0.f;
+    blo[j] = (box_rows && j < n) ? hnr_row_b<NDOF>(A32, n + j) : 0.f;
   }
   for (int s = 0; s < n_mix; ++s) {
     uint32_t w[4 * WMAX];
@@ -193,7 +215,9 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
     if (box_rows) chord_box_r<NDOF>(n, bhi, blo, x, d, t_lo, t_hi);
-    chord_rows<NDOF>(A32, box_rows, m, 1, x, d, t_lo, t_hi);
+    float2 xx[NDOF], dd[NDOF];
+    dup_pairs<NDOF>(x, d, xx, dd);
+    chord_pairs<NDOF>(A32, box_rows >> 1, (m + 1) >> 1, 1, xx, dd, t_lo, t_hi);
     t_hi = fmaxf(t_hi, 0.f);
     t_lo = fminf(t_lo, 0.f);
     if (ok && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
@@ -263,7 +287,9 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
     for (int j = 0; j < NDOF; ++j) d[j] *= inv;
     float t_lo = -INFINITY, t_hi = INFINITY;
     if (box_rows) chord_box<NDOF>(A32, n, x, d, t_lo, t_hi);  // every lane: cheap, and min/max repeat safely
-    chord_rows<NDOF>(A32, box_rows + lw, m, TS, x, d, t_lo, t_hi);
+    float2 xx[NDOF], dd[NDOF];
+    dup_pairs<NDOF>(x, d, xx, dd);
+    chord_pairs<NDOF>(A32, (box_rows >> 1) + lw, (m + 1) >> 1, TS, xx, dd, t_lo, t_hi);
 #pragma unroll
     for (int o = 1; o < TS; o <<= 1) {
       t_hi = fminf(t_hi, __shfl_xor_sync(0xffffffffu, t_hi, o, TS));
@@ -279,13 +305,23 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
   }
 }
 
+// The polytope {A x <= b} (FP64, m rows, row stride lda) as the sampler's
+// paired FP32 image (see hnr_pair_stride); an odd last row is paired with a
+// zero row.
 template <int NDOF>
 __device__ __forceinline__ void stage_polytope(float* A32, const double* __restrict__ A,
                                                const double* __restrict__ b, int m, int lda, int n) {
-  constexpr int RS = hnr_row_stride<NDOF>();
-  for (int i = threadIdx.x; i < m * RS; i += blockDim.x) {
-    const int r = i / RS, c = i - r * RS;
-    A32[i] = (c < n) ? (float)A[(long long)r * lda + c] : (c == NDOF ? (float)b[r] : 0.f);
+  constexpr int PS = hnr_pair_stride<NDOF>();
+  const int np = (m + 1) >> 1;
+  for (int i = threadIdx.x; i < np * PS; i += blockDim.x) {
+    const int P = i / PS, c = i - P * PS;
+    const int r = 2 * P + (c & 1), j = c >> 1;
+    float v = 0.f;
+    if (r < m) {
+      if (j < n) v = (float)A[(long long)r * lda + j];
+      else if (j == NDOF) v = (float)b[r];
+    }
+    A32[i] = v;
   }
 }
 

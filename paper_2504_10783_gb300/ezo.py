@@ -112,6 +112,8 @@ def _sig(lib):
     f.ezo_probe_fp32_fma.argtypes = [_DP, _P]
     f.ezo_check_flops.argtypes = [_P, _P]
     f.ezo_check_flops.restype = C.c_double
+    f.ezo_sphere_centres.argtypes = [_P, _P, _I64, _I64, _I32, _P, _P]
+    f.ezo_fk_error.argtypes = [_P, _P, _I64, _I64, _P, _P]
     return lib
 
 
@@ -177,6 +179,9 @@ class Robot:
                                       _ip(k[9]), _ip(k[10]) if k[10] is not None else None, C.byref(h)))
         self.h = h
         self.n = r.n
+        self.n_spheres = r.n_spheres
+        # ezo_sphere_centres orders spheres by frame, stably
+        self.sphere_order = np.argsort(np.asarray(r.sphere_frame), kind="stable")
         if getattr(r, "n_boxes", 0):
             i32 = lambda x: np.ascontiguousarray(x, dtype=np.int32)
             sb = i32(r.self_sb if r.self_sb is not None else np.zeros((0, 2))).reshape(-1)
@@ -271,6 +276,34 @@ def signed_distance(robot: Robot, env: Env, q_dev, sd_dev, stream=None):
         raise ValueError("q_dev must be [n, N] with stride(1) == 1 and sd_dev must hold N entries")
     _check(lib().ezo_signed_distance(robot.h, env.h, C.c_void_p(q_dev.data_ptr()), N, _ld(q_dev),
                                      C.c_void_p(sd_dev.data_ptr()), _stream(stream)))
+
+
+def sphere_centres(robot: Robot, q_dev, out_dev, fp64: bool = False, stream=None):
+    """Sphere centres of the configurations q_dev (float32 [n, N]) into
+    out_dev (float64 CUDA tensor [n_spheres, 3, N]): the collision checker's
+    FP32 kinematics, or FP64 kinematics with fp64=True."""
+    import torch
+    _need_cuda(q_dev, torch.float32, "q_dev")
+    _need_cuda(out_dev, torch.float64, "out_dev")
+    n, N = q_dev.shape
+    if n != robot.n or (N > 1 and q_dev.stride(1) != 1) or out_dev.numel() < 3 * robot.n_spheres * N or \
+            not out_dev.is_contiguous():
+        raise ValueError("q_dev must be [n, N] with stride(1) == 1 and out_dev contiguous [n_spheres, 3, N]")
+    _check(lib().ezo_sphere_centres(robot.h, C.c_void_p(q_dev.data_ptr()), N, _ld(q_dev), 1 if fp64 else 0,
+                                    C.c_void_p(out_dev.data_ptr()), _stream(stream)))
+
+
+def fk_error(robot: Robot, q_dev, err_dev, stream=None):
+    """err_dev[i] (float32 CUDA tensor) = largest distance in metres between a
+    sphere centre of the checker's FP32 kinematics and of FP64 kinematics."""
+    import torch
+    _need_cuda(q_dev, torch.float32, "q_dev")
+    _need_cuda(err_dev, torch.float32, "err_dev")
+    n, N = q_dev.shape
+    if n != robot.n or (N > 1 and q_dev.stride(1) != 1) or err_dev.numel() < N:
+        raise ValueError("q_dev must be [n, N] with stride(1) == 1 and err_dev must hold N entries")
+    _check(lib().ezo_fk_error(robot.h, C.c_void_p(q_dev.data_ptr()), N, _ld(q_dev), C.c_void_p(err_dev.data_ptr()),
+                              _stream(stream)))
 
 
 def hit_and_run(A_dev, b_dev, v1, v2, N: int, n_mix: int, seed: int, stream_id: int, round_k: int, out_dev,
@@ -405,20 +438,22 @@ class Batch:
         return st, [A[g, : m[g]] for g in range(self.B)], [b[g, : m[g]] for g in range(self.B)]
 
     def state(self, g: int) -> dict:
-        o = np.zeros(12, dtype=np.int32)
+        o = np.zeros(13, dtype=np.int32)
         _check(lib().ezo_batch_read(self.h, g, 6, C.c_void_p(o.ctypes.data), o.nbytes))
         keys = ("k", "status", "m", "n_samples", "m_test", "count", "n_cand", "planes", "rounds", "n_placed",
-                "n_p", "env")
+                "n_p", "env", "s_cap")
         return dict(zip(keys, (int(x) for x in o)))
 
     def read(self, g: int, what: str) -> np.ndarray:
+        """A per-segment buffer of the current round; samples are [n, s_cap_g]
+        with the segment's own capacity s_cap_g (its stride on the device)."""
         st = self.state(g)
         n, npp = self.n, st["n_p"]
         if what == "samples":
-            o = np.zeros((n, self.s_cap), dtype=np.float32)
+            o = np.zeros((n, st["s_cap"]), dtype=np.float32)
             code = 0
         elif what == "labels":
-            o = np.zeros(self.s_cap, dtype=np.uint8)
+            o = np.zeros(st["s_cap"], dtype=np.uint8)
             code = 1
         elif what == "cand_idx":
             o = np.zeros(npp, dtype=np.int32)

@@ -12,6 +12,7 @@ Tolerances (stated here, derived in the design notes):
 * hit-and-run: start points within FP32 rounding; walks within 1e-3 for at
   least 99% of samples; every sample inside P up to 1e-5 (1 + |b|).
 """
+import functools
 import json
 import os
 
@@ -92,6 +93,55 @@ def test_check_collision_matches_oracle(ezo, which, lanes):
     got = gpu_labels(ezo, robot, env, q32, lanes)
     ref = assert_labels_match(rd, env_np, q32, got)
     assert 0 < ref.sum() < N
+
+
+def near_boundary_configs(rd, env_np, seed, n_seg=120, steps=(9, 17)):
+    """Configurations close to the collision boundary, where the FP32 fast form
+    is inside its rounding band and the direct re-check decides: the midpoints
+    of FP64 bisections between free and colliding uniform configurations
+    (oracle labels), from bisection step steps[0] to steps[1] - 1, so the
+    distances to tangency range from ~1e-3 m down to ~1e-6 m."""
+    q = wl.uniform_configs(seed, rd, 20 * n_seg)
+    lab = orc.in_collision(rd, env_np, q)
+    free, col = q[~lab][:n_seg], q[lab][:n_seg]
+    k = min(free.shape[0], col.shape[0])
+    lo, hi = free[:k].copy(), col[:k].copy()
+    out = []
+    for s in range(steps[1]):
+        mid = 0.5 * (lo + hi)
+        c = orc.in_collision(rd, env_np, mid)
+        if s >= steps[0]:
+            out.append(mid)
+        hi = np.where(c[:, None], mid, hi)
+        lo = np.where(c[:, None], lo, mid)
+    return np.concatenate(out).astype(np.float32)
+
+
+@functools.lru_cache(maxsize=None)
+def _near_boundary_case(which):
+    if which == "planar":
+        rd, env_np, _, _ = planar_scene()
+    elif which == "dh7":
+        rd, env_np, _ = dh7_scene()
+    else:
+        rd, env_np = wl.dh7_robot(), table_env()
+    return rd, env_np, near_boundary_configs(rd, env_np, 23)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("which", ["planar", "dh7", "table"])
+def test_check_collision_near_boundary(ezo, which, lanes):
+    """Labels of configurations within ~1e-3 m of tangency (many of them
+    inside the fast form's rounding band, where every lane re-checks its own
+    obstacles with the difference form) against the oracle, at every lane
+    count."""
+    rd, env_np, q32 = _near_boundary_case(which)
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    got = gpu_labels(ezo, robot, env, q32, lanes)
+    sd = orc.signed_distance(rd, env_np, q32.astype(np.float64))
+    near = np.abs(sd) < 1e-4
+    assert near.sum() > 100  # the case this test is for
+    assert_labels_match(rd, env_np, q32, got)
 
 
 def test_check_collision_full_batch_sampled(ezo):
@@ -592,13 +642,33 @@ def test_inflate_path_sequential_equals_speculative(ezo):
 
 
 def test_inflate_path_matches_oracle_skip_rule(ezo):
-    """A planar path whose second half lies inside the first polytope."""
+    """Sec. VI-A on a planar path whose second half lies inside the first
+    polytope and whose third segment leaves it: every segment is inflated
+    speculatively, the oracle applies the skip rule (both endpoints inside an
+    earlier kept polytope, 1e-9) to the GPU's polytopes in path order, and
+    the segments the library keeps, in the speculative and in the
+    sequential mode, are the ones the oracle keeps."""
     rd, env_np, v1, v2 = planar_scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
-    verts = np.array([v1, 0.5 * (v1 + v2), v2])
+    v3 = v2 + np.array([0.0, 0.0, 0.6])
+    assert orc.signed_distance(rd, env_np, v2[None, :] + np.linspace(0, 1, 100)[:, None] * (v3 - v2)[None, :]).min() > 0
+    verts = np.array([v1, 0.5 * (v1 + v2), v2, v3])
+    K = verts.shape[0] - 1
     prm = ezo.Params.make(eps=0.1, delta=0.05, n_p=500, n_f=10, n_b=10, n_mix=20, seed=2)
-    out = ezo.inflate_path(robot, env, verts, prm, sequential=True)
-    assert [k for k, _ in out] == [0]
+    bt = ezo.Batch(robot, [env], verts[:-1], verts[1:], prm, seg_stream=np.arange(K, dtype=np.uint32),
+                   path_first=np.zeros(K, np.int32))
+    bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)
+    res = [bt.segment(g) for g in range(K)]
+    kept = []
+    for k in range(K):
+        if not any(orc.segment_contained(res[j].A, res[j].b, verts[k], verts[k + 1]) for j in kept):
+            kept.append(k)
+    assert [k for k in range(K) if res[k].status != ezo.SEG_SKIPPED] == kept
+    assert kept[0] == 0 and 1 not in kept
+    seq = ezo.inflate_path(robot, env, verts, prm, sequential=True)
+    assert [k for k, _ in seq] == kept
+    for (k, r) in seq:
+        np.testing.assert_array_equal(r.A, res[k].A)
 
 
 def test_segment_in_collision_reports_tcol(ezo):
@@ -665,3 +735,47 @@ def test_fp32_fma_probe_within_the_nominal_peak(ezo):
     assert tf > 0
     if nominal is not None:
         assert 0.5 * nominal < tf < 1.05 * nominal, (tf, nominal)
+
+
+# --------------------------------------- kinematics error of the FP32 checker --
+@pytest.mark.parametrize("which", ["dh7", "chain10", "mixed"])
+def test_sphere_centres_and_fk_error_against_oracle(ezo, which):
+    """The checker's FP32 sphere centres and the library's FP64 ones against
+    the oracle's FP64 forward kinematics (Sec. II), on the same FP32
+    configurations: FP64 within 1e-12 m, FP32 within 1e-5 m (the label
+    band), and ezo_fk_error equal to the largest FP32-FP64 distance per
+    configuration."""
+    if which == "dh7":
+        rd = wl.dh7_robot()
+    elif which == "chain10":
+        rd = chain10_robot()
+    else:
+        rd = wl.Robot(name="mixed", a=np.array([0.1, 0.0, 0.3, 0.05]), alpha=np.array([0.4, -1.2, 0.0, 0.7]),
+                      d=np.array([0.2, 0.1, 0.0, 0.3]), theta_off=np.array([0.3, -0.5, 0.1, 0.0]),
+                      q_lo=np.array([-2.0, 0.0, -2.0, -0.5]), q_hi=np.array([2.0, 1.0, 2.0, 0.5]),
+                      sphere_frame=np.array([4, 1, 2, 2, 3, 0], dtype=np.int32),
+                      sphere_xyz=np.array([[0, 0, 0.1], [0.1, 0, 0], [0, 0.1, 0], [0, 0, 0], [0.05, 0, 0],
+                                           [0, 0, 0.05]]),
+                      sphere_r=np.full(6, 0.05), sphere_link=np.array([4, 1, 2, 2, 3, 0], dtype=np.int32),
+                      self_pairs=np.zeros((0, 2), dtype=np.int32), joint_type=np.array([0, 1, 0, 1], dtype=np.int32))
+    robot = ezo.Robot(rd)
+    N = 1537  # several blocks and a ragged tail
+    q32 = wl.uniform_configs(31, rd, N).astype(np.float32)
+    qd = to_dev(q32)
+    ns = rd.n_spheres
+    c32 = torch.empty((ns, 3, N), dtype=torch.float64, device="cuda")
+    c64 = torch.empty((ns, 3, N), dtype=torch.float64, device="cuda")
+    err = torch.empty(N, dtype=torch.float32, device="cuda")
+    ezo.sphere_centres(robot, qd, c32, fp64=False)
+    ezo.sphere_centres(robot, qd, c64, fp64=True)
+    ezo.fk_error(robot, qd, err)
+    torch.cuda.synchronize()
+    ref = orc.sphere_centres(rd, q32.astype(np.float64))[:, robot.sphere_order, :]  # [N, ns, 3]
+    g32 = c32.cpu().numpy().transpose(2, 0, 1)
+    g64 = c64.cpu().numpy().transpose(2, 0, 1)
+    assert np.abs(g64 - ref).max() < 1e-12
+    d32 = np.linalg.norm(g32 - ref, axis=2).max(axis=1)
+    assert d32.max() < 1e-5 and d32.max() > 0
+    np.testing.assert_allclose(err.cpu().numpy(), np.linalg.norm(g32 - g64, axis=2).max(axis=1), rtol=1e-6,
+                               atol=1e-12)
+    print(f"{which}: FP32 kinematics error max {d32.max():.2e} m, p99 {np.quantile(d32, 0.99):.2e} m")
