@@ -1,6 +1,7 @@
 """The BF16 tensor-core MLP surrogate against its FP64 oracle: gradients of
-one batch per parameter tensor (relative L2 error <= 1e-2, the BF16 bound),
-predictions, and training progress on exact signed-distance labels."""
+one batch element by element (within a bound derived from the BF16
+roundings of the training pass), predictions, and training progress on exact
+signed-distance labels."""
 import json
 import os
 
@@ -45,7 +46,55 @@ def _scene():
     return wl.dh7_robot(), wl.box_obstacles(s["env_seed"], s["n_obs"])
 
 
+U_BF16 = 2.0 ** -8  # unit roundoff of BF16 (8-bit significand, round to nearest)
+
+
+def bf16_gradient_sigma(p, X, t, u=U_BF16):
+    """Standard deviation of g_GPU - g per parameter under the probabilistic
+    model of rounding errors (each rounding an independent, mean-zero error,
+    uniform within +-u |x|, so of variance u^2 x^2 / 3): the GPU's training
+    pass rounds the activations H1..H3 and the pre-activation gradients
+    dZ3..dZ1 to BF16; the weights and features the oracle uses are the GPU's
+    BF16 values and add nothing. Variances are carried through the forward
+    pass (Var z = sum_k W^2 Var h), the output and the backward pass (SiLU'
+    and, for the perturbed pre-activation, SiLU'' <= 0.5) to every gradient,
+    which is a sum over the batch of products of two perturbed factors."""
+    P = so.unpack(p)
+    _, c = so.forward(P, X)
+    N = X.shape[0]
+    sig = lambda z: 1.0 / (1.0 + np.exp(-z))
+    dsilu = lambda z: sig(z) * (1.0 + z * (1.0 - sig(z)))
+    r = u * u / 3.0
+    W = {l: P[f"W{l}"] for l in (1, 2, 3)}
+    W2 = {l: W[l] ** 2 for l in (1, 2, 3)}
+    H = {0: X, 1: c["h1"], 2: c["h2"], 3: c["h3"]}
+    Z = {l: c[f"z{l}"] for l in (1, 2, 3)}
+    VH, VZ = {0: np.zeros_like(X)}, {}
+    for l in (1, 2, 3):
+        VZ[l] = VH[l - 1] @ W2[l].T
+        VH[l] = r * H[l] ** 2 + dsilu(Z[l]) ** 2 * VZ[l]
+    y = H[3] @ P["w4"] + P["b4"][0]
+    dy = 2.0 * (y - t) / N
+    Vdy = 4.0 * (VH[3] @ P["w4"] ** 2) / N ** 2
+    gH, VgH = np.outer(dy, P["w4"]), np.outer(Vdy, P["w4"] ** 2)
+    out = {"w4": np.sqrt(Vdy @ H[3] ** 2 + dy ** 2 @ VH[3]), "b4": np.array([np.sqrt(Vdy.sum())])}
+    for l in (3, 2, 1):
+        d = dsilu(Z[l])
+        gZ = gH * d
+        VgZ = r * gZ ** 2 + d ** 2 * VgH + (0.5 * gH) ** 2 * VZ[l]
+        out[f"W{l}"] = np.sqrt(VgZ.T @ H[l - 1] ** 2 + (gZ ** 2).T @ VH[l - 1])
+        out[f"b{l}"] = np.sqrt(VgZ.sum(axis=0))
+        gH, VgH = gZ @ W[l], VgZ @ W2[l]
+    return so.pack(out)
+
+
 def test_surrogate_gradient_matches_oracle(ezo):
+    """Gradient of the mean squared error on one batch, element by element:
+    |g_GPU - g_oracle| <= 7 sigma of the BF16 rounding model + 1e-6 x the
+    tensor's largest gradient (FP32 accumulation). A numpy model of the
+    GPU's roundings stays within 4 sigma on every one of ~200k gradients over
+    12 random networks; a wrong or missing term of the backward pass is
+    ~1000 sigma away."""
     rd, _ = _scene()
     robot = ezo.Robot(rd)
     sur = ezo.Surrogate(robot, seed=3)
@@ -60,13 +109,16 @@ def test_surrogate_gradient_matches_oracle(ezo):
     X = bf16_round(so.features(q.astype(np.float64)))
     loss_ref, g_ref = so.loss_and_grad(p, X, t.astype(np.float64))
     assert abs(loss - loss_ref) <= 1e-2 * abs(loss_ref)
+    sg = bf16_gradient_sigma(p, X, t.astype(np.float64))
     o = 0
     for name, shp in so.SHAPES:
-        c = int(np.prod(shp))
-        a, b = g[o:o + c].astype(np.float64), g_ref[o:o + c]
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert rel <= 1e-2, (name, rel)
-        o += c
+        cnt = int(np.prod(shp))
+        a, b, e = g[o:o + cnt].astype(np.float64), g_ref[o:o + cnt], sg[o:o + cnt]
+        err = np.abs(a - b)
+        lim = 7.0 * e + 1e-6 * np.abs(b).max()
+        print(f"{name}: max |err| / sigma = {float(np.max(err / (e + 1e-300))):.2f}, max |err| = {err.max():.3e}")
+        assert np.all(err <= lim), (name, float(np.max(err / lim)))
+        o += cnt
 
 
 @pytest.mark.parametrize("N", [1, 129, 1000, 40037])
@@ -159,7 +211,8 @@ def trained(ezo):
     rd, env_np = _scene()
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
     sur = ezo.Surrogate(robot, seed=6)
-    sur.train(env, n_samples=1 << 22, epochs=4, batch=4096, lr=1e-3, data_seed=12)
+    # 10^7 exact labels of uniform configurations in the joint box, mini-batches of 3200
+    sur.train(env, n_samples=10_000_000, epochs=4, batch=3200, lr=1e-3, data_seed=12)
     return rd, env_np, robot, env, sur
 
 
@@ -230,28 +283,30 @@ def test_surrogate_bisection_round_replay(ezo, trained):
 
 
 def test_surrogate_path_gain_and_validity(ezo, trained):
-    """The whole 10-segment path with and without the surrogate: every
-    polytope contains its segment and is accepted by the exact test, and the
-    surrogate cuts the exact checks spent in bisection."""
+    """The whole 10-segment path with and without the surrogate, Philox seeds
+    1..5: every polytope contains its segment and is accepted by the exact
+    test, and the surrogate cuts the exact checks spent in bisection to below
+    0.6 of the exact method's on average (per seed the cut depends on the
+    draw, how many surrogate end points verify in collision)."""
     rd, env_np, robot, env, sur = trained
     with open(os.path.join(GOLDEN, "workloads.json")) as f:
         path = np.asarray(json.load(f)["dh7"]["path"])
     K = path.shape[0] - 1
-    prm = ezo.Params.make(n_p=10000, seed=1)
-    out = {}
-    for use in (False, True):
-        bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm)
-        if use:
-            bt.attach_surrogate(sur, 0.0)
-        bt.run(ezo.RUN_GRAPH)
-        bis = sum(bt.check_split(g)[1] for g in range(K))
-        for g in range(K):
-            r = bt.segment(g)
-            assert r.status == ezo.SEG_ACCEPTED
-            assert orc.segment_contained(r.A, r.b, path[g], path[g + 1], tol=1e-12)
-        out[use] = (bis, sum(bt.surrogate_evals(g) for g in range(K)))
-    print(f"exact bisection checks: {out[False][0]} without, {out[True][0]} with the surrogate "
-          f"({out[True][1]} surrogate evaluations)")
-    # the saving depends on the draw (how many surrogate end points verify);
-    # over the seeds tried it is 38-50%
-    assert out[True][0] < 0.7 * out[False][0]
+    ratios = []
+    for seed in (1, 2, 3, 4, 5):
+        prm = ezo.Params.make(n_p=10000, seed=seed)
+        out = {}
+        for use in (False, True):
+            bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm)
+            if use:
+                bt.attach_surrogate(sur, 0.0)
+            bt.run(ezo.RUN_GRAPH)
+            bis = sum(bt.check_split(g)[1] for g in range(K))
+            for g in range(K):
+                r = bt.segment(g)
+                assert r.status == ezo.SEG_ACCEPTED
+                assert orc.segment_contained(r.A, r.b, path[g], path[g + 1], tol=1e-12)
+            out[use] = bis
+        ratios.append(out[True] / out[False])
+    print(f"exact bisection checks with / without the surrogate, seeds 1..5: {np.round(ratios, 3)}")
+    assert np.mean(ratios) < 0.6, ratios
