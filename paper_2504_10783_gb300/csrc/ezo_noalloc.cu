@@ -84,12 +84,19 @@ int na_test_size(int k, double eps, double delta, double tau) {
   return (int)std::ceil(2.0 * std::log(1.0 / dk) / (eps * tau * tau));
 }
 
+// Lanes per configuration of the label and bisection kernels: the rule of
+// ezo_batch_create for rounds of this size (two lanes per configuration below
+// 2^20 samples, eight per bisection candidate below 2^20 candidates; labels
+// do not depend on the choice); above that, the size rule of the collision
+// checker, since the tuner would allocate.
 int lanes_for(long long N) {
   if (N >= (1ll << 20)) return 1;
   if (N >= (1ll << 17)) return 2;
   if (N >= (1ll << 15)) return 4;
   return 8;
 }
+int check_lanes(long long s_cap) { return s_cap < (1ll << 20) ? 2 : lanes_for(s_cap); }
+int bisect_lanes(long long np) { return np >= (1ll << 20) ? lanes_for(np / 4) : 8; }
 
 }  // namespace
 
@@ -135,6 +142,11 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
                                          " bytes of working memory, more than the fixed " +
                                          std::to_string((long long)EZO_NOALLOC_SCRATCH_BYTES) +
                                          " (lower n_p or n_f * n_it_max, or use ezo_batch_create)");
+  // the collision kernels stage the robot spheres, the obstacles and one set
+  // of sphere centres per configuration group in shared memory
+  if (check_smem_bytes(nsp_pad, envf.e.n_obs_pad, 128, 1, ezo_internal_robot_boxes(robot), envf.e.n_box) >
+      220 * 1024)
+    return na_fail(EZO_ERR_INVALID_ARG, "robot spheres and obstacles exceed shared memory");
   void* base = nullptr;
   ezo_status st = scratch_address(&base);
   if (st != EZO_OK) return st;
@@ -186,10 +198,15 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   const int zero = 0;
   RoundSummary sum0{};
   cudaError_t e = cudaSuccess;
+  // On a failure after work was queued, the stream is drained before the
+  // error returns, so the shared array is idle when the call returns.
 #define NA_CUDA(call)                                                              \
   do {                                                                             \
     e = (call);                                                                    \
-    if (e != cudaSuccess) return na_fail(EZO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e)); \
+    if (e != cudaSuccess) {                                                        \
+      (void)cudaStreamSynchronize(s);                                              \
+      return na_fail(EZO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e)); \
+    }                                                                              \
   } while (0)
   NA_CUDA(cudaMemcpyAsync(d_st, &s0, sizeof(s0), cudaMemcpyHostToDevice, s));
   NA_CUDA(cudaMemcpyAsync(d_v1, v1, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -249,7 +266,7 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   int dev = 0, sms = 1;
   NA_CUDA(cudaGetDevice(&dev));
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int T_check = lanes_for(s_cap), T_bis = np >= (1 << 20) ? lanes_for((long long)np / 4) : 8;
+  const int T_check = check_lanes(s_cap), T_bis = bisect_lanes(np);
   const int grid_s = (int)std::max<long long>(1, std::min<long long>(st_tiles * 8, (long long)sms * 16));
   const int grid_c = (int)std::max<long long>(1, std::min<long long>(st_tiles * T_check, (long long)sms * 16));
   const int grid_b = (int)std::max<long long>(1, std::min<long long>(bi_tiles * T_bis, (long long)sms * 16));
