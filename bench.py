@@ -36,9 +36,10 @@ SEGSTATE_BYTES = 112  # sizeof(SegState): per-segment device state read back wit
 # DRAM bytes per launch of the round kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, ncu, this workload); None where not captured for the
 # current kernel
-TRAFFIC = {"sample": 94208}  # round kernel capture, one launch (10 segments x 1e4 walks)
-# DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe)
-CHECKER_TRAFFIC_2E6 = 56078336 + 154368
+TRAFFIC = {}
+# DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe);
+# None until captured for the current kernel
+CHECKER_TRAFFIC_2E6 = None
 KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
 
 
@@ -250,14 +251,128 @@ def _event_ms(torch, stream, fn, label=""):
     return ms
 
 
+def measure_batched(ezo, torch, stream, scenes, rd, robot, paths=256, speculative=True):
+    """Batched form (Sec. VI-A per path, many paths): 8 obstacle sets of
+    128-1024 spheres, seed paths of 1-40 segments, per-segment N_p
+    log-uniform in [1e3, 1e5]. The wavefront mode (each path in order, the
+    current segments of all paths in one graph launch per wave) and, with
+    `speculative`, all segments at once in one graph, against the per-segment
+    launch loop of the plain method. Configs/s count the exact checks of the
+    segments each mode keeps."""
+    from paper_2504_10783_gb300 import workloads as wl
+    sc = scenes["dh7_batched"]
+    envs_np = [wl.box_obstacles(e["env_seed"], e["n_obs"]) for e in sc["envs"]]
+    envs = [ezo.Env(e) for e in envs_np]
+    use = sc["paths"][:paths]
+    v1, v2, seg_env, path_first = [], [], [], []
+    for pth in use:
+        verts = np.asarray(pth["path"])
+        first = len(v1)
+        for k in range(verts.shape[0] - 1):
+            v1.append(verts[k])
+            v2.append(verts[k + 1])
+            seg_env.append(pth["env"])
+            path_first.append(first)
+    B = len(v1)
+    rng = np.random.default_rng(5)
+    seg_np = np.round(10 ** rng.uniform(3, 5, B)).astype(np.int32)
+    prm = ezo.Params.make(eps=0.05, delta=0.05, n_p=10000, n_f=10, n_b=10, n_mix=60, n_it_max=50, seed=1)
+    bt = ezo.Batch(robot, envs, np.asarray(v1), np.asarray(v2), prm, seg_env=seg_env, seg_np=seg_np,
+                   seg_stream=np.arange(B), path_first=path_first)
+
+    def kept_checks():
+        c = k = 0
+        for g in range(B):
+            if bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE):
+                k += 1
+                c += sum(bt.check_split(g))
+        return c, k
+
+    out = {"paths": len(use), "segments": B, "samples_per_round": int(seg_np.sum()),
+           "obstacles": [e["n_obs"] for e in sc["envs"]]}
+    t_wave = [_event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
+                        "wavefront graph") for _ in range(2)]
+    c_wave, k_wave = kept_checks()
+    polys_wave = bt.polytopes()
+    t_loop = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)), "per-segment loop")
+    c_loop, k_loop = kept_checks()
+    polys_loop = bt.polytopes()
+    same = bool(np.array_equal(polys_wave[0], polys_loop[0]) and
+                all(np.array_equal(a, b) for a, b in zip(polys_wave[1], polys_loop[1])))
+    out.update({"wavefront_graph_ms": float(min(t_wave)), "wavefront_kept_segments": int(k_wave),
+                "wavefront_configs_per_s": c_wave / (min(t_wave) / 1e3),
+                "per_segment_loop_ms": float(t_loop), "loop_kept_segments": int(k_loop),
+                "loop_configs_per_s": c_loop / (t_loop / 1e3),
+                "speedup_wavefront_vs_loop": float(t_loop / min(t_wave)),
+                "same_polytopes_wavefront_and_loop": same})
+    if speculative:
+        t_graph = [_event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
+                             "batched graph") for _ in range(2)]
+        c_all = sum(sum(bt.check_split(g)) for g in range(B))
+        c_spec, k_spec = kept_checks()
+        out.update({"speculative_graph_ms": float(min(t_graph)), "speculative_kept_segments": int(k_spec),
+                    "speculative_checks_all_segments": int(c_all),
+                    "speculative_configs_per_s_kept": c_spec / (min(t_graph) / 1e3),
+                    "speedup_speculative_vs_loop": float(t_loop / min(t_graph))})
+    return out
+
+
+def measure_stress(ezo, torch, stream, scenes, rd, robot, np_stress, sur_samples=1 << 23, graph_speculative=True):
+    """Perception-like stress scene: the 7-DOF arm among the 1024-sphere table
+    cloud, 64-segment path, np_stress samples per round: the plain method (one
+    segment at a time), the same order with every round in one graph, the
+    speculative batch, and the in-order run with surrogate-guided
+    bisection."""
+    from paper_2504_10783_gb300 import workloads as wl
+    sc = scenes["table_cloud"]
+    env_np = wl.table_cloud_obstacles(sc["cloud_seed"])
+    env = ezo.Env(env_np)
+    verts = np.asarray(sc["path"])
+    K = verts.shape[0] - 1
+    prm = ezo.Params.make(eps=0.05, delta=0.05, n_p=np_stress, n_f=10, n_b=10, n_mix=60, n_it_max=50, seed=1)
+    bt = ezo.Batch(robot, [env], verts[:-1], verts[1:], prm, seg_stream=np.arange(K),
+                   path_first=np.zeros(K, np.int32))
+
+    def counts():
+        c = k = 0
+        for g in range(K):
+            if bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE):
+                k += 1
+                c += sum(bt.check_split(g))
+        return int(c), int(k)
+
+    t_plain = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)), "plain")
+    c_plain, k_plain = counts()
+    t_wave = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
+                       "in order, rounds in one graph")
+    c_wave, k_wave = counts()
+    out = {"segments": K, "obstacles": int(env_np.n_obs), "n_p": np_stress,
+           "plain_ms": t_plain, "plain_kept_checks": c_plain, "plain_kept": k_plain,
+           "in_order_graph_ms": t_wave, "in_order_graph_kept_checks": c_wave}
+    if graph_speculative:
+        t_batch = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
+                            "batched")
+        c_batch, k_batch = counts()
+        out.update({"batched_ms": t_batch, "batched_kept_checks": c_batch, "batched_kept": k_batch})
+    sur = ezo.Surrogate(robot, seed=7)
+    t_train = _event_ms(torch, stream, lambda: sur.train(env, n_samples=sur_samples, epochs=4, batch=4096,
+                                                         lr=1e-3, data_seed=13), "surrogate training")
+    bt.attach_surrogate(sur, 0.0)
+    t_wave_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
+                           "in order + surrogate")
+    c_wave_sur, _ = counts()
+    evals = sum(bt.surrogate_evals(g) for g in range(K))
+    out.update({"surrogate_train_ms": t_train, "surrogate_train_samples": sur_samples,
+                "in_order_surrogate_ms": t_wave_sur, "in_order_surrogate_kept_checks": c_wave_sur,
+                "surrogate_evals": int(evals)})
+    return out
+
+
 def run_workload(args):
-    """--workload batched: 8 obstacle sets of 128-1024 spheres, seed paths of
-    1-40 segments, per-segment N_p log-uniform in [1e3, 1e5]; all segments of
-    all paths inflated in one batch under one CUDA graph, against the plain
-    per-segment launch loop. --workload stress: table point cloud (1024
-    spheres of 2 cm), 64-segment path, N_p = 1e6 samples per round: plain,
-    batched, batched + surrogate. --workload surrogate: the MLP's forward pass
-    alone on 2^rows_log2 configurations."""
+    """--workload batched: the batched form (measure_batched, all three
+    modes). --workload stress: the stress scene at --np-stress samples per
+    round (measure_stress). --workload surrogate: the MLP's forward pass alone
+    on 2^rows_log2 configurations."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -270,49 +385,7 @@ def run_workload(args):
     robot = ezo.Robot(rd)
     out = {"workload": args.workload}
     if args.workload == "batched":
-        sc = scenes["dh7_batched"]
-        envs_np = [wl.box_obstacles(e["env_seed"], e["n_obs"]) for e in sc["envs"]]
-        envs = [ezo.Env(e) for e in envs_np]
-        paths = sc["paths"][: args.paths]
-        v1, v2, seg_env, path_first = [], [], [], []
-        for pth in paths:
-            verts = np.asarray(pth["path"])
-            first = len(v1)
-            for k in range(verts.shape[0] - 1):
-                v1.append(verts[k])
-                v2.append(verts[k + 1])
-                seg_env.append(pth["env"])
-                path_first.append(first)
-        B = len(v1)
-        rng = np.random.default_rng(5)
-        seg_np = np.round(10 ** rng.uniform(3, 5, B)).astype(np.int32)
-        prm = ezo.Params.make(eps=0.05, delta=0.05, n_p=10000, n_f=10, n_b=10, n_mix=60, n_it_max=50, seed=1)
-        bt = ezo.Batch(robot, envs, np.asarray(v1), np.asarray(v2), prm, seg_env=seg_env, seg_np=seg_np,
-                       seg_stream=np.arange(B), path_first=path_first)
-        t_graph = []
-        for rep in range(2):
-            t_graph.append(_event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False,
-                                                                                     mode=ezo.RUN_GRAPH)),
-                                    "batched graph"))
-        checks = sum(sum(bt.check_split(g)) for g in range(B))
-        kept = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
-        t_wave = []
-        for rep in range(2):
-            t_wave.append(_event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
-                                    "wavefront graph"))
-        checks_wave = sum(sum(bt.check_split(g)) for g in range(B))
-        kept_wave = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
-        t_loop = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)), "per-segment loop")
-        kept_loop = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(B))
-        out.update({"paths": len(paths), "segments": B, "samples_per_round": int(seg_np.sum()),
-                    "obstacles": [e["n_obs"] for e in sc["envs"]],
-                    "batched_graph_ms": float(min(t_graph)), "batched_checks": int(checks),
-                    "batched_configs_per_s": checks / (min(t_graph) / 1e3), "kept_segments": int(kept),
-                    "wavefront_graph_ms": float(min(t_wave)), "wavefront_checks": int(checks_wave),
-                    "kept_segments_wavefront": int(kept_wave),
-                    "per_segment_loop_ms": float(t_loop), "kept_segments_loop": int(kept_loop),
-                    "speedup_wavefront_vs_loop": float(t_loop / min(t_wave)),
-                    "speedup_speculative_vs_loop": float(t_loop / min(t_graph))})
+        out.update(measure_batched(ezo, torch, stream, scenes, rd, robot, paths=args.paths))
     elif args.workload == "surrogate":
         # inference of the BF16 MLP alone (tensor-core forward pass with the
         # features computed in the kernel) on 2^rows_log2 configurations; the
@@ -337,47 +410,7 @@ def run_workload(args):
                     "peak_source": src, "frac": tf / peak, "nan_outputs": int(torch.isnan(y).sum()),
                     "wait_timed_out": sur.timed_out()})
     else:
-        sc = scenes["table_cloud"]
-        env_np = wl.table_cloud_obstacles(sc["cloud_seed"])
-        env = ezo.Env(env_np)
-        verts = np.asarray(sc["path"])
-        K = verts.shape[0] - 1
-        prm = ezo.Params.make(eps=0.05, delta=0.05, n_p=args.np_stress, n_f=10, n_b=10, n_mix=60, n_it_max=50,
-                              seed=1)
-        bt = ezo.Batch(robot, [env], verts[:-1], verts[1:], prm, seg_stream=np.arange(K),
-                       path_first=np.zeros(K, np.int32))
-
-        def counts():
-            c = sum(sum(bt.check_split(g)) for g in range(K))
-            kept = sum(bt.segment(g).status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE) for g in range(K))
-            return int(c), int(kept)
-
-        t_plain = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=True)), "plain")
-        c_plain, k_plain = counts()
-        t_batch = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
-                            "batched")
-        c_batch, k_batch = counts()
-        t_wave = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
-                           "in order, rounds in one graph")
-        c_wave, k_wave = counts()
-        sur = ezo.Surrogate(robot, seed=7)
-        t_train = _event_ms(torch, stream, lambda: sur.train(env, n_samples=1 << 23, epochs=4, batch=4096,
-                                                             lr=1e-3, data_seed=13), "surrogate training")
-        bt.attach_surrogate(sur, 0.0)
-        t_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=False, mode=ezo.RUN_GRAPH)),
-                          "batched + surrogate")
-        c_sur, k_sur = counts()
-        t_wave_sur = _event_ms(torch, stream, lambda: (bt.reset(), bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)),
-                               "in order + surrogate")
-        c_wave_sur, _ = counts()
-        evals = sum(bt.surrogate_evals(g) for g in range(K))
-        out.update({"segments": K, "obstacles": int(env_np.n_obs), "n_p": args.np_stress,
-                    "plain_ms": t_plain, "plain_checks": c_plain, "plain_kept": k_plain,
-                    "batched_ms": t_batch, "batched_checks": c_batch, "batched_kept": k_batch,
-                    "in_order_graph_ms": t_wave, "in_order_graph_checks": c_wave,
-                    "surrogate_train_ms": t_train, "batched_surrogate_ms": t_sur, "batched_surrogate_checks": c_sur,
-                    "surrogate_evals": int(evals), "batched_surrogate_kept": k_sur,
-                    "in_order_surrogate_ms": t_wave_sur, "in_order_surrogate_checks": c_wave_sur})
+        out.update(measure_stress(ezo, torch, stream, scenes, rd, robot, args.np_stress))
     print(json.dumps(out))
 
 
@@ -393,16 +426,19 @@ def bf16_peak():
 
 
 def measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream, flush, K, args):
-    """Trains the BF16 MLP on 2^22 exact labels (4 epochs), reports its
-    false-negative / false-positive rates on 2^16 fresh configurations, and
-    times the path with surrogate-guided bisection on the same Philox seeds
-    as the timed exact steps (mean over the seeds, like ms_per_step)."""
+    """Trains the BF16 MLP on 10^7 exact labels (4 epochs, mini-batches of
+    3200), reports its false-negative / false-positive rates on 2^20 fresh
+    uniform configurations and on the exact bisection midpoints of the
+    path's last rounds, and times the path with surrogate-guided bisection on
+    the same Philox seeds as the timed exact steps (mean over the seeds, like
+    ms_per_step)."""
     from paper_2504_10783_gb300 import workloads as wl
     sur = ezo.Surrogate(robot, seed=6)
+    n_train = 10_000_000
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    sur.train(env, n_samples=1 << 22, epochs=4, batch=4096, lr=1e-3, data_seed=12)
+    sur.train(env, n_samples=n_train, epochs=4, batch=3200, lr=1e-3, data_seed=12)
     e1.record(stream)
     e1.synchronize()
     train_ms = e0.elapsed_time(e1)
@@ -415,6 +451,48 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream,
     yv, col = y.cpu().numpy(), flags.cpu().numpy().astype(bool)
     fn0 = float(np.mean(yv[col] >= 0.0)) if col.any() else 0.0
     fp0 = float(np.mean(yv[~col] < 0.0))
+    # the exact bisection midpoints of round 1 of every segment (seed 1, run
+    # step by step up to the bisection): midpoint s of a candidate is
+    # c_proj + f_s (c - c_proj) with f_s from the decisions before it, and its
+    # exact label is decision s
+    bt0 = batches[0]
+    bt0.reset()
+    for step in range(5):
+        bt0.step(step)
+    bt0.sync()
+    n_b = PARAMS["n_b"]
+    mids, labs = [], []
+    for g in range(K):
+        st = bt0.state(g)
+        nc = st["n_cand"]
+        if nc == 0:
+            continue
+        S = bt0.read(g, "samples")[:, : st["n_samples"]].T.astype(np.float64)
+        c = S[bt0.read(g, "cand_idx")[:nc]]
+        v1, v2 = bt0.v1[g], bt0.v2[g]
+        e = v2 - v1
+        al = np.clip(((c - v1) @ e) / max(float(e @ e), 1e-300), 0.0, 1.0)
+        pp = v1[None, :] + al[:, None] * e[None, :]
+        bits = bt0.read(g, "bits")[:nc]
+        lo, hi = np.zeros(nc), np.ones(nc)
+        for s_ in range(n_b):
+            f = 0.5 * (lo + hi)
+            d = ((bits >> s_) & 1).astype(bool)
+            mids.append((pp + f[:, None] * (c - pp)).astype(np.float32))
+            labs.append(d)
+            hi = np.where(d, f, hi)
+            lo = np.where(d, lo, f)
+    fn_mid = fp_mid = None
+    n_mid = 0
+    if mids:
+        qm = torch.from_numpy(np.ascontiguousarray(np.concatenate(mids).T)).cuda()
+        ym = torch.empty(qm.shape[1], device="cuda")
+        sur.predict(qm, ym)
+        torch.cuda.synchronize()
+        ymv, lm = ym.cpu().numpy(), np.concatenate(labs)
+        n_mid = int(lm.size)
+        fn_mid = float(np.mean(ymv[lm] >= 0.0)) if lm.any() else 0.0
+        fp_mid = float(np.mean(ymv[~lm] < 0.0)) if (~lm).any() else 0.0
     times = []
     samp = bisc = evals = 0
     for bt in batches:
@@ -460,8 +538,12 @@ def measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream,
     peak_bf16, peak_src = bf16_peak()
     inf_tf = gemm_flops / (inf_ms / 1e3) / 1e12
     return {"ms_per_path": float(np.mean(times)), "ms_per_path_seed1": float(times[0]), "seeds": ns,
-            "train_ms": train_ms, "train_samples": 1 << 22, "epochs": 4,
-            "fn_rate_margin0": fn0, "fp_rate_margin0": fp0, "sample_checks_per_path": samp / ns,
+            "train_ms": train_ms, "train_samples": n_train, "epochs": 4,
+            "fn_rate_margin0": fn0, "fp_rate_margin0": fp0,
+            "bisection_midpoints": {"count": n_mid, "fn_rate_margin0": fn_mid, "fp_rate_margin0": fp_mid,
+                                    "what": "exact midpoints of round 1's bisections (exact run, seed 1, all "
+                                            "segments), labelled by the exact decisions"},
+            "sample_checks_per_path": samp / ns,
             "bisection_checks_per_path": bisc / ns, "surrogate_evals_per_path": evals / ns,
             "held_out_configs": 1 << 20,
             "end_points_verified_in_collision": (1.0 - n_fail / n_cand) if n_cand else None,
@@ -502,6 +584,25 @@ def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, fl
             "paper_context": "paper: ~8.6 M configs/s, Franka (1187 pairs), RTX 3090, same batch size",
             "launches": reps + 3}
 
+
+
+def measure_fk_error(ezo, torch, robot, bt, K):
+    """FP32 forward kinematics of the collision checker against FP64 (the same
+    chain from the FP64 constants) on the samples of the last round of every
+    segment of a bench batch: per configuration, the largest distance between
+    a sphere's FP32 and FP64 centre, in metres (ezo_fk_error)."""
+    qs = []
+    for g in range(K):
+        ns = bt.state(g)["n_samples"]
+        qs.append(bt.read(g, "samples")[:, :ns])
+    q = torch.from_numpy(np.ascontiguousarray(np.concatenate(qs, axis=1))).cuda()
+    err = torch.empty(q.shape[1], dtype=torch.float32, device="cuda")
+    ezo.fk_error(robot, q, err)
+    e = err.cpu().numpy().astype(np.float64)
+    return {"configs": int(e.size), "max_m": float(e.max()), "p99_m": float(np.quantile(e, 0.99)),
+            "median_m": float(np.median(e)), "label_band_m": 1e-5,
+            "what": "per configuration: max over the 40 spheres of |c_FP32 - c_FP64| (FP32 = the checker's "
+                    "kinematics), over the last round's samples of every segment of the seed-1 path"}
 
 
 def measure_forest(ezo, torch, stream, flush, props, sm_max, N=2_000_000, reps=10):
@@ -634,17 +735,20 @@ def main():
     # per-seed work: exact checks (sample labels, bisection midpoints), FP32
     # FLOPs of the walks, kept segments and rounds (the same on every run)
     flops_cfg = ezo.check_flops(robot, env)
+    pairs_cfg = rd.n_spheres * env_np.n_obs + rd.self_pairs.shape[0]
     work = []
     for b in batches:
-        samp = bisc = sflops = kept = 0
+        samp = bisc = sflops = kept = kept_checks = 0
         for g in range(K):
             x, y2 = b.check_split(g)
             samp += x
             bisc += y2
             sflops += b.sample_flops(g)
-            kept += b.segment(g).status != ezo.SEG_SKIPPED
+            if b.segment(g).status != ezo.SEG_SKIPPED:
+                kept += 1
+                kept_checks += x + y2
         work.append({"sample_checks": samp, "bisection_checks": bisc, "sample_flops": sflops, "kept": kept,
-                     "rounds": b.summary()["rounds"]})
+                     "kept_checks": kept_checks, "rounds": b.summary()["rounds"]})
 
     # ---- timed region: device-resident inputs, L2 flushed between steps ----
     clk = ClockSampler(local)
@@ -654,6 +758,7 @@ def main():
     times = []
     launches = 0
     units = 0
+    units_all_segments = 0
     for i in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -664,7 +769,9 @@ def main():
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         w = work[i % N_SEEDS]
-        units += w["sample_checks"] + w["bisection_checks"]
+        # useful work: the exact checks of the segments the skip rule keeps
+        units += w["kept_checks"]
+        units_all_segments += w["sample_checks"] + w["bisection_checks"]
         launches += 6 * w["rounds"] + 2  # first sizing, 6 kernels per round, containment
     torch.cuda.synchronize()
     barrier()
@@ -697,11 +804,21 @@ def main():
     dom = max(tot, key=lambda k: prof[k][0])
     ach = tot[dom] / (prof[dom][0] / 1e3) / 1e12
     path_tf = sum(tot.values()) / (float(np.sum(times)) / 1e3) / 1e12
+    per_kernel = {}
+    for k in tot:
+        a_k = tot[k] / (prof[k][0] / 1e3) / 1e12
+        per_kernel[k] = {"achieved": a_k, "frac": a_k / peak, "ms_per_step": prof[k][0] / args.steps,
+                         "launches_per_step": prof[k][1] / args.steps, "flops_per_step": tot[k] / args.steps,
+                         "traffic": TRAFFIC.get(k)}
+    per_kernel["sample"]["flops"] = "(2mn + 5m + 6n) x N_ms per walk (m rows, n joints)"
+    per_kernel["check"]["flops"] = f"{flops_cfg:.0f} per configuration (8 per pair x {pairs_cfg} pairs + FK)"
+    per_kernel["bisect"]["flops"] = f"{flops_cfg:.0f} per midpoint check (FP64 projection and planes not counted)"
     roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": TRAFFIC.get(dom),
                 "per_launch_ms": prof[dom][0] / prof[dom][1],
                 "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
                 "measured_in": "host-loop pass over the same steps, CUDA events around each launch",
+                "kernels": per_kernel,
                 "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
                 "whole_path": {"achieved": path_tf, "frac": path_tf / peak,
                                "what": "all algorithmic FP32 FLOPs of the path (walks + exact checks) / step time"}}
@@ -739,6 +856,11 @@ def main():
     sur_info = None
     if not args.no_surrogate and not args.no_extras:
         sur_info = measure_surrogate(ezo, torch, robot, env, rd, env_np, batches, mode, stream, flush, K, args)
+        exact_mean = float(np.mean([w["sample_checks"] + w["bisection_checks"] for w in work]))
+        sur_info["exact_checks_per_path_without_surrogate"] = exact_mean
+        sur_info["exact_checks_saved_per_path"] = exact_mean - (sur_info["sample_checks_per_path"] +
+                                                                sur_info["bisection_checks_per_path"])
+        sur_info["exact_only_ms_per_path"] = float(np.mean(times))
 
     # ---- the collision checker alone on the paper's batch size (2e6 configs) ----
     checker = checker_1e8 = forest = {"launches": 0}
@@ -761,6 +883,18 @@ def main():
             envs_more[name] = measure_checker(ezo, torch, rx, ex, rdx, stream, flush, props, sm_max,
                                               ezo.check_flops(rx, ex))
 
+    # ---- forward-kinematics error of the checker against FP64 ----
+    fk_err = measure_fk_error(ezo, torch, robot, batches[0], K)
+
+    # ---- batched form (8 obstacle sets, 256 paths, uneven N_p) and the
+    #      perception-like stress scene (1024 spheres, 64 segments) ----
+    batched = stress = None
+    if not args.no_extras:
+        with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+            scenes = json.load(f)
+        batched = measure_batched(ezo, torch, stream, scenes, rd, robot, paths=256, speculative=False)
+        stress = measure_stress(ezo, torch, stream, scenes, rd, robot, np_stress=100_000, sur_samples=1 << 22)
+
     # ---- end to end through the public API with host buffers ----
     # the step's inputs in pinned host memory
     v1h = torch.from_numpy(np.ascontiguousarray(path[:-1])).pin_memory().numpy()
@@ -780,7 +914,7 @@ def main():
         d2h = int(K * (m_read * (rd.n + 1) * 8 + SEGSTATE_BYTES))
         e2e_times.append(time.perf_counter() - t0)
         w = work[i % N_SEEDS]
-        e2e_units += w["sample_checks"] + w["bisection_checks"]
+        e2e_units += w["kept_checks"]
     e2e_s = float(np.sum(e2e_times))
     e2e = {"value": world * e2e_units / e2e_s, "unit": "configs/s",
            "h2d_bytes_per_step": int(v1h.nbytes + v2h.nbytes), "d2h_bytes_per_step": int(d2h),
@@ -794,13 +928,17 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": args.mode, "segments": K, "seeds": f"1..{N_SEEDS}, step i: seed 1 + i % {N_SEEDS}",
-                       "checks_per_step": checks_per_step, "seed1": {"kept_segments": kept, "sample_checks": samp,
+                       "checks_per_step": checks_per_step,
+                       "value_counts": "exact checks of the segments the skip rule keeps (Sec. VI-A); the "
+                                       "speculative run also inflates the segments it then drops",
+                       "checks_per_step_all_segments": units_all_segments / args.steps,
+                       "seed1": {"kept_segments": kept, "sample_checks": samp,
                                                                       "bisection_checks": bisc},
                        "ms_per_10_segment_path": ms / args.steps,
                        "ms_p50": float(np.percentile(times, 50)), "ms_p90": float(np.percentile(times, 90)),
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "checker_1e8": checker_1e8, "checker_other_envs_2e6": envs_more,
-            "forest": forest, "e2e": e2e,
+            "forest": forest, "fk_error": fk_err, "batched": batched, "stress": stress, "e2e": e2e,
             "gpu_launches": launches,
             "gpu_launches_outside_timed_region": other_launches + checker["launches"] + checker_1e8["launches"] +
             forest["launches"] + sum(c["launches"] for c in envs_more.values()) + 4,  # + the FMA probe
