@@ -36,10 +36,10 @@ SEGSTATE_BYTES = 112  # sizeof(SegState): per-segment device state read back wit
 # DRAM bytes per launch of the round kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, ncu, this workload); None where not captured for the
 # current kernel
-TRAFFIC = {}
+TRAFFIC = {"sample": 87552, "check": 2892288, "bisect": 2760704}  # one round of the 10 segments
 # DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe);
 # None until captured for the current kernel
-CHECKER_TRAFFIC_2E6 = None
+CHECKER_TRAFFIC_2E6 = 56084992 + 153600
 KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
 
 
@@ -668,6 +668,8 @@ def main():
                     help="only the collision checker on 2e6 configurations (for profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed path steps and the kernel pass (no plain, surrogate or checker legs)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch shapes of the round kernels (for profiling runs)")
     ap.add_argument("--workload", default="path", choices=["path", "batched", "stress", "surrogate"])
     ap.add_argument("--rows-log2", type=int, default=20, help="surrogate: log2 of the configurations per call")
     ap.add_argument("--paths", type=int, default=256, help="batched: number of seed paths")
@@ -726,7 +728,15 @@ def main():
         b.reset()
         b.run_path(sequential=False, mode=run_mode)
 
-    for i in range(N_SEEDS):  # every batch once (graph instantiation), then the warm-up steps
+    # launch shapes of the round kernels from the autotuner (timed on the
+    # seed-1 batch; the other batches are of the same class and take the
+    # cached shape), then every batch once (graph instantiation)
+    shape = batches[0].shape()
+    if not args.no_tune:
+        shape = batches[0].tune(reps=2)
+        for b in batches[1:]:
+            b.tune(reps=2)
+    for i in range(N_SEEDS):
         step(i)
     for i in range(max(3, args.warmup)):
         step(i)
@@ -936,7 +946,8 @@ def main():
                                                                       "bisection_checks": bisc},
                        "ms_per_10_segment_path": ms / args.steps,
                        "ms_p50": float(np.percentile(times, 50)), "ms_p90": float(np.percentile(times, 90)),
-                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
+                       "round_kernel_shape": shape},
             "roofline": roofline, "plain_sequential": plain, "surrogate": sur_info, "checker_2e6": checker, "checker_1e8": checker_1e8, "checker_other_envs_2e6": envs_more,
             "forest": forest, "fk_error": fk_err, "batched": batched, "stress": stress, "e2e": e2e,
             "gpu_launches": launches,

@@ -277,7 +277,35 @@ ezo_status ezo_batch_capacity(const ezo_batch* batch, int32_t* m_cap, int32_t* s
  * the speed differs. EZO_ERR_INVALID_ARG for any other value. */
 ezo_status ezo_batch_set_sample_lanes(ezo_batch* batch, int32_t lanes);
 
-/* Step-by-step access for tests and tools. ezo_batch_step runs one kernel of
+/* Launch shapes of a batch's round kernels. sample_fill_tiles: the walks'
+ * lane rule takes one lane per walk from 1.5 x this many 128-walk tiles per
+ * round up, two from half of it, four from an eighth, else eight (default:
+ * the tiles that fill every scheduler with one warp, 4 x SMs x 32 / 128);
+ * check_lanes: lanes per configuration of the label kernel; bisect_lanes:
+ * lanes per bisection candidate (1, 2, 4 or 8 each). Every shape gives the
+ * same samples, labels and polytopes bit for bit; only the speed differs. */
+typedef struct {
+  int32_t sample_fill_tiles;
+  int32_t check_lanes;
+  int32_t bisect_lanes;
+} ezo_shape;
+ezo_status ezo_batch_get_shape(const ezo_batch* batch, ezo_shape* shape);
+/* Sets the shape (EZO_ERR_INVALID_ARG for values out of range); a captured
+ * graph is rebuilt at the next graph run. */
+ezo_status ezo_batch_set_shape(ezo_batch* batch, const ezo_shape* shape);
+/* Autotuner of the shape: runs the whole batch (host-loop mode, best of
+ * `reps` timed runs after a warm-up) for the bisection lanes 2, 4, 8, then
+ * the label lanes 1, 2, 4, 8, then sample_fill_tiles at half, one and two
+ * times the default, keeping a change only when it is at least 2% faster,
+ * and sets the winner. Results are cached for the process per (device, robot
+ * shape, padded obstacle count, boxes, size classes of round 1's samples, of
+ * N_p and of the segment count, N_b, surrogate attached), so a later batch of
+ * the same class takes the cached shape without timing. The batch is left
+ * reset (round 1, polytopes = D). *chosen (nullable) receives the shape.
+ * Synchronous. */
+ezo_status ezo_batch_tune(ezo_batch* batch, int32_t reps, ezo_shape* chosen, void* cuda_stream);
+
+/* Step-by-step access for tests and tools./* Step-by-step access for tests and tools. ezo_batch_step runs one kernel of
  * the current round over the batch: 0 round size (a1), 1 hit-and-run (a2),
  * 2 collision labels (a3, a4), 3 certification and selection (a5, a6),
  * 4 projection and bisection (a7, a8), 5 hyperplane placement (a9), 6 round
@@ -305,6 +333,92 @@ ezo_status ezo_batch_read(const ezo_batch* batch, int32_t seg, int32_t what, voi
  * n x count dimension-major, count <= s_cap) so that a round can be replayed
  * on given samples; sets |S| to count. */
 ezo_status ezo_batch_write_samples(ezo_batch* batch, int32_t seg, const float* samples, int32_t count);
+
+/* ------------------------------------------------------- one-call inflation --
+ * The problem statement of Sec. IV-B (Algorithm 1): robot, obstacles, a
+ * collision-free segment L = conv{v1, v2}, the domain D and (eps, delta) in;
+ * a polytope P = {A x <= b} with L inside P out, which with probability at
+ * least 1 - delta has at most an eps fraction of its volume in collision.
+ * Path inflation (Sec. VI-A) inflates the segments of a piecewise-linear path
+ * in order and skips a segment whose endpoints lie in an earlier polytope of
+ * the path. Each call builds a batch (ezo_batch_create), runs it with the
+ * batch kernels, copies the results into host objects owned by the caller
+ * and frees the batch; it blocks until they are on the host. The device
+ * memory is allocated and freed inside the call.
+ *
+ * Per-polytope statistics (the segment's outcome and work). */
+typedef struct {
+  int32_t status;   /* ezo_segment_status: ACCEPTED, IN_COLLISION, CAPACITY or MAX_ITER */
+  int32_t rounds;   /* rounds of Algorithm 1 run */
+  int32_t m;        /* rows of A */
+  int32_t planes;   /* hyperplanes added to the domain */
+  int64_t checks;   /* exact collision checks (samples and bisection midpoints) */
+  int64_t checks_bisect;    /* of which at bisection midpoints */
+  int64_t surrogate_evals;  /* surrogate evaluations (0 without a surrogate) */
+} ezo_stats;
+
+typedef struct ezo_polytope ezo_polytope; /* host object: A (m x n, row major), b (m), stats */
+typedef struct ezo_scs ezo_scs;           /* sequence of polytopes of one path, in path order */
+
+/* Algorithm 1 on one segment: v1, v2 (host FP64, n values each); the domain
+ * D = {A0 x <= b0} (host FP64, m0 x n row major and m0 values), or the
+ * robot's joint-limit box when A0 = NULL (then m0 = 0); params as in
+ * ezo_batch_create; stream_id is the segment's Philox stream (the other
+ * counter words are the round and the walk), so the polytope equals that of
+ * the same segment in any batch with the same stream id. *out receives a new
+ * polytope (free it with ezo_polytope_free) whenever the call returns
+ * EZO_OK, EZO_ERR_SEGMENT_IN_COLLISION (the rows placed before the t_col rule
+ * fired; no region is certified), EZO_ERR_CAPACITY (no room for another N_f
+ * rows) or EZO_WARN_MAX_ITER (N_it rounds without acceptance; no
+ * guarantee); stats (nullable) receives its statistics. Other errors
+ * (EZO_ERR_INVALID_ARG, EZO_ERR_CUDA) leave *out NULL. */
+ezo_status ezo_inflate_segment(const ezo_robot* robot, const ezo_env* env, const double* v1, const double* v2,
+                               const double* A0, const double* b0, int32_t m0, const ezo_params* params,
+                               uint32_t stream_id, ezo_polytope** out, ezo_stats* stats, void* cuda_stream);
+
+/* Sec. VI-A on one path of n_verts vertices (host FP64, n_verts x n row
+ * major, n_verts >= 2): segment k = (verts[k], verts[k + 1]) draws from
+ * Philox stream stream_base + k. mode 0 runs the paper's order (one segment
+ * at a time, host launch loop); mode 1 ("wavefront") and mode 2 (every
+ * segment speculatively in one graph, the skip rule applied afterwards) keep
+ * the same polytopes. *out receives the path's sequence of convex sets: one
+ * polytope per segment that was inflated, in path order, each tagged with its
+ * segment index (ezo_polytope_stats); the path stops after a segment reported
+ * in collision. Returns the most severe outcome of its segments (an error
+ * before EZO_WARN_MAX_ITER before EZO_OK); *out is set for those outcomes as
+ * in ezo_inflate_segment. Free it with ezo_scs_free. */
+ezo_status ezo_inflate_path(const ezo_robot* robot, const ezo_env* env, const double* verts, int32_t n_verts,
+                            const double* A0, const double* b0, int32_t m0, const ezo_params* params, int32_t mode,
+                            uint32_t stream_base, ezo_scs** out, void* cuda_stream);
+
+/* Many paths over several obstacle sets at once (the batched form): path i
+ * has path_len[i] >= 1 segments, its path_len[i] + 1 vertices follow those of
+ * path i - 1 in verts (host FP64, row major), and it runs in obstacle set
+ * envs[path_env[i]] (path_env NULL: all in envs[0]). seg_np (nullable, one
+ * value per segment in path order) gives per-segment N_p. The segment with
+ * global index g (counting over all paths in order) draws from Philox stream
+ * stream_base + g. mode as in ezo_inflate_path; out (host array of n_path
+ * pointers) receives one sequence of convex sets per path. Returns the most
+ * severe outcome over all segments; on EZO_ERR_INVALID_ARG or EZO_ERR_CUDA
+ * every out[i] is NULL. */
+ezo_status ezo_inflate_batch(const ezo_robot* robot, int32_t n_env, const ezo_env* const* envs, int32_t n_path,
+                             const int32_t* path_len, const double* verts, const int32_t* path_env,
+                             const int32_t* seg_np, const double* A0, const double* b0, int32_t m0,
+                             const ezo_params* params, int32_t mode, uint32_t stream_base, ezo_scs** out,
+                             void* cuda_stream);
+
+/* Rows m and dimension n of a polytope, and (each nullable) A into a host
+ * buffer of m x n doubles (row major) and b into m doubles. */
+ezo_status ezo_polytope_get(const ezo_polytope* p, int32_t* m, int32_t* n, double* A, double* b);
+/* The segment index the polytope was inflated for (0 for ezo_inflate_segment,
+ * the index within its path otherwise) and its statistics; both nullable. */
+ezo_status ezo_polytope_stats(const ezo_polytope* p, int32_t* segment, ezo_stats* stats);
+void ezo_polytope_free(ezo_polytope* p);
+/* Number of polytopes of a sequence, polytope i (owned by the sequence; NULL
+ * when i is out of range), and freeing the sequence with its polytopes. */
+int32_t ezo_scs_size(const ezo_scs* scs);
+const ezo_polytope* ezo_scs_get(const ezo_scs* scs, int32_t i);
+void ezo_scs_free(ezo_scs* scs);
 
 /* ------------------------------------------------------------- recovery --
  * Sec. VI-B: a trajectory planned in the sets is checked at fine steps; the

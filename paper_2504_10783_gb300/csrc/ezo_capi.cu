@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <utility>
 #include <string>
@@ -603,6 +605,8 @@ struct ezo_batch {
   std::vector<double> v1h, v2h;
   BatchView view{};
   int T_check = 1, T_bisect = 4, split_below = 0;
+  long long tot_s1 = 0, tot_np = 0;  // samples of round 1 and N_p over the batch (tuning keys)
+  int sms = 1;
   int grid_sample = 1, grid_check = 1, grid_bisect = 1;
   // graph mode
   cudaGraph_t graph = nullptr;
@@ -987,6 +991,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   v.t_col = prm->t_col;
   v.key0 = (uint32_t)(prm->seed & 0xffffffffu);
   v.key1 = (uint32_t)(prm->seed >> 32);
+  v.keys = philox_keys(prm->seed);
   v.st = b->d_st;
   v.v1 = b->d_v1;
   v.v2 = b->d_v2;
@@ -1042,6 +1047,9 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   // walks share eight lanes in rounds with fewer walks than one warp per
   // scheduler would hold at one lane per walk
   b->split_below = (sms * 4 * 32) / kTile;
+  b->tot_s1 = tot_s1;
+  b->tot_np = tot_np;
+  b->sms = sms;
   b->grid_sample = std::max(1, std::min(b->max_sample_tiles * 8, sms * 16));
   b->grid_check = std::max(1, std::min(b->max_sample_tiles * b->T_check, sms * 16));
   b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * b->T_bisect, sms * 16));
@@ -1066,6 +1074,135 @@ ezo_status ezo_batch_set_sample_lanes(ezo_batch* b, int32_t lanes) {
     b->graph = nullptr;
   }
   b->view.sample_lanes = lanes;
+  return EZO_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+void apply_shape(ezo_batch* b, const ezo_shape& sh) {
+  b->split_below = sh.sample_fill_tiles;
+  b->T_check = sh.check_lanes;
+  b->T_bisect = sh.bisect_lanes;
+  b->grid_check = std::max(1, std::min(b->max_sample_tiles * b->T_check, b->sms * 16));
+  b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * b->T_bisect, b->sms * 16));
+  // a captured graph holds the old launch shapes
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+}
+
+int log2_class(long long x) {
+  int c = 0;
+  while ((1ll << c) < x && c < 48) ++c;
+  return c;
+}
+
+std::mutex g_shape_mu;
+std::map<std::vector<long long>, ezo_shape> g_shape_cache;
+
+}  // namespace
+
+extern "C" {
+
+ezo_status ezo_batch_get_shape(const ezo_batch* b, ezo_shape* sh) {
+  if (!b || !sh) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_get_shape: bad argument");
+  sh->sample_fill_tiles = b->split_below;
+  sh->check_lanes = b->T_check;
+  sh->bisect_lanes = b->T_bisect;
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_set_shape(ezo_batch* b, const ezo_shape* sh) {
+  if (!b || !sh) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_shape: bad argument");
+  auto lanes_ok = [](int t) { return t == 1 || t == 2 || t == 4 || t == 8; };
+  if (sh->sample_fill_tiles < 1 || !lanes_ok(sh->check_lanes) || !lanes_ok(sh->bisect_lanes))
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_shape: sample_fill_tiles >= 1, lanes 1, 2, 4 or 8");
+  apply_shape(b, *sh);
+  g_err.clear();
+  return EZO_OK;
+}
+
+ezo_status ezo_batch_tune(ezo_batch* b, int32_t reps, ezo_shape* chosen, void* stream_v) {
+  if (!b || reps < 1) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_tune: bad argument");
+  cudaStream_t s = (cudaStream_t)stream_v;
+  int dev = 0;
+  EZO_CUDA(cudaGetDevice(&dev));
+  std::vector<long long> key = {dev, b->n, b->robot->nsp_pad, b->robot->n_self, b->max_obs_pad, b->max_ebox,
+                                b->robot->n_box, log2_class(b->tot_s1), log2_class(b->tot_np), log2_class(b->B),
+                                b->prm.n_b, b->sur ? 1 : 0};
+  ezo_shape best{};
+  ezo_batch_get_shape(b, &best);
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    auto it = g_shape_cache.find(key);
+    if (it != g_shape_cache.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    cudaEvent_t e0, e1;
+    EZO_CUDA(cudaEventCreate(&e0));
+    EZO_CUDA(cudaEventCreate(&e1));
+    auto time_shape = [&](const ezo_shape& sh, float* out_ms) -> ezo_status {
+      apply_shape(b, sh);
+      float t = 1e30f;
+      for (int r = 0; r < reps + 1; ++r) {  // the first run warms up (module loading, caches)
+        ezo_status st = ezo_batch_reset(b, nullptr, nullptr, s);
+        if (st != EZO_OK) return st;
+        EZO_CUDA(cudaEventRecord(e0, s));
+        st = run_host_loop(b, s);
+        if (st != EZO_OK) return st;
+        EZO_CUDA(cudaEventRecord(e1, s));
+        EZO_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        EZO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) t = std::min(t, ms);
+      }
+      *out_ms = t;
+      return EZO_OK;
+    };
+    // coordinate search: bisection lanes, then label lanes, then the walks'
+    // fill threshold, each with the others at their current best
+    float best_ms = 1e30f;
+    ezo_status st = time_shape(best, &best_ms);
+    const int S = (b->sms * 4 * 32) / kTile;
+    const int bis[3] = {2, 4, 8}, chk[4] = {1, 2, 4, 8}, fill[3] = {std::max(1, S / 2), S, 2 * S};
+    for (int stage = 0; stage < 3 && st == EZO_OK; ++stage) {
+      const int* cand = stage == 0 ? bis : (stage == 1 ? chk : fill);
+      const int nc = stage == 1 ? 4 : 3;
+      for (int i = 0; i < nc && st == EZO_OK; ++i) {
+        ezo_shape sh = best;
+        if (stage == 0) sh.bisect_lanes = cand[i];
+        if (stage == 1) sh.check_lanes = cand[i];
+        if (stage == 2) sh.sample_fill_tiles = cand[i];
+        if (sh.bisect_lanes == best.bisect_lanes && sh.check_lanes == best.check_lanes &&
+            sh.sample_fill_tiles == best.sample_fill_tiles)
+          continue;
+        float ms = 0.f;
+        st = time_shape(sh, &ms);
+        if (st == EZO_OK && ms < 0.98f * best_ms) {  // a clear win only
+          best_ms = ms;
+          best = sh;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != EZO_OK) return st;
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    g_shape_cache[key] = best;
+  }
+  apply_shape(b, best);
+  ezo_status st = ezo_batch_reset(b, nullptr, nullptr, s);
+  if (st != EZO_OK) return st;
+  EZO_CUDA(cudaStreamSynchronize(s));
+  if (chosen) *chosen = best;
+  g_err.clear();
   return EZO_OK;
 }
 

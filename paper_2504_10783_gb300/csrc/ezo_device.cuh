@@ -48,6 +48,37 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The ten round keys of Philox4x32-10 for one seed: (k0 + r 0x9E3779B9,
+// k1 + r 0xBB67AE85) for r = 0..9, computed on the host and passed in kernel
+// parameters, so the rounds read them as constant operands.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys ks;
+  uint32_t a = (uint32_t)(seed & 0xffffffffu), b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    ks.k0[r] = a;
+    ks.k1[r] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return ks;
+}
+
+// philox4x32_10 with the round keys given (the same bits).
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const PhiloxKeys& ks) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+    c = u32x4{hi1 ^ c.y ^ ks.k0[r], lo1, hi0 ^ c.w ^ ks.k1[r], lo0};
+  }
+  return c;
+}
+
 // [0, 1): top 24 bits times 2^-24 (exact in FP32).
 __device__ __forceinline__ float u01_co(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-8f; }
 // (0, 1]: (top 24 bits + 1) times 2^-24 (exact in FP32).

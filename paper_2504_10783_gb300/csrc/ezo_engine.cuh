@@ -68,6 +68,7 @@ struct BatchView {
   int n_f, n_b, n_mix, n_it_max;
   double eps, delta, tau, step_back_max, t_col;
   uint32_t key0, key1;
+  PhiloxKeys keys;  // round keys of the seed (key0, key1)
   SegState* st;
   const double* v1;  // [B][n]
   const double* v2;  // [B][n]

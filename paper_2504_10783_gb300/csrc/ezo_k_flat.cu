@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(128) k_sample_flat(const double* __restrict__ 
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     float x[NDOF];
-    hnr_walk<NDOF>(A32, m, n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x);
+    hnr_walk<NDOF>(A32, m, n, p.v1f, p.ef, p.n_mix, p.keys, (uint32_t)i, p.round_k, p.stream, x);
 #pragma unroll
     for (int j = 0; j < NDOF; ++j)
       if (j < n) out[(long long)j * ldo + i] = x[j];
@@ -260,8 +260,7 @@ cudaError_t launch_sample_flat(const double* A, const double* b, int m, int lda,
     p.ef[j] = (float)(v2h[j] - v1h[j]);
   }
   p.n_mix = n_mix;
-  p.key0 = (uint32_t)(seed & 0xffffffffu);
-  p.key1 = (uint32_t)(seed >> 32);
+  p.keys = philox_keys(seed);
   p.stream = stream;
   p.round_k = (uint32_t)k;
   const int threads = 128;

@@ -123,11 +123,11 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
   float x[NDOF];
   if (TSS == 1) {
     if (i >= st.n_samples) return;
-    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)i, p.round_k, p.stream, x,
+    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, v.keys, (uint32_t)i, p.round_k, p.stream, x,
                    st.box_rows);
   } else {
     const int ic = i < st.n_samples ? i : tile.y;
-    hnr_walk_split<NDOF, TSS>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, p.key0, p.key1, (uint32_t)ic, p.round_k,
+    hnr_walk_split<NDOF, TSS>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, v.keys, (uint32_t)ic, p.round_k,
                               p.stream, lw, x, st.box_rows);
     if (i >= st.n_samples || lw != 0) return;
   }
@@ -174,8 +174,6 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
       }
       if (threadIdx.x == 0) {
         p.n_mix = v.n_mix;
-        p.key0 = v.key0;
-        p.key1 = v.key1;
         p.stream = st.stream;
         p.round_k = (uint32_t)st.k;
         cur_seg = tile.x;

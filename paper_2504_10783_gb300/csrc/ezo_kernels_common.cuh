@@ -20,7 +20,8 @@ struct SampleParams {
   float v1f[EZO_MAX_DOF];
   float ef[EZO_MAX_DOF];
   int n_mix;
-  uint32_t key0, key1, stream, round_k;
+  uint32_t stream, round_k;
+  PhiloxKeys keys;
 };
 
 // One hit-and-run walk of `n_mix` steps inside {x : A32 x <= b32}.
@@ -166,13 +167,13 @@ __device__ __forceinline__ void dup_pairs(const float (&x)[NDOF], const float (&
 
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
-                                         int n, const float* v1f, const float* ef, int n_mix, uint32_t key0,
-                                         uint32_t key1, uint32_t walk, uint32_t rk, uint32_t stream,
+                                         int n, const float* v1f, const float* ef, int n_mix,
+                                         const PhiloxKeys& ks, uint32_t walk, uint32_t rk, uint32_t stream,
                                          float (&x)[NDOF], int box_rows = 0) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
   const int npair = (n + 1) / 2;
   const int W = max(1, (2 * npair + 3) / 4);
-  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
+  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, ks);
   const float u0 = u01_co(r0.x);
 #pragma unroll
   for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
@@ -188,7 +189,7 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 #pragma unroll
     for (int b = 0; b < WMAX; ++b) {
       if (b < W) {
-        const u32x4 r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, key0, key1);
+        const u32x4 r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, ks);
         w[4 * b] = r.x;
         w[4 * b + 1] = r.y;
         w[4 * b + 2] = r.z;
@@ -238,14 +239,14 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
 // other walks share its round. All lanes of the warp must call this together.
 template <int NDOF, int TS>
 __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, int m, int n, const float* v1f,
-                                               const float* ef, int n_mix, uint32_t key0, uint32_t key1,
+                                               const float* ef, int n_mix, const PhiloxKeys& ks,
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
                                                float (&x)[NDOF], int box_rows = 0) {
   constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
   constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
   const int npair = (n + 1) / 2;
   const int W = max(1, (2 * npair + 3) / 4);
-  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, key0, key1);
+  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, ks);
   const float u0 = u01_co(r0.x);
 #pragma unroll
   for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
@@ -257,7 +258,7 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
     for (int bl = 0; bl < BPL; ++bl) {
       const int b = lw + bl * TS;
       u32x4 r = u32x4{0u, 0u, 0u, 0u};
-      if (b < W) r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, key0, key1);
+      if (b < W) r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, ks);
       const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
       for (int h = 0; h < 2; ++h) {

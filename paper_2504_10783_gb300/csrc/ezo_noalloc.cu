@@ -232,6 +232,7 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   v.t_col = prm->t_col;
   v.key0 = (uint32_t)(prm->seed & 0xffffffffu);
   v.key1 = (uint32_t)(prm->seed >> 32);
+  v.keys = philox_keys(prm->seed);
   v.st = d_st;
   v.v1 = d_v1;
   v.v2 = d_v2;

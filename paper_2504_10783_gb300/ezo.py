@@ -46,6 +46,14 @@ class Params(C.Structure):
         return p
 
 
+class Shape(C.Structure):
+    """Launch shapes of a batch's round kernels (ezo_shape)."""
+    _fields_ = [("sample_fill_tiles", C.c_int32), ("check_lanes", C.c_int32), ("bisect_lanes", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 _lib = None
 _P = C.c_void_p
 _I32 = C.c_int32
@@ -112,6 +120,24 @@ def _sig(lib):
     f.ezo_probe_fp32_fma.argtypes = [_DP, _P]
     f.ezo_check_flops.argtypes = [_P, _P]
     f.ezo_check_flops.restype = C.c_double
+    f.ezo_batch_get_shape.argtypes = [_P, C.POINTER(Shape)]
+    f.ezo_batch_set_shape.argtypes = [_P, C.POINTER(Shape)]
+    f.ezo_batch_tune.argtypes = [_P, _I32, C.POINTER(Shape), _P]
+    f.ezo_inflate_segment.argtypes = [_P, _P, _DP, _DP, _DP, _DP, _I32, C.POINTER(Params), C.c_uint32,
+                                      C.POINTER(_P), _P, _P]
+    f.ezo_inflate_path.argtypes = [_P, _P, _DP, _I32, _DP, _DP, _I32, C.POINTER(Params), _I32, C.c_uint32,
+                                   C.POINTER(_P), _P]
+    f.ezo_inflate_batch.argtypes = [_P, _I32, C.POINTER(_P), _I32, C.POINTER(_I32), _DP, C.POINTER(_I32),
+                                    C.POINTER(_I32), _DP, _DP, _I32, C.POINTER(Params), _I32, C.c_uint32,
+                                    C.POINTER(_P), _P]
+    f.ezo_polytope_get.argtypes = [_P, C.POINTER(_I32), C.POINTER(_I32), _DP, _DP]
+    f.ezo_polytope_stats.argtypes = [_P, C.POINTER(_I32), _P]
+    f.ezo_polytope_free.argtypes = [_P]
+    f.ezo_scs_size.argtypes = [_P]
+    f.ezo_scs_size.restype = _I32
+    f.ezo_scs_get.argtypes = [_P, _I32]
+    f.ezo_scs_get.restype = _P
+    f.ezo_scs_free.argtypes = [_P]
     f.ezo_sphere_centres.argtypes = [_P, _P, _I64, _I64, _I32, _P, _P]
     f.ezo_fk_error.argtypes = [_P, _P, _I64, _I64, _P, _P]
     return lib
@@ -523,6 +549,22 @@ class Batch:
             raise ValueError("which must have one entry per segment")
         _check(lib().ezo_batch_reinflate(self.h, w.ctypes.data_as(C.POINTER(C.c_uint8)), mode, _stream(stream)))
 
+    def shape(self) -> dict:
+        sh = Shape()
+        _check(lib().ezo_batch_get_shape(self.h, C.byref(sh)))
+        return sh.as_dict()
+
+    def set_shape(self, sample_fill_tiles: int, check_lanes: int, bisect_lanes: int):
+        sh = Shape(sample_fill_tiles, check_lanes, bisect_lanes)
+        _check(lib().ezo_batch_set_shape(self.h, C.byref(sh)))
+
+    def tune(self, reps: int = 2, stream=None) -> dict:
+        """Autotune the round kernels' launch shapes on this batch (cached per
+        problem class); leaves the batch reset."""
+        sh = Shape()
+        _check(lib().ezo_batch_tune(self.h, reps, C.byref(sh), _stream(stream)))
+        return sh.as_dict()
+
     def set_sample_lanes(self, lanes: int):
         """Lanes per hit-and-run walk (0 = chosen per round, else 1, 2, 4, 8)."""
         _check(lib().ezo_batch_set_sample_lanes(self.h, int(lanes)))
@@ -579,29 +621,109 @@ def check_flops(robot: Robot, env: Env) -> float:
     return float(lib().ezo_check_flops(robot.h, env.h))
 
 
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("rounds", C.c_int32), ("m", C.c_int32), ("planes", C.c_int32),
+                ("checks", C.c_int64), ("checks_bisect", C.c_int64), ("surrogate_evals", C.c_int64)]
+
+
+# outcomes for which the one-call entry points still return their polytopes
+_OUTCOMES = (EZO_OK, 2, 3, 6)
+
+
+def _polytope_result(p) -> SegmentResult:
+    m, n = _I32(), _I32()
+    _check(lib().ezo_polytope_get(p, C.byref(m), C.byref(n), None, None))
+    A = np.zeros((m.value, n.value))
+    b = np.zeros(m.value)
+    _check(lib().ezo_polytope_get(p, None, None, _dp(A), _dp(b)))
+    st = Stats()
+    _check(lib().ezo_polytope_stats(p, None, C.byref(st)))
+    return SegmentResult(st.status, st.rounds, st.m, st.planes, st.checks, A, b)
+
+
+def _domain(A0, b0):
+    if A0 is None:
+        return None, None, 0, []
+    A0 = np.ascontiguousarray(A0, dtype=np.float64)
+    b0 = np.ascontiguousarray(b0, dtype=np.float64)
+    return _dp(A0), _dp(b0), A0.shape[0], [A0, b0]
+
+
 def inflate_segment(robot: Robot, env: Env, v1, v2, params: Params, A0=None, b0=None, stream_id: int = 0,
-                    mode: int = RUN_HOST_LOOP) -> SegmentResult:
-    """Algorithm 1 on one segment (batch of one)."""
-    bt = Batch(robot, [env], v1, v2, params, seg_stream=[stream_id], A0=A0, b0=b0)
-    bt.run(mode)
-    return bt.segment(0)
+                    stream=None) -> SegmentResult:
+    """Algorithm 1 on one segment through ezo_inflate_segment; the domain is
+    {A0 x <= b0}, or the joint-limit box when A0 is None."""
+    v1 = np.ascontiguousarray(v1, dtype=np.float64)
+    v2 = np.ascontiguousarray(v2, dtype=np.float64)
+    Ap, bp, m0, keep = _domain(A0, b0)
+    out = _P()
+    st = lib().ezo_inflate_segment(robot.h, env.h, _dp(v1), _dp(v2), Ap, bp, m0, C.byref(params), stream_id,
+                                   C.byref(out), None, _stream(stream))
+    if st not in _OUTCOMES or not out.value:
+        _check(st)
+    try:
+        return _polytope_result(out)
+    finally:
+        lib().ezo_polytope_free(out)
 
 
-def inflate_path(robot: Robot, env: Env, verts, params: Params, sequential: bool = True, mode: int = RUN_HOST_LOOP,
-                 stream_base: int = 0, A0=None, b0=None):
-    """Sec. VI-A path inflation; returns [(segment index, SegmentResult)] for
-    the segments that were inflated (not skipped), in path order."""
-    verts = np.asarray(verts, dtype=np.float64)
-    K = verts.shape[0] - 1
-    bt = Batch(robot, [env], verts[:-1], verts[1:], params, seg_stream=np.arange(K) + stream_base,
-               path_first=np.zeros(K, dtype=np.int32), A0=A0, b0=b0)
-    bt.run_path(sequential=sequential, mode=mode)
+def _path_mode(sequential) -> int:
+    """sequential True/1: the paper's order (0), 2: wavefront (1), False/0:
+    speculative (2)."""
+    return 1 if sequential == 2 else (0 if sequential else 2)
+
+
+def _scs_results(scs):
     out = []
-    for k in range(K):
-        r = bt.segment(k)
-        if r.status not in (SEG_SKIPPED, SEG_IDLE):
-            out.append((k, r))
+    for i in range(lib().ezo_scs_size(scs)):
+        p = lib().ezo_scs_get(scs, i)
+        seg = _I32()
+        _check(lib().ezo_polytope_stats(p, C.byref(seg), None))
+        out.append((seg.value, _polytope_result(p)))
     return out
+
+
+def inflate_path(robot: Robot, env: Env, verts, params: Params, sequential=True, stream_base: int = 0, A0=None,
+                 b0=None, stream=None):
+    """Sec. VI-A path inflation through ezo_inflate_path; returns [(segment
+    index, SegmentResult)] for the segments that were inflated (not skipped),
+    in path order."""
+    verts = np.ascontiguousarray(verts, dtype=np.float64)
+    Ap, bp, m0, keep = _domain(A0, b0)
+    out = _P()
+    st = lib().ezo_inflate_path(robot.h, env.h, _dp(verts), verts.shape[0], Ap, bp, m0, C.byref(params),
+                                _path_mode(sequential), stream_base, C.byref(out), _stream(stream))
+    if st not in _OUTCOMES or not out.value:
+        _check(st)
+    try:
+        return _scs_results(out)
+    finally:
+        lib().ezo_scs_free(out)
+
+
+def inflate_batch(robot: Robot, envs, paths, params: Params, path_env=None, seg_np=None, sequential=2,
+                  stream_base: int = 0, A0=None, b0=None, stream=None):
+    """Many paths over several obstacle sets through ezo_inflate_batch:
+    paths is a list of vertex arrays [n_verts_i, n]; returns one list of
+    (segment index, SegmentResult) per path."""
+    envs = list(envs)
+    arr = (_P * len(envs))(*[e.h for e in envs])
+    verts = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in paths]), dtype=np.float64)
+    lens = np.ascontiguousarray([np.asarray(p).shape[0] - 1 for p in paths], dtype=np.int32)
+    pe = None if path_env is None else np.ascontiguousarray(path_env, dtype=np.int32)
+    sn = None if seg_np is None else np.ascontiguousarray(seg_np, dtype=np.int32)
+    Ap, bp, m0, keep = _domain(A0, b0)
+    out = (_P * len(paths))()
+    st = lib().ezo_inflate_batch(robot.h, len(envs), arr, len(paths), _ip(lens), _dp(verts),
+                                 _ip(pe) if pe is not None else None, _ip(sn) if sn is not None else None, Ap, bp,
+                                 m0, C.byref(params), _path_mode(sequential), stream_base, out, _stream(stream))
+    if st not in _OUTCOMES or not out[0]:
+        _check(st)
+    try:
+        return [_scs_results(out[i]) for i in range(len(paths))]
+    finally:
+        for i in range(len(paths)):
+            lib().ezo_scs_free(out[i])
 
 
 class Surrogate:

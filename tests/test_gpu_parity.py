@@ -629,10 +629,12 @@ def test_inflate_path_sequential_equals_speculative(ezo):
     robot, env = ezo.Robot(rd), ezo.Env(env_np)
     prm = ezo.Params.make(n_p=3000, seed=7)
     seq = ezo.inflate_path(robot, env, path, prm, sequential=True)
-    spec = ezo.inflate_path(robot, env, path, prm, sequential=False, mode=ezo.RUN_GRAPH)
-    assert [k for k, _ in seq] == [k for k, _ in spec]
-    for (_, a), (_, b) in zip(seq, spec):
+    spec = ezo.inflate_path(robot, env, path, prm, sequential=False)
+    wave = ezo.inflate_path(robot, env, path, prm, sequential=2)
+    assert [k for k, _ in seq] == [k for k, _ in spec] == [k for k, _ in wave]
+    for (_, a), (_, b), (_, c) in zip(seq, spec, wave):
         np.testing.assert_array_equal(a.A, b.A)
+        np.testing.assert_array_equal(a.A, c.A)
     K = path.shape[0] - 1
     for k in range(K):
         assert any(orc.segment_contained(r.A, r.b, path[k], path[k + 1]) for _, r in seq)
@@ -779,3 +781,126 @@ def test_sphere_centres_and_fk_error_against_oracle(ezo, which):
     np.testing.assert_allclose(err.cpu().numpy(), np.linalg.norm(g32 - g64, axis=2).max(axis=1), rtol=1e-6,
                                atol=1e-12)
     print(f"{which}: FP32 kinematics error max {d32.max():.2e} m, p99 {np.quantile(d32, 0.99):.2e} m")
+
+
+# ---------------------------------------------- one-call entry points (C ABI) --
+def test_one_call_segment_equals_batch_and_keeps_its_domain(ezo):
+    """ezo_inflate_segment (Algorithm 1 in one call) against a one-segment
+    batch with the same stream, bit for bit, from the joint box and from a
+    caller's domain D (the joint box cut by one plane that keeps the
+    segment); the result contains the segment and keeps D's rows."""
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(n_p=3000, seed=12)
+    A0, b0 = orc.joint_box(rd)
+    a = np.zeros(7)
+    a[0] = 1.0
+    A1 = np.vstack([A0, a])
+    b1 = np.concatenate([b0, [max(path[2][0], path[3][0]) + 0.3]])
+    for dom in (None, (A1, b1)):
+        kw = {} if dom is None else dict(A0=dom[0], b0=dom[1])
+        one = ezo.inflate_segment(robot, env, path[2], path[3], prm, stream_id=5, **kw)
+        bt = ezo.Batch(robot, [env], path[2], path[3], prm, seg_stream=[5], **kw)
+        bt.run()
+        ref = bt.segment(0)
+        assert (one.status, one.rounds, one.planes, one.checks) == (ref.status, ref.rounds, ref.planes, ref.checks)
+        np.testing.assert_array_equal(one.A, ref.A)
+        np.testing.assert_array_equal(one.b, ref.b)
+        assert one.status == ezo.SEG_ACCEPTED
+        assert orc.segment_contained(one.A, one.b, path[2], path[3], tol=1e-12)
+        D = A0 if dom is None else dom[0]
+        np.testing.assert_array_equal(one.A[: D.shape[0]], D)
+
+
+def test_one_call_path_and_batch(ezo):
+    """ezo_inflate_path in its three modes and ezo_inflate_batch over three
+    paths in two obstacle sets with per-segment N_p, against batches built
+    segment by segment with the same streams (bit for bit), with the oracle's
+    skip rule (Sec. VI-A) and coverage of every seed segment."""
+    sc = scenes()["dh7_batched"]
+    rd = wl.dh7_robot()
+    robot = ezo.Robot(rd)
+    use = [p for p in sc["paths"] if 3 <= len(p["path"]) <= 5][:3]
+    env_ids = sorted({p["env"] for p in use})[:2]
+    use = [p for p in use if p["env"] in env_ids]
+    envs_np = [wl.box_obstacles(sc["envs"][e]["env_seed"], sc["envs"][e]["n_obs"]) for e in env_ids]
+    envs = [ezo.Env(e) for e in envs_np]
+    prm = ezo.Params.make(n_p=2000, n_mix=30, seed=4)
+    paths = [np.asarray(p["path"]) for p in use]
+    pe = [env_ids.index(p["env"]) for p in use]
+    nseg = [p.shape[0] - 1 for p in paths]
+    seg_np = np.asarray([1000 + 500 * (g % 3) for g in range(sum(nseg))], np.int32)
+    got = ezo.inflate_batch(robot, envs, paths, prm, path_env=pe, seg_np=seg_np, sequential=2, stream_base=40)
+    # the same segments as one batch (wavefront mode)
+    v1 = np.concatenate([p[:-1] for p in paths])
+    v2 = np.concatenate([p[1:] for p in paths])
+    first = np.concatenate([[sum(nseg[:i])] * nseg[i] for i in range(len(paths))]).astype(np.int32)
+    seg_env = np.concatenate([[pe[i]] * nseg[i] for i in range(len(paths))]).astype(np.int32)
+    bt = ezo.Batch(robot, envs, v1, v2, prm, seg_env=seg_env, seg_np=seg_np, path_first=first,
+                   seg_stream=np.arange(40, 40 + v1.shape[0], dtype=np.uint32))
+    bt.run_path(sequential=2, mode=ezo.RUN_GRAPH)
+    for i, p in enumerate(paths):
+        g0 = int(sum(nseg[:i]))
+        kept = []
+        for k in range(nseg[i]):
+            r = bt.segment(g0 + k)
+            if r.status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE):
+                kept.append((k, r))
+        assert [k for k, _ in got[i]] == [k for k, _ in kept]
+        for (_, a), (_, b) in zip(got[i], kept):
+            np.testing.assert_array_equal(a.A, b.A)
+            np.testing.assert_array_equal(a.b, b.b)
+        # the oracle's skip rule on these polytopes, and coverage
+        okept = []
+        for k in range(nseg[i]):
+            if not any(orc.segment_contained(r.A, r.b, p[k], p[k + 1]) for _, r in okept):
+                okept.append((k, dict(got[i])[k]))
+        assert [k for k, _ in okept] == [k for k, _ in got[i]]
+        assert orc.path_coverage([(r.A, r.b) for _, r in got[i]], p).all()
+    # one path through ezo_inflate_path: the three modes agree with each other
+    # and with the batch call's first path
+    outs = [ezo.inflate_path(robot, envs[pe[0]], paths[0], prm, sequential=s_, stream_base=40) for s_ in (True, 2, False)]
+    for o in outs:
+        assert [k for k, _ in o] == [k for k, _ in outs[0]]
+        for (_, a), (_, b) in zip(o, outs[0]):
+            np.testing.assert_array_equal(a.A, b.A)
+    with pytest.raises(ezo.EzoError):
+        ezo.inflate_path(robot, envs[0], paths[0][:1], prm)
+
+
+def test_round_kernel_shapes_are_bit_identical_and_tuned(ezo):
+    """Every launch shape of the round kernels (the walks' lane rule, label
+    lanes, bisection lanes) gives the same polytopes bit for bit; the
+    autotuner picks one of them and the result is unchanged."""
+    rd, env_np, path = dh7_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    K = 4
+    prm = ezo.Params.make(n_p=3000, seed=14)
+    bt = ezo.Batch(robot, [env], path[:K], path[1:K + 1], prm, seg_stream=np.arange(K, dtype=np.uint32))
+    base = bt.shape()
+    S = base["sample_fill_tiles"]
+
+    def run():
+        bt.reset()
+        bt.run(ezo.RUN_GRAPH)
+        return [bt.segment(g) for g in range(K)]
+
+    ref = run()
+    for sh in ((1, 1, 2), (S // 2, 4, 4), (2 * S, 8, 1), (100000, 2, 8)):
+        bt.set_shape(*sh)
+        got = run()
+        for a, b in zip(got, ref):
+            assert (a.status, a.rounds, a.checks) == (b.status, b.rounds, b.checks), sh
+            np.testing.assert_array_equal(a.A, b.A)
+            np.testing.assert_array_equal(a.b, b.b)
+    with pytest.raises(ezo.EzoError):
+        bt.set_shape(S, 3, 8)
+    tuned = bt.tune(reps=1)
+    assert tuned["check_lanes"] in (1, 2, 4, 8) and tuned["bisect_lanes"] in (2, 4, 8)
+    assert bt.shape() == tuned
+    got = run()
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a.A, b.A)
+    # a second batch of the same class takes the cached shape
+    bt2 = ezo.Batch(robot, [env], path[:K], path[1:K + 1], prm, seg_stream=np.arange(K, dtype=np.uint32))
+    assert bt2.tune(reps=1) == tuned
