@@ -88,33 +88,33 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
         // verify the surrogate's end point with one exact check
         hi = (double)v.s_hi[row];
         bits = v.s_bits[row];
-        float qq[NDOF];
-#pragma unroll
-        for (int j = 0; j < NDOF; ++j) qq[j] = fmaf((float)hi, dv32[j], p32[j]);
-        const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
-                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
-        if (valid && lg == 0) {
-          v.s_ok[row] = hit ? 1 : 0;
-          atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), 1ull);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), 1ull);
-        }
-        if (!hit) valid = false;  // no output: the exact pass (mode 2) redoes this candidate
       } else if (v.bis_mode == 2 && valid && lg == 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), (unsigned long long)v.n_b);
         atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), (unsigned long long)v.n_b);
       }
-      for (int s = 0; s < (v.bis_mode == 1 ? 0 : v.n_b); ++s) {
-        const double mid = 0.5 * (lo + hi);
+      // one call site of the collision test for both modes keeps the kernel
+      // small enough for the instruction cache: the end point's check (mode
+      // 1) or the N_b halvings
+      const int steps = v.bis_mode == 1 ? 1 : v.n_b;
+      for (int s = 0; s < steps; ++s) {
+        const double f = v.bis_mode == 1 ? hi : 0.5 * (lo + hi);
         float qq[NDOF];
 #pragma unroll
-        for (int j = 0; j < NDOF; ++j) qq[j] = fmaf((float)mid, dv32[j], p32[j]);
+        for (int j = 0; j < NDOF; ++j) qq[j] = fmaf((float)f, dv32[j], p32[j]);
         const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
                                                 robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
-        if (hit) {
-          hi = mid;
+        if (v.bis_mode == 1) {
+          if (valid && lg == 0) {
+            v.s_ok[row] = hit ? 1 : 0;
+            atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), 1ull);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), 1ull);
+          }
+          if (!hit) valid = false;  // no output: the exact pass (mode 2) redoes this candidate
+        } else if (hit) {
+          hi = f;
           bits |= 1u << s;
         } else {
-          lo = mid;
+          lo = f;
         }
       }
       if (valid && lg == 0) {
