@@ -537,7 +537,8 @@ ezo_status ezo_profile_read(double* ms, int64_t* launches, int32_t n_kinds);
  * the accumulators in tensor memory and SiLU on the hardware tanh
  * approximation, relative error ~2^-11 before the BF16 rounding of each
  * activation); weights have FP32 masters trained with Adam
- * (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the mean squared error. It
+ * (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the mean squared error,
+ * every hidden-layer product of training on tcgen05 tensor cores too. It
  * only orders and prefilters bisection candidates (ezo_batch_attach_surrogate);
  * labels and certification stay exact.
  * Parameters are one flat FP32 vector of ezo_surrogate_num_params() values:
@@ -568,9 +569,10 @@ ezo_status ezo_surrogate_grad(ezo_surrogate* sur, const float* q_dev, int64_t ld
                               float* grad, float* loss, void* cuda_stream);
 ezo_status ezo_surrogate_predict(ezo_surrogate* sur, const float* q_dev, int64_t ldq, int64_t N, float* out_dev,
                                  void* cuda_stream);
-/* Health of the tensor-core forward pass: every wait inside it is bounded
- * (about 2 s); a wait that gave up writes NaN for the rows not finished and
- * sets a flag on the device. *timed_out receives that flag (0 or 1) after the
+/* Health of the tensor-core kernels (the forward pass and the training
+ * GEMMs): every wait inside them is bounded (about 2 s); a wait that gave up
+ * sets a flag on the device, and the forward pass writes NaN for the rows it
+ * did not finish. *timed_out receives that flag (0 or 1) after the
  * work queued on cuda_stream has finished; reset != 0 clears it.
  * Synchronous. EZO_ERR_INVALID_ARG for NULL arguments. */
 ezo_status ezo_surrogate_status(ezo_surrogate* sur, int32_t* timed_out, int32_t reset, void* cuda_stream);

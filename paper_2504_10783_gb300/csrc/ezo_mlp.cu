@@ -5,10 +5,12 @@
 // certification sample is still checked exactly.
 //
 // Weights are kept in FP32 (master, Adam moments) and in BF16 copies that
-// feed the tensor cores: every hidden-layer product is a BF16 x BF16 -> FP32
-// GEMM on mma.sync m16n8k16 with ldmatrix fragment loads, bias/SiLU (forward)
-// and SiLU' (backward) fused into the epilogue. The output layer (H -> 1) and
-// the reductions are small CUDA-core kernels.
+// feed the tensor cores: every hidden-layer product of training is a
+// BF16 x BF16 -> FP32 GEMM on tcgen05.mma with the accumulator in tensor
+// memory (ezo_mlp_gemm_tc.cu), bias/SiLU (forward) and SiLU' (backward) fused
+// into its epilogue; inference runs the whole network in one tensor-core
+// kernel (ezo_mlp_tc.cu). The output layer (H -> 1), the column sums and Adam
+// are small CUDA-core kernels.
 //
 // GEMM convention ("NT"): C[M x N] = A[M x K] B[N x K]^T, both operands
 // K-contiguous (row-major with leading dimensions lda, ldb). Forward
@@ -25,6 +27,7 @@
 
 #include "../../include/ezo.h"
 #include "ezo_engine.cuh"
+#include "ezo_mlp.cuh"
 
 namespace ezo {
 
@@ -41,27 +44,7 @@ cudaError_t mlp_tc_bisect(int n, long long rows_cap, const int* m_dev, const voi
 
 constexpr int kF = 64;   // padded input features
 constexpr int kH = 256;  // hidden width
-constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8;
 
-enum Epi : int {
-  EPI_F32 = 0,        // C (FP32) = acc
-  EPI_BIAS_SILU = 1,  // Z = acc + bias (FP32), H = SiLU(Z) (BF16, and transposed)
-  EPI_DSILU = 2       // D = acc * SiLU'(Z) (BF16, and transposed)
-};
-
-struct GemmArgs {
-  const __nv_bfloat16* A;
-  const __nv_bfloat16* B;
-  int M, N, K, lda, ldb;
-  const int* m_dev;  // optional device row count (rows >= *m_dev are skipped)
-  float* C;          // EPI_F32 output, ldc
-  int ldc;
-  const float* bias;
-  float* Z;          // EPI_BIAS_SILU: pre-activation out; EPI_DSILU: pre-activation in (ldz = N)
-  __nv_bfloat16* H;  // BF16 output, row-major (ldh = N)
-  __nv_bfloat16* Ht; // BF16 output, transposed [N x ldt]
-  int ldt;
-};
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z) {
@@ -69,117 +52,38 @@ __device__ __forceinline__ float dsilu(float z) {
   return s * (1.f + z * (1.f - s));
 }
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* smem_row) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// 64 x 64 block tile, 4 warps of 32 x 32 (2 m16 x 4 n8 mma tiles each), K in
-// steps of 32 staged through shared memory (rows padded by 8 BF16 so the
-// eight 16-byte rows of an ldmatrix hit distinct banks).
-// Persistent over M tiles: block (x, y) takes M tiles x, x + gridDim.x, ..
-// below the row count (device-side when m_dev is set, so a graph launched
-// with a fixed grid does no work for absent rows).
-template <int EPI>
-__global__ void __launch_bounds__(128) k_gemm_nt(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[kBM][kBK + kPad];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kBK + kPad];
-  const int m_lim = g.m_dev ? min(g.M, *g.m_dev) : g.M;
-  const int n0 = blockIdx.y * kBN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int m0 = blockIdx.x * kBM; m0 < m_lim; m0 += gridDim.x * kBM) {
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-  #pragma unroll
-    for (int i = 0; i < 2; ++i)
-  #pragma unroll
-      for (int j = 0; j < 4; ++j)
-  #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    for (int k0 = 0; k0 < g.K; k0 += kBK) {
-      // 64 rows x 32 BF16 = 64 x 4 chunks of 16 bytes per operand, 2 per thread
-  #pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const int c = threadIdx.x + it * 128;
-        const int r = c >> 2, q = (c & 3) * 8;
-        const int gm = m0 + r, gn = n0 + r;
-        uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-        if (gm < m_lim) va = *reinterpret_cast<const uint4*>(g.A + (long long)gm * g.lda + k0 + q);
-        if (gn < g.N) vb = *reinterpret_cast<const uint4*>(g.B + (long long)gn * g.ldb + k0 + q);
-        *reinterpret_cast<uint4*>(&As[r][q]) = va;
-        *reinterpret_cast<uint4*>(&Bs[r][q]) = vb;
-      }
-      __syncthreads();
-  #pragma unroll
-      for (int kk = 0; kk < kBK; kk += 16) {
-        uint32_t af[2][4];
-  #pragma unroll
-        for (int i = 0; i < 2; ++i) ldmatrix_x4(af[i], &As[wm + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-        uint32_t bf[2][4];
-  #pragma unroll
-        for (int j = 0; j < 2; ++j)
-          ldmatrix_x4(bf[j], &Bs[wn + j * 16 + (lane & 7) + ((lane >> 4) << 3)][kk + ((lane >> 3) & 1) * 8]);
-  #pragma unroll
-        for (int i = 0; i < 2; ++i)
-  #pragma unroll
-          for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j >> 1][(j & 1) * 2], bf[j >> 1][(j & 1) * 2 + 1]);
-      }
-      __syncthreads();
-    }
-    // epilogue: fragment element e of tile (i, j) is row wm+16i+lane/4 (+8 for
-    // e >= 2), column wn+8j+2(lane%4) (+1 for odd e)
-  #pragma unroll
-    for (int i = 0; i < 2; ++i)
-  #pragma unroll
-      for (int j = 0; j < 4; ++j)
-  #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = m0 + wm + i * 16 + (lane >> 2) + (e >= 2 ? 8 : 0);
-          const int c = n0 + wn + j * 8 + (lane & 3) * 2 + (e & 1);
-          if (r >= m_lim || c >= g.N) continue;
-          const float v = acc[i][j][e];
-          if (EPI == EPI_F32) {
-            g.C[(long long)r * g.ldc + c] = v;
-          } else if (EPI == EPI_BIAS_SILU) {
-            const float z = v + g.bias[c];
-            const __nv_bfloat16 h = __float2bfloat16(silu(z));
-            g.H[(long long)r * g.N + c] = h;
-            g.Z[(long long)r * g.N + c] = z;
-            g.Ht[(long long)c * g.ldt + r] = h;
-          } else {
-            const float d = v * dsilu(g.Z[(long long)r * g.N + c]);
-            const __nv_bfloat16 h = __float2bfloat16(d);
-            g.H[(long long)r * g.N + c] = h;
-            g.Ht[(long long)c * g.ldt + r] = h;
-          }
-        }
-  }
-}
-
 // ------------------------------------------------------------ small kernels --
 // features of configuration i: sin q_j, cos q_j (j < n), zero padding to kF;
-// row-major [rows x kF] and transposed [kF x ldt]
-__global__ void k_features(const float* __restrict__ q, long long ldq, int n, long long N,
-                           __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ Xt, int ldt) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    for (int f = 0; f < kF; ++f) {
+// row-major [rows x kF] and transposed [kF x ldt]. A block takes 64 rows at a
+// time through a shared-memory tile, so both outputs are written along their
+// contiguous dimension.
+__global__ void __launch_bounds__(256) k_features(const float* __restrict__ q, long long ldq, int n, long long N,
+                                                  __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ Xt,
+                                                  int ldt) {
+  __shared__ float tile[64][kF + 1];
+  for (long long r0 = (long long)blockIdx.x * 64; r0 < N; r0 += (long long)gridDim.x * 64) {
+    for (int e = threadIdx.x; e < 64 * kF; e += blockDim.x) {
+      const int rr = e & 63, f = e >> 6;
+      const long long i = r0 + rr;
       float v = 0.f;
-      if (f < n) v = sinf(q[(long long)f * ldq + i]);
-      else if (f < 2 * n) v = cosf(q[(long long)(f - n) * ldq + i]);
-      const __nv_bfloat16 h = __float2bfloat16(v);
-      X[i * kF + f] = h;
-      if (Xt) Xt[(long long)f * ldt + i] = h;
+      if (i < N) {
+        if (f < n) v = sinf(q[(long long)f * ldq + i]);
+        else if (f < 2 * n) v = cosf(q[(long long)(f - n) * ldq + i]);
+      }
+      tile[rr][f] = v;
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * kF; e += blockDim.x) {
+      const int rr = e / kF, f = e % kF;
+      if (r0 + rr < N) X[(r0 + rr) * kF + f] = __float2bfloat16(tile[rr][f]);
+    }
+    if (Xt) {
+      for (int e = threadIdx.x; e < 64 * kF; e += blockDim.x) {
+        const int f = e >> 6, rr = e & 63;
+        if (r0 + rr < N) Xt[(long long)f * ldt + r0 + rr] = __float2bfloat16(tile[rr][f]);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -266,10 +170,20 @@ __global__ void k_rowsum(const __nv_bfloat16* __restrict__ Mt, int rows, int N, 
 }
 
 // Adam on FP32 masters (Kingma and Ba, 2015, Algorithm 1) and the BF16
-// copies the GEMMs read: W [rows x cols] and its transpose.
-__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       long long count, float lr, float b1, float b2, float eps, float c1, float c2,
-                       __nv_bfloat16* __restrict__ W, __nv_bfloat16* __restrict__ Wt, int rows, int cols) {
+// copies the GEMMs read, over the whole flat parameter vector in one launch:
+// segment k covers
+// [begin[k], end[k]); a segment with a matrix W (rows x cols, row major) also
+// receives the BF16 copy of the new value, and its transpose when Wt is set.
+struct AdamSegs {
+  long long begin[6], end[6];
+  __nv_bfloat16* W[6];
+  __nv_bfloat16* Wt[6];
+  int rows[6], cols[6];
+};
+
+__global__ void k_adam_all(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                           float* __restrict__ v, long long count, float lr, float b1, float b2, float eps, float c1,
+                           float c2, AdamSegs segs) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -278,11 +192,14 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     v[i] = vi;
     const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     p[i] = pi;
-    if (W) {
-      const int r = (int)(i / cols), c = (int)(i % cols);
+    int k = 0;
+    while (k < 5 && i >= segs.end[k]) ++k;
+    if (segs.W[k]) {
+      const long long j = i - segs.begin[k];
+      const int r = (int)(j / segs.cols[k]), c = (int)(j % segs.cols[k]);
       const __nv_bfloat16 h = __float2bfloat16(pi);
-      W[i] = h;
-      if (Wt) Wt[(long long)c * rows + r] = h;
+      segs.W[k][j] = h;
+      if (segs.Wt[k]) segs.Wt[k][(long long)c * segs.rows[k] + r] = h;
     }
   }
 }
@@ -354,6 +271,7 @@ struct ezo_surrogate {
                 *H3 = nullptr, *H3t = nullptr, *dZ3 = nullptr, *dZ3t = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
                 *dZ1 = nullptr, *dZ1t = nullptr;
   float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *loss = nullptr;
+  float* ws = nullptr;  // partial products of the weight gradients (K split over blocks)
   // inference: the swizzled weight image of the tensor-core forward kernel
   // and its error flag
   void* wimg = nullptr;
@@ -364,23 +282,11 @@ namespace {
 
 using namespace ezo;
 
-cudaError_t gemm(int epi, const GemmArgs& a, cudaStream_t s) {
-  // M tiles on x, at most a few waves of blocks (the kernel loops over the rest)
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int n_tiles = (a.N + kBN - 1) / kBN;
-  const long long m_tiles = (a.M + kBM - 1) / kBM;
-  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(m_tiles, (long long)sms * 16 / n_tiles + 1)), n_tiles);
-  switch (epi) {
-    case EPI_F32: k_gemm_nt<EPI_F32><<<grid, 128, 0, s>>>(a); break;
-    case EPI_BIAS_SILU: k_gemm_nt<EPI_BIAS_SILU><<<grid, 128, 0, s>>>(a); break;
-    default: k_gemm_nt<EPI_DSILU><<<grid, 128, 0, s>>>(a); break;
-  }
-  return cudaGetLastError();
+// every hidden-layer product of training on the tensor cores (tcgen05, FP32
+// accumulators in tensor memory); the weight gradients split the batch
+// dimension over blocks and add the partial products in a fixed order
+cudaError_t gemm(ezo_surrogate* S, int epi, const GemmArgs& a, cudaStream_t s) {
+  return gemm_tc(epi, a, epi == EPI_F32 ? S->ws : nullptr, S->tc_err, s);
 }
 
 int blocks_for(long long n, int t) { return (int)std::max<long long>(1, std::min<long long>((n + t - 1) / t, 4096)); }
@@ -406,8 +312,11 @@ cudaError_t ensure_train_cap(ezo_surrogate* S, int B) {
   cudaFree(S->Z2);
   cudaFree(S->Z3);
   cudaFree(S->y);
+  cudaFree(S->ws);
+  S->ws = nullptr;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 14 && e == cudaSuccess; ++i) e = dal(bufs[i], (size_t)B * (i < 2 ? kF : kH));
+  if (e == cudaSuccess) e = dal(&S->ws, gemm_tc_ws_floats(kH, kH, B));
   if (e == cudaSuccess) e = dal(&S->Z1, (size_t)B * kH);
   if (e == cudaSuccess) e = dal(&S->Z2, (size_t)B * kH);
   if (e == cudaSuccess) e = dal(&S->Z3, (size_t)B * kH);
@@ -423,18 +332,18 @@ cudaError_t train_grad(ezo_surrogate* S, const float* q, long long ldq, const fl
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(S->g, 0, sizeof(float) * kNumParams, s);
   cudaMemsetAsync(S->loss, 0, sizeof(float), s);
-  k_features<<<blocks_for(B, 256), 256, 0, s>>>(q, ldq, S->n, B, S->X, S->Xt, B);
+  k_features<<<blocks_for(B, 64), 256, 0, s>>>(q, ldq, S->n, B, S->X, S->Xt, B);
   GemmArgs a{};
   a.M = B;
   a.N = kH;
   a.ldt = B;
   // forward
   a.A = S->X; a.lda = kF; a.B = S->W1; a.ldb = kF; a.K = kF; a.bias = S->p + kOffB1; a.Z = S->Z1; a.H = S->H1; a.Ht = S->H1t;
-  if ((e = gemm(EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
   a.A = S->H1; a.lda = kH; a.B = S->W2; a.ldb = kH; a.K = kH; a.bias = S->p + kOffB2; a.Z = S->Z2; a.H = S->H2; a.Ht = S->H2t;
-  if ((e = gemm(EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
   a.A = S->H2; a.B = S->W3; a.bias = S->p + kOffB3; a.Z = S->Z3; a.H = S->H3; a.Ht = S->H3t;
-  if ((e = gemm(EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
   k_out<<<blocks_for((long long)B * 32, 256), 256, 0, s>>>(S->H3, S->p + kOffW4, S->p + kOffB4, B, nullptr, S->y);
   // backward
   k_out_backward<<<std::min(256, blocks_for((long long)B * 32, 256)), 256, 0, s>>>(
@@ -442,21 +351,21 @@ cudaError_t train_grad(ezo_surrogate* S, const float* q, long long ldq, const fl
   GemmArgs w{};
   // dW3 = dZ3^T H2, db3 = column sums of dZ3
   w.A = S->dZ3t; w.lda = B; w.B = S->H2t; w.ldb = B; w.M = kH; w.N = kH; w.K = B; w.C = S->g + kOffW3; w.ldc = kH;
-  if ((e = gemm(EPI_F32, w, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_F32, w, s)) != cudaSuccess) return e;
   k_rowsum<<<kH, 256, 0, s>>>(S->dZ3t, kH, B, S->g + kOffB3);
   // dZ2 = (dZ3 W3) * SiLU'(Z2)
   GemmArgs d{};
   d.M = B; d.N = kH; d.K = kH; d.ldt = B;
   d.A = S->dZ3; d.lda = kH; d.B = S->W3t; d.ldb = kH; d.Z = S->Z2; d.H = S->dZ2; d.Ht = S->dZ2t;
-  if ((e = gemm(EPI_DSILU, d, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_DSILU, d, s)) != cudaSuccess) return e;
   w.A = S->dZ2t; w.B = S->H1t; w.C = S->g + kOffW2;
-  if ((e = gemm(EPI_F32, w, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_F32, w, s)) != cudaSuccess) return e;
   k_rowsum<<<kH, 256, 0, s>>>(S->dZ2t, kH, B, S->g + kOffB2);
   d.A = S->dZ2; d.B = S->W2t; d.Z = S->Z1; d.H = S->dZ1; d.Ht = S->dZ1t;
-  if ((e = gemm(EPI_DSILU, d, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_DSILU, d, s)) != cudaSuccess) return e;
   // dW1 = dZ1^T X
   w.A = S->dZ1t; w.B = S->Xt; w.N = kF; w.C = S->g + kOffW1; w.ldc = kF;
-  if ((e = gemm(EPI_F32, w, s)) != cudaSuccess) return e;
+  if ((e = gemm(S, EPI_F32, w, s)) != cudaSuccess) return e;
   k_rowsum<<<kH, 256, 0, s>>>(S->dZ1t, kH, B, S->g + kOffB1);
   return cudaGetLastError();
 }
@@ -465,17 +374,19 @@ cudaError_t adam_step(ezo_surrogate* S, float lr, cudaStream_t s) {
   S->step += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = 1.f - std::pow(b1, (float)S->step), c2 = 1.f - std::pow(b2, (float)S->step);
-  struct T {
-    long long off, count;
-    __nv_bfloat16 *W, *Wt;
-    int rows, cols;
-  } ts[] = {{kOffW1, (long long)kH * kF, S->W1, nullptr, kH, kF}, {kOffB1, kH, nullptr, nullptr, 0, 1},
-            {kOffW2, (long long)kH * kH, S->W2, S->W2t, kH, kH},   {kOffB2, kH, nullptr, nullptr, 0, 1},
-            {kOffW3, (long long)kH * kH, S->W3, S->W3t, kH, kH},   {kOffB3, kH, nullptr, nullptr, 0, 1},
-            {kOffW4, kH + 1, nullptr, nullptr, 0, 1}};
-  for (auto& t : ts)
-    k_adam<<<blocks_for(t.count, 256), 256, 0, s>>>(S->p + t.off, S->g + t.off, S->m + t.off, S->v + t.off, t.count, lr,
-                                                    b1, b2, eps, c1, c2, t.W, t.Wt, t.rows, t.cols);
+  // one launch over the flat parameter vector; the BF16 copies (and
+  // transposes) of W1..W3 are refreshed on the way
+  AdamSegs segs{};
+  segs.end[0] = kOffB1;  segs.W[0] = S->W1; segs.Wt[0] = nullptr; segs.rows[0] = kH; segs.cols[0] = kF;
+  segs.end[1] = kOffW2;  segs.W[1] = nullptr;
+  segs.end[2] = kOffB2;  segs.W[2] = S->W2; segs.Wt[2] = S->W2t; segs.rows[2] = kH; segs.cols[2] = kH;
+  segs.end[3] = kOffW3;  segs.W[3] = nullptr;
+  segs.end[4] = kOffB3;  segs.W[4] = S->W3; segs.Wt[4] = S->W3t; segs.rows[4] = kH; segs.cols[4] = kH;
+  segs.end[5] = kNumParams; segs.W[5] = nullptr;
+  const long long starts[6] = {kOffW1, kOffB1, kOffW2, kOffB2, kOffW3, kOffB3};
+  for (int k = 0; k < 6; ++k) segs.begin[k] = starts[k];
+  k_adam_all<<<blocks_for(kNumParams, 256), 256, 0, s>>>(S->p, S->g, S->m, S->v, kNumParams, lr, b1, b2, eps, c1, c2,
+                                                          segs);
   return cudaGetLastError();
 }
 
@@ -577,7 +488,7 @@ void ezo_surrogate_free(ezo_surrogate* S) {
   if (!S) return;
   void* ps[] = {S->p,  S->g,   S->m,   S->v,   S->W1,  S->W2,  S->W3,   S->W2t,  S->W3t, S->X,   S->Xt,  S->H1,
                 S->H1t, S->H2, S->H2t, S->H3, S->H3t, S->dZ3, S->dZ3t, S->dZ2, S->dZ2t, S->dZ1, S->dZ1t, S->Z1, S->Z2,
-                S->Z3, S->y,   S->loss, S->wimg, S->tc_err};
+                S->Z3, S->y,   S->loss, S->wimg, S->tc_err, S->ws};
   for (void* q : ps)
     if (q) cudaFree(q);
   delete S;
