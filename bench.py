@@ -782,7 +782,9 @@ def main():
         # useful work: the exact checks of the segments the skip rule keeps
         units += w["kept_checks"]
         units_all_segments += w["sample_checks"] + w["bisection_checks"]
-        launches += 6 * w["rounds"] + 2  # first sizing, 6 kernels per round, containment
+        # first sizing, 7 kernels per round (the one-lane and the shared-walk
+        # sampler, one of which returns at once), containment
+        launches += 7 * w["rounds"] + 2
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()

@@ -278,8 +278,8 @@ ezo_status ezo_batch_capacity(const ezo_batch* batch, int32_t* m_cap, int32_t* s
 ezo_status ezo_batch_set_sample_lanes(ezo_batch* batch, int32_t lanes);
 
 /* Launch shapes of a batch's round kernels. sample_fill_tiles: the walks'
- * lane rule takes one lane per walk from 1.5 x this many 128-walk tiles per
- * round up, two from half of it, four from an eighth, else eight (default:
+ * lane rule takes one lane per walk from 2 x this many 128-walk tiles per
+ * round up, two from this many, four from a quarter, else eight (default:
  * the tiles that fill every scheduler with one warp, 4 x SMs x 32 / 128);
  * check_lanes: lanes per configuration of the label kernel; bisect_lanes:
  * lanes per bisection candidate (1, 2, 4 or 8 each). Every shape gives the

@@ -136,25 +136,34 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
     if (j < v.n) S[(long long)j * st.s_cap + i] = x[j];
 }
 
+// Lanes per walk for a round of n_tiles sample tiles: S = split_below_tiles
+// tiles of 128 walks put one warp on every scheduler at one lane per walk;
+// measured on the 7-DOF arm (1e4 to 1e5 walks, 14 to 54 rows), one lane is
+// fastest from about 2 S tiles up, two from S, four from S / 4, and eight
+// below. A nonzero sample_lanes fixes the count.
+__device__ __forceinline__ int sample_passes(const BatchView& v, int n_tiles, int S) {
+  if (v.sample_lanes) return v.sample_lanes;
+  return n_tiles >= 2 * S ? 1 : (n_tiles >= S ? 2 : (4 * n_tiles >= S ? 4 : 8));
+}
+
 // Hit-and-run for every active segment. When the round has few walks (few
 // active segments) several lanes share each walk, which cuts the latency of
 // the sequential N_ms steps and fills the GPU; with many walks each lane runs
 // one. The choice is made on the device from the round's tile count, so it
-// also works inside a graph. Work units are (tile, pass) pairs: a tile of
-// kTile walks takes one pass at one lane per walk, or 2, 4 or 8 passes at 2,
-// 4 or 8 lanes per walk, and the passes of a tile go to different blocks.
-template <int NDOF>
+// also works inside a graph: the one-lane form (SPLIT = false) and the shared
+// forms (SPLIT = true) are separate kernels, each with its own register
+// budget, launched one after the other, and the one not chosen returns at
+// once. Work units are (tile, pass) pairs: a tile of kTile walks takes one
+// pass at one lane per walk, or 2, 4 or 8 passes at 2, 4 or 8 lanes per walk,
+// and the passes of a tile go to different blocks.
+template <int NDOF, bool SPLIT>
 __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_below_tiles) {
   extern __shared__ float4 smf4[];
   __shared__ SampleParams p;
   __shared__ int cur_seg;
   const int n_tiles = v.summary->n_sample_tiles;
-  // S = split_below_tiles tiles of 128 walks at 4 warps per SM scheduler
-  // fill the GPU with one lane per walk; measured on the 7-DOF arm, one lane
-  // is fastest from 1.5 S tiles up, two from S / 2, four from S / 8
-  const int S = split_below_tiles;
-  const int passes = v.sample_lanes ? v.sample_lanes
-                                    : (2 * n_tiles >= 3 * S ? 1 : (2 * n_tiles >= S ? 2 : (8 * n_tiles >= S ? 4 : 8)));
+  const int passes = sample_passes(v, n_tiles, split_below_tiles);
+  if ((passes > 1) != SPLIT) return;
   float* A32 = reinterpret_cast<float*>(smf4);
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();
@@ -180,10 +189,10 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
       }
       __syncthreads();
     }
-    if (passes == 8) sample_pass<NDOF, 8>(v, st, A32, p, tile, u % passes);
+    if (!SPLIT) sample_pass<NDOF, 1>(v, st, A32, p, tile, 0);
+    else if (passes == 8) sample_pass<NDOF, 8>(v, st, A32, p, tile, u % passes);
     else if (passes == 4) sample_pass<NDOF, 4>(v, st, A32, p, tile, u % passes);
-    else if (passes == 2) sample_pass<NDOF, 2>(v, st, A32, p, tile, u % passes);
-    else sample_pass<NDOF, 1>(v, st, A32, p, tile, 0);
+    else sample_pass<NDOF, 2>(v, st, A32, p, tile, u % passes);
   }
 }
 
@@ -371,10 +380,13 @@ cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int g
   cudaError_t err = cudaSuccess;
   EZO_DISPATCH_NDOF(v.n, {
     const size_t smem = hnr_smem_bytes<ND>(v.m_cap);
-    auto kern = k_round_sample<ND>;
-    err = set_smem(kern, smem);
+    auto kern1 = k_round_sample<ND, false>;
+    auto kern2 = k_round_sample<ND, true>;
+    err = set_smem(kern1, smem);
+    if (err == cudaSuccess) err = set_smem(kern2, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, 128, smem, s>>>(v, split_below_tiles);
+    kern1<<<grid, 128, smem, s>>>(v, split_below_tiles);
+    kern2<<<grid, 128, smem, s>>>(v, split_below_tiles);
   });
   return cudaGetLastError();
 }

@@ -24,40 +24,78 @@ struct SampleParams {
   PhiloxKeys keys;
 };
 
+// The walk's approximate functions, each one PTX instruction with subnormal
+// operands and results taken as zero (.ftz): reciprocal, base-2 logarithm,
+// reciprocal square root, sine and cosine. The walk's values reach the
+// subnormal range only in measure-zero cases (a direction component or a
+// row's rate a . d within 2^-126 of zero); the flush spares the scaling that
+// the non-flushing forms put around each instruction.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+  float r;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // One hit-and-run walk of `n_mix` steps inside {x : A32 x <= b32}.
 // Random stream: Philox block (walk, draw, round, stream); draw 0 gives the
 // start x = v1 + u (v2 - v1); step s uses draws 1 + s W .. 1 + s W + W - 1,
 // W = max(1, ceil(2 ceil(n/2) / 4)), whose words w_0.. give Gaussian pair i
 // from the top 24 bits of (w_2i, w_2i+1) by Box-Muller and the step length
 // from the low bytes of w_0, w_1, w_2 (one 24-bit integer, w_0 lowest).
-// One Box-Muller pair from two 32-bit words: rho = sqrt(-2 ln u1) with u1 in
-// (0, 1], angle 2 pi u2 with u2 in [0, 1). The hardware approximations of ln,
-// of the reciprocal square root and of sin/cos (absolute error ~2^-21 on
-// [-pi, pi]) are used; the angle is shifted to pi (2 u2 - 1) in [-pi, pi),
-// which negates sine and cosine.
 __device__ __forceinline__ float step_uniform(uint32_t w0, uint32_t w1, uint32_t w2) {
   const uint32_t t = (w0 & 0xffu) | ((w1 & 0xffu) << 8) | ((w2 & 0xffu) << 16);
   return (float)t * 5.9604644775390625e-8f;  // 2^-24
 }
 
+// One Box-Muller pair from two 32-bit words: rho = sqrt(-2 ln u1) with u1 in
+// (0, 1], angle 2 pi u2 with u2 in [0, 1). -2 ln u1 = -2 ln 2 log2 u1, and the
+// square root is tt times its reciprocal square root; sine and cosine are the
+// hardware approximations (absolute error ~2^-21 on [-pi, pi]), so the angle
+// is shifted to pi (2 u2 - 1) in [-pi, pi), which negates both.
 __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& za, float& zb) {
-  const float tt = -2.f * __logf(u01_oc(w1));
-  const float rho = tt > 0.f ? tt * rsqrtf(tt) : 0.f;  // sqrt(tt) from the reciprocal square root
-  float sn, cs;
-  __sincosf(3.14159265358979f * fmaf(2.f, u01_co(w2), -1.f), &sn, &cs);
-  za = -rho * cs;
-  zb = -rho * sn;
+  const float tt = lg2_approx(u01_oc(w1)) * -1.38629436f;  // -2 ln 2 in FP32
+  const float rho = tt > 0.f ? tt * rsqrt_approx(tt) : 0.f;
+  const float a = 3.14159265358979f * fmaf(2.f, u01_co(w2), -1.f);
+  za = -rho * cos_approx(a);
+  zb = -rho * sin_approx(a);
+}
+
+// Philox blocks per walk step (the W above)
+__host__ __device__ constexpr int hnr_blocks_per_step(int n) {
+  return (2 * ((n + 1) / 2) + 3) / 4 > 1 ? (2 * ((n + 1) / 2) + 3) / 4 : 1;
 }
 
 // Shared-memory image of a polytope for the sampler, two rows per record:
 // record P holds rows 2P and 2P + 1 interleaved, a_{2P,j} and a_{2P+1,j} at
-// floats 2j and 2j + 1 (j < NDOF, zero-padded), then b_{2P} and b_{2P+1}, the
-// record rounded up to whole float4s. One 64-bit load gives a coefficient of
-// two rows as the float2 operand of a packed FP32 FMA. A missing last row of
-// an odd count is a zero row (rate 0, so it bounds nothing).
+// floats 2j and 2j + 1 (j < NDOF, zero-padded), then b_{2P} and b_{2P+1}. The
+// record is rounded up to an odd number of float4s, so that the eight
+// consecutive records which the lanes of a shared walk read at once fall in
+// different shared-memory banks. One 64-bit load gives a coefficient of two
+// rows as the float2 operand of a packed FP32 FMA. A missing last row of an
+// odd count is a zero row (rate 0, so it bounds nothing).
 template <int NDOF>
 __host__ __device__ constexpr int hnr_pair_stride() {
-  return (2 * NDOF + 5) & ~3;
+  return ((2 * NDOF + 5) & ~3) + ((((2 * NDOF + 5) & ~3) / 4) % 2 == 0 ? 4 : 0);
 }
 
 template <int NDOF>
@@ -72,14 +110,15 @@ __device__ __forceinline__ float hnr_row_b(const float* __restrict__ A32, int r)
 }
 
 // Chord bounds from the row pairs P0, P0 + step, .. < P1: for row r the slack
-// b_r - a_r . x and the rate a_r . d give the crossing t = slack / rate, which
-// bounds the chord from above when the rate is positive and from below when
-// it is negative. Both rows of a pair advance together in packed FP32 FMAs
-// against x and d duplicated into both halves (xx, dd); each half is the
-// scalar chain fmaf(a_j, x_j, .) over j = 0 .. NDOF-1 from 0, so every row's
-// slack, rate and ratio are bit for bit those of a row taken alone, and
-// min/max do not depend on the order or on how the pairs are split between
-// lanes. Four pairs per iteration let the chains overlap.
+// b_r - a_r . x and the rate a_r . d give the crossing t = slack / rate
+// (slack times the reciprocal of the rate), which bounds the chord from above
+// when the rate is positive and from below when it is negative. Both rows of
+// a pair advance together in packed FP32 FMAs against x and d duplicated into
+// both halves (xx, dd); each half is the scalar chain fmaf(a_j, x_j, .) over
+// j = 0 .. NDOF-1 from 0, so every row's slack, rate and ratio are bit for
+// bit those of a row taken alone, and min/max do not depend on the order or
+// on how the pairs are split between lanes. Four pairs per iteration let the
+// chains overlap.
 template <int NDOF>
 __device__ __forceinline__ void chord_pairs(const float* __restrict__ A32, int P0, int P1, int step,
                                             const float2 (&xx)[NDOF], const float2 (&dd)[NDOF], float& t_lo,
@@ -96,8 +135,8 @@ __device__ __forceinline__ void chord_pairs(const float* __restrict__ A32, int P
       ad = __ffma2_rn(a, dd[j], ad);
     }
     const float2 bb = rec[NDOF];
-    const float q0 = __fdividef(bb.x - ax.x, ad.x);
-    const float q1 = __fdividef(bb.y - ax.y, ad.y);
+    const float q0 = (bb.x - ax.x) * rcp_approx(ad.x);
+    const float q1 = (bb.y - ax.y) * rcp_approx(ad.y);
     if (ad.x > 0.f) t_hi = fminf(t_hi, q0);
     if (ad.x < 0.f) t_lo = fmaxf(t_lo, q0);
     if (ad.y > 0.f) t_hi = fminf(t_hi, q1);
@@ -105,52 +144,33 @@ __device__ __forceinline__ void chord_pairs(const float* __restrict__ A32, int P
   }
 }
 
-// The same chord bounds for the joint-box rows 0..2n-1 (row j: +e_j x <= hi_j,
-// row n + j: -e_j x <= -lo_j) without their dot products: with a = +-e_j the
-// general rows compute a^T x = +-x_j and a^T d = +-d_j exactly, so the slack,
-// the ratio and the bounds below are bit for bit theirs.
-template <int NDOF>
-__device__ __forceinline__ void chord_box(const float* __restrict__ A32, int n, const float (&x)[NDOF],
-                                          const float (&d)[NDOF], float& t_lo, float& t_hi) {
-#pragma unroll
-  for (int j = 0; j < NDOF; ++j) {
-    if (j < n) {
-      const float q1 = __fdividef(hnr_row_b<NDOF>(A32, j) - x[j], d[j]);
-      const float q2 = __fdividef(hnr_row_b<NDOF>(A32, n + j) + x[j], -d[j]);
-      if (d[j] > 0.f) {
-        t_hi = fminf(t_hi, q1);
-        t_lo = fmaxf(t_lo, q2);
-      }
-      if (d[j] < 0.f) {
-        t_lo = fmaxf(t_lo, q1);
-        t_hi = fminf(t_hi, q2);
-      }
-    }
+// The chord bounds of the joint-box rows j (+e_j x <= hi_j, b = bh) and n + j
+// (-e_j x <= -lo_j, b = bl) without their dot products. With a = +-e_j the
+// general rows compute a . x = +-x_j and a . d = +-d_j exactly, so the
+// crossings are q1 = (bh - x_j) r and q2 = (bl + x_j) (-r), r = 1 / d_j, bit for
+// bit theirs (the reciprocal is odd). For d_j > 0 row j bounds from above and
+// row n + j from below, for d_j < 0 the reverse, and in both cases
+// q1 - q2 has the sign of d_j (bh >= -bl and rounding is monotone), so the
+// upper bound is max(q1, q2) and the lower min(q1, q2); d_j = 0 bounds nothing.
+__device__ __forceinline__ void chord_joint(float bh, float bl, float xj, float dj, float& t_lo, float& t_hi) {
+  const float r = rcp_approx(dj);
+  const float q1 = (bh - xj) * r;
+  const float q2 = (bl + xj) * -r;
+  if (dj != 0.f) {
+    t_hi = fminf(t_hi, fmaxf(q1, q2));
+    t_lo = fmaxf(t_lo, fminf(q1, q2));
   }
 }
 
-// chord_box with the joint-box bounds held in registers (bhi[j] = b of row j,
-// blo[j] = b of row n + j): the same arithmetic, without reloading the
-// bounds at every walk step
+// chord_joint over every joint, the box bounds in registers (bhi[j] = b of
+// row j, blo[j] = b of row n + j)
 template <int NDOF>
 __device__ __forceinline__ void chord_box_r(int n, const float (&bhi)[NDOF], const float (&blo)[NDOF],
                                             const float (&x)[NDOF], const float (&d)[NDOF], float& t_lo,
                                             float& t_hi) {
 #pragma unroll
-  for (int j = 0; j < NDOF; ++j) {
-    if (j < n) {
-      const float q1 = __fdividef(bhi[j] - x[j], d[j]);
-      const float q2 = __fdividef(blo[j] + x[j], -d[j]);
-      if (d[j] > 0.f) {
-        t_hi = fminf(t_hi, q1);
-        t_lo = fmaxf(t_lo, q2);
-      }
-      if (d[j] < 0.f) {
-        t_lo = fmaxf(t_lo, q1);
-        t_hi = fminf(t_hi, q2);
-      }
-    }
-  }
+  for (int j = 0; j < NDOF; ++j)
+    if (j < n) chord_joint(bhi[j], blo[j], x[j], d[j], t_lo, t_hi);
 }
 
 // x and d in both halves of a float2, the operands chord_pairs multiplies
@@ -165,18 +185,70 @@ __device__ __forceinline__ void dup_pairs(const float (&x)[NDOF], const float (&
   }
 }
 
+// Unit direction d (zero beyond n) and step uniform u_t of walk step s; u_t =
+// -1 marks a step whose Gaussians are all zero, which does not move.
+template <int NDOF>
+__device__ __forceinline__ void hnr_direction(const PhiloxKeys& ks, uint32_t walk, uint32_t rk, uint32_t stream,
+                                              int s, int n, int W, float (&d)[NDOF], float& ut) {
+  constexpr int WMAX = hnr_blocks_per_step(NDOF);
+  uint32_t w[4 * WMAX];
+#pragma unroll
+  for (int b = 0; b < WMAX; ++b) {
+    u32x4 r = u32x4{0u, 0u, 0u, 0u};
+    if (b < W) r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, ks);
+    w[4 * b] = r.x;
+    w[4 * b + 1] = r.y;
+    w[4 * b + 2] = r.z;
+    w[4 * b + 3] = r.w;
+  }
+#pragma unroll
+  for (int i = 0; i < (NDOF + 1) / 2; ++i) {
+    float za = 0.f, zb = 0.f;
+    if (2 * i < n) box_muller(w[2 * i], w[2 * i + 1], za, zb);
+    d[2 * i] = za;
+    if (2 * i + 1 < NDOF) d[2 * i + 1] = (2 * i + 1 < n) ? zb : 0.f;
+  }
+  float nrm2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) nrm2 = fmaf(d[j], d[j], nrm2);
+  const float inv = nrm2 > 0.f ? rsqrt_approx(nrm2) : 0.f;
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) d[j] *= inv;
+  ut = nrm2 > 0.f ? step_uniform(w[0], w[1], w[2]) : -1.f;
+}
+
+// The move of one step: t = t_lo + u_t (t_hi - t_lo) on the chord [t_lo, t_hi]
+// (clamped to contain 0), skipped for a degenerate or unbounded chord.
+template <int NDOF>
+__device__ __forceinline__ void hnr_move(float ut, float t_lo, float t_hi, const float (&d)[NDOF],
+                                         float (&x)[NDOF]) {
+  t_hi = fmaxf(t_hi, 0.f);
+  t_lo = fminf(t_lo, 0.f);
+  if (ut >= 0.f && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
+    const float t = fmaf(ut, t_hi - t_lo, t_lo);
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) x[j] = fmaf(t, d[j], x[j]);
+  }
+}
+
+template <int NDOF>
+__device__ __forceinline__ void hnr_start(const PhiloxKeys& ks, uint32_t walk, uint32_t rk, uint32_t stream, int n,
+                                          const float* v1f, const float* ef, float (&x)[NDOF]) {
+  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, ks);
+  const float u0 = u01_co(r0.x);
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
+}
+
+// When box_rows = 2n the polytope's first 2n rows are the joint box (row j:
+// +e_j x <= hi_j, row n + j: -e_j x <= -lo_j) and take the chord_joint form.
 template <int NDOF>
 __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
                                          int n, const float* v1f, const float* ef, int n_mix,
                                          const PhiloxKeys& ks, uint32_t walk, uint32_t rk, uint32_t stream,
                                          float (&x)[NDOF], int box_rows = 0) {
-  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
-  const int npair = (n + 1) / 2;
-  const int W = max(1, (2 * npair + 3) / 4);
-  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, ks);
-  const float u0 = u01_co(r0.x);
-#pragma unroll
-  for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
+  const int W = hnr_blocks_per_step(n);
+  hnr_start<NDOF>(ks, walk, rk, stream, n, v1f, ef, x);
   // the joint-box bounds, loaded once for all steps
   float bhi[NDOF], blo[NDOF];
 #pragma unroll
@@ -185,123 +257,86 @@ __device__ __forceinline__ void hnr_walk(const float* __restrict__ A32, int m,
     blo[j] = (box_rows && j < n) ? hnr_row_b<NDOF>(A32, n + j) : 0.f;
   }
   for (int s = 0; s < n_mix; ++s) {
-    uint32_t w[4 * WMAX];
-#pragma unroll
-    for (int b = 0; b < WMAX; ++b) {
-      if (b < W) {
-        const u32x4 r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, ks);
-        w[4 * b] = r.x;
-        w[4 * b + 1] = r.y;
-        w[4 * b + 2] = r.z;
-        w[4 * b + 3] = r.w;
-      } else {
-        w[4 * b] = w[4 * b + 1] = w[4 * b + 2] = w[4 * b + 3] = 0u;
-      }
-    }
-    float d[NDOF];
-    float nrm2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < (NDOF + 1) / 2; ++i) {
-      float za, zb;
-      box_muller(w[2 * i], w[2 * i + 1], za, zb);
-      if (2 * i < NDOF) d[2 * i] = (2 * i < n) ? za : 0.f;
-      if (2 * i + 1 < NDOF) d[2 * i + 1] = (2 * i + 1 < n) ? zb : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) nrm2 = fmaf(d[j], d[j], nrm2);
-    const float ut = step_uniform(w[0], w[1], w[2]);
-    const bool ok = nrm2 > 0.f;
-    const float inv = ok ? rsqrtf(nrm2) : 0.f;
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) d[j] *= inv;
+    float d[NDOF], ut;
+    hnr_direction<NDOF>(ks, walk, rk, stream, s, n, W, d, ut);
     float t_lo = -INFINITY, t_hi = INFINITY;
     if (box_rows) chord_box_r<NDOF>(n, bhi, blo, x, d, t_lo, t_hi);
     float2 xx[NDOF], dd[NDOF];
     dup_pairs<NDOF>(x, d, xx, dd);
     chord_pairs<NDOF>(A32, box_rows >> 1, (m + 1) >> 1, 1, xx, dd, t_lo, t_hi);
-    t_hi = fmaxf(t_hi, 0.f);
-    t_lo = fminf(t_lo, 0.f);
-    if (ok && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
-      const float t = fmaf(ut, t_hi - t_lo, t_lo);
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) x[j] = fmaf(t, d[j], x[j]);
-    }
+    hnr_move<NDOF>(ut, t_lo, t_hi, d, x);
   }
 }
 
 // The same walk as hnr_walk, shared by TS consecutive lanes of a warp (TS in
-// 2, 4, 8): lane lw draws Philox blocks lw, lw + TS, .. of each step and the
-// Box-Muller pairs they hold; the direction and the step uniform are
-// broadcast by shuffles; lane lw scans polytope rows lw, lw + TS, .. and the
+// 2, 4, 8). The steps go in groups of TS: lane lw draws the direction and
+// step uniform of step s0 + lw of the group, and each step of the group takes
+// its direction from its lane by shuffles. Lane lw scans the polytope row
+// pairs lw, lw + TS, .. (and, from four lanes up, the joints lw, lw + TS, ..
+// of the box rows; with two lanes each lane takes the whole box), and the
 // chord bounds are combined with min/max shuffles. Every lane ends with the
-// same x, bit-identical to hnr_walk's (same per-row arithmetic; min and max do
-// not depend on the order), so a segment's samples do not depend on how many
-// other walks share its round. All lanes of the warp must call this together.
+// same x, bit-identical to hnr_walk's (same arithmetic per direction and per
+// row; min and max do not depend on the order), so a segment's samples do not
+// depend on how many other walks share its round. All lanes of the warp must
+// call this together.
 template <int NDOF, int TS>
 __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, int m, int n, const float* v1f,
                                                const float* ef, int n_mix, const PhiloxKeys& ks,
                                                uint32_t walk, uint32_t rk, uint32_t stream, int lw,
                                                float (&x)[NDOF], int box_rows = 0) {
-  constexpr int WMAX = (2 * ((NDOF + 1) / 2) + 3) / 4;
-  constexpr int BPL = (WMAX + TS - 1) / TS;  // Philox blocks per lane
-  const int npair = (n + 1) / 2;
-  const int W = max(1, (2 * npair + 3) / 4);
-  const u32x4 r0 = philox4x32_10(u32x4{walk, 0u, rk, stream}, ks);
-  const float u0 = u01_co(r0.x);
+  constexpr int JS = TS >= 4 ? (NDOF + TS - 1) / TS : NDOF;  // box joints per lane
+  const int W = hnr_blocks_per_step(n);
+  hnr_start<NDOF>(ks, walk, rk, stream, n, v1f, ef, x);
+  // this lane's joint-box bounds: joint jj TS + lw (TS >= 4) or jj (TS = 2)
+  float bhi[JS], blo[JS];
 #pragma unroll
-  for (int j = 0; j < NDOF; ++j) x[j] = (j < n) ? fmaf(u0, ef[j], v1f[j]) : 0.f;
-  for (int s = 0; s < n_mix; ++s) {
-    // this lane's blocks: Gaussians z[4b .. 4b+3] from words 4b .. 4b+3
-    float z[4 * BPL];
-    float ut_part = 0.f;
+  for (int jj = 0; jj < JS; ++jj) {
+    const int j = TS >= 4 ? jj * TS + lw : jj;
+    bhi[jj] = (box_rows && j < n) ? hnr_row_b<NDOF>(A32, j) : 0.f;
+    blo[jj] = (box_rows && j < n) ? hnr_row_b<NDOF>(A32, n + j) : 0.f;
+  }
+  for (int s0 = 0; s0 < n_mix; s0 += TS) {
+    float dn[NDOF], un = -1.f;
+    if (s0 + lw < n_mix) {
+      hnr_direction<NDOF>(ks, walk, rk, stream, s0 + lw, n, W, dn, un);
+    } else {
 #pragma unroll
-    for (int bl = 0; bl < BPL; ++bl) {
-      const int b = lw + bl * TS;
-      u32x4 r = u32x4{0u, 0u, 0u, 0u};
-      if (b < W) r = philox4x32_10(u32x4{walk, (uint32_t)(1 + s * W + b), rk, stream}, ks);
-      const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+      for (int j = 0; j < NDOF; ++j) dn[j] = 0.f;
+    }
+#pragma unroll 1
+    for (int l = 0; l < TS && s0 + l < n_mix; ++l) {
+      float d[NDOF];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int pair = 2 * b + h;  // words 4b + 2h, 4b + 2h + 1
-        float za = 0.f, zb = 0.f;
-        if (pair < npair) box_muller(wv[2 * h], wv[2 * h + 1], za, zb);
-        z[4 * bl + 2 * h] = za;
-        z[4 * bl + 2 * h + 1] = zb;
+      for (int j = 0; j < NDOF; ++j) d[j] = __shfl_sync(0xffffffffu, dn[j], l, TS);
+      const float ut = __shfl_sync(0xffffffffu, un, l, TS);
+      float t_lo = -INFINITY, t_hi = INFINITY;
+      if (box_rows) {
+#pragma unroll
+        for (int jj = 0; jj < JS; ++jj) {
+          if (TS >= 4) {
+            // joint jj TS + lw: its coordinate and direction by selection
+            float xs = 0.f, ds = 0.f;
+#pragma unroll
+            for (int l2 = 0; l2 < TS; ++l2)
+              if (jj * TS + l2 < NDOF && l2 == lw) {
+                xs = x[jj * TS + l2];
+                ds = d[jj * TS + l2];
+              }
+            if (jj * TS + lw < n) chord_joint(bhi[jj], blo[jj], xs, ds, t_lo, t_hi);
+          } else if (jj < n) {
+            chord_joint(bhi[jj], blo[jj], x[jj], d[jj], t_lo, t_hi);
+          }
+        }
       }
-      if (b == 0) ut_part = step_uniform(wv[0], wv[1], wv[2]);
-    }
-    // gather the direction: component j lives in lane (j / 4) % TS, slot
-    // 4 * ((j / 4) / TS) + j % 4
-    float d[NDOF];
-    float nrm2 = 0.f;
+      float2 xx[NDOF], dd[NDOF];
+      dup_pairs<NDOF>(x, d, xx, dd);
+      chord_pairs<NDOF>(A32, (box_rows >> 1) + lw, (m + 1) >> 1, TS, xx, dd, t_lo, t_hi);
 #pragma unroll
-    for (int j = 0; j < NDOF; ++j) {
-      const int b = j / 4;
-      const float v = __shfl_sync(0xffffffffu, z[4 * (b / TS) + (j & 3)], b % TS, TS);
-      d[j] = (j < n) ? v : 0.f;
-      nrm2 = fmaf(d[j], d[j], nrm2);
-    }
-    const float ut = __shfl_sync(0xffffffffu, ut_part, 0, TS);  // block 0 lives in lane 0
-    const bool ok = nrm2 > 0.f;
-    const float inv = ok ? rsqrtf(nrm2) : 0.f;
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) d[j] *= inv;
-    float t_lo = -INFINITY, t_hi = INFINITY;
-    if (box_rows) chord_box<NDOF>(A32, n, x, d, t_lo, t_hi);  // every lane: cheap, and min/max repeat safely
-    float2 xx[NDOF], dd[NDOF];
-    dup_pairs<NDOF>(x, d, xx, dd);
-    chord_pairs<NDOF>(A32, (box_rows >> 1) + lw, (m + 1) >> 1, TS, xx, dd, t_lo, t_hi);
-#pragma unroll
-    for (int o = 1; o < TS; o <<= 1) {
-      t_hi = fminf(t_hi, __shfl_xor_sync(0xffffffffu, t_hi, o, TS));
-      t_lo = fmaxf(t_lo, __shfl_xor_sync(0xffffffffu, t_lo, o, TS));
-    }
-    t_hi = fmaxf(t_hi, 0.f);
-    t_lo = fminf(t_lo, 0.f);
-    if (ok && isfinite(t_hi) && isfinite(t_lo) && (t_hi - t_lo) >= 1e-12f) {
-      const float t = fmaf(ut, t_hi - t_lo, t_lo);
-#pragma unroll
-      for (int j = 0; j < NDOF; ++j) x[j] = fmaf(t, d[j], x[j]);
+      for (int o = 1; o < TS; o <<= 1) {
+        t_hi = fminf(t_hi, __shfl_xor_sync(0xffffffffu, t_hi, o, TS));
+        t_lo = fmaxf(t_lo, __shfl_xor_sync(0xffffffffu, t_lo, o, TS));
+      }
+      hnr_move<NDOF>(ut, t_lo, t_hi, d, x);
     }
   }
 }
