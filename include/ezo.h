@@ -281,9 +281,11 @@ ezo_status ezo_batch_set_sample_lanes(ezo_batch* batch, int32_t lanes);
  * lane rule takes one lane per walk from 2 x this many 128-walk tiles per
  * round up, two from this many, four from a quarter, else eight (default:
  * the tiles that fill every scheduler with one warp, 4 x SMs x 32 / 128);
- * check_lanes: lanes per configuration of the label kernel; bisect_lanes:
- * lanes per bisection candidate (1, 2, 4 or 8 each). Every shape gives the
- * same samples, labels and polytopes bit for bit; only the speed differs. */
+ * check_lanes: lanes per configuration of the label kernel (1, 2, 4 or 8);
+ * bisect_lanes: lanes per bisection candidate (1, 2, 4, 8, 16 or 32; scenes
+ * with boxes run 16 and 32 at 8). Every shape gives the same samples and
+ * polytopes, and the same labels outside the FP32 rounding band of a
+ * contact, bit for bit; only the speed differs. */
 typedef struct {
   int32_t sample_fill_tiles;
   int32_t check_lanes;
@@ -294,7 +296,7 @@ ezo_status ezo_batch_get_shape(const ezo_batch* batch, ezo_shape* shape);
  * graph is rebuilt at the next graph run. */
 ezo_status ezo_batch_set_shape(ezo_batch* batch, const ezo_shape* shape);
 /* Autotuner of the shape: runs the whole batch (host-loop mode, best of
- * `reps` timed runs after a warm-up) for the bisection lanes 2, 4, 8, then
+ * `reps` timed runs after a warm-up) for the bisection lanes 4, 8, 16, 32, 2, then
  * the label lanes 1, 2, 4, 8, then sample_fill_tiles at half, one and two
  * times the default, keeping a change only when it is at least 2% faster,
  * and sets the winner. Results are cached for the process per (device, robot
@@ -305,7 +307,7 @@ ezo_status ezo_batch_set_shape(ezo_batch* batch, const ezo_shape* shape);
  * Synchronous. */
 ezo_status ezo_batch_tune(ezo_batch* batch, int32_t reps, ezo_shape* chosen, void* cuda_stream);
 
-/* Step-by-step access for tests and tools./* Step-by-step access for tests and tools. ezo_batch_step runs one kernel of
+/* Step-by-step access for tests and tools. ezo_batch_step runs one kernel of
  * the current round over the batch: 0 round size (a1), 1 hit-and-run (a2),
  * 2 collision labels (a3, a4), 3 certification and selection (a5, a6),
  * 4 projection and bisection (a7, a8), 5 hyperplane placement (a9), 6 round
@@ -511,7 +513,8 @@ ezo_status ezo_batch_reinflate(ezo_batch* batch, const uint8_t* which, int32_t m
  * Errors: EZO_ERR_INVALID_ARG (also when the robot's spheres and the
  * obstacles do not fit the collision kernels' shared memory, checked before
  * anything runs); EZO_ERR_CAPACITY when the segment needs more
- * working memory than the array holds (roughly n_p <= 16384 for n = 16) or
+ * working memory than the array holds (roughly n_p <= 11000 for n = 16,
+ * 23000 for n = 7, at n_f = 10 and n_it_max = 50) or
  * more than 2048 rows; EZO_ERR_CUDA. */
 #define EZO_NOALLOC_SCRATCH_BYTES (6u * 1024u * 1024u)
 ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const ezo_env* env, const double* v1,

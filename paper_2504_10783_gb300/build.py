@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libezo.so")
 SOURCES = ["ezo_capi.cu", "ezo_api.cu", "ezo_k_flat.cu", "ezo_k_round_a.cu", "ezo_k_round_b.cu", "ezo_noalloc.cu", "ezo_tune.cu",
-           "ezo_mlp.cu", "ezo_mlp_tc.cu", "ezo_mlp_gemm_tc.cu", "ezo_k_sbis.cu", "ezo_k_recover.cu"]
+           "ezo_mlp.cu", "ezo_mlp_tc.cu", "ezo_mlp_gemm_tc.cu", "ezo_k_recover.cu"]
 # the collision kernels for scenes with box geometries: the same sources built
 # a second time with EZO_BOX_TU=1, in parallel with the rest
 BOX_SOURCES = ["ezo_k_flat.cu", "ezo_k_round_a.cu", "ezo_k_round_b.cu", "ezo_k_recover.cu"]

@@ -655,16 +655,16 @@ extern "C" int ezo_internal_surrogate_dof(const ezo_surrogate* S);
 
 namespace {
 
-// Step 4 with a surrogate: N_b surrogate bisection steps for every candidate
-// (all of them in one tensor-core launch), one exact check of each end point,
-// exact bisection for the candidates whose end point is free.
+// Step 4: the candidates' projections, then the exact halvings, then c* and
+// its plane. With a surrogate, between the projections and c*: N_b surrogate
+// bisection steps for every candidate (all of them in one tensor-core
+// launch), one exact check of each end point, exact halvings for the
+// candidates whose end point is free.
 cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
-  if (!b->sur) {
-    b->view.bis_mode = 0;
-    return launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
-  }
-  const int g = (int)std::max<long long>(1, std::min<long long>((b->sur_rows + 255) / 256, 4096));
-  cudaError_t e = launch_sbis_init(b->view, g, s);
+  const int g = row_grid((long long)b->max_bisect_tiles * kTile);
+  if (!b->sur) return launch_bisect_exact(b->view, b->T_bisect, b->grid_bisect, g, s);
+  b->view.bis_mode = 0;
+  cudaError_t e = launch_bisect_prep(b->view, g, s);
   if (e == cudaSuccess)
     e = ezo_internal_mlp_bisect(b->sur, b->sur_rows, b->view.s_rows, b->view.s_p32, b->view.s_d32, b->view.s_lo,
                                 b->view.s_hi, b->view.s_bits, b->prm.n_b, b->view.sbis_margin, s);
@@ -677,6 +677,7 @@ cudaError_t launch_bisect_step(ezo_batch* b, cudaStream_t s) {
     e = launch_round_bisect(b->view, b->T_bisect, b->grid_bisect, s);
   }
   b->view.bis_mode = 0;
+  if (e == cudaSuccess) e = launch_bisect_finish(b->view, g, s);
   return e;
 }
 
@@ -943,6 +944,10 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   EZO_ALLOC(b->d_st0, B);
   EZO_ALLOC(b->d_A0, B * mc * n);
   EZO_ALLOC(b->d_b0, B * mc);
+  // the bisection's projected candidate rows (c_proj, c - c_proj in FP32)
+  b->view.s_ld = n <= 8 ? 8 : EZO_MAX_DOF;
+  EZO_ALLOC(b->view.s_p32, (long long)b->max_bisect_tiles * kTile * b->view.s_ld);
+  EZO_ALLOC(b->view.s_d32, (long long)b->max_bisect_tiles * kTile * b->view.s_ld);
 #undef EZO_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_sum, sizeof(RoundSummary));
   if (e != cudaSuccess) {
@@ -1041,9 +1046,13 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   // tuner ranks them within its noise); larger rounds take the tuner's pick
   b->T_check = tot_s1 < (1ll << 20) ? 2 : ezo_internal_tuned_lanes(robot, envs[e_big], tot_s1, nullptr);
   // Bisection runs N_b dependent checks per candidate on the few thousand
-  // candidates of a round, so it is latency bound: eight lanes per candidate
-  // unless a round can hold enough candidates to fill the GPU at fewer lanes.
-  b->T_bisect = tot_np >= (1ll << 20) ? ezo_internal_tuned_lanes(robot, envs[e_big], tot_np / 4, nullptr) : 8;
+  // candidates of a round, so it is latency bound: sixteen lanes per
+  // candidate (the wide check; eight in scenes with boxes), unless a round
+  // can hold enough candidates to fill the GPU at fewer lanes. Measured on
+  // the 7-DOF arm's path (800 to 14,000 candidates a round), 16 lanes beat 8
+  // by 5-30% in every round but the largest.
+  b->T_bisect = tot_np >= (1ll << 20) ? ezo_internal_tuned_lanes(robot, envs[e_big], tot_np / 4, nullptr)
+                                      : ((robot->n_box || b->max_ebox) ? 8 : 16);
   // walks share eight lanes in rounds with fewer walks than one warp per
   // scheduler would hold at one lane per walk
   b->split_below = (sms * 4 * 32) / kTile;
@@ -1118,8 +1127,10 @@ ezo_status ezo_batch_get_shape(const ezo_batch* b, ezo_shape* sh) {
 ezo_status ezo_batch_set_shape(ezo_batch* b, const ezo_shape* sh) {
   if (!b || !sh) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_shape: bad argument");
   auto lanes_ok = [](int t) { return t == 1 || t == 2 || t == 4 || t == 8; };
-  if (sh->sample_fill_tiles < 1 || !lanes_ok(sh->check_lanes) || !lanes_ok(sh->bisect_lanes))
-    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_shape: sample_fill_tiles >= 1, lanes 1, 2, 4 or 8");
+  const bool bis_ok = lanes_ok(sh->bisect_lanes) || sh->bisect_lanes == 16 || sh->bisect_lanes == 32;
+  if (sh->sample_fill_tiles < 1 || !lanes_ok(sh->check_lanes) || !bis_ok)
+    return fail(EZO_ERR_INVALID_ARG,
+                "ezo_batch_set_shape: sample_fill_tiles >= 1, check lanes 1, 2, 4 or 8, bisect lanes 1 to 32");
   apply_shape(b, *sh);
   g_err.clear();
   return EZO_OK;
@@ -1171,10 +1182,10 @@ ezo_status ezo_batch_tune(ezo_batch* b, int32_t reps, ezo_shape* chosen, void* s
     float best_ms = 1e30f;
     ezo_status st = time_shape(best, &best_ms);
     const int S = (b->sms * 4 * 32) / kTile;
-    const int bis[3] = {2, 4, 8}, chk[4] = {1, 2, 4, 8}, fill[3] = {std::max(1, S / 2), S, 2 * S};
+    const int bis[5] = {4, 8, 16, 32, 2}, chk[4] = {1, 2, 4, 8}, fill[3] = {std::max(1, S / 2), S, 2 * S};
     for (int stage = 0; stage < 3 && st == EZO_OK; ++stage) {
       const int* cand = stage == 0 ? bis : (stage == 1 ? chk : fill);
-      const int nc = stage == 1 ? 4 : 3;
+      const int nc = stage == 0 ? 5 : (stage == 1 ? 4 : 3);
       for (int i = 0; i < nc && st == EZO_OK; ++i) {
         ezo_shape sh = best;
         if (stage == 0) sh.bisect_lanes = cand[i];
@@ -1223,13 +1234,12 @@ ezo_status ezo_batch_attach_surrogate(ezo_batch* b, ezo_surrogate* sur, float ma
     return fail(EZO_ERR_INVALID_ARG, "ezo_batch_attach_surrogate: surrogate of another robot, or more than 8 joints");
   const long long rows = (long long)b->max_bisect_tiles * kTile;
   if (rows > b->sur_rows) {
-    void* ps[] = {b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
-                  b->view.s_bits, b->view.s_ok, b->view.s_rows};
+    // the surrogate's brackets and end-point records (the projected rows
+    // s_p32 / s_d32 exist from ezo_batch_create on)
+    void* ps[] = {b->view.s_lo, b->view.s_hi, b->view.s_bits, b->view.s_ok, b->view.s_rows};
     for (void* p : ps)
       if (p) cudaFree(p);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dalloc(&b->view.s_p32, rows * 8);
-    if (e == cudaSuccess) e = dalloc(&b->view.s_d32, rows * 8);
     if (e == cudaSuccess) e = dalloc(&b->view.s_lo, rows);
     if (e == cudaSuccess) e = dalloc(&b->view.s_hi, rows);
     if (e == cudaSuccess) e = dalloc(&b->view.s_bits, rows);

@@ -362,7 +362,7 @@ __device__ __forceinline__ bool box_pairs_hit(const RobotSmem& rs, const float4*
 // (padding spheres get an infinite last entry), and BOX poses the robot's
 // boxes. Ends with a warp barrier; every lane of the warp must call it.
 template <int NDOF, int T, bool BOX = false>
-__device__ __forceinline__ void fk_group(const float* __restrict__ q, const RobotSmem& rs,
+__device__ __forceinline__ void fk_group(const float (&q)[NDOF], const RobotSmem& rs,
                                          const float4* __restrict__ sph_s, float4* __restrict__ cen, int lg,
                                          const BoxCtx& bx) {
   float c0x = 1.f, c0y = 0.f, c0z = 0.f;
@@ -451,7 +451,7 @@ __device__ __forceinline__ void fk_group(const float* __restrict__ q, const Robo
 // Every lane of the warp must call this together (invalid configurations are
 // evaluated and discarded).
 template <int NDOF, int T, bool BOX = false>
-__device__ __forceinline__ bool collide_group(const float* __restrict__ q, const RobotSmem& rs,
+__device__ __forceinline__ bool collide_group(const float (&q)[NDOF], const RobotSmem& rs,
                                               const float4* __restrict__ sph_s,
                                               const float4* __restrict__ obs_s,
                                               const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
@@ -588,6 +588,98 @@ __device__ __forceinline__ bool collide_group(const float* __restrict__ q, const
     hit = h != 0u;
   }
   return hit;
+}
+
+// One configuration evaluated by a group of T = 16 or 32 lanes (sphere
+// geometries only). The kinematics are fk_group's. The obstacle pairs are
+// split two ways: lane lg = sg OG + og takes the robot spheres s with
+// s % SG == sg (SG = T / OG) against the obstacle pairs p with p % OG == og,
+// so each lane holds a few spheres for a few pairs instead of one chunk of
+// spheres per handful of pairs; the same fast form, rounding band and direct
+// re-check as collide_group decide each sphere, over the lane's obstacles.
+// Self pairs come from the explicit pair list, p % T == lg, in the direct
+// difference form. Returns the group-wide OR; every lane of the warp must
+// call this together.
+template <int NDOF, int T>
+__device__ __forceinline__ bool collide_wide(const float (&q)[NDOF], const RobotSmem& rs,
+                                             const float4* __restrict__ sph_s, const float4* __restrict__ obs_s,
+                                             const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
+                                             const ushort2* __restrict__ self_pairs,
+                                             const float* __restrict__ self_rr, float E,
+                                             float4* __restrict__ cen, int lg, const BoxCtx& bx) {
+  static_assert(T == 16 || T == 32, "wide groups are 16 or 32 lanes");
+  constexpr int OG = 8, SG = T / OG, CW = 4;
+  fk_group<NDOF, T, false>(q, rs, sph_s, cen, lg, bx);
+  bool hit = false;
+  const int n_pairs = n_obs_pad >> 1;
+  const float2* __restrict__ nhw2 = reinterpret_cast<const float2*>(nhw_s);
+  const int sg = lg / OG, og = lg % OG;
+  const int nsp = rs.n_spheres_pad;
+  for (int s0 = sg; s0 < nsp; s0 += SG * CW) {
+    float2 cx[CW], cy[CW], cz[CW], cr[CW];
+    float hu[CW], m[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+      const int s = s0 + k * SG;
+      const float4 c = s < nsp ? cen[s] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+      const float r = s < nsp ? sph_s[s].w : 0.f;
+      cx[k] = make_float2(c.x, c.x);
+      cy[k] = make_float2(c.y, c.y);
+      cz[k] = make_float2(c.z, c.z);
+      cr[k] = make_float2(r, r);
+      hu[k] = c.w;
+      m[k] = -3.0e38f;
+    }
+    for (int p = og; p < n_pairs; p += OG) {
+      const float4 xy = obs_s[2 * p], zr = obs_s[2 * p + 1];
+      const float2 w = nhw2[p];
+      const float2 ox = make_float2(xy.x, xy.y), oy = make_float2(xy.z, xy.w);
+      const float2 oz = make_float2(zr.x, zr.y), oR = make_float2(zr.z, zr.w);
+#pragma unroll
+      for (int k = 0; k < CW; ++k) {
+        float2 t = __ffma2_rn(cr[k], oR, w);
+        t = __ffma2_rn(cz[k], oz, t);
+        t = __ffma2_rn(cy[k], oy, t);
+        t = __ffma2_rn(cx[k], ox, t);
+        m[k] = fmax3f(m[k], t.x, t.y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+      const float diff = m[k] - hu[k];
+      if (diff > E) {
+        hit = true;
+      } else if (diff >= -E) {
+        // inside the rounding band: direct differences over this lane's
+        // obstacles (2p, 2p + 1 for its pairs p)
+        for (int jj = 2 * og; jj < n_obs; jj += 2 * OG) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (jj + h < n_obs) {
+              const float4 o = obs_at(obs_s, jj + h);
+              const float dx = cx[k].x - o.x, dy = cy[k].x - o.y, dz = cz[k].x - o.z;
+              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float sr = cr[k].x + o.w;
+              if (d2 < sr * sr) hit = true;
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll 4
+  for (int p = lg; p < rs.n_self; p += T) {
+    const ushort2 pr = self_pairs[p];
+    const float4 a = cen[pr.x], b = cen[pr.y];
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (d2 < self_rr[p]) hit = true;
+  }
+  __syncwarp();
+  unsigned h = hit ? 1u : 0u;
+#pragma unroll
+  for (int off = 1; off < T; off <<= 1) h |= __shfl_xor_sync(0xffffffffu, h, off, T);
+  return h != 0u;
 }
 
 // Signed distance min over pairs of ||c_i - c_j|| - r_i - r_j for one

@@ -21,6 +21,13 @@ enum SegStatus : int {
 };
 
 constexpr int kTile = 128;  // samples / candidates per work tile
+// threads per block of the one-thread-per-candidate bisection kernels: small
+// blocks spread their FP64 work (1/64 of the FP32 rate) over many SMs
+constexpr int kRowBlock = 64;
+inline int row_grid(long long rows) {
+  const long long g = (rows + kRowBlock - 1) / kRowBlock;
+  return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+}
 
 struct SegState {
   int k;          // current round (1-based)
@@ -107,8 +114,9 @@ struct BatchView {
   int max_ebox;      // largest obstacle box count over the environments
   int sample_lanes;  // lanes per hit-and-run walk: 0 = chosen per round from the tile count, else 1, 2, 4 or 8
   int edit;          // set editing (Sec. VI-B): the samples are given configurations, no test
-  float* s_p32;      // [row * 8 + j] projection onto L (FP32)
-  float* s_d32;      // [row * 8 + j] c - c_proj (FP32)
+  float* s_p32;      // [row * s_ld + j] projection c_proj of the candidate onto L (FP32)
+  float* s_d32;      // [row * s_ld + j] c - c_proj (FP32)
+  int s_ld;          // row stride of s_p32 and s_d32: 8 for n <= 8 (the MLP's input), else EZO_MAX_DOF
   float* s_lo;       // [row] bracket (fractions along [c_proj, c])
   float* s_hi;
   uint32_t* s_bits;  // [row] surrogate decisions
@@ -133,9 +141,16 @@ cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s);
 cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int grid, cudaStream_t s);
 cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t s);
 cudaError_t launch_round_certify(const BatchView& v, cudaStream_t s);
+// Bisection (ezo_k_round_b.cu): prep projects every candidate row (and, with
+// a surrogate attached, resets its brackets), round_bisect takes the halvings
+// (bis_mode 0), checks the surrogate end points (1) or redoes the failed ones
+// (2), finish forms c*, its distance and the tangent plane; bisect_exact is
+// prep + halvings + finish. grid_rows: row_grid(rows) for the batch's
+// largest candidate row count.
+cudaError_t launch_bisect_prep(const BatchView& v, int grid_rows, cudaStream_t s);
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s);
-// surrogate-guided bisection helpers (ezo_k_sbis.cu)
-cudaError_t launch_sbis_init(const BatchView& v, int grid, cudaStream_t s);
+cudaError_t launch_bisect_finish(const BatchView& v, int grid_rows, cudaStream_t s);
+cudaError_t launch_bisect_exact(const BatchView& v, int T, int grid, int grid_rows, cudaStream_t s);
 cudaError_t launch_round_place(const BatchView& v, cudaStream_t s);
 cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 

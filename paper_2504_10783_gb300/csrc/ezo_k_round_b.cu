@@ -1,6 +1,10 @@
 // EI-ZO round kernels, second half (arXiv 2504.10783, Algorithm 1, Sec. VI-A):
 //   bisect       - projection onto L (Eqs. 6-7) and N_b bisection steps
-//                  toward it (Sec. IV-B, IV-C)
+//                  toward it (Sec. IV-B, IV-C); with a learned surrogate
+//                  attached (not in the paper) the N_b steps are first taken
+//                  on its predicted signed distance (ezo_mlp_tc.cu), each end
+//                  point is verified with one exact check, and the exact
+//                  steps are redone where it is free
 //   place        - order by distance to L, place up to N_f half spaces with
 //                  step back (Eqs. 10-12), discard separated candidates
 //   round_end    - round counter, iteration cap N_it (Sec. IV-C)
@@ -13,11 +17,144 @@
 
 namespace ezo {
 
+// Bisection of one round in three kernels. k_bisect_prep (one thread per
+// candidate) projects each candidate c onto L in FP64 (Eqs. 6-7) and keeps
+// c_proj and c - c_proj in FP32; k_round_bisect takes the N_b halvings of
+// Sec. IV-B toward c_proj with T lanes per candidate and records the
+// decisions; k_bisect_finish (one thread per candidate) forms the end point
+// c* = c_proj + f (c - c_proj), f the bracket's upper end, in FP64, with its
+// distance to L and the tangent plane of Eq. (10). GB300 runs FP64 at 1/64 of
+// the FP32 rate, so the FP64 steps go where every lane of a warp does useful
+// work, and the halvings, which only need FP32 configurations, run without it.
+//
+// Row r of the round's candidate rows is candidate tile.y + (r % kTile) of
+// bisection tile r / kTile (the numbering the surrogate's MLP batch uses too).
+#if !EZO_BOX_TU
+template <int NDOF>
+__global__ void __launch_bounds__(kRowBlock) k_bisect_prep(BatchView v) {
+  const int n_tiles = v.summary->n_bisect_tiles;
+  const int rows = n_tiles * kTile;
+  const int ld = v.s_ld;
+  if (v.sbis && blockIdx.x == 0 && threadIdx.x == 0) *v.s_rows = rows;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const int2 tile = v.bisect_tiles[r / kTile];
+    const int c = tile.y + r % kTile;
+    const SegState& st = v.st[tile.x];
+    if (v.sbis) {
+      // the surrogate's bracket [0, 1] and its end-point record
+      v.s_lo[r] = 0.f;
+      v.s_hi[r] = 1.f;
+      v.s_bits[r] = 0u;
+      v.s_ok[r] = 0;
+    }
+    if (c >= st.n_cand) {
+      for (int j = 0; j < ld; ++j) v.s_p32[(long long)r * ld + j] = v.s_d32[(long long)r * ld + j] = 0.f;
+      continue;
+    }
+    const int n = v.n;
+    const int si = v.cand_idx[st.cand_off + c];
+    const float* S = v.S + (long long)n * st.sample_off;
+    double cs[NDOF], p[NDOF];
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
+    project_fp64<NDOF>(cs, v.v1 + (long long)tile.x * n, v.v2 + (long long)tile.x * n, n, p);
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      if (j < ld) {
+        v.s_p32[(long long)r * ld + j] = j < n ? (float)p[j] : 0.f;
+        v.s_d32[(long long)r * ld + j] = j < n ? (float)(cs[j] - p[j]) : 0.f;
+      }
+    }
+    for (int j = NDOF; j < ld; ++j) v.s_p32[(long long)r * ld + j] = v.s_d32[(long long)r * ld + j] = 0.f;
+  }
+}
+
+template <int NDOF>
+__global__ void __launch_bounds__(kRowBlock) k_bisect_finish(BatchView v) {
+  const int n_tiles = v.summary->n_bisect_tiles;
+  const int rows = n_tiles * kTile;
+  const int n = v.n;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const int2 tile = v.bisect_tiles[r / kTile];
+    const int c = tile.y + r % kTile;
+    const int g = tile.x;
+    const SegState& st = v.st[g];
+    if (c >= st.n_cand) continue;
+    const long long co = st.cand_off;
+    const int np = st.n_p;
+    const uint32_t bits = v.bits[co + c];
+    // the bracket's upper end: the surrogate's verified end point, or after
+    // the exact halvings lo + 2^-N_b with lo the sum of 2^-(s+1) over the
+    // steps s whose midpoint was free
+    double hi;
+    if (v.sbis && v.s_ok[r]) {
+      hi = (double)v.s_hi[r];
+    } else {
+      uint64_t lo_u = 0;
+      for (int s = 0; s < v.n_b; ++s)
+        if (!((bits >> s) & 1u)) lo_u += 1ull << (v.n_b - 1 - s);
+      hi = ldexp((double)(lo_u + 1), -v.n_b);
+    }
+    const double* v1 = v.v1 + (long long)g * n;
+    const double* v2 = v.v2 + (long long)g * n;
+    const float* S = v.S + (long long)n * st.sample_off;
+    const int si = v.cand_idx[co + c];
+    // c* = c_proj + hi (c - c_proj) in FP64
+    double cs[NDOF], p[NDOF], cst[NDOF], ps[NDOF];
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
+    project_fp64<NDOF>(cs, v1, v2, n, p);
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, cs[j] - p[j], p[j]) : 0.0;
+    project_fp64<NDOF>(cst, v1, v2, n, ps);
+    double d2 = 0.0;
+    float cn2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      if (j < n) {
+        const double e = cst[j] - ps[j];
+        d2 = fma(e, e, d2);
+        v.cstar[(long long)n * co + (long long)j * np + c] = cst[j];
+        const float f = (float)cst[j];
+        v.c32[(long long)n * co + (long long)j * np + c] = f;
+        cn2 = fmaf(f, f, cn2);
+      }
+    }
+    const double dist = sqrt(d2);
+    v.dist[co + c] = dist;
+    v.cnorm[co + c] = sqrtf(cn2);
+    // tangent plane of Eq. (10) at c*: a = (c* - c_proj) / dist_L(c*), b = a^T c*
+    const double inv = dist > 0.0 ? 1.0 / dist : 0.0;
+    double bval = 0.0;
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      if (j < n) {
+        const double a = (cst[j] - ps[j]) * inv;
+        v.ga[(long long)n * co + (long long)j * np + c] = a;
+        bval = fma(a, cst[j], bval);
+      }
+    }
+    v.gb[co + c] = bval;
+  }
+}
+#endif  // !EZO_BOX_TU
+
+// The halvings: the bracket [0, 1] of fractions along [c_proj, c] is kept as
+// the integer lo_u in units of 2^-N_b (every midpoint of N_b <= 32 halvings
+// is such a multiple, so the FP32 midpoint fraction is mid_u 2^-N_b rounded
+// once, the value the FP64 bracket would give), and the configuration tested
+// is c_proj + f (c - c_proj) in FP32. Bit s of the record is set when the
+// midpoint of step s collides (the bracket's upper end moves there).
+// bis_mode 1 instead checks the surrogate's end point once (s_ok records the
+// outcome), and bis_mode 2 redoes the exact halvings for the candidates whose
+// surrogate end point was free.
 template <int NDOF, int T, bool BOX>
 __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_pad) {
   extern __shared__ float4 smem4[];
   __shared__ RobotSmem rs;
   __shared__ int cur_env;
+  const int n_tiles = v.summary->n_bisect_tiles;
+  if (blockIdx.x >= n_tiles * T) return;  // no work unit for this block
   const RobotDev* robot = v.robot;
   const int nsp = robot->n_spheres_pad, nrbox = robot->n_box;
   const int groups = blockDim.x / T;
@@ -31,8 +168,8 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
   __syncthreads();
   const int gi = threadIdx.x / T, lg = threadIdx.x % T;
   float4* cen = gs.cen_all + gi * (nsp + 1);
-  const int n = v.n;
-  const int n_tiles = v.summary->n_bisect_tiles;
+  const int ld = v.s_ld;
+  const float scale = ldexpf(1.f, -v.n_b);
   static_assert(kTile % (128 / T) == 0, "tile must be a whole number of passes");
   // work units are (tile, pass): the T passes of a tile go to different blocks
   for (int u = blockIdx.x; u < n_tiles * T; u += gridDim.x) {
@@ -49,115 +186,64 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
       __syncthreads();
     }
     const BoxCtx bx = box_ctx(gs, robot, nrbox, ef.e.n_box, gi);
-    const double* v1 = v.v1 + (long long)g * n;
-    const double* v2 = v.v2 + (long long)g * n;
-    const float* S = v.S + (long long)n * st.sample_off;
-    const int np = st.n_p;
-    {
-      const int c = tile.y + sub + gi;
-      const int row = (u / T) * kTile + sub + gi;  // surrogate row of this candidate
-      bool valid = c < st.n_cand;
-      if (v.bis_mode == 2) {
-        // exact bisection only where the surrogate end point failed; a warp
-        // whose candidates all passed skips the work together
-        const bool need = valid && !v.s_ok[row];
-        if (!__any_sync(0xffffffffu, need)) continue;
-        valid = need;
-      }
-      const int cc = valid ? c : tile.y;
-      const int si = v.cand_idx[st.cand_off + cc];
-      // the bracket [c_proj, c] in FP32 for the midpoints: q = c_proj + f (c -
-      // c_proj) with dyadic f (GB300's FP64 rate is 1/64 of FP32; the
-      // decisions only need the FP32 configuration); the end point c* is
-      // formed in FP64 after the loop
-      float p32[NDOF], dv32[NDOF];
-      {
-        double cs[NDOF], p[NDOF];
+    // the scene's scalars in registers for the N_b checks
+    const int n_obs = ef.e.n_obs, n_obs_pad = ef.e.n_obs_pad;
+    const float E = ef.E;
+    const ushort2* self_pairs = robot->self_pairs;
+    const float* self_rr = robot->self_rr;
+    const int c = tile.y + sub + gi;
+    const int row = (u / T) * kTile + sub + gi;
+    bool valid = c < st.n_cand;
+    if (v.bis_mode == 2) {
+      // exact halvings only where the surrogate end point failed; a warp
+      // whose candidates all passed skips the work together
+      const bool need = valid && !v.s_ok[row];
+      if (!__any_sync(0xffffffffu, need)) continue;
+      valid = need;
+    }
+    float p32[NDOF], dv32[NDOF];
 #pragma unroll
-        for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
-        project_fp64<NDOF>(cs, v1, v2, n, p);
+    for (int j = 0; j < NDOF; ++j) {
+      p32[j] = j < ld ? v.s_p32[(long long)row * ld + j] : 0.f;
+      dv32[j] = j < ld ? v.s_d32[(long long)row * ld + j] : 0.f;
+    }
+    uint32_t lo_u = 0u, bits = 0u;
+    if (v.bis_mode == 1) {
+      bits = v.s_bits[row];
+    } else if (v.bis_mode == 2 && valid && lg == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), (unsigned long long)v.n_b);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), (unsigned long long)v.n_b);
+    }
+    // one call site of the collision test for both modes keeps the kernel
+    // small enough for the instruction cache
+    const int steps = v.bis_mode == 1 ? 1 : v.n_b;
+    for (int s = 0; s < steps; ++s) {
+      const uint32_t mid_u = v.bis_mode == 1 ? 0u : lo_u + (1u << (v.n_b - 1 - s));
+      const float f = v.bis_mode == 1 ? v.s_hi[row] : __uint2float_rn(mid_u) * scale;
+      float qq[NDOF];
 #pragma unroll
-        for (int j = 0; j < NDOF; ++j) {
-          p32[j] = (float)p[j];
-          dv32[j] = (j < n) ? (float)(cs[j] - p[j]) : 0.f;
-        }
-      }
-      double lo = 0.0, hi = 1.0;
-      uint32_t bits = 0u;
+      for (int j = 0; j < NDOF; ++j) qq[j] = fmaf(f, dv32[j], p32[j]);
+      bool hit;
+      if constexpr (T > 8)
+        hit = collide_wide<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, self_pairs, self_rr, E, cen, lg,
+                                    bx);
+      else
+        hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, self_pairs, self_rr, E,
+                                          cen, lg, bx);
       if (v.bis_mode == 1) {
-        // verify the surrogate's end point with one exact check
-        hi = (double)v.s_hi[row];
-        bits = v.s_bits[row];
-      } else if (v.bis_mode == 2 && valid && lg == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), (unsigned long long)v.n_b);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), (unsigned long long)v.n_b);
-      }
-      // one call site of the collision test for both modes keeps the kernel
-      // small enough for the instruction cache: the end point's check (mode
-      // 1) or the N_b halvings
-      const int steps = v.bis_mode == 1 ? 1 : v.n_b;
-      for (int s = 0; s < steps; ++s) {
-        const double f = v.bis_mode == 1 ? hi : 0.5 * (lo + hi);
-        float qq[NDOF];
-#pragma unroll
-        for (int j = 0; j < NDOF; ++j) qq[j] = fmaf((float)f, dv32[j], p32[j]);
-        const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
-                                                robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
-        if (v.bis_mode == 1) {
-          if (valid && lg == 0) {
-            v.s_ok[row] = hit ? 1 : 0;
-            atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), 1ull);
-            atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), 1ull);
-          }
-          if (!hit) valid = false;  // no output: the exact pass (mode 2) redoes this candidate
-        } else if (hit) {
-          hi = f;
-          bits |= 1u << s;
-        } else {
-          lo = f;
+        if (valid && lg == 0) {
+          v.s_ok[row] = hit ? 1 : 0;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), 1ull);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), 1ull);
         }
-      }
-      if (valid && lg == 0) {
-        // c* = c_proj + hi (c - c_proj) in FP64 (the bracket again, exactly)
-        double cs[NDOF], p[NDOF], cst[NDOF], ps[NDOF];
-#pragma unroll
-        for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
-        project_fp64<NDOF>(cs, v1, v2, n, p);
-#pragma unroll
-        for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, cs[j] - p[j], p[j]) : 0.0;
-        project_fp64<NDOF>(cst, v1, v2, n, ps);
-        double d2 = 0.0;
-        float cn2 = 0.f;
-        const long long co = st.cand_off;
-#pragma unroll
-        for (int j = 0; j < NDOF; ++j) {
-          if (j < n) {
-            const double e = cst[j] - ps[j];
-            d2 = fma(e, e, d2);
-            v.cstar[(long long)n * co + (long long)j * np + c] = cst[j];
-            const float f = (float)cst[j];
-            v.c32[(long long)n * co + (long long)j * np + c] = f;
-            cn2 = fmaf(f, f, cn2);
-          }
-        }
-        const double dist = sqrt(d2);
-        v.dist[co + c] = dist;
-        v.cnorm[co + c] = sqrtf(cn2);
-        v.bits[co + c] = bits;
-        // tangent plane of Eq. (10) at c*: a = (c* - c_proj) / dist_L(c*), b = a^T c*
-        const double inv = dist > 0.0 ? 1.0 / dist : 0.0;
-        double bval = 0.0;
-#pragma unroll
-        for (int j = 0; j < NDOF; ++j) {
-          if (j < n) {
-            const double a = (cst[j] - ps[j]) * inv;
-            v.ga[(long long)n * co + (long long)j * np + c] = a;
-            bval = fma(a, cst[j], bval);
-          }
-        }
-        v.gb[co + c] = bval;
+        if (!hit) valid = false;  // no record: the exact pass (mode 2) redoes this candidate
+      } else if (hit) {
+        bits |= 1u << s;
+      } else {
+        lo_u = mid_u;
       }
     }
+    if (valid && lg == 0) v.bits[st.cand_off + c] = bits;
   }
 }
 
@@ -422,12 +508,14 @@ cudaError_t launch_round_bisect_box(const BatchView& v, int T, int grid, cudaStr
   return cudaGetLastError();
 }
 #else
+// T = 16 or 32 lanes per candidate take the wide check (sphere scenes; box
+// scenes run at 8)
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s) {
-  if (v.n_rbox || v.max_ebox) return launch_round_bisect_box(v, T, grid, s);
+  if (v.n_rbox || v.max_ebox) return launch_round_bisect_box(v, T > 8 ? 8 : T, grid, s);
   cudaError_t err = cudaSuccess;
   const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T, v.n_rbox, v.max_ebox);
   constexpr bool BB = EZO_BOX_TU != 0;
-  EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T(T, {
+  EZO_DISPATCH_NDOF(v.n, EZO_DISPATCH_T_WIDE(T, {
     auto kern = k_round_bisect<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
@@ -438,6 +526,25 @@ cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_
 #endif
 
 #if !EZO_BOX_TU
+
+cudaError_t launch_bisect_prep(const BatchView& v, int grid, cudaStream_t s) {
+  EZO_DISPATCH_NDOF(v.n, { k_bisect_prep<ND><<<grid, kRowBlock, 0, s>>>(v); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bisect_finish(const BatchView& v, int grid, cudaStream_t s) {
+  EZO_DISPATCH_NDOF(v.n, { k_bisect_finish<ND><<<grid, kRowBlock, 0, s>>>(v); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bisect_exact(const BatchView& v, int T, int grid, int grid_rows, cudaStream_t s) {
+  BatchView w = v;
+  w.bis_mode = 0;
+  cudaError_t e = launch_bisect_prep(w, grid_rows, s);
+  if (e == cudaSuccess) e = launch_round_bisect(w, T, grid, s);
+  if (e == cudaSuccess) e = launch_bisect_finish(w, grid_rows, s);
+  return e;
+}
 
 cudaError_t launch_round_place(const BatchView& v, cudaStream_t s) {
   // alive bitmask for the largest N_p of the batch

@@ -504,6 +504,20 @@ __device__ __forceinline__ void project_fp64(const double (&c)[NDOF], const doub
     }                                        \
   } while (0)
 
+// EZO_DISPATCH_T with the wide groups of 16 and 32 lanes (the bisection)
+#define EZO_DISPATCH_T_WIDE(T, ...)          \
+  do {                                       \
+    if ((T) == 16) {                         \
+      constexpr int TT = 16;                 \
+      __VA_ARGS__;                           \
+    } else if ((T) == 32) {                  \
+      constexpr int TT = 32;                 \
+      __VA_ARGS__;                           \
+    } else {                                 \
+      EZO_DISPATCH_T(T, __VA_ARGS__);        \
+    }                                        \
+  } while (0)
+
 // Raises a kernel's dynamic shared memory limit once per (kernel, size).
 // The cache is keyed by the kernel's address: instantiations that share a
 // signature must not share an entry.

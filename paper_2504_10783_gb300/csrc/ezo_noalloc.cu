@@ -86,9 +86,9 @@ int na_test_size(int k, double eps, double delta, double tau) {
 
 // Lanes per configuration of the label and bisection kernels: the rule of
 // ezo_batch_create for rounds of this size (two lanes per configuration below
-// 2^20 samples, eight per bisection candidate below 2^20 candidates; labels
-// do not depend on the choice); above that, the size rule of the collision
-// checker, since the tuner would allocate.
+// 2^20 samples, sixteen per bisection candidate below 2^20 candidates, eight
+// with boxes; labels do not depend on the choice); above that, the size rule
+// of the collision checker, since the tuner would allocate.
 int lanes_for(long long N) {
   if (N >= (1ll << 20)) return 1;
   if (N >= (1ll << 17)) return 2;
@@ -96,7 +96,7 @@ int lanes_for(long long N) {
   return 8;
 }
 int check_lanes(long long s_cap) { return s_cap < (1ll << 20) ? 2 : lanes_for(s_cap); }
-int bisect_lanes(long long np) { return np >= (1ll << 20) ? lanes_for(np / 4) : 8; }
+int bisect_lanes(long long np, bool boxes) { return np >= (1ll << 20) ? lanes_for(np / 4) : (boxes ? 8 : 16); }
 
 }  // namespace
 
@@ -132,11 +132,13 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   const long long s_cap = std::max<long long>(np, na_test_size(prm->n_it_max, prm->eps, prm->delta, prm->tau) + 16);
   const long long st_tiles = (s_cap + kTile - 1) / kTile, bi_tiles = (np + kTile - 1) / kTile;
   const size_t pad = 256;
-  const size_t need = sizeof(SegState) + 2 * n * sizeof(double) + m_cap * n * sizeof(double) +
+  const int s_ld = n <= 8 ? 8 : EZO_MAX_DOF;
+  const size_t rows_b = (size_t)bi_tiles * kTile;
+  const size_t need = 2 * rows_b * s_ld * sizeof(float) + sizeof(SegState) + 2 * n * sizeof(double) + m_cap * n * sizeof(double) +
                       m_cap * sizeof(double) + s_cap * n * sizeof(float) + s_cap + (size_t)np * sizeof(int) +
                       (size_t)np * n * (2 * sizeof(double) + sizeof(float)) + (size_t)np * (2 * sizeof(double) + 8) +
                       (size_t)prm->n_f * (sizeof(int) + sizeof(double)) + (st_tiles + bi_tiles) * sizeof(int2) +
-                      sizeof(RoundSummary) + sizeof(EnvDevFull) + sizeof(int) + 24 * pad;
+                      sizeof(RoundSummary) + sizeof(EnvDevFull) + sizeof(int) + 26 * pad;
   if (need > (size_t)EZO_NOALLOC_SCRATCH_BYTES)
     return na_fail(EZO_ERR_CAPACITY, "this segment needs " + std::to_string(need) +
                                          " bytes of working memory, more than the fixed " +
@@ -175,6 +177,8 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   RoundSummary* d_sum = c.take<RoundSummary>(1);
   EnvDevFull* d_env = c.take<EnvDevFull>(1);
   int* d_pf = c.take<int>(1);
+  float* d_sp = c.take<float>(rows_b * s_ld);
+  float* d_sd = c.take<float>(rows_b * s_ld);
   if (c.off > (size_t)EZO_NOALLOC_SCRATCH_BYTES) return na_fail(EZO_ERR_CAPACITY, "scratch layout overflow");
 
   // initial contents: everything a kernel reads before writing it
@@ -263,21 +267,25 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   v.path_first = d_pf;
   v.max_path_len = 1;
   v.graph_cond = 0;
+  v.s_p32 = d_sp;
+  v.s_d32 = d_sd;
+  v.s_ld = s_ld;
 
   int dev = 0, sms = 1;
   NA_CUDA(cudaGetDevice(&dev));
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int T_check = check_lanes(s_cap), T_bis = bisect_lanes(np);
+  const int T_check = check_lanes(s_cap), T_bis = bisect_lanes(np, ezo_internal_robot_boxes(robot) || envf.e.n_box);
   const int grid_s = (int)std::max<long long>(1, std::min<long long>(st_tiles * 8, (long long)sms * 16));
   const int grid_c = (int)std::max<long long>(1, std::min<long long>(st_tiles * T_check, (long long)sms * 16));
   const int grid_b = (int)std::max<long long>(1, std::min<long long>(bi_tiles * T_bis, (long long)sms * 16));
+  const int grid_r = row_grid((long long)rows_b);
   RoundSummary h{};
   for (int r = 0; r <= prm->n_it_max + 1; ++r) {
     NA_CUDA(launch_round_begin(v, s));
     NA_CUDA(launch_round_sample(v, (sms * 4 * 32) / kTile, grid_s, s));
     NA_CUDA(launch_round_check(v, T_check, grid_c, s));
     NA_CUDA(launch_round_certify(v, s));
-    NA_CUDA(launch_round_bisect(v, T_bis, grid_b, s));
+    NA_CUDA(launch_bisect_exact(v, T_bis, grid_b, grid_r, s));
     NA_CUDA(launch_round_place(v, s));
     NA_CUDA(launch_round_end(v, s));
     NA_CUDA(cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s));
