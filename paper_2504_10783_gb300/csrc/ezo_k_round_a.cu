@@ -121,14 +121,21 @@ __device__ __forceinline__ void sample_pass(const BatchView& v, const SegState& 
   float* S = v.S + (long long)v.n * st.sample_off;
   const int i = tile.y + pass * WPB + gi;
   float x[NDOF];
+  // one lane per walk: a chain of exactly NDOF joints (the usual case) takes
+  // n as a constant, which removes the walk's j < n tests (the arithmetic is
+  // the same); the shared-walk kernel keeps one form, for its register budget
   if (TSS == 1) {
     if (i >= st.n_samples) return;
-    hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, v.keys, (uint32_t)i, p.round_k, p.stream, x,
-                   st.box_rows);
+    if (v.n == NDOF)
+      hnr_walk<NDOF>(A32, st.m, NDOF, p.v1f, p.ef, p.n_mix, v.keys, (uint32_t)i, p.round_k, p.stream, x,
+                     st.box_rows);
+    else
+      hnr_walk<NDOF>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, v.keys, (uint32_t)i, p.round_k, p.stream, x,
+                     st.box_rows);
   } else {
     const int ic = i < st.n_samples ? i : tile.y;
-    hnr_walk_split<NDOF, TSS>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, v.keys, (uint32_t)ic, p.round_k,
-                              p.stream, lw, x, st.box_rows);
+    hnr_walk_split<NDOF, TSS>(A32, st.m, v.n, p.v1f, p.ef, p.n_mix, v.keys, (uint32_t)ic, p.round_k, p.stream,
+                              lw, x, st.box_rows);
     if (i >= st.n_samples || lw != 0) return;
   }
 #pragma unroll
@@ -385,8 +392,8 @@ cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int g
     err = set_smem(kern1, smem);
     if (err == cudaSuccess) err = set_smem(kern2, smem);
     if (err != cudaSuccess) return err;
-    kern1<<<grid, 128, smem, s>>>(v, split_below_tiles);
-    kern2<<<grid, 128, smem, s>>>(v, split_below_tiles);
+    kern1<<<resident_grid(kern1, 128, smem, grid), 128, smem, s>>>(v, split_below_tiles);
+    kern2<<<resident_grid(kern2, 128, smem, grid), 128, smem, s>>>(v, split_below_tiles);
   });
   return cudaGetLastError();
 }
@@ -402,7 +409,7 @@ cudaError_t launch_round_check_box(const BatchView& v, int T, int grid, cudaStre
     auto kern = k_round_check<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+    kern<<<resident_grid(kern, 128, smem, grid), 128, smem, s>>>(v, v.max_obs_pad);
   }));
   return cudaGetLastError();
 }
@@ -416,7 +423,7 @@ cudaError_t launch_round_check(const BatchView& v, int T, int grid, cudaStream_t
     auto kern = k_round_check<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+    kern<<<resident_grid(kern, 128, smem, grid), 128, smem, s>>>(v, v.max_obs_pad);
   }));
   return cudaGetLastError();
 }

@@ -503,7 +503,7 @@ cudaError_t launch_round_bisect_box(const BatchView& v, int T, int grid, cudaStr
     auto kern = k_round_bisect<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+    kern<<<resident_grid(kern, 128, smem, grid), 128, smem, s>>>(v, v.max_obs_pad);
   }));
   return cudaGetLastError();
 }
@@ -519,7 +519,7 @@ cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_
     auto kern = k_round_bisect<ND, TT, BB>;
     err = set_smem(kern, smem);
     if (err != cudaSuccess) return err;
-    kern<<<grid, 128, smem, s>>>(v, v.max_obs_pad);
+    kern<<<resident_grid(kern, 128, smem, grid), 128, smem, s>>>(v, v.max_obs_pad);
   }));
   return cudaGetLastError();
 }

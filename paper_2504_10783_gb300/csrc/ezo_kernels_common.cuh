@@ -547,4 +547,39 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
   return set_smem_impl(reinterpret_cast<const void*>(kernel), bytes);
 }
 
+// At most one wave of resident blocks (cached per kernel, block size, shared
+// memory and device): the round kernels loop over their work units with a
+// grid stride, so blocks beyond what the SMs hold at once would only be
+// dispatched to find no work.
+inline int resident_grid_impl(const void* kernel, int threads, size_t smem, int grid_cap) {
+  struct Entry {
+    const void* k;
+    int threads;
+    size_t smem;
+    int dev;
+    int blocks;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return grid_cap;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : cache)
+    if (e.k == kernel && e.threads == threads && e.smem == smem && e.dev == dev)
+      return std::max(1, std::min(grid_cap, e.blocks));
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || sms < 1) {
+    (void)cudaGetLastError();
+    return grid_cap;
+  }
+  cache.push_back(Entry{kernel, threads, smem, dev, per_sm * sms});
+  return std::max(1, std::min(grid_cap, per_sm * sms));
+}
+
+template <typename K>
+inline int resident_grid(K kernel, int threads, size_t smem, int grid_cap) {
+  return resident_grid_impl(reinterpret_cast<const void*>(kernel), threads, smem, grid_cap);
+}
+
 }  // namespace ezo
