@@ -224,7 +224,7 @@ void ezo_batch_free(ezo_batch* batch);
 ezo_status ezo_batch_reset(ezo_batch* batch, const double* v1, const double* v2, void* cuda_stream);
 
 /* Run modes. HOST_LOOP launches the round kernels per round and reads a
- * 16-byte round summary back to decide whether to go on; GRAPH captures one
+ * small round summary back to decide whether to go on; GRAPH captures one
  * round into a CUDA graph whose conditional WHILE node repeats it on the
  * device until no segment is active (one launch, no host round trips). */
 typedef enum { EZO_RUN_HOST_LOOP = 0, EZO_RUN_GRAPH = 1 } ezo_run_mode;
@@ -241,7 +241,8 @@ ezo_status ezo_batch_run(ezo_batch* batch, int32_t mode, void* cuda_stream);
  * paper's order, a host-driven launch loop); sequential = 2 ("wavefront")
  * keeps each path's order but runs the current segment of every path in one
  * batched run per wave; sequential = 0 inflates all segments speculatively
- * in one batched run and applies the same skip rule afterwards. All three
+ * in one batched run and applies the same skip rule afterwards on the device
+ * (one synchronisation at the end). All three
  * keep the same polytopes. Skipped segments report EZO_SEG_SKIPPED, segments
  * after a collision EZO_SEG_IDLE. Errors: EZO_ERR_CUDA. */
 ezo_status ezo_batch_run_path(ezo_batch* batch, int32_t sequential, int32_t mode, void* cuda_stream);
@@ -258,14 +259,25 @@ ezo_status ezo_batch_get_segment(const ezo_batch* batch, int32_t seg, int32_t* s
 ezo_status ezo_batch_get_polytope(const ezo_batch* batch, int32_t seg, int32_t* m, double* A, double* b);
 
 /* Every segment at once, for end-to-end readers: status[g] and m[g] (host,
- * n_seg entries each), and, when A / b are given, the first m_read = max_g
- * m[g] rows of every polytope into A (host, n_seg x rows x n, row major per
- * segment: segment g's row r at A[(g * rows + r) * n]) and b (n_seg x rows);
- * rows beyond m[g] are not meaningful. *m_read (nullable) receives m_read.
- * One state copy and one strided copy each for A and b. Synchronous.
- * EZO_ERR_CAPACITY when rows < m_read. */
+ * n_seg entries each), and, when A / b are given, the first m_read rows of
+ * every polytope into A (host, n_seg x rows x n, row major per segment:
+ * segment g's row r at A[(g * rows + r) * n]) and b (n_seg x rows); rows
+ * beyond m[g] are not meaningful. m_read >= max_g m[g]: when the buffers
+ * hold at most 4 MiB (n_seg x min(rows, m_cap) x (n + 1) doubles) every
+ * row up to min(rows, m_cap) is copied together with the states (one
+ * synchronisation), otherwise the states are read first and max_g m[g] rows
+ * follow. *m_read (nullable) receives m_read. One state copy and one strided
+ * copy each for A and b. Synchronous. EZO_ERR_CAPACITY when rows <
+ * max_g m[g]. */
 ezo_status ezo_batch_get_polytopes(const ezo_batch* batch, int32_t* status, int32_t* m, double* A, double* b,
                                    int32_t rows, int32_t* m_read, void* cuda_stream);
+
+/* Page-locked host memory (cudaMallocHost) for the host side of the copies
+ * above: copies into it run at the host link's rate without staging through
+ * a driver buffer. *out receives the buffer (NULL when bytes = 0); free it
+ * with ezo_host_free. Errors: EZO_ERR_INVALID_ARG (out NULL), EZO_ERR_CUDA. */
+ezo_status ezo_host_alloc(size_t bytes, void** out);
+void ezo_host_free(void* p);
 
 /* Row capacity per segment (m0 + n_f * n_it_max) and sample capacity. */
 ezo_status ezo_batch_capacity(const ezo_batch* batch, int32_t* m_cap, int32_t* s_cap);

@@ -628,7 +628,7 @@ ezo_status batch_free_device(ezo_batch* b) {
                   b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx, b->d_ga, b->d_gb,
                   b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0,
                   b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
-                  b->view.s_bits, b->view.s_ok, b->view.s_rows};
+                  b->view.s_bits, b->view.s_ok, b->view.s_rows, b->view.sm_seats};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_sum) cudaFreeHost(b->h_sum);
@@ -787,18 +787,20 @@ ezo_status build_graph(ezo_batch* b) {
 #endif
 }
 
-ezo_status run_graph(ezo_batch* b, cudaStream_t s) {
+// sync = false leaves the graph running on the stream (the host loop reads
+// the round summary every round, so it always ends synchronised)
+ezo_status run_graph(ezo_batch* b, cudaStream_t s, bool sync = true) {
   if (!b->gexec) {
     ezo_status st = build_graph(b);
     if (st != EZO_OK) return st;
   }
   EZO_CUDA(cudaGraphLaunch(b->gexec, s));
-  EZO_CUDA(cudaStreamSynchronize(s));
+  if (sync) EZO_CUDA(cudaStreamSynchronize(s));
   return EZO_OK;
 }
 
-ezo_status run_batch(ezo_batch* b, int mode, cudaStream_t s) {
-  if (mode == EZO_RUN_GRAPH) return run_graph(b, s);
+ezo_status run_batch(ezo_batch* b, int mode, cudaStream_t s, bool sync = true) {
+  if (mode == EZO_RUN_GRAPH) return run_graph(b, s, sync);
   return run_host_loop(b, s);
 }
 
@@ -948,6 +950,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   b->view.s_ld = n <= 8 ? 8 : EZO_MAX_DOF;
   EZO_ALLOC(b->view.s_p32, (long long)b->max_bisect_tiles * kTile * b->view.s_ld);
   EZO_ALLOC(b->view.s_d32, (long long)b->max_bisect_tiles * kTile * b->view.s_ld);
+  EZO_ALLOC(b->view.sm_seats, kSeatSlots);
 #undef EZO_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_sum, sizeof(RoundSummary));
   if (e != cudaSuccess) {
@@ -975,6 +978,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   EZO_H2D(b->d_b0, bh.data(), sizeof(double) * bh.size());
 #undef EZO_H2D
   if (e == cudaSuccess) e = cudaMemset(b->d_sum, 0, sizeof(RoundSummary));
+  if (e == cudaSuccess) e = cudaMemset(b->view.sm_seats, 0, sizeof(int) * kSeatSlots);
   if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, (size_t)std::max<long long>(1, b->total_s));
   if (e != cudaSuccess) {
     batch_free_device(b);
@@ -1059,6 +1063,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   b->tot_s1 = tot_s1;
   b->tot_np = tot_np;
   b->sms = sms;
+  b->view.n_sm = sms;
   b->grid_sample = std::max(1, std::min(b->max_sample_tiles * 8, sms * 16));
   b->grid_check = std::max(1, std::min(b->max_sample_tiles * b->T_check, sms * 16));
   b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * b->T_bisect, sms * 16));
@@ -1368,28 +1373,15 @@ ezo_status ezo_batch_run_path(ezo_batch* b, int32_t sequential, int32_t mode, vo
     }
     (void)mode;
   } else {
-    ezo_status st = run_batch(b, mode, s);
+    // every segment at once, then containment and the skip rule on the
+    // device, behind the run on the same stream: one synchronisation
+    ezo_status st = run_batch(b, mode, s, false);
     if (st != EZO_OK) return st;
     EZO_CUDA(cudaMemsetAsync(b->d_contained, 0, (size_t)B * L, s));
     cudaError_t e = launch_containment(b->view, b->d_contained, 1e-9, s);
-    if (e != cudaSuccess) return cuda_fail(e, "containment");
-    EZO_CUDA(cudaMemcpyAsync(contained.data(), b->d_contained, (size_t)B * L, cudaMemcpyDeviceToHost, s));
-    st = read_states(b, sts, s);
-    if (st != EZO_OK) return st;
-    std::vector<int> stopped(B, 0);
-    for (int g = 0; g < B; ++g) {
-      const int pf = b->path_first[g];
-      bool skip = stopped[pf] != 0;
-      for (int j = pf; j < g && !skip; ++j)
-        if (kept[j] && contained[(size_t)g * L + (j - pf)]) skip = true;
-      if (skip) {
-        st = set_status(b, g, stopped[pf] ? SEG_IDLE : SEG_SKIPPED, s);
-        if (st != EZO_OK) return st;
-        continue;
-      }
-      kept[g] = 1;
-      if (sts[g].status == SEG_IN_COLLISION) stopped[pf] = 1;
-    }
+    if (e == cudaSuccess) e = launch_path_skip(b->view, b->d_contained, s);
+    if (e != cudaSuccess) return cuda_fail(e, "containment and skip rule");
+    EZO_CUDA(cudaStreamSynchronize(s));
   }
   g_err.clear();
   return EZO_OK;
@@ -1425,7 +1417,24 @@ ezo_status ezo_batch_get_polytopes(const ezo_batch* b, int32_t* status, int32_t*
     return fail(EZO_ERR_INVALID_ARG, "ezo_batch_get_polytopes: bad argument");
   cudaStream_t s = (cudaStream_t)stream_v;
   std::vector<SegState> sts(b->B);
+  const size_t n = b->n, mc = b->m_cap;
+  const int all_rows = (int)std::min<size_t>((size_t)rows, mc);
+  // small batches: the states and every row the buffers hold in one pass
+  // (one synchronisation); large ones read the states first and copy only
+  // the rows in use
+  const bool one_pass = (A || bv) && (size_t)b->B * all_rows * (n + 1) * sizeof(double) <= (4u << 20);
+  auto copy_rows = [&](int r) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (A && r)
+      e = cudaMemcpy2DAsync(A, sizeof(double) * rows * n, b->d_A, sizeof(double) * mc * n, sizeof(double) * r * n,
+                            b->B, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && bv && r)
+      e = cudaMemcpy2DAsync(bv, sizeof(double) * rows, b->d_b, sizeof(double) * mc, sizeof(double) * r, b->B,
+                            cudaMemcpyDeviceToHost, s);
+    return e;
+  };
   EZO_CUDA(cudaMemcpyAsync(sts.data(), b->d_st, sizeof(SegState) * b->B, cudaMemcpyDeviceToHost, s));
+  if (one_pass) EZO_CUDA(copy_rows(all_rows));
   EZO_CUDA(cudaStreamSynchronize(s));
   int mmax = 0;
   for (int g = 0; g < b->B; ++g) {
@@ -1433,19 +1442,26 @@ ezo_status ezo_batch_get_polytopes(const ezo_batch* b, int32_t* status, int32_t*
     m[g] = sts[g].m;
     mmax = std::max(mmax, sts[g].m);
   }
-  if (m_read) *m_read = mmax;
+  if (m_read) *m_read = one_pass ? all_rows : mmax;
   if ((A || bv) && mmax > rows) return fail(EZO_ERR_CAPACITY, "ezo_batch_get_polytopes: rows below the largest m");
-  const size_t n = b->n, mc = b->m_cap;
-  // the first mmax rows of every segment: one strided copy each for A and b
-  if (A && mmax)
-    EZO_CUDA(cudaMemcpy2DAsync(A, sizeof(double) * rows * n, b->d_A, sizeof(double) * mc * n, sizeof(double) * mmax * n,
-                               b->B, cudaMemcpyDeviceToHost, s));
-  if (bv && mmax)
-    EZO_CUDA(cudaMemcpy2DAsync(bv, sizeof(double) * rows, b->d_b, sizeof(double) * mc, sizeof(double) * mmax, b->B,
-                               cudaMemcpyDeviceToHost, s));
-  EZO_CUDA(cudaStreamSynchronize(s));
+  if ((A || bv) && !one_pass) {
+    EZO_CUDA(copy_rows(mmax));
+    EZO_CUDA(cudaStreamSynchronize(s));
+  }
   g_err.clear();
   return EZO_OK;
+}
+
+ezo_status ezo_host_alloc(size_t bytes, void** out) {
+  if (!out) return fail(EZO_ERR_INVALID_ARG, "ezo_host_alloc: null output");
+  *out = nullptr;
+  if (bytes == 0) return EZO_OK;
+  EZO_CUDA(cudaMallocHost(out, bytes));
+  return EZO_OK;
+}
+
+void ezo_host_free(void* p) {
+  if (p) cudaFreeHost(p);
 }
 
 ezo_status ezo_batch_capacity(const ezo_batch* b, int32_t* m_cap, int32_t* s_cap) {
@@ -1502,8 +1518,9 @@ ezo_status ezo_batch_read(const ezo_batch* b, int32_t seg, int32_t what, void* d
       return EZO_OK;
     }
     case 10: {
-      if (bytes < (int64_t)sizeof(RoundSummary)) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
-      EZO_CUDA(cudaMemcpy(dst, b->d_sum, sizeof(RoundSummary), cudaMemcpyDeviceToHost));
+      // the public part of the summary: active, rounds, sample and bisection tiles
+      if (bytes < (int64_t)(4 * sizeof(int32_t))) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_read: buffer too small");
+      EZO_CUDA(cudaMemcpy(dst, b->d_sum, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost));
       return EZO_OK;
     }
     case 7: need = sizeof(int) * (size_t)b->prm.n_f; src = b->d_pidx + (size_t)seg * b->prm.n_f; break;

@@ -21,6 +21,7 @@ enum SegStatus : int {
 };
 
 constexpr int kTile = 128;  // samples / candidates per work tile
+constexpr int kSeatSlots = 1024;  // bound on the SM ids of a device (work-queue seats)
 // threads per block of the one-thread-per-candidate bisection kernels: small
 // blocks spread their FP64 work (1/64 of the FP32 rate) over many SMs
 constexpr int kRowBlock = 64;
@@ -65,6 +66,12 @@ struct RoundSummary {
   int round;
   int n_sample_tiles;
   int n_bisect_tiles;
+  // work queues of the sampling, label and bisection launches (one per
+  // bisection mode): units taken so far and blocks that have left; the last
+  // block of a launch to leave resets both for the next launch
+  int q_sample, left_sample;
+  int q_check, left_check;
+  int q_bisect[3], left_bisect[3];
 };
 
 // Everything a round kernel needs, by value (kernel parameter space).
@@ -122,6 +129,10 @@ struct BatchView {
   uint32_t* s_bits;  // [row] surrogate decisions
   uint8_t* s_ok;     // [row] 1 when the surrogate end point was verified in collision
   int* s_rows;       // device row count of this round (n_bisect_tiles * kTile)
+  // work-queue seats: working blocks per SM in the current launch
+  // ([kSeatSlots], indexed by the SM id; zero between launches)
+  int* sm_seats;
+  int n_sm;          // SMs of the device
 };
 
 // Launchers (ezo_kernels.cu). T = lanes per configuration.
@@ -158,6 +169,8 @@ cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 // (Sec. VI-A): contained[k*max_path_len + d] = 1 iff both endpoints of
 // segment k satisfy A_j x <= b_j + tol for j = path_first[k] + d < k.
 cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s);
+// the skip rule after a speculative run, from the containment flags
+cudaError_t launch_path_skip(const BatchView& v, const uint8_t* contained, cudaStream_t s);
 // round end fused with the next round's sizing (the run loops' last kernel)
 cudaError_t launch_round_close(const BatchView& v, cudaStream_t s);
 // recovery (Sec. VI-B)

@@ -161,8 +161,8 @@ __device__ __forceinline__ int sample_passes(const BatchView& v, int n_tiles, in
 // forms (SPLIT = true) are separate kernels, each with its own register
 // budget, launched one after the other, and the one not chosen returns at
 // once. Work units are (tile, pass) pairs: a tile of kTile walks takes one
-// pass at one lane per walk, or 2, 4 or 8 passes at 2, 4 or 8 lanes per walk,
-// and the passes of a tile go to different blocks.
+// pass at one lane per walk, or 2, 4 or 8 passes at 2, 4 or 8 lanes per walk;
+// blocks take them from the round's work queue.
 template <int NDOF, bool SPLIT>
 __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_below_tiles) {
   extern __shared__ float4 smf4[];
@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
   float* A32 = reinterpret_cast<float*>(smf4);
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();
-  for (int u = blockIdx.x; u < n_tiles * passes; u += gridDim.x) {
+  int* q = &v.summary->q_sample;
+  for (int u = queue_first(v, q, n_tiles * passes); u < n_tiles * passes; u = queue_take(q)) {
     const int2 tile = v.sample_tiles[u / passes];
     const SegState& st = v.st[tile.x];
     if (tile.x != cur_seg) {
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
     else if (passes == 4) sample_pass<NDOF, 4>(v, st, A32, p, tile, u % passes);
     else sample_pass<NDOF, 2>(v, st, A32, p, tile, u % passes);
   }
+  queue_leave(v, q, &v.summary->left_sample);
 }
 
 #endif  // !EZO_BOX_TU
@@ -210,6 +212,16 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
   extern __shared__ float4 smem4[];
   __shared__ RobotSmem rs;
   __shared__ int cur_env;
+  const int n_tiles = v.summary->n_sample_tiles;
+  constexpr int PASSES = kTile / (128 / T);
+  // work units are (tile, pass), taken from the round's work queue; a block
+  // that finds none leaves before staging anything
+  int* q = &v.summary->q_check;
+  int u = queue_first(v, q, n_tiles * PASSES);
+  if (u >= n_tiles * PASSES) {
+    queue_leave(v, q, &v.summary->left_check);
+    return;
+  }
   const RobotDev* robot = v.robot;
   const int nsp = robot->n_spheres_pad, nrbox = robot->n_box;
   const int groups = blockDim.x / T;
@@ -223,10 +235,7 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
   __syncthreads();
   const int gi = threadIdx.x / T, lg = threadIdx.x % T;
   float4* cen = gs.cen_all + gi * (nsp + 1);
-  const int n_tiles = v.summary->n_sample_tiles;
-  constexpr int PASSES = kTile / (128 / T);
-  // work units are (tile, pass): the passes of a tile go to different blocks
-  for (int u = blockIdx.x; u < n_tiles * PASSES; u += gridDim.x) {
+  for (; u < n_tiles * PASSES; u = queue_take(q)) {
     const int2 tile = v.sample_tiles[u / PASSES];
     const int sub = (u % PASSES) * groups;
     const SegState& st = v.st[tile.x];
@@ -253,6 +262,7 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
       if (valid && lg == 0) fl[i] = hit ? 1 : 0;
     }
   }
+  queue_leave(v, q, &v.summary->left_check);
 }
 
 #if !EZO_BOX_TU

@@ -154,7 +154,15 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
   __shared__ RobotSmem rs;
   __shared__ int cur_env;
   const int n_tiles = v.summary->n_bisect_tiles;
-  if (blockIdx.x >= n_tiles * T) return;  // no work unit for this block
+  // work units are (tile, pass), taken from this mode's work queue; a block
+  // that finds none leaves before staging anything
+  int* q = &v.summary->q_bisect[v.bis_mode];
+  int* left = &v.summary->left_bisect[v.bis_mode];
+  int u = queue_first(v, q, n_tiles * T);
+  if (u >= n_tiles * T) {
+    queue_leave(v, q, left);
+    return;
+  }
   const RobotDev* robot = v.robot;
   const int nsp = robot->n_spheres_pad, nrbox = robot->n_box;
   const int groups = blockDim.x / T;
@@ -171,8 +179,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
   const int ld = v.s_ld;
   const float scale = ldexpf(1.f, -v.n_b);
   static_assert(kTile % (128 / T) == 0, "tile must be a whole number of passes");
-  // work units are (tile, pass): the T passes of a tile go to different blocks
-  for (int u = blockIdx.x; u < n_tiles * T; u += gridDim.x) {
+  for (; u < n_tiles * T; u = queue_take(q)) {
     const int2 tile = v.bisect_tiles[u / T];
     const int sub = (u % T) * groups;
     const int g = tile.x;
@@ -245,6 +252,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
     }
     if (valid && lg == 0) v.bits[st.cand_off + c] = bits;
   }
+  queue_leave(v, q, left);
 }
 
 #if !EZO_BOX_TU
@@ -492,6 +500,32 @@ __global__ void k_containment(BatchView v, uint8_t* contained, double tol) {
   if (threadIdx.x == 0) contained[(long long)k * v.max_path_len + blockIdx.y] = s_out ? 0 : 1;
 }
 
+// The skip rule of Sec. VI-A after a speculative run, on the device: one
+// thread per path (its segments are consecutive, from path_first) walks the
+// segments in order; a segment is skipped when both its endpoints lie in the
+// polytope of an earlier kept segment of the path (contained), and every
+// segment after one reported in collision goes idle. A segment is kept when
+// its status is neither skipped nor idle once the earlier ones are decided.
+__global__ void k_path_skip(BatchView v, const uint8_t* __restrict__ contained) {
+  const int L = v.max_path_len;
+  for (int g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < v.B; g0 += gridDim.x * blockDim.x) {
+    if (v.path_first[g0] != g0) continue;
+    bool stopped = false;
+    for (int g = g0; g < v.B && v.path_first[g] == g0; ++g) {
+      bool skip = stopped;
+      for (int j = g0; j < g && !skip; ++j) {
+        const int sj = v.st[j].status;
+        if (sj != SEG_SKIPPED && sj != SEG_IDLE && contained[(long long)g * L + (j - g0)]) skip = true;
+      }
+      if (skip) {
+        v.st[g].status = stopped ? SEG_IDLE : SEG_SKIPPED;
+        continue;
+      }
+      if (v.st[g].status == SEG_IN_COLLISION) stopped = true;
+    }
+  }
+}
+
 #endif  // !EZO_BOX_TU
 
 #if EZO_BOX_TU
@@ -568,6 +602,11 @@ cudaError_t launch_round_end(const BatchView& v, cudaStream_t s) {
 cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s) {
   dim3 grid(v.B, v.max_path_len);
   k_containment<<<grid, 128, 0, s>>>(v, contained, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_path_skip(const BatchView& v, const uint8_t* contained, cudaStream_t s) {
+  k_path_skip<<<(v.B + 127) / 128, 128, 0, s>>>(v, contained);
   return cudaGetLastError();
 }
 

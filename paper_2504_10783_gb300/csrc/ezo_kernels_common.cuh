@@ -361,6 +361,63 @@ __device__ __forceinline__ void stage_polytope(float* A32, const double* __restr
   }
 }
 
+// ------------------------------------------------------------ work queue --
+// The round kernels take their work units from a counter in arrival order.
+// Blocks are dispatched SM by SM, so a round with fewer units than resident
+// blocks would otherwise crowd its units onto the first SMs: a block first
+// takes a seat on its SM, and only the first ceil(units / SMs) blocks of each
+// SM take units; the others leave at once. The seated blocks take units until
+// none is left, so every unit is done whatever the placement. queue_seat and
+// queue_take are called by every thread of the block together.
+__device__ __forceinline__ bool queue_seat(const BatchView& v, int units) {
+  __shared__ int s_seated;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    const int cap = v.n_sm > 0 ? (units + v.n_sm - 1) / v.n_sm : units;
+    s_seated = (sm >= (unsigned)kSeatSlots || !v.sm_seats) ? 1 : (atomicAdd(&v.sm_seats[sm], 1) < cap);
+  }
+  __syncthreads();
+  return s_seated != 0;
+}
+
+__device__ __forceinline__ int queue_take(int* q) {
+  __shared__ int s_unit;
+  __syncthreads();  // the previous unit's value has been read by every thread
+  if (threadIdx.x == 0) s_unit = atomicAdd(q, 1);
+  __syncthreads();
+  return s_unit;
+}
+
+// Called once by every block of the launch when it takes no more units: the
+// last block to leave resets the queue and the seats for the next launch
+// (every other block of the kernel is done with them by then).
+__device__ __forceinline__ void queue_leave(const BatchView& v, int* q, int* left) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(left, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    if (v.sm_seats)
+      for (int i = threadIdx.x; i < kSeatSlots; i += blockDim.x) v.sm_seats[i] = 0;
+    if (threadIdx.x == 0) {
+      atomicExch(q, 0);
+      atomicExch(left, 0);
+    }
+  }
+}
+
+// The first unit of a seated block, or `units` (none) for a block without a
+// seat; blocks that get none call queue_leave and return.
+__device__ __forceinline__ int queue_first(const BatchView& v, int* q, int units) {
+  if (!queue_seat(v, units)) return units;
+  return queue_take(q);
+}
+
 // ------------------------------------------------------------- round end --
 // Sec. IV-C "Maximum iterations": an active segment that ran N_it rounds
 // stops with EZO_SEG_MAX_ITER, the others move to the next round. Returns the

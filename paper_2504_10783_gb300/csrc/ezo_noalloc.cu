@@ -134,11 +134,11 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   const size_t pad = 256;
   const int s_ld = n <= 8 ? 8 : EZO_MAX_DOF;
   const size_t rows_b = (size_t)bi_tiles * kTile;
-  const size_t need = 2 * rows_b * s_ld * sizeof(float) + sizeof(SegState) + 2 * n * sizeof(double) + m_cap * n * sizeof(double) +
+  const size_t need = 2 * rows_b * s_ld * sizeof(float) + kSeatSlots * sizeof(int) + sizeof(SegState) + 2 * n * sizeof(double) + m_cap * n * sizeof(double) +
                       m_cap * sizeof(double) + s_cap * n * sizeof(float) + s_cap + (size_t)np * sizeof(int) +
                       (size_t)np * n * (2 * sizeof(double) + sizeof(float)) + (size_t)np * (2 * sizeof(double) + 8) +
                       (size_t)prm->n_f * (sizeof(int) + sizeof(double)) + (st_tiles + bi_tiles) * sizeof(int2) +
-                      sizeof(RoundSummary) + sizeof(EnvDevFull) + sizeof(int) + 26 * pad;
+                      sizeof(RoundSummary) + sizeof(EnvDevFull) + sizeof(int) + 27 * pad;
   if (need > (size_t)EZO_NOALLOC_SCRATCH_BYTES)
     return na_fail(EZO_ERR_CAPACITY, "this segment needs " + std::to_string(need) +
                                          " bytes of working memory, more than the fixed " +
@@ -179,6 +179,7 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   int* d_pf = c.take<int>(1);
   float* d_sp = c.take<float>(rows_b * s_ld);
   float* d_sd = c.take<float>(rows_b * s_ld);
+  int* d_seats = c.take<int>(kSeatSlots);
   if (c.off > (size_t)EZO_NOALLOC_SCRATCH_BYTES) return na_fail(EZO_ERR_CAPACITY, "scratch layout overflow");
 
   // initial contents: everything a kernel reads before writing it
@@ -221,6 +222,7 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   NA_CUDA(cudaMemcpyAsync(d_env, &envf, sizeof(envf), cudaMemcpyHostToDevice, s));
   NA_CUDA(cudaMemcpyAsync(d_pf, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   NA_CUDA(cudaMemsetAsync(d_flags, 0, (size_t)s_cap, s));
+  NA_CUDA(cudaMemsetAsync(d_seats, 0, sizeof(int) * kSeatSlots, s));
 
   v.B = 1;
   v.n = n;
@@ -270,10 +272,12 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   v.s_p32 = d_sp;
   v.s_d32 = d_sd;
   v.s_ld = s_ld;
+  v.sm_seats = d_seats;
 
   int dev = 0, sms = 1;
   NA_CUDA(cudaGetDevice(&dev));
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  v.n_sm = sms;
   const int T_check = check_lanes(s_cap), T_bis = bisect_lanes(np, ezo_internal_robot_boxes(robot) || envf.e.n_box);
   const int grid_s = (int)std::max<long long>(1, std::min<long long>(st_tiles * 8, (long long)sms * 16));
   const int grid_c = (int)std::max<long long>(1, std::min<long long>(st_tiles * T_check, (long long)sms * 16));

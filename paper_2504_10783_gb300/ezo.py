@@ -105,6 +105,9 @@ def _sig(lib):
     f.ezo_batch_attach_surrogate.argtypes = [_P, _P, C.c_float]
     f.ezo_batch_set_sample_lanes.argtypes = [_P, _I32]
     f.ezo_batch_get_polytopes.argtypes = [_P, C.POINTER(_I32), C.POINTER(_I32), _DP, _DP, _I32, C.POINTER(_I32), _P]
+    f.ezo_host_alloc.argtypes = [C.c_size_t, C.POINTER(C.c_void_p)]
+    f.ezo_host_free.argtypes = [C.c_void_p]
+    f.ezo_host_free.restype = None
     f.ezo_robot_add_boxes.argtypes = [_P, _I32, C.POINTER(_I32), _DP, _DP, _DP, _I32, C.POINTER(_I32), _I32,
                                       C.POINTER(_I32)]
     f.ezo_env_add_boxes.argtypes = [_P, _I32, _DP]
@@ -413,6 +416,10 @@ class Batch:
         if getattr(self, "h", None) and _lib is not None:
             _lib.ezo_batch_free(self.h)
             self.h = None
+        if getattr(self, "_pin", None) is not None and _lib is not None:
+            self._pin = None
+            for p in self._pin_ptrs:
+                _lib.ezo_host_free(p)
 
     def reset(self, v1=None, v2=None, stream=None):
         a1 = a2 = None
@@ -451,17 +458,34 @@ class Batch:
         return SegmentResult(st.value, rd.value, m.value, pl.value, ch.value, A[: mm.value].copy(),
                              b[: mm.value].copy())
 
+    def _pinned_io(self):
+        """Page-locked host buffers for polytopes(), made once per batch."""
+        if getattr(self, "_pin", None) is None:
+            B, mc, n = self.B, self.m_cap, self.n
+            sizes = ((B,), (B,), (B, mc, n), (B, mc))
+            dts = (np.int32, np.int32, np.float64, np.float64)
+            arrs, ptrs = [], []
+            for shape, dt in zip(sizes, dts):
+                nbytes = int(np.prod(shape)) * np.dtype(dt).itemsize
+                p = C.c_void_p()
+                _check(lib().ezo_host_alloc(nbytes, C.byref(p)))
+                ptrs.append(p.value)
+                buf = (C.c_char * nbytes).from_address(p.value)
+                arrs.append(np.frombuffer(buf, dtype=dt).reshape(shape))
+            self._pin, self._pin_ptrs = arrs, ptrs
+        return self._pin
+
     def polytopes(self, stream=None):
-        """Every segment's (status, A, b) with three device-to-host copies:
-        returns (status int32 [B], list of A [m_g, n], list of b [m_g])."""
-        st = np.zeros(self.B, dtype=np.int32)
-        m = np.zeros(self.B, dtype=np.int32)
-        A = np.empty((self.B, self.m_cap, self.n))
-        b = np.empty((self.B, self.m_cap))
+        """Every segment's (status, A, b) with three device-to-host copies
+        into page-locked buffers: returns (status int32 [B], list of A
+        [m_g, n], list of b [m_g]) as copies; rows_read is then the rows
+        copied per segment."""
+        st, m, A, b = self._pinned_io()
         mr = _I32()
         _check(lib().ezo_batch_get_polytopes(self.h, st.ctypes.data_as(C.POINTER(_I32)), m.ctypes.data_as(C.POINTER(_I32)),
                                              _dp(A), _dp(b), self.m_cap, C.byref(mr), _stream(stream)))
-        return st, [A[g, : m[g]] for g in range(self.B)], [b[g, : m[g]] for g in range(self.B)]
+        self.rows_read = int(mr.value)  # rows copied per segment (>= max m)
+        return st.copy(), [A[g, : m[g]].copy() for g in range(self.B)], [b[g, : m[g]].copy() for g in range(self.B)]
 
     def state(self, g: int) -> dict:
         o = np.zeros(13, dtype=np.int32)
