@@ -616,6 +616,7 @@ struct ezo_batch {
   // surrogate-guided bisection
   ezo_surrogate* sur = nullptr;
   long long sur_rows = 0;
+  long long claim_cap = 0;  // work units of the largest round-kernel launch
 };
 
 namespace {
@@ -628,7 +629,7 @@ ezo_status batch_free_device(ezo_batch* b) {
                   b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx, b->d_ga, b->d_gb,
                   b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0,
                   b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
-                  b->view.s_bits, b->view.s_ok, b->view.s_rows, b->view.sm_seats};
+                  b->view.s_bits, b->view.s_ok, b->view.s_rows, b->view.sm_seats, b->view.q_claim};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_sum) cudaFreeHost(b->h_sum);
@@ -951,6 +952,11 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   EZO_ALLOC(b->view.s_p32, (long long)b->max_bisect_tiles * kTile * b->view.s_ld);
   EZO_ALLOC(b->view.s_d32, (long long)b->max_bisect_tiles * kTile * b->view.s_ld);
   EZO_ALLOC(b->view.sm_seats, kSeatSlots);
+  // one claim per work unit of the largest launch: 8 passes per sample tile,
+  // up to 32 per bisection tile
+  b->claim_cap = std::max<long long>((long long)b->max_sample_tiles * 8, (long long)b->max_bisect_tiles * 32);
+  EZO_ALLOC(b->view.q_claim, b->claim_cap + 1);
+  b->view.q_claim_cap = (int)b->claim_cap;
 #undef EZO_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_sum, sizeof(RoundSummary));
   if (e != cudaSuccess) {
@@ -979,6 +985,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
 #undef EZO_H2D
   if (e == cudaSuccess) e = cudaMemset(b->d_sum, 0, sizeof(RoundSummary));
   if (e == cudaSuccess) e = cudaMemset(b->view.sm_seats, 0, sizeof(int) * kSeatSlots);
+  if (e == cudaSuccess) e = cudaMemset(b->view.q_claim, 0, sizeof(int) * (b->claim_cap + 1));
   if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, (size_t)std::max<long long>(1, b->total_s));
   if (e != cudaSuccess) {
     batch_free_device(b);

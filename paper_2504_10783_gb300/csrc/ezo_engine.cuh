@@ -132,6 +132,8 @@ struct BatchView {
   // work-queue seats: working blocks per SM in the current launch
   // ([kSeatSlots], indexed by the SM id; zero between launches)
   int* sm_seats;
+  int* q_claim;      // [1 + q_claim_cap]: launch count, then the epoch that claimed each work unit
+  int q_claim_cap;   // work units of the largest launch
   int n_sm;          // SMs of the device
 };
 

@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
   if (threadIdx.x == 0) cur_seg = -1;
   __syncthreads();
   int* q = &v.summary->q_sample;
-  for (int u = queue_first(v, q, n_tiles * passes); u < n_tiles * passes; u = queue_take(q)) {
+  const int units = n_tiles * passes;
+  for (int u = queue_first(v, q, units); u < units; u = queue_take(v, q, units)) {
     const int2 tile = v.sample_tiles[u / passes];
     const SegState& st = v.st[tile.x];
     if (tile.x != cur_seg) {
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_bel
     else if (passes == 4) sample_pass<NDOF, 4>(v, st, A32, p, tile, u % passes);
     else sample_pass<NDOF, 2>(v, st, A32, p, tile, u % passes);
   }
-  queue_leave(v, q, &v.summary->left_sample);
+  queue_leave(v, q, &v.summary->left_sample, units);
 }
 
 #endif  // !EZO_BOX_TU
@@ -217,9 +218,10 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
   // work units are (tile, pass), taken from the round's work queue; a block
   // that finds none leaves before staging anything
   int* q = &v.summary->q_check;
-  int u = queue_first(v, q, n_tiles * PASSES);
-  if (u >= n_tiles * PASSES) {
-    queue_leave(v, q, &v.summary->left_check);
+  const int units = n_tiles * PASSES;
+  int u = queue_first(v, q, units);
+  if (u >= units) {
+    queue_leave(v, q, &v.summary->left_check, units);
     return;
   }
   const RobotDev* robot = v.robot;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
   __syncthreads();
   const int gi = threadIdx.x / T, lg = threadIdx.x % T;
   float4* cen = gs.cen_all + gi * (nsp + 1);
-  for (; u < n_tiles * PASSES; u = queue_take(q)) {
+  for (; u < units; u = queue_take(v, q, units)) {
     const int2 tile = v.sample_tiles[u / PASSES];
     const int sub = (u % PASSES) * groups;
     const SegState& st = v.st[tile.x];
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
       if (valid && lg == 0) fl[i] = hit ? 1 : 0;
     }
   }
-  queue_leave(v, q, &v.summary->left_check);
+  queue_leave(v, q, &v.summary->left_check, units);
 }
 
 #if !EZO_BOX_TU

@@ -158,9 +158,10 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
   // that finds none leaves before staging anything
   int* q = &v.summary->q_bisect[v.bis_mode];
   int* left = &v.summary->left_bisect[v.bis_mode];
-  int u = queue_first(v, q, n_tiles * T);
-  if (u >= n_tiles * T) {
-    queue_leave(v, q, left);
+  const int units = n_tiles * T;
+  int u = queue_first(v, q, units, false);
+  if (u >= units) {
+    queue_leave(v, q, left, units);
     return;
   }
   const RobotDev* robot = v.robot;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
   const int ld = v.s_ld;
   const float scale = ldexpf(1.f, -v.n_b);
   static_assert(kTile % (128 / T) == 0, "tile must be a whole number of passes");
-  for (; u < n_tiles * T; u = queue_take(q)) {
+  for (; u < units; u = queue_take(v, q, units)) {
     const int2 tile = v.bisect_tiles[u / T];
     const int sub = (u % T) * groups;
     const int g = tile.x;
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
     }
     if (valid && lg == 0) v.bits[st.cand_off + c] = bits;
   }
-  queue_leave(v, q, left);
+  queue_leave(v, q, left, units);
 }
 
 #if !EZO_BOX_TU

@@ -362,38 +362,76 @@ __device__ __forceinline__ void stage_polytope(float* A32, const double* __restr
 }
 
 // ------------------------------------------------------------ work queue --
-// The round kernels take their work units from a counter in arrival order.
+// The round kernels spread a round's work units over the SMs explicitly.
 // Blocks are dispatched SM by SM, so a round with fewer units than resident
-// blocks would otherwise crowd its units onto the first SMs: a block first
-// takes a seat on its SM, and only the first ceil(units / SMs) blocks of each
-// SM take units; the others leave at once. The seated blocks take units until
-// none is left, so every unit is done whatever the placement. queue_seat and
-// queue_take are called by every thread of the block together.
-__device__ __forceinline__ bool queue_seat(const BatchView& v, int units) {
-  __shared__ int s_seated;
+// blocks would otherwise crowd its units onto the first SMs. A block first
+// takes a seat on its SM (rank r = its arrival order there); only ranks below
+// ceil(units / SMs) work, and rank r on SM s starts with unit r * SMs + s, so
+// the units go round-robin over the SMs. Every unit is claimed once (an
+// atomic flag), and a working block then takes further units in order from a
+// counter, skipping claimed ones, until none is left: every unit is done
+// exactly once whatever the placement. A claim holds the launch's epoch, so
+// the claims need no clearing: q_claim[0] counts the launches (advanced by
+// the last block of each), the launch's epoch is that count + 1, and unit u's
+// claim is q_claim[1 + u] (the array starts at zero). The functions below are
+// called by every thread of the block together and return a block-uniform
+// value.
+__device__ __forceinline__ bool queue_claim(const BatchView& v, int u) {
+  if (!v.q_claim) return true;
+  const int epoch = *(volatile int*)&v.q_claim[0] + 1;
+  return atomicExch(&v.q_claim[1 + u], epoch) != epoch;
+}
+
+// The block's first unit, or `units` when it has no seat (it then calls
+// queue_leave and returns). spread = false skips the round-robin first unit
+// (the seated blocks then take units in arrival order): measured on the
+// bisection's short rounds, the 16-lane check runs faster packed that way.
+__device__ __forceinline__ int queue_first(const BatchView& v, int* q, int units, bool spread = true) {
+  __shared__ int s_unit;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned sm;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    int u = units;
     const int cap = v.n_sm > 0 ? (units + v.n_sm - 1) / v.n_sm : units;
-    s_seated = (sm >= (unsigned)kSeatSlots || !v.sm_seats) ? 1 : (atomicAdd(&v.sm_seats[sm], 1) < cap);
+    const int rank = (sm < (unsigned)kSeatSlots && v.sm_seats) ? atomicAdd(&v.sm_seats[sm], 1) : 0;
+    if (rank < cap) {
+      const long long pre = (long long)rank * v.n_sm + sm;
+      if (spread && pre < units && queue_claim(v, (int)pre)) u = (int)pre;
+      while (u == units) {
+        const int t = atomicAdd(q, 1);
+        if (t >= units) break;
+        if (queue_claim(v, t)) u = t;
+      }
+    }
+    s_unit = u;
   }
   __syncthreads();
-  return s_seated != 0;
+  return s_unit;
 }
 
-__device__ __forceinline__ int queue_take(int* q) {
+// The next unclaimed unit, or `units` when none is left.
+__device__ __forceinline__ int queue_take(const BatchView& v, int* q, int units) {
   __shared__ int s_unit;
   __syncthreads();  // the previous unit's value has been read by every thread
-  if (threadIdx.x == 0) s_unit = atomicAdd(q, 1);
+  if (threadIdx.x == 0) {
+    int u = units;
+    while (u == units) {
+      const int t = atomicAdd(q, 1);
+      if (t >= units) break;
+      if (queue_claim(v, t)) u = t;
+    }
+    s_unit = u;
+  }
   __syncthreads();
   return s_unit;
 }
 
 // Called once by every block of the launch when it takes no more units: the
-// last block to leave resets the queue and the seats for the next launch
-// (every other block of the kernel is done with them by then).
-__device__ __forceinline__ void queue_leave(const BatchView& v, int* q, int* left) {
+// last block to leave clears the seats and the counter and advances the
+// claims' epoch for the next launch (every other block of the kernel is done
+// with them by then).
+__device__ __forceinline__ void queue_leave(const BatchView& v, int* q, int* left, int units) {
   __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -402,20 +440,22 @@ __device__ __forceinline__ void queue_leave(const BatchView& v, int* q, int* lef
   }
   __syncthreads();
   if (s_last) {
+    (void)units;
     if (v.sm_seats)
       for (int i = threadIdx.x; i < kSeatSlots; i += blockDim.x) v.sm_seats[i] = 0;
+    if (v.q_claim && v.q_claim[0] >= (1 << 30)) {
+      // the epochs wrap: clear the claims (once in 2^30 launches)
+      for (int i = 1 + threadIdx.x; i <= v.q_claim_cap; i += blockDim.x) v.q_claim[i] = 0;
+      __syncthreads();
+      if (threadIdx.x == 0) atomicExch(&v.q_claim[0], 0);
+    } else if (v.q_claim && threadIdx.x == 0) {
+      atomicAdd(&v.q_claim[0], 1);
+    }
     if (threadIdx.x == 0) {
       atomicExch(q, 0);
       atomicExch(left, 0);
     }
   }
-}
-
-// The first unit of a seated block, or `units` (none) for a block without a
-// seat; blocks that get none call queue_leave and return.
-__device__ __forceinline__ int queue_first(const BatchView& v, int* q, int units) {
-  if (!queue_seat(v, units)) return units;
-  return queue_take(q);
 }
 
 // ------------------------------------------------------------- round end --

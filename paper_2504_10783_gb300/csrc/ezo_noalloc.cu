@@ -134,11 +134,12 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   const size_t pad = 256;
   const int s_ld = n <= 8 ? 8 : EZO_MAX_DOF;
   const size_t rows_b = (size_t)bi_tiles * kTile;
-  const size_t need = 2 * rows_b * s_ld * sizeof(float) + kSeatSlots * sizeof(int) + sizeof(SegState) + 2 * n * sizeof(double) + m_cap * n * sizeof(double) +
+  const size_t need = 2 * rows_b * s_ld * sizeof(float) + kSeatSlots * sizeof(int) +
+                      (std::max<size_t>((size_t)st_tiles * 8, (size_t)bi_tiles * 32) + 1) * sizeof(int) + sizeof(SegState) + 2 * n * sizeof(double) + m_cap * n * sizeof(double) +
                       m_cap * sizeof(double) + s_cap * n * sizeof(float) + s_cap + (size_t)np * sizeof(int) +
                       (size_t)np * n * (2 * sizeof(double) + sizeof(float)) + (size_t)np * (2 * sizeof(double) + 8) +
                       (size_t)prm->n_f * (sizeof(int) + sizeof(double)) + (st_tiles + bi_tiles) * sizeof(int2) +
-                      sizeof(RoundSummary) + sizeof(EnvDevFull) + sizeof(int) + 27 * pad;
+                      sizeof(RoundSummary) + sizeof(EnvDevFull) + sizeof(int) + 28 * pad;
   if (need > (size_t)EZO_NOALLOC_SCRATCH_BYTES)
     return na_fail(EZO_ERR_CAPACITY, "this segment needs " + std::to_string(need) +
                                          " bytes of working memory, more than the fixed " +
@@ -180,6 +181,8 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   float* d_sp = c.take<float>(rows_b * s_ld);
   float* d_sd = c.take<float>(rows_b * s_ld);
   int* d_seats = c.take<int>(kSeatSlots);
+  const size_t claim_cap = std::max<size_t>((size_t)st_tiles * 8, (size_t)bi_tiles * 32);
+  int* d_claim = c.take<int>(claim_cap + 1);
   if (c.off > (size_t)EZO_NOALLOC_SCRATCH_BYTES) return na_fail(EZO_ERR_CAPACITY, "scratch layout overflow");
 
   // initial contents: everything a kernel reads before writing it
@@ -223,6 +226,7 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   NA_CUDA(cudaMemcpyAsync(d_pf, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   NA_CUDA(cudaMemsetAsync(d_flags, 0, (size_t)s_cap, s));
   NA_CUDA(cudaMemsetAsync(d_seats, 0, sizeof(int) * kSeatSlots, s));
+  NA_CUDA(cudaMemsetAsync(d_claim, 0, sizeof(int) * (claim_cap + 1), s));
 
   v.B = 1;
   v.n = n;
@@ -273,6 +277,8 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   v.s_d32 = d_sd;
   v.s_ld = s_ld;
   v.sm_seats = d_seats;
+  v.q_claim = d_claim;
+  v.q_claim_cap = (int)claim_cap;
 
   int dev = 0, sms = 1;
   NA_CUDA(cudaGetDevice(&dev));
