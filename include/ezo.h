@@ -294,8 +294,10 @@ ezo_status ezo_batch_set_sample_lanes(ezo_batch* batch, int32_t lanes);
  * round up, two from this many, four from a quarter, else eight (default:
  * the tiles that fill every scheduler with one warp, 4 x SMs x 32 / 128);
  * check_lanes: lanes per configuration of the label kernel (1, 2, 4 or 8);
- * bisect_lanes: lanes per bisection candidate (1, 2, 4, 8, 16 or 32; scenes
- * with boxes run 16 and 32 at 8). Every shape gives the same samples and
+ * bisect_lanes: lanes per bisection candidate (1, 2, 4, 8, 16 or 32), or 96:
+ * three warps per candidate testing the three points of two halvings at
+ * once (fewer dependent checks, half again the checks; scenes with boxes
+ * run 16, 32 and 96 at 8). Every shape gives the same samples and
  * polytopes, and the same labels outside the FP32 rounding band of a
  * contact, bit for bit; only the speed differs. */
 typedef struct {
@@ -308,7 +310,7 @@ ezo_status ezo_batch_get_shape(const ezo_batch* batch, ezo_shape* shape);
  * graph is rebuilt at the next graph run. */
 ezo_status ezo_batch_set_shape(ezo_batch* batch, const ezo_shape* shape);
 /* Autotuner of the shape: runs the whole batch (host-loop mode, best of
- * `reps` timed runs after a warm-up) for the bisection lanes 4, 8, 16, 32, 2, then
+ * `reps` timed runs after a warm-up) for the bisection lanes 4, 8, 16, 32, 96, 2, then
  * the label lanes 1, 2, 4, 8, then sample_fill_tiles at half, one and two
  * times the default, keeping a change only when it is at least 2% faster,
  * and sets the winner. Results are cached for the process per (device, robot

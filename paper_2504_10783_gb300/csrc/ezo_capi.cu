@@ -1139,7 +1139,8 @@ ezo_status ezo_batch_get_shape(const ezo_batch* b, ezo_shape* sh) {
 ezo_status ezo_batch_set_shape(ezo_batch* b, const ezo_shape* sh) {
   if (!b || !sh) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_shape: bad argument");
   auto lanes_ok = [](int t) { return t == 1 || t == 2 || t == 4 || t == 8; };
-  const bool bis_ok = lanes_ok(sh->bisect_lanes) || sh->bisect_lanes == 16 || sh->bisect_lanes == 32;
+  const bool bis_ok = lanes_ok(sh->bisect_lanes) || sh->bisect_lanes == 16 || sh->bisect_lanes == 32 ||
+                      sh->bisect_lanes == kBisectPairLanes;
   if (sh->sample_fill_tiles < 1 || !lanes_ok(sh->check_lanes) || !bis_ok)
     return fail(EZO_ERR_INVALID_ARG,
                 "ezo_batch_set_shape: sample_fill_tiles >= 1, check lanes 1, 2, 4 or 8, bisect lanes 1 to 32");
@@ -1194,10 +1195,11 @@ ezo_status ezo_batch_tune(ezo_batch* b, int32_t reps, ezo_shape* chosen, void* s
     float best_ms = 1e30f;
     ezo_status st = time_shape(best, &best_ms);
     const int S = (b->sms * 4 * 32) / kTile;
-    const int bis[5] = {4, 8, 16, 32, 2}, chk[4] = {1, 2, 4, 8}, fill[3] = {std::max(1, S / 2), S, 2 * S};
+    const int bis[6] = {4, 8, 16, 32, kBisectPairLanes, 2}, chk[4] = {1, 2, 4, 8},
+              fill[3] = {std::max(1, S / 2), S, 2 * S};
     for (int stage = 0; stage < 3 && st == EZO_OK; ++stage) {
       const int* cand = stage == 0 ? bis : (stage == 1 ? chk : fill);
-      const int nc = stage == 0 ? 5 : (stage == 1 ? 4 : 3);
+      const int nc = stage == 0 ? 6 : (stage == 1 ? 4 : 3);
       for (int i = 0; i < nc && st == EZO_OK; ++i) {
         ezo_shape sh = best;
         if (stage == 0) sh.bisect_lanes = cand[i];

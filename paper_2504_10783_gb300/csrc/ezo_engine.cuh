@@ -22,6 +22,9 @@ enum SegStatus : int {
 
 constexpr int kTile = 128;  // samples / candidates per work tile
 constexpr int kSeatSlots = 1024;  // bound on the SM ids of a device (work-queue seats)
+// bisect_lanes value of the two-halvings-at-a-time bisection (three warps,
+// 96 lanes, per candidate)
+constexpr int kBisectPairLanes = 96;
 // threads per block of the one-thread-per-candidate bisection kernels: small
 // blocks spread their FP64 work (1/64 of the FP32 rate) over many SMs
 constexpr int kRowBlock = 64;

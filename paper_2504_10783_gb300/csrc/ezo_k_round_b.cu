@@ -257,6 +257,111 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
 }
 
 #if !EZO_BOX_TU
+// Two halvings at a time, three warps per candidate (sphere scenes; bisection
+// modes 0 and 2). Halving s tests the bracket's midpoint lo + 2h and halving
+// s + 1 then tests lo + h if that collided, else lo + 3h (h = 2^(N_b-2-s) in
+// units of 2^-N_b): warps 0, 1, 2 test lo + h, lo + 2h, lo + 3h together, each
+// with the 32-lane check, and the two decisions follow from the three labels
+// exactly as the two halvings would take them, so the record and the end
+// point are the sequential halvings' bit for bit. Half the dependent checks
+// for half again the checks; an odd last halving is warp 1's alone.
+template <int NDOF>
+__global__ void __launch_bounds__(96) k_round_bisect_pair(BatchView v, int max_obs_pad) {
+  extern __shared__ float4 smem4[];
+  __shared__ RobotSmem rs;
+  __shared__ int cur_env;
+  __shared__ int s_hit[3];
+  const int n_tiles = v.summary->n_bisect_tiles;
+  int* q = &v.summary->q_bisect[v.bis_mode];
+  int* left = &v.summary->left_bisect[v.bis_mode];
+  const int units = n_tiles * kTile;  // one candidate row per unit
+  int u = queue_first(v, q, units, false);
+  if (u >= units) {
+    queue_leave(v, q, left, units);
+    return;
+  }
+  const RobotDev* robot = v.robot;
+  const int nsp = robot->n_spheres_pad;
+  const GeomSmem gs = carve_geom(smem4, nsp, max_obs_pad, 3, 0, 0);
+  float4* sph_s = gs.sph;
+  float4* obs_s = gs.obs;
+  float* nhw_s = gs.nhw;
+  stage_robot(rs, sph_s, robot);
+  if (threadIdx.x == 0) cur_env = -1;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lg = threadIdx.x & 31;
+  float4* cen = gs.cen_all + w * (nsp + 1);
+  const BoxCtx bx{};
+  const int ld = v.s_ld;
+  const int nb = v.n_b;
+  const float scale = ldexpf(1.f, -nb);
+  for (; u < units; u = queue_take(v, q, units)) {
+    const int2 tile = v.bisect_tiles[u / kTile];
+    const int c = tile.y + u % kTile;
+    const int g = tile.x;
+    const SegState& st = v.st[g];
+    const EnvDevFull& ef = v.envs[st.env];
+    if (st.env != cur_env) {
+      __syncthreads();
+      stage_env(obs_s, nhw_s, ef.e);
+      if (threadIdx.x == 0) cur_env = st.env;
+      __syncthreads();
+    }
+    const int n_obs = ef.e.n_obs, n_obs_pad = ef.e.n_obs_pad;
+    const float E = ef.E;
+    const ushort2* self_pairs = robot->self_pairs;
+    const float* self_rr = robot->self_rr;
+    bool valid = c < st.n_cand;
+    if (v.bis_mode == 2) valid = valid && !v.s_ok[u];
+    if (!valid) continue;  // the whole block: u is the block's
+    float p32[NDOF], dv32[NDOF];
+#pragma unroll
+    for (int j = 0; j < NDOF; ++j) {
+      p32[j] = j < ld ? v.s_p32[(long long)u * ld + j] : 0.f;
+      dv32[j] = j < ld ? v.s_d32[(long long)u * ld + j] : 0.f;
+    }
+    if (v.bis_mode == 2 && threadIdx.x == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks), (unsigned long long)nb);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&v.st[g].checks_bisect), (unsigned long long)nb);
+    }
+    uint32_t lo_u = 0u, bits = 0u;
+    for (int s = 0; s < nb; s += 2) {
+      const bool pair = s + 1 < nb;
+      const uint32_t h = pair ? 1u << (nb - 2 - s) : 0u;
+      // pair: warp w tests lo + (w + 1) h; single: warp 1 tests the midpoint
+      const uint32_t mid_u = pair ? lo_u + (uint32_t)(w + 1) * h : lo_u + (1u << (nb - 1 - s));
+      if (pair || w == 1) {
+        const float f = __uint2float_rn(mid_u) * scale;
+        float qq[NDOF];
+#pragma unroll
+        for (int j = 0; j < NDOF; ++j) qq[j] = fmaf(f, dv32[j], p32[j]);
+        const bool hit =
+            collide_wide<NDOF, 32>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, self_pairs, self_rr, E, cen, lg, bx);
+        if (lg == 0) s_hit[w] = hit ? 1 : 0;
+      }
+      __syncthreads();
+      const bool h1 = s_hit[0] != 0, h2 = s_hit[1] != 0, h3 = s_hit[2] != 0;
+      __syncthreads();  // read before the next step's labels are written
+      if (!pair) {
+        if (h2) bits |= 1u << s;
+        else lo_u += 1u << (nb - 1 - s);
+      } else if (h2) {
+        bits |= 1u << s;
+        if (h1) bits |= 1u << (s + 1);
+        else lo_u += h;
+      } else {
+        lo_u += 2u * h;
+        if (h3) bits |= 1u << (s + 1);
+        else lo_u += h;
+      }
+    }
+    if (threadIdx.x == 0) v.bits[st.cand_off + c] = bits;
+  }
+  queue_leave(v, q, left, units);
+}
+#endif  // !EZO_BOX_TU
+
+#if !EZO_BOX_TU
 
 // Greedy placement: repeatedly take the closest surviving candidate (ties by
 // sample index), place a_i^T x <= b_i - Delta_i, discard candidates with
@@ -547,6 +652,18 @@ cudaError_t launch_round_bisect_box(const BatchView& v, int T, int grid, cudaStr
 // scenes run at 8)
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s) {
   if (v.n_rbox || v.max_ebox) return launch_round_bisect_box(v, T > 8 ? 8 : T, grid, s);
+  if (T == kBisectPairLanes && v.bis_mode == 1) T = 32;  // one check per candidate: the 32-lane kernel
+  if (T == kBisectPairLanes) {
+    cudaError_t err = cudaSuccess;
+    const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 96, 32, 0, 0);
+    EZO_DISPATCH_NDOF(v.n, {
+      auto kern = k_round_bisect_pair<ND>;
+      err = set_smem(kern, smem);
+      if (err != cudaSuccess) return err;
+      kern<<<resident_grid(kern, 96, smem, std::max(grid, 1) * 4), 96, smem, s>>>(v, v.max_obs_pad);
+    });
+    return cudaGetLastError();
+  }
   cudaError_t err = cudaSuccess;
   const size_t smem = check_smem_layout(v.nsp_pad, v.max_obs_pad, 128, T, v.n_rbox, v.max_ebox);
   constexpr bool BB = EZO_BOX_TU != 0;

@@ -886,7 +886,7 @@ def test_round_kernel_shapes_are_bit_identical_and_tuned(ezo):
         return [bt.segment(g) for g in range(K)]
 
     ref = run()
-    for sh in ((1, 1, 2), (S // 2, 4, 4), (2 * S, 8, 1), (100000, 2, 8), (S, 2, 16), (S, 4, 32)):
+    for sh in ((1, 1, 2), (S // 2, 4, 4), (2 * S, 8, 1), (100000, 2, 8), (S, 2, 16), (S, 4, 32), (S, 2, 96)):
         bt.set_shape(*sh)
         got = run()
         for a, b in zip(got, ref):
@@ -898,7 +898,7 @@ def test_round_kernel_shapes_are_bit_identical_and_tuned(ezo):
     with pytest.raises(ezo.EzoError):
         bt.set_shape(S, 2, 64)
     tuned = bt.tune(reps=1)
-    assert tuned["check_lanes"] in (1, 2, 4, 8) and tuned["bisect_lanes"] in (2, 4, 8, 16, 32)
+    assert tuned["check_lanes"] in (1, 2, 4, 8) and tuned["bisect_lanes"] in (2, 4, 8, 16, 32, 96)
     assert bt.shape() == tuned
     got = run()
     for a, b in zip(got, ref):
