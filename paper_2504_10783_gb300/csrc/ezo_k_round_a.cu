@@ -163,8 +163,12 @@ __device__ __forceinline__ int sample_passes(const BatchView& v, int n_tiles, in
 // once. Work units are (tile, pass) pairs: a tile of kTile walks takes one
 // pass at one lane per walk, or 2, 4 or 8 passes at 2, 4 or 8 lanes per walk;
 // blocks take them from the round's work queue.
+// Register budgets: the one-lane form of chains up to 7 joints is held to 72
+// registers (seven blocks per SM, no spills), which a round of ten segments'
+// 1e4 walks fills in one wave; the shared forms to five blocks per SM.
 template <int NDOF, bool SPLIT>
-__global__ void __launch_bounds__(128) k_round_sample(BatchView v, int split_below_tiles) {
+__global__ void __launch_bounds__(128, NDOF <= 7 ? (SPLIT ? 5 : 7) : 4)
+    k_round_sample(BatchView v, int split_below_tiles) {
   extern __shared__ float4 smf4[];
   __shared__ SampleParams p;
   __shared__ int cur_seg;
