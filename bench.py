@@ -33,10 +33,12 @@ PARAMS = dict(eps=0.05, delta=0.05, tau=0.5, step_back_max=0.01, t_col=1e-3, n_p
               n_it_max=50, seed=1)
 N_SEEDS = 20
 SEGSTATE_BYTES = 112  # sizeof(SegState): per-segment device state read back with the polytopes
-# DRAM bytes per launch of the round kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum, ncu, this workload); None where not captured for the
-# current kernel
-TRAFFIC = {"sample": 87552, "check": 2892288, "bisect": 2760704}  # one round of the 10 segments
+# DRAM bytes of one round step (dram__bytes_read.sum + dram__bytes_write.sum,
+# ncu, the second round of this workload's 10 segments), summed over the
+# step's kernels: sampling = the one-lane and the shared-walk kernels,
+# bisection = projection, halvings and end points; None where not captured
+# for the current kernels
+TRAFFIC = {"sample": 55552 + 46336, "check": 1497600, "bisect": 466944 + 140800 + 485376}
 # DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe);
 # None until captured for the current kernel
 CHECKER_TRAFFIC_2E6 = 56084992 + 153600
