@@ -41,7 +41,7 @@ SEGSTATE_BYTES = 112  # sizeof(SegState): per-segment device state read back wit
 TRAFFIC = {"sample": 55552 + 46336, "check": 1497600, "bisect": 466944 + 140800 + 485376}
 # DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe);
 # None until captured for the current kernel
-CHECKER_TRAFFIC_2E6 = 56084992 + 153600
+CHECKER_TRAFFIC_2E6 = 56085248 + 133888
 KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
 
 
