@@ -29,6 +29,82 @@ namespace ezo {
 //
 // Row r of the round's candidate rows is candidate tile.y + (r % kTile) of
 // bisection tile r / kTile (the numbering the surrogate's MLP batch uses too).
+// c_proj (FP64 projection of sample si onto the segment's L, Eqs. 6-7) and
+// c - c_proj, rounded to FP32
+template <int NDOF>
+__device__ __forceinline__ void bisect_project(const BatchView& v, const SegState& st, int g, int si,
+                                               float (&p32)[NDOF], float (&dv32)[NDOF]) {
+  const int n = v.n;
+  const float* S = v.S + (long long)n * st.sample_off;
+  double cs[NDOF], p[NDOF];
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
+  project_fp64<NDOF>(cs, v.v1 + (long long)g * n, v.v2 + (long long)g * n, n, p);
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    p32[j] = j < n ? (float)p[j] : 0.f;
+    dv32[j] = j < n ? (float)(cs[j] - p[j]) : 0.f;
+  }
+}
+
+// The bracket's upper end after the exact halvings: lo + 2^-N_b, lo the sum
+// of 2^-(s+1) over the steps s whose midpoint was free
+__device__ __forceinline__ double bisect_hi(uint32_t bits, int n_b) {
+  uint64_t lo_u = 0;
+  for (int s = 0; s < n_b; ++s)
+    if (!((bits >> s) & 1u)) lo_u += 1ull << (n_b - 1 - s);
+  return ldexp((double)(lo_u + 1), -n_b);
+}
+
+// c* = c_proj + hi (c - c_proj) of candidate c in FP64, its distance to L, the
+// FP32 copy and its norm, and the tangent plane of Eq. (10) at c*:
+// a = (c* - c_proj) / dist_L(c*), b = a^T c*
+template <int NDOF>
+__device__ __forceinline__ void bisect_end_point(const BatchView& v, const SegState& st, int g, int c,
+                                                 double hi) {
+  const int n = v.n;
+  const long long co = st.cand_off;
+  const int np = st.n_p;
+  const double* v1 = v.v1 + (long long)g * n;
+  const double* v2 = v.v2 + (long long)g * n;
+  const float* S = v.S + (long long)n * st.sample_off;
+  const int si = v.cand_idx[co + c];
+  double cs[NDOF], p[NDOF], cst[NDOF], ps[NDOF];
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
+  project_fp64<NDOF>(cs, v1, v2, n, p);
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, cs[j] - p[j], p[j]) : 0.0;
+  project_fp64<NDOF>(cst, v1, v2, n, ps);
+  double d2 = 0.0;
+  float cn2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    if (j < n) {
+      const double e = cst[j] - ps[j];
+      d2 = fma(e, e, d2);
+      v.cstar[(long long)n * co + (long long)j * np + c] = cst[j];
+      const float f = (float)cst[j];
+      v.c32[(long long)n * co + (long long)j * np + c] = f;
+      cn2 = fmaf(f, f, cn2);
+    }
+  }
+  const double dist = sqrt(d2);
+  v.dist[co + c] = dist;
+  v.cnorm[co + c] = sqrtf(cn2);
+  const double inv = dist > 0.0 ? 1.0 / dist : 0.0;
+  double bval = 0.0;
+#pragma unroll
+  for (int j = 0; j < NDOF; ++j) {
+    if (j < n) {
+      const double a = (cst[j] - ps[j]) * inv;
+      v.ga[(long long)n * co + (long long)j * np + c] = a;
+      bval = fma(a, cst[j], bval);
+    }
+  }
+  v.gb[co + c] = bval;
+}
+
 #if !EZO_BOX_TU
 template <int NDOF>
 __global__ void __launch_bounds__(kRowBlock) k_bisect_prep(BatchView v) {
@@ -51,18 +127,13 @@ __global__ void __launch_bounds__(kRowBlock) k_bisect_prep(BatchView v) {
       for (int j = 0; j < ld; ++j) v.s_p32[(long long)r * ld + j] = v.s_d32[(long long)r * ld + j] = 0.f;
       continue;
     }
-    const int n = v.n;
-    const int si = v.cand_idx[st.cand_off + c];
-    const float* S = v.S + (long long)n * st.sample_off;
-    double cs[NDOF], p[NDOF];
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
-    project_fp64<NDOF>(cs, v.v1 + (long long)tile.x * n, v.v2 + (long long)tile.x * n, n, p);
+    float p32[NDOF], dv32[NDOF];
+    bisect_project<NDOF>(v, st, tile.x, v.cand_idx[st.cand_off + c], p32, dv32);
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) {
       if (j < ld) {
-        v.s_p32[(long long)r * ld + j] = j < n ? (float)p[j] : 0.f;
-        v.s_d32[(long long)r * ld + j] = j < n ? (float)(cs[j] - p[j]) : 0.f;
+        v.s_p32[(long long)r * ld + j] = p32[j];
+        v.s_d32[(long long)r * ld + j] = dv32[j];
       }
     }
     for (int j = NDOF; j < ld; ++j) v.s_p32[(long long)r * ld + j] = v.s_d32[(long long)r * ld + j] = 0.f;
@@ -73,68 +144,16 @@ template <int NDOF>
 __global__ void __launch_bounds__(kRowBlock) k_bisect_finish(BatchView v) {
   const int n_tiles = v.summary->n_bisect_tiles;
   const int rows = n_tiles * kTile;
-  const int n = v.n;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
     const int2 tile = v.bisect_tiles[r / kTile];
     const int c = tile.y + r % kTile;
     const int g = tile.x;
     const SegState& st = v.st[g];
     if (c >= st.n_cand) continue;
-    const long long co = st.cand_off;
-    const int np = st.n_p;
-    const uint32_t bits = v.bits[co + c];
-    // the bracket's upper end: the surrogate's verified end point, or after
-    // the exact halvings lo + 2^-N_b with lo the sum of 2^-(s+1) over the
-    // steps s whose midpoint was free
-    double hi;
-    if (v.sbis && v.s_ok[r]) {
-      hi = (double)v.s_hi[r];
-    } else {
-      uint64_t lo_u = 0;
-      for (int s = 0; s < v.n_b; ++s)
-        if (!((bits >> s) & 1u)) lo_u += 1ull << (v.n_b - 1 - s);
-      hi = ldexp((double)(lo_u + 1), -v.n_b);
-    }
-    const double* v1 = v.v1 + (long long)g * n;
-    const double* v2 = v.v2 + (long long)g * n;
-    const float* S = v.S + (long long)n * st.sample_off;
-    const int si = v.cand_idx[co + c];
-    // c* = c_proj + hi (c - c_proj) in FP64
-    double cs[NDOF], p[NDOF], cst[NDOF], ps[NDOF];
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) cs[j] = (j < n) ? (double)S[(long long)j * st.s_cap + si] : 0.0;
-    project_fp64<NDOF>(cs, v1, v2, n, p);
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) cst[j] = (j < n) ? fma(hi, cs[j] - p[j], p[j]) : 0.0;
-    project_fp64<NDOF>(cst, v1, v2, n, ps);
-    double d2 = 0.0;
-    float cn2 = 0.f;
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) {
-      if (j < n) {
-        const double e = cst[j] - ps[j];
-        d2 = fma(e, e, d2);
-        v.cstar[(long long)n * co + (long long)j * np + c] = cst[j];
-        const float f = (float)cst[j];
-        v.c32[(long long)n * co + (long long)j * np + c] = f;
-        cn2 = fmaf(f, f, cn2);
-      }
-    }
-    const double dist = sqrt(d2);
-    v.dist[co + c] = dist;
-    v.cnorm[co + c] = sqrtf(cn2);
-    // tangent plane of Eq. (10) at c*: a = (c* - c_proj) / dist_L(c*), b = a^T c*
-    const double inv = dist > 0.0 ? 1.0 / dist : 0.0;
-    double bval = 0.0;
-#pragma unroll
-    for (int j = 0; j < NDOF; ++j) {
-      if (j < n) {
-        const double a = (cst[j] - ps[j]) * inv;
-        v.ga[(long long)n * co + (long long)j * np + c] = a;
-        bval = fma(a, cst[j], bval);
-      }
-    }
-    v.gb[co + c] = bval;
+    const uint32_t bits = v.bits[st.cand_off + c];
+    // the surrogate's verified end point, or the exact halvings' upper end
+    const double hi = (v.sbis && v.s_ok[r]) ? (double)v.s_hi[r] : bisect_hi(bits, v.n_b);
+    bisect_end_point<NDOF>(v, st, g, c, hi);
   }
 }
 #endif  // !EZO_BOX_TU
