@@ -242,7 +242,8 @@ ezo_status ezo_batch_run(ezo_batch* batch, int32_t mode, void* cuda_stream);
  * keeps each path's order but runs the current segment of every path in one
  * batched run per wave; sequential = 0 inflates all segments speculatively
  * in one batched run and applies the same skip rule afterwards on the device
- * (one synchronisation at the end). All three
+ * (one synchronisation at the end). Returns after the stream has finished.
+ * All three
  * keep the same polytopes. Skipped segments report EZO_SEG_SKIPPED, segments
  * after a collision EZO_SEG_IDLE. Errors: EZO_ERR_CUDA. */
 ezo_status ezo_batch_run_path(ezo_batch* batch, int32_t sequential, int32_t mode, void* cuda_stream);

@@ -1272,13 +1272,12 @@ ezo_status ezo_batch_attach_surrogate(ezo_batch* b, ezo_surrogate* sur, float ma
 ezo_status ezo_batch_reset(ezo_batch* b, const double* v1, const double* v2, void* stream_v) {
   if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_reset: null batch");
   cudaStream_t s = (cudaStream_t)stream_v;
-  const size_t B = b->B, n = b->n, mc = b->m_cap;
+  const size_t B = b->B, n = b->n;
   if (v1) EZO_CUDA(cudaMemcpyAsync(b->d_v1, v1, sizeof(double) * B * n, cudaMemcpyHostToDevice, s));
   if (v2) EZO_CUDA(cudaMemcpyAsync(b->d_v2, v2, sizeof(double) * B * n, cudaMemcpyHostToDevice, s));
-  EZO_CUDA(cudaMemcpyAsync(b->d_st, b->d_st0, sizeof(SegState) * B, cudaMemcpyDeviceToDevice, s));
-  EZO_CUDA(cudaMemcpyAsync(b->d_A, b->d_A0, sizeof(double) * B * mc * n, cudaMemcpyDeviceToDevice, s));
-  EZO_CUDA(cudaMemcpyAsync(b->d_b, b->d_b0, sizeof(double) * B * mc, cudaMemcpyDeviceToDevice, s));
-  EZO_CUDA(cudaMemsetAsync(b->d_sum, 0, sizeof(RoundSummary), s));
+  // states, starting polytopes and the summary in one kernel (the summary's
+  // work-queue fields reset themselves at the end of every launch)
+  EZO_CUDA(launch_batch_reset(b->view, b->d_st0, b->d_A0, b->d_b0, s));
   g_err.clear();
   return EZO_OK;
 }

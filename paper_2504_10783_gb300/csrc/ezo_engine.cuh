@@ -152,6 +152,9 @@ cudaError_t launch_sample_flat(const double* A, const double* b, int m, int lda,
                                float* out, long long ldo, cudaStream_t s);
 
 cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s);
+// a batch's reset to its initial states and polytopes in one launch
+cudaError_t launch_batch_reset(const BatchView& v, const SegState* st0, const double* A0, const double* b0,
+                               cudaStream_t s);
 // Walks share eight lanes when the round has fewer than split_below_tiles
 // sample tiles (0: never).
 cudaError_t launch_round_sample(const BatchView& v, int split_below_tiles, int grid, cudaStream_t s);

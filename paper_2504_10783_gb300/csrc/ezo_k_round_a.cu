@@ -95,6 +95,26 @@ __device__ __forceinline__ void round_begin_block(const BatchView& v) {
 
 __global__ void __launch_bounds__(1024) k_round_begin(BatchView v) { round_begin_block(v); }
 
+// Reset of a batch in one launch: every segment's state and the rows of its
+// starting polytope (st0[g].m rows; rows past a segment's m are never read),
+// and the round summary's public part. One block per segment.
+__global__ void __launch_bounds__(256) k_batch_reset(BatchView v, const SegState* __restrict__ st0,
+                                                     const double* __restrict__ A0, const double* __restrict__ b0) {
+  const int g = blockIdx.x;
+  if (g >= v.B) return;
+  const int m = st0[g].m;
+  const long long base = (long long)g * v.m_cap;
+  for (int i = threadIdx.x; i < m * v.n; i += blockDim.x) v.A[base * v.n + i] = A0[base * v.n + i];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) v.b[base + i] = b0[base + i];
+  if (threadIdx.x == 0) v.st[g] = st0[g];
+  if (g == 0 && threadIdx.x == 0) {
+    v.summary->active = 0;
+    v.summary->round = 0;
+    v.summary->n_sample_tiles = 0;
+    v.summary->n_bisect_tiles = 0;
+  }
+}
+
 // End of a round fused with the next round's sizing (one launch fewer per
 // round in the run loops): every active segment that reached N_it stops
 // (Sec. IV-C), the others go to round k + 1, the next round's sample tiles are
@@ -390,6 +410,13 @@ __global__ void __launch_bounds__(1024) k_round_certify(BatchView v) {
 
 cudaError_t launch_round_begin(const BatchView& v, cudaStream_t s) {
   k_round_begin<<<1, 1024, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reset(const BatchView& v, const SegState* st0, const double* A0, const double* b0,
+                               cudaStream_t s) {
+  if (v.B <= 0) return cudaSuccess;
+  k_batch_reset<<<v.B, 256, 0, s>>>(v, st0, A0, b0);
   return cudaGetLastError();
 }
 

@@ -626,27 +626,56 @@ __global__ void k_containment(BatchView v, uint8_t* contained, double tol) {
 }
 
 // The skip rule of Sec. VI-A after a speculative run, on the device: one
-// thread per path (its segments are consecutive, from path_first) walks the
+// warp per path (its segments are consecutive, from path_first) walks the
 // segments in order; a segment is skipped when both its endpoints lie in the
 // polytope of an earlier kept segment of the path (contained), and every
-// segment after one reported in collision goes idle. A segment is kept when
-// its status is neither skipped nor idle once the earlier ones are decided.
-__global__ void k_path_skip(BatchView v, const uint8_t* __restrict__ contained) {
+// segment after one reported in collision goes idle. For paths of up to 32
+// segments lane j holds segment j's status and column j of the containment
+// flags, all loaded at once, and each segment's test is a ballot over the
+// lanes; longer paths take lane 0's sequential walk over global memory.
+__global__ void __launch_bounds__(128) k_path_skip(BatchView v, const uint8_t* __restrict__ contained) {
   const int L = v.max_path_len;
-  for (int g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < v.B; g0 += gridDim.x * blockDim.x) {
-    if (v.path_first[g0] != g0) continue;
-    bool stopped = false;
-    for (int g = g0; g < v.B && v.path_first[g] == g0; ++g) {
-      bool skip = stopped;
-      for (int j = g0; j < g && !skip; ++j) {
-        const int sj = v.st[j].status;
-        if (sj != SEG_SKIPPED && sj != SEG_IDLE && contained[(long long)g * L + (j - g0)]) skip = true;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int g0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g0 < v.B; g0 += warps) {
+    if (v.path_first[g0] != g0) continue;  // the whole warp
+    // path length (up to 33 read here; longer paths take the fallback)
+    const bool in = g0 + lane < v.B && v.path_first[g0 + lane] == g0;
+    const unsigned run = __ballot_sync(0xffffffffu, in);
+    const int K = (~run == 0u) ? 33 : __ffs(~run) - 1;
+    if (K <= 32) {
+      const int st_l = lane < K ? v.st[g0 + lane].status : 0;
+      unsigned col = 0u;  // bit k: segment k's endpoints lie in segment `lane`'s polytope
+      for (int k = lane + 1; k < K; ++k)
+        if (contained[(long long)(g0 + k) * L + lane]) col |= 1u << k;
+      unsigned kept = 0u;
+      bool stopped = false;
+      for (int k = 0; k < K; ++k) {
+        const bool in_kept = lane < k && ((kept >> lane) & 1u) && st_l != SEG_SKIPPED && st_l != SEG_IDLE &&
+                             ((col >> k) & 1u);
+        const bool skip = stopped || __ballot_sync(0xffffffffu, in_kept) != 0u;
+        const int st_k = __shfl_sync(0xffffffffu, st_l, k);
+        if (skip) {
+          if (lane == 0) v.st[g0 + k].status = stopped ? SEG_IDLE : SEG_SKIPPED;
+        } else {
+          kept |= 1u << k;
+          if (st_k == SEG_IN_COLLISION) stopped = true;
+        }
       }
-      if (skip) {
-        v.st[g].status = stopped ? SEG_IDLE : SEG_SKIPPED;
-        continue;
+    } else if (lane == 0) {
+      bool stopped = false;
+      for (int g = g0; g < v.B && v.path_first[g] == g0; ++g) {
+        bool skip = stopped;
+        for (int j = g0; j < g && !skip; ++j) {
+          const int sj = v.st[j].status;
+          if (sj != SEG_SKIPPED && sj != SEG_IDLE && contained[(long long)g * L + (j - g0)]) skip = true;
+        }
+        if (skip) {
+          v.st[g].status = stopped ? SEG_IDLE : SEG_SKIPPED;
+          continue;
+        }
+        if (v.st[g].status == SEG_IN_COLLISION) stopped = true;
       }
-      if (v.st[g].status == SEG_IN_COLLISION) stopped = true;
     }
   }
 }
@@ -743,7 +772,7 @@ cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double to
 }
 
 cudaError_t launch_path_skip(const BatchView& v, const uint8_t* contained, cudaStream_t s) {
-  k_path_skip<<<(v.B + 127) / 128, 128, 0, s>>>(v, contained);
+  k_path_skip<<<(v.B + 3) / 4, 128, 0, s>>>(v, contained);  // one warp per segment index
   return cudaGetLastError();
 }
 
