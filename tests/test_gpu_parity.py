@@ -643,6 +643,31 @@ def test_inflate_path_sequential_equals_speculative(ezo):
         assert orc.segment_contained(r.A, r.b, path[k], path[k + 1], tol=1e-12)
 
 
+@pytest.mark.parametrize("pieces", [20, 40])
+def test_device_skip_rule_on_long_paths(ezo, pieces):
+    """The skip rule after a speculative run runs on the device, one warp per
+    path, with a sequential fallback for paths of more than 32 segments: a
+    collision-free planar segment cut into 20 and into 40 pieces (most of
+    them inside an earlier polytope) keeps, skips and inflates the same
+    segments, with the same polytopes, as the paper's one-at-a-time order."""
+    rd, env_np, v1, v2 = planar_scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    t = np.linspace(0.0, 1.0, pieces + 1)[:, None]
+    path = (1.0 - t) * v1[None, :] + t * v2[None, :]
+    prm = ezo.Params.make(n_p=500, seed=23)
+    res = {}
+    for seq in (True, False):
+        bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm, path_first=np.zeros(pieces, np.int32))
+        bt.run_path(sequential=seq, mode=ezo.RUN_HOST_LOOP if seq else ezo.RUN_GRAPH)
+        res[seq] = [bt.segment(g) for g in range(pieces)]
+    assert [r.status for r in res[True]] == [r.status for r in res[False]]
+    assert sum(r.status == ezo.SEG_SKIPPED for r in res[False]) >= pieces // 2
+    for a, b in zip(res[True], res[False]):
+        if a.status != ezo.SEG_SKIPPED:
+            np.testing.assert_array_equal(a.A, b.A)
+            np.testing.assert_array_equal(a.b, b.b)
+
+
 def test_inflate_path_matches_oracle_skip_rule(ezo):
     """Sec. VI-A on a planar path whose second half lies inside the first
     polytope and whose third segment leaves it: every segment is inflated
