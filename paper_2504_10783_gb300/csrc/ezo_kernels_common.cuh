@@ -86,8 +86,9 @@ __host__ __device__ constexpr int hnr_blocks_per_step(int n) {
 }
 
 // Shared-memory image of a polytope for the sampler, two rows per record:
-// record P holds rows 2P and 2P + 1 interleaved, a_{2P,j} and a_{2P+1,j} at
-// floats 2j and 2j + 1 (j < NDOF, zero-padded), then b_{2P} and b_{2P+1}. The
+// record P holds rows 2P and 2P + 1 interleaved, -a_{2P,j} and -a_{2P+1,j} at
+// floats 2j and 2j + 1 (j < NDOF, zero-padded; negated, so that the slack
+// b - a . x is one FMA chain from b), then b_{2P} and b_{2P+1}. The
 // record is rounded up to an odd number of float4s, so that the eight
 // consecutive records which the lanes of a shared walk read at once fall in
 // different shared-memory banks. One 64-bit load gives a coefficient of two
@@ -110,15 +111,18 @@ __device__ __forceinline__ float hnr_row_b(const float* __restrict__ A32, int r)
 }
 
 // Chord bounds from the row pairs P0, P0 + step, .. < P1: for row r the slack
-// b_r - a_r . x and the rate a_r . d give the crossing t = slack / rate
-// (slack times the reciprocal of the rate), which bounds the chord from above
-// when the rate is positive and from below when it is negative. Both rows of
-// a pair advance together in packed FP32 FMAs against x and d duplicated into
-// both halves (xx, dd); each half is the scalar chain fmaf(a_j, x_j, .) over
-// j = 0 .. NDOF-1 from 0, so every row's slack, rate and ratio are bit for
-// bit those of a row taken alone, and min/max do not depend on the order or
-// on how the pairs are split between lanes. Four pairs per iteration let the
-// chains overlap.
+// s = b_r - a_r . x and the rate a_r . d give the crossing t = s / rate,
+// which bounds the chord from above when the rate is positive and from below
+// when it is negative. From the negated coefficients the slack is the chain
+// fmaf(-a_j, x_j, .) over j = 0 .. NDOF-1 from b_r, and nr = -rate the chain
+// fmaf(-a_j, d_j, .) from 0, so t = -(s / nr): s times the reciprocal of nr,
+// negated. Both rows of a pair advance together in packed FP32 operations
+// against x and d duplicated into both halves (xx, dd); each half is a
+// row's scalar chain, so every row's slack, rate and ratio are bit for bit
+// those of a row taken alone, and min/max do not depend on the order or on
+// how the pairs are split between lanes. For a joint-box row (a = +-e_j) the
+// chains are exact but for the one term, so the bounds equal chord_joint's.
+// Four pairs per iteration let the chains overlap.
 template <int NDOF>
 __device__ __forceinline__ void chord_pairs(const float* __restrict__ A32, int P0, int P1, int step,
                                             const float2 (&xx)[NDOF], const float2 (&dd)[NDOF], float& t_lo,
@@ -127,20 +131,18 @@ __device__ __forceinline__ void chord_pairs(const float* __restrict__ A32, int P
 #pragma unroll 4
   for (int P = P0; P < P1; P += step) {
     const float2* rec = reinterpret_cast<const float2*>(A32 + P * PS);
-    float2 ax = make_float2(0.f, 0.f), ad = make_float2(0.f, 0.f);
+    float2 sl = rec[NDOF], nr = make_float2(0.f, 0.f);  // slack from b, -rate from 0
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) {
-      const float2 a = rec[j];
-      ax = __ffma2_rn(a, xx[j], ax);
-      ad = __ffma2_rn(a, dd[j], ad);
+      const float2 na = rec[j];
+      sl = __ffma2_rn(na, xx[j], sl);
+      nr = __ffma2_rn(na, dd[j], nr);
     }
-    const float2 bb = rec[NDOF];
-    const float q0 = (bb.x - ax.x) * rcp_approx(ad.x);
-    const float q1 = (bb.y - ax.y) * rcp_approx(ad.y);
-    if (ad.x > 0.f) t_hi = fminf(t_hi, q0);
-    if (ad.x < 0.f) t_lo = fmaxf(t_lo, q0);
-    if (ad.y > 0.f) t_hi = fminf(t_hi, q1);
-    if (ad.y < 0.f) t_lo = fmaxf(t_lo, q1);
+    const float2 q = __fmul2_rn(sl, make_float2(rcp_approx(nr.x), rcp_approx(nr.y)));  // -t
+    if (nr.x < 0.f) t_hi = fminf(t_hi, -q.x);
+    if (nr.x > 0.f) t_lo = fmaxf(t_lo, -q.x);
+    if (nr.y < 0.f) t_hi = fminf(t_hi, -q.y);
+    if (nr.y > 0.f) t_lo = fmaxf(t_lo, -q.y);
   }
 }
 
@@ -342,8 +344,8 @@ __device__ __forceinline__ void hnr_walk_split(const float* __restrict__ A32, in
 }
 
 // The polytope {A x <= b} (FP64, m rows, row stride lda) as the sampler's
-// paired FP32 image (see hnr_pair_stride); an odd last row is paired with a
-// zero row.
+// paired FP32 image (see hnr_pair_stride; coefficients negated); an odd last
+// row is paired with a zero row.
 template <int NDOF>
 __device__ __forceinline__ void stage_polytope(float* A32, const double* __restrict__ A,
                                                const double* __restrict__ b, int m, int lda, int n) {
@@ -354,7 +356,7 @@ __device__ __forceinline__ void stage_polytope(float* A32, const double* __restr
     const int r = 2 * P + (c & 1), j = c >> 1;
     float v = 0.f;
     if (r < m) {
-      if (j < n) v = (float)A[(long long)r * lda + j];
+      if (j < n) v = -(float)A[(long long)r * lda + j];
       else if (j == NDOF) v = (float)b[r];
     }
     A32[i] = v;
