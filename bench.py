@@ -784,9 +784,12 @@ def main():
         # useful work: the exact checks of the segments the skip rule keeps
         units += w["kept_checks"]
         units_all_segments += w["sample_checks"] + w["bisection_checks"]
-        # first sizing, 7 kernels per round (the one-lane and the shared-walk
-        # sampler, one of which returns at once), containment
-        launches += 7 * w["rounds"] + 2
+        # the reset and the first sizing, 8 kernels per round (the one-lane
+        # and the shared-walk sampler, one of which returns at once; labels;
+        # certification; the bisection's projection, halvings and end
+        # points; the placement that closes the round), containment and the
+        # skip rule
+        launches += 8 * w["rounds"] + 4
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()

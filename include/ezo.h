@@ -326,7 +326,9 @@ ezo_status ezo_batch_tune(ezo_batch* batch, int32_t reps, ezo_shape* chosen, voi
  * the current round over the batch: 0 round size (a1), 1 hit-and-run (a2),
  * 2 collision labels (a3, a4), 3 certification and selection (a5, a6),
  * 4 projection and bisection (a7, a8), 5 hyperplane placement (a9), 6 round
- * end. Stream-ordered; call ezo_batch_sync before reading. */
+ * end; 7 round end fused with the next round's size, and 8 placement whose
+ * last block then runs 7 (the run loops' kernels). Stream-ordered; call
+ * ezo_batch_sync before reading. */
 ezo_status ezo_batch_step(ezo_batch* batch, int32_t step, void* cuda_stream);
 ezo_status ezo_batch_sync(ezo_batch* batch, void* cuda_stream);
 

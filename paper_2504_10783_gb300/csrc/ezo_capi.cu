@@ -688,7 +688,9 @@ ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
   if (g_prof_on) {
     e0 = b->events.get();
     e1 = b->events.get();
-    b->events.kind.push_back(step == 7 ? 6 : step);  // the fused close counts as round end
+    // the fused close counts as round end, the placement that closes the
+    // round as placement
+    b->events.kind.push_back(step == 7 ? 6 : (step == 8 ? 5 : step));
     cudaEventRecord(e0, s);
   }
   switch (step) {
@@ -700,7 +702,8 @@ ezo_status launch_step(ezo_batch* b, int step, cudaStream_t s) {
     case 5: e = launch_round_place(b->view, s); break;
     case 6: e = launch_round_end(b->view, s); break;
     case 7: e = launch_round_close(b->view, s); break;  // 6 fused with the next round's 0
-    default: return fail(EZO_ERR_INVALID_ARG, "ezo_batch_step: step must be in [0, 6]");
+    case 8: e = launch_round_place(b->view, s, true); break;  // 5 whose last block runs 7
+    default: return fail(EZO_ERR_INVALID_ARG, "ezo_batch_step: step must be in [0, 8]");
   }
   if (g_prof_on) cudaEventRecord(e1, s);
   if (e != cudaSuccess) return cuda_fail(e, "round kernel launch");
@@ -722,7 +725,9 @@ void collect_profile(ezo_batch* b) {
 
 // The run loops size the first round once; every round then ends with the
 // fused round-close kernel, which also sizes the next round.
-const int kRoundSteps[6] = {1, 2, 3, 4, 5, 7};
+// a round of the run loops: walks, labels, certification, bisection, and the
+// placement whose last block closes the round (step 8)
+const int kRoundSteps[5] = {1, 2, 3, 4, 8};
 
 ezo_status run_host_loop(ezo_batch* b, cudaStream_t s) {
   ezo_status st0 = launch_step(b, 0, s);

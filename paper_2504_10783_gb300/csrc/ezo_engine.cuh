@@ -75,6 +75,7 @@ struct RoundSummary {
   int q_sample, left_sample;
   int q_check, left_check;
   int q_bisect[3], left_bisect[3];
+  int left_place;  // placement blocks done (the fused round close)
 };
 
 // Everything a round kernel needs, by value (kernel parameter space).
@@ -170,7 +171,8 @@ cudaError_t launch_bisect_prep(const BatchView& v, int grid_rows, cudaStream_t s
 cudaError_t launch_round_bisect(const BatchView& v, int T, int grid, cudaStream_t s);
 cudaError_t launch_bisect_finish(const BatchView& v, int grid_rows, cudaStream_t s);
 cudaError_t launch_bisect_exact(const BatchView& v, int T, int grid, int grid_rows, cudaStream_t s);
-cudaError_t launch_round_place(const BatchView& v, cudaStream_t s);
+// close = true: the last block also closes the round (the run loops' form)
+cudaError_t launch_round_place(const BatchView& v, cudaStream_t s, bool close = false);
 cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 
 // Containment of segment endpoints in earlier polytopes of the same path

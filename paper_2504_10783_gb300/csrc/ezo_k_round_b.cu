@@ -387,8 +387,10 @@ __global__ void __launch_bounds__(96) k_round_bisect_pair(BatchView v, int max_o
 // a_i^T c_j > b_i - Delta_i; at most N_f planes. One block per segment.
 // The discard test runs in FP32 with a rounding bound and falls back to FP64
 // inside the bound, so every decision equals the FP64 decision.
+// CLOSE: the run loops' form, whose last block to finish also closes the
+// round (round_close_block), one launch fewer per round.
 template <int NDOF>
-__global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
+__device__ __forceinline__ void place_segment(const BatchView& v) {
   const int g = blockIdx.x;
   SegState& st = v.st[g];
   if (st.status != SEG_ACTIVE) return;
@@ -589,6 +591,27 @@ __global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
   }
 }
 
+template <int NDOF, bool CLOSE>
+__global__ void __launch_bounds__(1024) k_round_place(BatchView v) {
+  place_segment<NDOF>(v);
+  if constexpr (CLOSE) {
+    // every block reports when its segment is placed; the last one closes
+    // the round for all of them
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(&v.summary->left_place, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (threadIdx.x == 0) v.summary->left_place = 0;
+      round_close_block(v);
+    }
+  }
+}
+
 __global__ void k_round_end(BatchView v) {
   __shared__ int s_active;
   if (threadIdx.x == 0) s_active = 0;
@@ -746,14 +769,20 @@ cudaError_t launch_bisect_exact(const BatchView& v, int T, int grid, int grid_ro
   return e;
 }
 
-cudaError_t launch_round_place(const BatchView& v, cudaStream_t s) {
+cudaError_t launch_round_place(const BatchView& v, cudaStream_t s, bool close) {
   // alive bitmask for the largest N_p of the batch
   const size_t smem = (size_t)((v.np_max + 31) / 32) * sizeof(uint32_t);
   cudaError_t err = cudaSuccess;
   EZO_DISPATCH_NDOF(v.n, {
-    err = set_smem(k_round_place<ND>, smem);
-    if (err != cudaSuccess) return err;
-    k_round_place<ND><<<v.B, 1024, smem, s>>>(v);
+    if (close) {
+      err = set_smem(k_round_place<ND, true>, smem);
+      if (err != cudaSuccess) return err;
+      k_round_place<ND, true><<<v.B, 1024, smem, s>>>(v);
+    } else {
+      err = set_smem(k_round_place<ND, false>, smem);
+      if (err != cudaSuccess) return err;
+      k_round_place<ND, false><<<v.B, 1024, smem, s>>>(v);
+    }
   });
   return cudaGetLastError();
 }

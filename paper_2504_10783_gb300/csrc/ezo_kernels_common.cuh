@@ -491,6 +491,101 @@ __device__ __forceinline__ void round_summary_close(const BatchView& v, int acti
 #endif
 }
 
+// --------------------------------------------------------- round sizing --
+// Round size of Sec. IV-B: delta_k = 6 delta / (pi^2 k^2),
+// M = ceil(2 ln(1/delta_k) / (eps tau^2)), |S| = max(N_p, M).
+__device__ __forceinline__ int round_test_size(int k, double eps, double delta, double tau) {
+  const double dk = 6.0 * delta / (3.141592653589793 * 3.141592653589793 * (double)k * (double)k);
+  return (int)ceil(2.0 * log(1.0 / dk) / (eps * tau * tau));
+}
+
+// Round size of every active segment and the round's list of sample tiles
+// (block-wide exclusive scan over the segments). Runs in one block.
+__device__ __forceinline__ void round_begin_block(const BatchView& v) {
+  __shared__ int warp_sum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < v.B; base += blockDim.x) {
+    const int g = base + threadIdx.x;
+    int tiles = 0;
+    if (g < v.B) {
+      SegState& st = v.st[g];
+      if (st.status == SEG_ACTIVE && v.edit) {
+        // set editing: the given configurations are already in place
+        st.m_test = 0;
+        st.n_cand = 0;
+        st.count = 0;
+        st.n_placed = 0;
+        tiles = (st.n_samples + kTile - 1) / kTile;
+      } else if (st.status == SEG_ACTIVE) {
+        const int M = round_test_size(st.k, v.eps, v.delta, v.tau);
+        int S = M > st.n_p ? M : st.n_p;
+        if (S > st.s_cap) S = st.s_cap;  // capacity is sized for M at N_it; never hit
+        st.m_test = M;
+        st.n_samples = S;
+        // algorithmic FP32 work of this round's walks, per walk step
+        // 2mn + 5m + 6n: the rate a_r . d of every row (2n), the slack update
+        // s_r -= t q_r, the ratio and the two bound updates (5 per row), and
+        // the direction's normalisation and the move (6n). The Gaussians'
+        // transcendental functions and the random-number generator are not
+        // counted, nor the second dot product per row that this kernel uses
+        // instead of carrying the slack.
+        st.sample_flops += (long long)S * v.n_mix * (2ll * st.m * v.n + 5ll * st.m + 6ll * v.n);
+        st.n_cand = 0;
+        st.count = 0;
+        st.n_placed = 0;
+        tiles = (S + kTile - 1) / kTile;
+      }
+    }
+    // block exclusive scan of tiles
+    int x = tiles;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < nw ? warp_sum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const int excl = carry + (wid ? warp_sum[wid - 1] : 0) + x - tiles;
+    for (int t = 0; t < tiles; ++t) v.sample_tiles[excl + t] = make_int2(g, t * kTile);
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sum[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    v.summary->n_sample_tiles = carry;
+    v.summary->n_bisect_tiles = 0;
+  }
+}
+
+// End of a round fused with the next round's sizing, by one block: every
+// active segment that reached N_it stops (Sec. IV-C), the others go to round
+// k + 1, the next round's sample tiles are listed, and the round summary (and
+// a graph's WHILE condition) is set.
+__device__ __forceinline__ void round_close_block(const BatchView& v) {
+  __shared__ int s_active;
+  if (threadIdx.x == 0) s_active = 0;
+  __syncthreads();
+  const int act = round_end_segments(v);
+  if (act) atomicAdd(&s_active, act);
+  __syncthreads();
+  round_begin_block(v);
+  __syncthreads();
+  if (threadIdx.x == 0) round_summary_close(v, s_active);
+}
+
 // ------------------------------------------------------- collision checks --
 // Shared memory of the collision kernels: robot spheres, obstacles, per group
 // sphere centres, obstacle offsets, then the boxes (robot boxes in their

@@ -1,11 +1,14 @@
 """Round-by-round replay of the product run loop against the FP64 oracle.
 
-The batch is driven through ezo_batch_step with exactly the kernel sequence
-of the run loops (ezo_batch_run in either mode): the first round's sizing
-(step 0) once, then per round sampling, labels, certification, bisection,
-placement (steps 1-5) and the fused round-close kernel that ends the round
-and sizes the next one (step 7), with the batch's own launch shapes (device
-lane rule for the walks, the tuned lanes for the labels). After each round
+The batch is driven through ezo_batch_step with the kernel sequence of the
+run loops (ezo_batch_run in either mode): the first round's sizing (step 0)
+once, then per round sampling, labels, certification, bisection, placement
+(steps 1-5) and the round close that ends the round and sizes the next one
+(step 7), with the batch's own launch shapes (device lane rule for the
+walks, the tuned lanes for the labels). The run loops launch steps 5 and 7
+as one kernel (step 8: the placement's last block runs the close, the same
+two device functions); stopping after step 5 lets the test read each
+round's placement before the close. After each round
 every segment that took part is replayed with the oracle (Algorithm 1,
 Sec. IV-B, IV-C) on its own obstacle set, its own N_p and that round's GPU
 samples and polytope, at the parity tolerances of tests/test_gpu_parity.py.
