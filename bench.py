@@ -257,7 +257,8 @@ def measure_batched(ezo, torch, stream, scenes, rd, robot, paths=256, speculativ
     """Batched form (Sec. VI-A per path, many paths): 8 obstacle sets of
     128-1024 spheres, seed paths of 1-40 segments, per-segment N_p
     log-uniform in [1e3, 1e5]. The wavefront mode (each path in order, the
-    current segments of all paths in one graph launch per wave) and, with
+    current segments of all paths in one batched run per wave; every wave,
+    its skip rule and its rounds in one graph launch) and, with
     `speculative`, all segments at once in one graph, against the per-segment
     launch loop of the plain method. Configs/s count the exact checks of the
     segments each mode keeps."""

@@ -240,7 +240,10 @@ ezo_status ezo_batch_run(ezo_batch* batch, int32_t mode, void* cuda_stream);
  * collision. sequential = 1 runs one segment at a time over all paths (the
  * paper's order, a host-driven launch loop); sequential = 2 ("wavefront")
  * keeps each path's order but runs the current segment of every path in one
- * batched run per wave; sequential = 0 inflates all segments speculatively
+ * batched run per wave (with mode EZO_RUN_GRAPH all waves, each with its
+ * skip rule on the device and its rounds, run inside one graph launch; with
+ * EZO_RUN_HOST_LOOP the host applies the skip rule between waves);
+ * sequential = 0 inflates all segments speculatively
  * in one batched run and applies the same skip rule afterwards on the device
  * (one synchronisation at the end). Returns after the stream has finished.
  * All three

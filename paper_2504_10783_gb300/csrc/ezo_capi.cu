@@ -611,6 +611,11 @@ struct ezo_batch {
   // graph mode
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // the wavefront order in one graph (waves and rounds as nested WHILE nodes)
+  cudaGraph_t wgraph = nullptr;
+  cudaGraphExec_t wgexec = nullptr;
+  int *d_wnext = nullptr, *d_wlast = nullptr;
+  uint8_t* d_wkept = nullptr;
   cudaStream_t cap_stream = nullptr;
   EventPool events;
   // surrogate-guided bisection
@@ -621,15 +626,28 @@ struct ezo_batch {
 
 namespace {
 
-ezo_status batch_free_device(ezo_batch* b) {
+// The captured graphs hold the batch view and the launch shapes by value:
+// dropped whenever either changes, rebuilt on the next graph run.
+void drop_graphs(ezo_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->wgexec) cudaGraphExecDestroy(b->wgexec);
+  if (b->wgraph) cudaGraphDestroy(b->wgraph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->wgexec = nullptr;
+  b->wgraph = nullptr;
+}
+
+ezo_status batch_free_device(ezo_batch* b) {
+  drop_graphs(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   void* ptrs[] = {b->d_st,    b->d_v1,    b->d_v2,   b->d_A,    b->d_b,      b->d_S,      b->d_flags,
                   b->d_cidx,  b->d_cstar, b->d_dist, b->d_c32,  b->d_cn,     b->d_bits,   b->d_pidx, b->d_ga, b->d_gb,
                   b->d_pdelta, b->d_stiles, b->d_btiles, b->d_sum, b->d_envs, b->d_path_first, b->d_contained, b->d_st0, b->d_A0, b->d_b0,
                   b->view.s_p32, b->view.s_d32, b->view.s_lo, b->view.s_hi,
-                  b->view.s_bits, b->view.s_ok, b->view.s_rows, b->view.sm_seats, b->view.q_claim};
+                  b->view.s_bits, b->view.s_ok, b->view.s_rows, b->view.sm_seats, b->view.q_claim,
+                  b->d_wnext, b->d_wlast, b->d_wkept};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_sum) cudaFreeHost(b->h_sum);
@@ -803,6 +821,130 @@ ezo_status run_graph(ezo_batch* b, cudaStream_t s, bool sync = true) {
   EZO_CUDA(cudaGraphLaunch(b->gexec, s));
   if (sync) EZO_CUDA(cudaStreamSynchronize(s));
   return EZO_OK;
+}
+
+#if CUDART_VERSION >= 12040
+// The last node of a graph whose nodes form one chain (captured on one
+// stream).
+cudaError_t chain_tail(cudaGraph_t g, cudaGraphNode_t* tail) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if ((e = cudaGraphGetNodes(g, nodes.data(), &n)) != cudaSuccess) return e;
+  *tail = nullptr;
+  for (cudaGraphNode_t nd : nodes) {
+    size_t out = 0;
+    if ((e = cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &out)) != cudaSuccess) return e;
+    if (out == 0) *tail = nd;
+  }
+  return *tail ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// A WHILE node after `dep` in graph g; its handle (made on g) is not reset at
+// launch: the kernels set it before the node runs.
+cudaError_t add_while(cudaGraph_t g, cudaGraphNode_t dep, unsigned default_value, unsigned flags,
+                      cudaGraphConditionalHandle* h, cudaGraph_t* body) {
+  cudaError_t e = cudaGraphConditionalHandleCreate(h, g, default_value, flags);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = *h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &cp);
+  if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+  return e;
+}
+#endif
+
+// The wavefront order (Sec. VI-A: each path in order with the skip rule, the
+// current segments of all paths in one batched run) as one graph:
+//   wave_init -> WHILE(waves) { containment -> wave_select -> first sizing
+//                               -> WHILE(rounds) { one round } }
+// wave_select applies the skip rule and the stop after a collision, picks the
+// next segment of every path and sets both conditions from the count of
+// active segments; the round body is the one of build_graph.
+ezo_status build_wave_graph(ezo_batch* b) {
+#if CUDART_VERSION >= 12040
+  const size_t B = b->B;
+  if (!b->d_wnext) {
+    cudaError_t e = dalloc(&b->d_wnext, B);
+    if (e == cudaSuccess) e = dalloc(&b->d_wlast, B);
+    if (e == cudaSuccess) e = dalloc(&b->d_wkept, B);
+    if (e != cudaSuccess) return cuda_fail(e, "wave graph: allocation");
+  }
+  if (!b->cap_stream) EZO_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  const BatchView saved = b->view;
+  ezo_status st = EZO_OK;
+  cudaGraph_t captured = nullptr, wbody = nullptr, rbody = nullptr;
+  cudaGraphNode_t tail = nullptr;
+  cudaGraphConditionalHandle hw = 0, hr = 0;
+  auto cap = [&](cudaGraph_t g, cudaGraphNode_t dep, auto&& fn) -> cudaError_t {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(b->cap_stream, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0,
+                                                  cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    fn();
+    return cudaStreamEndCapture(b->cap_stream, &captured);
+  };
+  cudaError_t e = cudaGraphCreate(&b->wgraph, 0);
+  if (e == cudaSuccess)
+    e = cap(b->wgraph, nullptr, [&] {
+      cudaError_t le = launch_wave_init(b->view, b->d_wnext, b->d_wlast, b->d_wkept, b->cap_stream);
+      if (le != cudaSuccess) st = cuda_fail(le, "wave graph: init");
+    });
+  if (e == cudaSuccess && st == EZO_OK) e = chain_tail(b->wgraph, &tail);
+  if (e == cudaSuccess && st == EZO_OK) e = add_while(b->wgraph, tail, 1, cudaGraphCondAssignDefault, &hw, &wbody);
+  if (e == cudaSuccess && st == EZO_OK) {
+    hr = 0;
+    e = cudaGraphConditionalHandleCreate(&hr, wbody, 0, 0);
+  }
+  if (e == cudaSuccess && st == EZO_OK)
+    e = cap(wbody, nullptr, [&] {
+      cudaError_t le = cudaMemsetAsync(b->d_contained, 0, B * (size_t)b->max_path_len, b->cap_stream);
+      if (le == cudaSuccess) le = launch_containment(b->view, b->d_contained, 1e-9, b->cap_stream);
+      if (le == cudaSuccess)
+        le = launch_wave_select(b->view, b->d_contained, b->d_wnext, b->d_wlast, b->d_wkept,
+                                (unsigned long long)hw, (unsigned long long)hr, b->cap_stream);
+      if (le != cudaSuccess) st = cuda_fail(le, "wave graph: skip rule");
+      if (st == EZO_OK) st = launch_step(b, 0, b->cap_stream);
+    });
+  if (e == cudaSuccess && st == EZO_OK) e = chain_tail(wbody, &tail);
+  if (e == cudaSuccess && st == EZO_OK) {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hr;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, wbody, &tail, nullptr, 1, &cp);
+    if (e == cudaSuccess) rbody = cp.conditional.phGraph_out[0];
+  }
+  if (e == cudaSuccess && st == EZO_OK) {
+    b->view.graph_cond = (unsigned long long)hr;
+    e = cap(rbody, nullptr, [&] {
+      for (int step : kRoundSteps) {
+        if (st != EZO_OK) break;
+        st = launch_step(b, step, b->cap_stream);
+      }
+    });
+  }
+  g_prof_on = prof;
+  b->view = saved;
+  if (e == cudaSuccess && st == EZO_OK) e = cudaGraphInstantiate(&b->wgexec, b->wgraph, 0);
+  if (st == EZO_OK && e != cudaSuccess) st = cuda_fail(e, "wave graph");
+  if (st != EZO_OK) {
+    if (b->wgraph) cudaGraphDestroy(b->wgraph);
+    b->wgraph = nullptr;
+    b->wgexec = nullptr;
+  }
+  return st;
+#else
+  return fail(EZO_ERR_CUDA, "graph mode needs CUDA 12.4 or newer");
+#endif
 }
 
 ezo_status run_batch(ezo_batch* b, int mode, cudaStream_t s, bool sync = true) {
@@ -1093,12 +1235,7 @@ void ezo_batch_free(ezo_batch* b) {
 ezo_status ezo_batch_set_sample_lanes(ezo_batch* b, int32_t lanes) {
   if (!b || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8))
     return fail(EZO_ERR_INVALID_ARG, "ezo_batch_set_sample_lanes: lanes must be 0, 1, 2, 4 or 8");
-  if (b->gexec) {  // the graph holds the view by value
-    cudaGraphExecDestroy(b->gexec);
-    cudaGraphDestroy(b->graph);
-    b->gexec = nullptr;
-    b->graph = nullptr;
-  }
+  drop_graphs(b);  // the graphs hold the view by value
   b->view.sample_lanes = lanes;
   return EZO_OK;
 }
@@ -1113,11 +1250,7 @@ void apply_shape(ezo_batch* b, const ezo_shape& sh) {
   b->T_bisect = sh.bisect_lanes;
   b->grid_check = std::max(1, std::min(b->max_sample_tiles * b->T_check, b->sms * 16));
   b->grid_bisect = std::max(1, std::min(b->max_bisect_tiles * b->T_bisect, b->sms * 16));
-  // a captured graph holds the old launch shapes
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  b->gexec = nullptr;
-  b->graph = nullptr;
+  drop_graphs(b);  // a captured graph holds the old launch shapes
 }
 
 int log2_class(long long x) {
@@ -1238,12 +1371,7 @@ ezo_status ezo_batch_tune(ezo_batch* b, int32_t reps, ezo_shape* chosen, void* s
 
 ezo_status ezo_batch_attach_surrogate(ezo_batch* b, ezo_surrogate* sur, float margin) {
   if (!b) return fail(EZO_ERR_INVALID_ARG, "ezo_batch_attach_surrogate: null batch");
-  if (b->gexec) {
-    cudaGraphExecDestroy(b->gexec);
-    cudaGraphDestroy(b->graph);
-    b->gexec = nullptr;
-    b->graph = nullptr;
-  }
+  drop_graphs(b);
   if (!sur) {
     b->sur = nullptr;
     b->view.sbis = 0;
@@ -1301,9 +1429,18 @@ ezo_status ezo_batch_run_path(ezo_batch* b, int32_t sequential, int32_t mode, vo
   std::vector<SegState> sts;
   std::vector<uint8_t> contained((size_t)B * L);
   std::vector<int> kept(B, 0);
-  if (sequential == 2) {
-    // wavefront: each path runs its segments in order with the skip rule;
-    // the current segments of all paths share one batched run per wave
+  if (sequential == 2 && mode == EZO_RUN_GRAPH) {
+    // wavefront as one graph launch (build_wave_graph)
+    if (!b->wgexec) {
+      ezo_status st = build_wave_graph(b);
+      if (st != EZO_OK) return st;
+    }
+    EZO_CUDA(cudaGraphLaunch(b->wgexec, s));
+    EZO_CUDA(cudaStreamSynchronize(s));
+  } else if (sequential == 2) {
+    // wavefront with a host launch loop: each path runs its segments in
+    // order with the skip rule; the current segments of all paths share one
+    // batched run per wave
     ezo_status st = read_states(b, sts, s);
     if (st != EZO_OK) return st;
     for (int g = 0; g < B; ++g) sts[g].status = SEG_IDLE;

@@ -181,6 +181,13 @@ cudaError_t launch_round_end(const BatchView& v, cudaStream_t s);
 cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double tol, cudaStream_t s);
 // the skip rule after a speculative run, from the containment flags
 cudaError_t launch_path_skip(const BatchView& v, const uint8_t* contained, cudaStream_t s);
+// the wavefront order on the device (one wave graph): statuses and per-path
+// wave state reset, then per wave the skip rule and the next segment of
+// every path, which also sets the waves' and the rounds' WHILE conditions
+cudaError_t launch_wave_init(const BatchView& v, int* w_next, int* w_last, uint8_t* w_kept, cudaStream_t s);
+cudaError_t launch_wave_select(const BatchView& v, const uint8_t* contained, int* w_next, int* w_last,
+                               uint8_t* w_kept, unsigned long long cond_waves, unsigned long long cond_rounds,
+                               cudaStream_t s);
 // round end fused with the next round's sizing (the run loops' last kernel)
 cudaError_t launch_round_close(const BatchView& v, cudaStream_t s);
 // recovery (Sec. VI-B)

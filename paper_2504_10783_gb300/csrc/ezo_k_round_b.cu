@@ -703,6 +703,73 @@ __global__ void __launch_bounds__(128) k_path_skip(BatchView v, const uint8_t* _
   }
 }
 
+// The wavefront order of Sec. VI-A on the device, one wave per call: every
+// path runs its segments in order, the current segment of every path in the
+// same batched run. Per path (indexed by its first segment g0): w_next[g0] is
+// the next segment to consider (-1 when the path is done), w_last[g0] the
+// segment the previous wave ran (-1 if none), w_kept[g] = 1 for a segment
+// that ran. The previous wave's segment ends the path when it reports a
+// collision (t_col, Sec. IV-C); otherwise the next segments whose endpoints
+// lie in the polytope of a kept earlier segment of the path (contained, from
+// k_containment) are skipped and the first other one becomes active. One
+// block; the block's count of active segments sets both WHILE conditions of
+// the wave graph (waves and rounds).
+__global__ void k_wave_init(BatchView v, int* w_next, int* w_last, uint8_t* w_kept) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < v.B; g += gridDim.x * blockDim.x) {
+    v.st[g].status = SEG_IDLE;
+    w_kept[g] = 0;
+    w_next[g] = v.path_first[g] == g ? g : -1;
+    w_last[g] = -1;
+  }
+}
+
+__global__ void k_wave_select(BatchView v, const uint8_t* __restrict__ contained, int* w_next, int* w_last,
+                              uint8_t* w_kept, unsigned long long cond_waves, unsigned long long cond_rounds) {
+  __shared__ int s_active;
+  if (threadIdx.x == 0) s_active = 0;
+  __syncthreads();
+  const int L = v.max_path_len;
+  int act = 0;
+  for (int g0 = threadIdx.x; g0 < v.B; g0 += blockDim.x) {
+    if (v.path_first[g0] != g0) continue;
+    int g = w_next[g0];
+    const int last = w_last[g0];
+    if (last >= 0 && v.st[last].status == SEG_IN_COLLISION) g = -1;
+    if (g < 0) {
+      w_next[g0] = -1;
+      w_last[g0] = -1;
+      continue;
+    }
+    while (g < v.B && v.path_first[g] == g0) {
+      bool skip = false;
+      for (int j = g0; j < g && !skip; ++j)
+        if (w_kept[j] && contained[(long long)g * L + (j - g0)]) skip = true;
+      if (!skip) break;
+      v.st[g].status = SEG_SKIPPED;
+      ++g;
+    }
+    if (g < v.B && v.path_first[g] == g0) {
+      v.st[g].status = SEG_ACTIVE;
+      w_kept[g] = 1;
+      w_last[g0] = g;
+      w_next[g0] = g + 1;
+      ++act;
+    } else {
+      w_next[g0] = -1;
+      w_last[g0] = -1;
+    }
+  }
+  if (act) atomicAdd(&s_active, act);
+  __syncthreads();
+#if CUDART_VERSION >= 12040
+  if (threadIdx.x == 0) {
+    const unsigned c = s_active > 0 ? 1u : 0u;
+    if (cond_waves) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_waves, c);
+    if (cond_rounds) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_rounds, c);
+  }
+#endif
+}
+
 #endif  // !EZO_BOX_TU
 
 #if EZO_BOX_TU
@@ -802,6 +869,18 @@ cudaError_t launch_containment(const BatchView& v, uint8_t* contained, double to
 
 cudaError_t launch_path_skip(const BatchView& v, const uint8_t* contained, cudaStream_t s) {
   k_path_skip<<<(v.B + 3) / 4, 128, 0, s>>>(v, contained);  // one warp per segment index
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wave_init(const BatchView& v, int* w_next, int* w_last, uint8_t* w_kept, cudaStream_t s) {
+  k_wave_init<<<(v.B + 255) / 256, 256, 0, s>>>(v, w_next, w_last, w_kept);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wave_select(const BatchView& v, const uint8_t* contained, int* w_next, int* w_last,
+                               uint8_t* w_kept, unsigned long long cond_waves, unsigned long long cond_rounds,
+                               cudaStream_t s) {
+  k_wave_select<<<1, 1024, 0, s>>>(v, contained, w_next, w_last, w_kept, cond_waves, cond_rounds);
   return cudaGetLastError();
 }
 

@@ -753,6 +753,92 @@ def test_wavefront_equals_sequential_on_several_paths(ezo):
         np.testing.assert_array_equal(a.A, b.A)
 
 
+def test_wave_graph_equals_host_wavefront_and_oracle_order(ezo):
+    """The wavefront order (Sec. VI-A) as one graph launch: two obstacle sets,
+    three paths with uneven N_p, one of them running into an obstacle (t_col,
+    Sec. IV-C) so that the rest of its path must stay idle. The single graph
+    (the skip rule and the next segment of every path chosen on the device,
+    waves and rounds as nested WHILE nodes) keeps, skips and stops the same
+    segments with the same polytopes as the host-driven wavefront loop; the
+    kept segments are the ones the oracle's skip rule picks from the GPU
+    polytopes in path order; a second launch after a reset and a launch after
+    the graph is rebuilt for another launch shape give the same bits."""
+    rd, env_np, v1, v2 = planar_scene()
+    c = orc.sphere_centres(rd, (0.5 * (v1 + v2))[None])[0]
+    blocked = np.vstack([env_np.spheres, [[c[10, 0], c[10, 1], 0.0, 0.15]]])
+    robot = ezo.Robot(rd)
+    envs = [ezo.Env(env_np), ezo.Env(blocked)]
+    # path 0: a free segment in six pieces (most of them skipped);
+    # path 1 (blocked set, whose new sphere covers the first 65% of that
+    # segment): a free step back from v2, then a segment ending at the
+    # blocked midpoint, then one more segment (never run); path 2: three
+    # pieces of path 0's segment
+    q = v1 + 0.85 * (v2 - v1)
+    assert orc.signed_distance(rd, wl.Env("b", blocked),
+                               v2[None, :] + np.linspace(0, 1, 50)[:, None] * (q - v2)[None, :]).min() > 0
+    t6 = np.linspace(0.0, 1.0, 7)[:, None]
+    t3 = np.linspace(0.0, 1.0, 4)[:, None]
+    paths = [((1.0 - t6) * v1 + t6 * v2, 0), (np.array([v2, q, 0.5 * (v1 + v2), v1 + 0.3 * (v2 - v1)]), 1),
+             ((1.0 - t3) * v1 + t3 * v2, 0)]
+    V1, V2, seg_env, pf, where = [], [], [], [], []
+    for pi, (verts, e) in enumerate(paths):
+        first = len(V1)
+        for k in range(verts.shape[0] - 1):
+            V1.append(verts[k])
+            V2.append(verts[k + 1])
+            seg_env.append(e)
+            pf.append(first)
+            where.append((pi, k))
+    B = len(V1)
+    seg_np = np.asarray([400 + 150 * (g % 3) for g in range(B)], dtype=np.int32)
+    prm = ezo.Params.make(eps=0.1, delta=0.05, n_p=700, n_f=10, n_b=10, n_mix=20, seed=29, t_col=1e-3)
+
+    def batch():
+        return ezo.Batch(robot, envs, np.asarray(V1), np.asarray(V2), prm, seg_env=seg_env, seg_np=seg_np,
+                         seg_stream=np.arange(B, dtype=np.uint32), path_first=pf)
+
+    def run(bt, mode):
+        bt.reset()
+        bt.run_path(sequential=2, mode=mode)
+        return [bt.segment(g) for g in range(B)]
+
+    host = run(batch(), ezo.RUN_HOST_LOOP)
+    bt = batch()
+    graph = run(bt, ezo.RUN_GRAPH)
+    again = run(bt, ezo.RUN_GRAPH)
+    sh = bt.shape()
+    bt.set_shape(sh["sample_fill_tiles"], 1 if sh["check_lanes"] != 1 else 2, sh["bisect_lanes"])
+    rebuilt = run(bt, ezo.RUN_GRAPH)
+    for other in (graph, again, rebuilt):
+        assert [r.status for r in other] == [r.status for r in host]
+        for a, b in zip(host, other):
+            if a.status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE):
+                np.testing.assert_array_equal(a.A, b.A)
+                np.testing.assert_array_equal(a.b, b.b)
+    st = [r.status for r in graph]
+    # the oracle's order: per path, skip a segment inside a kept polytope,
+    # stop after a collision
+    for pi, (verts, _) in enumerate(paths):
+        gs = [g for g in range(B) if where[g][0] == pi]
+        kept, stopped = [], False
+        for g in gs:
+            k = where[g][1]
+            if stopped:
+                assert st[g] == ezo.SEG_IDLE
+                continue
+            if any(orc.segment_contained(graph[j].A, graph[j].b, verts[k], verts[k + 1]) for j in kept):
+                assert st[g] == ezo.SEG_SKIPPED
+                continue
+            assert st[g] not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE)
+            kept.append(g)
+            if st[g] == ezo.SEG_IN_COLLISION:
+                stopped = True
+            else:
+                assert orc.segment_contained(graph[g].A, graph[g].b, verts[k], verts[k + 1], tol=1e-12)
+    assert st[6 + 1] == ezo.SEG_IN_COLLISION and st[6 + 2] == ezo.SEG_IDLE
+    assert sum(s == ezo.SEG_SKIPPED for s in st) >= 3
+
+
 def test_fp32_fma_probe_within_the_nominal_peak(ezo):
     """The FMA calibration lies between half and 105% of the nominal FP32 rate
     (SMs x 128 lanes x 2 flops x the maximum SM clock)."""
