@@ -255,12 +255,29 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
       }
       int e = i + 1;
       while (e < n_spheres && runs[e] == runs[i]) ++e;
-      for (auto& rn : runs[i]) blocks.push_back(make_int4(i, e - i, rn.first, rn.second));
+      for (auto& rn : runs[i]) {
+        // the kernels take a block's rows in register chunks of EZO_CH
+        // spheres (a short last chunk is padded): each block is oriented
+        // for the fewer padded pair tests (the test is symmetric in the two
+        // spheres of a pair)
+        const int ni = e - i, nk = rn.second;
+        const long pad_rows = (long)((ni + EZO_CH - 1) / EZO_CH) * nk;
+        const long pad_cols = (long)((nk + EZO_CH - 1) / EZO_CH) * ni;
+        blocks.push_back(pad_cols < pad_rows ? make_int4(rn.first, nk, i, ni) : make_int4(i, ni, rn.first, nk));
+      }
       i = e;
     }
-    if (ok && !blocks.empty() && (int)blocks.size() <= EZO_MAX_SBLK) {
-      h.n_sblk = (int)blocks.size();
-      for (size_t b = 0; b < blocks.size(); ++b) h.sblk[b] = blocks[b];
+    // work items: one chunk of at most EZO_CH rows against all partners of
+    // its block, sorted by partner count so that the lanes that take
+    // consecutive items run loops of about the same length
+    std::vector<int4> items;
+    for (const int4& B : blocks)
+      for (int r0 = B.x; r0 < B.x + B.y; r0 += EZO_CH)
+        items.push_back(make_int4(r0, std::min(EZO_CH, B.x + B.y - r0), B.z, B.w));
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+    if (ok && !items.empty() && (int)items.size() <= EZO_MAX_SBLK) {
+      h.n_sblk = (int)items.size();
+      for (size_t b = 0; b < items.size(); ++b) h.sblk[b] = items[b];
     } else {
       h.n_sblk = 0;
     }

@@ -21,7 +21,7 @@
 #define EZO_MAX_SPHERES 256
 #define EZO_MAX_OBS 4096
 #define EZO_CH 8
-#define EZO_MAX_SBLK 16
+#define EZO_MAX_SBLK 32
 #define EZO_MAX_BOX 32    // robot boxes
 #define EZO_MAX_EBOX 64   // obstacle boxes per environment
 
@@ -100,9 +100,10 @@ struct RobotDev {
   float4 sph[EZO_MAX_SPHERES];       // local x, y, z and radius (sorted by frame)
   const ushort2* self_pairs;         // [n_self] indices into the sorted spheres
   const float* self_rr;              // [n_self] (r_i + r_j)^2
-  // Self pairs as blocks of sorted spheres [i0, i0 + ni) x [k0, k0 + nk) when
-  // the pair list is such a union (n_sblk > 0, then n_self pairs are not
-  // used); swept like obstacles with band E_self.
+  // Self pairs as work items (r0, nr, k0, nk): sorted spheres [r0, r0 + nr),
+  // nr <= EZO_CH, each against the partners [k0, k0 + nk), when the pair
+  // list is a union of such blocks (n_sblk > 0, then the n_self pairs are
+  // not used); swept like obstacles with band E_self.
   int n_sblk;
   float E_self;
   int4 sblk[EZO_MAX_SBLK];
@@ -494,74 +495,95 @@ __device__ __forceinline__ bool collide_group(const float (&q)[NDOF], const Robo
         m[k] = fmax3f(m[k], t.x, t.y);
       }
     }
+    // spheres inside the rounding band of the fast form, as a bit mask; the
+    // rare re-check is one rolled loop (short code: the unrolled sweep
+    // already fills the instruction cache)
+    unsigned band = 0u;
 #pragma unroll
     for (int k = 0; k < EZO_CH; ++k) {
+      const float diff = m[k] - cen[s0 + k].w;
+      if (diff > E) hit = true;
+      else if (diff >= -E) band |= 1u << k;
+    }
+    while (band) {
+      // decide with differences, over the same obstacles as this lane's
+      // maximum (its pairs)
+      const int k = __ffs(band) - 1;
+      band &= band - 1u;
       const float4 c = cen[s0 + k];
-      const float diff = m[k] - c.w;
-      if (diff > E) {
-        hit = true;
-      } else if (diff >= -E) {
-        // inside the rounding band of the fast form: decide with differences,
-        // over the same obstacles as this lane's maximum (its pairs)
-        const float r = cr[k].x;
-        for (int jj = 2 * lg; jj < n_obs; jj += 2 * T) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (jj + h < n_obs) {
-              const float4 o = obs_at(obs_s, jj + h);
-              const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
-              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const float sr = r + o.w;
-              if (d2 < sr * sr) hit = true;
-            }
-          }
-        }
+      const float r = sph_s[s0 + k].w;
+      for (int j = 2 * lg; j < n_obs; j += (j & 1) ? 2 * T - 1 : 1) {
+        const float4 o = obs_at(obs_s, j);
+        const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float sr = r + o.w;
+        if (d2 < sr * sr) hit = true;
       }
     }
   }
   // ---- self pairs ----
   if (rs.n_sblk > 0) {
-    // blocks [i0, i0 + ni) x [k0, k0 + nk) of sorted spheres, same fast form
-    // with the partner's (c_k, r_k) as the obstacle and -hu_k as its offset
+    // work items (r0, nr, k0, nk) of up to EZO_CH rows, lane lg of the group
+    // taking items lg, lg + T, .. (the lanes run the same instructions on
+    // their own items); same fast form as the obstacles with the partner's
+    // (c_k, r_k) as the obstacle and -hu_k as its offset. The partners go two
+    // at a time through packed FP32 FMAs; each half is the scalar fma.rn
+    // chain of its pair, and a missing second partner of an odd count gets
+    // offset -inf, which no maximum keeps.
     const float Es = rs.E_self;
-    for (int bk = 0; bk < rs.n_sblk; ++bk) {
-      const int4 B = rs.sblk[bk];
-      for (int s0 = B.x; s0 < B.x + B.y; s0 += EZO_CH) {
-        float4 cc[EZO_CH];
-        float rr[EZO_CH], m[EZO_CH];
+    for (int it0 = 0; it0 < rs.n_sblk; it0 += T) {
+      const int it = it0 + lg;
+      const int4 I = it < rs.n_sblk ? rs.sblk[it] : make_int4(0, 0, 0, 0);
+      float2 cx[EZO_CH], cy[EZO_CH], cz[EZO_CH], cr[EZO_CH];
+      float hu[EZO_CH], m[EZO_CH];
+#pragma unroll
+      for (int k = 0; k < EZO_CH; ++k) {
+        const bool in = k < I.y;
+        const float4 c = in ? cen[I.x + k] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+        const float r = in ? sph_s[I.x + k].w : 0.f;
+        cx[k] = make_float2(c.x, c.x);
+        cy[k] = make_float2(c.y, c.y);
+        cz[k] = make_float2(c.z, c.z);
+        cr[k] = make_float2(r, r);
+        hu[k] = c.w;
+        m[k] = -3.0e38f;
+      }
+      for (int u = 0; 2 * u < I.w; ++u) {
+        const int qa = I.z + 2 * u;
+        const bool two = 2 * u + 1 < I.w;
+        const float4 a = cen[qa];
+        const float4 b = two ? cen[qa + 1] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+        const float2 ox = make_float2(a.x, b.x), oy = make_float2(a.y, b.y), oz = make_float2(a.z, b.z);
+        const float2 oR = make_float2(sph_s[qa].w, two ? sph_s[qa + 1].w : 0.f);
+        const float2 w = make_float2(-a.w, -b.w);
 #pragma unroll
         for (int k = 0; k < EZO_CH; ++k) {
-          const bool in = s0 + k < B.x + B.y;
-          cc[k] = in ? cen[s0 + k] : make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
-          rr[k] = in ? sph_s[s0 + k].w : 0.f;
-          m[k] = -3.0e38f;
+          float2 t = __ffma2_rn(cr[k], oR, w);
+          t = __ffma2_rn(cz[k], oz, t);
+          t = __ffma2_rn(cy[k], oy, t);
+          t = __ffma2_rn(cx[k], ox, t);
+          m[k] = fmax3f(m[k], t.x, t.y);
         }
-        for (int q = B.z + lg; q < B.z + B.w; q += T) {
+      }
+      unsigned band = 0u;
+#pragma unroll
+      for (int k = 0; k < EZO_CH; ++k) {
+        const float diff = m[k] - hu[k];
+        if (diff > Es) hit = true;
+        else if (diff >= -Es) band |= 1u << k;
+      }
+      while (band) {
+        // rounding band: direct differences over the item's partners
+        const int k = __ffs(band) - 1;
+        band &= band - 1u;
+        const float4 c = cen[I.x + k];
+        const float r = sph_s[I.x + k].w;
+        for (int q = I.z; q < I.z + I.w; ++q) {
           const float4 o = cen[q];
-          const float ro = sph_s[q].w;
-#pragma unroll
-          for (int k = 0; k < EZO_CH; ++k) {
-            float t = fmaf(rr[k], ro, -o.w);
-            t = fmaf(cc[k].z, o.z, t);
-            t = fmaf(cc[k].y, o.y, t);
-            t = fmaf(cc[k].x, o.x, t);
-            m[k] = fmaxf(m[k], t);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < EZO_CH; ++k) {
-          const float diff = m[k] - cc[k].w;
-          if (diff > Es) {
-            hit = true;
-          } else if (diff >= -Es) {
-            for (int q = B.z + lg; q < B.z + B.w; q += T) {
-              const float4 o = cen[q];
-              const float dx = cc[k].x - o.x, dy = cc[k].y - o.y, dz = cc[k].z - o.z;
-              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const float sr = rr[k] + sph_s[q].w;
-              if (d2 < sr * sr) hit = true;
-            }
-          }
+          const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float sr = r + sph_s[q].w;
+          if (d2 < sr * sr) hit = true;
         }
       }
     }
@@ -644,26 +666,27 @@ __device__ __forceinline__ bool collide_wide(const float (&q)[NDOF], const Robot
         m[k] = fmax3f(m[k], t.x, t.y);
       }
     }
+    unsigned band = 0u;
 #pragma unroll
     for (int k = 0; k < CW; ++k) {
       const float diff = m[k] - hu[k];
-      if (diff > E) {
-        hit = true;
-      } else if (diff >= -E) {
-        // inside the rounding band: direct differences over this lane's
-        // obstacles (2p, 2p + 1 for its pairs p)
-        for (int jj = 2 * og; jj < n_obs; jj += 2 * OG) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (jj + h < n_obs) {
-              const float4 o = obs_at(obs_s, jj + h);
-              const float dx = cx[k].x - o.x, dy = cy[k].x - o.y, dz = cz[k].x - o.z;
-              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const float sr = cr[k].x + o.w;
-              if (d2 < sr * sr) hit = true;
-            }
-          }
-        }
+      if (diff > E) hit = true;
+      else if (diff >= -E) band |= 1u << k;
+    }
+    while (band) {
+      // inside the rounding band: direct differences over this lane's
+      // obstacles (2p, 2p + 1 for its pairs p), in one rolled loop
+      const int k = __ffs(band) - 1;
+      band &= band - 1u;
+      const int s = s0 + k * SG;
+      const float4 c = cen[s];
+      const float r = sph_s[s].w;
+      for (int j = 2 * og; j < n_obs; j += (j & 1) ? 2 * OG - 1 : 1) {
+        const float4 o = obs_at(obs_s, j);
+        const float dx = c.x - o.x, dy = c.y - o.y, dz = c.z - o.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float sr = r + o.w;
+        if (d2 < sr * sr) hit = true;
       }
     }
   }
