@@ -412,6 +412,35 @@ def run_workload(args):
         out.update({"rows": nb, "ms": ms, "rows_per_s": nb / (ms / 1e3), "gemm_tflops": tf, "peak": peak,
                     "peak_source": src, "frac": tf / peak, "nan_outputs": int(torch.isnan(y).sum()),
                     "wait_timed_out": sur.timed_out()})
+    elif args.workload == "train":
+        # surrogate training on exact labels of the benchmark scene: 2^rows_log2
+        # uniform configurations labelled by the exact signed-distance kernel,
+        # `steps` epochs of mini-batches of 3200 (every hidden-layer GEMM of the
+        # forward and backward passes on tcgen05), Adam; CUDA events around
+        # the whole call (labels, features, GEMMs, Adam)
+        nb = 1 << args.rows_log2
+        s7 = scenes["dh7"]
+        env = ezo.Env(wl.box_obstacles(s7["env_seed"], s7["n_obs"]))
+        sur = ezo.Surrogate(robot, seed=6)
+        for _ in range(args.warmup):
+            sur.train(env, n_samples=4 * 3200, epochs=1, batch=3200, lr=1e-3, data_seed=3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        losses = sur.train(env, n_samples=nb, epochs=args.steps, batch=3200, lr=1e-3, data_seed=12)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        # GEMM flops per sample and epoch: forward 2 (64 + 256 + 256) 256,
+        # backward (dW3, dZ2, dW2, dZ1, dW1) 2 (4 x 256 + 64) 256
+        gemm_per_sample = 2.0 * 256 * (64 + 256 + 256) + 2.0 * 256 * (4 * 256 + 64)
+        peak, src = bf16_peak()
+        tf = gemm_per_sample * nb * args.steps / (ms / 1e3) / 1e12
+        out.update({"samples": nb, "epochs": args.steps, "batch": 3200, "ms": ms,
+                    "samples_per_s": nb * args.steps / (ms / 1e3), "gemm_flops_per_sample": gemm_per_sample,
+                    "gemm_tflops_whole_call": tf, "peak": peak, "peak_source": src, "frac_whole_call": tf / peak,
+                    "what": "GEMM flops over the whole training call (labels, features, Adam included): "
+                            "a lower bound on the GEMM kernels' rate",
+                    "loss_per_epoch": [float(x) for x in losses]})
     else:
         out.update(measure_stress(ezo, torch, stream, scenes, rd, robot, args.np_stress))
     print(json.dumps(out))
@@ -673,8 +702,9 @@ def main():
                     help="only the timed path steps and the kernel pass (no plain, surrogate or checker legs)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes of the round kernels (for profiling runs)")
-    ap.add_argument("--workload", default="path", choices=["path", "batched", "stress", "surrogate"])
-    ap.add_argument("--rows-log2", type=int, default=20, help="surrogate: log2 of the configurations per call")
+    ap.add_argument("--workload", default="path", choices=["path", "batched", "stress", "surrogate", "train"])
+    ap.add_argument("--rows-log2", type=int, default=20,
+                    help="surrogate: log2 of the configurations per call; train: log2 of the labelled samples")
     ap.add_argument("--paths", type=int, default=256, help="batched: number of seed paths")
     ap.add_argument("--np-stress", type=int, default=1_000_000, help="stress: samples per round and segment")
     args = ap.parse_args()
