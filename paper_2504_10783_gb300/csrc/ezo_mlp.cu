@@ -103,24 +103,26 @@ __global__ void k_out(const __nv_bfloat16* __restrict__ H3, const float* __restr
 }
 
 // loss 1/N sum (y - t)^2, dy = 2 (y - t) / N, dZ3 = dy w4 * SiLU'(Z3)
-// (row-major and transposed BF16); dw4 = sum_i dy_i H3_i and db4 = sum_i dy_i
-// reduced per block in shared memory, then one atomic per column per block.
+// (row-major and transposed BF16); the block's partial sums of dw4 = sum_i
+// dy_i H3_i, db4 = sum_i dy_i and the loss go to part[blockIdx.x] (kOutPart
+// floats: kH columns, then db4 and the loss), summed per warp and then over
+// the warps in a fixed order; k_out_reduce adds the blocks' partials in a
+// fixed order, so training is reproducible bit for bit.
+constexpr int kOutPart = kH + 2;
+constexpr int kOutBlocks = 256;
+
 __global__ void __launch_bounds__(256) k_out_backward(const float* __restrict__ y, const float* __restrict__ t,
                                                       const float* __restrict__ Z3, const __nv_bfloat16* __restrict__ H3,
                                                       const float* __restrict__ w4, int N,
                                                       __nv_bfloat16* __restrict__ dZ3, __nv_bfloat16* __restrict__ dZ3t,
-                                                      float* __restrict__ gw4, float* __restrict__ gb4,
-                                                      float* __restrict__ loss) {
-  __shared__ float sw[kH];
-  __shared__ float sb, sl;
-  for (int c = threadIdx.x; c < kH; c += blockDim.x) sw[c] = 0.f;
-  if (threadIdx.x == 0) sb = sl = 0.f;
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
+                                                      float* __restrict__ part_out) {
+  __shared__ float sw[8][kH];
+  __shared__ float sbl[8][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float part[kH / 32];
 #pragma unroll
   for (int k = 0; k < kH / 32; ++k) part[k] = 0.f;
-  float pb = 0.f, pl = 0.f;
+  float pb = 0.f, pl = 0.f;  // the same on every lane of the warp (one row per warp step)
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N; i += (gridDim.x * blockDim.x) >> 5) {
     const float e = y[i] - t[i];
     const float dy = 2.f * e / (float)N;
@@ -137,20 +139,33 @@ __global__ void __launch_bounds__(256) k_out_backward(const float* __restrict__ 
     }
   }
 #pragma unroll
-  for (int k = 0; k < kH / 32; ++k) atomicAdd(&sw[lane + 32 * k], part[k]);
+  for (int k = 0; k < kH / 32; ++k) sw[warp][lane + 32 * k] = part[k];
   if (lane == 0) {
-    atomicAdd(&sb, pb);
-    atomicAdd(&sl, pl);
+    sbl[warp][0] = pb;
+    sbl[warp][1] = pl;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < kH; c += blockDim.x) atomicAdd(&gw4[c], sw[c]);
-  if (threadIdx.x == 0) {
-    atomicAdd(gb4, sb);
-    atomicAdd(loss, sl);
+  const int nw = blockDim.x >> 5;
+  float* out = part_out + (long long)blockIdx.x * kOutPart;
+  for (int c = threadIdx.x; c < kOutPart; c += blockDim.x) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v += c < kH ? sw[w][c] : sbl[w][c - kH];
+    out[c] = v;
   }
 }
 
-// column sums of a transposed [rows x N] BF16 matrix: out[r] = sum_i Mt[r][i]
+// dw4, db4 and the loss: the blocks' partials added in block order
+__global__ void k_out_reduce(const float* __restrict__ part, int blocks, float* __restrict__ gw4,
+                             float* __restrict__ gb4, float* __restrict__ loss) {
+  for (int c = threadIdx.x; c < kOutPart; c += blockDim.x) {
+    float v = 0.f;
+    for (int b = 0; b < blocks; ++b) v += part[(long long)b * kOutPart + c];
+    if (c < kH) gw4[c] = v;
+    else if (c == kH) gb4[0] = v;
+    else loss[0] = v;
+  }
+}
+
 __global__ void k_rowsum(const __nv_bfloat16* __restrict__ Mt, int rows, int N, float* __restrict__ out) {
   const int r = blockIdx.x;
   if (r >= rows) return;
@@ -272,6 +287,7 @@ struct ezo_surrogate {
                 *dZ1 = nullptr, *dZ1t = nullptr;
   float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *loss = nullptr;
   float* ws = nullptr;  // partial products of the weight gradients (K split over blocks)
+  float* ows = nullptr;  // the output layer's per-block gradient and loss partials
   // inference: the swizzled weight image of the tensor-core forward kernel
   // and its error flag
   void* wimg = nullptr;
@@ -346,8 +362,9 @@ cudaError_t train_grad(ezo_surrogate* S, const float* q, long long ldq, const fl
   if ((e = gemm(S, EPI_BIAS_SILU, a, s)) != cudaSuccess) return e;
   k_out<<<blocks_for((long long)B * 32, 256), 256, 0, s>>>(S->H3, S->p + kOffW4, S->p + kOffB4, B, nullptr, S->y);
   // backward
-  k_out_backward<<<std::min(256, blocks_for((long long)B * 32, 256)), 256, 0, s>>>(
-      S->y, t, S->Z3, S->H3, S->p + kOffW4, B, S->dZ3, S->dZ3t, S->g + kOffW4, S->g + kOffB4, S->loss);
+  const int ob = std::min(kOutBlocks, blocks_for((long long)B * 32, 256));
+  k_out_backward<<<ob, 256, 0, s>>>(S->y, t, S->Z3, S->H3, S->p + kOffW4, B, S->dZ3, S->dZ3t, S->ows);
+  k_out_reduce<<<1, 288, 0, s>>>(S->ows, ob, S->g + kOffW4, S->g + kOffB4, S->loss);
   GemmArgs w{};
   // dW3 = dZ3^T H2, db3 = column sums of dZ3
   w.A = S->dZ3t; w.lda = B; w.B = S->H2t; w.ldb = B; w.M = kH; w.N = kH; w.K = B; w.C = S->g + kOffW3; w.ldc = kH;
@@ -440,6 +457,7 @@ ezo_status ezo_surrogate_create(const ezo_robot* robot, uint64_t seed, ezo_surro
   if (e == cudaSuccess) e = dal(&S->W2t, (size_t)kH * kH);
   if (e == cudaSuccess) e = dal(&S->W3t, (size_t)kH * kH);
   if (e == cudaSuccess) e = dal(&S->loss, 1);
+  if (e == cudaSuccess) e = dal(&S->ows, (size_t)kOutBlocks * kOutPart);
   if (e == cudaSuccess) e = cudaMalloc(&S->wimg, mlp_tc_image_bytes());
   if (e == cudaSuccess) e = dal(&S->tc_err, 1);
   if (e == cudaSuccess) e = cudaMemset(S->tc_err, 0, sizeof(int));
@@ -488,7 +506,7 @@ void ezo_surrogate_free(ezo_surrogate* S) {
   if (!S) return;
   void* ps[] = {S->p,  S->g,   S->m,   S->v,   S->W1,  S->W2,  S->W3,   S->W2t,  S->W3t, S->X,   S->Xt,  S->H1,
                 S->H1t, S->H2, S->H2t, S->H3, S->H3t, S->dZ3, S->dZ3t, S->dZ2, S->dZ2t, S->dZ1, S->dZ1t, S->Z1, S->Z2,
-                S->Z3, S->y,   S->loss, S->wimg, S->tc_err, S->ws};
+                S->Z3, S->y,   S->loss, S->wimg, S->tc_err, S->ws, S->ows};
   for (void* q : ps)
     if (q) cudaFree(q);
   delete S;

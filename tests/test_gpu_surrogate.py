@@ -206,6 +206,23 @@ def test_surrogate_training_learns_signed_distance(ezo):
     assert after < 0.5 * before and after < 0.7 * float(np.std(sd)), (before, after, float(np.std(sd)))
 
 
+def test_surrogate_training_is_reproducible(ezo):
+    """Two trainings from the same seeds (initial weights, data, labels) end
+    with the same parameters bit for bit: every reduction of the training
+    step (split-K weight gradients, column sums, the output layer's gradient
+    and the loss) adds its partial sums in a fixed order. A ragged last
+    mini-batch (2^16 samples in batches of 3200) is included."""
+    rd, env_np = _scene()
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    params, losses = [], []
+    for _ in range(2):
+        sur = ezo.Surrogate(robot, seed=5)
+        losses.append(sur.train(env, n_samples=1 << 16, epochs=2, batch=3200, lr=1e-3, data_seed=21))
+        params.append(sur.params())
+    np.testing.assert_array_equal(params[0], params[1])
+    np.testing.assert_array_equal(losses[0], losses[1])
+
+
 @pytest.fixture(scope="module")
 def trained(ezo):
     rd, env_np = _scene()
