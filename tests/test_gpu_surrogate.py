@@ -327,3 +327,30 @@ def test_surrogate_path_gain_and_validity(ezo, trained):
         ratios.append(out[True] / out[False])
     print(f"exact bisection checks with / without the surrogate, seeds 1..5: {np.round(ratios, 3)}")
     assert np.mean(ratios) < 0.6, ratios
+
+
+def test_surrogate_wavefront_graph_equals_host_loop(ezo, trained):
+    """The wavefront order with surrogate-guided bisection as one graph
+    launch (waves and rounds as nested WHILE nodes, the tensor-core
+    bisection steps inside the round body) keeps, skips and inflates the
+    same segments with the same polytopes, bit for bit, as the host-driven
+    wavefront; the benchmark path is split into two paths of five segments."""
+    rd, env_np, robot, env, sur = trained
+    with open(os.path.join(GOLDEN, "workloads.json")) as f:
+        path = np.asarray(json.load(f)["dh7"]["path"])
+    K = path.shape[0] - 1
+    pf = np.asarray([0] * 5 + [5] * (K - 5), dtype=np.int32)
+    prm = ezo.Params.make(n_p=2000, seed=9)
+    res = {}
+    for mode in (ezo.RUN_HOST_LOOP, ezo.RUN_GRAPH):
+        bt = ezo.Batch(robot, [env], path[:-1], path[1:], prm, seg_stream=np.arange(K, dtype=np.uint32),
+                       path_first=pf)
+        bt.attach_surrogate(sur, 0.0)
+        bt.run_path(sequential=2, mode=mode)
+        res[mode] = [bt.segment(g) for g in range(K)]
+    assert [r.status for r in res[ezo.RUN_HOST_LOOP]] == [r.status for r in res[ezo.RUN_GRAPH]]
+    for a, b in zip(res[ezo.RUN_HOST_LOOP], res[ezo.RUN_GRAPH]):
+        if a.status not in (ezo.SEG_SKIPPED, ezo.SEG_IDLE):
+            np.testing.assert_array_equal(a.A, b.A)
+            np.testing.assert_array_equal(a.b, b.b)
+    assert any(r.status == ezo.SEG_ACCEPTED for r in res[ezo.RUN_GRAPH])
