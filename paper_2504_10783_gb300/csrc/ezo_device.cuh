@@ -448,7 +448,9 @@ __device__ __forceinline__ void fk_group(const float (&q)[NDOF], const RobotSmem
 // Lane lg of the group computes the centres of spheres s with s % T == lg
 // (every lane walks the chain), the group shares them through smem slot
 // `cen`, then lane lg sweeps the obstacle pairs p (obstacles 2p, 2p + 1) with
-// p % T == lg and self pairs p with p % T == lg. Returns the group-wide OR.
+// p % T == lg, and the self pairs: the work items it % T == lg when the
+// pairs form link blocks, else the listed pairs p % T == lg. Returns the
+// group-wide OR.
 // Every lane of the warp must call this together (invalid configurations are
 // evaluated and discarded).
 template <int NDOF, int T, bool BOX = false>
