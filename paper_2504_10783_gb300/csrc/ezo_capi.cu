@@ -85,6 +85,7 @@ struct ezo_robot {
   ushort2 *d_sbp = nullptr, *d_bbp = nullptr;  // self pairs with a box
   std::vector<int> sphere_sorted;              // caller's sphere index -> sorted index
   int n = 0, n_spheres = 0, nsp_pad = 0, n_self = 0;
+  int n_base = 0;  // sorted spheres on frame 0 (the fixed base), the first n_base
   std::vector<double> q_lo, q_hi;
   double reach = 0.0, r_max = 0.0;
   double fk_flops = 0.0;
@@ -99,8 +100,37 @@ struct ezo_env {
   double o_max = 0.0, R_max = 0.0;
   float4* d_box = nullptr;  // obstacle boxes, 4 float4 each
   int n_box = 0;
+  std::vector<float4> h_obs;  // the obstacle spheres as uploaded (FP32)
   EnvDev dev() const { return EnvDev{d_obs, d_nhw, n_obs, n_obs_pad, d_box, n_box, 0}; }
+  EnvDev dev_for(const ezo_robot* r) const;
 };
+
+// The robot spheres on the fixed base frame sit where they are for every
+// configuration, so their pairs with a static obstacle set need no test per
+// configuration when every such pair is clear. The sweep then starts at the
+// first whole chunk of EZO_CH spheres past them; the clearance is checked in
+// FP64 on the FP32 values the kernels use, against 1e-4 m, far above the
+// rounding band of the FP32 test (the kernels place a base sphere exactly at
+// its FP32 local coordinates), so every label is what the full sweep gives.
+// Any base sphere within 1e-4 m of an obstacle keeps the full sweep.
+static int sweep_first(const ezo_robot* r, const ezo_env* e) {
+  const int cut = (r->n_base / EZO_CH) * EZO_CH;
+  if (cut == 0) return 0;
+  for (int s = 0; s < cut; ++s) {
+    const float4 l = r->host.sph[s];
+    for (const float4& o : e->h_obs) {
+      const double dx = (double)l.x - o.x, dy = (double)l.y - o.y, dz = (double)l.z - o.z;
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) - (double)l.w - (double)o.w <= 1e-4) return 0;
+    }
+  }
+  return cut;
+}
+
+EnvDev ezo_env::dev_for(const ezo_robot* r) const {
+  EnvDev d = dev();
+  d.s_first = sweep_first(r, this);
+  return d;
+}
 
 static float band_E(const ezo_robot* r, const ezo_env* e) {
   // rounding bound of max_j t_ij - hu_i for the fast pair form (|c| <= reach,
@@ -210,6 +240,7 @@ ezo_status ezo_robot_create(int32_t n, const double* a, const double* alpha, con
     }
     h.frame_first[n + 1] = n_spheres;
   }
+  r->n_base = h.frame_first[1];
   r->reach = chain + loc_max;
   r->sphere_sorted = inv;
   std::vector<ushort2> pairs(std::max(1, n_self_pairs));
@@ -358,6 +389,7 @@ ezo_status ezo_env_create(int32_t n_obs, const double* xyzr, ezo_env** out) {
   for (int j = 0; j < n_obs; ++j) {
     const double x = xyzr[4 * j], y = xyzr[4 * j + 1], z = xyzr[4 * j + 2], R = xyzr[4 * j + 3];
     obs[j] = make_float4((float)x, (float)y, (float)z, (float)R);
+    e->h_obs.push_back(obs[j]);
     const double xf = (float)x, yf = (float)y, zf = (float)z, Rf = (float)R;
     nhw[j] = (float)(-0.5 * (xf * xf + yf * yf + zf * zf - Rf * Rf));
     e->o_max = std::max(e->o_max, std::sqrt(x * x + y * y + z * z));
@@ -489,7 +521,7 @@ ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const
   if (lanes == 0) lanes = ezo_internal_tuned_lanes(robot, env, N, (cudaStream_t)stream);
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
     return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: lanes_per_config must be 0, 1, 2, 4 or 8");
-  cudaError_t e = launch_check_flat(robot->d_robot, robot->n, robot->nsp_pad, robot->n_box, env->dev(), band_E(robot, env), q_dev, ldq, N,
+  cudaError_t e = launch_check_flat(robot->d_robot, robot->n, robot->nsp_pad, robot->n_box, env->dev_for(robot), band_E(robot, env), q_dev, ldq, N,
                                     flags_dev, lanes, sm_count() * 32, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "ezo_check_collision");
   g_err.clear();
@@ -563,7 +595,7 @@ __attribute__((visibility("hidden"))) const RobotDev* ezo_internal_robot_dev(con
 __attribute__((visibility("hidden"))) int ezo_internal_env_dev(const ezo_robot* r, const ezo_env* e,
                                                                 EnvDevFull* out) {
   if (!r || !e || !out) return 1;
-  out->e = e->dev();
+  out->e = e->dev_for(r);
   out->E = band_E(r, e);
   out->pad = 0.f;
   return 0;
@@ -582,7 +614,10 @@ __attribute__((visibility("hidden"))) int ezo_internal_env_boxes(const ezo_env* 
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env) {
   if (!robot || !env) return 0.0;
   // 8 flops per sphere pair, ~30 per sphere-box pair, ~330 per box-box pair
-  return robot->fk_flops + 8.0 * ((double)robot->n_spheres * env->n_obs + robot->n_self) +
+  // the base spheres the sweep skips (sweep_first) are tested once per
+  // obstacle set, not per configuration
+  const double swept = (double)robot->n_spheres - sweep_first(robot, env);
+  return robot->fk_flops + 8.0 * (swept * env->n_obs + robot->n_self) +
          30.0 * ((double)robot->n_spheres * env->n_box + (double)robot->n_box * env->n_obs + robot->n_sbp) +
          330.0 * ((double)robot->n_box * env->n_box + robot->n_bbp);
 }
@@ -1071,7 +1106,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   }
   b->envs.resize(n_env);
   for (int e = 0; e < n_env; ++e) {
-    b->envs[e].e = envs[e]->dev();
+    b->envs[e].e = envs[e]->dev_for(robot);
     b->envs[e].E = band_E(robot, envs[e]);
     b->max_obs_pad = std::max(b->max_obs_pad, envs[e]->n_obs_pad);
     b->max_ebox = std::max(b->max_ebox, envs[e]->n_box);
@@ -1880,7 +1915,7 @@ ezo_status ezo_check_path(const ezo_robot* robot, const ezo_env* env, const doub
   if (e == cudaSuccess) e = cudaMemsetAsync(d_edge, 0, (size_t)K, s);
   if (e == cudaSuccess) {
     const int lanes = ezo_internal_tuned_lanes(robot, env, N, s);
-    e = launch_check_path(robot->d_robot, n, robot->nsp_pad, robot->n_box, env->dev(), band_E(robot, env), d_verts, K, d_off, N,
+    e = launch_check_path(robot->d_robot, n, robot->nsp_pad, robot->n_box, env->dev_for(robot), band_E(robot, env), d_verts, K, d_off, N,
                           point_flags_dev, d_edge, lanes, sm_count() * 32, s);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(edge_flags, d_edge, (size_t)K, cudaMemcpyDeviceToHost, s);

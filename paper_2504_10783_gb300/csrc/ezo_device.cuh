@@ -187,7 +187,12 @@ struct EnvDev {
   int n_obs_pad;
   const float4* box;  // obstacle boxes, 4 float4 each: (centre, h_x), (axis 0, h_y), (axis 1, h_z), (axis 2, 0)
   int n_box;
-  int pad;
+  // first robot sphere of the obstacle sweep (a multiple of EZO_CH): the
+  // spheres before it sit on the fixed base frame, so their pairs with these
+  // obstacles are the same for every configuration, and they were found
+  // clear of every obstacle by more than any rounding band when the pair
+  // (robot, obstacle set) was set up; 0 when that does not hold
+  int s_first;
 };
 
 // Shared-memory image of an obstacle set, in pairs of spheres (2p, 2p + 1):
@@ -458,7 +463,7 @@ __device__ __forceinline__ bool collide_group(const float (&q)[NDOF], const Robo
                                               const float4* __restrict__ sph_s,
                                               const float4* __restrict__ obs_s,
                                               const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
-                                              const ushort2* __restrict__ self_pairs,
+                                              int s_first, const ushort2* __restrict__ self_pairs,
                                               const float* __restrict__ self_rr, float E,
                                               float4* __restrict__ cen, int lg, const BoxCtx& bx) {
   fk_group<NDOF, T, BOX>(q, rs, sph_s, cen, lg, bx);
@@ -469,7 +474,7 @@ __device__ __forceinline__ bool collide_group(const float (&q)[NDOF], const Robo
   bool hit = false;
   const int n_pairs = n_obs_pad >> 1;
   const float2* __restrict__ nhw2 = reinterpret_cast<const float2*>(nhw_s);
-  for (int s0 = 0; s0 < rs.n_spheres_pad; s0 += EZO_CH) {
+  for (int s0 = s_first; s0 < rs.n_spheres_pad; s0 += EZO_CH) {
     float2 cx[EZO_CH], cy[EZO_CH], cz[EZO_CH], cr[EZO_CH];
     float m[EZO_CH];
 #pragma unroll
@@ -628,7 +633,7 @@ template <int NDOF, int T>
 __device__ __forceinline__ bool collide_wide(const float (&q)[NDOF], const RobotSmem& rs,
                                              const float4* __restrict__ sph_s, const float4* __restrict__ obs_s,
                                              const float* __restrict__ nhw_s, int n_obs, int n_obs_pad,
-                                             const ushort2* __restrict__ self_pairs,
+                                             int s_first, const ushort2* __restrict__ self_pairs,
                                              const float* __restrict__ self_rr, float E,
                                              float4* __restrict__ cen, int lg, const BoxCtx& bx) {
   static_assert(T == 16 || T == 32, "wide groups are 16 or 32 lanes");
@@ -639,7 +644,7 @@ __device__ __forceinline__ bool collide_wide(const float (&q)[NDOF], const Robot
   const float2* __restrict__ nhw2 = reinterpret_cast<const float2*>(nhw_s);
   const int sg = lg / OG, og = lg % OG;
   const int nsp = rs.n_spheres_pad;
-  for (int s0 = sg; s0 < nsp; s0 += SG * CW) {
+  for (int s0 = s_first + sg; s0 < nsp; s0 += SG * CW) {
     float2 cx[CW], cy[CW], cz[CW], cr[CW];
     float hu[CW], m[CW];
 #pragma unroll

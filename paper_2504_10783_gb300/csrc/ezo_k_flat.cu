@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(128) k_check_flat(const RobotDev* __restrict__
 #pragma unroll
     for (int j = 0; j < NDOF; ++j) qq[j] = (j < rs.n) ? q[j * ldq + ic] : 0.f;
     const bool hit =
-        collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, env.n_obs, env.n_obs_pad, sp, srr, E, cen, lg, bx);
+        collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, env.n_obs, env.n_obs_pad, env.s_first, sp, srr, E, cen,
+                                    lg, bx);
     if (i < N && lg == 0) flags[i] = hit ? 1 : 0;
   }
 }

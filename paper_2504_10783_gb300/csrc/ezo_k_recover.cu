@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128) k_check_path(const RobotDev* __restrict__
     for (int j = 0; j < NDOF; ++j)
       qq[j] = (j < n) ? (float)__dadd_rn(va[j], __dmul_rn(t, __dsub_rn(vb[j], va[j]))) : 0.f;
     const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, env.n_obs, env.n_obs_pad,
-                                            robot->self_pairs, robot->self_rr, E, cen, lg, bx);
+                                            env.s_first, robot->self_pairs, robot->self_rr, E, cen, lg, bx);
     if (i < N && lg == 0) {
       if (point_flags) point_flags[i] = hit ? 1 : 0;
       if (hit) edge_flags[k] = 1;  // every writer stores the same value

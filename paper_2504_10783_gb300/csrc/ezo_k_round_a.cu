@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128) k_round_check(BatchView v, int max_obs_pa
 #pragma unroll
       for (int j = 0; j < NDOF; ++j) qq[j] = (j < v.n) ? S[(long long)j * st.s_cap + ic] : 0.f;
       const bool hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, ef.e.n_obs, ef.e.n_obs_pad,
-                                              robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
+                                              ef.e.s_first, robot->self_pairs, robot->self_rr, ef.E, cen, lg, bx);
       if (valid && lg == 0) fl[i] = hit ? 1 : 0;
     }
   }

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
     }
     const BoxCtx bx = box_ctx(gs, robot, nrbox, ef.e.n_box, gi);
     // the scene's scalars in registers for the N_b checks
-    const int n_obs = ef.e.n_obs, n_obs_pad = ef.e.n_obs_pad;
+    const int n_obs = ef.e.n_obs, n_obs_pad = ef.e.n_obs_pad, s_first = ef.e.s_first;
     const float E = ef.E;
     const ushort2* self_pairs = robot->self_pairs;
     const float* self_rr = robot->self_rr;
@@ -252,10 +252,10 @@ __global__ void __launch_bounds__(128) k_round_bisect(BatchView v, int max_obs_p
       for (int j = 0; j < NDOF; ++j) qq[j] = fmaf(f, dv32[j], p32[j]);
       bool hit;
       if constexpr (T > 8)
-        hit = collide_wide<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, self_pairs, self_rr, E, cen, lg,
-                                    bx);
+        hit = collide_wide<NDOF, T>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, s_first, self_pairs, self_rr, E, cen,
+                                    lg, bx);
       else
-        hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, self_pairs, self_rr, E,
+        hit = collide_group<NDOF, T, BOX>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, s_first, self_pairs, self_rr, E,
                                           cen, lg, bx);
       if (v.bis_mode == 1) {
         if (valid && lg == 0) {
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(96) k_round_bisect_pair(BatchView v, int max_o
       if (threadIdx.x == 0) cur_env = st.env;
       __syncthreads();
     }
-    const int n_obs = ef.e.n_obs, n_obs_pad = ef.e.n_obs_pad;
+    const int n_obs = ef.e.n_obs, n_obs_pad = ef.e.n_obs_pad, s_first = ef.e.s_first;
     const float E = ef.E;
     const ushort2* self_pairs = robot->self_pairs;
     const float* self_rr = robot->self_rr;
@@ -355,7 +355,8 @@ __global__ void __launch_bounds__(96) k_round_bisect_pair(BatchView v, int max_o
 #pragma unroll
         for (int j = 0; j < NDOF; ++j) qq[j] = fmaf(f, dv32[j], p32[j]);
         const bool hit =
-            collide_wide<NDOF, 32>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, self_pairs, self_rr, E, cen, lg, bx);
+            collide_wide<NDOF, 32>(qq, rs, sph_s, obs_s, nhw_s, n_obs, n_obs_pad, s_first, self_pairs, self_rr, E, cen, lg,
+                                   bx);
         if (lg == 0) s_hit[w] = hit ? 1 : 0;
       }
       __syncthreads();
