@@ -38,10 +38,10 @@ SEGSTATE_BYTES = 112  # sizeof(SegState): per-segment device state read back wit
 # step's kernels: sampling = the one-lane and the shared-walk kernels,
 # bisection = projection, halvings and end points; None where not captured
 # for the current kernels
-TRAFFIC = {"sample": 60672 + 45824, "check": 2867456, "bisect": 1277952 + 247552 + 1303296}
+TRAFFIC = {"sample": 60416 + 46080, "check": 2866688, "bisect": 1279488 + 248064 + 1303296}
 # DRAM bytes of one 2e6-configuration checker launch (same ncu capture recipe);
 # None until captured for the current kernel
-CHECKER_TRAFFIC_2E6 = 56046848 + 120320
+CHECKER_TRAFFIC_2E6 = 56046848 + 139008
 KIND_NAMES = ("round_size", "sample", "check", "certify", "bisect", "place", "round_end")
 
 
