@@ -149,7 +149,11 @@ void ezo_env_free(ezo_env* env);
  * configuration q_dev (n x N, dimension-major, stride ldq) and a test of
  * every robot sphere against every obstacle sphere and of every listed self
  * pair; flags_dev[i] = 1 iff some pair overlaps (squared centre distance
- * below the squared sum of radii), else 0. Stream-ordered, asynchronous.
+ * below the squared sum of radii), else 0. Robot spheres on the fixed base
+ * frame have the same centre for every configuration: when they all clear
+ * every obstacle sphere by more than 1e-4 m (checked on the host at each
+ * call) their obstacle pairs are not swept again; the flags are the same.
+ * Stream-ordered, asynchronous.
  * lanes_per_config selects 1, 2, 4 or 8 cooperating lanes per configuration
  * (0 = choose from N). Errors: EZO_ERR_INVALID_ARG (null handle, N < 0,
  * ldq < N, bad lanes value), EZO_ERR_CUDA (launch failure). */
@@ -633,7 +637,11 @@ ezo_status ezo_set_autotune(int32_t on);
 ezo_status ezo_probe_fp32_fma(double* tflops, void* cuda_stream);
 
 /* Algorithmic FP32 work of one exact configuration check (forward kinematics
- * plus 8 flops per obstacle pair and per self pair), as used for rooflines. */
+ * plus 8 flops per obstacle pair and per self pair), as used for rooflines.
+ * Obstacle pairs of robot spheres on the fixed base frame that the sweep
+ * skips for this obstacle set (every such sphere clear of every obstacle by
+ * more than 1e-4 m, whole chunks of eight spheres) are not counted: they are
+ * decided once per robot and obstacle set, not per configuration. */
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env);
 
 #ifdef __cplusplus
