@@ -637,12 +637,16 @@ ezo_status ezo_set_autotune(int32_t on);
 ezo_status ezo_probe_fp32_fma(double* tflops, void* cuda_stream);
 
 /* Algorithmic FP32 work of one exact configuration check (forward kinematics
- * plus 8 flops per obstacle pair and per self pair), as used for rooflines.
- * Obstacle pairs of robot spheres on the fixed base frame that the sweep
- * skips for this obstacle set (every such sphere clear of every obstacle by
- * more than 1e-4 m, whole chunks of eight spheres) are not counted: they are
- * decided once per robot and obstacle set, not per configuration. */
+ * plus 8 flops per obstacle pair and per self pair, every pair counted), as
+ * used for rooflines. */
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env);
+/* The robot spheres (the first ones, on the fixed base frame) whose obstacle
+ * pairs the checker's sweep decides once for this obstacle set instead of per
+ * configuration: every such sphere clears every obstacle sphere by more than
+ * 1e-4 m, whole chunks of eight spheres; 0 when none qualifies or for NULL
+ * handles. Their 8 x count x n_obs flops per configuration are part of
+ * ezo_check_flops but are not executed per configuration. */
+int32_t ezo_check_static_spheres(const ezo_robot* robot, const ezo_env* env);
 
 #ifdef __cplusplus
 }

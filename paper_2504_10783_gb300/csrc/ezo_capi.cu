@@ -614,12 +614,13 @@ __attribute__((visibility("hidden"))) int ezo_internal_env_boxes(const ezo_env* 
 double ezo_check_flops(const ezo_robot* robot, const ezo_env* env) {
   if (!robot || !env) return 0.0;
   // 8 flops per sphere pair, ~30 per sphere-box pair, ~330 per box-box pair
-  // the base spheres the sweep skips (sweep_first) are tested once per
-  // obstacle set, not per configuration
-  const double swept = (double)robot->n_spheres - sweep_first(robot, env);
-  return robot->fk_flops + 8.0 * (swept * env->n_obs + robot->n_self) +
+  return robot->fk_flops + 8.0 * ((double)robot->n_spheres * env->n_obs + robot->n_self) +
          30.0 * ((double)robot->n_spheres * env->n_box + (double)robot->n_box * env->n_obs + robot->n_sbp) +
          330.0 * ((double)robot->n_box * env->n_box + robot->n_bbp);
+}
+
+int32_t ezo_check_static_spheres(const ezo_robot* robot, const ezo_env* env) {
+  return (robot && env) ? sweep_first(robot, env) : 0;
 }
 
 // ------------------------------------------------------------------ batch --

@@ -123,6 +123,8 @@ def _sig(lib):
     f.ezo_probe_fp32_fma.argtypes = [_DP, _P]
     f.ezo_check_flops.argtypes = [_P, _P]
     f.ezo_check_flops.restype = C.c_double
+    f.ezo_check_static_spheres.argtypes = [_P, _P]
+    f.ezo_check_static_spheres.restype = _I32
     f.ezo_batch_get_shape.argtypes = [_P, C.POINTER(Shape)]
     f.ezo_batch_set_shape.argtypes = [_P, C.POINTER(Shape)]
     f.ezo_batch_tune.argtypes = [_P, _I32, C.POINTER(Shape), _P]
@@ -643,6 +645,12 @@ def probe_fp32_fma(stream=None) -> float:
 
 def check_flops(robot: Robot, env: Env) -> float:
     return float(lib().ezo_check_flops(robot.h, env.h))
+
+
+def check_static_spheres(robot: Robot, env: Env) -> int:
+    """Robot spheres whose obstacle pairs the checker decides once for this
+    obstacle set instead of per configuration (ezo_check_static_spheres)."""
+    return int(lib().ezo_check_static_spheres(robot.h, env.h))
 
 
 class Stats(C.Structure):

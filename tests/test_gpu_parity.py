@@ -100,11 +100,11 @@ def test_base_spheres_skipped_only_when_clear(ezo, lanes):
     """The 7-DOF arm's first eight spheres sit on the fixed base frame; the
     obstacle sweep skips them only when every base sphere clears every
     obstacle by more than 1e-4 m (their pairs are the same for every
-    configuration). With one obstacle added far away the counted flops drop
-    by 8 spheres x 65 obstacles x 8 against the sets where the full sweep
-    runs: the obstacle overlapping a base sphere (every configuration
-    collides) and the obstacle 5e-5 m from one. Labels match the oracle in
-    all three sets. (The bisection's wide check takes the same start; the
+    configuration). With one obstacle added far away the sweep starts past
+    8 spheres; with the obstacle overlapping a base sphere (every
+    configuration collides) or 5e-5 m from one the full sweep runs. The
+    algorithmic flop count is the same in all three sets. Labels match the
+    oracle in all three sets. (The bisection's wide check takes the same start; the
     round replays on this scene compare its decisions with the oracle.)"""
     rd, env_np, _ = dh7_scene()
     base = np.flatnonzero(np.asarray(rd.sphere_frame) == 0)
@@ -117,17 +117,18 @@ def test_base_spheres_skipped_only_when_clear(ezo, lanes):
     robot = ezo.Robot(rd)
     N = 3001
     q32 = wl.uniform_configs(19, rd, N).astype(np.float32)
-    flops = {}
+    flops, static = {}, {}
     for name, ob in extra.items():
         envw = wl.Env(name, np.vstack([env_np.spheres, [ob]]))
         env = ezo.Env(envw)
         flops[name] = ezo.check_flops(robot, env)
+        static[name] = ezo.check_static_spheres(robot, env)
         got = gpu_labels(ezo, robot, env, q32, lanes)
         ref = assert_labels_match(rd, envw, q32, got)
         if name == "touch":
             assert ref.all() and got.all()
-    assert flops["touch"] - flops["far"] == 8 * 8 * (env_np.n_obs + 1)
-    assert flops["near"] == flops["touch"]
+    assert static == {"far": 8, "touch": 0, "near": 0}
+    assert flops["far"] == flops["touch"] == flops["near"]
 
 
 def near_boundary_configs(rd, env_np, seed, n_seg=120, steps=(9, 17)):
