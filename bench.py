@@ -609,7 +609,7 @@ def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, fl
     per = ms / reps
     tf = N * flops_cfg / (per / 1e3) / 1e12
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    # the pair tests run per configuration: the survey's count less the
+    # the pair tests run per configuration: the count of every pair less the
     # obstacle pairs of the base-frame spheres decided once per obstacle set
     static = ezo.check_static_spheres(robot, env)
     tested = flops_cfg - 8.0 * static * env.spheres.shape[0]
@@ -619,8 +619,9 @@ def measure_checker(ezo, torch, robot, env, rd, stream, flush, props, sm_max, fl
                          "flops_per_config": flops_cfg,
                          "static_spheres": static, "flops_per_config_tested": tested,
                          "achieved_tested": tf_tested, "frac_tested": tf_tested / peak,
-                         "flops_note": "flops_per_config counts every pair (the survey's per-configuration "
-                                       "figure); the obstacle pairs of the first static_spheres robot spheres, "
+                         "flops_note": "flops_per_config counts every pair (8 flops per robot-obstacle and "
+                                       "self pair, plus the kinematics); the obstacle pairs of the first "
+                                       "static_spheres robot spheres, "
                                        "on the fixed base frame and clear of every obstacle, are decided once "
                                        "per obstacle set, so the pair tests run per configuration come to "
                                        "flops_per_config_tested",
