@@ -155,14 +155,21 @@ void ezo_env_free(ezo_env* env);
  * call) their obstacle pairs are not swept again; the flags are the same.
  * Stream-ordered, asynchronous.
  * lanes_per_config selects 1, 2, 4 or 8 cooperating lanes per configuration
- * (0 = choose from N). Errors: EZO_ERR_INVALID_ARG (null handle, N < 0,
- * ldq < N, bad lanes value), EZO_ERR_CUDA (launch failure). */
+ * (0 = choose from N, among the counts that fit). Each group of lanes keeps
+ * its sphere centres in shared memory, so large robots with many obstacles
+ * need more lanes: at the maximum sizes (256 spheres, 4096 obstacles) only 4
+ * and 8 fit. Errors: EZO_ERR_INVALID_ARG (null handle, N < 0, ldq < N, bad
+ * lanes value, spheres and obstacles beyond shared memory at that lanes
+ * value; nothing is launched), EZO_ERR_CUDA (launch failure). */
 ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
                                int64_t ldq, uint8_t* flags_dev, int32_t lanes_per_config, void* cuda_stream);
 
 /* Signed distance per configuration: min over the same pairs of
  * ||c_i - c_j|| - r_i - r_j in FP32 (negative iff in collision). Used to
- * label data and to bound ambiguous decisions. Stream-ordered. */
+ * label data and to bound ambiguous decisions. Stream-ordered.
+ * EZO_ERR_INVALID_ARG when the robot or env has boxes, or when its spheres
+ * and obstacles exceed the kernel's shared memory (one lane per
+ * configuration: (spheres + 1) x 64 centres plus the obstacles). */
 ezo_status ezo_signed_distance(const ezo_robot* robot, const ezo_env* env, const float* q_dev, int64_t N,
                                int64_t ldq, float* sd_dev, void* cuda_stream);
 
@@ -471,7 +478,9 @@ ezo_status ezo_path_points(const double* verts, int32_t n_verts, int32_t n, doub
  * collides. point_flags_dev (nullable, device, point_cap bytes): 1 per
  * colliding point, in edge order. *n_points (nullable) receives the point
  * count. Synchronous; uses stream-ordered scratch (cudaMallocAsync).
- * EZO_ERR_CAPACITY when point_cap is below the point count. */
+ * EZO_ERR_CAPACITY when point_cap is below the point count;
+ * EZO_ERR_INVALID_ARG when spheres and obstacles exceed shared memory even at
+ * 8 lanes per point (the lane count is chosen as in ezo_check_collision). */
 ezo_status ezo_check_path(const ezo_robot* robot, const ezo_env* env, const double* verts, int32_t n_verts,
                           double step, uint8_t* edge_flags, uint8_t* point_flags_dev, int64_t point_cap,
                           int64_t* n_points, void* cuda_stream);

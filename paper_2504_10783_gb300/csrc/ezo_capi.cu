@@ -30,6 +30,7 @@ ezo_status fail(ezo_status s, const std::string& msg) {
 
 ezo_status cuda_fail(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  (void)cudaGetLastError();  // the runtime's record of a non-sticky error, which the caller's next check would see
   return EZO_ERR_CUDA;
 }
 
@@ -521,6 +522,9 @@ ezo_status ezo_check_collision(const ezo_robot* robot, const ezo_env* env, const
   if (lanes == 0) lanes = ezo_internal_tuned_lanes(robot, env, N, (cudaStream_t)stream);
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
     return fail(EZO_ERR_INVALID_ARG, "ezo_check_collision: lanes_per_config must be 0, 1, 2, 4 or 8");
+  if (check_smem_bytes(robot->nsp_pad, env->n_obs_pad, 128, lanes, robot->n_box, env->n_box) > kSmemBudget)
+    return fail(EZO_ERR_INVALID_ARG,
+                "ezo_check_collision: robot and obstacle spheres exceed shared memory at this lanes_per_config");
   cudaError_t e = launch_check_flat(robot->d_robot, robot->n, robot->nsp_pad, robot->n_box, env->dev_for(robot), band_E(robot, env), q_dev, ldq, N,
                                     flags_dev, lanes, sm_count() * 32, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "ezo_check_collision");
@@ -535,6 +539,8 @@ ezo_status ezo_signed_distance(const ezo_robot* robot, const ezo_env* env, const
   if (N > 0 && (!q_dev || !sd_dev)) return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: null buffer");
   if (robot->n_box || env->n_box)
     return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: sphere geometries only (the robot or env has boxes)");
+  if (check_smem_bytes(robot->nsp_pad, env->n_obs_pad, 64, 1) > kSmemBudget)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_signed_distance: robot and obstacle spheres exceed shared memory");
   cudaError_t e = launch_sd_flat(robot->d_robot, robot->n, robot->nsp_pad, env->dev(), q_dev, ldq, N, sd_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "ezo_signed_distance");
   g_err.clear();
@@ -1113,7 +1119,7 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
     b->max_ebox = std::max(b->max_ebox, envs[e]->n_box);
   }
   const size_t smem_check = check_smem_bytes(robot->nsp_pad, b->max_obs_pad, 128, 1, robot->n_box, b->max_ebox);
-  if (smem_check > 220 * 1024) {
+  if (smem_check > kSmemBudget) {
     delete b;
     return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: robot spheres and obstacles exceed shared memory");
   }
@@ -1899,6 +1905,8 @@ ezo_status ezo_check_path(const ezo_robot* robot, const ezo_env* env, const doub
   if (st != EZO_OK) return st;
   if (n_points) *n_points = N;
   if (point_flags_dev && point_cap < N) return fail(EZO_ERR_CAPACITY, "ezo_check_path: point_cap < points");
+  if (check_smem_bytes(robot->nsp_pad, env->n_obs_pad, 128, 8, robot->n_box, env->n_box) > kSmemBudget)
+    return fail(EZO_ERR_INVALID_ARG, "ezo_check_path: robot and obstacle spheres exceed shared memory");
   if (K == 0) {
     g_err.clear();
     return EZO_OK;

@@ -209,5 +209,10 @@ cudaError_t launch_round_bisect_box(const BatchView& v, int T, int grid, cudaStr
 cudaError_t launch_fk_centres(const RobotDev* robot, const RobotFK64* r64, int n, int nsp_pad, const float* q,
                               long long ldq, long long N, int mode, double* out_c, float* err, cudaStream_t s);
 size_t check_smem_bytes(int n_spheres_pad, int n_obs_pad, int threads, int T, int n_rbox = 0, int n_ebox = 0);
+// Dynamic shared memory a collision kernel may request: the opt-in maximum
+// per block (227 KB) less the static robot image and a margin. The sphere
+// centres take (spheres + 1) x 16 bytes per group of lanes, so more lanes per
+// configuration need less.
+constexpr size_t kSmemBudget = 220 * 1024;
 
 }  // namespace ezo

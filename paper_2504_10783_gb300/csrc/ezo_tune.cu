@@ -60,18 +60,28 @@ extern "C" __attribute__((visibility("hidden"))) int ezo_internal_tuned_lanes(co
     if (M >= (1ll << 15)) return 4;
     return 8;
   };
-  if (!g_autotune || N <= 0) return rule(N);
   int n = 0, nsp = 0;
   double lo[EZO_MAX_DOF], hi[EZO_MAX_DOF];
   const RobotDev* rd = ezo_internal_robot_dev(robot, &n, &nsp, lo, hi);
   EnvDevFull ef{};
   if (!rd || ezo_internal_env_dev(robot, env, &ef) != 0) return rule(N);
+  const int nrbox = ezo_internal_robot_boxes(robot);
+  // only lane counts whose sphere centres fit in shared memory (more lanes,
+  // fewer groups per block, less memory); 8 when none does, which the entry
+  // points reject before launching
+  auto fits = [&](int T) {
+    return check_smem_bytes(nsp, ef.e.n_obs_pad, 128, T, nrbox, ef.e.n_box) <= kSmemBudget;
+  };
+  auto fit_up = [&](int T) {
+    while (T < 8 && !fits(T)) T *= 2;
+    return T;
+  };
+  if (!g_autotune || N <= 0) return fit_up(rule(N));
   RobotDev head;
   if (cudaMemcpy(&head, rd, sizeof(int) * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return rule(N);
   int dev = 0;
   cudaGetDevice(&dev);
   const int cls = size_class(N);
-  const int nrbox = ezo_internal_robot_boxes(robot);
   const auto key = std::make_tuple(dev, n, nsp, head.n_self, ef.e.n_obs_pad, cls, nrbox, ef.e.n_box);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -82,7 +92,7 @@ extern "C" __attribute__((visibility("hidden"))) int ezo_internal_tuned_lanes(co
   float* q = nullptr;
   uint8_t* flags = nullptr;
   float* bounds = nullptr;
-  int best = rule(N);
+  int best = fit_up(rule(N));
   if (cudaMalloc(&q, sizeof(float) * n * M) == cudaSuccess && cudaMalloc(&flags, M) == cudaSuccess &&
       cudaMalloc(&bounds, sizeof(float) * 2 * EZO_MAX_DOF) == cudaSuccess) {
     float hb[2 * EZO_MAX_DOF];
@@ -102,6 +112,7 @@ extern "C" __attribute__((visibility("hidden"))) int ezo_internal_tuned_lanes(co
     const int lanes[4] = {1, 2, 4, 8};
     for (int li = 0; li < 4; ++li) {
       const int T = lanes[li];
+      if (!fits(T)) continue;
       // one warm-up launch, then the best of three
       if (launch_check_flat(rd, n, nsp, nrbox, ef.e, ef.E, q, M, M, flags, T, sms * 32, s) != cudaSuccess) continue;
       float t_best = 1e30f;

@@ -240,19 +240,20 @@ def dh7_robot(r_base: float = 0.08, r_tip: float = 0.04) -> Robot:
     )
 
 
-def chain_robot(n: int = 10, a: float = 0.15, r: float = 0.04) -> Robot:
+def chain_robot(n: int = 10, a: float = 0.15, r: float = 0.04, per_link: int = 2) -> Robot:
     """An n-joint DH chain for chains longer than the 7-DOF arm: link length a,
     twists alternating +-pi/2, a base offset d_1 = 0.2 m, joint limits +-2.5
-    rad, two spheres of radius r per link on its distal frame k at
-    o_k - (1 - f) a x_k, f = 1/4 and 3/4 (along the a part of the link), and
-    self pairs between links at least three apart."""
+    rad, per_link spheres of radius r per link on its distal frame k at
+    o_k - (1 - f) a x_k, f = (i + 1/2) / per_link (along the a part of the
+    link; 1/4 and 3/4 for two), and self pairs between links at least three
+    apart."""
     a_ = np.full(n, a)
     alpha = np.array([np.pi / 2 if i % 2 == 0 else -np.pi / 2 for i in range(n)])
     d = np.zeros(n)
     d[0] = 0.2
     frames, xyz, rad, link = [], [], [], []
     for k in range(1, n + 1):
-        for f in (0.25, 0.75):
+        for f in ((i + 0.5) / per_link for i in range(per_link)):
             frames.append(k)
             xyz.append((-(1 - f) * a, 0.0, 0.0))
             rad.append(r)

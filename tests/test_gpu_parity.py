@@ -406,6 +406,36 @@ def test_chain10_labels_match_oracle(ezo, lanes):
     assert 0 < ref.sum() < q32.shape[0]
 
 
+def test_maximum_sizes_labels_match_oracle(ezo):
+    """The largest robot and obstacle set the library takes: 16 joints, 256
+    robot spheres (16 per link, 23,296 self pairs) and 4,096 obstacle
+    spheres. Each group of lanes keeps its sphere centres in shared memory,
+    so only 4 and 8 lanes per configuration fit; those (and the automatic
+    choice) match the oracle, while 1 and 2 lanes and the one-lane signed
+    distance are refused on the host with nothing launched, and the next
+    CUDA work runs normally."""
+    rd = wl.chain_robot(16, r=0.02, per_link=16)
+    env_np = wl.box_obstacles(41, 4096, box_lo=(-2.5, -2.5, -2.5), box_hi=(2.5, 2.5, 2.5), r_lo=0.02, r_hi=0.05)
+    assert rd.sphere_r.shape[0] == 256 and rd.self_pairs.shape[0] == 23296
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    q32 = wl.uniform_configs(23, rd, 96).astype(np.float32)
+    q64 = q32.astype(np.float64)
+    ref = orc.in_collision(rd, env_np, q64, chunk=4)  # 4 x 256 x 4096 pairs per chunk
+    assert 0 < ref.sum() < ref.size
+    sd = orc.signed_distance(rd, env_np, q64, chunk=4)
+    for lanes in (4, 8, 0):
+        got = gpu_labels(ezo, robot, env, q32, lanes)
+        diff = got != ref
+        assert np.all(np.abs(sd[diff]) < AMB), f"lanes {lanes}: {int(diff.sum())} labels differ outside the band"
+    for lanes in (1, 2):
+        with pytest.raises(ezo.EzoError):
+            gpu_labels(ezo, robot, env, q32, lanes)
+    with pytest.raises(ezo.EzoError):
+        ezo.signed_distance(robot, env, to_dev(q32), torch.empty(96, device="cuda"))
+    x = torch.full((1024,), 2.0, device="cuda")
+    assert float(x.sum()) == 2048.0
+
+
 def test_round_replay_chain10(ezo):
     """Rounds of a 10-joint chain replayed step by step against the oracle
     (walks, labels, test, candidates, bisection, planes)."""
