@@ -221,7 +221,11 @@ ezo_status ezo_hit_and_run(const double* A_dev, const double* b_dev, int32_t m, 
  * to (segments of a path are consecutive); used by ezo_batch_run_path.
  * The batch allocates its own device memory (state, polytopes, samples,
  * candidates) sized for m0 + n_f * n_it_max rows (at most 2048) and
- * max(N_p, M_{N_it}) samples per segment. Errors: EZO_ERR_INVALID_ARG, EZO_ERR_CUDA. */
+ * max(N_p, M_{N_it}) samples per segment. Its label and bisection kernels
+ * take at least the fewest lanes per configuration whose sphere centres fit
+ * in shared memory (4 for 256 robot spheres with 4096 obstacles; 1 for the
+ * usual robots); ezo_batch_set_shape refuses fewer. Errors:
+ * EZO_ERR_INVALID_ARG (also when even 8 lanes do not fit), EZO_ERR_CUDA. */
 ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env* const* envs, int32_t n_seg,
                             const double* v1, const double* v2, const int32_t* seg_env, const int32_t* seg_np,
                             const uint32_t* seg_stream, const int32_t* path_first, const double* A0,

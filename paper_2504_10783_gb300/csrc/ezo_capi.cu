@@ -664,6 +664,7 @@ struct ezo_batch {
   std::vector<double> v1h, v2h;
   BatchView view{};
   int T_check = 1, T_bisect = 4, split_below = 0;
+  int t_min = 1;  // fewest lanes per configuration whose sphere centres fit in shared memory
   long long tot_s1 = 0, tot_np = 0;  // samples of round 1 and N_p over the batch (tuning keys)
   int sms = 1;
   int grid_sample = 1, grid_check = 1, grid_bisect = 1;
@@ -1118,10 +1119,15 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
     b->max_obs_pad = std::max(b->max_obs_pad, envs[e]->n_obs_pad);
     b->max_ebox = std::max(b->max_ebox, envs[e]->n_box);
   }
-  const size_t smem_check = check_smem_bytes(robot->nsp_pad, b->max_obs_pad, 128, 1, robot->n_box, b->max_ebox);
-  if (smem_check > kSmemBudget) {
+  // the collision kernels keep one set of sphere centres per group of lanes
+  // in shared memory: large robots with many obstacles need more lanes per
+  // configuration (and per bisection candidate)
+  while (b->t_min <= 8 &&
+         check_smem_bytes(robot->nsp_pad, b->max_obs_pad, 128, b->t_min, robot->n_box, b->max_ebox) > kSmemBudget)
+    b->t_min *= 2;
+  if (b->t_min > 8) {
     delete b;
-    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: robot spheres and obstacles exceed shared memory");
+    return fail(EZO_ERR_INVALID_ARG, "ezo_batch_create: robot spheres and obstacles exceed shared memory at 8 lanes");
   }
   const long long B = n_seg, mc = b->m_cap;
   cudaError_t e = cudaSuccess;
@@ -1270,6 +1276,8 @@ ezo_status ezo_batch_create(const ezo_robot* robot, int32_t n_env, const ezo_env
   // by 5-30% in every round but the largest.
   b->T_bisect = tot_np >= (1ll << 20) ? ezo_internal_tuned_lanes(robot, envs[e_big], tot_np / 4, nullptr)
                                       : ((robot->n_box || b->max_ebox) ? 8 : 16);
+  b->T_check = std::max(b->T_check, b->t_min);
+  b->T_bisect = std::max(b->T_bisect, b->t_min);
   // walks share eight lanes in rounds with fewer walks than one warp per
   // scheduler would hold at one lane per walk
   b->split_below = (sms * 4 * 32) / kTile;
@@ -1341,6 +1349,9 @@ ezo_status ezo_batch_set_shape(ezo_batch* b, const ezo_shape* sh) {
   if (sh->sample_fill_tiles < 1 || !lanes_ok(sh->check_lanes) || !bis_ok)
     return fail(EZO_ERR_INVALID_ARG,
                 "ezo_batch_set_shape: sample_fill_tiles >= 1, check lanes 1, 2, 4 or 8, bisect lanes 1 to 32");
+  if (sh->check_lanes < b->t_min || sh->bisect_lanes < b->t_min)
+    return fail(EZO_ERR_INVALID_ARG,
+                "ezo_batch_set_shape: fewer lanes than the robot's sphere centres need in shared memory");
   apply_shape(b, *sh);
   g_err.clear();
   return EZO_OK;
@@ -1402,6 +1413,7 @@ ezo_status ezo_batch_tune(ezo_batch* b, int32_t reps, ezo_shape* chosen, void* s
         if (stage == 0) sh.bisect_lanes = cand[i];
         if (stage == 1) sh.check_lanes = cand[i];
         if (stage == 2) sh.sample_fill_tiles = cand[i];
+        if (sh.check_lanes < b->t_min || sh.bisect_lanes < b->t_min) continue;  // does not fit shared memory
         if (sh.bisect_lanes == best.bisect_lanes && sh.check_lanes == best.check_lanes &&
             sh.sample_fill_tiles == best.sample_fill_tiles)
           continue;

@@ -146,10 +146,13 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
                                          std::to_string((long long)EZO_NOALLOC_SCRATCH_BYTES) +
                                          " (lower n_p or n_f * n_it_max, or use ezo_batch_create)");
   // the collision kernels stage the robot spheres, the obstacles and one set
-  // of sphere centres per configuration group in shared memory
-  if (check_smem_bytes(nsp_pad, envf.e.n_obs_pad, 128, 1, ezo_internal_robot_boxes(robot), envf.e.n_box) >
-      220 * 1024)
-    return na_fail(EZO_ERR_INVALID_ARG, "robot spheres and obstacles exceed shared memory");
+  // of sphere centres per group of lanes in shared memory: large robots with
+  // many obstacles need more lanes per configuration
+  int t_min = 1;
+  while (t_min <= 8 && check_smem_bytes(nsp_pad, envf.e.n_obs_pad, 128, t_min, ezo_internal_robot_boxes(robot),
+                                        envf.e.n_box) > kSmemBudget)
+    t_min *= 2;
+  if (t_min > 8) return na_fail(EZO_ERR_INVALID_ARG, "robot spheres and obstacles exceed shared memory at 8 lanes");
   void* base = nullptr;
   ezo_status st = scratch_address(&base);
   if (st != EZO_OK) return st;
@@ -284,7 +287,8 @@ extern "C" ezo_status ezo_inflate_segment_noalloc(const ezo_robot* robot, const 
   NA_CUDA(cudaGetDevice(&dev));
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   v.n_sm = sms;
-  const int T_check = check_lanes(s_cap), T_bis = bisect_lanes(np, ezo_internal_robot_boxes(robot) || envf.e.n_box);
+  const int T_check = std::max(check_lanes(s_cap), t_min);
+  const int T_bis = std::max(bisect_lanes(np, ezo_internal_robot_boxes(robot) || envf.e.n_box), t_min);
   const int grid_s = (int)std::max<long long>(1, std::min<long long>(st_tiles * 8, (long long)sms * 16));
   const int grid_c = (int)std::max<long long>(1, std::min<long long>(st_tiles * T_check, (long long)sms * 16));
   const int grid_b = (int)std::max<long long>(1, std::min<long long>(bi_tiles * T_bis, (long long)sms * 16));

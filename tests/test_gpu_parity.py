@@ -436,6 +436,51 @@ def test_maximum_sizes_labels_match_oracle(ezo):
     assert float(x.sum()) == 2048.0
 
 
+# a collision-free seed segment of the maximum-size scene (oracle clearance
+# above 0.05 m at 41 points along it)
+MAX_V1 = np.array([-1.4826, -1.746, -2.3949, 2.4696, 1.6865, 1.8756, -1.3964, -2.1476, 2.3273, 1.6844, 1.2096,
+                   0.2345, 0.7711, 1.3283, 0.1993, 1.0377])
+MAX_V2 = np.array([-1.5623, -1.8776, -2.4, 2.4, 1.7994, 1.8865, -1.4513, -2.2256, 2.4, 1.8468, 1.2367, 0.112,
+                   0.6759, 1.4873, 0.2195, 0.8656])
+
+
+def test_maximum_sizes_segment_inflation(ezo):
+    """Algorithm 1 on the maximum-size scene (16 joints, 256 robot spheres,
+    4,096 obstacles): the batch raises its label and bisection lanes to the
+    fewest whose sphere centres fit in shared memory and refuses a shape
+    below them; the polytope contains the segment, the last round's sample
+    labels match the oracle outside the band, and 8 lanes give the same
+    polytope bit for bit."""
+    rd = wl.chain_robot(16, r=0.02, per_link=16)
+    env_np = wl.box_obstacles(41, 4096, box_lo=(-2.5, -2.5, -2.5), box_hi=(2.5, 2.5, 2.5), r_lo=0.02, r_hi=0.05)
+    line = MAX_V1[None, :] + np.linspace(0, 1, 41)[:, None] * (MAX_V2 - MAX_V1)[None, :]
+    assert orc.signed_distance(rd, env_np, line, chunk=4).min() > 0.05
+    robot, env = ezo.Robot(rd), ezo.Env(env_np)
+    prm = ezo.Params.make(eps=0.1, delta=0.05, n_p=1000, n_f=10, n_b=10, n_mix=30, seed=2)
+    bt = ezo.Batch(robot, [env], MAX_V1, MAX_V2, prm)
+    sh = bt.shape()
+    assert sh["check_lanes"] >= 4 and sh["bisect_lanes"] >= 4
+    with pytest.raises(ezo.EzoError):
+        bt.set_shape(sh["sample_fill_tiles"], 2, sh["bisect_lanes"])
+    bt.run()
+    ref = bt.segment(0)
+    assert ref.status in (ezo.SEG_ACCEPTED, ezo.SEG_MAX_ITER)
+    assert orc.segment_contained(ref.A, ref.b, MAX_V1, MAX_V2, tol=1e-12)
+    S = bt.read(0, "samples")[:, :48].T.astype(np.float64)
+    lab = bt.read(0, "labels")[:48].astype(bool)
+    want = orc.in_collision(rd, env_np, S, chunk=4)
+    diff = lab != want
+    if diff.any():
+        assert np.all(np.abs(orc.signed_distance(rd, env_np, S[diff], chunk=4)) < AMB)
+    bt.set_shape(sh["sample_fill_tiles"], 8, 8)
+    bt.reset()
+    bt.run()
+    got = bt.segment(0)
+    assert (got.status, got.rounds, got.checks) == (ref.status, ref.rounds, ref.checks)
+    np.testing.assert_array_equal(got.A, ref.A)
+    np.testing.assert_array_equal(got.b, ref.b)
+
+
 def test_round_replay_chain10(ezo):
     """Rounds of a 10-joint chain replayed step by step against the oracle
     (walks, labels, test, candidates, bisection, planes)."""
