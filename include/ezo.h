@@ -325,8 +325,10 @@ typedef struct {
   int32_t bisect_lanes;
 } ezo_shape;
 ezo_status ezo_batch_get_shape(const ezo_batch* batch, ezo_shape* shape);
-/* Sets the shape (EZO_ERR_INVALID_ARG for values out of range); a captured
- * graph is rebuilt at the next graph run. */
+/* Sets the shape (EZO_ERR_INVALID_ARG for values out of range, or for label
+ * or bisection lanes below the fewest whose sphere centres fit in shared
+ * memory, see ezo_batch_create); a captured graph is rebuilt at the next
+ * graph run. The autotuner skips such shapes. */
 ezo_status ezo_batch_set_shape(ezo_batch* batch, const ezo_shape* shape);
 /* Autotuner of the shape: runs the whole batch (host-loop mode, best of
  * `reps` timed runs after a warm-up) for the bisection lanes 4, 8, 16, 32, 96, 2, then
