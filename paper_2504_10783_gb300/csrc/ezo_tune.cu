@@ -78,7 +78,7 @@ extern "C" __attribute__((visibility("hidden"))) int ezo_internal_tuned_lanes(co
   };
   if (!g_autotune || N <= 0) return fit_up(rule(N));
   RobotDev head;
-  if (cudaMemcpy(&head, rd, sizeof(int) * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return rule(N);
+  if (cudaMemcpy(&head, rd, sizeof(int) * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return fit_up(rule(N));
   int dev = 0;
   cudaGetDevice(&dev);
   const int cls = size_class(N);
