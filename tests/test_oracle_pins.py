@@ -151,6 +151,17 @@ def test_chain_robot_layout():
             np.testing.assert_allclose(c[:, j], o[:, k] - (1 - f) * 0.15 * R[:, k][:, :, 0], atol=1e-12)
             if k >= 2:
                 np.testing.assert_allclose(c[:, j], o[:, k - 1] + f * (o[:, k] - o[:, k - 1]), atol=1e-12)
+    # the largest robot the library takes: 16 links of 16 spheres, f = (i + 1/2) / 16
+    m = wl.chain_robot(16, r=0.02, per_link=16)
+    assert m.sphere_r.shape == (256,) and np.all(m.sphere_r == 0.02)
+    assert m.self_pairs.shape == (16 * 16 * sum(max(0, 16 - (i + 2)) for i in range(1, 17)), 2) == (23296, 2)
+    q = wl.uniform_configs(6, m, 4)
+    R, o = orc.dh_frames(m, q)
+    c = orc.sphere_centres(m, q)
+    for k in (2, 9, 16):
+        for i in (0, 7, 15):
+            f = (i + 0.5) / 16
+            np.testing.assert_allclose(c[:, 16 * (k - 1) + i], o[:, k - 1] + f * (o[:, k] - o[:, k - 1]), atol=1e-12)
 
 
 def test_dh7_sphere_layout():
